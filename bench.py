@@ -1,0 +1,320 @@
+"""Benchmark of the GKE Parseval path on GB300.
+
+One step = one whole pass of the hot path over one batch of snapshots:
+Step-1 ensemble mean, fluctuations and in-plane products, per-wavenumber
+contractions over snapshots, inverse transforms to separation space and the
+Step-3 stencils, i.e. every GKE term for every (Y1 <= Y2) pair and every
+separation.  Throughput is counted in pair-snapshots per second:
+(number of pairs Y1 <= Y2) x (snapshots in the batch) / step time.
+
+Default workload: the Re_tau~200-shaped synthetic channel (nx = nz = 256,
+ny = 129 Chebyshev points, 16 snapshots), plain FP64 path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision f64|bf16x3]
+                    [--workload NAME] [--impl ours|reference]
+
+--impl reference times the CPU oracle (direct averages, C/OpenMP) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "GKE (y,y')-pair correlations/s & tensor-pipe %, split-BF16 vs FP64 at 1e-6 rel err"
+UNIT = "pair-snapshots/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 FMA rate: the nominal 1.25 TFLOP/s of GB300 over 152 SMs at the 2070 MHz
+# maximum clock is 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM.
+FP64_FLOP_PER_CLK_SM = 4.0
+N_SM = 152
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def correlator_cmac(wl, ns):
+    """Complex multiply-adds of the per-wavenumber contractions of one pass.
+
+    D (Hermitian, pairs y <= y'): K = 3 ns; square jobs over all ordered
+    pairs: E, F, QV (K = ns), X (3 ns), Gx, Gz (4 ns each)."""
+    Nk = wl.nz * wl.nxh
+    return Nk * ns * (3 * wl.npair + 14 * wl.ny * wl.ny)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return None
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r[1:]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------- CPU oracle
+def oracle_sample(wl, phys, npts, nplanes, seed=0):
+    """Time the oracle on npts sampled (pair, separation) points of the workload.
+
+    Returns (pair-snapshots/s extrapolated from points to whole pairs, seconds,
+    description)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    planes = sorted(rng.choice(wl.ny, size=nplanes, replace=False).tolist())
+    pts = []
+    for _ in range(npts):
+        a, b = sorted(rng.choice(planes, 2))
+        pts.append((a, b, int(rng.integers(wl.nz)), int(rng.integers(wl.nx))))
+    t0 = time.perf_counter()
+    oracle.points(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu, pts)
+    dt = time.perf_counter() - t0
+    pair_equiv = npts / float(wl.nx * wl.nz)
+    rate = pair_equiv * wl.nsnap / dt
+    desc = (f"{npts} (pair, separation) points on {nplanes} wall-normal planes of {wl.name}, "
+            f"all terms but the residual; rate = points/(nx nz) x snapshots / time")
+    return rate, dt, desc
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    wl = S.WORKLOADS[args.workload]
+    phys = S.physical(wl)
+    import oracle
+    oracle.build()
+    cores = os.cpu_count()
+    npts, nplanes = args.ref_points, 2
+    for _ in range(args.warmup):
+        oracle_sample(wl, phys, max(8, npts // 8), nplanes, seed=99)
+    times, rates = [], []
+    for k in range(args.steps):
+        r, dt, desc = oracle_sample(wl, phys, npts, nplanes, seed=k)
+        times.append(dt)
+        rates.append(r)
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl, args.precision),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, precision):
+    return {"workload": wl.name, "nx": wl.nx, "nz": wl.nz, "ny": wl.ny, "snapshots": wl.nsnap,
+            "pairs": wl.npair, "precision": precision, "Lx": round(wl.Lx, 6), "Lz": round(wl.Lz, 6),
+            "nu": wl.nu, "l2": "inputs and accumulators larger than L2 (no flush)"}
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = S.WORKLOADS[args.workload]
+    ns = wl.nsnap
+    prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3}[args.precision]
+    coef = S.coefficients(wl)
+    in_bytes = coef.nbytes
+    stream = torch.cuda.current_stream()
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), ns, prec,
+                      stream=stream.cuda_stream)
+    npair = N.gke_npair(plan)
+    f_dev = torch.from_numpy(coef).cuda()
+    terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        N.gke_compute(plan, f_dev, ns, terms)
+    torch.cuda.synchronize()
+    N.gke_set_timing(plan, True)
+    N.gke_stage_times(plan)            # clear
+    l0 = N.gke_launch_count(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            N.gke_compute(plan, f_dev, ns, terms)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    launches = N.gke_launch_count(plan) - l0
+    stage = N.gke_stage_times(plan)
+    N.gke_set_timing(plan, False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * npair * ns / (ms / 1e3)
+
+    # end to end through the public call with host buffers (pinned)
+    e2e = None
+    if not args.no_e2e:
+        f_host = torch.from_numpy(coef).pin_memory()
+        out_host = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=torch.float64).pin_memory()
+        N.gke_compute(plan, f_host, ns, out_host)     # warm-up (allocates staging once)
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ke):
+            N.gke_compute(plan, f_host, ns, out_host)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / ke
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": world * npair * ns / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": int(out_host.numel() * 8)}
+        del out_host, f_host
+    N.gke_destroy(plan)
+
+    # roofline of the dominant kernel (the correlator)
+    pk, pk_kind = peaks()
+    corr_ms = stage["correlate"] / args.steps
+    flops = 8.0 * correlator_cmac(wl, ns)
+    clocks = clk.summary()
+    if args.precision == "f64":
+        sm_mhz = pk.get("sm_max_mhz", 2070.0)
+        peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "k_correlate_f64", "achieved": flops / (corr_ms / 1e3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock (nominal 1.25 TFLOP/s FP64)"}
+    else:
+        peak = pk["bf16_tflops"]
+        bf16_flops = 6 * flops            # three-slice split: 6 slice products per FP64-equivalent product
+        roof = {"bound": "tensor", "kernel": "split correlator", "achieved": bf16_flops / (corr_ms / 1e3) / 1e12,
+                "peak": peak, "unit": "TFLOP/s", "peak_source": f"bf16_tflops ({pk_kind})"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["launch_ms"] = corr_ms
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        phys = S.physical(wl)
+        r, dt, desc = oracle_sample(wl, phys, args.cpu_points, 2, seed=123)
+        cpu = {"value": r, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "seconds": dt}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config_of(wl, args.precision), "parallelism": f"replicas{world}",
+                "stage_ms": {k: v / args.steps for k, v in stage.items()},
+                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
+                "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("f64", "bf16x3"), default="f64")
+    ap.add_argument("--workload", default=S.RETAU200.name, choices=sorted(S.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-points", type=int, default=512)
+    ap.add_argument("--ref-points", type=int, default=256)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

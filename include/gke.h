@@ -1,0 +1,174 @@
+/*
+ * gke.h -- C ABI of the GB300 Parseval evaluator of the Generalised
+ * Kolmogorov Equation (GKE) for plane channel flow.
+ *
+ * Method: Gatti, Remigi, Chiarini, Cimarelli, Quadrio, "An efficient
+ * numerical method for the Generalised Kolmogorov Equation".  The terms of
+ * the GKE for the plane channel (Sec. 2, Eq. 2-6) are written as sums of
+ * two-point correlations plus one-point moments (Sec. 3.1, Eq. 7); each
+ * correlation over the homogeneous directions is the inverse Fourier
+ * transform of a product of Fourier coefficients (Parseval, Eq. 8-9); the
+ * correlations are averaged over snapshots (Step 2, Sec. 3.2) and the
+ * wall-normal derivatives are taken afterwards with a 5-point finite
+ * difference stencil in Y1 = Y - r_y/2, Y2 = Y + r_y/2 (Step 3, Eq. 10-11),
+ * values across the diagonal Y2 < Y1 coming from r-inversion (Sec. 3.3).
+ *
+ * Conventions
+ *   - Grid: nx x nz points over the periodic box Lx x Lz; ny wall-normal
+ *     points y[0..ny) (strictly increasing, walls included, no ghost nodes).
+ *   - Input snapshot layout (complex128 = two doubles, re/im interleaved):
+ *       fields[nsnap][4][ny][nz][nx/2 + 1]   fields u, v, w, p (mean included)
+ *     Coefficients are forward-normalised,
+ *       a_hat(y, kz, kx) = 1/(nx nz) sum_{x,z} a(x, y, z) e^{-i (kx x + kz z)},
+ *     kz in FFT order (index m -> m for m < nz/2, m - nz above), kx = 0..nx/2:
+ *     exactly numpy/torch rfft2(a, norm="forward") over the last two axes.
+ *   - Pairs: the npair = ny (ny + 1) / 2 ordered pairs (i1, i2), i1 <= i2,
+ *     enumerated row-major (i1 outer); Y1 = y[i1], Y2 = y[i2];
+ *     Y = (Y1 + Y2)/2, r_y = Y2 - Y1 (gke_pair_labels).  Terms at Y2 < Y1
+ *     follow from the stored ones by r-inversion: A, phi, xi are even,
+ *     Phi_x, Phi_y, Phi_z odd under (Y1, Y2, r) -> (Y2, Y1, -r).
+ *   - Separations: index (m_z, m_x) in [0, nz) x [0, nx), FFT order,
+ *     r_x = m_x Lx / nx, r_z = m_z Lz / nz (periodic).
+ *   - Output terms (double):
+ *       terms[GKE_NTERM][npair][nz][nx]
+ *     in the order GKE_TERM_* below: <du^2>, Phi_x, Phi_y, Phi_z, phi, xi
+ *     and the residual of Eq. 3 (div_r Phi + d phi/dY - xi).
+ *   - Profiles (double): profiles[GKE_NPROF][ny], order GKE_PROF_*.
+ *
+ * Memory: every data pointer may be a device pointer or a host pointer
+ * (pageable or pinned); the library detects which.  Host inputs are staged
+ * through library-owned device buffers, so the caller may reuse them as soon
+ * as the call returns; device inputs must stay valid until the plan's stream
+ * reaches the next synchronisation point.  The caller owns every buffer it
+ * passes; the plan owns its workspaces and accumulators.
+ *
+ * Asynchrony: device-pointer calls are asynchronous on the plan's stream,
+ * except gke_finalize_terms, which synchronises the stream to read the
+ * non-finite-input flag before it returns.
+ *
+ * Errors: every call returns a gke_status; no call aborts or throws.
+ * gke_last_error(plan) (or NULL for gke_plan failures) gives a message.
+ */
+#ifndef GKE_H
+#define GKE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gke_plan_s* gke_plan_t;
+
+typedef enum {
+    GKE_OK = 0,
+    GKE_ERR_ARG = -1,          /* invalid argument (sizes, NULL pointers)            */
+    GKE_ERR_STATE = -2,        /* call out of order (no mean, no samples, finalized) */
+    GKE_ERR_OOM = -3,          /* device or host allocation failed                   */
+    GKE_ERR_CUDA = -4,         /* a CUDA runtime call failed                         */
+    GKE_ERR_NONFINITE = -5,    /* a NaN or Inf was found in the input               */
+    GKE_ERR_IO = -6,           /* checkpoint file could not be read or written       */
+    GKE_ERR_UNSUPPORTED = -7   /* grid size or option not supported by this build    */
+} gke_status;
+
+enum { GKE_PREC_F64 = 0,       /* plain FP64 correlator (DFMA)                        */
+       GKE_PREC_BF16X3 = 1 };  /* split-BF16 correlator on the tensor cores           */
+
+enum { GKE_TERM_A = 0, GKE_TERM_PHI_X, GKE_TERM_PHI_Y, GKE_TERM_PHI_Z, GKE_TERM_PHI,
+       GKE_TERM_XI, GKE_TERM_RESIDUAL, GKE_NTERM };
+
+enum { GKE_PROF_U = 0, GKE_PROF_V, GKE_PROF_W, GKE_PROF_P, GKE_PROF_DUDY, GKE_PROF_EPS, GKE_NPROF };
+
+typedef struct {
+    int nx, nz, ny;        /* grid; nx, nz powers of two in [8, 1024]; 5 <= ny <= 1024 */
+    double Lx, Lz;         /* box lengths of the homogeneous directions (> 0)            */
+    double nu;             /* kinematic viscosity (> 0)                                  */
+    const double* y;       /* host pointer, y[ny], strictly increasing; copied            */
+    int max_snap;          /* largest nsnap of any accumulate call (sizes workspaces)    */
+    int precision;         /* GKE_PREC_*                                                 */
+} gke_desc;
+
+/* Create a plan: validates the descriptor, computes the FD weights and
+ * twiddles on the host, allocates every workspace on the current device.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Nothing is
+ * allocated later except the staging buffer of a first host-output finalize. */
+gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* out);
+
+/* Step 1 (Sec. 3.2): add nsnap snapshots to the ensemble mean of u, v, w, p.
+ * Only the k = 0 coefficients are read.  Must precede the first
+ * gke_accumulate_snapshot; GKE_ERR_STATE afterwards.                         */
+gke_status gke_accumulate_mean(gke_plan_t plan, const void* fields, int nsnap);
+
+/* Alternative to gke_accumulate_mean: set the mean profiles directly,
+ * mean[4][ny] (u, v, w, p), host or device pointer.                           */
+gke_status gke_set_mean(gke_plan_t plan, const double* mean);
+
+/* Step 2 (Sec. 3.2): add nsnap (1 <= nsnap <= max_snap) snapshots to the
+ * two-point statistics.  The first call freezes the mean (GKE_ERR_STATE if
+ * none was given).  Linear in the snapshots: any split into calls gives the
+ * same result up to rounding.  GKE_ERR_STATE after gke_finalize_terms until
+ * gke_reset.                                                                 */
+gke_status gke_accumulate_snapshot(gke_plan_t plan, const void* fields, int nsnap);
+
+/* Step 3 (Sec. 3.2): write all terms for every pair and separation and,
+ * if profiles != NULL, the profiles.  GKE_ERR_STATE without samples;
+ * GKE_ERR_NONFINITE if any accumulated input held a NaN or Inf (outputs are
+ * then undefined).  May be called again; accumulators are left unchanged.  */
+gke_status gke_finalize_terms(gke_plan_t plan, double* terms, double* profiles);
+
+/* One full pass: gke_accumulate_mean + gke_accumulate_snapshot +
+ * gke_finalize_terms on a fresh plan state, staging host data once.        */
+gke_status gke_compute(gke_plan_t plan, const void* fields, int nsnap, double* terms, double* profiles);
+
+/* Host arrays of the pair labels: Y[npair], ry[npair], i1[npair], i2[npair]
+ * (any may be NULL).                                                         */
+gke_status gke_pair_labels(gke_plan_t plan, double* Y, double* ry, int* i1, int* i2);
+
+/* Sizes: number of pairs, and bytes of the terms array.                     */
+long long gke_npair(gke_plan_t plan);
+long long gke_terms_bytes(gke_plan_t plan);
+
+/* Forget all accumulated statistics and the mean.                            */
+gke_status gke_reset(gke_plan_t plan);
+
+/* Save / restore the accumulated state (mean sums, one-point sums, spectral
+ * sums, counts) to / from a file; linear, so restored partial sums combine
+ * exactly with further calls (the paper's merge of independent jobs,
+ * Sec. 3.4).  gke_merge adds a checkpoint's sums to the plan's.             */
+gke_status gke_checkpoint(gke_plan_t plan, const char* path);
+gke_status gke_restore(gke_plan_t plan, const char* path);
+gke_status gke_merge(gke_plan_t plan, const char* path);
+
+/* Host utility (no GPU needed): the 5-point first-derivative weights the
+ * plan uses at row j of the grid y[ny] (Step 3, Sec. 3.2): w[0..5) on rows
+ * l0..l0+4, l0 = clamp(j - 2, 0, ny - 5), exact for polynomials of degree
+ * <= 4.  Returns l0, or -1 on bad arguments.                               */
+int gke_fd_weights(const double* y, int ny, int j, double* w);
+
+/* Diagnostics.  While timing is on, the plan records CUDA events on its
+ * stream around each stage of the path; gke_stage_times synchronises the
+ * stream, writes the device milliseconds summed per stage since the last
+ * read into ms[GKE_NSTAGE] and clears them.  gke_launch_count is the number
+ * of kernels the plan has launched since it was created.                    */
+enum { GKE_STAGE_MEAN = 0,       /* Step 1 ensemble mean                          */
+       GKE_STAGE_PRODUCTS,       /* fluctuations, in-plane products, one-point sums */
+       GKE_STAGE_CORRELATE,      /* per-wavenumber contractions over snapshots    */
+       GKE_STAGE_TERMS,          /* spectral combinations + inverse transforms    */
+       GKE_STAGE_STENCIL,        /* Step 3 Y1/Y2 finite differences               */
+       GKE_NSTAGE };
+gke_status gke_set_timing(gke_plan_t plan, int on);
+gke_status gke_stage_times(gke_plan_t plan, double* ms);
+long long gke_launch_count(gke_plan_t plan);
+
+/* Message of the last failed call on this plan (plan == NULL: last gke_plan
+ * failure of the calling thread).  Valid until the next call on the plan.  */
+const char* gke_last_error(gke_plan_t plan);
+
+/* Free every resource of the plan (synchronises its stream).  NULL is a no-op. */
+void gke_destroy(gke_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKE_H */

@@ -1,0 +1,111 @@
+// gke_correlate_f64.cu -- plain FP64 correlator.
+//
+// For every wavenumber k the paper's Parseval step (Sec. 3.1, Eq. 8-9) needs
+// sums over snapshots of conj(a_hat(y, k)) b_hat(y', k) for the field pairs
+// of the expansion (Eq. 7).  Per k these are small dense complex products
+//   S(y, y') = sum_t c_t sum_s conj(A_t[s][y]) B_t[s][y']
+// over the operand blocks Xop[f][k][s][y].  The contractions ("jobs"):
+//   D   = sum_i conj(u_i) u_i                    (Hermitian: pairs y <= y')
+//   E   = conj(u) v,   F = conj(p) v
+//   Gx  = conj(q) u + 2 [conj(uu) u + conj(uv) v + conj(uw) w]
+//   QV  = conj(q) v,   X = conj(uv) u + conj(vv) v + conj(vw) w
+//   Gz  = conj(q) w + 2 [conj(uw) u + conj(vw) v + conj(ww) w]
+// (the y-flux triple terms are QV + 2 X and QV - 2 X, formed later).
+//
+// CTA = one wavenumber and one job; it walks 32 x 32 tiles of (y, y'), each
+// thread holding a 2 x 2 block of complex accumulators.  DFMA bound.
+#include "gke_common.cuh"
+#include "gke_kernels.h"
+
+namespace gke {
+
+struct JobDesc { int nterm; int fa[4]; int fb[4]; double c[4]; };
+
+__constant__ JobDesc c_jobs[NJSQ + 1];   // index NJSQ = D
+
+void upload_jobs(cudaStream_t st)
+{
+    JobDesc h[NJSQ + 1] = {
+        /* E  */ {1, {F_U, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
+        /* F  */ {1, {F_P, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
+        /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {F_U, F_U, F_V, F_W}, {1, 2, 2, 2}},
+        /* QV */ {1, {F_Q, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
+        /* X  */ {3, {F_UV, F_VV, F_VW, 0}, {F_U, F_V, F_W, 0}, {1, 1, 1, 0}},
+        /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {F_W, F_U, F_V, F_W}, {1, 2, 2, 2}},
+        /* D  */ {3, {F_U, F_V, F_W, 0}, {F_U, F_V, F_W, 0}, {1, 1, 1, 0}},
+    };
+    cudaMemcpyToSymbolAsync(c_jobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
+}
+
+#define CT 32       // tile edge
+#define SCH 8       // snapshots per shared-memory chunk
+
+__global__ void __launch_bounds__(256)
+k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, int beta,
+                zd* __restrict__ acc_sq, zd* __restrict__ acc_D)
+{
+    __shared__ zd As[SCH][CT];
+    __shared__ zd Bs[SCH][CT];
+    const int k = blockIdx.x, job = blockIdx.y;
+    const bool herm = (job == NJSQ);
+    const JobDesc jd = c_jobs[job];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int nt = (ny + CT - 1) / CT;
+    for (int tb0 = 0; tb0 < nt; ++tb0) {
+        for (int tb1 = herm ? tb0 : 0; tb1 < nt; ++tb1) {
+            const int y0 = tb0 * CT, y1 = tb1 * CT;
+            zd acc[2][2];
+            #pragma unroll
+            for (int a = 0; a < 2; ++a)
+                #pragma unroll
+                for (int b = 0; b < 2; ++b) acc[a][b] = mk(0.0, 0.0);
+            for (int t = 0; t < jd.nterm; ++t) {
+                const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+                const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+                const double c = jd.c[t];
+                for (int s0 = 0; s0 < ns; s0 += SCH) {
+                    __syncthreads();
+                    for (int e = threadIdx.x; e < SCH * CT; e += blockDim.x) {
+                        int ss = e / CT, yy = e - ss * CT;
+                        int s = s0 + ss;
+                        zd va = mk(0.0, 0.0), vb = mk(0.0, 0.0);
+                        if (s < ns && y0 + yy < ny) va = A[(long long)s * ny + y0 + yy];
+                        if (s < ns && y1 + yy < ny) vb = B[(long long)s * ny + y1 + yy];
+                        As[ss][yy] = c * va;
+                        Bs[ss][yy] = vb;
+                    }
+                    __syncthreads();
+                    #pragma unroll
+                    for (int ss = 0; ss < SCH; ++ss) {
+                        zd a0 = As[ss][ty], a1 = As[ss][ty + 16];
+                        zd b0 = Bs[ss][tx], b1 = Bs[ss][tx + 16];
+                        // conj(a) * b
+                        acc[0][0].x += a0.x * b0.x + a0.y * b0.y; acc[0][0].y += a0.x * b0.y - a0.y * b0.x;
+                        acc[0][1].x += a0.x * b1.x + a0.y * b1.y; acc[0][1].y += a0.x * b1.y - a0.y * b1.x;
+                        acc[1][0].x += a1.x * b0.x + a1.y * b0.y; acc[1][0].y += a1.x * b0.y - a1.y * b0.x;
+                        acc[1][1].x += a1.x * b1.x + a1.y * b1.y; acc[1][1].y += a1.x * b1.y - a1.y * b1.x;
+                    }
+                }
+            }
+            #pragma unroll
+            for (int a = 0; a < 2; ++a)
+                #pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    int y = y0 + ty + 16 * a, yp = y1 + tx + 16 * b;
+                    if (y >= ny || yp >= ny) continue;
+                    zd* dst;
+                    if (herm) {
+                        if (yp < y) continue;
+                        dst = acc_D + pair_index(y, yp, ny) * Nk + k;
+                    } else {
+                        dst = acc_sq + (((long long)job * ny + y) * ny + yp) * Nk + k;
+                    }
+                    zd v = acc[a][b];
+                    if (beta) v = v + *dst;
+                    *dst = v;
+                }
+        }
+    }
+}
+
+}  // namespace gke
