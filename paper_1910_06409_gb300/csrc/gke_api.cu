@@ -523,6 +523,10 @@ extern "C" gke_status gke_finalize_terms(gke_plan_t p, double* terms, double* pr
     CUDA_TRY(p, cudaMemcpyAsync(&bad, p->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, p->st));
     CUDA_TRY(p, cudaStreamSynchronize(p->st));
     p->finalized = true;
+    if (p->d.precision == GKE_PREC_BF16X3) {
+        gke_status ss = split_check(p->split, p->st, p->err);
+        if (ss != GKE_OK) return ss;
+    }
     if (bad) return fail(p, GKE_ERR_NONFINITE, "non-finite value in the accumulated input");
     return GKE_OK;
 }

@@ -20,7 +20,7 @@ namespace gke {
 // correlated fields (Sec. 3.1: the linear fields and the in-plane products)
 enum Field { F_U = 0, F_V, F_W, F_P, F_UU, F_VV, F_WW, F_UV, F_UW, F_VW, F_Q, NFIELD };
 // cross contractions over snapshots (ordered pairs); D (Hermitian) is kept apart
-enum JobSq { J_E = 0, J_F, J_GX, J_QV, J_X, J_GZ, NJSQ };
+enum JobSq { J_E = 0, J_F, J_GX, J_QV, J_X, J_GZ, NJSQ };   // J_X holds X2 = 2 X
 // output terms
 enum Term { T_A = 0, T_PHIX, T_PHIY, T_PHIZ, T_PHI, T_XI, T_RES, NTERM };
 // one-point statistics per y (FP64 sums over snapshots and the plane)

@@ -8,9 +8,9 @@
 //   D   = sum_i conj(u_i) u_i                    (Hermitian: pairs y <= y')
 //   E   = conj(u) v,   F = conj(p) v
 //   Gx  = conj(q) u + 2 [conj(uu) u + conj(uv) v + conj(uw) w]
-//   QV  = conj(q) v,   X = conj(uv) u + conj(vv) v + conj(vw) w
+//   QV  = conj(q) v,   X2 = 2 [conj(uv) u + conj(vv) v + conj(vw) w]
 //   Gz  = conj(q) w + 2 [conj(uw) u + conj(vw) v + conj(ww) w]
-// (the y-flux triple terms are QV + 2 X and QV - 2 X, formed later).
+// (the y-flux triple terms are QV + X2 and QV - X2, formed later).
 //
 // CTA = one wavenumber and one job; it walks 32 x 32 tiles of (y, y'), each
 // thread holding a 2 x 2 block of complex accumulators.  DFMA bound.
@@ -30,7 +30,7 @@ void upload_jobs(cudaStream_t st)
         /* F  */ {1, {F_P, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
         /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {F_U, F_U, F_V, F_W}, {1, 2, 2, 2}},
         /* QV */ {1, {F_Q, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
-        /* X  */ {3, {F_UV, F_VV, F_VW, 0}, {F_U, F_V, F_W, 0}, {1, 1, 1, 0}},
+        /* X2 */ {3, {F_UV, F_VV, F_VW, 0}, {F_U, F_V, F_W, 0}, {2, 2, 2, 0}},
         /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {F_W, F_U, F_V, F_W}, {1, 2, 2, 2}},
         /* D  */ {3, {F_U, F_V, F_W, 0}, {F_U, F_V, F_W, 0}, {1, 1, 1, 0}},
     };

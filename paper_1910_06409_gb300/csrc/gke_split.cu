@@ -1,17 +1,452 @@
-// gke_split.cu -- split-precision correlator (placeholder until the tcgen05
-// kernel lands): reports GKE_ERR_UNSUPPORTED.
+// gke_split.cu -- split-precision correlator on the 5th-generation tensor cores.
+//
+// The per-wavenumber contractions of the Parseval step (Sec. 3.1, Eq. 8-9),
+//   S(y, y') = sum_t sum_s conj(A_t[s][y]) B_t[s][y'],
+// written as real products (Re S = ar br + ai bi, Im S = ar bi - ai br) with
+// every real operand split into three BF16 slices x = x0 + x1 + x2 (each the
+// BF16 rounding of what the previous ones leave; BF16 has the FP32 exponent
+// range, so every slice is relative to its own value and no scaling is
+// needed).  The six slice products with i + j <= 2 keep ~24 significant bits:
+//   x y ~ x0 y0 + x0 y1 + x1 y0 + x0 y2 + x1 y1 + x2 y0,
+// accumulated in FP32 in tensor memory, then added to the FP64 spectral sums.
+// FP32 accumulation rounds against the running sum, so the small cross-slice
+// products of all terms go first and the large x0 y0 products last: an output
+// then sees 2 T G large additions (T terms, G snapshot groups) instead of 12 T G.
+//
+// Tensor-core mapping (one CTA = one wavenumber k, one contraction, one
+// 128 x 128 tile of (y, y')): D[128 x 256] in TMEM, columns 0..127 = Re,
+// 128..255 = Im.  Per term, snapshot group of 16 and slice pair (i, j):
+//   mma(A = ar_i, B = [br_j | bi_j])      -> Re += ar br, Im += ar bi
+//   mma(A = ai_i, B = [bi_j | -br_j])     -> Re += ai bi, Im -= ai br
+// (M = 128, N = 256, K = 16, BF16 in, FP32 accumulate).  The B block holds
+// the rows br, bi, -br back to back, so both B views are 256-row windows of
+// it.  Operands are written by k_split_prep_* in the canonical K-major
+// no-swizzle layout (8 x 16-byte core matrices; K-adjacent core matrices LBO
+// bytes apart, M/N-adjacent ones SBO = 128 bytes apart) and copied to shared
+// memory by the bulk-copy engine (cp.async.bulk, mbarrier transaction count).
+// Wall-normal sizes ny = 128 m + 1 (Chebyshev-Gauss-Lobatto grids) leave one
+// row and one column outside the tiles; k_corr_edge does those in FP32 on the
+// CUDA cores.
+#include <cuda_bf16.h>
+
 #include "gke_split.h"
+#include "gke_kernels.h"
 
 namespace gke {
 
-gke_status split_alloc(SplitWork& w, int, int, int) { w.ops = nullptr; w.ops_bytes = 0; return GKE_OK; }
-cudaError_t split_setup(cudaStream_t) { return cudaSuccess; }
-gke_status split_correlate(SplitWork&, const zd*, int, int, int, int, zd*, zd*, cudaStream_t, std::string& err, int* launches)
-{
-    *launches = 0;
-    err = "split-precision correlator not available in this build";
-    return GKE_ERR_UNSUPPORTED;
+typedef __nv_bfloat16 bf16;
+
+constexpr int TM = 128;                 // tile rows (y) = tile cols (y')
+constexpr int KS = 16;                  // snapshots per group = one MMA K step
+constexpr int A_BLK = TM * KS;          // bf16 per A block (128 rows x 16)
+constexpr int B_BLK = 3 * TM * KS;      // bf16 per B block (br | bi | -br rows x 16)
+constexpr int A_STAGE = 6 * A_BLK;      // slices x parts (re, im), slice-major
+constexpr int B_STAGE = 3 * B_BLK;      // slices
+constexpr int SM_A = A_STAGE * 2;       // 24576 bytes
+constexpr int SM_B = B_STAGE * 2;       // 36864 bytes
+constexpr int SM_BAR = SM_A + SM_B;     // mbarriers + TMEM address slot
+constexpr int SM_TOTAL = 100 * 1024;    // at most two CTAs per SM: 2 x 256 TMEM columns
+constexpr int A_LBO = (TM / 8) * 128;       // 2048: K-adjacent core matrices in an A block
+constexpr int B_LBO = (3 * TM / 8) * 128;   // 6144: K-adjacent core matrices in a B block
+constexpr int CM_SBO = 128;                 // M/N-adjacent core matrices
+constexpr int TMEM_COLS = 256;
+
+// instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16 (7-9, 10-12),
+// K-major A and B (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+
+struct TcJob { int nterm; int fa[4]; int fb[4]; };
+__constant__ TcJob c_tcjobs[NJSQ + 1];
+
+// cross-slice pairs (i, j), 0 < i + j <= 2; the pair (0, 0) goes last
+__constant__ int c_pi[5] = {1, 0, 2, 1, 0};
+__constant__ int c_pj[5] = {1, 2, 0, 0, 1};
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
 }
-void split_free(SplitWork& w) { w.ops = nullptr; }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait: false after ~2^22 polls with back-off (about a second)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try(b, parity)) return true;
+        if (it > 32) __nanosleep(200);
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29),
+// SBO >> 4 (32-45), version 1 (46-47), no swizzle (61-63 = 0)
+__device__ __forceinline__ uint64_t sdesc(const void* p, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((su32(p) & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(dtm), "l"(da), "l"(db), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                   "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                   "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------ operand prep
+// element (row r, k) of a core-matrix tile whose K-adjacent core matrices are
+// `rows/8` cores apart: ((k/8) * rows/8 + r/8) * 64 + (r%8) * 8 + k%8
+__device__ __forceinline__ int cm_index(int r, int kk, int rows) {
+    return (((kk >> 3) * (rows >> 3) + (r >> 3)) << 6) + ((r & 7) << 3) + (kk & 7);
+}
+
+__device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
+    s0 = __float2bfloat16_rn(x);
+    float r1 = x - __bfloat162float(s0);
+    s1 = __float2bfloat16_rn(r1);
+    float r2 = r1 - __bfloat162float(s1);
+    s2 = __float2bfloat16_rn(r2);
+}
+
+// Aop[k][f][g][mt][slice * 2 + part][A_BLK]; products (uu .. vw) carry the
+// factor 2 of the expansion; rows >= cov and snapshots >= ns are zero.
+__global__ void k_split_prep_A(const zd* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
+                               bf16* __restrict__ Aop)
+{
+    long long b = blockIdx.x;
+    const int mt = (int)(b % MT); b /= MT;
+    const int g = (int)(b % G); b /= G;
+    const int f = (int)(b % NFIELD);
+    const int k = (int)(b / NFIELD);
+    const double sc = (f >= F_UU && f <= F_VW) ? 2.0 : 1.0;
+    bf16* dst = Aop + ((((long long)k * NFIELD + f) * G + g) * MT + mt) * (long long)A_STAGE;
+    for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
+        const int s_l = e / TM, r = e - s_l * TM;
+        const int y = mt * TM + r, s = g * KS + s_l;
+        zd v = mk(0.0, 0.0);
+        if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k) * ns + s) * ny + y];
+        bf16 a0, a1, a2, b0, b1, b2;
+        split3((float)(sc * v.x), a0, a1, a2);
+        split3((float)(sc * v.y), b0, b1, b2);
+        const int idx = cm_index(r, s_l, TM);
+        dst[0 * A_BLK + idx] = a0; dst[2 * A_BLK + idx] = a1; dst[4 * A_BLK + idx] = a2;
+        dst[1 * A_BLK + idx] = b0; dst[3 * A_BLK + idx] = b1; dst[5 * A_BLK + idx] = b2;
+    }
+}
+
+// Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi | -br
+__global__ void k_split_prep_B(const zd* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
+                               bf16* __restrict__ Bop)
+{
+    long long b = blockIdx.x;
+    const int nt = (int)(b % MT); b /= MT;
+    const int g = (int)(b % G); b /= G;
+    const int fb = (int)(b % 3);
+    const int k = (int)(b / 3);
+    bf16* dst = Bop + ((((long long)k * 3 + fb) * G + g) * MT + nt) * (long long)B_STAGE;
+    for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
+        const int s_l = e / TM, r = e - s_l * TM;
+        const int y = nt * TM + r, s = g * KS + s_l;
+        zd v = mk(0.0, 0.0);
+        if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k) * ns + s) * ny + y];
+        bf16 r0, r1, r2, i0, i1, i2;
+        split3((float)v.x, r0, r1, r2);
+        split3((float)v.y, i0, i1, i2);
+        const bf16 sr[3] = {r0, r1, r2}, si[3] = {i0, i1, i2};
+        for (int sl = 0; sl < 3; ++sl) {
+            bf16* d = dst + sl * B_BLK;
+            d[cm_index(r, s_l, 3 * TM)] = sr[sl];
+            d[cm_index(TM + r, s_l, 3 * TM)] = si[sl];
+            d[cm_index(2 * TM + r, s_l, 3 * TM)] = __hneg(sr[sl]);
+        }
+    }
+}
+
+// ------------------------------------------------------ tensor-core kernel
+__device__ __forceinline__ void decode_tile(int jt, int MT, int& job, int& mt, int& nt)
+{
+    const int sq = MT * MT;
+    if (jt < NJSQ * sq) {
+        job = jt / sq;
+        int r = jt - job * sq;
+        mt = r / MT;
+        nt = r - mt * MT;
+    } else {
+        job = NJSQ;
+        int r = jt - NJSQ * sq;
+        mt = 0;
+        while (r >= MT - mt) { r -= MT - mt; ++mt; }
+        nt = mt + r;
+    }
+}
+
+__global__ void __launch_bounds__(128, 1)
+k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, int G, int MT, int ny, int cov,
+          int beta, zd* __restrict__ acc_sq, zd* __restrict__ acc_D, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + SM_A;
+    uint64_t* bar_ld = (uint64_t*)(smem + SM_BAR);
+    uint64_t* bar_mma = bar_ld + 1;
+    uint32_t* tslot = (uint32_t*)(bar_ld + 2);
+    int* s_ok = (int*)(tslot + 1);
+    const int njt = NJSQ * MT * MT + MT * (MT + 1) / 2;
+    const int k = (int)(blockIdx.x / njt);
+    int job, mt, nt;
+    decode_tile((int)(blockIdx.x % njt), MT, job, mt, nt);
+    const int warp = threadIdx.x >> 5;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar_ld, 1);
+        mbar_init(bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // once any CTA has reported a timed-out wait, the rest skip their work
+        *s_ok = (*(volatile int*)err == 0) ? 1 : 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                     "r"(TMEM_COLS) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    if (threadIdx.x == 0 && *s_ok) {
+        const TcJob jd = c_tcjobs[job];
+        uint32_t ph_ld = 0, ph_mma = 0, acc = 0;
+        bool ok = true;
+        // pass 0: the cross-slice products of every term; pass 1: x0 y0 only
+        for (int pass = 0; pass < 2 && ok; ++pass) {
+            const uint32_t bytes_a = pass ? 2 * A_BLK * 2 : SM_A;
+            const uint32_t bytes_b = pass ? B_BLK * 2 : SM_B;
+            for (int t = 0; t < jd.nterm && ok; ++t) {
+                for (int g = 0; g < G && ok; ++g) {
+                    const bf16* srcA =
+                        Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + mt) * (long long)A_STAGE;
+                    const bf16* srcB =
+                        Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + nt) * (long long)B_STAGE;
+                    mbar_expect_tx(bar_ld, bytes_a + bytes_b);
+                    bulk_g2s(sA, srcA, bytes_a, bar_ld);
+                    bulk_g2s(sB, srcB, bytes_b, bar_ld);
+                    if (!mbar_wait(bar_ld, ph_ld)) {
+                        ok = false;
+                        mbar_wait(bar_ld, ph_ld);          // let copies in flight land before leaving
+                        break;
+                    }
+                    ph_ld ^= 1;
+                    tc_fence_after();
+                    const int npr = pass ? 1 : 5;
+                    for (int pr = 0; pr < npr; ++pr) {
+                        const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
+                        const uint64_t a_re = sdesc(sA + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
+                        const uint64_t a_im = sdesc(sA + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
+                        const uint64_t b_1 = sdesc(sB + j * B_BLK * 2, B_LBO, CM_SBO);
+                        const uint64_t b_2 = sdesc(sB + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
+                        mma_bf16(tmem, a_re, b_1, IDESC, acc);
+                        acc = 1;
+                        mma_bf16(tmem, a_im, b_2, IDESC, 1);
+                    }
+                    mma_commit(bar_mma);
+                    if (!mbar_wait(bar_mma, ph_mma)) {
+                        ok = false;
+                        mbar_wait(bar_mma, ph_mma);
+                        break;
+                    }
+                    ph_mma ^= 1;
+                }
+            }
+        }
+        if (!ok) { *s_ok = 0; atomicExch(err, 1); }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (*s_ok) {
+        const int row = threadIdx.x;
+        const int y = mt * TM + row;
+        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < 4; ++c) {
+            uint32_t re[32], im[32];
+            tmem_ld32(tbase + c * 32, re);
+            tmem_ld32(tbase + 128 + c * 32, im);
+            tmem_ld_wait();
+            if (y < cov) {
+                #pragma unroll 4
+                for (int j = 0; j < 32; ++j) {
+                    const int yp = nt * TM + c * 32 + j;
+                    if (yp >= cov) break;
+                    zd v = mk((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
+                    zd* dst;
+                    if (job == NJSQ) {
+                        if (yp < y) continue;
+                        dst = acc_D + pair_index(y, yp, ny) * Nk + k;
+                    } else {
+                        dst = acc_sq + (((long long)job * ny + y) * ny + yp) * Nk + k;
+                    }
+                    if (beta) v = v + *dst;
+                    *dst = v;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------- edge rows / columns (FP32)
+// Entries with y >= cov or y' >= cov (the last row / column of a 128 m + 1
+// grid), FP32 products and sums on the CUDA cores, same coefficients.
+__global__ void k_corr_edge(const zd* __restrict__ Xop, int ns, int ny, int Nk, int cov, int beta,
+                            zd* __restrict__ acc_sq, zd* __restrict__ acc_D)
+{
+    const int k = blockIdx.x, job = blockIdx.y;
+    const TcJob jd = c_tcjobs[job];
+    const int ne = ny - cov;
+    const int n_row = ne * ny, n_col = cov * ne;
+    for (int e = threadIdx.x; e < n_row + n_col; e += blockDim.x) {
+        int y, yp;
+        if (e < n_row) { y = cov + e / ny; yp = e % ny; }
+        else { int r = e - n_row; y = r / ne; yp = cov + r % ne; }
+        if (job == NJSQ && yp < y) continue;
+        float sr = 0.f, si = 0.f;
+        for (int t = 0; t < jd.nterm; ++t) {
+            const float c = (jd.fa[t] >= F_UU && jd.fa[t] <= F_VW) ? 2.f : 1.f;
+            const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+            const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+            for (int s = 0; s < ns; ++s) {
+                const zd a = A[(long long)s * ny + y], b = B[(long long)s * ny + yp];
+                const float ar = c * (float)a.x, ai = c * (float)a.y, br = (float)b.x, bi = (float)b.y;
+                sr = fmaf(ar, br, fmaf(ai, bi, sr));
+                si = fmaf(ar, bi, fmaf(-ai, br, si));
+            }
+        }
+        zd v = mk((double)sr, (double)si);
+        zd* dst = (job == NJSQ) ? acc_D + pair_index(y, yp, ny) * Nk + k
+                                : acc_sq + (((long long)job * ny + y) * ny + yp) * Nk + k;
+        if (beta) v = v + *dst;
+        *dst = v;
+    }
+}
+
+// ------------------------------------------------------------------- host
+static void tile_geometry(int ny, int& MT, int& cov)
+{
+    if (ny > 1 && (ny - 1) % TM == 0) { MT = (ny - 1) / TM; cov = ny - 1; }
+    else { MT = (ny + TM - 1) / TM; cov = ny; }
+}
+
+gke_status split_alloc(SplitWork& w, int ny, int ns, int Nk)
+{
+    int MT, cov;
+    tile_geometry(ny, MT, cov);
+    const int G = (ns + KS - 1) / KS;
+    w.a_bytes = (size_t)Nk * NFIELD * G * MT * A_STAGE * sizeof(bf16);
+    w.b_bytes = (size_t)Nk * 3 * G * MT * B_STAGE * sizeof(bf16);
+    if (cudaMalloc(&w.ops, w.a_bytes + w.b_bytes) != cudaSuccess) { w.ops = nullptr; return GKE_ERR_OOM; }
+    if (cudaMalloc((void**)&w.err, sizeof(int)) != cudaSuccess) { w.err = nullptr; return GKE_ERR_OOM; }
+    if (cudaMemset(w.err, 0, sizeof(int)) != cudaSuccess) return GKE_ERR_CUDA;
+    w.ops_bytes = w.a_bytes + w.b_bytes;
+    return GKE_OK;
+}
+
+cudaError_t split_setup(cudaStream_t st)
+{
+    TcJob h[NJSQ + 1] = {
+        /* E  */ {1, {F_U, 0, 0, 0}, {1, 0, 0, 0}},
+        /* F  */ {1, {F_P, 0, 0, 0}, {1, 0, 0, 0}},
+        /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {0, 0, 1, 2}},
+        /* QV */ {1, {F_Q, 0, 0, 0}, {1, 0, 0, 0}},
+        /* X2 */ {3, {F_UV, F_VV, F_VW, 0}, {0, 1, 2, 0}},
+        /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {2, 0, 1, 2}},
+        /* D  */ {3, {F_U, F_V, F_W, 0}, {0, 1, 2, 0}},
+    };
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_tcjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
+}
+
+gke_status split_correlate(SplitWork& w, const zd* Xop, int ns, int ny, int Nk, int beta, zd* acc_sq, zd* acc_D,
+                           cudaStream_t st, std::string& err, int* launches)
+{
+    int MT, cov;
+    tile_geometry(ny, MT, cov);
+    const int G = (ns + KS - 1) / KS;
+    bf16* Aop = (bf16*)w.ops;
+    bf16* Bop = (bf16*)((char*)w.ops + (size_t)Nk * NFIELD * G * MT * A_STAGE * sizeof(bf16));
+    *launches = 0;
+    k_split_prep_A<<<(unsigned)((long long)Nk * NFIELD * G * MT), 256, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Aop);
+    k_split_prep_B<<<(unsigned)((long long)Nk * 3 * G * MT), 256, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Bop);
+    const long long njt = (long long)NJSQ * MT * MT + MT * (MT + 1) / 2;
+    k_corr_tc<<<(unsigned)(Nk * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Nk, G, MT, ny, cov, beta, acc_sq, acc_D, w.err);
+    *launches = 3;
+    if (cov < ny) {
+        k_corr_edge<<<dim3(Nk, NJSQ + 1), 128, 0, st>>>(Xop, ns, ny, Nk, cov, beta, acc_sq, acc_D);
+        *launches += 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { err = std::string("split correlator launch: ") + cudaGetErrorString(e); return GKE_ERR_CUDA; }
+    return GKE_OK;
+}
+
+gke_status split_check(SplitWork& w, cudaStream_t st, std::string& err)
+{
+    if (!w.err) return GKE_OK;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, w.err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        err = "split correlator: cannot read the error flag";
+        return GKE_ERR_CUDA;
+    }
+    if (h) { err = "split correlator: a tensor-core pipeline wait timed out"; return GKE_ERR_CUDA; }
+    return GKE_OK;
+}
+
+void split_free(SplitWork& w)
+{
+    if (w.ops) cudaFree(w.ops);
+    if (w.err) cudaFree(w.err);
+    w.ops = nullptr;
+    w.err = nullptr;
+}
 
 }  // namespace gke

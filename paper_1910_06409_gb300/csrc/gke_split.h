@@ -9,14 +9,16 @@
 namespace gke {
 
 struct SplitWork {
-    void* ops = nullptr;        // split operand planes
-    size_t ops_bytes = 0;
+    void* ops = nullptr;        // BF16 slice operands (A blocks, then B blocks)
+    size_t ops_bytes = 0, a_bytes = 0, b_bytes = 0;
+    int* err = nullptr;         // device flag: a pipeline wait timed out
 };
 
 gke_status split_alloc(SplitWork& w, int ny, int ns, int Nk);
 cudaError_t split_setup(cudaStream_t st);
 gke_status split_correlate(SplitWork& w, const zd* Xop, int ns, int ny, int Nk, int beta, zd* acc_sq, zd* acc_D,
                            cudaStream_t st, std::string& err, int* launches);
+gke_status split_check(SplitWork& w, cudaStream_t st, std::string& err);
 void split_free(SplitWork& w);
 
 }  // namespace gke

@@ -7,7 +7,8 @@
 //
 // With S0 = D, S1 = E + E^H, S2 = E^H - E, S3 = F + F^H, S4 = Gx - Gx^H,
 // S5 = Gy - Gy^H, S6 = Gz - Gz^H, S7 = H + H^H (X^H(y, y') = conj X(y', y),
-// Gy = QV + 2X, H = QV - 2X), every term is one inverse transform of a
+// Gy = QV + X2, H = QV - X2 with X2 the stored 2 sum_i conj(u_i v) u_i),
+// every term is one inverse transform of a
 // linear combination of the S_n plus a part that depends only on (Y1, Y2):
 //   A     = F^-1[-2 S0]                                 + <q>1 + <q>2
 //   Phi_x = F^-1[S4 + (-2 dU + 4 i nu kx) S0]           + <qu>2 - <qu>1 + dU (<q>1 + <q>2)
@@ -41,8 +42,8 @@ __device__ __forceinline__ void combos(const zd* __restrict__ acc_sq, const zd* 
     zd X12 = acc_sq[J_X * sq * Nk + o12], X21 = conj(acc_sq[J_X * sq * Nk + o21]);
     zd S1 = ic * (E12 + E21), S2 = ic * (E21 - E12), S3 = ic * (F12 + F21);
     zd S4 = ic * (Gx12 - Gx21), S6 = ic * (Gz12 - Gz21);
-    zd S5 = ic * ((Q12 + 2.0 * X12) - (Q21 + 2.0 * X21));
-    zd S7 = ic * ((Q12 - 2.0 * X12) + (Q21 - 2.0 * X21));
+    zd S5 = ic * ((Q12 + X12) - (Q21 + X21));
+    zd S7 = ic * ((Q12 - X12) + (Q21 - X21));
     const double nu = pc.nu;
     T[T_A] = -2.0 * S0;
     T[T_PHIX] = S4 + (-2.0 * pc.dU) * S0 + (4.0 * nu * kx) * mul_i(S0);

@@ -69,8 +69,11 @@ GROUP_A = Workload("group_128x128x65_s32", 4, 128, 128, 65, 32)
 GROUP_B = Workload("group_256x256x129_s16", 4, 256, 256, 129, 16)
 GROUP_C = Workload("group_384x384x193_s8", 4, 384, 384, 193, 8)
 RETAU1000 = Workload("retau1000_512x512x257_s32", 5, 512, 512, 257, 32, nu=1.0 / 1000.0)
+# a narrow case with the Re_tau~200 wall-normal grid and snapshot count, small
+# enough for multi-pass profiler captures (a few GB on the device)
+PROFILE = Workload("profile_32x32x129_s16", 6, 32, 32, 129, 16)
 
-WORKLOADS = {w.name: w for w in (TINY, RETAU200, GROUP_A, GROUP_B, GROUP_C, RETAU1000)}
+WORKLOADS = {w.name: w for w in (TINY, RETAU200, GROUP_A, GROUP_B, GROUP_C, RETAU1000, PROFILE)}
 
 
 def small(nx: int, nz: int, ny: int, nsnap: int, wid: int = 90, nu: float = 1.0 / 200.0,

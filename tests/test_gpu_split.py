@@ -1,0 +1,53 @@
+"""Split-precision (BF16 x 3 slices, tcgen05) correlator against the FP64 path.
+
+The bar (per term, relative to the term's largest magnitude) is
+TOL_SPLIT = 1e-6: each real operand keeps ~24 significant bits in its three
+BF16 slices, the six kept slice products drop terms of relative size 2^-24,
+and the tensor cores accumulate in FP32, so a contraction over K <= 4 x 32
+snapshot-field products carries ~1e-7 of the magnitude of its terms; the
+inverse transforms and the Step-3 stencils run in FP64 here.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from test_gpu_parity import rel_err, run_gpu
+
+TOL_SPLIT = 1e-6
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1910_06409_gb300 import build as B
+    B.build()
+    import paper_1910_06409_gb300._native as native
+    return native
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 33, 4), (16, 16, 129, 3), (8, 8, 257, 2), (16, 8, 65, 20)])
+def test_split_matches_f64(N, shape):
+    nx, nz, ny, ns = shape
+    wl = S.small(nx, nz, ny, ns, wid=60 + ny)
+    coef = S.coefficients(wl)
+    ref, pref = run_gpu(N, wl, coef, precision=N.GKE_PREC_F64)
+    got, pgot = run_gpu(N, wl, coef, precision=N.GKE_PREC_BF16X3)
+    errs = [rel_err(got[t], ref[t]) for t in range(N.GKE_NTERM)]
+    assert max(errs) <= TOL_SPLIT, dict(zip(N.TERMS, errs))
+    assert max(errs) > 0.0          # the split path really ran (not the FP64 one)
+
+
+def test_split_tiny_vs_oracle(N):
+    import oracle
+    wl = S.TINY
+    phys = S.physical(wl)
+    ref = oracle.full(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu)
+    got, prof = run_gpu(N, wl, S.to_coefficients(phys), precision=N.GKE_PREC_BF16X3)
+    iu = np.triu_indices(wl.ny)
+    for t in range(N.GKE_NTERM):
+        e = rel_err(got[t], ref["terms"][t][iu])
+        assert e <= TOL_SPLIT, (N.TERMS[t], e)
