@@ -195,7 +195,8 @@ def run_ours(args, world, rank, local):
                       stream=stream.cuda_stream)
     npair = N.gke_npair(plan)
     f_dev = torch.from_numpy(coef).cuda()
-    terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=torch.float64, device="cuda")
+    tdt = torch.float64 if args.precision == "f64" else torch.float32      # terms element type
+    terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=tdt, device="cuda")
 
     def barrier():
         if world > 1:
@@ -233,7 +234,7 @@ def run_ours(args, world, rank, local):
     e2e = None
     if not args.no_e2e:
         f_host = torch.from_numpy(coef).pin_memory()
-        out_host = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=torch.float64).pin_memory()
+        out_host = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=tdt).pin_memory()
         N.gke_compute(plan, f_host, ns, out_host)     # warm-up (allocates staging once)
         torch.cuda.synchronize()
         ke = max(1, min(args.steps, 3))
@@ -252,7 +253,7 @@ def run_ours(args, world, rank, local):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms_e2e = float(t.item())
         e2e = {"value": world * npair * ns / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
-               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": int(out_host.numel() * 8)}
+               "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": int(out_host.numel() * out_host.element_size())}
         del out_host, f_host
     N.gke_destroy(plan)
 
@@ -285,8 +286,8 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": config_of(wl, args.precision), "parallelism": f"replicas{world}",
+                "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "bf16x3/f32",
+                "data": "synthetic", "config": config_of(wl, args.precision), "parallelism": f"replicas{world}",
                 "stage_ms": {k: v / args.steps for k, v in stage.items()},
                 "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
                 "cpu_baseline": cpu}

@@ -29,7 +29,7 @@
  *     Phi_x, Phi_y, Phi_z odd under (Y1, Y2, r) -> (Y2, Y1, -r).
  *   - Separations: index (m_z, m_x) in [0, nz) x [0, nx), FFT order,
  *     r_x = m_x Lx / nx, r_z = m_z Lz / nz (periodic).
- *   - Output terms (double):
+ *   - Output terms (double on the FP64 path, float on the split path):
  *       terms[GKE_NTERM][npair][nz][nx]
  *     in the order GKE_TERM_* below: <du^2>, Phi_x, Phi_y, Phi_z, phi, xi
  *     and the residual of Eq. 3 (div_r Phi + d phi/dY - xi).
@@ -111,28 +111,30 @@ gke_status gke_set_mean(gke_plan_t plan, const double* mean);
 gke_status gke_accumulate_snapshot(gke_plan_t plan, const void* fields, int nsnap);
 
 /* Step 3 (Sec. 3.2): write all terms for every pair and separation and,
- * if profiles != NULL, the profiles.  GKE_ERR_STATE without samples;
+ * if profiles != NULL, the profiles.  terms holds double on the FP64 path
+ * (GKE_PREC_F64) and float on the split path (GKE_PREC_BF16X3).  GKE_ERR_STATE without samples;
  * GKE_ERR_NONFINITE if any accumulated input held a NaN or Inf (outputs are
  * then undefined).  May be called again; accumulators are left unchanged.  */
-gke_status gke_finalize_terms(gke_plan_t plan, double* terms, double* profiles);
+gke_status gke_finalize_terms(gke_plan_t plan, void* terms, double* profiles);
 
 /* One full pass: gke_accumulate_mean + gke_accumulate_snapshot +
  * gke_finalize_terms on a fresh plan state, staging host data once.        */
-gke_status gke_compute(gke_plan_t plan, const void* fields, int nsnap, double* terms, double* profiles);
+gke_status gke_compute(gke_plan_t plan, const void* fields, int nsnap, void* terms, double* profiles);
 
 /* Host arrays of the pair labels: Y[npair], ry[npair], i1[npair], i2[npair]
  * (any may be NULL).                                                         */
 gke_status gke_pair_labels(gke_plan_t plan, double* Y, double* ry, int* i1, int* i2);
 
-/* Sizes: number of pairs, and bytes of the terms array.                     */
+/* Sizes: number of pairs, and bytes of the terms array (element size 8 on
+ * the FP64 path, 4 on the split path).                                       */
 long long gke_npair(gke_plan_t plan);
 long long gke_terms_bytes(gke_plan_t plan);
 
 /* Forget all accumulated statistics and the mean.                            */
 gke_status gke_reset(gke_plan_t plan);
 
-/* Save / restore the accumulated state (mean sums, one-point sums, spectral
- * sums, counts) to / from a file; linear, so restored partial sums combine
+/* Save / restore the accumulated state (mean sums, one-point sums, per-pair
+ * term spectra, counts) to / from a file; linear, so restored partial sums combine
  * exactly with further calls (the paper's merge of independent jobs,
  * Sec. 3.4).  gke_merge adds a checkpoint's sums to the plan's.             */
 gke_status gke_checkpoint(gke_plan_t plan, const char* path);
@@ -153,7 +155,8 @@ int gke_fd_weights(const double* y, int ny, int j, double* w);
 enum { GKE_STAGE_MEAN = 0,       /* Step 1 ensemble mean                          */
        GKE_STAGE_PRODUCTS,       /* fluctuations, in-plane products, one-point sums */
        GKE_STAGE_CORRELATE,      /* per-wavenumber contractions over snapshots    */
-       GKE_STAGE_TERMS,          /* spectral combinations + inverse transforms    */
+       GKE_STAGE_COMBINE,        /* per-pair term spectra, FP64 sum over batches  */
+       GKE_STAGE_TERMS,          /* inverse transforms + one-point parts          */
        GKE_STAGE_STENCIL,        /* Step 3 Y1/Y2 finite differences               */
        GKE_NSTAGE };
 gke_status gke_set_timing(gke_plan_t plan, int on);

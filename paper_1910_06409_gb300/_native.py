@@ -27,7 +27,7 @@ EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_sn
            "gke_compute", "gke_pair_labels", "gke_npair", "gke_terms_bytes", "gke_reset", "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_last_error", "gke_destroy")
-STAGES = ("mean", "products", "correlate", "terms", "stencil")
+STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
 
 
 class gke_desc(ctypes.Structure):

@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/gke.h"
@@ -26,9 +27,20 @@ struct gke_plan_s {
     cudaStream_t st = nullptr;
     int nxh = 0, Nk = 0;
     long long npair = 0;
-    // device workspaces
-    zd *Xop = nullptr, *G = nullptr, *H = nullptr, *acc_sq = nullptr, *acc_D = nullptr, *W = nullptr;
-    zd *tw_x = nullptr, *tw_z = nullptr, *stage_in = nullptr;
+    // device workspaces; Xop, G, H, raw and W hold complex<TF>, TF = double on
+    // the plain path and float on the split path
+    void *Xop = nullptr, *G = nullptr, *H = nullptr, *raw = nullptr, *W = nullptr;
+    // per-pair term spectra summed over batches: FP64 (comb) on the plain path;
+    // on the split path the first batch goes to comb32 and a second batch
+    // promotes the sum to FP64 (comb, allocated then)
+    zd* comb = nullptr;
+    zf* comb32 = nullptr;
+    bool comb_is64 = false;
+    float* spec = nullptr;                    // split path: spectral parts of A, Phi_y, phi
+    size_t tsz = 8;                           // bytes of one output term value
+    zd *tw_xd = nullptr, *tw_zd = nullptr, *stage_in = nullptr;
+    zf *tw_xf = nullptr, *tw_zf = nullptr;
+    size_t csz = 16;                          // bytes of one complex<TF>
     double *mean_sum = nullptr, *mean = nullptr, *stats = nullptr, *prof = nullptr, *fdw = nullptr;
     double *stage_terms = nullptr, *stage_prof = nullptr, *part = nullptr;
     size_t part_count = 0;
@@ -132,34 +144,32 @@ static int smem_limit()
     return v;
 }
 
-// tile parameters of the transform kernels for a grid (bounded by shared memory)
+// tile parameters of the transform kernels for a grid and a complex size:
+// each CTA keeps its ping-pong buffers and twiddles within 64 KB, so three
+// CTAs fit on an SM
 struct Tiles { int cw_ci, rz_rp, cw_cf, yb_cf, cw_tc, rz_tr; };
-static Tiles pick_tiles(int nx, int nz)
+static Tiles pick_tiles(int nx, int nz, size_t csz)
 {
     Tiles t;
-    const int lim = 96 * 1024;   // keep two CTAs per SM possible
-    t.cw_ci = 8; while (t.cw_ci > 1 && t.cw_ci * nz * 16 > lim) t.cw_ci /= 2;
-    t.rz_rp = 4; while (t.rz_rp > 1 && t.rz_rp * 6 * nx * 16 > lim) t.rz_rp /= 2;
-    t.cw_cf = 4; t.yb_cf = 4; while (t.cw_cf * t.yb_cf > 1 && t.cw_cf * t.yb_cf * nz * 16 > lim) {
-        if (t.yb_cf > 1) t.yb_cf /= 2; else t.cw_cf /= 2; }
-    t.cw_tc = 4; while (t.cw_tc > 1 && NTERM * t.cw_tc * nz * 16 > lim) t.cw_tc /= 2;
-    t.rz_tr = 4; while (t.rz_tr > 1 && t.rz_tr * 4 * nx * 16 > lim) t.rz_tr /= 2;
+    const size_t lim = 64 * 1024;
+    auto fits = [&](size_t elems) { return elems * csz <= lim; };
+    t.cw_ci = 16; while (t.cw_ci > 1 && !fits((size_t)(1 + 2 * t.cw_ci) * nz)) t.cw_ci /= 2;
+    t.rz_rp = 8;  while (t.rz_rp > 1 && !fits((size_t)(1 + 8 * t.rz_rp) * nx)) t.rz_rp /= 2;
+    t.cw_cf = 4; t.yb_cf = 8;
+    while (t.cw_cf * t.yb_cf > 1 && !fits((size_t)(1 + 2 * t.cw_cf * t.yb_cf) * nz)) {
+        if (t.cw_cf > 1) t.cw_cf /= 2; else t.yb_cf /= 2;
+    }
+    t.cw_tc = 16; while (t.cw_tc > 1 && !fits((size_t)(1 + 2 * t.cw_tc) * nz)) t.cw_tc /= 2;
+    t.rz_tr = 8;  while (t.rz_tr > 1 && !fits((size_t)(1 + 8 * t.rz_tr) * nx)) t.rz_tr /= 2;
     return t;
 }
 
 static cudaError_t set_smem_attrs()
 {
     int lim = smem_limit();
-    cudaError_t e = cudaSuccess;
-    const void* ks[] = {(const void*)k_col_inverse, (const void*)k_row_products, (const void*)k_col_forward,
-                        (const void*)k_terms_colpass, (const void*)k_terms_rowpass};
-    for (const void* k : ks) {
-        cudaFuncAttributes fa;
-        cudaError_t r = cudaFuncGetAttributes(&fa, k);
-        if (r == cudaSuccess)
-            r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - (int)fa.sharedSizeBytes);
-        if (r != cudaSuccess) e = r;
-    }
+    cudaError_t e = products_set_attrs(lim);
+    if (e == cudaSuccess) e = terms_set_attrs(lim);
+    if (e == cudaSuccess) e = combine_set_attrs();
     return e;
 }
 
@@ -211,15 +221,36 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         if (e != cudaSuccess) return bail(GKE_ERR_OOM, std::string("cudaMalloc " #ptr ": ") +  \
                                                            cudaGetErrorString(e));             \
     } while (0)
-    ALLOC(p->Xop, (size_t)NFIELD * Nk * ns * ny);
-    ALLOC(p->G, (size_t)4 * ny * plane);
-    ALLOC(p->H, (size_t)7 * ny * plane);
-    ALLOC(p->acc_sq, (size_t)NJSQ * ny * ny * Nk);
-    ALLOC(p->acc_D, (size_t)p->npair * Nk);
-    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, (2LL << 30) / ((long long)NTERM * Nk * 16)));
-    ALLOC(p->W, (size_t)p->pair_chunk * NTERM * Nk);
-    ALLOC(p->tw_x, d.nx / 2);
-    ALLOC(p->tw_z, d.nz / 2);
+    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    p->csz = f32 ? sizeof(zf) : sizeof(zd);
+#define ALLOCB(ptr, bytes)                                                                          \
+    do {                                                                                            \
+        e = cudaMalloc((void**)&(ptr), (size_t)(bytes));                                            \
+        if (e != cudaSuccess) return bail(GKE_ERR_OOM, std::string("cudaMalloc " #ptr ": ") +       \
+                                                           cudaGetErrorString(e));                  \
+    } while (0)
+    ALLOCB(p->Xop, (size_t)NFIELD * Nk * ns * ny * p->csz);
+    ALLOCB(p->G, (size_t)4 * ny * plane * p->csz);
+    ALLOCB(p->H, (size_t)7 * ny * plane * p->csz);
+    ALLOCB(p->raw, (size_t)NJOB * Nk * ny * ny * p->csz);
+    if (f32) {
+        ALLOC(p->comb32, (size_t)p->npair * NTERM * Nk);
+        // spectral parts of A, Phi_y, phi, then 13 per-pair stencil scalars
+        ALLOC(p->spec, (size_t)3 * p->npair * d.nx * d.nz + 13 * (size_t)p->npair);
+        p->tsz = sizeof(float);
+    } else {
+        ALLOC(p->comb, (size_t)p->npair * NTERM * Nk);
+        p->comb_is64 = true;
+        p->tsz = sizeof(double);
+    }
+    // pairs per inverse-transform chunk: keep the chunk's W scratch (~60 MB) in L2
+    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, (60LL << 20) / ((long long)NTERM * Nk * p->csz)));
+    ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * Nk * p->csz);
+    ALLOC(p->tw_xd, d.nx);
+    ALLOC(p->tw_zd, d.nz);
+    ALLOC(p->tw_xf, d.nx);
+    ALLOC(p->tw_zf, d.nz);
+#undef ALLOCB
     ALLOC(p->mean_sum, 4 * ny);
     ALLOC(p->mean, 4 * ny);
     ALLOC(p->stats, NSTAT * ny);
@@ -229,7 +260,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOC(p->pair_i, 2 * p->npair);
     ALLOC(p->nonfinite, 1);
     {
-        const Tiles tl = pick_tiles(d.nx, d.nz);
+        const Tiles tl = pick_tiles(d.nx, d.nz, p->csz);
         size_t a1 = (size_t)6 * ny * ((d.nz + tl.rz_rp - 1) / tl.rz_rp);
         size_t a2 = (size_t)ny * ((Nk + EPS_KCHUNK - 1) / EPS_KCHUNK);
         p->part_count = std::max(a1, a2);
@@ -241,9 +272,13 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     }
 #undef ALLOC
     // host tables
-    std::vector<zd> twx(d.nx / 2), twz(d.nz / 2);
-    for (int m = 0; m < d.nx / 2; ++m) { twx[m].x = std::cos(2.0 * M_PI * m / d.nx); twx[m].y = -std::sin(2.0 * M_PI * m / d.nx); }
-    for (int m = 0; m < d.nz / 2; ++m) { twz[m].x = std::cos(2.0 * M_PI * m / d.nz); twz[m].y = -std::sin(2.0 * M_PI * m / d.nz); }
+    // twiddles e^{-2 pi i m / n}, m < n, from the host's libm in FP64
+    std::vector<zd> twx(d.nx), twz(d.nz);
+    std::vector<zf> twxf(d.nx), twzf(d.nz);
+    for (int m = 0; m < d.nx; ++m) { twx[m].x = std::cos(2.0 * M_PI * m / d.nx); twx[m].y = -std::sin(2.0 * M_PI * m / d.nx); }
+    for (int m = 0; m < d.nz; ++m) { twz[m].x = std::cos(2.0 * M_PI * m / d.nz); twz[m].y = -std::sin(2.0 * M_PI * m / d.nz); }
+    for (int m = 0; m < d.nx; ++m) { twxf[m].x = (float)twx[m].x; twxf[m].y = (float)twx[m].y; }
+    for (int m = 0; m < d.nz; ++m) { twzf[m].x = (float)twz[m].x; twzf[m].y = (float)twz[m].y; }
     std::vector<double> w(5 * ny);
     std::vector<int> l0(ny);
     for (int j = 0; j < ny; ++j) {
@@ -256,8 +291,10 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     for (int i1 = 0; i1 < ny; ++i1)
         for (int i2 = i1; i2 < ny; ++i2) { pi[2 * q] = i1; pi[2 * q + 1] = i2; ++q; }
     cudaStream_t st = p->st;
-    if ((e = cudaMemcpyAsync(p->tw_x, twx.data(), twx.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync(p->tw_z, twz.data(), twz.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
+    if ((e = cudaMemcpyAsync(p->tw_xd, twx.data(), twx.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(p->tw_zd, twz.data(), twz.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(p->tw_xf, twxf.data(), twxf.size() * sizeof(zf), cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync(p->tw_zf, twzf.data(), twzf.size() * sizeof(zf), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->fdw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->fdl0, l0.data(), l0.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->pair_i, pi.data(), pi.size() * sizeof(int), cudaMemcpyHostToDevice, st)) ||
@@ -283,6 +320,7 @@ extern "C" gke_status gke_reset(gke_plan_t p)
     p->mean_count = 0.0;
     p->snap_count = 0.0;
     p->mean_frozen = p->have_acc = p->finalized = false;
+    p->comb_is64 = (p->d.precision == GKE_PREC_F64);
     return GKE_OK;
 }
 
@@ -290,7 +328,7 @@ extern "C" void gke_destroy(gke_plan_t p)
 {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
-    void* ptrs[] = {p->Xop, p->G, p->H, p->acc_sq, p->acc_D, p->W, p->tw_x, p->tw_z, p->stage_in,
+    void* ptrs[] = {p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
                     p->fdl0, p->pair_i, p->nonfinite, p->part};
     for (void* q : ptrs) if (q) cudaFree(q);
@@ -337,7 +375,7 @@ extern "C" const char* gke_last_error(gke_plan_t p) { return p ? p->err.c_str() 
 extern "C" long long gke_npair(gke_plan_t p) { return p ? p->npair : -1; }
 extern "C" long long gke_terms_bytes(gke_plan_t p)
 {
-    return p ? (long long)NTERM * p->npair * p->d.nx * p->d.nz * (long long)sizeof(double) : -1;
+    return p ? (long long)NTERM * p->npair * p->d.nx * p->d.nz * (long long)p->tsz : -1;
 }
 
 extern "C" gke_status gke_pair_labels(gke_plan_t p, double* Y, double* ry, int* i1, int* i2)
@@ -398,10 +436,26 @@ extern "C" gke_status gke_set_mean(gke_plan_t p, const double* mean)
     return GKE_OK;
 }
 
+static void products_stage(gke_plan_t p, const zd* f, int ns)
+{
+    const gke_desc& d = p->d;
+    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    const Tiles t = pick_tiles(d.nx, d.nz, p->csz);
+    ProdArgs a;
+    a.fields = f; a.ns = ns; a.ny = d.ny; a.nz = d.nz; a.nx = d.nx; a.nxh = p->nxh; a.Nk = p->Nk;
+    a.mean = p->mean; a.Xop = p->Xop; a.G = p->G; a.H = p->H;
+    a.tw_x = f32 ? (const void*)p->tw_xf : (const void*)p->tw_xd;
+    a.tw_z = f32 ? (const void*)p->tw_zf : (const void*)p->tw_zd;
+    a.part = p->part; a.stats = p->stats; a.nonfinite = p->nonfinite;
+    a.cw_ci = t.cw_ci; a.rz_rp = t.rz_rp; a.cw_cf = t.cw_cf; a.yb_cf = t.yb_cf; a.eps_kchunk = EPS_KCHUNK;
+    a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = p->fdw; a.fdl0 = p->fdl0; a.st = p->st;
+    p->launches += f32 ? products_launch<float>(a) : products_launch<double>(a);
+}
+
 static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
 {
     const gke_desc& d = p->d;
-    const int ny = d.ny, Nk = p->Nk, nxh = p->nxh;
+    const int ny = d.ny, Nk = p->Nk;
     cudaStream_t st = p->st;
     if (!p->mean_frozen) {
         // mean = mean_sum / mean_count, computed once (host round trip of 4 ny doubles)
@@ -410,44 +464,42 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
         CUDA_TRY(p, cudaStreamSynchronize(st));
         for (double& v : m) v /= p->mean_count;
         CUDA_TRY(p, cudaMemcpyAsync(p->mean, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        // U and U' rows of the profiles, used by the term combinations
+        k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, 1.0,
+                                                      (long long)d.nx * d.nz, d.nu, p->fdw, p->fdl0, ny, p->prof);
+        p->launches += 1;
         CUDA_TRY(p, cudaStreamSynchronize(st));
         p->mean_frozen = true;
     }
-    const Tiles t = pick_tiles(d.nx, d.nz);
-    dim3 b32(32, 8);
-    StageScope* sc_prod = new StageScope(p, GKE_STAGE_PRODUCTS);
-    k_load_linear<<<dim3((Nk + 31) / 32, (ny + 31) / 32, ns * 4), b32, 0, st>>>(f, ns, ny, Nk, p->mean, p->Xop,
-                                                                              p->nonfinite);
-    for (int s = 0; s < ns; ++s) {
-        const zd* fs = f + (size_t)s * 4 * ny * Nk;
-        k_col_inverse<<<dim3((nxh + t.cw_ci - 1) / t.cw_ci, ny, 4), 256, t.cw_ci * d.nz * sizeof(zd), st>>>(
-            fs, ny, d.nz, nxh, t.cw_ci, p->mean, p->tw_z, p->G);
-        const int nrb = (d.nz + t.rz_rp - 1) / t.rz_rp;
-        k_row_products<<<dim3(nrb, ny), 256, t.rz_rp * 6 * d.nx * sizeof(zd), st>>>(
-            p->G, ny, d.nz, d.nx, t.rz_rp, p->tw_x, p->H, p->part);
-        k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(p->part, 6 * ny, nrb, p->stats);
-        p->launches += 3;
-        k_col_forward<<<dim3((nxh + t.cw_cf - 1) / t.cw_cf, (ny + t.yb_cf - 1) / t.yb_cf, 7), 256,
-                        t.cw_cf * t.yb_cf * d.nz * sizeof(zd), st>>>(p->H, ny, d.nz, nxh, t.cw_cf, t.yb_cf, s, ns,
-                                                                     p->tw_z, p->Xop);
-        p->launches += 1;
+    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    {
+        StageScope sc(p, GKE_STAGE_PRODUCTS);
+        products_stage(p, f, ns);
     }
-    const int neb = (Nk + EPS_KCHUNK - 1) / EPS_KCHUNK;
-    k_eps<<<neb, 128, 0, st>>>(p->Xop, ns, ny, d.nz, nxh, d.nx, d.Lx, d.Lz, p->fdw, p->fdl0, EPS_KCHUNK, p->part);
-    k_reduce_partials<<<(ny + 127) / 128, 128, 0, st>>>(p->part, ny, neb, p->stats + S_EPS * ny);
-    p->launches += 3;
-    delete sc_prod;
-    StageScope sc_corr(p, GKE_STAGE_CORRELATE);
-    if (d.precision == GKE_PREC_F64) {
-        k_correlate_f64<<<dim3(Nk, NJSQ + 1), 256, 0, st>>>(p->Xop, ns, ny, Nk, p->have_acc ? 1 : 0, p->acc_sq,
-                                                             p->acc_D);
-        p->launches += 1;
-    } else {
-        int nl = 0;
-        gke_status s = split_correlate(p->split, p->Xop, ns, ny, Nk, p->have_acc ? 1 : 0, p->acc_sq, p->acc_D, st,
-                                       p->err, &nl);
-        p->launches += nl;
-        if (s != GKE_OK) return s;
+    {
+        StageScope sc(p, GKE_STAGE_CORRELATE);
+        if (!f32) {
+            k_correlate_f64<<<dim3(Nk, NJOB), 256, 0, st>>>((const zd*)p->Xop, ns, ny, Nk, (zd*)p->raw);
+            p->launches += 1;
+        } else {
+            int nl = 0;
+            gke_status s = split_correlate(p->split, (const zf*)p->Xop, ns, ny, Nk, (zf*)p->raw, st, p->err, &nl);
+            p->launches += nl;
+            if (s != GKE_OK) return s;
+        }
+    }
+    {
+        StageScope sc(p, GKE_STAGE_COMBINE);
+        const long long ncomb = p->npair * NTERM * (long long)Nk;
+        if (f32 && p->have_acc && !p->comb_is64) {
+            // second batch on the split path: promote the per-pair sums to FP64
+            if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, (size_t)ncomb));
+            p->launches += promote_launch(p->comb32, ncomb, p->comb, st);
+            p->comb_is64 = true;
+        }
+        void* dst = p->comb_is64 ? (void*)p->comb : (void*)p->comb32;
+        p->launches += combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof,
+                                      p->have_acc ? 1 : 0, dst, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     p->snap_count += ns;
@@ -467,33 +519,41 @@ extern "C" gke_status gke_accumulate_snapshot(gke_plan_t p, const void* fields, 
     return snapshot_impl(p, f, nsnap);
 }
 
-static gke_status finalize_impl(gke_plan_t p, double* terms_dev)
+static void terms_stage(gke_plan_t p, void* terms_dev)
 {
     const gke_desc& d = p->d;
-    const int ny = d.ny, nxh = p->nxh;
+    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    const Tiles t = pick_tiles(d.nx, d.nz, p->csz);
+    TermArgs a;
+    a.fp32 = f32; a.comb64 = p->comb_is64;
+    a.comb = p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32; a.W = p->W; a.spec = p->spec; a.pair_i = p->pair_i; a.npair = p->npair; a.pair_chunk = p->pair_chunk;
+    a.ny = d.ny; a.nz = d.nz; a.nx = d.nx;
+    a.cw = t.cw_tc;
+    a.rz = t.rz_tr;
+    a.inv_count = 1.0 / p->snap_count; a.prof = p->prof;
+    a.tw_x = f32 ? (const void*)p->tw_xf : (const void*)p->tw_xd;
+    a.tw_z = f32 ? (const void*)p->tw_zf : (const void*)p->tw_zd;
+    a.terms = terms_dev; a.st = p->st;
+    p->launches += terms_launch(a);
+}
+
+static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
+{
+    const gke_desc& d = p->d;
+    const int ny = d.ny;
     cudaStream_t st = p->st;
-    const Tiles t = pick_tiles(d.nx, d.nz);
-    StageScope* sc_terms = new StageScope(p, GKE_STAGE_TERMS);
-    k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, p->snap_count,
-                                                  (long long)d.nx * d.nz, d.nu, p->fdw, p->fdl0, ny, p->prof);
-    const double inv_count = 1.0 / p->snap_count;
-    for (long long p0 = 0; p0 < p->npair; p0 += p->pair_chunk) {
-        long long np = std::min(p->pair_chunk, p->npair - p0);
-        k_terms_colpass<<<dim3((nxh + t.cw_tc - 1) / t.cw_tc, (unsigned)np), 256, NTERM * t.cw_tc * d.nz * sizeof(zd),
-                          st>>>(p->acc_sq, p->acc_D, p->pair_i, p0, ny, d.nz, d.nx, t.cw_tc, d.Lx, d.Lz, d.nu,
-                                inv_count, p->prof, p->tw_z, p->W);
-        k_terms_rowpass<<<dim3((d.nz + t.rz_tr - 1) / t.rz_tr, (unsigned)np), 256, t.rz_tr * 4 * d.nx * sizeof(zd),
-                          st>>>(p->W, p->pair_i, p0, p->npair, ny, d.nz, d.nx, t.rz_tr, p->prof, p->tw_x, terms_dev);
-        p->launches += 2;
+    {
+        StageScope sc(p, GKE_STAGE_TERMS);
+        k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, p->snap_count,
+                                                      (long long)d.nx * d.nz, d.nu, p->fdw, p->fdl0, ny, p->prof);
+        p->launches += 1;
+        terms_stage(p, terms_dev);
     }
-    p->launches += 1;
-    delete sc_terms;
-    StageScope sc_st(p, GKE_STAGE_STENCIL);
-    const long long N = (long long)d.nx * d.nz;
-    dim3 gs((unsigned)((N + 255) / 256), (unsigned)p->npair);
-    k_stencil_A<<<gs, 256, 0, st>>>(terms_dev, p->npair, p->pair_i, ny, d.nz, d.nx, d.nu, p->fdw, p->fdl0);
-    k_stencil_res<<<gs, 256, 0, st>>>(terms_dev, p->npair, p->pair_i, ny, d.nz, d.nx, p->fdw, p->fdl0);
-    p->launches += 2;
+    {
+        StageScope sc(p, GKE_STAGE_STENCIL);
+        p->launches += stencil_launch(d.precision == GKE_PREC_BF16X3, terms_dev, p->spec, p->npair, p->pair_i, ny,
+                                      d.nz, d.nx, d.nu, p->fdw, p->fdl0, p->prof, st);
+    }
     CUDA_TRY(p, cudaGetLastError());
     return GKE_OK;
 }
@@ -503,13 +563,13 @@ static_assert((int)PR_U == (int)GKE_PROF_U && (int)PR_V == (int)GKE_PROF_V && (i
               (int)PR_P == (int)GKE_PROF_P && (int)PR_DU == (int)GKE_PROF_DUDY && (int)PR_EPS == (int)GKE_PROF_EPS,
               "profile order");
 
-extern "C" gke_status gke_finalize_terms(gke_plan_t p, double* terms, double* profiles)
+extern "C" gke_status gke_finalize_terms(gke_plan_t p, void* terms, double* profiles)
 {
     if (!p || !terms) return p ? fail(p, GKE_ERR_ARG, "terms is NULL") : GKE_ERR_ARG;
     if (!p->have_acc || p->snap_count <= 0) return fail(p, GKE_ERR_STATE, "no snapshots accumulated");
     const bool dev_out = is_device_ptr(terms);
     const size_t tbytes = (size_t)gke_terms_bytes(p);
-    double* tdev = terms;
+    void* tdev = terms;
     if (!dev_out) {
         if (!p->stage_terms) CUDA_TRY(p, dalloc(&p->stage_terms, tbytes / sizeof(double)));
         tdev = p->stage_terms;
@@ -531,7 +591,7 @@ extern "C" gke_status gke_finalize_terms(gke_plan_t p, double* terms, double* pr
     return GKE_OK;
 }
 
-extern "C" gke_status gke_compute(gke_plan_t p, const void* fields, int nsnap, double* terms, double* profiles)
+extern "C" gke_status gke_compute(gke_plan_t p, const void* fields, int nsnap, void* terms, double* profiles)
 {
     if (!p || !fields || !terms) return p ? fail(p, GKE_ERR_ARG, "NULL argument") : GKE_ERR_ARG;
     if (nsnap < 1 || nsnap > p->d.max_snap) return fail(p, GKE_ERR_ARG, "nsnap out of range [1, max_snap]");
@@ -556,14 +616,22 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     if (!p || !path) return p ? fail(p, GKE_ERR_ARG, "path is NULL") : GKE_ERR_ARG;
     const int ny = p->d.ny;
     const size_t n_mean = 4 * ny, n_stat = (size_t)NSTAT * ny;
-    const size_t n_sq = (size_t)NJSQ * ny * ny * p->Nk, n_D = (size_t)p->npair * p->Nk;
+    const size_t n_comb = (size_t)p->npair * NTERM * p->Nk;
+    // the stored per-pair sums are FP64; a split plan holding one batch in FP32 promotes first
+    if (p->have_acc && !p->comb_is64) {
+        if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
+        promote_launch(p->comb32, (long long)n_comb, p->comb, p->st);
+        p->comb_is64 = true;
+    }
+    if (mode != 0 && !p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
+    CUDA_TRY(p, cudaStreamSynchronize(p->st));
     CUDA_TRY(p, cudaStreamSynchronize(p->st));
     if (mode == 0) {
         FILE* fp = fopen(path, "wb");
         if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for writing: ") + path);
         CkptHeader h{};
         memcpy(h.magic, "GKECKPT", 8);
-        h.version = 1; h.nx = p->d.nx; h.nz = p->d.nz; h.ny = ny; h.precision = p->d.precision;
+        h.version = 2; h.nx = p->d.nx; h.nz = p->d.nz; h.ny = ny; h.precision = p->d.precision;
         h.have_acc = p->have_acc; h.mean_count = p->mean_count; h.snap_count = p->snap_count;
         h.Lx = p->d.Lx; h.Lz = p->d.Lz; h.nu = p->d.nu;
         bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
@@ -574,14 +642,14 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
             return fwrite(buf.data(), 1, bytes, fp) == bytes;
         };
         ok = ok && put(p->mean_sum, n_mean * 8) && put(p->stats, n_stat * 8);
-        if (p->have_acc) ok = ok && put(p->acc_sq, n_sq * 16) && put(p->acc_D, n_D * 16);
+        if (p->have_acc) ok = ok && put(p->comb, n_comb * 16);
         ok = (fclose(fp) == 0) && ok;
         return ok ? GKE_OK : fail(p, GKE_ERR_IO, std::string("write failed: ") + path);
     }
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for reading: ") + path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != 1) {
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != 2) {
         fclose(fp);
         return fail(p, GKE_ERR_IO, "not a GKE checkpoint");
     }
@@ -615,11 +683,11 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     get(p->stats, n_stat * 8, add, false);
     if (h.have_acc) {
         const bool add_acc = add && p->have_acc;
-        get(p->acc_sq, n_sq * 16, false, add_acc);
-        get(p->acc_D, n_D * 16, false, add_acc);
+        get(p->comb, n_comb * 16, false, add_acc);
     }
     fclose(fp);
     if (!ok) return fail(p, GKE_ERR_IO, std::string("read failed or truncated: ") + path);
+    if (h.have_acc) p->comb_is64 = true;
     if (add) {
         p->mean_count += h.mean_count;
         p->snap_count += h.snap_count;
@@ -636,6 +704,10 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         CUDA_TRY(p, cudaMemcpy(m.data(), p->mean_sum, m.size() * 8, cudaMemcpyDeviceToHost));
         for (double& v : m) v /= p->mean_count;
         CUDA_TRY(p, cudaMemcpy(p->mean, m.data(), m.size() * 8, cudaMemcpyHostToDevice));
+        k_profiles<<<(ny + 127) / 128, 128, 0, p->st>>>(p->mean_sum, p->mean_count, p->stats, 1.0,
+                                                         (long long)p->d.nx * p->d.nz, p->d.nu, p->fdw, p->fdl0, ny,
+                                                         p->prof);
+        CUDA_TRY(p, cudaStreamSynchronize(p->st));
         p->mean_frozen = true;
     }
     p->finalized = false;

@@ -1,0 +1,170 @@
+// gke_combine.cu -- per-pair term spectra from one batch's contractions.
+//
+// Every GKE term is one inverse transform of a linear combination of the
+// contraction spectra plus a part that depends on (Y1, Y2) only (correlation
+// expansion, Sec. 3.1 Eq. 7; Parseval, Eq. 8-9).  With X^H(y, y') =
+// conj X(y', y), S0 = D, S1 = E + E^H, S2 = E^H - E, S3 = F + F^H,
+// S4 = Gx - Gx^H, S5 = Gy - Gy^H, S6 = Gz - Gz^H, S7 = H + H^H, where
+// Gy = QV + X2 and H = QV - X2:
+//   A     : -2 S0
+//   Phi_x : S4 + (-2 dU + 4 i nu kx) S0
+//   Phi_y : S5
+//   Phi_z : S6 + 4 i nu kz S0
+//   phi   : S7 / 2 - 2 S3
+//   xi    : 2 U'* S1 - dU' S2
+//   res   : i kx S4 + i kz S6 - 2 i dU kx S0 - 4 nu |k|^2 S0 - xi
+// (dU = U(Y2) - U(Y1), U'* = (U'(Y1) + U'(Y2))/2, dU' = U'(Y2) - U'(Y1), kx,
+// kz the signed wavenumbers with 0 on the Nyquist lines).  The combinations
+// are linear in the contractions and their coefficients depend only on the
+// mean (frozen before the first batch), so batches are summed here:
+//   comb[p][t][k] (+)= T_t(p, k)
+// with the arithmetic in TC and the sum in TO: double / double on the plain
+// path; on the split path float / float for the first batch and float /
+// double once a second batch arrives (the per-pair sum is then promoted to
+// FP64 by k_promote).
+//
+// CTA = an 8 x 8 block of pairs (i1 in [8a, 8a+8), i2 in [8b, 8b+8), b >= a)
+// and KC consecutive wavenumbers.  All contractions of the block and of its
+// transposed partner block are staged through shared memory (rows of 8
+// consecutive y' values); then each thread forms the terms of its (pair, k)
+// items; stores are k-contiguous.
+#include "gke_common.cuh"
+#include "gke_kernels.h"
+
+namespace gke {
+
+constexpr int PB = 8;     // pair block edge
+
+template <typename TI> struct CombCfg;
+template <> struct CombCfg<float> { static constexpr int KC = 8; };
+template <> struct CombCfg<double> { static constexpr int KC = 4; };
+
+template <typename TI> constexpr size_t combine_smem_bytes()
+{
+    return (size_t)(2 * NJOB - 1) * CombCfg<TI>::KC * PB * (PB + 1) * sizeof(cplx<TI>);
+}
+size_t combine_smem(bool fp32) { return fp32 ? combine_smem_bytes<float>() : combine_smem_bytes<double>(); }
+int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::KC; }
+
+template <typename TI, typename TC, typename TO>
+__global__ void __launch_bounds__(256)
+k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
+          const double* __restrict__ prof, int beta, cplx<TO>* __restrict__ comb)
+{
+    constexpr int KC = CombCfg<TI>::KC;
+    typedef cplx<TI> C;
+    typedef cplx<TC> Z;
+    extern __shared__ __align__(16) unsigned char sh_raw_cb[];
+    // stage[slot][q][rr][cc]: slot 2 j = block of job j, 2 j + 1 = partner block
+    // (rows y in [8b, 8b+8), columns y' in [8a, 8a+8)); D has no partner slot
+    C* stage = (C*)sh_raw_cb;
+    const int nxh = nx / 2 + 1, Nk = nz * nxh;
+    const int nblk = (ny + PB - 1) / PB;
+    int bt = blockIdx.y, a = 0;
+    while (bt >= nblk - a) { bt -= nblk - a; ++a; }
+    const int b = a + bt;
+    const int k0 = blockIdx.x * KC;
+    const int nslot = 2 * NJOB - 1;
+    auto at = [&](int slot, int q, int rr, int cc) -> C& {
+        return stage[((slot * KC + q) * PB + rr) * (PB + 1) + cc];
+    };
+    for (int e = threadIdx.x; e < nslot * KC * PB * PB; e += blockDim.x) {
+        const int slot = e / (KC * PB * PB);
+        const int rem = e - slot * KC * PB * PB;
+        const int q = rem / (PB * PB), rr = (rem / PB) % PB, cc = rem % PB;
+        const int j = slot >> 1, partner = slot & 1;
+        const int kq = k0 + q;
+        const int y = partner ? PB * b + rr : PB * a + rr;
+        const int yp = partner ? PB * a + cc : PB * b + cc;
+        C v = mk((TI)0, (TI)0);
+        if (kq < Nk && y < ny && yp < ny) v = raw[(((long long)j * Nk + kq) * ny + y) * ny + yp];
+        at(slot, q, rr, cc) = v;
+    }
+    __syncthreads();
+    for (int it = threadIdx.x; it < KC * PB * PB; it += blockDim.x) {
+        const int kk = it % KC, pm = it / KC, r = pm / PB, m = pm % PB;
+        const int k = k0 + kk, i1 = PB * a + r, i2 = PB * b + m;
+        if (k >= Nk || i1 >= ny || i2 >= ny || i2 < i1) continue;
+        const int kz_i = k / nxh, kx_i = k - kz_i * nxh;
+        const TC kx = (TC)(6.283185307179586476925286766559 * signed_bin(kx_i, nx) / Lx);
+        const TC kz = (TC)(6.283185307179586476925286766559 * signed_bin(kz_i, nz) / Lz);
+        const TC dU = (TC)(prof[PR_U * ny + i2] - prof[PR_U * ny + i1]);
+        const TC Upm = (TC)(0.5 * (prof[PR_DU * ny + i1] + prof[PR_DU * ny + i2]));
+        const TC dUp = (TC)(prof[PR_DU * ny + i2] - prof[PR_DU * ny + i1]);
+        const TC nuc = (TC)nu;
+        auto v12 = [&](int j) { C v = at(2 * j, kk, r, m); return mk((TC)v.x, (TC)v.y); };
+        auto v21 = [&](int j) { C v = at(2 * j + 1, kk, m, r); return mk((TC)v.x, -(TC)v.y); };  // conj
+        const Z S0 = v12(J_D);
+        const Z E12 = v12(J_E), E21 = v21(J_E);
+        const Z S1 = E12 + E21, S2 = E21 - E12;
+        const Z S3 = v12(J_F) + v21(J_F);
+        const Z S4 = v12(J_GX) - v21(J_GX);
+        const Z S6 = v12(J_GZ) - v21(J_GZ);
+        const Z Q12 = v12(J_QV), Q21 = v21(J_QV), X12 = v12(J_X), X21 = v21(J_X);
+        const Z S5 = (Q12 + X12) - (Q21 + X21);
+        const Z S7 = (Q12 - X12) + (Q21 - X21);
+        Z T[NTERM];
+        T[T_A] = (TC)(-2) * S0;
+        T[T_PHIX] = S4 + ((TC)(-2) * dU) * S0 + ((TC)4 * nuc * kx) * mul_i(S0);
+        T[T_PHIY] = S5;
+        T[T_PHIZ] = S6 + ((TC)4 * nuc * kz) * mul_i(S0);
+        T[T_PHI] = (TC)0.5 * S7 - (TC)2 * S3;
+        T[T_XI] = ((TC)2 * Upm) * S1 - dUp * S2;
+        T[T_RES] = kx * mul_i(S4) + kz * mul_i(S6) + ((TC)(-2) * dU * kx) * mul_i(S0)
+                 + ((TC)(-4) * nuc * (kx * kx + kz * kz)) * S0 - T[T_XI];
+        cplx<TO>* dst = comb + pair_index(i1, i2, ny) * NTERM * (long long)Nk + k;
+        #pragma unroll
+        for (int t = 0; t < NTERM; ++t) {
+            cplx<TO> v = mk((TO)T[t].x, (TO)T[t].y);
+            if (beta) v = v + dst[(long long)t * Nk];
+            dst[(long long)t * Nk] = v;
+        }
+    }
+}
+
+// comb64[i] = comb32[i] (promotion of the first batch's per-pair sums)
+__global__ void k_promote(const zf* __restrict__ src, long long n, zd* __restrict__ dst)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = mk((double)src[i].x, (double)src[i].y);
+}
+
+// comb (+)= term spectra of one batch.  fp32_in: raw and arithmetic in FP32;
+// out64: comb is FP64 (else FP32)
+int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
+                   double nu, const double* prof, int beta, void* comb, cudaStream_t st)
+{
+    const int nxh = nx / 2 + 1, Nk = nz * nxh;
+    const int kc = combine_kc(fp32_in);
+    const int nblk = (ny + PB - 1) / PB;
+    dim3 grid((Nk + kc - 1) / kc, nblk * (nblk + 1) / 2);
+    if (!fp32_in)
+        k_combine<double, double, double><<<grid, 256, combine_smem(false), st>>>(
+            (const zd*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, (zd*)comb);
+    else if (out64)
+        k_combine<float, float, double><<<grid, 256, combine_smem(true), st>>>(
+            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, (zd*)comb);
+    else
+        k_combine<float, float, float><<<grid, 256, combine_smem(true), st>>>(
+            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, (zf*)comb);
+    return 1;
+}
+
+int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st)
+{
+    k_promote<<<152 * 8, 256, 0, st>>>((const zf*)comb32, n, (zd*)comb64);
+    return 1;
+}
+
+cudaError_t combine_set_attrs()
+{
+    const void* ks[] = {(const void*)k_combine<float, float, float>, (const void*)k_combine<float, float, double>};
+    for (const void* k : ks) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(true));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaFuncSetAttribute((const void*)k_combine<double, double, double>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(false));
+}
+
+}  // namespace gke

@@ -1,14 +1,16 @@
 // gke_common.cuh -- device helpers shared by the GKE kernels.
 //
 // Layout conventions of the Parseval path (all device memory, C order):
-//   fields   complex [nsnap][4][ny][nz][nxh]   input Fourier coefficients of
+//   fields   complex128 [nsnap][4][ny][nz][nxh] input Fourier coefficients of
 //            u, v, w, p, forward-normalised: a_hat(k) = (1/(nx nz)) sum_x a e^{-ik.x}
-//   Xop      complex [NFIELD][Nk][ns][ny]      correlator operands, one block
+//   Xop      complex<TF> [NFIELD][Nk][ns][ny]  correlator operands, one block
 //            of ns x ny values per (field, wavenumber); Nk = nz * nxh,
-//            k = kz_index * nxh + kx_index
-//   acc_sq   complex [NJSQ][ny][ny][Nk]        per-wavenumber spectral sums of
-//            the cross contractions, ordered pairs (y, y')
-//   acc_D    complex [npair][Nk]               Hermitian contraction, pairs y <= y'
+//            k = kz_index * nxh + kx_index; TF = double (plain path) or
+//            float (split path)
+//   raw      complex [NJOB][Nk][ny][ny]        one batch's contractions, ordered
+//            pairs (y, y'), k-major (D: only y <= y' written)
+//   comb     complex128 [npair][NTERM][Nk]     per-pair term spectra summed over
+//            batches (the FP64 snapshot-sum accumulator)
 //   terms    double  [NTERM][npair][nz][nx]    GKE terms in separation space,
 //            separation index (m_z, m_x) in FFT order, r = (m_x Lx/nx, m_z Lz/nz)
 #pragma once
@@ -21,6 +23,8 @@ namespace gke {
 enum Field { F_U = 0, F_V, F_W, F_P, F_UU, F_VV, F_WW, F_UV, F_UW, F_VW, F_Q, NFIELD };
 // cross contractions over snapshots (ordered pairs); D (Hermitian) is kept apart
 enum JobSq { J_E = 0, J_F, J_GX, J_QV, J_X, J_GZ, NJSQ };   // J_X holds X2 = 2 X
+constexpr int J_D = NJSQ;          // Hermitian contraction D, stored after the square jobs
+constexpr int NJOB = NJSQ + 1;
 // output terms
 enum Term { T_A = 0, T_PHIX, T_PHIY, T_PHIZ, T_PHI, T_XI, T_RES, NTERM };
 // one-point statistics per y (FP64 sums over snapshots and the plane)
@@ -43,35 +47,84 @@ template <typename T> __device__ __forceinline__ cplx<T> mul_i(cplx<T> a) { retu
 
 __host__ __device__ __forceinline__ int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
-__device__ __forceinline__ int bitrev(int v, int bits) { return (int)(__brev((unsigned)v) >> (32 - bits)); }
 
-// In-place radix-2 decimation-in-time FFT of `nb` sequences of length n = 2^lg
-// stored at buf[b * ld + i], done by the whole thread block.  The data must
-// already be in bit-reversed order (use bitrev() when loading).
-// tw[m] = exp(-2 pi i m / n), m < n/2 (host-computed); sign = -1 forward, +1
-// inverse (the inverse is unnormalised).  Ends with __syncthreads().
-template <typename T>
-__device__ void fft_radix2_block(cplx<T>* buf, int ld, int nb, int lg, const cplx<T>* __restrict__ tw, int sign)
+// Forward transform X[k] = sum_n x[n] e^{-2 pi i n k / N}, N = 2^lg, of nb
+// sequences x[b * ld + n], by the whole thread block: Stockham autosort
+// (natural order in and out), one radix-2 stage first when lg is odd, then
+// radix-4 stages.  Stage with current span Ns and radix R: butterfly j takes
+// x[j + r N/R] (r < R), multiplies by w^(r (j mod Ns) N/(Ns R)), applies the
+// R-point DFT and stores to y[(j / Ns) Ns R + (j mod Ns) + r Ns]; the buffers
+// then swap.  tw[m] = e^{-2 pi i m / N}, m < N (host-computed, staged in
+// shared memory by the caller).  INV = true computes the unnormalised inverse
+// (conjugate in, forward transform, conjugate out).  Returns the buffer that
+// holds the result (x or y); begins and ends with __syncthreads().
+template <typename T, bool INV>
+__device__ cplx<T>* fft_block(cplx<T>* x, cplx<T>* y, int ld, int nb, int lg, const cplx<T>* tw)
 {
-    const int n = 1 << lg;
-    const int nh = n >> 1;
+    const int N = 1 << lg;
     __syncthreads();
-    for (int s = 1; s <= lg; ++s) {
-        const int half = 1 << (s - 1);
-        const int tstride = n >> s;            // twiddle step for this stage
-        for (int t = threadIdx.x; t < nb * nh; t += blockDim.x) {
-            int b = t / nh, j = t - b * nh;
-            int grp = j >> (s - 1), pos = j & (half - 1);
-            int i0 = grp * (half << 1) + pos, i1 = i0 + half;
-            cplx<T> w = tw[pos * tstride];
-            if (sign > 0) w.y = -w.y;
-            cplx<T>* p = buf + (size_t)b * ld;
-            cplx<T> a = p[i0], c = w * p[i1];
-            p[i0] = a + c;
-            p[i1] = a - c;
+    int Ns = 1;
+    bool first = true;
+    if (lg & 1) {
+        const int nbf = N >> 1;
+        for (int t = threadIdx.x; t < nb * nbf; t += blockDim.x) {
+            const int b = t / nbf, j = t - b * nbf;
+            const cplx<T>* src = x + (size_t)b * ld;
+            cplx<T> v0 = src[j], v1 = src[j + nbf];
+            if (INV) { v0.y = -v0.y; v1.y = -v1.y; }
+            cplx<T>* dst = y + (size_t)b * ld;
+            dst[2 * j] = v0 + v1;          // Ns = 1: no twiddle, idxD = 2 j
+            dst[2 * j + 1] = v0 - v1;
+        }
+        __syncthreads();
+        cplx<T>* tmp = x; x = y; y = tmp;
+        Ns = 2;
+        first = false;
+    }
+    while (Ns < N) {
+        const int nbf = N >> 2;
+        const int tws = N / (Ns * 4);
+        for (int t = threadIdx.x; t < nb * nbf; t += blockDim.x) {
+            const int b = t / nbf, j = t - b * nbf;
+            const int jm = j & (Ns - 1);
+            const cplx<T>* src = x + (size_t)b * ld;
+            cplx<T> v0 = src[j], v1 = src[j + nbf], v2 = src[j + 2 * nbf], v3 = src[j + 3 * nbf];
+            if (INV && first) { v0.y = -v0.y; v1.y = -v1.y; v2.y = -v2.y; v3.y = -v3.y; }
+            if (Ns > 1) {
+                const int m = jm * tws;
+                v1 = v1 * tw[m];
+                v2 = v2 * tw[2 * m];
+                v3 = v3 * tw[3 * m];
+            }
+            const cplx<T> a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3;
+            const cplx<T> d = v1 - v3;
+            const cplx<T> a3 = mk(d.y, -d.x);          // -i (v1 - v3)
+            cplx<T>* dst = y + (size_t)b * ld + (j - jm) * 4 + jm;
+            dst[0] = a0 + a2;
+            dst[Ns] = a1 + a3;
+            dst[2 * Ns] = a0 - a2;
+            dst[3 * Ns] = a1 - a3;
+        }
+        __syncthreads();
+        cplx<T>* tmp = x; x = y; y = tmp;
+        Ns <<= 2;
+        first = false;
+    }
+    if (INV) {
+        for (int t = threadIdx.x; t < nb * N; t += blockDim.x) {
+            const int b = t / N, i = t - b * N;
+            x[(size_t)b * ld + i].y = -x[(size_t)b * ld + i].y;
         }
         __syncthreads();
     }
+    return x;
+}
+
+// stage the N-entry twiddle table in shared memory (call before fft_block)
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cplx<T>* sh_tw, const cplx<T>* __restrict__ tw, int N)
+{
+    for (int i = threadIdx.x; i < N; i += blockDim.x) sh_tw[i] = tw[i];
 }
 
 // signed wavenumber index of FFT bin m of an n-point transform, 0 at Nyquist

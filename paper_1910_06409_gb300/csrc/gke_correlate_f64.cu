@@ -13,7 +13,8 @@
 // (the y-flux triple terms are QV + X2 and QV - X2, formed later).
 //
 // CTA = one wavenumber and one job; it walks 32 x 32 tiles of (y, y'), each
-// thread holding a 2 x 2 block of complex accumulators.  DFMA bound.
+// thread holding a 2 x 2 block of complex accumulators, and writes the batch's
+// contraction to raw[job][k][y][y'] (D: y <= y' only).  DFMA bound.
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -41,8 +42,7 @@ void upload_jobs(cudaStream_t st)
 #define SCH 8       // snapshots per shared-memory chunk
 
 __global__ void __launch_bounds__(256)
-k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, int beta,
-                zd* __restrict__ acc_sq, zd* __restrict__ acc_D)
+k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restrict__ raw)
 {
     __shared__ zd As[SCH][CT];
     __shared__ zd Bs[SCH][CT];
@@ -93,16 +93,8 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, int beta,
                 for (int b = 0; b < 2; ++b) {
                     int y = y0 + ty + 16 * a, yp = y1 + tx + 16 * b;
                     if (y >= ny || yp >= ny) continue;
-                    zd* dst;
-                    if (herm) {
-                        if (yp < y) continue;
-                        dst = acc_D + pair_index(y, yp, ny) * Nk + k;
-                    } else {
-                        dst = acc_sq + (((long long)job * ny + y) * ny + yp) * Nk + k;
-                    }
-                    zd v = acc[a][b];
-                    if (beta) v = v + *dst;
-                    *dst = v;
+                    if (herm && yp < y) continue;
+                    raw[(((long long)job * Nk + k) * ny + y) * ny + yp] = acc[a][b];
                 }
         }
     }

@@ -2,6 +2,7 @@
 // library (not part of the public C ABI, which is include/gke.h).
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include "gke_common.cuh"
 
 namespace gke {
@@ -9,28 +10,45 @@ namespace gke {
 // rows of the device profile array prof[NPR][ny]
 enum Prof { PR_U = 0, PR_V, PR_W, PR_P, PR_DU, PR_EPS, PR_Q, PR_UV, PR_PV, PR_QU, PR_QV, PR_QW, NPR };
 
-struct PairCoef { double dU, Upm, dUp, nu, inv_count; };
-
 void upload_jobs(cudaStream_t st);
+size_t combine_smem(bool fp32);
+int combine_kc(bool fp32);
 
 __global__ void k_mean_accum(const zd* fields, int ns, int ny, long long plane, double* mean_sum);
-__global__ void k_load_linear(const zd* fields, int ns, int ny, int Nk, const double* mean, zd* Xop,
-                              int* nonfinite);
-__global__ void k_col_inverse(const zd* fields_s, int ny, int nz, int nxh, int CW, const double* mean,
-                              const zd* tw_z, zd* G);
-__global__ void k_row_products(const zd* G, int ny, int nz, int nx, int RZ, const zd* tw_x, zd* H,
-                               double* part);
-__global__ void k_col_forward(const zd* H, int ny, int nz, int nxh, int CW, int YB, int s, int ns,
-                              const zd* tw_z, zd* Xop);
-__global__ void k_eps(const zd* Xop, int ns, int ny, int nz, int nxh, int nx, double Lx, double Lz,
-                      const double* fdw, const int* fdl0, int kchunk, double* part);
 __global__ void k_reduce_partials(const double* part, int nvals, int nb, double* out);
-__global__ void k_correlate_f64(const zd* Xop, int ns, int ny, int Nk, int beta, zd* acc_sq, zd* acc_D);
-__global__ void k_terms_colpass(const zd* acc_sq, const zd* acc_D, const int* pair_i, long long pair0,
-                                int ny, int nz, int nx, int CW, double Lx, double Lz, double nu,
-                                double inv_count, const double* prof, const zd* tw_z, zd* W);
-__global__ void k_terms_rowpass(const zd* W, const int* pair_i, long long pair0, long long npair, int ny,
-                                int nz, int nx, int RZ, const double* prof, const zd* tw_x, double* terms);
+__global__ void k_correlate_f64(const zd* Xop, int ns, int ny, int Nk, zd* raw);
+
+// products stage (gke_products.cu); complex<TF> buffers passed as void*
+struct ProdArgs {
+    const zd* fields; int ns, ny, nz, nx, nxh, Nk;
+    const double* mean; void* Xop; void* G; void* H; const void* tw_x; const void* tw_z;
+    double* part; double* stats; int* nonfinite;
+    int cw_ci, rz_rp, cw_cf, yb_cf, eps_kchunk;
+    double Lx, Lz; const double* fdw; const int* fdl0;
+    cudaStream_t st;
+};
+template <typename TF> int products_launch(const ProdArgs& a);
+cudaError_t products_set_attrs(int lim);
+
+// term spectra (gke_combine.cu)
+int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
+                   double nu, const double* prof, int beta, void* comb, cudaStream_t st);
+int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st);
+cudaError_t combine_set_attrs();
+
+// inverse transforms (gke_terms.cu)
+struct TermArgs {
+    bool fp32;            // split path: FP32 transforms and FP32 terms
+    bool comb64;          // comb holds complex128 (else complex64)
+    const void* comb; void* W; const int* pair_i; long long npair, pair_chunk;
+    int ny, nz, nx, cw, rz; double inv_count; const double* prof; const void* tw_x; const void* tw_z;
+    void* terms; float* spec; cudaStream_t st;
+};
+int terms_launch(const TermArgs& a);
+cudaError_t terms_set_attrs(int lim);
+int stencil_launch(bool fp32, void* terms, float* spec, long long npair, const int* pair_i, int ny, int nz, int nx,
+                   double nu, const double* fdw, const int* fdl0, const double* prof, cudaStream_t st);
+
 __global__ void k_stencil_A(double* terms, long long npair, const int* pair_i, int ny, int nz, int nx,
                             double nu, const double* fdw, const int* fdl0);
 __global__ void k_stencil_res(double* terms, long long npair, const int* pair_i, int ny, int nz, int nx,

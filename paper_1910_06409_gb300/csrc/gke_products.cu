@@ -5,7 +5,8 @@
 //
 // Transforms along z act on tiles of adjacent kx columns; transforms along x
 // on two real rows at a time (packed as real and imaginary part of one
-// complex sequence).  All in FP64.
+// complex sequence).  The transform arithmetic runs in TF = double (plain
+// path) or float (split path); one-point sums are always FP64.
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -25,11 +26,14 @@ __global__ void k_mean_accum(const zd* __restrict__ fields, int ns, int ny, long
     mean_sum[idx] += acc;
 }
 
+template <typename TF> __device__ __forceinline__ cplx<TF> cvt(zd v) { return mk((TF)v.x, (TF)v.y); }
+
 // ---------------------------------------------- linear fields -> operands
 // Xop[f][k][s][y] = fields[s][f][y][k] - mean_f(y) [k == 0], f = u, v, w, p.
 // 32x32 (k, y) tile transpose through shared memory; flags non-finite input.
+template <typename TF>
 __global__ void k_load_linear(const zd* __restrict__ fields, int ns, int ny, int Nk,
-                              const double* __restrict__ mean, zd* __restrict__ Xop,
+                              const double* __restrict__ mean, cplx<TF>* __restrict__ Xop,
                               int* __restrict__ nonfinite)
 {
     __shared__ zd tile[32][33];
@@ -49,21 +53,28 @@ __global__ void k_load_linear(const zd* __restrict__ fields, int ns, int ny, int
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         int k = k0 + r, y = y0 + threadIdx.x;
-        if (y < ny && k < Nk) Xop[(((long long)f * Nk + k) * ns + s) * ny + y] = tile[threadIdx.x][r];
+        if (y < ny && k < Nk)
+            Xop[(((long long)f * Nk + k) * ns + s) * ny + y] = cvt<TF>(tile[threadIdx.x][r]);
     }
 }
 
 // ------------------------------------- inverse transform along z (columns)
 // One snapshot: G[f][y][z][kx] = sum_kz f_hat(y, kz, kx) e^{+i kz z} for f =
 // u, v, w, p, mean removed from the (0,0) coefficient.  CTA = CW adjacent kx
-// columns of one (field, y) plane; dynamic shared memory CW * nz complex.
+// columns of one (field, y) plane; dynamic shared memory (1 + 2 CW) nz complex.
+template <typename TF>
 __global__ void k_col_inverse(const zd* __restrict__ fields_s, int ny, int nz, int nxh, int CW,
-                              const double* __restrict__ mean, const zd* __restrict__ tw_z,
-                              zd* __restrict__ G)
+                              const double* __restrict__ mean, const cplx<TF>* __restrict__ tw_z,
+                              cplx<TF>* __restrict__ G)
 {
-    extern __shared__ zd sh_ci[];
+    typedef cplx<TF> C;
+    extern __shared__ __align__(16) unsigned char sh_raw_ci[];
+    C* stw = (C*)sh_raw_ci;                  // [nz] twiddles
+    C* b0 = stw + nz;                        // [CW][nz] x2 (ping-pong)
+    C* b1 = b0 + CW * nz;
     const int kx0 = blockIdx.x * CW, y = blockIdx.y, f = blockIdx.z;
     const int lg = ilog2(nz);
+    load_twiddles(stw, tw_z, nz);
     const zd* src = fields_s + ((long long)f * ny + y) * nz * nxh;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
         int c = t % CW, kz = t / CW, kx = kx0 + c;
@@ -72,13 +83,13 @@ __global__ void k_col_inverse(const zd* __restrict__ fields_s, int ny, int nz, i
             v = src[(long long)kz * nxh + kx];
             if (kx == 0 && kz == 0) v.x -= mean[f * ny + y];
         }
-        sh_ci[c * nz + bitrev(kz, lg)] = v;
+        b0[c * nz + kz] = cvt<TF>(v);
     }
-    fft_radix2_block(sh_ci, nz, CW, lg, tw_z, +1);
-    zd* dst = G + ((long long)f * ny + y) * nz * nxh;
+    const C* res = fft_block<TF, true>(b0, b1, nz, CW, lg, stw);
+    C* dst = G + ((long long)f * ny + y) * nz * nxh;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
         int c = t % CW, z = t / CW, kx = kx0 + c;
-        if (kx < nxh) dst[(long long)z * nxh + kx] = sh_ci[c * nz + z];
+        if (kx < nxh) dst[(long long)z * nxh + kx] = res[c * nz + z];
     }
 }
 
@@ -97,50 +108,56 @@ __device__ __forceinline__ double warp_sum(double v) {
 // 1/nx.  Row sums of q, uv, pv, q u, q v, q w of the CTA's rows go to
 // part[6][ny][gridDim.x] (reduced in a fixed order by k_reduce_partials, so
 // repeated runs give bit-identical results).
-// Shared memory: RZ * 6 * nx complex.
-__global__ void k_row_products(const zd* __restrict__ G, int ny, int nz, int nx, int RZ,
-                               const zd* __restrict__ tw_x, zd* __restrict__ H,
+// Shared memory: (1 + 8 RZ) nx complex.
+template <typename TF>
+__global__ void k_row_products(const cplx<TF>* __restrict__ G, int ny, int nz, int nx, int RZ,
+                               const cplx<TF>* __restrict__ tw_x, cplx<TF>* __restrict__ H,
                                double* __restrict__ part)
 {
-    extern __shared__ zd sh_rp[];
+    typedef cplx<TF> C;
+    extern __shared__ __align__(16) unsigned char sh_raw_rp[];
     const int nxh = nx / 2 + 1, lg = ilog2(nx);
     const int z0 = blockIdx.x * RZ, y = blockIdx.y;
     const int nrow = min(RZ, nz - z0);
-    zd* inv = sh_rp;                  // [nrow][2][nx]
-    zd* fwd = sh_rp + RZ * 2 * nx;    // [nrow][4][nx]
+    C* stw = (C*)sh_raw_rp;           // [nx] twiddles
+    C* inv0 = stw + nx;               // [nrow][2][nx]  x2 (ping-pong)
+    C* inv1 = inv0 + RZ * 2 * nx;
+    C* fwd = inv1 + RZ * 2 * nx;      // [nrow][4][nx]; its scratch is inv0..inv1
+    load_twiddles(stw, tw_x, nx);
     for (int t = threadIdx.x; t < nrow * 2 * nx; t += blockDim.x) {
         int r = t / (2 * nx), rem = t - r * 2 * nx, q = rem / nx, k = rem - q * nx;
         int z = z0 + r;
-        const zd* ga = G + (((long long)(2 * q) * ny + y) * nz + z) * nxh;
-        const zd* gb = G + (((long long)(2 * q + 1) * ny + y) * nz + z) * nxh;
-        zd A, B;
+        const C* ga = G + (((long long)(2 * q) * ny + y) * nz + z) * nxh;
+        const C* gb = G + (((long long)(2 * q + 1) * ny + y) * nz + z) * nxh;
+        C A, B;
         if (k < nxh) { A = ga[k]; B = gb[k]; } else { A = conj(ga[nx - k]); B = conj(gb[nx - k]); }
-        if (k == 0 || 2 * k == nx) { A.y = 0.0; B.y = 0.0; }
-        inv[(r * 2 + q) * nx + bitrev(k, lg)] = mk(A.x - B.y, A.y + B.x);   // A + i B
+        if (k == 0 || 2 * k == nx) { A.y = 0; B.y = 0; }
+        inv0[(r * 2 + q) * nx + k] = mk(A.x - B.y, A.y + B.x);   // A + i B
     }
-    fft_radix2_block(inv, nx, 2 * nrow, lg, tw_x, +1);
+    const C* ph = fft_block<TF, true>(inv0, inv1, nx, 2 * nrow, lg, stw);
     double s_q = 0, s_uv = 0, s_pv = 0, s_qu = 0, s_qv = 0, s_qw = 0;
     for (int t = threadIdx.x; t < nrow * nx; t += blockDim.x) {
         int r = t / nx, x = t - r * nx;
-        zd a = inv[(r * 2) * nx + x], b = inv[(r * 2 + 1) * nx + x];
-        double u = a.x, v = a.y, w = b.x, p = b.y;
-        double q = u * u + v * v + w * w;
-        s_q += q; s_uv += u * v; s_pv += p * v; s_qu += q * u; s_qv += q * v; s_qw += q * w;
-        int br = bitrev(x, lg);
-        fwd[(r * 4 + 0) * nx + br] = mk(u * u, v * v);
-        fwd[(r * 4 + 1) * nx + br] = mk(w * w, u * v);
-        fwd[(r * 4 + 2) * nx + br] = mk(u * w, v * w);
-        fwd[(r * 4 + 3) * nx + br] = mk(q, 0.0);
+        C a = ph[(r * 2) * nx + x], b = ph[(r * 2 + 1) * nx + x];
+        TF u = a.x, v = a.y, w = b.x, p = b.y;
+        TF q = u * u + v * v + w * w;
+        double ud = u, vd = v, wd = w, qd = (double)ud * ud + vd * vd + wd * wd;
+        s_q += qd; s_uv += ud * vd; s_pv += (double)p * vd; s_qu += qd * ud; s_qv += qd * vd; s_qw += qd * wd;
+        fwd[(r * 4 + 0) * nx + x] = mk(u * u, v * v);
+        fwd[(r * 4 + 1) * nx + x] = mk(w * w, u * v);
+        fwd[(r * 4 + 2) * nx + x] = mk(u * w, v * w);
+        fwd[(r * 4 + 3) * nx + x] = mk(q, (TF)0);
     }
-    fft_radix2_block(fwd, nx, 4 * nrow, lg, tw_x, -1);
-    const double inx = 1.0 / nx;
+    const C* sp = fft_block<TF, false>(fwd, inv0, nx, 4 * nrow, lg, stw);
+    const TF inx = (TF)1 / (TF)nx;
+    const TF h = (TF)0.5 * inx;
     for (int t = threadIdx.x; t < nrow * 4 * nxh; t += blockDim.x) {
         int r = t / (4 * nxh), rem = t - r * 4 * nxh, j = rem / nxh, k = rem - j * nxh;
-        const zd* seq = fwd + (r * 4 + j) * nx;
-        zd Z = seq[k], Zc = conj(seq[(nx - k) & (nx - 1)]);
-        zd A = (0.5 * inx) * (Z + Zc);
-        zd D = Z - Zc;
-        zd B = mk(0.5 * inx * D.y, -0.5 * inx * D.x);     // -i/2 (Z - Zc)
+        const C* seq = sp + (r * 4 + j) * nx;
+        C Z = seq[k], Zc = conj(seq[(nx - k) & (nx - 1)]);
+        C A = h * (Z + Zc);
+        C D = Z - Zc;
+        C B = mk(h * D.y, -h * D.x);     // -i/2 (Z - Zc)
         int z = z0 + r;
         H[(((long long)(2 * j) * ny + y) * nz + z) * nxh + k] = A;
         if (j < 3) H[(((long long)(2 * j + 1) * ny + y) * nz + z) * nxh + k] = B;
@@ -164,30 +181,36 @@ __global__ void k_row_products(const zd* __restrict__ G, int ny, int nz, int nx,
 // ---------------------------------- forward transform along z (columns)
 // One snapshot: Xop[4 + j][k][s][y] = (1/nz) sum_z H[j][y][z][kx] e^{-i kz z}
 // for the seven products.  CTA = CW kx columns x YB planes of one product;
-// dynamic shared memory CW * YB * nz complex.
-__global__ void k_col_forward(const zd* __restrict__ H, int ny, int nz, int nxh, int CW, int YB,
-                              int s, int ns, const zd* __restrict__ tw_z, zd* __restrict__ Xop)
+// dynamic shared memory (1 + 2 CW YB) nz complex.
+template <typename TF>
+__global__ void k_col_forward(const cplx<TF>* __restrict__ H, int ny, int nz, int nxh, int CW, int YB,
+                              int s, int ns, const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ Xop)
 {
-    extern __shared__ zd sh_cf[];
+    typedef cplx<TF> C;
+    extern __shared__ __align__(16) unsigned char sh_raw_cf[];
+    C* stw = (C*)sh_raw_cf;                 // [nz] twiddles
+    const int nb = CW * YB;
+    C* b0 = stw + nz;                       // [nb][nz] x2 (ping-pong)
+    C* b1 = b0 + nb * nz;
     const int kx0 = blockIdx.x * CW, y0 = blockIdx.y * YB, j = blockIdx.z;
     const int lg = ilog2(nz);
     const int Nk = nz * nxh;
-    const int nb = CW * YB;
+    load_twiddles(stw, tw_z, nz);
     for (int t = threadIdx.x; t < nb * nz; t += blockDim.x) {
         int c = t % CW, rem = t / CW, yy = rem % YB, z = rem / YB;
         int kx = kx0 + c, y = y0 + yy;
-        zd v = mk(0.0, 0.0);
+        C v = mk((TF)0, (TF)0);
         if (kx < nxh && y < ny) v = H[(((long long)j * ny + y) * nz + z) * nxh + kx];
-        sh_cf[(yy * CW + c) * nz + bitrev(z, lg)] = v;
+        b0[(yy * CW + c) * nz + z] = v;
     }
-    fft_radix2_block(sh_cf, nz, nb, lg, tw_z, -1);
-    const double inz = 1.0 / nz;
+    const C* res = fft_block<TF, false>(b0, b1, nz, nb, lg, stw);
+    const TF inz = (TF)1 / (TF)nz;
     for (int t = threadIdx.x; t < nb * nz; t += blockDim.x) {
         int yy = t % YB, rem = t / YB, c = rem % CW, kz = rem / CW;
         int kx = kx0 + c, y = y0 + yy;
         if (kx < nxh && y < ny) {
             long long k = (long long)kz * nxh + kx;
-            Xop[((((long long)(F_UU + j)) * Nk + k) * ns + s) * ny + y] = inz * sh_cf[(yy * CW + c) * nz + kz];
+            Xop[((((long long)(F_UU + j)) * Nk + k) * ns + s) * ny + y] = inz * res[(yy * CW + c) * nz + kz];
         }
     }
 }
@@ -197,8 +220,9 @@ __global__ void k_col_forward(const zd* __restrict__ H, int ny, int nz, int nxh,
 //   part[y][chunk] = sum_{s, k in chunk, i} w_k [ (kx^2 + kz^2) |u_i(y,k)|^2 + |d_y u_i(y,k)|^2 ],
 // d_y by the 5-point FD stencil applied to the coefficients (it commutes with
 // the transform); w_k = 1 on the kx = 0 and kx = nx/2 lines, 2 elsewhere (half
-// spectrum).  One thread per y; partials reduced in a fixed order later.
-__global__ void k_eps(const zd* __restrict__ Xop, int ns, int ny, int nz, int nxh, int nx,
+// spectrum).  One thread per y, FP64 sums; partials reduced in a fixed order.
+template <typename TF>
+__global__ void k_eps(const cplx<TF>* __restrict__ Xop, int ns, int ny, int nz, int nxh, int nx,
                       double Lx, double Lz, const double* __restrict__ fdw, const int* __restrict__ fdl0,
                       int kchunk, double* __restrict__ part)
 {
@@ -217,11 +241,11 @@ __global__ void k_eps(const zd* __restrict__ Xop, int ns, int ny, int nz, int nx
             double k2 = kx * kx + kz * kz;
             for (int i = 0; i < 3; ++i)
                 for (int s = 0; s < ns; ++s) {
-                    const zd* col = Xop + (((long long)i * Nk + k) * ns + s) * ny;
-                    zd a = col[y];
-                    zd d = mk(0.0, 0.0);
-                    for (int l = 0; l < 5; ++l) d = d + w5[l] * col[l0 + l];
-                    acc += wk * (k2 * (a.x * a.x + a.y * a.y) + d.x * d.x + d.y * d.y);
+                    const cplx<TF>* col = Xop + (((long long)i * Nk + k) * ns + s) * ny;
+                    cplx<TF> a = col[y];
+                    double dr = 0.0, di = 0.0;
+                    for (int l = 0; l < 5; ++l) { dr += w5[l] * (double)col[l0 + l].x; di += w5[l] * (double)col[l0 + l].y; }
+                    acc += wk * (k2 * ((double)a.x * a.x + (double)a.y * a.y) + dr * dr + di * di);
                 }
         }
         part[(long long)y * gridDim.x + blockIdx.x] = acc;
@@ -237,5 +261,74 @@ __global__ void k_reduce_partials(const double* __restrict__ part, int nvals, in
     for (int b = 0; b < nb; ++b) acc += part[(long long)j * nb + b];
     out[j] += acc;
 }
+
+// ------------------------------------------------------------------ host
+// Launch sequence of the products stage for one batch (snapshots one by one).
+template <typename TF>
+int products_launch(const ProdArgs& a)
+{
+    typedef cplx<TF> C;
+    const int ny = a.ny, Nk = a.Nk, nxh = a.nxh, nz = a.nz, nx = a.nx, ns = a.ns;
+    cudaStream_t st = a.st;
+    C* Xop = (C*)a.Xop;
+    int launches = 0;
+    k_load_linear<TF><<<dim3((Nk + 31) / 32, (ny + 31) / 32, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk,
+                                                                                           a.mean, Xop, a.nonfinite);
+    ++launches;
+    for (int s = 0; s < ns; ++s) {
+        const zd* fs = a.fields + (size_t)s * 4 * ny * Nk;
+        k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), st>>>(
+            fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, (C*)a.G);
+        const int nrb = (nz + a.rz_rp - 1) / a.rz_rp;
+        k_row_products<TF><<<dim3(nrb, ny), 256, (1 + 8 * a.rz_rp) * nx * sizeof(C), st>>>(
+            (const C*)a.G, ny, nz, nx, a.rz_rp, (const C*)a.tw_x, (C*)a.H, a.part);
+        k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(a.part, 6 * ny, nrb, a.stats);
+        k_col_forward<TF><<<dim3((nxh + a.cw_cf - 1) / a.cw_cf, (ny + a.yb_cf - 1) / a.yb_cf, 7), 256,
+                            (1 + 2 * a.cw_cf * a.yb_cf) * nz * sizeof(C), st>>>((const C*)a.H, ny, nz, nxh, a.cw_cf,
+                                                                                  a.yb_cf,
+                                                                        s, ns, (const C*)a.tw_z, Xop);
+        launches += 4;
+    }
+    const int neb = (Nk + a.eps_kchunk - 1) / a.eps_kchunk;
+    k_eps<TF><<<neb, 128, 0, st>>>(Xop, ns, ny, nz, nxh, nx, a.Lx, a.Lz, a.fdw, a.fdl0, a.eps_kchunk, a.part);
+    k_reduce_partials<<<(ny + 127) / 128, 128, 0, st>>>(a.part, ny, neb, a.stats + S_EPS * ny);
+    return launches + 2;
+}
+template int products_launch<double>(const ProdArgs&);
+template int products_launch<float>(const ProdArgs&);
+
+static cudaError_t set_dyn_smem(const void* k, int lim)
+{
+    cudaFuncAttributes fa;
+    cudaError_t r = cudaFuncGetAttributes(&fa, k);
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - (int)fa.sharedSizeBytes);
+    return r;
+}
+
+cudaError_t products_set_attrs(int lim)
+{
+    const void* ks[] = {(const void*)k_col_inverse<double>, (const void*)k_row_products<double>,
+                        (const void*)k_col_forward<double>, (const void*)k_col_inverse<float>,
+                        (const void*)k_row_products<float>, (const void*)k_col_forward<float>};
+    cudaError_t e = cudaSuccess;
+    for (const void* k : ks) { cudaError_t r = set_dyn_smem(k, lim); if (r != cudaSuccess) e = r; }
+    return e;
+}
+
+// explicit instantiations
+#define GKE_INST(TF)                                                                                       \
+    template __global__ void k_load_linear<TF>(const zd*, int, int, int, const double*, cplx<TF>*, int*);  \
+    template __global__ void k_col_inverse<TF>(const zd*, int, int, int, int, const double*,               \
+                                               const cplx<TF>*, cplx<TF>*);                                \
+    template __global__ void k_row_products<TF>(const cplx<TF>*, int, int, int, int, const cplx<TF>*,      \
+                                                cplx<TF>*, double*);                                       \
+    template __global__ void k_col_forward<TF>(const cplx<TF>*, int, int, int, int, int, int, int,         \
+                                               const cplx<TF>*, cplx<TF>*);                                \
+    template __global__ void k_eps<TF>(const cplx<TF>*, int, int, int, int, int, double, double,           \
+                                       const double*, const int*, int, double*);
+GKE_INST(double)
+GKE_INST(float)
+#undef GKE_INST
 
 }  // namespace gke

@@ -8,7 +8,9 @@
 // range, so every slice is relative to its own value and no scaling is
 // needed).  The six slice products with i + j <= 2 keep ~24 significant bits:
 //   x y ~ x0 y0 + x0 y1 + x1 y0 + x0 y2 + x1 y1 + x2 y0,
-// accumulated in FP32 in tensor memory, then added to the FP64 spectral sums.
+// accumulated in FP32 in tensor memory and written as the batch's FP32
+// contraction raw[job][k][y][y'] (k_combine then adds it, in FP64, to the
+// per-pair term spectra).
 // FP32 accumulation rounds against the running sum, so the small cross-slice
 // products of all terms go first and the large x0 y0 products last: an output
 // then sees 2 T G large additions (T terms, G snapshot groups) instead of 12 T G.
@@ -142,7 +144,7 @@ __device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
 
 // Aop[k][f][g][mt][slice * 2 + part][A_BLK]; products (uu .. vw) carry the
 // factor 2 of the expansion; rows >= cov and snapshots >= ns are zero.
-__global__ void k_split_prep_A(const zd* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
+__global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
                                bf16* __restrict__ Aop)
 {
     long long b = blockIdx.x;
@@ -150,16 +152,16 @@ __global__ void k_split_prep_A(const zd* __restrict__ Xop, int ns, int ny, int N
     const int g = (int)(b % G); b /= G;
     const int f = (int)(b % NFIELD);
     const int k = (int)(b / NFIELD);
-    const double sc = (f >= F_UU && f <= F_VW) ? 2.0 : 1.0;
+    const float sc = (f >= F_UU && f <= F_VW) ? 2.f : 1.f;
     bf16* dst = Aop + ((((long long)k * NFIELD + f) * G + g) * MT + mt) * (long long)A_STAGE;
     for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
         const int s_l = e / TM, r = e - s_l * TM;
         const int y = mt * TM + r, s = g * KS + s_l;
-        zd v = mk(0.0, 0.0);
+        zf v = mk(0.f, 0.f);
         if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k) * ns + s) * ny + y];
         bf16 a0, a1, a2, b0, b1, b2;
-        split3((float)(sc * v.x), a0, a1, a2);
-        split3((float)(sc * v.y), b0, b1, b2);
+        split3(sc * v.x, a0, a1, a2);
+        split3(sc * v.y, b0, b1, b2);
         const int idx = cm_index(r, s_l, TM);
         dst[0 * A_BLK + idx] = a0; dst[2 * A_BLK + idx] = a1; dst[4 * A_BLK + idx] = a2;
         dst[1 * A_BLK + idx] = b0; dst[3 * A_BLK + idx] = b1; dst[5 * A_BLK + idx] = b2;
@@ -167,7 +169,7 @@ __global__ void k_split_prep_A(const zd* __restrict__ Xop, int ns, int ny, int N
 }
 
 // Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi | -br
-__global__ void k_split_prep_B(const zd* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
+__global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
                                bf16* __restrict__ Bop)
 {
     long long b = blockIdx.x;
@@ -179,11 +181,11 @@ __global__ void k_split_prep_B(const zd* __restrict__ Xop, int ns, int ny, int N
     for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
         const int s_l = e / TM, r = e - s_l * TM;
         const int y = nt * TM + r, s = g * KS + s_l;
-        zd v = mk(0.0, 0.0);
+        zf v = mk(0.f, 0.f);
         if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k) * ns + s) * ny + y];
         bf16 r0, r1, r2, i0, i1, i2;
-        split3((float)v.x, r0, r1, r2);
-        split3((float)v.y, i0, i1, i2);
+        split3(v.x, r0, r1, r2);
+        split3(v.y, i0, i1, i2);
         const bf16 sr[3] = {r0, r1, r2}, si[3] = {i0, i1, i2};
         for (int sl = 0; sl < 3; ++sl) {
             bf16* d = dst + sl * B_BLK;
@@ -214,7 +216,7 @@ __device__ __forceinline__ void decode_tile(int jt, int MT, int& job, int& mt, i
 
 __global__ void __launch_bounds__(128, 1)
 k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, int G, int MT, int ny, int cov,
-          int beta, zd* __restrict__ acc_sq, zd* __restrict__ acc_D, int* __restrict__ err)
+          zf* __restrict__ raw, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* sA = smem;
@@ -298,31 +300,27 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
     tc_fence_after();
 
     if (*s_ok) {
-        const int row = threadIdx.x;
-        const int y = mt * TM + row;
+        // TMEM lane = tile row; each warp moves its 32 rows x 32 columns through
+        // shared memory (the operand area is free now) so that every store
+        // writes 32 consecutive y' of one row (256 contiguous bytes).
+        const int lane = threadIdx.x & 31;
+        zf* xp = (zf*)smem + warp * 32 * 33;
         const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        zf* out = raw + ((long long)job * Nk + k) * ny * (long long)ny;
         for (int c = 0; c < 4; ++c) {
             uint32_t re[32], im[32];
             tmem_ld32(tbase + c * 32, re);
             tmem_ld32(tbase + 128 + c * 32, im);
             tmem_ld_wait();
-            if (y < cov) {
-                #pragma unroll 4
-                for (int j = 0; j < 32; ++j) {
-                    const int yp = nt * TM + c * 32 + j;
-                    if (yp >= cov) break;
-                    zd v = mk((double)__uint_as_float(re[j]), (double)__uint_as_float(im[j]));
-                    zd* dst;
-                    if (job == NJSQ) {
-                        if (yp < y) continue;
-                        dst = acc_D + pair_index(y, yp, ny) * Nk + k;
-                    } else {
-                        dst = acc_sq + (((long long)job * ny + y) * ny + yp) * Nk + k;
-                    }
-                    if (beta) v = v + *dst;
-                    *dst = v;
-                }
+            #pragma unroll
+            for (int j = 0; j < 32; ++j) xp[lane * 33 + j] = mk(__uint_as_float(re[j]), __uint_as_float(im[j]));
+            __syncwarp();
+            const int yp = nt * TM + c * 32 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int y = mt * TM + warp * 32 + rr;
+                if (y < cov && yp < cov && (job != NJSQ || yp >= y)) out[(long long)y * ny + yp] = xp[rr * 33 + lane];
             }
+            __syncwarp();
         }
     }
     tc_fence_before();
@@ -336,8 +334,7 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
 // ------------------------------------------- edge rows / columns (FP32)
 // Entries with y >= cov or y' >= cov (the last row / column of a 128 m + 1
 // grid), FP32 products and sums on the CUDA cores, same coefficients.
-__global__ void k_corr_edge(const zd* __restrict__ Xop, int ns, int ny, int Nk, int cov, int beta,
-                            zd* __restrict__ acc_sq, zd* __restrict__ acc_D)
+__global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, int cov, zf* __restrict__ raw)
 {
     const int k = blockIdx.x, job = blockIdx.y;
     const TcJob jd = c_tcjobs[job];
@@ -351,20 +348,16 @@ __global__ void k_corr_edge(const zd* __restrict__ Xop, int ns, int ny, int Nk, 
         float sr = 0.f, si = 0.f;
         for (int t = 0; t < jd.nterm; ++t) {
             const float c = (jd.fa[t] >= F_UU && jd.fa[t] <= F_VW) ? 2.f : 1.f;
-            const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
-            const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+            const zf* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+            const zf* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
             for (int s = 0; s < ns; ++s) {
-                const zd a = A[(long long)s * ny + y], b = B[(long long)s * ny + yp];
-                const float ar = c * (float)a.x, ai = c * (float)a.y, br = (float)b.x, bi = (float)b.y;
-                sr = fmaf(ar, br, fmaf(ai, bi, sr));
-                si = fmaf(ar, bi, fmaf(-ai, br, si));
+                const zf a = A[(long long)s * ny + y], b = B[(long long)s * ny + yp];
+                const float ar = c * a.x, ai = c * a.y;
+                sr = fmaf(ar, b.x, fmaf(ai, b.y, sr));
+                si = fmaf(ar, b.y, fmaf(-ai, b.x, si));
             }
         }
-        zd v = mk((double)sr, (double)si);
-        zd* dst = (job == NJSQ) ? acc_D + pair_index(y, yp, ny) * Nk + k
-                                : acc_sq + (((long long)job * ny + y) * ny + yp) * Nk + k;
-        if (beta) v = v + *dst;
-        *dst = v;
+        raw[(((long long)job * Nk + k) * ny + y) * ny + yp] = mk(sr, si);
     }
 }
 
@@ -405,8 +398,8 @@ cudaError_t split_setup(cudaStream_t st)
     return cudaFuncSetAttribute((const void*)k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
 }
 
-gke_status split_correlate(SplitWork& w, const zd* Xop, int ns, int ny, int Nk, int beta, zd* acc_sq, zd* acc_D,
-                           cudaStream_t st, std::string& err, int* launches)
+gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, zf* raw, cudaStream_t st,
+                           std::string& err, int* launches)
 {
     int MT, cov;
     tile_geometry(ny, MT, cov);
@@ -417,10 +410,10 @@ gke_status split_correlate(SplitWork& w, const zd* Xop, int ns, int ny, int Nk, 
     k_split_prep_A<<<(unsigned)((long long)Nk * NFIELD * G * MT), 256, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Aop);
     k_split_prep_B<<<(unsigned)((long long)Nk * 3 * G * MT), 256, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Bop);
     const long long njt = (long long)NJSQ * MT * MT + MT * (MT + 1) / 2;
-    k_corr_tc<<<(unsigned)(Nk * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Nk, G, MT, ny, cov, beta, acc_sq, acc_D, w.err);
+    k_corr_tc<<<(unsigned)(Nk * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Nk, G, MT, ny, cov, raw, w.err);
     *launches = 3;
     if (cov < ny) {
-        k_corr_edge<<<dim3(Nk, NJSQ + 1), 128, 0, st>>>(Xop, ns, ny, Nk, cov, beta, acc_sq, acc_D);
+        k_corr_edge<<<dim3(Nk, NJSQ + 1), 128, 0, st>>>(Xop, ns, ny, Nk, cov, raw);
         *launches += 1;
     }
     cudaError_t e = cudaGetLastError();

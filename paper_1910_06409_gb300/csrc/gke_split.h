@@ -16,8 +16,8 @@ struct SplitWork {
 
 gke_status split_alloc(SplitWork& w, int ny, int ns, int Nk);
 cudaError_t split_setup(cudaStream_t st);
-gke_status split_correlate(SplitWork& w, const zd* Xop, int ns, int ny, int Nk, int beta, zd* acc_sq, zd* acc_D,
-                           cudaStream_t st, std::string& err, int* launches);
+gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, zf* raw, cudaStream_t st,
+                           std::string& err, int* launches);
 gke_status split_check(SplitWork& w, cudaStream_t st, std::string& err);
 void split_free(SplitWork& w);
 

@@ -1,150 +1,77 @@
-// gke_terms.cu -- from per-wavenumber spectral sums to the GKE terms.
+// gke_terms.cu -- from per-pair term spectra to the GKE terms.
 //
-// Inverse transform (Sec. 3.1, Eq. 9) of the spectra each term needs, the
-// one-point parts of the correlation expansion (Eq. 7), and the Step-3
-// finite-difference derivatives in Y1 / Y2 (Sec. 3.2, Eq. 10-11) with values
-// across the diagonal recovered by r-inversion (Sec. 3.3).
+// Inverse transform (Sec. 3.1, Eq. 9) of the term spectra comb[p][t][k]
+// (formed by k_combine), the one-point parts of the correlation expansion
+// (Eq. 7), and the Step-3 finite-difference derivatives in Y1 / Y2
+// (Sec. 3.2, Eq. 10-11) with values across the diagonal recovered by
+// r-inversion (Sec. 3.3).  One-point parts, with q = u_i u_i:
+//   A     : <q>1 + <q>2
+//   Phi_x : <qu>2 - <qu>1 + dU (<q>1 + <q>2)
+//   Phi_y : <qv>2 - <qv>1                                   (+ FD part)
+//   Phi_z : <qw>2 - <qw>1
+//   phi   : (<qv>1 + <qv>2)/2 + 2 (<pv>1 + <pv>2)          (+ FD part)
+//   xi    : -2 U'* (<uv>1 + <uv>2) - dU' (<uv>2 - <uv>1) - 2 (eps1 + eps2)
+//   res   : -xi                                             (+ FD parts)
 //
-// With S0 = D, S1 = E + E^H, S2 = E^H - E, S3 = F + F^H, S4 = Gx - Gx^H,
-// S5 = Gy - Gy^H, S6 = Gz - Gz^H, S7 = H + H^H (X^H(y, y') = conj X(y', y),
-// Gy = QV + X2, H = QV - X2 with X2 the stored 2 sum_i conj(u_i v) u_i),
-// every term is one inverse transform of a
-// linear combination of the S_n plus a part that depends only on (Y1, Y2):
-//   A     = F^-1[-2 S0]                                 + <q>1 + <q>2
-//   Phi_x = F^-1[S4 + (-2 dU + 4 i nu kx) S0]           + <qu>2 - <qu>1 + dU (<q>1 + <q>2)
-//   Phi_y = F^-1[S5]                                    + <qv>2 - <qv>1     (+ FD part)
-//   Phi_z = F^-1[S6 + 4 i nu kz S0]                     + <qw>2 - <qw>1
-//   phi   = F^-1[S7 / 2 - 2 S3]                         + (<qv>1 + <qv>2)/2 + 2 (<pv>1 + <pv>2)  (+ FD)
-//   xi    = F^-1[2 U'* S1 - dU' S2]                     - 2 U'* (<uv>1 + <uv>2) - dU' (<uv>2 - <uv>1) - 2 (eps1 + eps2)
-//   res   = F^-1[i kx S4 + i kz S6 - 2 i dU kx S0 - 4 nu |k|^2 S0] - xi   (+ FD parts)
-// (q = u_i u_i, dU = U(Y2) - U(Y1), U'* = (U'(Y1) + U'(Y2))/2, dU' = U'(Y2) - U'(Y1)).
+// Plain path: transforms, terms and stencils in FP64.  Split path:
+// transforms in FP32 and FP32 terms; the Step-3 stencils difference the
+// spectral part of each term (kept apart in FP32 scratch) in FP32 and the
+// one-point part, a function of (Y1, Y2) only, in FP64 once per pair, so the
+// large one-point values never pass through an FP32 difference.
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
 namespace gke {
 
-#define TWO_PI 6.283185307179586476925286766559
-
-// per-wavenumber combination of the spectral sums for one pair
-__device__ __forceinline__ void combos(const zd* __restrict__ acc_sq, const zd* __restrict__ acc_D,
-                                       long long p, int i1, int i2, int ny, int Nk, long long k,
-                                       double kx, double kz, const PairCoef& pc, zd T[NTERM])
+// -------------------------- column pass: inverse transform along z
+// W[pl][t][z][kx] = inv_count * sum_kz comb[p][t][kz, kx] e^{+i kz z}.
+// CTA = CW kx columns of one term of one pair; shared memory (1 + 2 CW) nz
+// complex.
+template <typename TF, typename TB>
+__global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pair0, int nz, int nx, int CW,
+                                double inv_count, const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ W)
 {
-    const long long sq = (long long)ny * ny;
-    const long long o12 = ((long long)i1 * ny + i2) * Nk + k, o21 = ((long long)i2 * ny + i1) * Nk + k;
-    const double ic = pc.inv_count;
-    zd S0 = ic * acc_D[p * Nk + k];
-    zd E12 = acc_sq[J_E * sq * Nk + o12], E21 = conj(acc_sq[J_E * sq * Nk + o21]);
-    zd F12 = acc_sq[J_F * sq * Nk + o12], F21 = conj(acc_sq[J_F * sq * Nk + o21]);
-    zd Gx12 = acc_sq[J_GX * sq * Nk + o12], Gx21 = conj(acc_sq[J_GX * sq * Nk + o21]);
-    zd Gz12 = acc_sq[J_GZ * sq * Nk + o12], Gz21 = conj(acc_sq[J_GZ * sq * Nk + o21]);
-    zd Q12 = acc_sq[J_QV * sq * Nk + o12], Q21 = conj(acc_sq[J_QV * sq * Nk + o21]);
-    zd X12 = acc_sq[J_X * sq * Nk + o12], X21 = conj(acc_sq[J_X * sq * Nk + o21]);
-    zd S1 = ic * (E12 + E21), S2 = ic * (E21 - E12), S3 = ic * (F12 + F21);
-    zd S4 = ic * (Gx12 - Gx21), S6 = ic * (Gz12 - Gz21);
-    zd S5 = ic * ((Q12 + X12) - (Q21 + X21));
-    zd S7 = ic * ((Q12 - X12) + (Q21 - X21));
-    const double nu = pc.nu;
-    T[T_A] = -2.0 * S0;
-    T[T_PHIX] = S4 + (-2.0 * pc.dU) * S0 + (4.0 * nu * kx) * mul_i(S0);
-    T[T_PHIY] = S5;
-    T[T_PHIZ] = S6 + (4.0 * nu * kz) * mul_i(S0);
-    T[T_PHI] = 0.5 * S7 - 2.0 * S3;
-    T[T_XI] = (2.0 * pc.Upm) * S1 - pc.dUp * S2;
-    T[T_RES] = kx * mul_i(S4) + kz * mul_i(S6) + (-2.0 * pc.dU * kx) * mul_i(S0)
-             + (-4.0 * nu * (kx * kx + kz * kz)) * S0 - T[T_XI];
-}
-
-__device__ __forceinline__ PairCoef pair_coef(const double* __restrict__ prof, int ny, int i1, int i2,
-                                              double nu, double inv_count)
-{
-    PairCoef pc;
-    pc.dU = prof[PR_U * ny + i2] - prof[PR_U * ny + i1];
-    pc.Upm = 0.5 * (prof[PR_DU * ny + i1] + prof[PR_DU * ny + i2]);
-    pc.dUp = prof[PR_DU * ny + i2] - prof[PR_DU * ny + i1];
-    pc.nu = nu;
-    pc.inv_count = inv_count;
-    return pc;
-}
-
-// -------------------------- column pass: combine + inverse transform along z
-// W[pl][t][z][kx] = sum_kz T_t(kz, kx) e^{+i kz z}, pl = local pair index.
-// CTA = CW kx columns of one pair; shared memory NTERM * CW * nz complex.
-__global__ void k_terms_colpass(const zd* __restrict__ acc_sq, const zd* __restrict__ acc_D,
-                                const int* __restrict__ pair_i, long long pair0, int ny, int nz, int nx,
-                                int CW, double Lx, double Lz, double nu, double inv_count,
-                                const double* __restrict__ prof, const zd* __restrict__ tw_z,
-                                zd* __restrict__ W)
-{
-    extern __shared__ zd sh_tc[];
+    typedef cplx<TF> C;
+    extern __shared__ __align__(16) unsigned char sh_raw_tc[];
+    C* stw = (C*)sh_raw_tc;
+    C* b0 = stw + nz;
+    C* b1 = b0 + CW * nz;
     const int nxh = nx / 2 + 1, Nk = nz * nxh, lg = ilog2(nz);
-    const int kx0 = blockIdx.x * CW;
-    const long long pl = blockIdx.y, p = pair0 + pl;
-    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
-    const PairCoef pc = pair_coef(prof, ny, i1, i2, nu, inv_count);
+    const int kx0 = blockIdx.x * CW, q = blockIdx.y;
+    const long long pl = blockIdx.z, p = pair0 + pl;
+    const TF ic = (TF)inv_count;
+    load_twiddles(stw, tw_z, nz);
+    const cplx<TB>* src = comb + (p * NTERM + q) * (long long)Nk;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
-        int c = t % CW, kz_i = t / CW, kx_i = kx0 + c;
-        zd T[NTERM];
+        const int c = t % CW, kz_i = t / CW, kx_i = kx0 + c;
+        C v = mk((TF)0, (TF)0);
         if (kx_i < nxh) {
-            double kx = TWO_PI * signed_bin(kx_i, nx) / Lx;
-            double kz = TWO_PI * signed_bin(kz_i, nz) / Lz;
-            combos(acc_sq, acc_D, p, i1, i2, ny, Nk, (long long)kz_i * nxh + kx_i, kx, kz, pc, T);
-        } else {
-            for (int q = 0; q < NTERM; ++q) T[q] = mk(0.0, 0.0);
+            const cplx<TB> x = src[(long long)kz_i * nxh + kx_i];
+            v = mk(ic * (TF)x.x, ic * (TF)x.y);
         }
-        int br = bitrev(kz_i, lg);
-        for (int q = 0; q < NTERM; ++q) sh_tc[(q * CW + c) * nz + br] = T[q];
+        b0[c * nz + kz_i] = v;
     }
-    fft_radix2_block(sh_tc, nz, NTERM * CW, lg, tw_z, +1);
-    for (int t = threadIdx.x; t < NTERM * CW * nz; t += blockDim.x) {
-        int c = t % CW, rem = t / CW, z = rem % nz, q = rem / nz, kx_i = kx0 + c;
-        if (kx_i < nxh) W[((pl * NTERM + q) * nz + z) * nxh + kx_i] = sh_tc[(q * CW + c) * nz + z];
+    const C* res = fft_block<TF, true>(b0, b1, nz, CW, lg, stw);
+    C* dst = W + (pl * NTERM + q) * (long long)nz * nxh;
+    for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
+        const int c = t % CW, z = t / CW, kx_i = kx0 + c;
+        if (kx_i < nxh) dst[(long long)z * nxh + kx_i] = res[c * nz + z];
     }
 }
 
-// ------------------------------ row pass: C2R along x + one-point parts
-// terms[t][p][z][x] = sum_kx W[pl][t][z][kx] e^{+i kx x} + onepoint_t(Y1, Y2).
-// Terms are transformed two at a time (t0 + i t1).  CTA = RZ rows of one pair;
-// shared memory RZ * 4 * nx complex.
-__global__ void k_terms_rowpass(const zd* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
-                                long long npair, int ny, int nz, int nx, int RZ,
-                                const double* __restrict__ prof, const zd* __restrict__ tw_x,
-                                double* __restrict__ terms)
+// one-point parts of the seven terms at the pair (i1, i2), FP64
+__device__ __forceinline__ void onepoint(const double* __restrict__ pr, int ny, int i1, int i2, double one[NTERM])
 {
-    extern __shared__ zd sh_tr[];
-    const int nxh = nx / 2 + 1, lg = ilog2(nx);
-    const int z0 = blockIdx.x * RZ;
-    const int nrow = min(RZ, nz - z0);
-    const long long pl = blockIdx.y, p = pair0 + pl;
-    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
-    for (int t = threadIdx.x; t < nrow * 4 * nx; t += blockDim.x) {
-        int r = t / (4 * nx), rem = t - r * 4 * nx, j = rem / nx, k = rem - j * nx;
-        int z = z0 + r;
-        int ta = 2 * j, tb = 2 * j + 1;
-        const zd* wa = W + ((pl * NTERM + ta) * nz + z) * nxh;
-        zd A, B = mk(0.0, 0.0);
-        if (k < nxh) A = wa[k]; else A = conj(wa[nx - k]);
-        if (tb < NTERM) {
-            const zd* wb = W + ((pl * NTERM + tb) * nz + z) * nxh;
-            if (k < nxh) B = wb[k]; else B = conj(wb[nx - k]);
-        }
-        if (k == 0 || 2 * k == nx) { A.y = 0.0; B.y = 0.0; }
-        sh_tr[(r * 4 + j) * nx + bitrev(k, lg)] = mk(A.x - B.y, A.y + B.x);
-    }
-    fft_radix2_block(sh_tr, nx, 4 * nrow, lg, tw_x, +1);
-    // one-point parts (Eq. 7): they depend on (Y1, Y2) only
-    const double* pr = prof;
-    double q1 = pr[PR_Q * ny + i1], q2 = pr[PR_Q * ny + i2];
-    double uv1 = pr[PR_UV * ny + i1], uv2 = pr[PR_UV * ny + i2];
-    double pv1 = pr[PR_PV * ny + i1], pv2 = pr[PR_PV * ny + i2];
-    double qu1 = pr[PR_QU * ny + i1], qu2 = pr[PR_QU * ny + i2];
-    double qv1 = pr[PR_QV * ny + i1], qv2 = pr[PR_QV * ny + i2];
-    double qw1 = pr[PR_QW * ny + i1], qw2 = pr[PR_QW * ny + i2];
-    double e1 = pr[PR_EPS * ny + i1], e2 = pr[PR_EPS * ny + i2];
-    double dU = pr[PR_U * ny + i2] - pr[PR_U * ny + i1];
-    double Upm = 0.5 * (pr[PR_DU * ny + i1] + pr[PR_DU * ny + i2]);
-    double dUp = pr[PR_DU * ny + i2] - pr[PR_DU * ny + i1];
-    double one[NTERM];
+    const double q1 = pr[PR_Q * ny + i1], q2 = pr[PR_Q * ny + i2];
+    const double uv1 = pr[PR_UV * ny + i1], uv2 = pr[PR_UV * ny + i2];
+    const double pv1 = pr[PR_PV * ny + i1], pv2 = pr[PR_PV * ny + i2];
+    const double qu1 = pr[PR_QU * ny + i1], qu2 = pr[PR_QU * ny + i2];
+    const double qv1 = pr[PR_QV * ny + i1], qv2 = pr[PR_QV * ny + i2];
+    const double qw1 = pr[PR_QW * ny + i1], qw2 = pr[PR_QW * ny + i2];
+    const double e1 = pr[PR_EPS * ny + i1], e2 = pr[PR_EPS * ny + i2];
+    const double dU = pr[PR_U * ny + i2] - pr[PR_U * ny + i1];
+    const double Upm = 0.5 * (pr[PR_DU * ny + i1] + pr[PR_DU * ny + i2]);
+    const double dUp = pr[PR_DU * ny + i2] - pr[PR_DU * ny + i1];
     one[T_A] = q1 + q2;
     one[T_PHIX] = (qu2 - qu1) + dU * (q1 + q2);
     one[T_PHIY] = qv2 - qv1;
@@ -152,37 +79,133 @@ __global__ void k_terms_rowpass(const zd* __restrict__ W, const int* __restrict_
     one[T_PHI] = 0.5 * (qv1 + qv2) + 2.0 * (pv1 + pv2);
     one[T_XI] = -2.0 * Upm * (uv1 + uv2) - dUp * (uv2 - uv1) - 2.0 * (e1 + e2);
     one[T_RES] = -one[T_XI];
+}
+
+// ------------------------------ row pass: C2R along x + one-point parts
+// terms[t][p][z][x] = sum_kx W[pl][t][z][kx] e^{+i kx x} + onepoint_t(Y1, Y2),
+// stored as TO.  With spec != NULL the spectral parts of A, Phi_y and phi
+// (the terms the Step-3 stencils difference) also go to spec[3][p][z][x].
+// Terms are transformed two at a time (t0 + i t1).  CTA = RZ rows of one pair;
+// shared memory (1 + 8 RZ) nx complex.
+template <typename TF, typename TO>
+__global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
+                                long long npair, int ny, int nz, int nx, int RZ,
+                                const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x,
+                                TO* __restrict__ terms, float* __restrict__ spec)
+{
+    typedef cplx<TF> C;
+    extern __shared__ __align__(16) unsigned char sh_raw_tr[];
+    C* stw = (C*)sh_raw_tr;
+    C* b0 = stw + nx;
+    C* b1 = b0 + RZ * 4 * nx;
+    __shared__ TF s_one[NTERM];
+    const int nxh = nx / 2 + 1, lg = ilog2(nx);
+    const int z0 = blockIdx.x * RZ;
+    const int nrow = min(RZ, nz - z0);
+    const long long pl = blockIdx.y, p = pair0 + pl;
+    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+    load_twiddles(stw, tw_x, nx);
+    if (threadIdx.x == 0) {
+        double one[NTERM];
+        onepoint(prof, ny, i1, i2, one);
+        for (int t = 0; t < NTERM; ++t) s_one[t] = (TF)one[t];
+    }
+    for (int t = threadIdx.x; t < nrow * 4 * nx; t += blockDim.x) {
+        int r = t / (4 * nx), rem = t - r * 4 * nx, j = rem / nx, k = rem - j * nx;
+        int z = z0 + r;
+        int ta = 2 * j, tb = 2 * j + 1;
+        const C* wa = W + ((pl * NTERM + ta) * nz + z) * nxh;
+        C A, B = mk((TF)0, (TF)0);
+        if (k < nxh) A = wa[k]; else A = conj(wa[nx - k]);
+        if (tb < NTERM) {
+            const C* wb = W + ((pl * NTERM + tb) * nz + z) * nxh;
+            if (k < nxh) B = wb[k]; else B = conj(wb[nx - k]);
+        }
+        if (k == 0 || 2 * k == nx) { A.y = 0; B.y = 0; }
+        b0[(r * 4 + j) * nx + k] = mk(A.x - B.y, A.y + B.x);
+    }
+    const C* sh = fft_block<TF, true>(b0, b1, nx, 4 * nrow, lg, stw);
     const long long N = (long long)nz * nx;
     for (int t = threadIdx.x; t < nrow * NTERM * nx; t += blockDim.x) {
         int r = t / (NTERM * nx), rem = t - r * NTERM * nx, q = rem / nx, x = rem - q * nx;
-        zd v = sh_tr[(r * 4 + (q >> 1)) * nx + x];
-        double val = ((q & 1) ? v.y : v.x) + one[q];
-        terms[((long long)q * npair + p) * N + (long long)(z0 + r) * nx + x] = val;
+        C v = sh[(r * 4 + (q >> 1)) * nx + x];
+        const TF sp = (q & 1) ? v.y : v.x;
+        const long long e = (long long)(z0 + r) * nx + x;
+        terms[((long long)q * npair + p) * N + e] = (TO)(sp + s_one[q]);
+        if (spec != nullptr) {
+            const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
+            if (si >= 0) spec[((long long)si * npair + p) * N + e] = (float)sp;
+        }
     }
 }
 
-// ----------------------------------------------- Step 3 FD stencils
-// value of term t at the ordered pair (a, b) and separation index rr, taken
-// from the stored triangle a <= b, or by r-inversion (Sec. 3.3) with parity sg
-__device__ __forceinline__ double tri_value(const double* __restrict__ term, int a, int b, int ny, int nz, int nx,
-                                            int mz, int mx, double sg)
+template <typename TF, typename TB, typename TO>
+int terms_launch_t(const TermArgs& a)
 {
-    const long long N = (long long)nz * nx;
-    if (a <= b) return term[pair_index(a, b, ny) * N + (long long)mz * nx + mx];
-    int mzn = (nz - mz) % nz, mxn = (nx - mx) % nx;
-    return sg * term[pair_index(b, a, ny) * N + (long long)mzn * nx + mxn];
+    typedef cplx<TF> C;
+    const int nxh = a.nx / 2 + 1;
+    int launches = 0;
+    for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk) {
+        const long long np = a.pair_chunk < a.npair - p0 ? a.pair_chunk : a.npair - p0;
+        k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
+                                  (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
+            (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, (C*)a.W);
+        k_terms_rowpass<TF, TO><<<dim3((a.nz + a.rz - 1) / a.rz, (unsigned)np), 256, (1 + 8 * a.rz) * a.nx * sizeof(C),
+                                  a.st>>>((const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, a.nx, a.rz, a.prof,
+                                          (const C*)a.tw_x, (TO*)a.terms, a.spec);
+        launches += 2;
+    }
+    return launches;
 }
 
-// pass 1: Phi_y -= 2 nu dA/dr_y, phi -= (nu/2) dA/dY, dA/dr_y = (d_Y2 - d_Y1) A / 2,
-// dA/dY = (d_Y1 + d_Y2) A (Eq. 10-11).  A is even under r-inversion.
-// grid: (ceil(nz*nx / blockDim), npair)
+int terms_launch(const TermArgs& a)
+{
+    if (!a.fp32) return terms_launch_t<double, double, double>(a);
+    if (a.comb64) return terms_launch_t<float, double, float>(a);
+    return terms_launch_t<float, float, float>(a);
+}
+
+cudaError_t terms_set_attrs(int lim)
+{
+    const void* ks[] = {(const void*)k_terms_colpass<double, double>, (const void*)k_terms_rowpass<double, double>,
+                        (const void*)k_terms_colpass<float, float>, (const void*)k_terms_colpass<float, double>,
+                        (const void*)k_terms_rowpass<float, float>};
+    cudaError_t e = cudaSuccess;
+    for (const void* k : ks) {
+        cudaFuncAttributes fa;
+        cudaError_t r = cudaFuncGetAttributes(&fa, k);
+        if (r == cudaSuccess)
+            r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, lim - (int)fa.sharedSizeBytes);
+        if (r != cudaSuccess) e = r;
+    }
+    return e;
+}
+
+// ----------------------------------------------- Step 3 FD stencils
+// value of a field at the ordered pair (a, b) and separation index
+// (mz, mx), taken from the stored triangle a <= b, or by r-inversion
+// (Sec. 3.3) with parity sg
+template <typename T>
+__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, int nz, int nx, int mz, int mx,
+                                       T sg)
+{
+    const long long N = (long long)nz * nx;
+    if (a <= b) return f[pair_index(a, b, ny) * N + (long long)mz * nx + mx];
+    const int mzn = (nz - mz) % nz, mxn = (nx - mx) % nx;
+    return sg * f[pair_index(b, a, ny) * N + (long long)mzn * nx + mxn];
+}
+
+// plain path, pass 1: Phi_y -= 2 nu dA/dr_y, phi -= (nu/2) dA/dY, with
+// dA/dr_y = (d_Y2 - d_Y1) A / 2, dA/dY = (d_Y1 + d_Y2) A (Eq. 10-11); A even
+// under r-inversion.  grid (npair, separation chunks): consecutive CTAs take
+// the same separation chunk of consecutive pairs, so neighbour rows stay in L2.
 __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
                             int ny, int nz, int nx, double nu, const double* __restrict__ fdw,
                             const int* __restrict__ fdl0)
 {
     const long long N = (long long)nz * nx;
-    const long long p = blockIdx.y;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p = blockIdx.x;
+    const long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= N) return;
     const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
@@ -198,15 +221,15 @@ __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const i
     terms[((long long)T_PHI * npair + p) * N + e] += -0.5 * nu * (d1 + d2);
 }
 
-// pass 2: res += dPhi_y/dr_y + dphi/dY by the same stencil; Phi_y is odd and
-// phi even under r-inversion.
+// plain path, pass 2: res += dPhi_y/dr_y + dphi/dY by the same stencil;
+// Phi_y odd and phi even under r-inversion.
 __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
                               int ny, int nz, int nx, const double* __restrict__ fdw,
                               const int* __restrict__ fdl0)
 {
     const long long N = (long long)nz * nx;
-    const long long p = blockIdx.y;
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long p = blockIdx.x;
+    const long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= N) return;
     const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
@@ -223,6 +246,155 @@ __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const
         h2 += w2 * tri_value(Ph, i1, a2 + l, ny, nz, nx, mz, mx, 1.0);
     }
     terms[((long long)T_RES * npair + p) * N + e] += 0.5 * (y2 - y1) + (h1 + h2);
+}
+
+// ------------------------------------- split path: FP32 stencils
+// One-point part of A, a function of the ordered pair only
+__device__ __forceinline__ double op_A(const double* pr, int ny, int a, int b)
+{
+    return pr[PR_Q * ny + a] + pr[PR_Q * ny + b];
+}
+
+// final one-point parts of Phi_y and phi at the ordered pair (a, b), their FD
+// parts included (FP64)
+__device__ __forceinline__ void op_final(const double* pr, int ny, double nu, const double* fdw, const int* fdl0,
+                                         int a, int b, double& py, double& ph)
+{
+    const int la = fdl0[a], lb = fdl0[b];
+    double d1 = 0.0, d2 = 0.0;
+    for (int l = 0; l < 5; ++l) {
+        d1 += fdw[5 * a + l] * op_A(pr, ny, la + l, b);
+        d2 += fdw[5 * b + l] * op_A(pr, ny, a, lb + l);
+    }
+    const double qv_a = pr[PR_QV * ny + a], qv_b = pr[PR_QV * ny + b];
+    const double pv_a = pr[PR_PV * ny + a], pv_b = pr[PR_PV * ny + b];
+    py = (qv_b - qv_a) - nu * (d2 - d1);
+    ph = 0.5 * (qv_a + qv_b) + 2.0 * (pv_a + pv_b) - 0.5 * nu * (d1 + d2);
+}
+
+// Per-pair scalars of the split stencils, computed once in FP64:
+//   sc[p] = { w1[0..5), w2[0..5) (FP32 copies of the FD weights of rows i1, i2),
+//             -nu (d_Y2 - d_Y1) A1, -(nu/2) (d_Y1 + d_Y2) A1,
+//             (d_Y2 - d_Y1) Phi_y1 / 2 + (d_Y1 + d_Y2) phi1 }
+// with A1, Phi_y1, phi1 the one-point parts (FD parts included).
+constexpr int NSC = 13;
+__global__ void k_stencil_pairs(const int* __restrict__ pair_i, long long npair, int ny, double nu,
+                                const double* __restrict__ fdw, const int* __restrict__ fdl0,
+                                const double* __restrict__ prof, float* __restrict__ sc)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npair) return;
+    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+    const int a1 = fdl0[i1], a2 = fdl0[i2];
+    double d1 = 0.0, d2 = 0.0, y1 = 0.0, y2 = 0.0, h1 = 0.0, h2 = 0.0;
+    for (int l = 0; l < 5; ++l) {
+        const double w1 = fdw[5 * i1 + l], w2 = fdw[5 * i2 + l];
+        d1 += w1 * op_A(prof, ny, a1 + l, i2);
+        d2 += w2 * op_A(prof, ny, i1, a2 + l);
+        double py, ph;
+        op_final(prof, ny, nu, fdw, fdl0, a1 + l, i2, py, ph);
+        y1 += w1 * py;
+        h1 += w1 * ph;
+        op_final(prof, ny, nu, fdw, fdl0, i1, a2 + l, py, ph);
+        y2 += w2 * py;
+        h2 += w2 * ph;
+        sc[p * NSC + l] = (float)w1;
+        sc[p * NSC + 5 + l] = (float)w2;
+    }
+    sc[p * NSC + 10] = (float)(-nu * (d2 - d1));
+    sc[p * NSC + 11] = (float)(-0.5 * nu * (d1 + d2));
+    sc[p * NSC + 12] = (float)(0.5 * (y2 - y1) + (h1 + h2));
+}
+
+constexpr int SPT = 4;   // separations per thread in the split stencils
+
+// pass 1, FP32: with S = spectral part of A (spec[0]),
+//   Phi_y += -nu (d_Y2 - d_Y1)(S + A1),  phi += -(nu/2) (d_Y1 + d_Y2)(S + A1);
+// spec[1], spec[2] (spectral parts of Phi_y, phi) receive the FD parts of S.
+// grid (npair, separation chunks of 256 SPT).
+__global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spec, long long npair,
+                              const int* __restrict__ pair_i, int ny, int nz, int nx, double nu,
+                              const int* __restrict__ fdl0, const float* __restrict__ sc)
+{
+    const long long N = (long long)nz * nx;
+    const long long p = blockIdx.x;
+    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+    const int a1 = fdl0[i1], a2 = fdl0[i2];
+    float w1[5], w2[5];
+    #pragma unroll
+    for (int l = 0; l < 5; ++l) { w1[l] = sc[p * NSC + l]; w2[l] = sc[p * NSC + 5 + l]; }
+    const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
+    const float nuf = (float)nu;
+    #pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+        const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
+        if (e >= N) return;
+        const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
+        float d1 = 0.f, d2 = 0.f;
+        #pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            d1 += w1[l] * tri_value(spec, a1 + l, i2, ny, nz, nx, mz, mx, 1.f);
+            d2 += w2[l] * tri_value(spec, i1, a2 + l, ny, nz, nx, mz, mx, 1.f);
+        }
+        const float fy = -nuf * (d2 - d1), fp = -0.5f * nuf * (d1 + d2);
+        terms[((long long)T_PHIY * npair + p) * N + e] += fy + oy;
+        terms[((long long)T_PHI * npair + p) * N + e] += fp + oh;
+        spec[((long long)1 * npair + p) * N + e] += fy;
+        spec[((long long)2 * npair + p) * N + e] += fp;
+    }
+}
+
+// pass 2, FP32: res += (d_Y2 - d_Y1) Phi_y / 2 + (d_Y1 + d_Y2) phi, the
+// spectral parts (spec[1] odd, spec[2] even) in FP32 plus the per-pair
+// one-point scalar.
+__global__ void k_stencil_res32(float* __restrict__ terms, const float* __restrict__ spec, long long npair,
+                                const int* __restrict__ pair_i, int ny, int nz, int nx,
+                                const int* __restrict__ fdl0, const float* __restrict__ sc)
+{
+    const long long N = (long long)nz * nx;
+    const long long p = blockIdx.x;
+    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+    const int a1 = fdl0[i1], a2 = fdl0[i2];
+    float w1[5], w2[5];
+    #pragma unroll
+    for (int l = 0; l < 5; ++l) { w1[l] = sc[p * NSC + l]; w2[l] = sc[p * NSC + 5 + l]; }
+    const float o = sc[p * NSC + 12];
+    const float* Py = spec + (long long)1 * npair * N;
+    const float* Ph = spec + (long long)2 * npair * N;
+    #pragma unroll
+    for (int u = 0; u < SPT; ++u) {
+        const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
+        if (e >= N) return;
+        const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
+        float y1 = 0.f, y2 = 0.f, h1 = 0.f, h2 = 0.f;
+        #pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            y1 += w1[l] * tri_value(Py, a1 + l, i2, ny, nz, nx, mz, mx, -1.f);
+            y2 += w2[l] * tri_value(Py, i1, a2 + l, ny, nz, nx, mz, mx, -1.f);
+            h1 += w1[l] * tri_value(Ph, a1 + l, i2, ny, nz, nx, mz, mx, 1.f);
+            h2 += w2[l] * tri_value(Ph, i1, a2 + l, ny, nz, nx, mz, mx, 1.f);
+        }
+        terms[((long long)T_RES * npair + p) * N + e] += 0.5f * (y2 - y1) + (h1 + h2) + o;
+    }
+}
+
+int stencil_launch(bool fp32, void* terms, float* spec, long long npair, const int* pair_i, int ny, int nz, int nx,
+                   double nu, const double* fdw, const int* fdl0, const double* prof, cudaStream_t st)
+{
+    const long long N = (long long)nx * nz;
+    dim3 gs((unsigned)npair, (unsigned)((N + 255) / 256));
+    if (!fp32) {
+        k_stencil_A<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, nz, nx, nu, fdw, fdl0);
+        k_stencil_res<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, nz, nx, fdw, fdl0);
+    } else {
+        float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
+        k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
+        dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
+        k_stencil_A32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, nz, nx, nu, fdl0, sc);
+        k_stencil_res32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, nz, nx, fdl0, sc);
+        return 3;
+    }
+    return 2;
 }
 
 // ------------------------------------------- profiles from the raw sums

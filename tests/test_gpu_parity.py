@@ -39,15 +39,16 @@ def run_gpu(N, wl, coef, precision=0, calls=None, host=False):
     import torch
     y = S.cgl_grid(wl.ny)
     plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, coef.shape[0], precision)
+    tdt = torch.float64 if precision == N.GKE_PREC_F64 else torch.float32    # terms element type
     try:
         npair = N.gke_npair(plan)
         if host:
             f = torch.from_numpy(np.ascontiguousarray(coef))
-            terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=torch.float64)
+            terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=tdt)
             prof = torch.empty((N.GKE_NPROF, wl.ny), dtype=torch.float64)
         else:
             f = torch.from_numpy(np.ascontiguousarray(coef)).cuda()
-            terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=torch.float64, device="cuda")
+            terms = torch.empty((N.GKE_NTERM, npair, wl.nz, wl.nx), dtype=tdt, device="cuda")
             prof = torch.empty((N.GKE_NPROF, wl.ny), dtype=torch.float64, device="cuda")
         if calls is None:
             N.gke_compute(plan, f, coef.shape[0], terms, prof)
@@ -59,7 +60,7 @@ def run_gpu(N, wl, coef, precision=0, calls=None, host=False):
                 s0 += n
             N.gke_finalize_terms(plan, terms, prof)
         torch.cuda.synchronize()
-        return terms.cpu().numpy(), prof.cpu().numpy()
+        return terms.cpu().numpy().astype(np.float64), prof.cpu().numpy()
     finally:
         N.gke_destroy(plan)
 

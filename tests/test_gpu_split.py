@@ -5,7 +5,8 @@ TOL_SPLIT = 1e-6: each real operand keeps ~24 significant bits in its three
 BF16 slices, the six kept slice products drop terms of relative size 2^-24,
 and the tensor cores accumulate in FP32, so a contraction over K <= 4 x 32
 snapshot-field products carries ~1e-7 of the magnitude of its terms; the
-inverse transforms and the Step-3 stencils run in FP64 here.
+transforms, the terms and the spectral parts of the Step-3 stencils are FP32
+(the one-point parts are differenced in FP64), adding a few 1e-7.
 """
 import numpy as np
 import pytest
@@ -39,6 +40,18 @@ def test_split_matches_f64(N, shape):
     errs = [rel_err(got[t], ref[t]) for t in range(N.GKE_NTERM)]
     assert max(errs) <= TOL_SPLIT, dict(zip(N.TERMS, errs))
     assert max(errs) > 0.0          # the split path really ran (not the FP64 one)
+
+
+def test_split_multi_batch_promotes_to_fp64(N):
+    """A second batch promotes the per-pair sums to FP64; the result matches one batch."""
+    wl = S.small(16, 8, 33, 6, wid=77)
+    coef = S.coefficients(wl)
+    one, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_BF16X3)
+    three, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_BF16X3, calls=[2, 3, 1])
+    ref, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_F64)
+    for t in range(N.GKE_NTERM):
+        assert rel_err(three[t], ref[t]) <= TOL_SPLIT, N.TERMS[t]
+        assert rel_err(three[t], one[t]) <= TOL_SPLIT, N.TERMS[t]
 
 
 def test_split_tiny_vs_oracle(N):
