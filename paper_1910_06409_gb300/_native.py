@@ -26,7 +26,7 @@ GKE_NTERM, GKE_NPROF = len(TERMS), len(PROFILES)
 EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_snapshot", "gke_finalize_terms",
            "gke_compute", "gke_pair_labels", "gke_npair", "gke_terms_bytes", "gke_reset", "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
-           "gke_launch_count", "gke_last_error", "gke_destroy")
+           "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy")
 STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
 
 
@@ -73,6 +73,7 @@ def lib():
             "gke_set_timing": (i, [vp, i]),
             "gke_stage_times": (i, [vp, vp]),
             "gke_launch_count": (ctypes.c_longlong, [vp]),
+            "gke_compute_noalloc": (i, [ctypes.POINTER(gke_desc), vp, i, vp, vp, vp]),
             "gke_last_error": (cp, [vp]),
             "gke_destroy": (None, [vp]),
         }
@@ -176,6 +177,17 @@ def gke_fd_weights(y, j):
     if l0 < 0:
         raise GkeError(-1, "bad arguments")
     return l0, w
+
+
+def gke_compute_noalloc(nx, nz, ny, Lx, Lz, nu, y, fields, nsnap, terms, profiles=None, stream=None):
+    """FP64 pass without device allocation (device pointers only); raises GkeError."""
+    import numpy as np
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsnap,
+                    GKE_PREC_F64)
+    st = lib().gke_compute_noalloc(ctypes.byref(desc), ptr(fields), nsnap, ptr(terms), ptr(profiles), stream)
+    if st != GKE_OK:
+        raise GkeError(st, "gke_compute_noalloc")
 
 
 def gke_set_timing(plan, on: bool):
