@@ -72,8 +72,11 @@ RETAU1000 = Workload("retau1000_512x512x257_s32", 5, 512, 512, 257, 32, nu=1.0 /
 # a narrow case with the Re_tau~200 wall-normal grid and snapshot count, small
 # enough for multi-pass profiler captures (a few GB on the device)
 PROFILE = Workload("profile_32x32x129_s16", 6, 32, 32, 129, 16)
+# the Re_tau~200 plane size and snapshot count with few wall-normal points:
+# the transform, combine and stencil kernels see production shapes
+PROFILE_PLANE = Workload("profile_256x256x17_s16", 7, 256, 256, 17, 16)
 
-WORKLOADS = {w.name: w for w in (TINY, RETAU200, GROUP_A, GROUP_B, GROUP_C, RETAU1000, PROFILE)}
+WORKLOADS = {w.name: w for w in (TINY, RETAU200, GROUP_A, GROUP_B, GROUP_C, RETAU1000, PROFILE, PROFILE_PLANE)}
 
 
 def small(nx: int, nz: int, ny: int, nsnap: int, wid: int = 90, nu: float = 1.0 / 200.0,
