@@ -127,6 +127,121 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* sh_tw, const cplx<T>* __r
     for (int i = threadIdx.x; i < N; i += blockDim.x) sh_tw[i] = tw[i];
 }
 
+// ---------------------------------------------------------------- register FFT
+// W_32^j = e^{-2 pi i j / 32}, j < 16: values of the host libm cos / sin,
+// written out (each translation unit has its own copy)
+static __constant__ zd c_tw32d[16] = {
+    {1.0, -0.0},
+    {0.98078528040323043, -0.19509032201612825},
+    {0.92387953251128674, -0.38268343236508978},
+    {0.83146961230254524, -0.55557023301960218},
+    {0.70710678118654757, -0.70710678118654746},
+    {0.55557023301960229, -0.83146961230254524},
+    {0.38268343236508984, -0.92387953251128674},
+    {0.19509032201612833, -0.98078528040323043},
+    {6.123233995736766e-17, -1},
+    {-0.19509032201612819, -0.98078528040323043},
+    {-0.38268343236508973, -0.92387953251128674},
+    {-0.55557023301960196, -0.83146961230254546},
+    {-0.70710678118654746, -0.70710678118654757},
+    {-0.83146961230254535, -0.55557023301960218},
+    {-0.92387953251128674, -0.38268343236508989},
+    {-0.98078528040323043, -0.19509032201612861}};
+static __constant__ zf c_tw32f[16] = {
+    {1.0f, -0.0f},
+    {0.98078528f, -0.195090322f},
+    {0.923879533f, -0.382683432f},
+    {0.831469612f, -0.555570233f},
+    {0.707106781f, -0.707106781f},
+    {0.555570233f, -0.831469612f},
+    {0.382683432f, -0.923879533f},
+    {0.195090322f, -0.98078528f},
+    {6.123234e-17f, -1.0f},
+    {-0.195090322f, -0.98078528f},
+    {-0.382683432f, -0.923879533f},
+    {-0.555570233f, -0.831469612f},
+    {-0.707106781f, -0.707106781f},
+    {-0.831469612f, -0.555570233f},
+    {-0.923879533f, -0.382683432f},
+    {-0.98078528f, -0.195090322f}};
+template <typename T> __device__ __forceinline__ cplx<T> tw32(int j);
+template <> __device__ __forceinline__ zf tw32<float>(int j) { return c_tw32f[j]; }
+template <> __device__ __forceinline__ zd tw32<double>(int j) { return c_tw32d[j]; }
+
+template <int M> struct Lg2 { static constexpr int v = Lg2<M / 2>::v + 1; };
+template <> struct Lg2<1> { static constexpr int v = 0; };
+__host__ __device__ constexpr int brev_ct(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r = (r << 1) | ((x >> i) & 1);
+    return r;
+}
+
+// M-point DFT (M <= 32, power of two) of v[0..M) in registers, natural order in
+// and out: radix-2 decimation in time on the bit-reversed copy; INV conjugates
+// the twiddles (unnormalised inverse).
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void dft_reg(cplx<T>* v)
+{
+    cplx<T> a[M];
+    #pragma unroll
+    for (int i = 0; i < M; ++i) a[brev_ct(i, Lg2<M>::v)] = v[i];
+    #pragma unroll
+    for (int len = 2; len <= M; len <<= 1) {
+        #pragma unroll
+        for (int i = 0; i < M; i += len) {
+            #pragma unroll
+            for (int j = 0; j < len / 2; ++j) {
+                cplx<T> u = a[i + j], w = a[i + j + len / 2];
+                if (j != 0) {
+                    cplx<T> t = tw32<T>(j * (32 / len));
+                    if (INV) t.y = -t.y;
+                    w = w * t;
+                }
+                a[i + j] = u + w;
+                a[i + j + len / 2] = u - w;
+            }
+        }
+    }
+    #pragma unroll
+    for (int i = 0; i < M; ++i) v[i] = a[i];
+}
+
+// Two-level transform of one sequence of N = N1 N2 points held by N2 lanes:
+// on entry lane n2 holds v[m] = x[n2 + N2 m] (m < N1); on exit v[m] =
+// X[n2 + N2 m], X[k] = sum_n x[n] w^{n k} (w = e^{-2 pi i / N}, conjugate if
+// INV, unnormalised).  n = N2 n1 + n2, k = k1 + N1 k2:
+//   X[k1 + N1 k2] = sum_n2 W_N2^{n2 k2} [ w^{n2 k1} sum_n1 x[N2 n1 + n2] W_N1^{n1 k1} ].
+// The inner DFT runs in registers, its twiddled result goes through the
+// exchange buffer xs[k1 s1 + n2 s2] and the outer DFT (rows k1 = n2 + N2 j)
+// runs in registers again.  stw: the N-point twiddle table in shared memory.
+// Contains one __syncthreads(); every thread of the block must call it.
+template <typename T, int N1, int N2, bool INV>
+__device__ __forceinline__ void fft2l(cplx<T>* v, int lane, cplx<T>* xs, int s1, int s2, const cplx<T>* stw)
+{
+    static_assert(N1 % N2 == 0, "N1 must be a multiple of N2");
+    constexpr int R = N1 / N2;
+    dft_reg<T, N1, INV>(v);
+    #pragma unroll
+    for (int k1 = 1; k1 < N1; ++k1) {
+        cplx<T> w = stw[lane * k1];
+        if (INV) w.y = -w.y;
+        v[k1] = v[k1] * w;
+    }
+    #pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) xs[k1 * s1 + lane * s2] = v[k1];
+    __syncthreads();
+    #pragma unroll
+    for (int jj = 0; jj < R; ++jj) {
+        const int k1 = lane + N2 * jj;
+        cplx<T> b[N2];
+        #pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) b[n2] = xs[k1 * s1 + n2 * s2];
+        dft_reg<T, N2, INV>(b);
+        #pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) v[jj + R * k2] = b[k2];     // X[lane + N2 (jj + R k2)]
+    }
+}
+
 // signed wavenumber index of FFT bin m of an n-point transform, 0 at Nyquist
 __host__ __device__ __forceinline__ int signed_bin(int m, int n) {
     if (2 * m == n) return 0;

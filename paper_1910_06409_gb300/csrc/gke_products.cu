@@ -93,6 +93,80 @@ __global__ void k_col_inverse(const zd* __restrict__ fields_s, int ny, int nz, i
     }
 }
 
+// Register-FFT versions of the column passes for nz = N1 N2 (two-level
+// transform, fft2l): CTA = CW adjacent columns x N2 lanes; lane n2 of column c
+// loads rows n2 + N2 m straight from global memory (consecutive columns =
+// consecutive addresses), one shared-memory exchange, stores straight back.
+// Shared memory: N twiddles + N1 (N2 CW + 1) complex.
+template <typename TF, int N1, int N2>
+__global__ void __launch_bounds__(256)
+k_col_inverse_r(const zd* __restrict__ fields_s, int ny, int nxh, int CW, const double* __restrict__ mean,
+                const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ G)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2;
+    extern __shared__ __align__(16) unsigned char sh_raw_cir[];
+    C* stw = (C*)sh_raw_cir;
+    C* xs = stw + N;
+    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
+    const int kx = blockIdx.x * CW + c, y = blockIdx.y, f = blockIdx.z;
+    load_twiddles(stw, tw_z, N);
+    const zd* src = fields_s + ((long long)f * ny + y) * N * nxh;
+    C v[N1];
+    #pragma unroll
+    for (int m = 0; m < N1; ++m) {
+        const int kz = lane + N2 * m;
+        zd x = mk(0.0, 0.0);
+        if (kx < nxh) {
+            x = src[(long long)kz * nxh + kx];
+            if (kx == 0 && kz == 0) x.x -= mean[f * ny + y];
+        }
+        v[m] = cvt<TF>(x);
+    }
+    __syncthreads();
+    fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
+    if (kx < nxh) {
+        C* dst = G + ((long long)f * ny + y) * N * nxh;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) dst[(long long)(lane + N2 * m) * nxh + kx] = v[m];
+    }
+}
+
+// forward column pass: CTA = CW columns x YB planes x N2 lanes, so that the
+// operand stores (y contiguous) and the loads (kx contiguous) both come in
+// runs of 32 bytes or more
+template <typename TF, int N1, int N2>
+__global__ void __launch_bounds__(256)
+k_col_forward_r(const cplx<TF>* __restrict__ H, int ny, int nxh, int CW, int YB, int s, int ns,
+                const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ Xop)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2;
+    extern __shared__ __align__(16) unsigned char sh_raw_cfr[];
+    C* stw = (C*)sh_raw_cfr;
+    C* xs = stw + N;
+    const int nseq = CW * YB;
+    const int c = threadIdx.x % CW, yl = (threadIdx.x / CW) % YB, lane = threadIdx.x / nseq;
+    const int kx = blockIdx.x * CW + c, y = blockIdx.y * YB + yl, j = blockIdx.z;
+    const bool live = kx < nxh && y < ny;
+    const int Nk = N * nxh;
+    load_twiddles(stw, tw_z, N);
+    const C* src = H + ((long long)j * ny + y) * N * nxh;
+    C v[N1];
+    #pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = live ? src[(long long)(lane + N2 * m) * nxh + kx] : mk((TF)0, (TF)0);
+    __syncthreads();
+    fft2l<TF, N1, N2, false>(v, lane, xs + (yl * CW + c), N2 * nseq + 1, nseq, stw);
+    if (live) {
+        const TF inz = (TF)1 / (TF)N;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const long long k = (long long)(lane + N2 * m) * nxh + kx;
+            Xop[((((long long)(F_UU + j)) * Nk + k) * ns + s) * ny + y] = inz * v[m];
+        }
+    }
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -277,16 +351,29 @@ int products_launch(const ProdArgs& a)
     ++launches;
     for (int s = 0; s < ns; ++s) {
         const zd* fs = a.fields + (size_t)s * 4 * ny * Nk;
-        k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), st>>>(
-            fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, (C*)a.G);
+        if (nz == 256) {
+            constexpr int CWR = 16;
+            k_col_inverse_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, ny, 4), CWR * 16,
+                                          (256 + 16 * (16 * CWR + 1)) * sizeof(C), st>>>(
+                fs, ny, nxh, CWR, a.mean, (const C*)a.tw_z, (C*)a.G);
+        } else {
+            k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), st>>>(
+                fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, (C*)a.G);
+        }
         const int nrb = (nz + a.rz_rp - 1) / a.rz_rp;
         k_row_products<TF><<<dim3(nrb, ny), 256, (1 + 8 * a.rz_rp) * nx * sizeof(C), st>>>(
             (const C*)a.G, ny, nz, nx, a.rz_rp, (const C*)a.tw_x, (C*)a.H, a.part);
         k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(a.part, 6 * ny, nrb, a.stats);
-        k_col_forward<TF><<<dim3((nxh + a.cw_cf - 1) / a.cw_cf, (ny + a.yb_cf - 1) / a.yb_cf, 7), 256,
-                            (1 + 2 * a.cw_cf * a.yb_cf) * nz * sizeof(C), st>>>((const C*)a.H, ny, nz, nxh, a.cw_cf,
-                                                                                  a.yb_cf,
-                                                                        s, ns, (const C*)a.tw_z, Xop);
+        if (nz == 256) {
+            constexpr int CWR = 4, YBR = 4;
+            k_col_forward_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, (ny + YBR - 1) / YBR, 7), CWR * YBR * 16,
+                                          (256 + 16 * (16 * CWR * YBR + 1)) * sizeof(C), st>>>(
+                (const C*)a.H, ny, nxh, CWR, YBR, s, ns, (const C*)a.tw_z, Xop);
+        } else {
+            k_col_forward<TF><<<dim3((nxh + a.cw_cf - 1) / a.cw_cf, (ny + a.yb_cf - 1) / a.yb_cf, 7), 256,
+                                (1 + 2 * a.cw_cf * a.yb_cf) * nz * sizeof(C), st>>>(
+                (const C*)a.H, ny, nz, nxh, a.cw_cf, a.yb_cf, s, ns, (const C*)a.tw_z, Xop);
+        }
         launches += 4;
     }
     const int neb = (Nk + a.eps_kchunk - 1) / a.eps_kchunk;
@@ -310,7 +397,9 @@ cudaError_t products_set_attrs(int lim)
 {
     const void* ks[] = {(const void*)k_col_inverse<double>, (const void*)k_row_products<double>,
                         (const void*)k_col_forward<double>, (const void*)k_col_inverse<float>,
-                        (const void*)k_row_products<float>, (const void*)k_col_forward<float>};
+                        (const void*)k_row_products<float>, (const void*)k_col_forward<float>,
+                        (const void*)k_col_inverse_r<double, 16, 16>, (const void*)k_col_inverse_r<float, 16, 16>,
+                        (const void*)k_col_forward_r<double, 16, 16>, (const void*)k_col_forward_r<float, 16, 16>};
     cudaError_t e = cudaSuccess;
     for (const void* k : ks) { cudaError_t r = set_dyn_smem(k, lim); if (r != cudaSuccess) e = r; }
     return e;

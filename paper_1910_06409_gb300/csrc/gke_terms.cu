@@ -59,6 +59,44 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
     }
 }
 
+// register-FFT column pass for nz = N1 N2: CTA = CW columns of one term of
+// one pair x N2 lanes (see fft2l)
+template <typename TF, typename TB, int N1, int N2>
+__global__ void __launch_bounds__(256)
+k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, int CW, double inv_count,
+                  const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ W)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2;
+    extern __shared__ __align__(16) unsigned char sh_raw_tcr[];
+    C* stw = (C*)sh_raw_tcr;
+    C* xs = stw + N;
+    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
+    const int kx = blockIdx.x * CW + c, q = blockIdx.y;
+    const long long pl = blockIdx.z, p = pair0 + pl;
+    const int Nk = N * nxh;
+    const TF ic = (TF)inv_count;
+    load_twiddles(stw, tw_z, N);
+    const cplx<TB>* src = comb + (p * NTERM + q) * (long long)Nk;
+    C v[N1];
+    #pragma unroll
+    for (int m = 0; m < N1; ++m) {
+        C x = mk((TF)0, (TF)0);
+        if (kx < nxh) {
+            const cplx<TB> b = src[(long long)(lane + N2 * m) * nxh + kx];
+            x = mk(ic * (TF)b.x, ic * (TF)b.y);
+        }
+        v[m] = x;
+    }
+    __syncthreads();
+    fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
+    if (kx < nxh) {
+        C* dst = W + (pl * NTERM + q) * (long long)N * nxh;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) dst[(long long)(lane + N2 * m) * nxh + kx] = v[m];
+    }
+}
+
 // one-point parts of the seven terms at the pair (i1, i2), FP64
 __device__ __forceinline__ void onepoint(const double* __restrict__ pr, int ny, int i1, int i2, double one[NTERM])
 {
@@ -139,6 +177,69 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
     }
 }
 
+// register-FFT row pass for nx = N1 N2: CTA = RZ rows of one pair x N2 lanes;
+// the seven terms are transformed as four packed sequences (t0 + i t1, ...)
+template <typename TF, typename TO, int N1, int N2>
+__global__ void __launch_bounds__(256)
+k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
+                  int ny, int nz, int RZ, const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x,
+                  TO* __restrict__ terms, float* __restrict__ spec)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2, nxh = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char sh_raw_trr[];
+    C* stw = (C*)sh_raw_trr;
+    C* xs = stw + N;
+    __shared__ TF s_one[NTERM];
+    const int lane = threadIdx.x % N2, r = threadIdx.x / N2;
+    const int z = blockIdx.x * RZ + r;
+    const bool live = z < nz;
+    const long long pl = blockIdx.y, p = pair0 + pl;
+    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+    load_twiddles(stw, tw_x, N);
+    if (threadIdx.x == 0) {
+        double one[NTERM];
+        onepoint(prof, ny, i1, i2, one);
+        for (int t = 0; t < NTERM; ++t) s_one[t] = (TF)one[t];
+    }
+    const long long NN = (long long)nz * N;
+    C* xr = xs + r * N1 * (N2 + 1);
+    for (int jq = 0; jq < 4; ++jq) {
+        const int ta = 2 * jq, tb = 2 * jq + 1;
+        const C* wa = W + ((pl * NTERM + ta) * nz + (live ? z : 0)) * nxh;
+        const C* wb = W + ((pl * NTERM + (tb < NTERM ? tb : ta)) * nz + (live ? z : 0)) * nxh;
+        C v[N1];
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const int k = lane + N2 * m;
+            C A, B = mk((TF)0, (TF)0);
+            if (k < nxh) A = wa[k]; else A = conj(wa[N - k]);
+            if (tb < NTERM) { if (k < nxh) B = wb[k]; else B = conj(wb[N - k]); }
+            if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
+            v[m] = mk(A.x - B.y, A.y + B.x);
+        }
+        __syncthreads();                     // exchange buffer free (and s_one, twiddles ready)
+        fft2l<TF, N1, N2, true>(v, lane, xr, N2 + 1, 1, stw);
+        if (live) {
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const long long e = (long long)z * N + lane + N2 * m;
+                #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = 2 * jq + h;
+                    if (q >= NTERM) break;
+                    const TF sp = h ? v[m].y : v[m].x;
+                    terms[((long long)q * npair + p) * NN + e] = (TO)(sp + s_one[q]);
+                    if (spec != nullptr) {
+                        const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
+                        if (si >= 0) spec[((long long)si * npair + p) * NN + e] = (float)sp;
+                    }
+                }
+            }
+        }
+    }
+}
+
 template <typename TF, typename TB, typename TO>
 int terms_launch_t(const TermArgs& a)
 {
@@ -147,12 +248,28 @@ int terms_launch_t(const TermArgs& a)
     int launches = 0;
     for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk) {
         const long long np = a.pair_chunk < a.npair - p0 ? a.pair_chunk : a.npair - p0;
-        k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
-                                  (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
-            (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, (C*)a.W);
-        k_terms_rowpass<TF, TO><<<dim3((a.nz + a.rz - 1) / a.rz, (unsigned)np), 256, (1 + 8 * a.rz) * a.nx * sizeof(C),
-                                  a.st>>>((const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, a.nx, a.rz, a.prof,
-                                          (const C*)a.tw_x, (TO*)a.terms, a.spec);
+        if (a.nz == 256) {
+            constexpr int CWR = 16;
+            k_terms_colpass_r<TF, TB, 16, 16><<<dim3((nxh + CWR - 1) / CWR, NTERM, (unsigned)np), CWR * 16,
+                                                (256 + 16 * (16 * CWR + 1)) * sizeof(C), a.st>>>(
+                (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, (C*)a.W);
+        } else {
+            k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
+                                      (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
+                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, (C*)a.W);
+        }
+        if (a.nx == 256) {
+            constexpr int RZR = 16;
+            k_terms_rowpass_r<TF, TO, 16, 16><<<dim3((a.nz + RZR - 1) / RZR, (unsigned)np), RZR * 16,
+                                                (256 + RZR * 16 * 17) * sizeof(C), a.st>>>(
+                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, RZR, a.prof, (const C*)a.tw_x, (TO*)a.terms,
+                a.spec);
+        } else {
+            k_terms_rowpass<TF, TO><<<dim3((a.nz + a.rz - 1) / a.rz, (unsigned)np), 256,
+                                      (1 + 8 * a.rz) * a.nx * sizeof(C), a.st>>>(
+                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, a.nx, a.rz, a.prof, (const C*)a.tw_x,
+                (TO*)a.terms, a.spec);
+        }
         launches += 2;
     }
     return launches;
@@ -169,7 +286,12 @@ cudaError_t terms_set_attrs(int lim)
 {
     const void* ks[] = {(const void*)k_terms_colpass<double, double>, (const void*)k_terms_rowpass<double, double>,
                         (const void*)k_terms_colpass<float, float>, (const void*)k_terms_colpass<float, double>,
-                        (const void*)k_terms_rowpass<float, float>};
+                        (const void*)k_terms_rowpass<float, float>,
+                        (const void*)k_terms_colpass_r<double, double, 16, 16>,
+                        (const void*)k_terms_colpass_r<float, float, 16, 16>,
+                        (const void*)k_terms_colpass_r<float, double, 16, 16>,
+                        (const void*)k_terms_rowpass_r<double, double, 16, 16>,
+                        (const void*)k_terms_rowpass_r<float, float, 16, 16>};
     cudaError_t e = cudaSuccess;
     for (const void* k : ks) {
         cudaFuncAttributes fa;
