@@ -125,7 +125,7 @@ static void fornberg_d1(const double* x, int n, double z0, double* w)
     for (int i = 0; i < n; ++i) w[i] = c1[i];
 }
 
-static const int EPS_KCHUNK = 64;
+static const int EPS_KCHUNK = 16;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -261,7 +261,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOC(p->nonfinite, 1);
     {
         const Tiles tl = pick_tiles(d.nx, d.nz, p->csz);
-        size_t a1 = (size_t)6 * ny * ((d.nz + tl.rz_rp - 1) / tl.rz_rp);
+        size_t a1 = (size_t)6 * ny * std::max((d.nz + tl.rz_rp - 1) / tl.rz_rp, (d.nz + 3) / 4);
         size_t a2 = (size_t)ny * ((Nk + EPS_KCHUNK - 1) / EPS_KCHUNK);
         p->part_count = std::max(a1, a2);
         ALLOC(p->part, p->part_count);

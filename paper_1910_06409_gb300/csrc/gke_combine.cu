@@ -36,8 +36,9 @@ namespace gke {
 constexpr int PB = 8;     // pair block edge
 
 template <typename TI> struct CombCfg;
-template <> struct CombCfg<float> { static constexpr int KC = 8; };
-template <> struct CombCfg<double> { static constexpr int KC = 4; };
+// ~30 KB of staging per CTA: several CTAs per SM hide the gather latency
+template <> struct CombCfg<float> { static constexpr int KC = 4; };
+template <> struct CombCfg<double> { static constexpr int KC = 2; };
 
 template <typename TI> constexpr size_t combine_smem_bytes()
 {

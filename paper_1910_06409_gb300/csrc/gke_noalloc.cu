@@ -112,7 +112,8 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     int cw_cf = 4, yb_cf = 8;
     while (cw_cf * yb_cf > 1 && (size_t)(1 + 2 * cw_cf * yb_cf) * nz * 16 > 65536) { if (cw_cf > 1) cw_cf /= 2; else yb_cf /= 2; }
     const int eps_kchunk = 64;
-    const int nrb = (nz + rz_rp - 1) / rz_rp, neb = (Nk + eps_kchunk - 1) / eps_kchunk;
+    const int nrb = (nz + rz_rp - 1) / rz_rp > (nz + 3) / 4 ? (nz + rz_rp - 1) / rz_rp : (nz + 3) / 4;
+    const int neb = (Nk + eps_kchunk - 1) / eps_kchunk;
 
     Carve c{g_scratch_dev[dev], 0, (size_t)GKE_NOALLOC_SCRATCH_BYTES};
     zd* Xop = c.take<zd>((size_t)NFIELD * Nk * ns * ny);

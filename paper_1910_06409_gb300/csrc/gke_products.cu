@@ -252,6 +252,98 @@ __global__ void k_row_products(const cplx<TF>* __restrict__ G, int ny, int nz, i
     }
 }
 
+// Register-FFT row pass for nx = N1 N2 (fft2l): CTA = RZ rows x N2 lanes.
+// Per row: two inverse transforms (u + i v, w + i p), the seven products in
+// registers, four forward transforms, Hermitian split through shared memory.
+// Row sums: FP32 over a thread's N1 points, FP64 across threads.
+template <typename TF, int N1, int N2, int RZ>
+__global__ void __launch_bounds__(RZ * N2)
+k_row_products_r(const cplx<TF>* __restrict__ G, int ny, int nz, const cplx<TF>* __restrict__ tw_x,
+                 cplx<TF>* __restrict__ H, double* __restrict__ part)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2, nxh = N / 2 + 1;
+    extern __shared__ __align__(16) unsigned char sh_raw_rpr[];
+    C* stw = (C*)sh_raw_rpr;
+    C* xs = stw + N;                        // [RZ][N1][N2 + 1] exchange
+    C* zb = xs + RZ * N1 * (N2 + 1);        // [RZ][4][N] forward spectra
+    const int lane = threadIdx.x % N2, r = threadIdx.x / N2;
+    const int z = blockIdx.x * RZ + r, y = blockIdx.y;
+    const bool live = z < nz;
+    const int zz = live ? z : 0;
+    C* xr = xs + r * N1 * (N2 + 1);
+    load_twiddles(stw, tw_x, N);
+    C v0[N1], v1[N1];
+    #pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const C* ga = G + (((long long)(2 * q) * ny + y) * nz + zz) * nxh;
+        const C* gb = G + (((long long)(2 * q + 1) * ny + y) * nz + zz) * nxh;
+        C* v = q ? v1 : v0;
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const int k = lane + N2 * m;
+            C A, B;
+            if (k < nxh) { A = ga[k]; B = gb[k]; } else { A = conj(ga[N - k]); B = conj(gb[N - k]); }
+            if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
+            v[m] = mk(A.x - B.y, A.y + B.x);     // A + i B
+        }
+        __syncthreads();
+        fft2l<TF, N1, N2, true>(v, lane, xr, N2 + 1, 1, stw);
+    }
+    // v0[m] = u + i v, v1[m] = w + i p at x = lane + N2 m
+    TF s6[6] = {0, 0, 0, 0, 0, 0};
+    #pragma unroll
+    for (int m = 0; m < N1; ++m) {
+        const TF u = v0[m].x, vv = v0[m].y, w = v1[m].x, pp = v1[m].y;
+        const TF q = u * u + vv * vv + w * w;
+        s6[0] += q; s6[1] += u * vv; s6[2] += pp * vv; s6[3] += q * u; s6[4] += q * vv; s6[5] += q * w;
+    }
+    #pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        C f[N1];
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const TF u = v0[m].x, vv = v0[m].y, w = v1[m].x;
+            if (j == 0) f[m] = mk(u * u, vv * vv);
+            else if (j == 1) f[m] = mk(w * w, u * vv);
+            else if (j == 2) f[m] = mk(u * w, vv * w);
+            else f[m] = mk(u * u + vv * vv + w * w, (TF)0);
+        }
+        __syncthreads();
+        fft2l<TF, N1, N2, false>(f, lane, xr, N2 + 1, 1, stw);
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) zb[(r * 4 + j) * N + lane + N2 * m] = f[m];
+    }
+    __syncthreads();
+    const TF h = (TF)0.5 / (TF)N;
+    if (live) {
+        for (int it = lane; it < 4 * nxh; it += N2) {
+            const int j = it / nxh, k = it - j * nxh;
+            const C* seq = zb + (r * 4 + j) * N;
+            const C Z = seq[k], Zc = conj(seq[(N - k) & (N - 1)]);
+            const C A = h * (Z + Zc);
+            const C D = Z - Zc;
+            const C B = mk(h * D.y, -h * D.x);     // -i/2 (Z - Zc)
+            H[(((long long)(2 * j) * ny + y) * nz + z) * nxh + k] = A;
+            if (j < 3) H[(((long long)(2 * j + 1) * ny + y) * nz + z) * nxh + k] = B;
+        }
+    }
+    // block reduction of the row sums (FP64 across threads)
+    __shared__ double red[6][32];
+    const int wl = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = 0; i < 6; ++i) {
+        double v = live ? (double)s6[i] : 0.0;
+        v = warp_sum(v);
+        if (wl == 0) red[i][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        double acc = 0.0;
+        for (int w = 0; w < nw; ++w) acc += red[threadIdx.x][w];
+        part[((long long)threadIdx.x * ny + y) * gridDim.x + blockIdx.x] = acc;
+    }
+}
+
 // ---------------------------------- forward transform along z (columns)
 // One snapshot: Xop[4 + j][k][s][y] = (1/nz) sum_z H[j][y][z][kx] e^{-i kz z}
 // for the seven products.  CTA = CW kx columns x YB planes of one product;
@@ -294,7 +386,9 @@ __global__ void k_col_forward(const cplx<TF>* __restrict__ H, int ny, int nz, in
 //   part[y][chunk] = sum_{s, k in chunk, i} w_k [ (kx^2 + kz^2) |u_i(y,k)|^2 + |d_y u_i(y,k)|^2 ],
 // d_y by the 5-point FD stencil applied to the coefficients (it commutes with
 // the transform); w_k = 1 on the kx = 0 and kx = nx/2 lines, 2 elsewhere (half
-// spectrum).  One thread per y, FP64 sums; partials reduced in a fixed order.
+// spectrum).  One thread per y; arithmetic in TF, the running sum compensated
+// (Kahan) so an FP32 pass keeps ~1e-7 relative accuracy; partials reduced in
+// FP64 in a fixed order by k_reduce_partials.
 template <typename TF>
 __global__ void k_eps(const cplx<TF>* __restrict__ Xop, int ns, int ny, int nz, int nxh, int nx,
                       double Lx, double Lz, const double* __restrict__ fdw, const int* __restrict__ fdl0,
@@ -302,27 +396,34 @@ __global__ void k_eps(const cplx<TF>* __restrict__ Xop, int ns, int ny, int nz, 
 {
     const int Nk = nz * nxh;
     const int kbeg = blockIdx.x * kchunk, kend = min(Nk, kbeg + kchunk);
+    const TF cx = (TF)(2.0 * 3.14159265358979323846 / Lx), cz = (TF)(2.0 * 3.14159265358979323846 / Lz);
     for (int y = threadIdx.x; y < ny; y += blockDim.x) {
         const int l0 = fdl0[y];
-        double w5[5];
-        for (int l = 0; l < 5; ++l) w5[l] = fdw[5 * y + l];
-        double acc = 0.0;
+        TF w5[5];
+        for (int l = 0; l < 5; ++l) w5[l] = (TF)fdw[5 * y + l];
+        TF sum = 0, comp = 0;
         for (int k = kbeg; k < kend; ++k) {
-            int kz_i = k / nxh, kx_i = k - kz_i * nxh;
-            double kx = 2.0 * 3.14159265358979323846 * signed_bin(kx_i, nx) / Lx;
-            double kz = 2.0 * 3.14159265358979323846 * signed_bin(kz_i, nz) / Lz;
-            double wk = (kx_i == 0 || 2 * kx_i == nx) ? 1.0 : 2.0;
-            double k2 = kx * kx + kz * kz;
+            const int kz_i = k / nxh, kx_i = k - kz_i * nxh;
+            const TF kx = cx * (TF)signed_bin(kx_i, nx), kz = cz * (TF)signed_bin(kz_i, nz);
+            const TF wk = (kx_i == 0 || 2 * kx_i == nx) ? (TF)1 : (TF)2;
+            const TF k2 = kx * kx + kz * kz;
+            TF acc = 0;
             for (int i = 0; i < 3; ++i)
                 for (int s = 0; s < ns; ++s) {
                     const cplx<TF>* col = Xop + (((long long)i * Nk + k) * ns + s) * ny;
-                    cplx<TF> a = col[y];
-                    double dr = 0.0, di = 0.0;
-                    for (int l = 0; l < 5; ++l) { dr += w5[l] * (double)col[l0 + l].x; di += w5[l] * (double)col[l0 + l].y; }
-                    acc += wk * (k2 * ((double)a.x * a.x + (double)a.y * a.y) + dr * dr + di * di);
+                    const cplx<TF> a = col[y];
+                    TF dr = 0, di = 0;
+                    #pragma unroll
+                    for (int l = 0; l < 5; ++l) { const cplx<TF> b = col[l0 + l]; dr += w5[l] * b.x; di += w5[l] * b.y; }
+                    acc += k2 * (a.x * a.x + a.y * a.y) + dr * dr + di * di;
                 }
+            // compensated add of this wavenumber's contribution
+            const TF yk = wk * acc - comp;
+            const TF t = sum + yk;
+            comp = (t - sum) - yk;
+            sum = t;
         }
-        part[(long long)y * gridDim.x + blockIdx.x] = acc;
+        part[(long long)y * gridDim.x + blockIdx.x] = (double)sum;
     }
 }
 
@@ -360,9 +461,14 @@ int products_launch(const ProdArgs& a)
             k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), st>>>(
                 fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, (C*)a.G);
         }
-        const int nrb = (nz + a.rz_rp - 1) / a.rz_rp;
-        k_row_products<TF><<<dim3(nrb, ny), 256, (1 + 8 * a.rz_rp) * nx * sizeof(C), st>>>(
-            (const C*)a.G, ny, nz, nx, a.rz_rp, (const C*)a.tw_x, (C*)a.H, a.part);
+        const int nrb = (nx == 256) ? (nz + 3) / 4 : (nz + a.rz_rp - 1) / a.rz_rp;
+        if (nx == 256) {
+            k_row_products_r<TF, 16, 16, 4><<<dim3(nrb, ny), 4 * 16, (256 + 4 * 16 * 17 + 4 * 4 * 256) * sizeof(C),
+                                              st>>>((const C*)a.G, ny, nz, (const C*)a.tw_x, (C*)a.H, a.part);
+        } else {
+            k_row_products<TF><<<dim3(nrb, ny), 256, (1 + 8 * a.rz_rp) * nx * sizeof(C), st>>>(
+                (const C*)a.G, ny, nz, nx, a.rz_rp, (const C*)a.tw_x, (C*)a.H, a.part);
+        }
         k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(a.part, 6 * ny, nrb, a.stats);
         if (nz == 256) {
             constexpr int CWR = 4, YBR = 4;
@@ -399,7 +505,8 @@ cudaError_t products_set_attrs(int lim)
                         (const void*)k_col_forward<double>, (const void*)k_col_inverse<float>,
                         (const void*)k_row_products<float>, (const void*)k_col_forward<float>,
                         (const void*)k_col_inverse_r<double, 16, 16>, (const void*)k_col_inverse_r<float, 16, 16>,
-                        (const void*)k_col_forward_r<double, 16, 16>, (const void*)k_col_forward_r<float, 16, 16>};
+                        (const void*)k_col_forward_r<double, 16, 16>, (const void*)k_col_forward_r<float, 16, 16>,
+                        (const void*)k_row_products_r<double, 16, 16, 4>, (const void*)k_row_products_r<float, 16, 16, 4>};
     cudaError_t e = cudaSuccess;
     for (const void* k : ks) { cudaError_t r = set_dyn_smem(k, lim); if (r != cudaSuccess) e = r; }
     return e;
