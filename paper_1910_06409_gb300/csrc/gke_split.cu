@@ -143,7 +143,11 @@ __device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
 }
 
 // Aop[k][f][g][mt][slice * 2 + part][A_BLK]; products (uu .. vw) carry the
-// factor 2 of the expansion; rows >= cov and snapshots >= ns are zero.
+// factor 2 of the expansion; rows >= cov and snapshots >= ns are zero.  Thread
+// = one row x 8 snapshots: the 8 values of a core-matrix row are contiguous,
+// so each slice goes out as one 16-byte store.
+struct alignas(16) bf16x8 { bf16 v[8]; };
+
 __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
                                bf16* __restrict__ Aop)
 {
@@ -154,18 +158,20 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
     const int k = (int)(b / NFIELD);
     const float sc = (f >= F_UU && f <= F_VW) ? 2.f : 1.f;
     bf16* dst = Aop + ((((long long)k * NFIELD + f) * G + g) * MT + mt) * (long long)A_STAGE;
-    for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
-        const int s_l = e / TM, r = e - s_l * TM;
-        const int y = mt * TM + r, s = g * KS + s_l;
+    const int r = threadIdx.x % TM, kc = threadIdx.x / TM;          // blockDim = 2 TM
+    const int y = mt * TM + r;
+    bf16x8 o[6];
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
         if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k) * ns + s) * ny + y];
-        bf16 a0, a1, a2, b0, b1, b2;
-        split3(sc * v.x, a0, a1, a2);
-        split3(sc * v.y, b0, b1, b2);
-        const int idx = cm_index(r, s_l, TM);
-        dst[0 * A_BLK + idx] = a0; dst[2 * A_BLK + idx] = a1; dst[4 * A_BLK + idx] = a2;
-        dst[1 * A_BLK + idx] = b0; dst[3 * A_BLK + idx] = b1; dst[5 * A_BLK + idx] = b2;
+        split3(sc * v.x, o[0].v[e], o[2].v[e], o[4].v[e]);      // slices of the real part
+        split3(sc * v.y, o[1].v[e], o[3].v[e], o[5].v[e]);      // slices of the imaginary part
     }
+    const int idx = cm_index(r, kc * 8, TM);
+    #pragma unroll
+    for (int q = 0; q < 6; ++q) *(bf16x8*)(dst + q * A_BLK + idx) = o[q];
 }
 
 // Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi | -br
@@ -178,21 +184,25 @@ __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int N
     const int fb = (int)(b % 3);
     const int k = (int)(b / 3);
     bf16* dst = Bop + ((((long long)k * 3 + fb) * G + g) * MT + nt) * (long long)B_STAGE;
-    for (int e = threadIdx.x; e < TM * KS; e += blockDim.x) {
-        const int s_l = e / TM, r = e - s_l * TM;
-        const int y = nt * TM + r, s = g * KS + s_l;
+    const int r = threadIdx.x % TM, kc = threadIdx.x / TM;          // blockDim = 2 TM
+    const int y = nt * TM + r;
+    bf16x8 br[3], bi[3], bn[3];
+    #pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
         if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k) * ns + s) * ny + y];
-        bf16 r0, r1, r2, i0, i1, i2;
-        split3(v.x, r0, r1, r2);
-        split3(v.y, i0, i1, i2);
-        const bf16 sr[3] = {r0, r1, r2}, si[3] = {i0, i1, i2};
-        for (int sl = 0; sl < 3; ++sl) {
-            bf16* d = dst + sl * B_BLK;
-            d[cm_index(r, s_l, 3 * TM)] = sr[sl];
-            d[cm_index(TM + r, s_l, 3 * TM)] = si[sl];
-            d[cm_index(2 * TM + r, s_l, 3 * TM)] = __hneg(sr[sl]);
-        }
+        split3(v.x, br[0].v[e], br[1].v[e], br[2].v[e]);
+        split3(v.y, bi[0].v[e], bi[1].v[e], bi[2].v[e]);
+        #pragma unroll
+        for (int sl = 0; sl < 3; ++sl) bn[sl].v[e] = __hneg(br[sl].v[e]);
+    }
+    #pragma unroll
+    for (int sl = 0; sl < 3; ++sl) {
+        bf16* d = dst + sl * B_BLK;
+        *(bf16x8*)(d + cm_index(r, kc * 8, 3 * TM)) = br[sl];
+        *(bf16x8*)(d + cm_index(TM + r, kc * 8, 3 * TM)) = bi[sl];
+        *(bf16x8*)(d + cm_index(2 * TM + r, kc * 8, 3 * TM)) = bn[sl];
     }
 }
 
@@ -336,11 +346,12 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
 // grid), FP32 products and sums on the CUDA cores, same coefficients.
 __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, int cov, zf* __restrict__ raw)
 {
-    const int k = blockIdx.x, job = blockIdx.y;
-    const TcJob jd = c_tcjobs[job];
+    const int k = blockIdx.x;
     const int ne = ny - cov;
     const int n_row = ne * ny, n_col = cov * ne;
-    for (int e = threadIdx.x; e < n_row + n_col; e += blockDim.x) {
+    for (int e2 = threadIdx.x; e2 < NJOB * (n_row + n_col); e2 += blockDim.x) {
+        const int job = e2 / (n_row + n_col), e = e2 - job * (n_row + n_col);
+        const TcJob jd = c_tcjobs[job];
         int y, yp;
         if (e < n_row) { y = cov + e / ny; yp = e % ny; }
         else { int r = e - n_row; y = r / ne; yp = cov + r % ne; }
@@ -407,13 +418,13 @@ gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, 
     bf16* Aop = (bf16*)w.ops;
     bf16* Bop = (bf16*)((char*)w.ops + (size_t)Nk * NFIELD * G * MT * A_STAGE * sizeof(bf16));
     *launches = 0;
-    k_split_prep_A<<<(unsigned)((long long)Nk * NFIELD * G * MT), 256, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Aop);
-    k_split_prep_B<<<(unsigned)((long long)Nk * 3 * G * MT), 256, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Bop);
+    k_split_prep_A<<<(unsigned)((long long)Nk * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Aop);
+    k_split_prep_B<<<(unsigned)((long long)Nk * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Bop);
     const long long njt = (long long)NJSQ * MT * MT + MT * (MT + 1) / 2;
     k_corr_tc<<<(unsigned)(Nk * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Nk, G, MT, ny, cov, raw, w.err);
     *launches = 3;
     if (cov < ny) {
-        k_corr_edge<<<dim3(Nk, NJSQ + 1), 128, 0, st>>>(Xop, ns, ny, Nk, cov, raw);
+        k_corr_edge<<<Nk, 256, 0, st>>>(Xop, ns, ny, Nk, cov, raw);
         *launches += 1;
     }
     cudaError_t e = cudaGetLastError();

@@ -430,6 +430,25 @@ __global__ void k_stencil_pairs(const int* __restrict__ pair_i, long long npair,
 
 constexpr int SPT = 4;   // separations per thread in the split stencils
 
+// the stencil's 10 neighbours of pair (i1, i2): rows (a1 + l, i2) and columns
+// (i1, a2 + l); a neighbour below the diagonal is read from its r-inverted
+// partner (mirrored separation, parity sg).  Resolved once per CTA so the
+// per-separation gathers are branch-free.
+struct Nb { const float* base[10]; float sg[10]; int mir[10]; };
+
+__device__ __forceinline__ void make_nb(Nb& nb, const float* f, float parity, int i1, int i2, int a1, int a2, int ny,
+                                        long long N)
+{
+    #pragma unroll
+    for (int l = 0; l < 10; ++l) {
+        const int a = l < 5 ? a1 + l : i1, b = l < 5 ? i2 : a2 + (l - 5);
+        const bool m = a > b;
+        nb.base[l] = f + pair_index(m ? b : a, m ? a : b, ny) * N;
+        nb.sg[l] = m ? parity : 1.f;
+        nb.mir[l] = m;
+    }
+}
+
 // pass 1, FP32: with S = spectral part of A (spec[0]),
 //   Phi_y += -nu (d_Y2 - d_Y1)(S + A1),  phi += -(nu/2) (d_Y1 + d_Y2)(S + A1);
 // spec[1], spec[2] (spectral parts of Phi_y, phi) receive the FD parts of S.
@@ -441,22 +460,24 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
     const long long N = (long long)nz * nx;
     const long long p = blockIdx.x;
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
-    const int a1 = fdl0[i1], a2 = fdl0[i2];
-    float w1[5], w2[5];
+    float w[10];
     #pragma unroll
-    for (int l = 0; l < 5; ++l) { w1[l] = sc[p * NSC + l]; w2[l] = sc[p * NSC + 5 + l]; }
+    for (int l = 0; l < 10; ++l) w[l] = sc[p * NSC + l];
     const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
     const float nuf = (float)nu;
+    Nb nb;
+    make_nb(nb, spec, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
     #pragma unroll
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
         if (e >= N) return;
         const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
+        const long long en = (long long)((nz - mz) % nz) * nx + (nx - mx) % nx;
         float d1 = 0.f, d2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
-            d1 += w1[l] * tri_value(spec, a1 + l, i2, ny, nz, nx, mz, mx, 1.f);
-            d2 += w2[l] * tri_value(spec, i1, a2 + l, ny, nz, nx, mz, mx, 1.f);
+            d1 += w[l] * nb.sg[l] * nb.base[l][nb.mir[l] ? en : e];
+            d2 += w[5 + l] * nb.sg[5 + l] * nb.base[5 + l][nb.mir[5 + l] ? en : e];
         }
         const float fy = -nuf * (d2 - d1), fp = -0.5f * nuf * (d1 + d2);
         terms[((long long)T_PHIY * npair + p) * N + e] += fy + oy;
@@ -476,25 +497,26 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
     const long long N = (long long)nz * nx;
     const long long p = blockIdx.x;
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
-    const int a1 = fdl0[i1], a2 = fdl0[i2];
-    float w1[5], w2[5];
+    float w[10];
     #pragma unroll
-    for (int l = 0; l < 5; ++l) { w1[l] = sc[p * NSC + l]; w2[l] = sc[p * NSC + 5 + l]; }
+    for (int l = 0; l < 10; ++l) w[l] = sc[p * NSC + l];
     const float o = sc[p * NSC + 12];
-    const float* Py = spec + (long long)1 * npair * N;
-    const float* Ph = spec + (long long)2 * npair * N;
+    Nb ny_, nh_;
+    make_nb(ny_, spec + (long long)1 * npair * N, -1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
+    make_nb(nh_, spec + (long long)2 * npair * N, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
     #pragma unroll
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
         if (e >= N) return;
         const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
+        const long long en = (long long)((nz - mz) % nz) * nx + (nx - mx) % nx;
         float y1 = 0.f, y2 = 0.f, h1 = 0.f, h2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
-            y1 += w1[l] * tri_value(Py, a1 + l, i2, ny, nz, nx, mz, mx, -1.f);
-            y2 += w2[l] * tri_value(Py, i1, a2 + l, ny, nz, nx, mz, mx, -1.f);
-            h1 += w1[l] * tri_value(Ph, a1 + l, i2, ny, nz, nx, mz, mx, 1.f);
-            h2 += w2[l] * tri_value(Ph, i1, a2 + l, ny, nz, nx, mz, mx, 1.f);
+            y1 += w[l] * ny_.sg[l] * ny_.base[l][ny_.mir[l] ? en : e];
+            y2 += w[5 + l] * ny_.sg[5 + l] * ny_.base[5 + l][ny_.mir[5 + l] ? en : e];
+            h1 += w[l] * nh_.sg[l] * nh_.base[l][nh_.mir[l] ? en : e];
+            h2 += w[5 + l] * nh_.sg[5 + l] * nh_.base[5 + l][nh_.mir[5 + l] ? en : e];
         }
         terms[((long long)T_RES * npair + p) * N + e] += 0.5f * (y2 - y1) + (h1 + h2) + o;
     }
