@@ -232,7 +232,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOCB(p->Xop, (size_t)NFIELD * Nk * ns * ny * p->csz);
     ALLOCB(p->G, (size_t)4 * ny * plane * p->csz);
     ALLOCB(p->H, (size_t)7 * ny * plane * p->csz);
-    ALLOCB(p->raw, (size_t)NJOB * Nk * ny * ny * p->csz);
+    ALLOCB(p->raw, (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * Nk * p->csz);
     if (f32) {
         ALLOC(p->comb32, (size_t)p->npair * NTERM * Nk);
         // spectral parts of A, Phi_y, phi, then 13 per-pair stencil scalars

@@ -24,10 +24,10 @@
 // FP64 by k_promote).
 //
 // CTA = an 8 x 8 block of pairs (i1 in [8a, 8a+8), i2 in [8b, 8b+8), b >= a)
-// and KC consecutive wavenumbers.  All contractions of the block and of its
-// transposed partner block are staged through shared memory (rows of 8
-// consecutive y' values); then each thread forms the terms of its (pair, k)
-// items; stores are k-contiguous.
+// and KC consecutive wavenumbers.  In the raw layout the block (a, b) of a
+// contraction over KC wavenumbers is KC x 64 contiguous values, and so is the
+// transposed partner block (b, a); both are staged through shared memory, then
+// each thread forms the terms of its (pair, k) items; stores are k-contiguous.
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -75,10 +75,9 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         const int q = rem / (PB * PB), rr = (rem / PB) % PB, cc = rem % PB;
         const int j = slot >> 1, partner = slot & 1;
         const int kq = k0 + q;
-        const int y = partner ? PB * b + rr : PB * a + rr;
-        const int yp = partner ? PB * a + cc : PB * b + cc;
+        const int yb = partner ? b : a, ypb = partner ? a : b;
         C v = mk((TI)0, (TI)0);
-        if (kq < Nk && y < ny && yp < ny) v = raw[(((long long)j * Nk + kq) * ny + y) * ny + yp];
+        if (kq < Nk) v = raw[((((long long)j * nblk + yb) * nblk + ypb) * Nk + kq) * 64 + rr * PB + cc];
         at(slot, q, rr, cc) = v;
     }
     __syncthreads();

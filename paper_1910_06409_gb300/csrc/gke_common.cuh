@@ -7,8 +7,10 @@
 //            of ns x ny values per (field, wavenumber); Nk = nz * nxh,
 //            k = kz_index * nxh + kx_index; TF = double (plain path) or
 //            float (split path)
-//   raw      complex [NJOB][Nk][ny][ny]        one batch's contractions, ordered
-//            pairs (y, y'), k-major (D: only y <= y' written)
+//   raw      complex [NJOB][YB][YB][Nk][8][8]  one batch's contractions on ordered
+//            pairs (y, y') in 8 x 8 blocks, YB = ceil(ny / 8): block (y/8, y'/8),
+//            then the wavenumber, then (y % 8, y' % 8) (raw_index; D: only
+//            y <= y' is meaningful)
 //   comb     complex128 [npair][NTERM][Nk]     per-pair term spectra summed over
 //            batches (the FP64 snapshot-sum accumulator)
 //   terms    double  [NTERM][npair][nz][nx]    GKE terms in separation space,
@@ -246,6 +248,10 @@ __device__ __forceinline__ void fft2l(cplx<T>* v, int lane, cplx<T>* xs, int s1,
 __host__ __device__ __forceinline__ int signed_bin(int m, int n) {
     if (2 * m == n) return 0;
     return (m < n / 2 + (n & 1)) ? m : m - n;
+}
+
+__host__ __device__ __forceinline__ long long raw_index(int job, long long k, int y, int yp, int Nk, int YB) {
+    return ((((long long)job * YB + (y >> 3)) * YB + (yp >> 3)) * Nk + k) * 64 + ((y & 7) << 3) + (yp & 7);
 }
 
 __host__ __device__ __forceinline__ long long pair_index(int i1, int i2, int ny) {

@@ -14,7 +14,8 @@
 //
 // CTA = one wavenumber and one job; it walks 32 x 32 tiles of (y, y'), each
 // thread holding a 2 x 2 block of complex accumulators, and writes the batch's
-// contraction to raw[job][k][y][y'] (D: y <= y' only).  DFMA bound.
+// contraction to raw (8 x 8 pair-block layout, raw_index; D: y <= y' only).
+// DFMA bound.
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -94,7 +95,7 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
                     int y = y0 + ty + 16 * a, yp = y1 + tx + 16 * b;
                     if (y >= ny || yp >= ny) continue;
                     if (herm && yp < y) continue;
-                    raw[(((long long)job * Nk + k) * ny + y) * ny + yp] = acc[a][b];
+                    raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc[a][b];
                 }
         }
     }

@@ -119,7 +119,7 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     zd* Xop = c.take<zd>((size_t)NFIELD * Nk * ns * ny);
     zd* G = c.take<zd>((size_t)4 * ny * Nk);
     zd* H = c.take<zd>((size_t)7 * ny * Nk);
-    zd* raw = c.take<zd>((size_t)NJOB * Nk * ny * ny);
+    zd* raw = c.take<zd>((size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * Nk);
     zd* comb = c.take<zd>((size_t)npair * NTERM * Nk);
     zd* W = c.take<zd>((size_t)npair * NTERM * Nk);
     zd* twx = c.take<zd>(nx);

@@ -310,13 +310,14 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
     tc_fence_after();
 
     if (*s_ok) {
-        // TMEM lane = tile row; each warp moves its 32 rows x 32 columns through
-        // shared memory (the operand area is free now) so that every store
-        // writes 32 consecutive y' of one row (256 contiguous bytes).
+        // TMEM lane = tile row.  Each warp moves its 32 rows x 32 columns
+        // through shared memory (the operand area is free now) and writes them
+        // as 16 8x8 pair blocks of the raw layout, 512 contiguous bytes per
+        // store instruction.
         const int lane = threadIdx.x & 31;
+        const int YB = (ny + 7) / 8;
         zf* xp = (zf*)smem + warp * 32 * 33;
         const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-        zf* out = raw + ((long long)job * Nk + k) * ny * (long long)ny;
         for (int c = 0; c < 4; ++c) {
             uint32_t re[32], im[32];
             tmem_ld32(tbase + c * 32, re);
@@ -325,10 +326,20 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
             #pragma unroll
             for (int j = 0; j < 32; ++j) xp[lane * 33 + j] = mk(__uint_as_float(re[j]), __uint_as_float(im[j]));
             __syncwarp();
-            const int yp = nt * TM + c * 32 + lane;
-            for (int rr = 0; rr < 32; ++rr) {
-                const int y = mt * TM + warp * 32 + rr;
-                if (y < cov && yp < cov && (job != NJSQ || yp >= y)) out[(long long)y * ny + yp] = xp[rr * 33 + lane];
+            const int e = 2 * lane, r8 = e >> 3, c8 = e & 7;          // two elements of an 8x8 block
+            #pragma unroll
+            for (int rg = 0; rg < 4; ++rg) {
+                const int yb = (mt * TM + warp * 32) / 8 + rg;
+                #pragma unroll
+                for (int cg = 0; cg < 4; ++cg) {
+                    const int ypb = (nt * TM + c * 32) / 8 + cg;
+                    if (yb < YB && ypb < YB) {
+                        const zf a0 = xp[(8 * rg + r8) * 33 + 8 * cg + c8], a1 = xp[(8 * rg + r8) * 33 + 8 * cg + c8 + 1];
+                        float4 v4 = make_float4(a0.x, a0.y, a1.x, a1.y);
+                        float4* dst = (float4*)(raw + ((((long long)job * YB + yb) * YB + ypb) * Nk + k) * 64 + e);
+                        *dst = v4;
+                    }
+                }
             }
             __syncwarp();
         }
@@ -368,7 +379,7 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
                 si = fmaf(ar, b.y, fmaf(-ai, b.x, si));
             }
         }
-        raw[(((long long)job * Nk + k) * ny + y) * ny + yp] = mk(sr, si);
+        raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = mk(sr, si);
     }
 }
 
