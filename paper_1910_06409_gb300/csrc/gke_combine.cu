@@ -34,6 +34,7 @@
 namespace gke {
 
 constexpr int PB = 8;     // pair block edge
+constexpr int CHUNKS = 1; // k chunks per CTA
 
 template <typename TI> struct CombCfg;
 // ~30 KB of staging per CTA: several CTAs per SM hide the gather latency
@@ -64,11 +65,15 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
     int bt = blockIdx.y, a = 0;
     while (bt >= nblk - a) { bt -= nblk - a; ++a; }
     const int b = a + bt;
-    const int k0 = blockIdx.x * KC;
     const int nslot = 2 * NJOB - 1;
     auto at = [&](int slot, int q, int rr, int cc) -> C& {
         return stage[((slot * KC + q) * PB + rr) * (PB + 1) + cc];
     };
+    // each CTA walks CHUNKS consecutive chunks of KC wavenumbers
+    for (int ch = 0; ch < CHUNKS; ++ch) {
+    const int k0 = (blockIdx.x * CHUNKS + ch) * KC;
+    if (k0 >= Nk) break;
+    __syncthreads();
     for (int e = threadIdx.x; e < nslot * KC * PB * PB; e += blockDim.x) {
         const int slot = e / (KC * PB * PB);
         const int rem = e - slot * KC * PB * PB;
@@ -120,6 +125,7 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
             dst[(long long)t * Nk] = v;
         }
     }
+    }
 }
 
 // comb64[i] = comb32[i] (promotion of the first batch's per-pair sums)
@@ -135,7 +141,7 @@ int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, in
                    double nu, const double* prof, int beta, void* comb, cudaStream_t st)
 {
     const int nxh = nx / 2 + 1, Nk = nz * nxh;
-    const int kc = combine_kc(fp32_in);
+    const int kc = combine_kc(fp32_in) * CHUNKS;
     const int nblk = (ny + PB - 1) / PB;
     dim3 grid((Nk + kc - 1) / kc, nblk * (nblk + 1) / 2);
     if (!fp32_in)
