@@ -243,8 +243,9 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         p->comb_is64 = true;
         p->tsz = sizeof(double);
     }
-    // pairs per inverse-transform chunk: keep the chunk's W scratch (~60 MB) in L2
-    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, (60LL << 20) / ((long long)NTERM * Nk * p->csz)));
+    // pairs per inverse-transform chunk: the chunk's W scratch (~120 MB) mostly
+    // stays in L2 and each launch still fills the GPU
+    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, (120LL << 20) / ((long long)NTERM * Nk * p->csz)));
     ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * Nk * p->csz);
     ALLOC(p->tw_xd, d.nx);
     ALLOC(p->tw_zd, d.nz);

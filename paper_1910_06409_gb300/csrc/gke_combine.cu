@@ -43,7 +43,7 @@ template <> struct CombCfg<double> { static constexpr int KC = 2; };
 
 template <typename TI> constexpr size_t combine_smem_bytes()
 {
-    return (size_t)(2 * NJOB - 1) * CombCfg<TI>::KC * PB * (PB + 1) * sizeof(cplx<TI>);
+    return (size_t)(2 * NJOB - 1) * CombCfg<TI>::KC * PB * (PB + 2) * sizeof(cplx<TI>);
 }
 size_t combine_smem(bool fp32) { return fp32 ? combine_smem_bytes<float>() : combine_smem_bytes<double>(); }
 int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::KC; }
@@ -66,24 +66,38 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
     while (bt >= nblk - a) { bt -= nblk - a; ++a; }
     const int b = a + bt;
     const int nslot = 2 * NJOB - 1;
+    // rows padded to PB + 2 values: 16-byte aligned rows, few bank conflicts
     auto at = [&](int slot, int q, int rr, int cc) -> C& {
-        return stage[((slot * KC + q) * PB + rr) * (PB + 1) + cc];
+        return stage[((slot * KC + q) * PB + rr) * (PB + 2) + cc];
     };
     // each CTA walks CHUNKS consecutive chunks of KC wavenumbers
     for (int ch = 0; ch < CHUNKS; ++ch) {
     const int k0 = (blockIdx.x * CHUNKS + ch) * KC;
     if (k0 >= Nk) break;
     __syncthreads();
-    for (int e = threadIdx.x; e < nslot * KC * PB * PB; e += blockDim.x) {
-        const int slot = e / (KC * PB * PB);
-        const int rem = e - slot * KC * PB * PB;
+    // two consecutive values per thread (one 16-byte load on the split path)
+    for (int e = threadIdx.x; e < nslot * KC * PB * PB / 2; e += blockDim.x) {
+        const int e2 = 2 * e;
+        const int slot = e2 / (KC * PB * PB);
+        const int rem = e2 - slot * KC * PB * PB;
         const int q = rem / (PB * PB), rr = (rem / PB) % PB, cc = rem % PB;
         const int j = slot >> 1, partner = slot & 1;
         const int kq = k0 + q;
         const int yb = partner ? b : a, ypb = partner ? a : b;
-        C v = mk((TI)0, (TI)0);
-        if (kq < Nk) v = raw[((((long long)j * nblk + yb) * nblk + ypb) * Nk + kq) * 64 + rr * PB + cc];
-        at(slot, q, rr, cc) = v;
+        C v0 = mk((TI)0, (TI)0), v1 = v0;
+        if (kq < Nk) {
+            const C* src = raw + ((((long long)j * nblk + yb) * nblk + ypb) * Nk + kq) * 64 + rr * PB + cc;
+            if (sizeof(C) == 8) {
+                const float4 f4 = *(const float4*)src;
+                v0 = *(const C*)&f4.x;
+                v1 = *(const C*)&f4.z;
+            } else {
+                v0 = src[0];
+                v1 = src[1];
+            }
+        }
+        at(slot, q, rr, cc) = v0;
+        at(slot, q, rr, cc + 1) = v1;
     }
     __syncthreads();
     for (int it = threadIdx.x; it < KC * PB * PB; it += blockDim.x) {

@@ -354,21 +354,38 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
 
 // ------------------------------------------- edge rows / columns (FP32)
 // Entries with y >= cov or y' >= cov (the last row / column of a 128 m + 1
-// grid), FP32 products and sums on the CUDA cores, same coefficients.
+// grid), FP32 products and sums on the CUDA cores, same coefficients.  A term
+// of a row-edge entry has the factor conj(A[s][y]) with y on the edge row, a
+// term of a column-edge entry the factor B[s][y']; where that factor is zero
+// for every snapshot the term is skipped (exact: it adds zeros).  With
+// no-slip walls (u = v = w = 0) only the p-v row survives.
 __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, int cov, zf* __restrict__ raw)
 {
+    __shared__ int nz_edge[NFIELD][4];       // field f has a nonzero value on edge row cov + i (i < 4)
     const int k = blockIdx.x;
     const int ne = ny - cov;
+    for (int i = threadIdx.x; i < NFIELD * 4; i += blockDim.x) nz_edge[i / 4][i % 4] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NFIELD * ns * ne; i += blockDim.x) {
+        const int f = i / (ns * ne), r = i - f * ns * ne, s = r / ne, d = r - s * ne;
+        const zf v = Xop[(((long long)f * Nk + k) * ns + s) * ny + cov + d];
+        if ((v.x != 0.f || v.y != 0.f) && d < 4) atomicOr(&nz_edge[f][d], 1);
+    }
+    __syncthreads();
     const int n_row = ne * ny, n_col = cov * ne;
+    const int YB = (ny + 7) / 8;
     for (int e2 = threadIdx.x; e2 < NJOB * (n_row + n_col); e2 += blockDim.x) {
         const int job = e2 / (n_row + n_col), e = e2 - job * (n_row + n_col);
-        const TcJob jd = c_tcjobs[job];
         int y, yp;
-        if (e < n_row) { y = cov + e / ny; yp = e % ny; }
+        const bool row_edge = e < n_row;
+        if (row_edge) { y = cov + e / ny; yp = e % ny; }
         else { int r = e - n_row; y = r / ne; yp = cov + r % ne; }
         if (job == NJSQ && yp < y) continue;
+        const TcJob jd = c_tcjobs[job];
         float sr = 0.f, si = 0.f;
         for (int t = 0; t < jd.nterm; ++t) {
+            const int d = row_edge ? y - cov : yp - cov;
+            if (d < 4 && !nz_edge[row_edge ? jd.fa[t] : jd.fb[t]][d]) continue;   // zero factor
             const float c = (jd.fa[t] >= F_UU && jd.fa[t] <= F_VW) ? 2.f : 1.f;
             const zf* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
             const zf* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
@@ -379,7 +396,7 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
                 si = fmaf(ar, b.y, fmaf(-ai, b.x, si));
             }
         }
-        raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = mk(sr, si);
+        raw[raw_index(job, k, y, yp, Nk, YB)] = mk(sr, si);
     }
 }
 
@@ -392,6 +409,7 @@ static void tile_geometry(int ny, int& MT, int& cov)
 
 gke_status split_alloc(SplitWork& w, int ny, int ns, int Nk)
 {
+
     int MT, cov;
     tile_geometry(ny, MT, cov);
     const int G = (ns + KS - 1) / KS;

@@ -259,7 +259,7 @@ int terms_launch_t(const TermArgs& a)
                 (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, (C*)a.W);
         }
         if (a.nx == 256) {
-            constexpr int RZR = 16;
+            constexpr int RZR = 4;
             k_terms_rowpass_r<TF, TO, 16, 16><<<dim3((a.nz + RZR - 1) / RZR, (unsigned)np), RZR * 16,
                                                 (256 + RZR * 16 * 17) * sizeof(C), a.st>>>(
                 (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, RZR, a.prof, (const C*)a.tw_x, (TO*)a.terms,

@@ -42,6 +42,25 @@ def test_split_matches_f64(N, shape):
     assert max(errs) > 0.0          # the split path really ran (not the FP64 one)
 
 
+def test_split_edge_row_with_nonzero_walls(N):
+    """ny = 128 m + 1 leaves the last row / column to the CUDA-core edge kernel;
+    give every field non-zero wall values so no edge term is skipped."""
+    wl = S.small(16, 16, 129, 3, wid=78)
+    coef = S.coefficients(wl)
+    rng = np.random.default_rng(5)
+    for j in (0, wl.ny - 1):
+        noise = 0.05 * (rng.standard_normal(coef[:, :, j].shape) + 1j * rng.standard_normal(coef[:, :, j].shape))
+        noise[..., 0] = noise[..., 0].real          # kx = 0 column of a real field stays real at kz = 0 ...
+        coef[:, :, j] += noise
+    # keep the fields real: rebuild the coefficients from their physical planes
+    phys = np.fft.irfft2(coef, s=(wl.nz, wl.nx), axes=(-2, -1), norm="forward")
+    coef = S.to_coefficients(phys)
+    ref, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_F64)
+    got, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_BF16X3)
+    errs = [rel_err(got[t], ref[t]) for t in range(N.GKE_NTERM)]
+    assert max(errs) <= TOL_SPLIT, dict(zip(N.TERMS, errs))
+
+
 def test_split_multi_batch_promotes_to_fp64(N):
     """A second batch promotes the per-pair sums to FP64; the result matches one batch."""
     wl = S.small(16, 8, 33, 6, wid=77)
