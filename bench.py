@@ -61,6 +61,69 @@ def correlator_cmac(wl, ns):
     return Nk * ns * (3 * wl.npair + 14 * wl.ny * wl.ny)
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernels, from the ncu launch list of this benchmark's command
+# (profiles/launches_retau200.md); None where the kernel changed since.
+NCU_TRAFFIC_GB = {}
+
+
+def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
+    """Algorithmic work of each stage of one pass, and its roofline.
+
+    Bytes count each stage's essential inputs read once and outputs written
+    once (workspaces between kernels of a stage are not counted); the
+    contraction stage counts flops (tensor BF16 on the split path, FP64 DFMA
+    on the plain path)."""
+    f32 = precision != "f64"
+    cz = 8 if f32 else 16                          # bytes of one complex operand / spectrum value
+    tz = 4 if f32 else 8                           # bytes of one term value
+    Nk, ny, N = wl.nz * wl.nxh, wl.ny, wl.nx * wl.nz
+    yb = (ny + 7) // 8
+    raw = 7 * yb * yb * 64 * Nk * cz
+    comb = wl.npair * 7 * Nk * cz
+    terms = 7 * wl.npair * N * tz
+    spec_arr = wl.npair * N * 4
+    hbm = {
+        "products": ns * 4 * ny * Nk * 16 + 11 * Nk * ns * ny * cz,
+        "combine": raw + comb,
+        "terms": comb + terms + (3 * spec_arr if f32 else 0),
+        "stencil": (13 * spec_arr) if f32 else (9 * wl.npair * N * 8),
+    }
+    if f32:
+        # contraction stage: operand split + tensor-core contractions + edge
+        hbm["correlate_bytes"] = 11 * Nk * ns * ny * cz + raw
+    peak_bw = pk["hbm_gbs"]
+    out = {}
+    for st, b in hbm.items():
+        if st.endswith("_bytes") or st not in stage_ms or stage_ms[st] <= 0:
+            continue
+        ach = b / (stage_ms[st] / 1e3) / 1e9
+        out[st] = {"bound": "hbm", "achieved": ach, "peak": peak_bw, "unit": "GB/s", "frac": ach / peak_bw,
+                   "bytes": b, "launch_ms": stage_ms[st], "traffic": NCU_TRAFFIC_GB.get(st),
+                   "peak_source": f"hbm_gbs ({pk_kind})"}
+    cm = correlator_cmac(wl, ns)
+    ms = stage_ms.get("correlate", 0.0)
+    if ms > 0:
+        if f32:
+            flops = 48.0 * cm                      # 6 BF16 slice products x 8 real flops per complex MAC
+            peak = pk["bf16_tflops"]
+            out["correlate"] = {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
+                                "unit": "TFLOP/s", "flops": flops, "launch_ms": ms,
+                                "traffic": NCU_TRAFFIC_GB.get("correlate"),
+                                "peak_source": f"bf16_tflops ({pk_kind})",
+                                "note": "stage = operand split + tcgen05 contractions + edge row"}
+        else:
+            flops = 8.0 * cm
+            peak = N_SM * FP64_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            out["correlate"] = {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
+                                "unit": "TFLOP/s", "flops": flops, "launch_ms": ms,
+                                "traffic": NCU_TRAFFIC_GB.get("correlate"),
+                                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock "
+                                               "(nominal 1.25 TFLOP/s FP64)"}
+        out["correlate"]["frac"] = out["correlate"]["achieved"] / out["correlate"]["peak"]
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
 
@@ -257,26 +320,18 @@ def run_ours(args, world, rank, local):
         del out_host, f_host
     N.gke_destroy(plan)
 
-    # roofline of the dominant kernel (the correlator)
-    pk, pk_kind = peaks()
-    corr_ms = stage["correlate"] / args.steps
-    flops = 8.0 * correlator_cmac(wl, ns)
-    clocks = clk.summary()
-    if args.precision == "f64":
-        sm_mhz = pk.get("sm_max_mhz", 2070.0)
-        peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "k_correlate_f64", "achieved": flops / (corr_ms / 1e3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock (nominal 1.25 TFLOP/s FP64)"}
-    else:
-        peak = pk["bf16_tflops"]
-        bf16_flops = 6 * flops            # three-slice split: 6 slice products per FP64-equivalent product
-        roof = {"bound": "tensor", "kernel": "split correlator", "achieved": bf16_flops / (corr_ms / 1e3) / 1e12,
-                "peak": peak, "unit": "TFLOP/s", "peak_source": f"bf16_tflops ({pk_kind})"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["launch_ms"] = corr_ms
+    # split-BF16 path on the same inputs: throughput, speed-up and per-term error vs the FP64 GPU path
+    split = None
+    if args.precision == "f64" and not args.no_split:
+        split = run_split_beside(args, wl, ns, f_dev, terms, ms, barrier, world)
 
+    # rooflines: every stage against its bound, the dominant stage reported as "roofline"
+    pk, pk_kind = peaks()
+    clocks = clk.summary()
+    stage_ms = {k: v / args.steps for k, v in stage.items()}
+    rl = stage_rooflines(wl, ns, args.precision, stage_ms, pk, pk_kind)
+    dominant = max(rl, key=lambda k: rl[k]["launch_ms"])
+    roof = dict(rl[dominant], stage=dominant)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         phys = S.physical(wl)
@@ -288,13 +343,70 @@ def run_ours(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "bf16x3/f32",
                 "data": "synthetic", "config": config_of(wl, args.precision), "parallelism": f"replicas{world}",
-                "stage_ms": {k: v / args.steps for k, v in stage.items()},
+                "stage_ms": stage_ms,
                 "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
+                "stage_roofline": rl, "split_bf16x3": split,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world):
+    """Time the split-BF16 path on the FP64 run's inputs and compare its terms.
+
+    Error per term: max |split - f64| / max |f64| over all pairs and
+    separations, against the FP64 GPU path (itself within 1e-12 of the
+    oracle)."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+    stream = torch.cuda.current_stream()
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), ns, N.GKE_PREC_BF16X3,
+                      stream=stream.cuda_stream)
+    npair = N.gke_npair(plan)
+    t32 = torch.empty_like(terms64, dtype=torch.float32)
+    for _ in range(args.warmup):
+        N.gke_compute(plan, f_dev, ns, t32)
+    torch.cuda.synchronize()
+    N.gke_set_timing(plan, True)
+    N.gke_stage_times(plan)
+    l0 = N.gke_launch_count(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        N.gke_compute(plan, f_dev, ns, t32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = N.gke_launch_count(plan) - l0
+    stage_ms = {k: v / args.steps for k, v in N.gke_stage_times(plan).items()}
+    N.gke_destroy(plan)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    err = {}
+    for t, name in enumerate(TERM_NAMES):
+        ref = terms64[t]
+        scale = float(ref.abs().max())
+        diff = float((t32[t].double() - ref).abs().max())
+        err[name] = diff / scale if scale > 0 else diff
+    del t32
+    pk, pk_kind = peaks()
+    rl = stage_rooflines(wl, ns, "bf16x3", stage_ms, pk, pk_kind)
+    return {"value": world * npair * ns / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "speedup_vs_f64": ms64 / ms, "max_rel_err": err, "tolerance": 1e-6,
+            "within_tolerance": all(e <= 1e-6 for e in err.values()),
+            "stage_ms": stage_ms, "gpu_launches": launches, "roofline": rl.get("correlate"),
+            "stage_roofline": rl}
+
+
+TERM_NAMES = ("A", "Phi_x", "Phi_y", "Phi_z", "phi", "xi", "residual")
 
 
 def main():
@@ -307,6 +419,8 @@ def main():
     ap.add_argument("--workload", default=S.RETAU200.name, choices=sorted(S.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-split", action="store_true",
+                    help="with --precision f64: skip the split-BF16 run beside it")
     ap.add_argument("--cpu-points", type=int, default=512)
     ap.add_argument("--ref-points", type=int, default=256)
     args = ap.parse_args()
