@@ -126,6 +126,8 @@ static void fornberg_d1(const double* x, int n, double z0, double* w)
 }
 
 static const int EPS_KCHUNK = 16;
+// bytes of inverse-transform scratch per pair chunk
+static const long long W_CHUNK_BYTES = 120LL << 20;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
@@ -243,9 +245,10 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         p->comb_is64 = true;
         p->tsz = sizeof(double);
     }
-    // pairs per inverse-transform chunk: the chunk's W scratch (~120 MB) mostly
-    // stays in L2 and each launch still fills the GPU
-    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, (120LL << 20) / ((long long)NTERM * Nk * p->csz)));
+    // pairs per inverse-transform chunk: the chunk's W scratch (W_CHUNK_BYTES)
+    // mostly stays in L2 between the two passes, and each launch still fills
+    // the GPU
+    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * Nk * p->csz)));
     ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * Nk * p->csz);
     ALLOC(p->tw_xd, d.nx);
     ALLOC(p->tw_zd, d.nz);

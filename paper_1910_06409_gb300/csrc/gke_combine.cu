@@ -70,11 +70,28 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
     auto at = [&](int slot, int q, int rr, int cc) -> C& {
         return stage[((slot * KC + q) * PB + rr) * (PB + 2) + cc];
     };
+    // per-wavenumber and per-pair coefficients, formed once per CTA (FP64
+    // arithmetic costs as much as ~60 FP32 operations here, so none is done
+    // per item)
+    __shared__ TC s_kx[KC], s_kz[KC];
+    __shared__ TC s_dU[PB * PB], s_Upm[PB * PB], s_dUp[PB * PB];
+    if (threadIdx.x < PB * PB) {
+        const int i1 = min(PB * a + threadIdx.x / PB, ny - 1), i2 = min(PB * b + threadIdx.x % PB, ny - 1);
+        s_dU[threadIdx.x] = (TC)(prof[PR_U * ny + i2] - prof[PR_U * ny + i1]);
+        s_Upm[threadIdx.x] = (TC)(0.5 * (prof[PR_DU * ny + i1] + prof[PR_DU * ny + i2]));
+        s_dUp[threadIdx.x] = (TC)(prof[PR_DU * ny + i2] - prof[PR_DU * ny + i1]);
+    }
     // each CTA walks CHUNKS consecutive chunks of KC wavenumbers
     for (int ch = 0; ch < CHUNKS; ++ch) {
     const int k0 = (blockIdx.x * CHUNKS + ch) * KC;
     if (k0 >= Nk) break;
     __syncthreads();
+    if (threadIdx.x >= 256 - KC) {
+        const int kk = threadIdx.x - (256 - KC), k = min(k0 + kk, Nk - 1);
+        const int kz_i = k / nxh, kx_i = k - kz_i * nxh;
+        s_kx[kk] = (TC)(6.283185307179586476925286766559 * signed_bin(kx_i, nx) / Lx);
+        s_kz[kk] = (TC)(6.283185307179586476925286766559 * signed_bin(kz_i, nz) / Lz);
+    }
     // two consecutive values per thread (one 16-byte load on the split path)
     for (int e = threadIdx.x; e < nslot * KC * PB * PB / 2; e += blockDim.x) {
         const int e2 = 2 * e;
@@ -88,7 +105,7 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         if (kq < Nk) {
             const C* src = raw + ((((long long)j * nblk + yb) * nblk + ypb) * Nk + kq) * 64 + rr * PB + cc;
             if (sizeof(C) == 8) {
-                const float4 f4 = *(const float4*)src;
+                const float4 f4 = __ldcs((const float4*)src);
                 v0 = *(const C*)&f4.x;
                 v1 = *(const C*)&f4.z;
             } else {
@@ -104,12 +121,8 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         const int kk = it % KC, pm = it / KC, r = pm / PB, m = pm % PB;
         const int k = k0 + kk, i1 = PB * a + r, i2 = PB * b + m;
         if (k >= Nk || i1 >= ny || i2 >= ny || i2 < i1) continue;
-        const int kz_i = k / nxh, kx_i = k - kz_i * nxh;
-        const TC kx = (TC)(6.283185307179586476925286766559 * signed_bin(kx_i, nx) / Lx);
-        const TC kz = (TC)(6.283185307179586476925286766559 * signed_bin(kz_i, nz) / Lz);
-        const TC dU = (TC)(prof[PR_U * ny + i2] - prof[PR_U * ny + i1]);
-        const TC Upm = (TC)(0.5 * (prof[PR_DU * ny + i1] + prof[PR_DU * ny + i2]));
-        const TC dUp = (TC)(prof[PR_DU * ny + i2] - prof[PR_DU * ny + i1]);
+        const TC kx = s_kx[kk], kz = s_kz[kk];
+        const TC dU = s_dU[pm], Upm = s_Upm[pm], dUp = s_dUp[pm];
         const TC nuc = (TC)nu;
         auto v12 = [&](int j) { C v = at(2 * j, kk, r, m); return mk((TC)v.x, (TC)v.y); };
         auto v21 = [&](int j) { C v = at(2 * j + 1, kk, m, r); return mk((TC)v.x, -(TC)v.y); };  // conj
@@ -135,8 +148,12 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         #pragma unroll
         for (int t = 0; t < NTERM; ++t) {
             cplx<TO> v = mk((TO)T[t].x, (TO)T[t].y);
-            if (beta) v = v + dst[(long long)t * Nk];
-            dst[(long long)t * Nk] = v;
+            if (beta) {
+                v = v + dst[(long long)t * Nk];
+                dst[(long long)t * Nk] = v;
+            } else {
+                st_stream(dst + (long long)t * Nk, v);
+            }
         }
     }
     }

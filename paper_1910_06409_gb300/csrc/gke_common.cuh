@@ -244,6 +244,23 @@ __device__ __forceinline__ void fft2l(cplx<T>* v, int lane, cplx<T>* xs, int s1,
     }
 }
 
+// streaming (evict-first) loads and stores for data touched once, so that
+// they do not push reused working sets out of L2
+__device__ __forceinline__ cplx<float> ld_stream(const cplx<float>* p) {
+    const float2 v = __ldcs((const float2*)p);
+    cplx<float> r; r.x = v.x; r.y = v.y; return r;
+}
+__device__ __forceinline__ cplx<double> ld_stream(const cplx<double>* p) {
+    const double2 v = __ldcs((const double2*)p);
+    cplx<double> r; r.x = v.x; r.y = v.y; return r;
+}
+__device__ __forceinline__ void st_stream(cplx<float>* p, cplx<float> v) { __stcs((float2*)p, make_float2(v.x, v.y)); }
+__device__ __forceinline__ void st_stream(cplx<double>* p, cplx<double> v) {
+    __stcs((double2*)p, make_double2(v.x, v.y));
+}
+__device__ __forceinline__ void st_stream(float* p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st_stream(double* p, double v) { __stcs(p, v); }
+
 // signed wavenumber index of FFT bin m of an n-point transform, 0 at Nyquist
 __host__ __device__ __forceinline__ int signed_bin(int m, int n) {
     if (2 * m == n) return 0;

@@ -15,7 +15,10 @@
 // CTA = one wavenumber and one job; it walks 32 x 32 tiles of (y, y'), each
 // thread holding a 2 x 2 block of complex accumulators, and writes the batch's
 // contraction to raw (8 x 8 pair-block layout, raw_index; D: y <= y' only).
-// DFMA bound.
+// DFMA bound.  When ny leaves a thin remainder past the last full tile (the
+// Chebyshev grids ny = 32 m + 1 leave one wall row), that remainder is done
+// as row and column strips, one (y, y') per thread, instead of as mostly empty
+// padded tiles (which cost half as much again as the useful work at ny = 129).
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -41,6 +44,7 @@ void upload_jobs(cudaStream_t st)
 
 #define CT 32       // tile edge
 #define SCH 8       // snapshots per shared-memory chunk
+#define STRIP_MAX 4 // widest remainder done as strips
 
 __global__ void __launch_bounds__(256)
 k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restrict__ raw)
@@ -49,9 +53,11 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
     __shared__ zd Bs[SCH][CT];
     const int k = blockIdx.x, job = blockIdx.y;
     const bool herm = (job == NJSQ);
-    const JobDesc jd = c_jobs[job];
+    const JobDesc& jd = c_jobs[job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int nt = (ny + CT - 1) / CT;
+    const int nfull = ny / CT, rem = ny - nfull * CT;
+    const bool strips = nfull > 0 && rem > 0 && rem <= STRIP_MAX;
+    const int nt = strips ? nfull : (ny + CT - 1) / CT;
     for (int tb0 = 0; tb0 < nt; ++tb0) {
         for (int tb1 = herm ? tb0 : 0; tb1 < nt; ++tb1) {
             const int y0 = tb0 * CT, y1 = tb1 * CT;
@@ -98,6 +104,35 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
                     raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc[a][b];
                 }
         }
+    }
+    if (!strips) return;
+    // remainder strips: rows y >= cov against every y' (D: y' >= y), then
+    // columns y' >= cov against y < cov
+    const int cov = nfull * CT;
+    const int nrow = rem * ny, ncol = cov * rem;
+    for (int e = threadIdx.x; e < nrow + ncol; e += blockDim.x) {
+        int y, yp;
+        if (e < nrow) {
+            y = cov + e / ny;
+            yp = e - (y - cov) * ny;
+            if (herm && yp < y) continue;
+        } else {
+            const int f = e - nrow;
+            y = f / rem;
+            yp = cov + (f - y * rem);
+        }
+        zd acc = mk(0.0, 0.0);
+        for (int t = 0; t < jd.nterm; ++t) {
+            const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+            const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+            const double c = jd.c[t];
+            for (int s = 0; s < ns; ++s) {
+                const zd a = c * A[(long long)s * ny + y], b = B[(long long)s * ny + yp];
+                acc.x += a.x * b.x + a.y * b.y;
+                acc.y += a.x * b.y - a.y * b.x;
+            }
+        }
+        raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc;
     }
 }
 

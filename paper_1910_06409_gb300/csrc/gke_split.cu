@@ -337,7 +337,7 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
                         const zf a0 = xp[(8 * rg + r8) * 33 + 8 * cg + c8], a1 = xp[(8 * rg + r8) * 33 + 8 * cg + c8 + 1];
                         float4 v4 = make_float4(a0.x, a0.y, a1.x, a1.y);
                         float4* dst = (float4*)(raw + ((((long long)job * YB + yb) * YB + ypb) * Nk + k) * 64 + e);
-                        *dst = v4;
+                        __stcs(dst, v4);
                     }
                 }
             }

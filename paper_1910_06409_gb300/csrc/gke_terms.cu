@@ -83,7 +83,7 @@ k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, i
     for (int m = 0; m < N1; ++m) {
         C x = mk((TF)0, (TF)0);
         if (kx < nxh) {
-            const cplx<TB> b = src[(long long)(lane + N2 * m) * nxh + kx];
+            const cplx<TB> b = ld_stream(src + (long long)(lane + N2 * m) * nxh + kx);
             x = mk(ic * (TF)b.x, ic * (TF)b.y);
         }
         v[m] = x;
@@ -229,10 +229,10 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
                     const int q = 2 * jq + h;
                     if (q >= NTERM) break;
                     const TF sp = h ? v[m].y : v[m].x;
-                    terms[((long long)q * npair + p) * NN + e] = (TO)(sp + s_one[q]);
+                    st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[q]));
                     if (spec != nullptr) {
                         const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
-                        if (si >= 0) spec[((long long)si * npair + p) * NN + e] = (float)sp;
+                        if (si >= 0) st_stream(spec + ((long long)si * npair + p) * NN + e, (float)sp);
                     }
                 }
             }
