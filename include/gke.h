@@ -22,11 +22,22 @@
  *       a_hat(y, kz, kx) = 1/(nx nz) sum_{x,z} a(x, y, z) e^{-i (kx x + kz z)},
  *     kz in FFT order (index m -> m for m < nz/2, m - nz above), kx = 0..nx/2:
  *     exactly numpy/torch rfft2(a, norm="forward") over the last two axes.
- *   - Pairs: the npair = ny (ny + 1) / 2 ordered pairs (i1, i2), i1 <= i2,
- *     enumerated row-major (i1 outer); Y1 = y[i1], Y2 = y[i2];
- *     Y = (Y1 + Y2)/2, r_y = Y2 - Y1 (gke_pair_labels).  Terms at Y2 < Y1
- *     follow from the stored ones by r-inversion: A, phi, xi are even,
- *     Phi_x, Phi_y, Phi_z odd under (Y1, Y2, r) -> (Y2, Y1, -r).
+ *   - Pairs (pair_domain = GKE_DOMAIN_TRIANGLE): the npair = ny (ny + 1) / 2
+ *     ordered pairs (i1, i2), i1 <= i2, enumerated row-major (i1 outer);
+ *     Y1 = y[i1], Y2 = y[i2]; Y = (Y1 + Y2)/2, r_y = Y2 - Y1
+ *     (gke_pair_labels).  Terms at Y2 < Y1 follow from the stored ones by
+ *     r-inversion: A, phi, xi are even, Phi_x, Phi_y, Phi_z odd under
+ *     (Y1, Y2, r) -> (Y2, Y1, -r).
+ *   - Pairs (pair_domain = GKE_DOMAIN_WEDGE, Sec. 3.2 Step 2 and Sec. 3.3):
+ *     every snapshot also contributes its mirror image about the centreline,
+ *     u(x, 2h - y, z), -v(x, 2h - y, z), w(x, 2h - y, z), p(x, 2h - y, z),
+ *     which doubles the statistical sample; the outputs are the pairs of the
+ *     half-channel wedge i1 <= i2, i1 + i2 <= ny - 1 (Y1 <= h, Y1 <= Y2 <=
+ *     2h - Y1), row-major, npair = sum over i1 of (ny - 2 i1).  The grid must
+ *     be symmetric (y[j] + y[ny-1-j] the same for every j).  Terms of the
+ *     other pairs follow by r-inversion and by the combined inversion of y
+ *     and r, (Y1, Y2, r) -> (2h - Y2, 2h - Y1, -r), under which Phi_x, Phi_z
+ *     and phi change sign and A, Phi_y, xi and the residual do not.
  *   - Separations: index (m_z, m_x) in [0, nz) x [0, nx), FFT order,
  *     r_x = m_x Lx / nx, r_z = m_z Lz / nz (periodic).
  *   - Output terms (double on the FP64 path, float on the split path):
@@ -74,6 +85,9 @@ typedef enum {
 enum { GKE_PREC_F64 = 0,       /* plain FP64 correlator (DFMA)                        */
        GKE_PREC_BF16X3 = 1 };  /* split-BF16 correlator on the tensor cores           */
 
+enum { GKE_DOMAIN_TRIANGLE = 0,  /* all pairs i1 <= i2                                  */
+       GKE_DOMAIN_WEDGE = 1 };   /* y-inversion mirror sampling, half-channel wedge     */
+
 enum { GKE_TERM_A = 0, GKE_TERM_PHI_X, GKE_TERM_PHI_Y, GKE_TERM_PHI_Z, GKE_TERM_PHI,
        GKE_TERM_XI, GKE_TERM_RESIDUAL, GKE_NTERM };
 
@@ -86,6 +100,7 @@ typedef struct {
     const double* y;       /* host pointer, y[ny], strictly increasing; copied            */
     int max_snap;          /* largest nsnap of any accumulate call (sizes workspaces)    */
     int precision;         /* GKE_PREC_*                                                 */
+    int pair_domain;       /* GKE_DOMAIN_*                                               */
 } gke_desc;
 
 /* Create a plan: validates the descriptor, computes the FD weights and

@@ -75,13 +75,40 @@ def fd_weights(y: np.ndarray, j: int):
     return l0, w
 
 
-def full(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, nthreads: int = 0):
+def mirror_augment(phys: np.ndarray) -> np.ndarray:
+    """The snapshot set doubled by the mirror images about the centreline.
+
+    Mirror sampling (Sec. 3.2, Step 2): the channel is statistically
+    symmetric under the inversion of the wall-normal axis, y -> 2h - y, which
+    maps a flow field to another flow field with the same statistics:
+    u(x, 2h - y, z), -v(x, 2h - y, z), w(x, 2h - y, z), p(x, 2h - y, z).
+    Each snapshot's image is one more sample.  On a grid symmetric about the
+    centreline the image of plane j is plane ny - 1 - j.
+    """
+    phys = np.asarray(phys, dtype=np.float64)
+    img = phys[:, :, ::-1].copy()
+    img[:, 1] *= -1.0
+    return np.concatenate([phys, img], axis=0)
+
+
+def wedge_pairs(ny: int):
+    """Pairs (i1, i2) of the half-channel wedge, row-major: i1 <= i2 and
+    i1 + i2 <= ny - 1, i.e. Y1 <= h and Y1 <= Y2 <= 2h - Y1 (Sec. 3.2, Step 2)."""
+    return [(a, b) for a in range(ny) for b in range(a, ny - a)]
+
+
+def full(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, nthreads: int = 0,
+         mirror: bool = False):
     """All components and terms on the full square of ordered pairs.
 
     phys: float64 [ns][4][ny][nz][nx] (u, v, w, p including the mean).
+    mirror: average over the snapshots and their mirror images
+    (mirror_augment; y must be symmetric about its centre).
     Returns dict(comp=[12][ny][ny][nz][nx], terms=[7][ny][ny][nz][nx],
     prof=[6][ny]) with names COMPONENTS, TERMS, PROFILES.
     """
+    if mirror:
+        phys = mirror_augment(phys)
     phys = np.ascontiguousarray(phys, dtype=np.float64)
     ns, nf, ny, nz, nx = phys.shape
     assert nf == 4
@@ -96,12 +123,15 @@ def full(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, nthre
     return {"comp": comp, "terms": terms, "prof": prof}
 
 
-def points(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, pts, nthreads: int = 0):
+def points(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, pts, nthreads: int = 0,
+           mirror: bool = False):
     """Components and terms (all but the residual) at points (i1, i2, m_z, m_x).
 
-    Returns dict(comp=[n][12], terms=[n][6], prof=[6][ny]); eps in prof is NaN on
-    planes no point touches.
+    mirror: as in full().  Returns dict(comp=[n][12], terms=[n][6],
+    prof=[6][ny]); eps in prof is NaN on planes no point touches.
     """
+    if mirror:
+        phys = mirror_augment(phys)
     phys = np.ascontiguousarray(phys, dtype=np.float64)
     ns, nf, ny, nz, nx = phys.shape
     y = np.ascontiguousarray(y, dtype=np.float64)

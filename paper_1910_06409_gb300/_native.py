@@ -18,6 +18,7 @@ GKE_OK = 0
 STATUS = {0: "GKE_OK", -1: "GKE_ERR_ARG", -2: "GKE_ERR_STATE", -3: "GKE_ERR_OOM", -4: "GKE_ERR_CUDA",
           -5: "GKE_ERR_NONFINITE", -6: "GKE_ERR_IO", -7: "GKE_ERR_UNSUPPORTED"}
 GKE_PREC_F64, GKE_PREC_BF16X3 = 0, 1
+GKE_DOMAIN_TRIANGLE, GKE_DOMAIN_WEDGE = 0, 1
 TERMS = ("A", "Phi_x", "Phi_y", "Phi_z", "phi", "xi", "residual")
 PROFILES = ("U", "V", "W", "P", "dUdy", "eps")
 GKE_NTERM, GKE_NPROF = len(TERMS), len(PROFILES)
@@ -34,7 +35,7 @@ class gke_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("ny", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("nu", ctypes.c_double),
                 ("y", ctypes.POINTER(ctypes.c_double)),
-                ("max_snap", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("max_snap", ctypes.c_int), ("precision", ctypes.c_int), ("pair_domain", ctypes.c_int)]
 
 
 class GkeError(RuntimeError):
@@ -104,11 +105,12 @@ def _check(status: int, plan) -> None:
         raise GkeError(status, msg.decode() if msg else "")
 
 
-def gke_plan(nx, nz, ny, Lx, Lz, nu, y, max_snap, precision=GKE_PREC_F64, stream=None):
+def gke_plan(nx, nz, ny, Lx, Lz, nu, y, max_snap, precision=GKE_PREC_F64, stream=None,
+             pair_domain=GKE_DOMAIN_TRIANGLE):
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), max_snap,
-                    precision)
+                    precision, pair_domain)
     out = ctypes.c_void_p()
     st = lib().gke_plan(ctypes.byref(desc), stream, ctypes.byref(out))
     _check(st, None)
@@ -184,7 +186,7 @@ def gke_compute_noalloc(nx, nz, ny, Lx, Lz, nu, y, fields, nsnap, terms, profile
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsnap,
-                    GKE_PREC_F64)
+                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE)
     st = lib().gke_compute_noalloc(ctypes.byref(desc), ptr(fields), nsnap, ptr(terms), ptr(profiles), stream)
     if st != GKE_OK:
         raise GkeError(st, "gke_compute_noalloc")

@@ -26,7 +26,12 @@ struct gke_plan_s {
     std::vector<double> y;
     cudaStream_t st = nullptr;
     int nxh = 0, Nk = 0;
-    long long npair = 0;
+    // npair: output pairs (the triangle, or the wedge with mirror sampling);
+    // npair_tri: pairs of the triangle, over which the spectra are summed
+    long long npair = 0, npair_tri = 0;
+    bool wedge = false;
+    void* fold = nullptr;                     // wedge: folded spectra (aliases raw when it fits)
+    bool fold_owned = false;
     // device workspaces; Xop, G, H, raw and W hold complex<TF>, TF = double on
     // the plain path and float on the split path
     void *Xop = nullptr, *G = nullptr, *H = nullptr, *raw = nullptr, *W = nullptr;
@@ -56,6 +61,7 @@ struct gke_plan_s {
     // host state
     double mean_count = 0.0, snap_count = 0.0;
     bool mean_frozen = false, have_acc = false, finalized = false;
+    std::vector<double> mean_sum_host;       // staging of the symmetrised mean sums
     std::string err;
 };
 
@@ -200,8 +206,21 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         g_plan_err = "unknown precision";
         return GKE_ERR_ARG;
     }
+    if (d.pair_domain != GKE_DOMAIN_TRIANGLE && d.pair_domain != GKE_DOMAIN_WEDGE) {
+        g_plan_err = "unknown pair_domain";
+        return GKE_ERR_ARG;
+    }
     for (int j = 1; j < d.ny; ++j)
         if (!(d.y[j] > d.y[j - 1])) { g_plan_err = "y must be strictly increasing"; return GKE_ERR_ARG; }
+    if (d.pair_domain == GKE_DOMAIN_WEDGE) {
+        // mirror sampling needs a grid symmetric about the centreline
+        const double c = d.y[0] + d.y[d.ny - 1], tol = 1e-12 * (d.y[d.ny - 1] - d.y[0]);
+        for (int j = 0; j < d.ny; ++j)
+            if (std::fabs(d.y[j] + d.y[d.ny - 1 - j] - c) > tol) {
+                g_plan_err = "pair_domain GKE_DOMAIN_WEDGE needs a y grid symmetric about its centre";
+                return GKE_ERR_ARG;
+            }
+    }
 
     gke_plan_t p = new (std::nothrow) gke_plan_s;
     if (!p) { g_plan_err = "host allocation failed"; return GKE_ERR_OOM; }
@@ -211,7 +230,13 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     p->st = (cudaStream_t)stream;
     p->nxh = d.nx / 2 + 1;
     p->Nk = d.nz * p->nxh;
-    p->npair = (long long)d.ny * (d.ny + 1) / 2;
+    p->npair_tri = (long long)d.ny * (d.ny + 1) / 2;
+    p->wedge = (d.pair_domain == GKE_DOMAIN_WEDGE);
+    p->npair = p->npair_tri;
+    if (p->wedge) {
+        p->npair = 0;
+        for (int i1 = 0; 2 * i1 <= d.ny - 1; ++i1) p->npair += d.ny - 2 * i1;
+    }
     const int ny = d.ny, ns = d.max_snap, Nk = p->Nk;
     const size_t plane = (size_t)d.nz * p->nxh;
 
@@ -234,14 +259,22 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOCB(p->Xop, (size_t)NFIELD * Nk * ns * ny * p->csz);
     ALLOCB(p->G, (size_t)4 * ny * plane * p->csz);
     ALLOCB(p->H, (size_t)7 * ny * plane * p->csz);
-    ALLOCB(p->raw, (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * Nk * p->csz);
+    const size_t raw_bytes = (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * Nk * p->csz;
+    ALLOCB(p->raw, raw_bytes);
+    if (p->wedge) {
+        // the folded spectra of the output pairs (at most complex128) are
+        // formed at finalize, when raw is free
+        const size_t fold_bytes = (size_t)p->npair * NTERM * Nk * sizeof(zd);
+        if (fold_bytes <= raw_bytes) p->fold = p->raw;
+        else { ALLOCB(p->fold, fold_bytes); p->fold_owned = true; }
+    }
     if (f32) {
-        ALLOC(p->comb32, (size_t)p->npair * NTERM * Nk);
+        ALLOC(p->comb32, (size_t)p->npair_tri * NTERM * Nk);
         // spectral parts of A, Phi_y, phi, then 13 per-pair stencil scalars
         ALLOC(p->spec, (size_t)3 * p->npair * d.nx * d.nz + 13 * (size_t)p->npair);
         p->tsz = sizeof(float);
     } else {
-        ALLOC(p->comb, (size_t)p->npair * NTERM * Nk);
+        ALLOC(p->comb, (size_t)p->npair_tri * NTERM * Nk);
         p->comb_is64 = true;
         p->tsz = sizeof(double);
     }
@@ -290,10 +323,11 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         l0[j] = a;
         fornberg_d1(p->y.data() + a, 5, p->y[j], w.data() + 5 * j);
     }
+    // output pair table, row-major: the triangle, or the wedge i1 + i2 <= ny - 1
     std::vector<int> pi(2 * p->npair);
     long long q = 0;
     for (int i1 = 0; i1 < ny; ++i1)
-        for (int i2 = i1; i2 < ny; ++i2) { pi[2 * q] = i1; pi[2 * q + 1] = i2; ++q; }
+        for (int i2 = i1; i2 < (p->wedge ? ny - i1 : ny); ++i2) { pi[2 * q] = i1; pi[2 * q + 1] = i2; ++q; }
     cudaStream_t st = p->st;
     if ((e = cudaMemcpyAsync(p->tw_xd, twx.data(), twx.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->tw_zd, twz.data(), twz.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
@@ -332,6 +366,7 @@ extern "C" void gke_destroy(gke_plan_t p)
 {
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
+    if (p->fold_owned) cudaFree(p->fold);
     void* ptrs[] = {p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
                     p->fdl0, p->pair_i, p->nonfinite, p->part};
@@ -387,7 +422,7 @@ extern "C" gke_status gke_pair_labels(gke_plan_t p, double* Y, double* ry, int* 
     if (!p) return GKE_ERR_ARG;
     long long q = 0;
     for (int a = 0; a < p->d.ny; ++a)
-        for (int b = a; b < p->d.ny; ++b, ++q) {
+        for (int b = a; b < (p->wedge ? p->d.ny - a : p->d.ny); ++b, ++q) {
             if (Y) Y[q] = 0.5 * (p->y[a] + p->y[b]);
             if (ry) ry[q] = p->y[b] - p->y[a];
             if (i1) i1[q] = a;
@@ -467,10 +502,23 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
         CUDA_TRY(p, cudaMemcpyAsync(m.data(), p->mean_sum, m.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(p, cudaStreamSynchronize(st));
         for (double& v : m) v /= p->mean_count;
+        if (p->wedge) {
+            // the ensemble of snapshots and mirror images: U, W, P even about
+            // the centreline, V odd
+            std::vector<double> ms(m.size());
+            for (int f = 0; f < 4; ++f)
+                for (int j = 0; j < ny; ++j)
+                    ms[f * ny + j] = 0.5 * (m[f * ny + j] + (f == 1 ? -1.0 : 1.0) * m[f * ny + ny - 1 - j]);
+            m.swap(ms);
+            p->mean_sum_host.assign(m.size(), 0.0);
+            for (size_t i = 0; i < m.size(); ++i) p->mean_sum_host[i] = m[i] * p->mean_count;
+            CUDA_TRY(p, cudaMemcpyAsync(p->mean_sum, p->mean_sum_host.data(), m.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, st));
+        }
         CUDA_TRY(p, cudaMemcpyAsync(p->mean, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         // U and U' rows of the profiles, used by the term combinations
         k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, 1.0,
-                                                      (long long)d.nx * d.nz, d.nu, p->fdw, p->fdl0, ny, p->prof);
+                                                      (long long)d.nx * d.nz, d.nu, p->wedge ? 1 : 0, p->fdw, p->fdl0, ny, p->prof);
         p->launches += 1;
         CUDA_TRY(p, cudaStreamSynchronize(st));
         p->mean_frozen = true;
@@ -494,7 +542,7 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
     }
     {
         StageScope sc(p, GKE_STAGE_COMBINE);
-        const long long ncomb = p->npair * NTERM * (long long)Nk;
+        const long long ncomb = p->npair_tri * NTERM * (long long)Nk;
         if (f32 && p->have_acc && !p->comb_is64) {
             // second batch on the split path: promote the per-pair sums to FP64
             if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, (size_t)ncomb));
@@ -530,7 +578,9 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     const Tiles t = pick_tiles(d.nx, d.nz, p->csz);
     TermArgs a;
     a.fp32 = f32; a.comb64 = p->comb_is64;
-    a.comb = p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32; a.W = p->W; a.spec = p->spec; a.pair_i = p->pair_i; a.npair = p->npair; a.pair_chunk = p->pair_chunk;
+    a.comb = p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32;
+    if (p->wedge) a.comb = p->fold;
+    a.W = p->W; a.spec = p->spec; a.pair_i = p->pair_i; a.npair = p->npair; a.pair_chunk = p->pair_chunk;
     a.ny = d.ny; a.nz = d.nz; a.nx = d.nx;
     a.cw = t.cw_tc;
     a.rz = t.rz_tr;
@@ -549,14 +599,18 @@ static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
     {
         StageScope sc(p, GKE_STAGE_TERMS);
         k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, p->snap_count,
-                                                      (long long)d.nx * d.nz, d.nu, p->fdw, p->fdl0, ny, p->prof);
+                                                      (long long)d.nx * d.nz, d.nu, p->wedge ? 1 : 0, p->fdw, p->fdl0, ny, p->prof);
         p->launches += 1;
+        if (p->wedge) {
+            p->launches += mirror_fold_launch(p->comb_is64, p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32,
+                                              p->pair_i, p->npair, ny, p->Nk, p->fold, st);
+        }
         terms_stage(p, terms_dev);
     }
     {
         StageScope sc(p, GKE_STAGE_STENCIL);
-        p->launches += stencil_launch(d.precision == GKE_PREC_BF16X3, terms_dev, p->spec, p->npair, p->pair_i, ny,
-                                      d.nz, d.nx, d.nu, p->fdw, p->fdl0, p->prof, st);
+        p->launches += stencil_launch(d.precision == GKE_PREC_BF16X3, p->wedge ? 1 : 0, terms_dev, p->spec, p->npair,
+                                      p->pair_i, ny, d.nz, d.nx, d.nu, p->fdw, p->fdl0, p->prof, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     return GKE_OK;
@@ -611,7 +665,7 @@ extern "C" gke_status gke_compute(gke_plan_t p, const void* fields, int nsnap, v
 // ------------------------------------------------------- checkpoint files
 struct CkptHeader {
     char magic[8];
-    int version, nx, nz, ny, precision, have_acc;
+    int version, nx, nz, ny, precision, have_acc, pair_domain;
     double mean_count, snap_count, Lx, Lz, nu;
 };
 
@@ -620,7 +674,7 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     if (!p || !path) return p ? fail(p, GKE_ERR_ARG, "path is NULL") : GKE_ERR_ARG;
     const int ny = p->d.ny;
     const size_t n_mean = 4 * ny, n_stat = (size_t)NSTAT * ny;
-    const size_t n_comb = (size_t)p->npair * NTERM * p->Nk;
+    const size_t n_comb = (size_t)p->npair_tri * NTERM * p->Nk;
     // the stored per-pair sums are FP64; a split plan holding one batch in FP32 promotes first
     if (p->have_acc && !p->comb_is64) {
         if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
@@ -635,9 +689,10 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for writing: ") + path);
         CkptHeader h{};
         memcpy(h.magic, "GKECKPT", 8);
-        h.version = 2; h.nx = p->d.nx; h.nz = p->d.nz; h.ny = ny; h.precision = p->d.precision;
+        h.version = 3; h.nx = p->d.nx; h.nz = p->d.nz; h.ny = ny; h.precision = p->d.precision;
         h.have_acc = p->have_acc; h.mean_count = p->mean_count; h.snap_count = p->snap_count;
         h.Lx = p->d.Lx; h.Lz = p->d.Lz; h.nu = p->d.nu;
+        h.pair_domain = p->d.pair_domain;
         bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
         std::vector<char> buf;
         auto put = [&](const void* dptr, size_t bytes) {
@@ -653,11 +708,12 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for reading: ") + path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != 2) {
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != 3) {
         fclose(fp);
         return fail(p, GKE_ERR_IO, "not a GKE checkpoint");
     }
-    if (h.nx != p->d.nx || h.nz != p->d.nz || h.ny != ny || h.Lx != p->d.Lx || h.Lz != p->d.Lz || h.nu != p->d.nu) {
+    if (h.nx != p->d.nx || h.nz != p->d.nz || h.ny != ny || h.Lx != p->d.Lx || h.Lz != p->d.Lz || h.nu != p->d.nu ||
+        h.pair_domain != p->d.pair_domain) {
         fclose(fp);
         return fail(p, GKE_ERR_ARG, "checkpoint grid does not match the plan");
     }
@@ -709,8 +765,8 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         for (double& v : m) v /= p->mean_count;
         CUDA_TRY(p, cudaMemcpy(p->mean, m.data(), m.size() * 8, cudaMemcpyHostToDevice));
         k_profiles<<<(ny + 127) / 128, 128, 0, p->st>>>(p->mean_sum, p->mean_count, p->stats, 1.0,
-                                                         (long long)p->d.nx * p->d.nz, p->d.nu, p->fdw, p->fdl0, ny,
-                                                         p->prof);
+                                                         (long long)p->d.nx * p->d.nz, p->d.nu, p->wedge ? 1 : 0,
+                                                         p->fdw, p->fdl0, ny, p->prof);
         CUDA_TRY(p, cudaStreamSynchronize(p->st));
         p->mean_frozen = true;
     }

@@ -28,6 +28,8 @@
 // contraction over KC wavenumbers is KC x 64 contiguous values, and so is the
 // transposed partner block (b, a); both are staged through shared memory, then
 // each thread forms the terms of its (pair, k) items; stores are k-contiguous.
+#include <algorithm>
+
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -164,6 +166,44 @@ __global__ void k_promote(const zf* __restrict__ src, long long n, zd* __restric
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         dst[i] = mk((double)src[i].x, (double)src[i].y);
+}
+
+// Mirror sampling (Sec. 3.2 Step 2, Sec. 3.3): the spectra of the wedge pair
+// (i1, i2) averaged with those of the snapshots' mirror images.  A mirror
+// image's term at (i1, i2, r) equals sigma_t times the snapshot's term at
+// (ny-1-i2, ny-1-i1, -r) (combined inversion of y and r), and r -> -r
+// conjugates the spectrum of a real field, so
+//   out[pw][t][k] = (comb[p][t][k] + sigma_t conj(comb[p'][t][k])) / 2,
+// p = (i1, i2), p' = (ny-1-i2, ny-1-i1) in the triangle's pair order.
+__constant__ float c_sigma[NTERM] = {1.f, -1.f, 1.f, -1.f, -1.f, 1.f, 1.f};
+
+template <typename T>
+__global__ void k_mirror_fold(const cplx<T>* __restrict__ comb, const int* __restrict__ pair_w, int ny, int Nk,
+                              cplx<T>* __restrict__ out)
+{
+    const long long row = blockIdx.x;                 // pw * NTERM + t
+    const long long pw = row / NTERM;
+    const int t = (int)(row - pw * NTERM);
+    const int i1 = pair_w[2 * pw], i2 = pair_w[2 * pw + 1];
+    const cplx<T>* a = comb + (pair_index(i1, i2, ny) * NTERM + t) * (long long)Nk;
+    const cplx<T>* b = comb + (pair_index(ny - 1 - i2, ny - 1 - i1, ny) * NTERM + t) * (long long)Nk;
+    cplx<T>* o = out + row * (long long)Nk;
+    const T sg = (T)c_sigma[t], h = (T)0.5;
+    for (int k = blockIdx.y * blockDim.x + threadIdx.x; k < Nk; k += gridDim.y * blockDim.x) {
+        const cplx<T> va = ld_stream(a + k), vb = ld_stream(b + k);
+        st_stream(o + k, mk(h * (va.x + sg * vb.x), h * (va.y - sg * vb.y)));
+    }
+}
+
+int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long nout, int ny, int Nk, void* out,
+                       cudaStream_t st)
+{
+    dim3 g((unsigned)(nout * NTERM), (unsigned)std::min(8, (Nk + 255) / 256));
+    if (c64)
+        k_mirror_fold<double><<<g, 256, 0, st>>>((const zd*)comb, pair_w, ny, Nk, (zd*)out);
+    else
+        k_mirror_fold<float><<<g, 256, 0, st>>>((const zf*)comb, pair_w, ny, Nk, (zf*)out);
+    return 1;
 }
 
 // comb (+)= term spectra of one batch.  fp32_in: raw and arithmetic in FP32;

@@ -276,4 +276,31 @@ __host__ __device__ __forceinline__ long long pair_index(int i1, int i2, int ny)
     return (long long)i1 * ny - (long long)i1 * (i1 - 1) / 2 + (i2 - i1);
 }
 
+__host__ __device__ __forceinline__ long long wedge_index(int i1, int i2, int ny) {
+    // row-major enumeration of the half-channel wedge i1 <= i2, i1 + i2 <= ny - 1
+    return (long long)i1 * ny - (long long)i1 * (i1 - 1) + (i2 - i1);
+}
+
+// Where the value of a term at the ordered pair (a, b) is stored: the pair
+// index, the sign and whether the separation is inverted (r -> -r).  Pairs
+// below the diagonal come from r-inversion, (a, b, r) -> (b, a, -r), parity
+// rho (Sec. 3.3); on the wedge, pairs past the anti-diagonal a + b = ny - 1
+// come from the combined inversion of y and r, (a, b, r) -> (ny-1-b, ny-1-a,
+// -r), parity sigma.
+template <typename T>
+__host__ __device__ __forceinline__ long long stored_pair(int a, int b, int ny, bool wedge, T rho, T sigma,
+                                                          T& sg, bool& flip)
+{
+    sg = (T)1;
+    flip = false;
+    if (a > b) { const int t = a; a = b; b = t; sg *= rho; flip = !flip; }
+    if (wedge && a + b > ny - 1) {
+        const int na = ny - 1 - b, nb = ny - 1 - a;
+        a = na; b = nb;
+        sg *= sigma;
+        flip = !flip;
+    }
+    return wedge ? wedge_index(a, b, ny) : pair_index(a, b, ny);
+}
+
 }  // namespace gke

@@ -42,6 +42,16 @@ void upload_jobs(cudaStream_t st)
     cudaMemcpyToSymbolAsync(c_jobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
 }
 
+// acc += conj(a) b as four fused multiply-adds (written out: the plain
+// expression would contract to a multiply, an FMA and an add per component)
+__device__ __forceinline__ void cmac_conj(zd& acc, const zd a, const zd b)
+{
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+
 #define CT 32       // tile edge
 #define SCH 8       // snapshots per shared-memory chunk
 #define STRIP_MAX 4 // widest remainder done as strips
@@ -84,13 +94,12 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
                     __syncthreads();
                     #pragma unroll
                     for (int ss = 0; ss < SCH; ++ss) {
-                        zd a0 = As[ss][ty], a1 = As[ss][ty + 16];
-                        zd b0 = Bs[ss][tx], b1 = Bs[ss][tx + 16];
-                        // conj(a) * b
-                        acc[0][0].x += a0.x * b0.x + a0.y * b0.y; acc[0][0].y += a0.x * b0.y - a0.y * b0.x;
-                        acc[0][1].x += a0.x * b1.x + a0.y * b1.y; acc[0][1].y += a0.x * b1.y - a0.y * b1.x;
-                        acc[1][0].x += a1.x * b0.x + a1.y * b0.y; acc[1][0].y += a1.x * b0.y - a1.y * b0.x;
-                        acc[1][1].x += a1.x * b1.x + a1.y * b1.y; acc[1][1].y += a1.x * b1.y - a1.y * b1.x;
+                        const zd a[2] = {As[ss][ty], As[ss][ty + 16]};
+                        const zd bb[2] = {Bs[ss][tx], Bs[ss][tx + 16]};
+                        #pragma unroll
+                        for (int i = 0; i < 2; ++i)
+                            #pragma unroll
+                            for (int j = 0; j < 2; ++j) cmac_conj(acc[i][j], a[i], bb[j]);
                     }
                 }
             }
@@ -126,11 +135,7 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
             const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
             const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
             const double c = jd.c[t];
-            for (int s = 0; s < ns; ++s) {
-                const zd a = c * A[(long long)s * ny + y], b = B[(long long)s * ny + yp];
-                acc.x += a.x * b.x + a.y * b.y;
-                acc.y += a.x * b.y - a.y * b.x;
-            }
+            for (int s = 0; s < ns; ++s) cmac_conj(acc, c * A[(long long)s * ny + y], B[(long long)s * ny + yp]);
         }
         raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc;
     }

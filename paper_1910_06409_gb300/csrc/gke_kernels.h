@@ -34,6 +34,8 @@ cudaError_t products_set_attrs(int lim);
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
                    double nu, const double* prof, int beta, void* comb, cudaStream_t st);
 int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st);
+int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long nout, int ny, int Nk, void* out,
+                       cudaStream_t st);
 cudaError_t combine_set_attrs();
 
 // inverse transforms (gke_terms.cu)
@@ -46,15 +48,12 @@ struct TermArgs {
 };
 int terms_launch(const TermArgs& a);
 cudaError_t terms_set_attrs(int lim);
-int stencil_launch(bool fp32, void* terms, float* spec, long long npair, const int* pair_i, int ny, int nz, int nx,
-                   double nu, const double* fdw, const int* fdl0, const double* prof, cudaStream_t st);
+int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
+                   int nz, int nx, double nu, const double* fdw, const int* fdl0, const double* prof,
+                   cudaStream_t st);
 
-__global__ void k_stencil_A(double* terms, long long npair, const int* pair_i, int ny, int nz, int nx,
-                            double nu, const double* fdw, const int* fdl0);
-__global__ void k_stencil_res(double* terms, long long npair, const int* pair_i, int ny, int nz, int nx,
-                              const double* fdw, const int* fdl0);
 __global__ void k_profiles(const double* mean_sum, double mean_count, const double* stats,
-                           double snap_count, long long plane_points, double nu, const double* fdw,
+                           double snap_count, long long plane_points, double nu, int mirror, const double* fdw,
                            const int* fdl0, int ny, double* prof);
 
 }  // namespace gke

@@ -90,6 +90,8 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     if (!desc || !desc->y || !fields || !terms) return fail(GKE_ERR_ARG, "NULL argument");
     const gke_desc& d = *desc;
     if (d.precision != GKE_PREC_F64) return fail(GKE_ERR_UNSUPPORTED, "gke_compute_noalloc runs the FP64 path only");
+    if (d.pair_domain != GKE_DOMAIN_TRIANGLE)
+        return fail(GKE_ERR_UNSUPPORTED, "gke_compute_noalloc computes the triangle pair domain only");
     if (d.nx < 8 || d.nz < 8 || d.nx > 1024 || d.nz > 1024 || (d.nx & (d.nx - 1)) || (d.nz & (d.nz - 1)) ||
         d.ny < 5 || d.ny > 1024 || nsnap < 1)
         return fail(GKE_ERR_ARG, "sizes out of range (nx, nz powers of two in [8, 1024], 5 <= ny <= 1024, nsnap >= 1)");
@@ -174,7 +176,7 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     const zd* f = (const zd*)fields;
     k_mean_accum<<<(4 * ny + 127) / 128, 128, 0, st>>>(f, ns, ny, (long long)Nk, mean_sum);
     k_div<<<(4 * ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, 4 * ny, mean);
-    k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, stats, 1.0, (long long)nx * nz, d.nu, fdw, fdl0,
+    k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, stats, 1.0, (long long)nx * nz, d.nu, 0, fdw, fdl0,
                                                   ny, prof);
     // Step 2: products, contractions, per-pair term spectra
     ProdArgs a;
@@ -187,14 +189,14 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     k_correlate_f64<<<dim3(Nk, NJOB), 256, 0, st>>>(Xop, ns, ny, Nk, raw);
     combine_launch(false, true, raw, ny, nz, nx, d.Lx, d.Lz, d.nu, prof, 0, comb, st);
     // Step 3: profiles, inverse transforms, stencils
-    k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, stats, (double)ns, (long long)nx * nz, d.nu, fdw,
+    k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, stats, (double)ns, (long long)nx * nz, d.nu, 0, fdw,
                                                   fdl0, ny, prof);
     TermArgs t;
     t.fp32 = false; t.comb64 = true; t.comb = comb; t.W = W; t.pair_i = pair_i; t.npair = npair; t.pair_chunk = npair;
     t.ny = ny; t.nz = nz; t.nx = nx; t.cw = cw_tc; t.rz = rz_tr; t.inv_count = 1.0 / ns; t.prof = prof;
     t.tw_x = twx; t.tw_z = twz; t.terms = terms; t.spec = nullptr; t.st = st;
     terms_launch(t);
-    stencil_launch(false, terms, nullptr, npair, pair_i, ny, nz, nx, d.nu, fdw, fdl0, prof, st);
+    stencil_launch(false, 0, terms, nullptr, npair, pair_i, ny, nz, nx, d.nu, fdw, fdl0, prof, st);
     if (profiles) TRY(cudaMemcpyAsync(profiles, prof, GKE_NPROF * ny * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int bad = 0;
     TRY(cudaMemcpyAsync(&bad, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));

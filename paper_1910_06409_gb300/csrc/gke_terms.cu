@@ -308,21 +308,30 @@ cudaError_t terms_set_attrs(int lim)
 // (mz, mx), taken from the stored triangle a <= b, or by r-inversion
 // (Sec. 3.3) with parity sg
 template <typename T>
-__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, int nz, int nx, int mz, int mx,
-                                       T sg)
+__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, bool wedge, int nz, int nx,
+                                       int mz, int mx, T rho, T sigma)
 {
     const long long N = (long long)nz * nx;
-    if (a <= b) return f[pair_index(a, b, ny) * N + (long long)mz * nx + mx];
-    const int mzn = (nz - mz) % nz, mxn = (nx - mx) % nx;
-    return sg * f[pair_index(b, a, ny) * N + (long long)mzn * nx + mxn];
+    T sg;
+    bool flip;
+    const long long q = stored_pair(a, b, ny, wedge, rho, sigma, sg, flip);
+    T v;
+    if (!flip) {
+        v = f[q * N + (long long)mz * nx + mx];
+    } else {
+        const int mzn = (nz - mz) % nz, mxn = (nx - mx) % nx;
+        v = f[q * N + (long long)mzn * nx + mxn];
+    }
+    return sg < (T)0 ? -v : v;          // a sign, not an FP64 multiply
 }
 
 // plain path, pass 1: Phi_y -= 2 nu dA/dr_y, phi -= (nu/2) dA/dY, with
 // dA/dr_y = (d_Y2 - d_Y1) A / 2, dA/dY = (d_Y1 + d_Y2) A (Eq. 10-11); A even
-// under r-inversion.  grid (npair, separation chunks): consecutive CTAs take
-// the same separation chunk of consecutive pairs, so neighbour rows stay in L2.
+// under r-inversion and under the combined inversion.  grid (npair,
+// separation chunks): consecutive CTAs take the same separation chunk of
+// consecutive pairs, so neighbour rows stay in L2.
 __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
-                            int ny, int nz, int nx, double nu, const double* __restrict__ fdw,
+                            int ny, int wedge, int nz, int nx, double nu, const double* __restrict__ fdw,
                             const int* __restrict__ fdl0)
 {
     const long long N = (long long)nz * nx;
@@ -336,17 +345,18 @@ __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const i
     const int a1 = fdl0[i1], a2 = fdl0[i2];
     #pragma unroll
     for (int l = 0; l < 5; ++l) {
-        d1 += fdw[5 * i1 + l] * tri_value(A, a1 + l, i2, ny, nz, nx, mz, mx, 1.0);
-        d2 += fdw[5 * i2 + l] * tri_value(A, i1, a2 + l, ny, nz, nx, mz, mx, 1.0);
+        d1 += fdw[5 * i1 + l] * tri_value(A, a1 + l, i2, ny, wedge, nz, nx, mz, mx, 1.0, 1.0);
+        d2 += fdw[5 * i2 + l] * tri_value(A, i1, a2 + l, ny, wedge, nz, nx, mz, mx, 1.0, 1.0);
     }
     terms[((long long)T_PHIY * npair + p) * N + e] += -2.0 * nu * 0.5 * (d2 - d1);
     terms[((long long)T_PHI * npair + p) * N + e] += -0.5 * nu * (d1 + d2);
 }
 
 // plain path, pass 2: res += dPhi_y/dr_y + dphi/dY by the same stencil;
-// Phi_y odd and phi even under r-inversion.
+// Phi_y odd and phi even under r-inversion, Phi_y even and phi odd under the
+// combined inversion.
 __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
-                              int ny, int nz, int nx, const double* __restrict__ fdw,
+                              int ny, int wedge, int nz, int nx, const double* __restrict__ fdw,
                               const int* __restrict__ fdl0)
 {
     const long long N = (long long)nz * nx;
@@ -362,10 +372,10 @@ __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const
     #pragma unroll
     for (int l = 0; l < 5; ++l) {
         double w1 = fdw[5 * i1 + l], w2 = fdw[5 * i2 + l];
-        y1 += w1 * tri_value(Py, a1 + l, i2, ny, nz, nx, mz, mx, -1.0);
-        y2 += w2 * tri_value(Py, i1, a2 + l, ny, nz, nx, mz, mx, -1.0);
-        h1 += w1 * tri_value(Ph, a1 + l, i2, ny, nz, nx, mz, mx, 1.0);
-        h2 += w2 * tri_value(Ph, i1, a2 + l, ny, nz, nx, mz, mx, 1.0);
+        y1 += w1 * tri_value(Py, a1 + l, i2, ny, wedge, nz, nx, mz, mx, -1.0, 1.0);
+        y2 += w2 * tri_value(Py, i1, a2 + l, ny, wedge, nz, nx, mz, mx, -1.0, 1.0);
+        h1 += w1 * tri_value(Ph, a1 + l, i2, ny, wedge, nz, nx, mz, mx, 1.0, -1.0);
+        h2 += w2 * tri_value(Ph, i1, a2 + l, ny, wedge, nz, nx, mz, mx, 1.0, -1.0);
     }
     terms[((long long)T_RES * npair + p) * N + e] += 0.5 * (y2 - y1) + (h1 + h2);
 }
@@ -431,21 +441,23 @@ __global__ void k_stencil_pairs(const int* __restrict__ pair_i, long long npair,
 constexpr int SPT = 4;   // separations per thread in the split stencils
 
 // the stencil's 10 neighbours of pair (i1, i2): rows (a1 + l, i2) and columns
-// (i1, a2 + l); a neighbour below the diagonal is read from its r-inverted
-// partner (mirrored separation, parity sg).  Resolved once per CTA so the
-// per-separation gathers are branch-free.
+// (i1, a2 + l); a neighbour outside the stored pairs is read from the stored
+// pair that the inversions map it to (stored_pair: sign, inverted
+// separation).  Resolved once per CTA so the per-separation gathers are
+// branch-free.
 struct Nb { const float* base[10]; float sg[10]; int mir[10]; };
 
-__device__ __forceinline__ void make_nb(Nb& nb, const float* f, float parity, int i1, int i2, int a1, int a2, int ny,
-                                        long long N)
+__device__ __forceinline__ void make_nb(Nb& nb, const float* f, float rho, float sigma, int i1, int i2, int a1,
+                                        int a2, int ny, bool wedge, long long N)
 {
     #pragma unroll
     for (int l = 0; l < 10; ++l) {
         const int a = l < 5 ? a1 + l : i1, b = l < 5 ? i2 : a2 + (l - 5);
-        const bool m = a > b;
-        nb.base[l] = f + pair_index(m ? b : a, m ? a : b, ny) * N;
-        nb.sg[l] = m ? parity : 1.f;
-        nb.mir[l] = m;
+        float sg;
+        bool flip;
+        nb.base[l] = f + stored_pair(a, b, ny, wedge, rho, sigma, sg, flip) * N;
+        nb.sg[l] = sg;
+        nb.mir[l] = flip;
     }
 }
 
@@ -454,7 +466,7 @@ __device__ __forceinline__ void make_nb(Nb& nb, const float* f, float parity, in
 // spec[1], spec[2] (spectral parts of Phi_y, phi) receive the FD parts of S.
 // grid (npair, separation chunks of 256 SPT).
 __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spec, long long npair,
-                              const int* __restrict__ pair_i, int ny, int nz, int nx, double nu,
+                              const int* __restrict__ pair_i, int ny, int wedge, int nz, int nx, double nu,
                               const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
     const long long N = (long long)nz * nx;
@@ -466,7 +478,7 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
     const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
     const float nuf = (float)nu;
     Nb nb;
-    make_nb(nb, spec, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
+    make_nb(nb, spec, 1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, wedge, N);
     #pragma unroll
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
@@ -491,7 +503,7 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
 // spectral parts (spec[1] odd, spec[2] even) in FP32 plus the per-pair
 // one-point scalar.
 __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restrict__ spec, long long npair,
-                                const int* __restrict__ pair_i, int ny, int nz, int nx,
+                                const int* __restrict__ pair_i, int ny, int wedge, int nz, int nx,
                                 const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
     const long long N = (long long)nz * nx;
@@ -502,8 +514,8 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
     for (int l = 0; l < 10; ++l) w[l] = sc[p * NSC + l];
     const float o = sc[p * NSC + 12];
     Nb ny_, nh_;
-    make_nb(ny_, spec + (long long)1 * npair * N, -1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
-    make_nb(nh_, spec + (long long)2 * npair * N, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
+    make_nb(ny_, spec + (long long)1 * npair * N, -1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, wedge, N);
+    make_nb(nh_, spec + (long long)2 * npair * N, 1.f, -1.f, i1, i2, fdl0[i1], fdl0[i2], ny, wedge, N);
     #pragma unroll
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
@@ -522,20 +534,21 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
     }
 }
 
-int stencil_launch(bool fp32, void* terms, float* spec, long long npair, const int* pair_i, int ny, int nz, int nx,
-                   double nu, const double* fdw, const int* fdl0, const double* prof, cudaStream_t st)
+int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
+                   int nz, int nx, double nu, const double* fdw, const int* fdl0, const double* prof,
+                   cudaStream_t st)
 {
     const long long N = (long long)nx * nz;
     dim3 gs((unsigned)npair, (unsigned)((N + 255) / 256));
     if (!fp32) {
-        k_stencil_A<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, nz, nx, nu, fdw, fdl0);
-        k_stencil_res<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, nz, nx, fdw, fdl0);
+        k_stencil_A<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, nz, nx, nu, fdw, fdl0);
+        k_stencil_res<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, nz, nx, fdw, fdl0);
     } else {
         float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
         k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
         dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
-        k_stencil_A32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, nz, nx, nu, fdl0, sc);
-        k_stencil_res32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, nz, nx, fdl0, sc);
+        k_stencil_A32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, nz, nx, nu, fdl0, sc);
+        k_stencil_res32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, nz, nx, fdl0, sc);
         return 3;
     }
     return 2;
@@ -546,8 +559,8 @@ int stencil_launch(bool fp32, void* terms, float* spec, long long npair, const i
 // products pass and eps = nu * (Parseval sum) / count.
 __global__ void k_profiles(const double* __restrict__ mean_sum, double mean_count,
                            const double* __restrict__ stats, double snap_count, long long plane_points,
-                           double nu, const double* __restrict__ fdw, const int* __restrict__ fdl0, int ny,
-                           double* __restrict__ prof)
+                           double nu, int mirror, const double* __restrict__ fdw, const int* __restrict__ fdl0,
+                           int ny, double* __restrict__ prof)
 {
     int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (y >= ny) return;
@@ -559,15 +572,23 @@ __global__ void k_profiles(const double* __restrict__ mean_sum, double mean_coun
     prof[PR_W * ny + y] = mean_sum[2 * ny + y] / mean_count;
     prof[PR_P * ny + y] = mean_sum[3 * ny + y] / mean_count;
     // physical-space sums: over snapshots and the nx * nz plane points
+    // with mirror sampling each statistic is the mean over the snapshots and
+    // their mirror images, whose value at y is the snapshot's at ny - 1 - y
+    // with the sign of v applied (odd in v: uv, pv, qv)
+    const int ym = ny - 1 - y;
+    auto st = [&](int s, double parity) {
+        const double a = stats[s * ny + y];
+        return mirror ? 0.5 * (a + parity * stats[s * ny + ym]) : a;
+    };
     const double inv = 1.0 / (snap_count * (double)plane_points);
-    prof[PR_Q * ny + y] = stats[S_Q * ny + y] * inv;
-    prof[PR_UV * ny + y] = stats[S_UV * ny + y] * inv;
-    prof[PR_PV * ny + y] = stats[S_PV * ny + y] * inv;
-    prof[PR_QU * ny + y] = stats[S_QU * ny + y] * inv;
-    prof[PR_QV * ny + y] = stats[S_QV * ny + y] * inv;
-    prof[PR_QW * ny + y] = stats[S_QW * ny + y] * inv;
+    prof[PR_Q * ny + y] = st(S_Q, 1.0) * inv;
+    prof[PR_UV * ny + y] = st(S_UV, -1.0) * inv;
+    prof[PR_PV * ny + y] = st(S_PV, -1.0) * inv;
+    prof[PR_QU * ny + y] = st(S_QU, 1.0) * inv;
+    prof[PR_QV * ny + y] = st(S_QV, -1.0) * inv;
+    prof[PR_QW * ny + y] = st(S_QW, 1.0) * inv;
     // Parseval sums are already plane means: divide by the snapshot count only
-    prof[PR_EPS * ny + y] = nu * stats[S_EPS * ny + y] / snap_count;
+    prof[PR_EPS * ny + y] = nu * st(S_EPS, 1.0) / snap_count;
 }
 
 }  // namespace gke

@@ -34,11 +34,11 @@ def N():
     return native
 
 
-def run_gpu(N, wl, coef, precision=0, calls=None, host=False):
+def run_gpu(N, wl, coef, precision=0, calls=None, host=False, domain=0):
     """All terms on the device through the C ABI; returns (terms, profiles) as numpy."""
     import torch
     y = S.cgl_grid(wl.ny)
-    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, coef.shape[0], precision)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, coef.shape[0], precision, pair_domain=domain)
     tdt = torch.float64 if precision == N.GKE_PREC_F64 else torch.float32    # terms element type
     try:
         npair = N.gke_npair(plan)

@@ -156,10 +156,9 @@ def test_single_mode_second_order(single_mode):
         assert np.abs(c[name[n]]).max() < 1e-13
 
 
-def test_single_mode_terms_and_residual(single_mode):
-    res, cf, g, nu = single_mode
+def closed_terms(cf, g, nu):
+    """The six terms and the Eq. 3 residual of a single-mode case, in closed form."""
     Y1, Y2 = g[0], g[1]
-    t = res["terms"]
     A = cf.ev(cf.A, *g)
     dU = cf.U(Y2) - cf.U(Y1)
     dUp1, dUp2 = cf.U.deriv()(Y1), cf.U.deriv()(Y2)
@@ -170,12 +169,6 @@ def test_single_mode_terms_and_residual(single_mode):
     phi = 2 * cf.ev(cf.P, *g) - 0.5 * nu * (A1 + A2)
     xi = (-2 * cf.ev(cf.Q, *g) * 0.5 * (dUp1 + dUp2) - 2 * cf.ev(cf.R, *g) * (dUp2 - dUp1)
           - 2 * (cf.eps(Y1) + cf.eps(Y2)))
-    _close(t[0], A)
-    _close(t[1], Phix)
-    _close(t[2], Phiy, 1e-10)
-    _close(t[3], Phiz)
-    _close(t[4], phi, 1e-10)
-    _close(t[5], xi)
     # Eq. 3 residual: d_rx Phi_x + d_rz Phi_z + d_ry Phi_y + d_Y phi - xi, all derivatives exact here
     A11 = cf.ev(cf.A, *g, d1=2)
     A22 = cf.ev(cf.A, *g, d2=2)
@@ -185,7 +178,41 @@ def test_single_mode_terms_and_residual(single_mode):
     dPhiy = -0.5 * nu * (A22 - 2 * A12 + A11)
     dphi = 2 * (cf.ev(cf.P, *g, d1=1) + cf.ev(cf.P, *g, d2=1)) - 0.5 * nu * (A11 + 2 * A12 + A22)
     resid = dPhix + dPhiz + dPhiy + dphi - xi
-    _close(t[6], resid, 1e-9)
+    return [A, Phix, Phiy, Phiz, phi, xi, resid]
+
+
+TERM_RTOL = (1e-11, 1e-11, 1e-10, 1e-11, 1e-10, 1e-11, 1e-9)
+
+
+def test_single_mode_terms_and_residual(single_mode):
+    res, cf, g, nu = single_mode
+    for k, want in enumerate(closed_terms(cf, g, nu)):
+        _close(res["terms"][k], want, TERM_RTOL[k])
+
+
+def test_mirror_sampling_single_mode():
+    # Mirror sampling (Sec. 3.2, Step 2) doubles the sample with each
+    # snapshot's image about the centreline.  The image of the single-mode
+    # field has the reflected profiles a_f(-y), v's with its sign changed; the
+    # ensemble mean U = 1 - y^2 is already even, so every term is the average
+    # of the closed forms of the two profile sets.
+    phys, y, (Lx, Lz, nu), cf = single_mode_case()
+    res = oracle.full(phys, y, Lx, Lz, nu, mirror=True)
+
+    def reflect(q):
+        return P(q.coef * (-1.0) ** np.arange(len(q.coef)))
+
+    a_img = [reflect(cf.a[0]), -reflect(cf.a[1]), reflect(cf.a[2]), reflect(cf.a[3])]
+    cf_img = Closed(a_img, cf.ph, cf.k, cf.G2, nu)
+    ns, _, ny, nz, nx = phys.shape
+    g = (y[:, None, None, None], y[None, :, None, None], (np.arange(nx) * Lx / nx)[None, None, None, :],
+         (np.arange(nz) * Lz / nz)[None, None, :, None])
+    for k, (w0, w1) in enumerate(zip(closed_terms(cf, g, nu), closed_terms(cf_img, g, nu))):
+        _close(res["terms"][k], 0.5 * (w0 + w1), TERM_RTOL[k])
+    _close(res["prof"][5], 0.5 * (cf.eps(y) + cf_img.eps(y)))
+    # the plain evaluation differs: the pin has teeth
+    plain = oracle.full(phys, y, Lx, Lz, nu)
+    assert np.abs(plain["terms"][5] - res["terms"][5]).max() > 1e-3 * np.abs(res["terms"][5]).max()
 
 
 # ------------------------------------------------------ triad: third order

@@ -8,7 +8,13 @@
 * r-average: with zero plane-mean fluctuations (the generator's), the mean
   over all separations of any two-point correlation vanishes, so the mean
   over r of <du^2> equals <u_i u_i>(Y1) + <u_i u_i>(Y2);
-* the spot-check entry point reproduces the full evaluation.
+* the spot-check entry point reproduces the full evaluation;
+* mirror sampling (Sec. 3.2 Step 2, Sec. 3.3): with each snapshot's mirror
+  image added, the statistics are symmetric under the combined inversion of
+  y and r, (Y1, Y2, r) -> (2h - Y2, 2h - Y1, -r), with the sign table the
+  paper states: Phi_x, Phi_z and phi change sign, A, Phi_y and xi do not
+  (nor does the residual, a sum of budget terms of one parity); U is even
+  about the centreline and V odd.
 """
 import numpy as np
 import pytest
@@ -76,3 +82,44 @@ def test_points_match_full(case):
     for n, (i1, i2, mz, mx) in enumerate(pts):
         np.testing.assert_allclose(p["comp"][n], r["comp"][:, i1, i2, mz, mx], rtol=1e-12, atol=1e-12)
         np.testing.assert_allclose(p["terms"][n], r["terms"][:6, i1, i2, mz, mx], rtol=1e-12, atol=1e-12)
+
+
+SIGMA = (1, -1, 1, -1, -1, 1, 1)      # A, Phi_x, Phi_y, Phi_z, phi, xi, residual
+
+
+def _combined_inversion(a):
+    """T(-r; ny-1-i2, ny-1-i1) as an array over (i1, i2, m_z, m_x)."""
+    return _neg(np.swapaxes(a[::-1, ::-1], 0, 1))
+
+
+def test_mirror_sampling_symmetries(case):
+    wl, phys, y, r = case
+    m = oracle.full(phys, y, wl.Lx, wl.Lz, wl.nu, mirror=True)
+    for k, sg in enumerate(SIGMA):
+        a = m["terms"][k]
+        assert np.abs(a - sg * _combined_inversion(a)).max() < 1e-10 * np.abs(a).max(), oracle.TERMS[k]
+    prof = m["prof"]
+    assert np.abs(prof[0] - prof[0][::-1]).max() < 1e-14        # U even
+    assert np.abs(prof[1] + prof[1][::-1]).max() < 1e-14        # V odd
+    assert np.abs(prof[5] - prof[5][::-1]).max() < 1e-12 * prof[5].max()
+    # the synthetic sample alone is not symmetric: the check has teeth
+    a = r["terms"][0]
+    assert np.abs(a - _combined_inversion(a)).max() > 1e-3 * np.abs(a).max()
+
+
+def test_mirror_of_mirrored_sample_is_plain(case):
+    # a sample that already holds every snapshot's image is unchanged by mirror sampling
+    wl, phys, y, r = case
+    aug = oracle.mirror_augment(phys)
+    a = oracle.full(aug, y, wl.Lx, wl.Lz, wl.nu)
+    b = oracle.full(aug, y, wl.Lx, wl.Lz, wl.nu, mirror=True)
+    for k in range(len(oracle.TERMS)):
+        assert np.abs(a["terms"][k] - b["terms"][k]).max() <= 1e-12 * np.abs(a["terms"][k]).max()
+
+
+def test_wedge_pairs():
+    for ny in (5, 6, 9, 33):
+        w = oracle.wedge_pairs(ny)
+        assert len(w) == sum(ny - 2 * a for a in range((ny + 1) // 2))
+        assert all(a <= b and a + b <= ny - 1 for a, b in w)
+        assert w == sorted(w)
