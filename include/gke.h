@@ -39,9 +39,18 @@
  *     and r, (Y1, Y2, r) -> (2h - Y2, 2h - Y1, -r), under which Phi_x, Phi_z
  *     and phi change sign and A, Phi_y, xi and the residual do not.
  *   - Separations: index (m_z, m_x) in [0, nz) x [0, nx), FFT order,
- *     r_x = m_x Lx / nx, r_z = m_z Lz / nz (periodic).
+ *     r_x = m_x Lx / nx, r_z = m_z Lz / nz (periodic).  With undersampling
+ *     (Sec. 3.4; desc.under_x / under_z) only the kept indices are stored,
+ *     nrz x nrx of them, in increasing order (gke_separation_labels).  Along
+ *     each direction, with d = min(m, n - m) the distance from r = 0 in grid
+ *     steps and {t1, t2, s1, s2} the option: m is kept when d < t1, or when
+ *     t1 <= d < t2 and d is a multiple of s1, or when d >= t2 and d is a
+ *     multiple of s2.  All four zero means every m (full resolution); e.g.
+ *     {0, 0, 1, 4} keeps every fourth separation.  Undersampling selects
+ *     from the full-resolution result (the transforms and every derivative
+ *     run at full resolution), so the kept values are exact.
  *   - Output terms (double on the FP64 path, float on the split path):
- *       terms[GKE_NTERM][npair][nz][nx]
+ *       terms[GKE_NTERM][npair][nrz][nrx]     (nrz = nz, nrx = nx at full resolution)
  *     in the order GKE_TERM_* below: <du^2>, Phi_x, Phi_y, Phi_z, phi, xi
  *     and the residual of Eq. 3 (div_r Phi + d phi/dY - xi).
  *   - Profiles (double): profiles[GKE_NPROF][ny], order GKE_PROF_*.
@@ -101,6 +110,8 @@ typedef struct {
     int max_snap;          /* largest nsnap of any accumulate call (sizes workspaces)    */
     int precision;         /* GKE_PREC_*                                                 */
     int pair_domain;       /* GKE_DOMAIN_*                                               */
+    int under_x[4];        /* undersampling of r_x {t1, t2, s1, s2}; all 0 = full        */
+    int under_z[4];        /* undersampling of r_z, same rule                            */
 } gke_desc;
 
 /* Create a plan: validates the descriptor, computes the FD weights and
@@ -143,6 +154,9 @@ gke_status gke_pair_labels(gke_plan_t plan, double* Y, double* ry, int* i1, int*
 /* Sizes: number of pairs, and bytes of the terms array (element size 8 on
  * the FP64 path, 4 on the split path).                                       */
 long long gke_npair(gke_plan_t plan);
+/* Kept separations: *nrz, *nrx (either may be NULL), and when mz / mx are
+ * not NULL the kept indices m_z[nrz], m_x[nrx] (host arrays).              */
+gke_status gke_separation_labels(gke_plan_t plan, int* nrz, int* nrx, int* mz, int* mx);
 long long gke_terms_bytes(gke_plan_t plan);
 
 /* Forget all accumulated statistics and the mean.                            */

@@ -25,7 +25,8 @@ GKE_NTERM, GKE_NPROF = len(TERMS), len(PROFILES)
 
 # every symbol include/gke.h declares
 EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_snapshot", "gke_finalize_terms",
-           "gke_compute", "gke_pair_labels", "gke_npair", "gke_terms_bytes", "gke_reset", "gke_checkpoint",
+           "gke_compute", "gke_pair_labels", "gke_npair", "gke_separation_labels", "gke_terms_bytes", "gke_reset",
+           "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy")
 STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
@@ -35,7 +36,8 @@ class gke_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("nz", ctypes.c_int), ("ny", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("nu", ctypes.c_double),
                 ("y", ctypes.POINTER(ctypes.c_double)),
-                ("max_snap", ctypes.c_int), ("precision", ctypes.c_int), ("pair_domain", ctypes.c_int)]
+                ("max_snap", ctypes.c_int), ("precision", ctypes.c_int), ("pair_domain", ctypes.c_int),
+                ("under_x", ctypes.c_int * 4), ("under_z", ctypes.c_int * 4)]
 
 
 class GkeError(RuntimeError):
@@ -65,6 +67,7 @@ def lib():
             "gke_compute": (i, [vp, vp, i, vp, vp]),
             "gke_pair_labels": (i, [vp, vp, vp, vp, vp]),
             "gke_npair": (ctypes.c_longlong, [vp]),
+            "gke_separation_labels": (i, [vp, vp, vp, vp, vp]),
             "gke_terms_bytes": (ctypes.c_longlong, [vp]),
             "gke_reset": (i, [vp]),
             "gke_checkpoint": (i, [vp, cp]),
@@ -106,11 +109,11 @@ def _check(status: int, plan) -> None:
 
 
 def gke_plan(nx, nz, ny, Lx, Lz, nu, y, max_snap, precision=GKE_PREC_F64, stream=None,
-             pair_domain=GKE_DOMAIN_TRIANGLE):
+             pair_domain=GKE_DOMAIN_TRIANGLE, under_x=(0, 0, 0, 0), under_z=(0, 0, 0, 0)):
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), max_snap,
-                    precision, pair_domain)
+                    precision, pair_domain, (ctypes.c_int * 4)(*under_x), (ctypes.c_int * 4)(*under_z))
     out = ctypes.c_void_p()
     st = lib().gke_plan(ctypes.byref(desc), stream, ctypes.byref(out))
     _check(st, None)
@@ -150,6 +153,16 @@ def gke_npair(plan) -> int:
     return lib().gke_npair(plan)
 
 
+def gke_separation_labels(plan):
+    """Kept separation indices (m_z[nrz], m_x[nrx]) as int32 arrays."""
+    import numpy as np
+    nrz, nrx = ctypes.c_int(), ctypes.c_int()
+    _check(lib().gke_separation_labels(plan, ctypes.addressof(nrz), ctypes.addressof(nrx), None, None), plan)
+    mz, mx = np.zeros(nrz.value, dtype=np.int32), np.zeros(nrx.value, dtype=np.int32)
+    _check(lib().gke_separation_labels(plan, None, None, ptr(mz), ptr(mx)), plan)
+    return mz, mx
+
+
 def gke_terms_bytes(plan) -> int:
     return lib().gke_terms_bytes(plan)
 
@@ -186,7 +199,7 @@ def gke_compute_noalloc(nx, nz, ny, Lx, Lz, nu, y, fields, nsnap, terms, profile
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsnap,
-                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE)
+                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE, (ctypes.c_int * 4)(), (ctypes.c_int * 4)())
     st = lib().gke_compute_noalloc(ctypes.byref(desc), ptr(fields), nsnap, ptr(terms), ptr(profiles), stream)
     if st != GKE_OK:
         raise GkeError(st, "gke_compute_noalloc")

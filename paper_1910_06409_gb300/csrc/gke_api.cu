@@ -32,6 +32,10 @@ struct gke_plan_s {
     bool wedge = false;
     void* fold = nullptr;                     // wedge: folded spectra (aliases raw when it fits)
     bool fold_owned = false;
+    // kept separations (undersampling): host lists and the device map
+    std::vector<int> keep_z, keep_x;
+    SepMap sep;
+    int* sep_tab = nullptr;
     // device workspaces; Xop, G, H, raw and W hold complex<TF>, TF = double on
     // the plain path and float on the split path
     void *Xop = nullptr, *G = nullptr, *H = nullptr, *raw = nullptr, *W = nullptr;
@@ -137,6 +141,25 @@ static const long long W_CHUNK_BYTES = 120LL << 20;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
+// separation indices kept along one direction (a-posteriori undersampling,
+// Sec. 3.4): with d = min(m, n - m), keep d < t1, multiples of s1 for
+// t1 <= d < t2 and multiples of s2 from t2 on; {0, 0, 0, 0} keeps all
+static bool under_valid(const int u[4])
+{
+    if (!u[0] && !u[1] && !u[2] && !u[3]) return true;
+    return u[0] >= 0 && u[1] >= u[0] && u[2] >= 1 && u[3] >= 1;
+}
+static std::vector<int> kept_indices(int n, const int u[4])
+{
+    std::vector<int> k;
+    const bool all = !u[0] && !u[1] && !u[2] && !u[3];
+    for (int m = 0; m < n; ++m) {
+        const int d = std::min(m, n - m);
+        if (all || d < u[0] || (d < u[1] ? d % u[2] == 0 : d % u[3] == 0)) k.push_back(m);
+    }
+    return k;
+}
+
 static bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes a;
@@ -210,6 +233,10 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         g_plan_err = "unknown pair_domain";
         return GKE_ERR_ARG;
     }
+    if (!under_valid(d.under_x) || !under_valid(d.under_z)) {
+        g_plan_err = "undersampling {t1, t2, s1, s2} needs 0 <= t1 <= t2, s1 >= 1, s2 >= 1 (or all zero)";
+        return GKE_ERR_ARG;
+    }
     for (int j = 1; j < d.ny; ++j)
         if (!(d.y[j] > d.y[j - 1])) { g_plan_err = "y must be strictly increasing"; return GKE_ERR_ARG; }
     if (d.pair_domain == GKE_DOMAIN_WEDGE) {
@@ -239,6 +266,13 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     }
     const int ny = d.ny, ns = d.max_snap, Nk = p->Nk;
     const size_t plane = (size_t)d.nz * p->nxh;
+    p->keep_z = kept_indices(d.nz, d.under_z);
+    p->keep_x = kept_indices(d.nx, d.under_x);
+    const int nrz = (int)p->keep_z.size(), nrx = (int)p->keep_x.size();
+    const bool under = nrz < d.nz || nrx < d.nx;
+    p->sep = full_sep(d.nz, d.nx);
+    p->sep.nrz = nrz;
+    p->sep.nrx = nrx;
 
     auto bail = [&](gke_status s, const std::string& m) { g_plan_err = m; gke_destroy(p); return s; };
     cudaError_t e;
@@ -271,7 +305,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     if (f32) {
         ALLOC(p->comb32, (size_t)p->npair_tri * NTERM * Nk);
         // spectral parts of A, Phi_y, phi, then 13 per-pair stencil scalars
-        ALLOC(p->spec, (size_t)3 * p->npair * d.nx * d.nz + 13 * (size_t)p->npair);
+        ALLOC(p->spec, (size_t)3 * p->npair * nrx * nrz + 13 * (size_t)p->npair);
         p->tsz = sizeof(float);
     } else {
         ALLOC(p->comb, (size_t)p->npair_tri * NTERM * Nk);
@@ -281,8 +315,9 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     // pairs per inverse-transform chunk: the chunk's W scratch (W_CHUNK_BYTES)
     // mostly stays in L2 between the two passes, and each launch still fills
     // the GPU
-    p->pair_chunk = std::max<long long>(1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * Nk * p->csz)));
-    ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * Nk * p->csz);
+    p->pair_chunk = std::max<long long>(
+        1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * nrz * p->nxh * p->csz)));
+    ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * nrz * p->nxh * p->csz);
     ALLOC(p->tw_xd, d.nx);
     ALLOC(p->tw_zd, d.nz);
     ALLOC(p->tw_xf, d.nx);
@@ -296,6 +331,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOC(p->fdl0, ny);
     ALLOC(p->pair_i, 2 * p->npair);
     ALLOC(p->nonfinite, 1);
+    if (under) ALLOC(p->sep_tab, (size_t)d.nz + d.nx + nrz + nrx);
     {
         const Tiles tl = pick_tiles(d.nx, d.nz, p->csz);
         size_t a1 = (size_t)6 * ny * std::max((d.nz + tl.rz_rp - 1) / tl.rz_rp, (d.nz + 3) / 4);
@@ -329,6 +365,23 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     for (int i1 = 0; i1 < ny; ++i1)
         for (int i2 = i1; i2 < (p->wedge ? ny - i1 : ny); ++i2) { pi[2 * q] = i1; pi[2 * q + 1] = i2; ++q; }
     cudaStream_t st = p->st;
+    std::vector<int> stab;
+    if (under) {
+        // [zpos (nz) | xpos (nx) | negz (nrz) | negx (nrx)]
+        std::vector<int> zpos(d.nz, -1), xpos(d.nx, -1);
+        for (int i = 0; i < nrz; ++i) zpos[p->keep_z[i]] = i;
+        for (int i = 0; i < nrx; ++i) xpos[p->keep_x[i]] = i;
+        stab.insert(stab.end(), zpos.begin(), zpos.end());
+        stab.insert(stab.end(), xpos.begin(), xpos.end());
+        for (int i = 0; i < nrz; ++i) stab.push_back(zpos[(d.nz - p->keep_z[i]) % d.nz]);
+        for (int i = 0; i < nrx; ++i) stab.push_back(xpos[(d.nx - p->keep_x[i]) % d.nx]);
+        p->sep.zpos = p->sep_tab;
+        p->sep.xpos = p->sep_tab + d.nz;
+        p->sep.negz = p->sep_tab + d.nz + d.nx;
+        p->sep.negx = p->sep_tab + d.nz + d.nx + nrz;
+        if ((e = cudaMemcpyAsync(p->sep_tab, stab.data(), stab.size() * sizeof(int), cudaMemcpyHostToDevice, st)))
+            return bail(GKE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
     if ((e = cudaMemcpyAsync(p->tw_xd, twx.data(), twx.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->tw_zd, twz.data(), twz.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->tw_xf, twxf.data(), twxf.size() * sizeof(zf), cudaMemcpyHostToDevice, st)) ||
@@ -369,7 +422,7 @@ extern "C" void gke_destroy(gke_plan_t p)
     if (p->fold_owned) cudaFree(p->fold);
     void* ptrs[] = {p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
-                    p->fdl0, p->pair_i, p->nonfinite, p->part};
+                    p->fdl0, p->pair_i, p->nonfinite, p->part, p->sep_tab};
     for (void* q : ptrs) if (q) cudaFree(q);
     split_free(p->split);
     for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
@@ -414,7 +467,17 @@ extern "C" const char* gke_last_error(gke_plan_t p) { return p ? p->err.c_str() 
 extern "C" long long gke_npair(gke_plan_t p) { return p ? p->npair : -1; }
 extern "C" long long gke_terms_bytes(gke_plan_t p)
 {
-    return p ? (long long)NTERM * p->npair * p->d.nx * p->d.nz * (long long)p->tsz : -1;
+    return p ? (long long)NTERM * p->npair * p->sep.nrx * p->sep.nrz * (long long)p->tsz : -1;
+}
+
+extern "C" gke_status gke_separation_labels(gke_plan_t p, int* nrz, int* nrx, int* mz, int* mx)
+{
+    if (!p) return GKE_ERR_ARG;
+    if (nrz) *nrz = p->sep.nrz;
+    if (nrx) *nrx = p->sep.nrx;
+    if (mz) std::copy(p->keep_z.begin(), p->keep_z.end(), mz);
+    if (mx) std::copy(p->keep_x.begin(), p->keep_x.end(), mx);
+    return GKE_OK;
 }
 
 extern "C" gke_status gke_pair_labels(gke_plan_t p, double* Y, double* ry, int* i1, int* i2)
@@ -587,7 +650,7 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     a.inv_count = 1.0 / p->snap_count; a.prof = p->prof;
     a.tw_x = f32 ? (const void*)p->tw_xf : (const void*)p->tw_xd;
     a.tw_z = f32 ? (const void*)p->tw_zf : (const void*)p->tw_zd;
-    a.terms = terms_dev; a.st = p->st;
+    a.terms = terms_dev; a.sep = p->sep; a.st = p->st;
     p->launches += terms_launch(a);
 }
 
@@ -610,7 +673,7 @@ static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
     {
         StageScope sc(p, GKE_STAGE_STENCIL);
         p->launches += stencil_launch(d.precision == GKE_PREC_BF16X3, p->wedge ? 1 : 0, terms_dev, p->spec, p->npair,
-                                      p->pair_i, ny, d.nz, d.nx, d.nu, p->fdw, p->fdl0, p->prof, st);
+                                      p->pair_i, ny, p->sep, d.nu, p->fdw, p->fdl0, p->prof, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     return GKE_OK;

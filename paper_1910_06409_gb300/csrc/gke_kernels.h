@@ -38,18 +38,42 @@ int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long 
                        cudaStream_t st);
 cudaError_t combine_set_attrs();
 
+// Separations kept in the output (a-posteriori undersampling, Sec. 3.4):
+// nrz rows and nrx columns of the nz x nx separation grid.  NULL tables mean
+// full resolution.
+struct SepMap {
+    int nz, nx, nrz, nrx;
+    const int* zpos;      // [nz]: kept row of separation index m_z, or -1
+    const int* xpos;      // [nx]: kept column of m_x, or -1
+    const int* negz;      // [nrz]: kept row of -r_z (the kept set is symmetric)
+    const int* negx;      // [nrx]: kept column of -r_x
+    __device__ __forceinline__ int zrow(int z) const { return zpos ? zpos[z] : z; }
+    __device__ __forceinline__ int xcol(int x) const { return xpos ? xpos[x] : x; }
+    __device__ __forceinline__ int zneg(int zr) const { return negz ? negz[zr] : (nz - zr) % nz; }
+    __device__ __forceinline__ int xneg(int xr) const { return negx ? negx[xr] : (nx - xr) % nx; }
+};
+
+inline SepMap full_sep(int nz, int nx)
+{
+    SepMap m;
+    m.nz = m.nrz = nz;
+    m.nx = m.nrx = nx;
+    m.zpos = m.xpos = m.negz = m.negx = nullptr;
+    return m;
+}
+
 // inverse transforms (gke_terms.cu)
 struct TermArgs {
     bool fp32;            // split path: FP32 transforms and FP32 terms
     bool comb64;          // comb holds complex128 (else complex64)
     const void* comb; void* W; const int* pair_i; long long npair, pair_chunk;
     int ny, nz, nx, cw, rz; double inv_count; const double* prof; const void* tw_x; const void* tw_z;
-    void* terms; float* spec; cudaStream_t st;
+    void* terms; float* spec; SepMap sep; cudaStream_t st;
 };
 int terms_launch(const TermArgs& a);
 cudaError_t terms_set_attrs(int lim);
 int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
-                   int nz, int nx, double nu, const double* fdw, const int* fdl0, const double* prof,
+                   const SepMap& sep, double nu, const double* fdw, const int* fdl0, const double* prof,
                    cudaStream_t st);
 
 __global__ void k_profiles(const double* mean_sum, double mean_count, const double* stats,

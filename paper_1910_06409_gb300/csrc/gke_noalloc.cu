@@ -92,6 +92,9 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     if (d.precision != GKE_PREC_F64) return fail(GKE_ERR_UNSUPPORTED, "gke_compute_noalloc runs the FP64 path only");
     if (d.pair_domain != GKE_DOMAIN_TRIANGLE)
         return fail(GKE_ERR_UNSUPPORTED, "gke_compute_noalloc computes the triangle pair domain only");
+    for (int i = 0; i < 4; ++i)
+        if (d.under_x[i] || d.under_z[i])
+            return fail(GKE_ERR_UNSUPPORTED, "gke_compute_noalloc writes full-resolution separations only");
     if (d.nx < 8 || d.nz < 8 || d.nx > 1024 || d.nz > 1024 || (d.nx & (d.nx - 1)) || (d.nz & (d.nz - 1)) ||
         d.ny < 5 || d.ny > 1024 || nsnap < 1)
         return fail(GKE_ERR_ARG, "sizes out of range (nx, nz powers of two in [8, 1024], 5 <= ny <= 1024, nsnap >= 1)");
@@ -194,9 +197,9 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     TermArgs t;
     t.fp32 = false; t.comb64 = true; t.comb = comb; t.W = W; t.pair_i = pair_i; t.npair = npair; t.pair_chunk = npair;
     t.ny = ny; t.nz = nz; t.nx = nx; t.cw = cw_tc; t.rz = rz_tr; t.inv_count = 1.0 / ns; t.prof = prof;
-    t.tw_x = twx; t.tw_z = twz; t.terms = terms; t.spec = nullptr; t.st = st;
+    t.tw_x = twx; t.tw_z = twz; t.terms = terms; t.spec = nullptr; t.sep = full_sep(nz, nx); t.st = st;
     terms_launch(t);
-    stencil_launch(false, 0, terms, nullptr, npair, pair_i, ny, nz, nx, d.nu, fdw, fdl0, prof, st);
+    stencil_launch(false, 0, terms, nullptr, npair, pair_i, ny, full_sep(nz, nx), d.nu, fdw, fdl0, prof, st);
     if (profiles) TRY(cudaMemcpyAsync(profiles, prof, GKE_NPROF * ny * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int bad = 0;
     TRY(cudaMemcpyAsync(&bad, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -29,7 +29,8 @@ namespace gke {
 // complex.
 template <typename TF, typename TB>
 __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pair0, int nz, int nx, int CW,
-                                double inv_count, const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ W)
+                                double inv_count, const cplx<TF>* __restrict__ tw_z, SepMap sm,
+                                cplx<TF>* __restrict__ W)
 {
     typedef cplx<TF> C;
     extern __shared__ __align__(16) unsigned char sh_raw_tc[];
@@ -52,10 +53,11 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
         b0[c * nz + kz_i] = v;
     }
     const C* res = fft_block<TF, true>(b0, b1, nz, CW, lg, stw);
-    C* dst = W + (pl * NTERM + q) * (long long)nz * nxh;
+    C* dst = W + (pl * NTERM + q) * (long long)sm.nrz * nxh;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
         const int c = t % CW, z = t / CW, kx_i = kx0 + c;
-        if (kx_i < nxh) dst[(long long)z * nxh + kx_i] = res[c * nz + z];
+        const int zr = sm.zrow(z);
+        if (kx_i < nxh && zr >= 0) dst[(long long)zr * nxh + kx_i] = res[c * nz + z];
     }
 }
 
@@ -64,7 +66,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
 template <typename TF, typename TB, int N1, int N2>
 __global__ void __launch_bounds__(256)
 k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, int CW, double inv_count,
-                  const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ W)
+                  const cplx<TF>* __restrict__ tw_z, SepMap sm, cplx<TF>* __restrict__ W)
 {
     typedef cplx<TF> C;
     constexpr int N = N1 * N2;
@@ -91,9 +93,12 @@ k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, i
     __syncthreads();
     fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
     if (kx < nxh) {
-        C* dst = W + (pl * NTERM + q) * (long long)N * nxh;
+        C* dst = W + (pl * NTERM + q) * (long long)sm.nrz * nxh;
         #pragma unroll
-        for (int m = 0; m < N1; ++m) dst[(long long)(lane + N2 * m) * nxh + kx] = v[m];
+        for (int m = 0; m < N1; ++m) {
+            const int zr = sm.zrow(lane + N2 * m);
+            if (zr >= 0) dst[(long long)zr * nxh + kx] = v[m];
+        }
     }
 }
 
@@ -127,8 +132,8 @@ __device__ __forceinline__ void onepoint(const double* __restrict__ pr, int ny, 
 // shared memory (1 + 8 RZ) nx complex.
 template <typename TF, typename TO>
 __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
-                                long long npair, int ny, int nz, int nx, int RZ,
-                                const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x,
+                                long long npair, int ny, int nx, int RZ,
+                                const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x, SepMap sm,
                                 TO* __restrict__ terms, float* __restrict__ spec)
 {
     typedef cplx<TF> C;
@@ -138,6 +143,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
     C* b1 = b0 + RZ * 4 * nx;
     __shared__ TF s_one[NTERM];
     const int nxh = nx / 2 + 1, lg = ilog2(nx);
+    const int nz = sm.nrz;                 // rows kept (all nz at full resolution)
     const int z0 = blockIdx.x * RZ;
     const int nrow = min(RZ, nz - z0);
     const long long pl = blockIdx.y, p = pair0 + pl;
@@ -163,12 +169,14 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
         b0[(r * 4 + j) * nx + k] = mk(A.x - B.y, A.y + B.x);
     }
     const C* sh = fft_block<TF, true>(b0, b1, nx, 4 * nrow, lg, stw);
-    const long long N = (long long)nz * nx;
+    const long long N = (long long)nz * sm.nrx;
     for (int t = threadIdx.x; t < nrow * NTERM * nx; t += blockDim.x) {
         int r = t / (NTERM * nx), rem = t - r * NTERM * nx, q = rem / nx, x = rem - q * nx;
+        const int xr = sm.xcol(x);
+        if (xr < 0) continue;
         C v = sh[(r * 4 + (q >> 1)) * nx + x];
         const TF sp = (q & 1) ? v.y : v.x;
-        const long long e = (long long)(z0 + r) * nx + x;
+        const long long e = (long long)(z0 + r) * sm.nrx + xr;
         terms[((long long)q * npair + p) * N + e] = (TO)(sp + s_one[q]);
         if (spec != nullptr) {
             const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
@@ -182,7 +190,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
 template <typename TF, typename TO, int N1, int N2>
 __global__ void __launch_bounds__(256)
 k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
-                  int ny, int nz, int RZ, const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x,
+                  int ny, int RZ, const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x, SepMap sm,
                   TO* __restrict__ terms, float* __restrict__ spec)
 {
     typedef cplx<TF> C;
@@ -192,6 +200,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
     C* xs = stw + N;
     __shared__ TF s_one[NTERM];
     const int lane = threadIdx.x % N2, r = threadIdx.x / N2;
+    const int nz = sm.nrz;                 // rows kept (all nz at full resolution)
     const int z = blockIdx.x * RZ + r;
     const bool live = z < nz;
     const long long pl = blockIdx.y, p = pair0 + pl;
@@ -202,7 +211,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
         onepoint(prof, ny, i1, i2, one);
         for (int t = 0; t < NTERM; ++t) s_one[t] = (TF)one[t];
     }
-    const long long NN = (long long)nz * N;
+    const long long NN = (long long)nz * sm.nrx;
     C* xr = xs + r * N1 * (N2 + 1);
     for (int jq = 0; jq < 4; ++jq) {
         const int ta = 2 * jq, tb = 2 * jq + 1;
@@ -223,7 +232,9 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
         if (live) {
             #pragma unroll
             for (int m = 0; m < N1; ++m) {
-                const long long e = (long long)z * N + lane + N2 * m;
+                const int xr = sm.xcol(lane + N2 * m);
+                if (xr < 0) continue;
+                const long long e = (long long)z * sm.nrx + xr;
                 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int q = 2 * jq + h;
@@ -252,22 +263,22 @@ int terms_launch_t(const TermArgs& a)
             constexpr int CWR = 16;
             k_terms_colpass_r<TF, TB, 16, 16><<<dim3((nxh + CWR - 1) / CWR, NTERM, (unsigned)np), CWR * 16,
                                                 (256 + 16 * (16 * CWR + 1)) * sizeof(C), a.st>>>(
-                (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, (C*)a.W);
+                (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
         } else {
             k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
                                       (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
-                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, (C*)a.W);
+                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
         }
         if (a.nx == 256) {
             constexpr int RZR = 4;
-            k_terms_rowpass_r<TF, TO, 16, 16><<<dim3((a.nz + RZR - 1) / RZR, (unsigned)np), RZR * 16,
+            k_terms_rowpass_r<TF, TO, 16, 16><<<dim3((a.sep.nrz + RZR - 1) / RZR, (unsigned)np), RZR * 16,
                                                 (256 + RZR * 16 * 17) * sizeof(C), a.st>>>(
-                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, RZR, a.prof, (const C*)a.tw_x, (TO*)a.terms,
+                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.prof, (const C*)a.tw_x, a.sep, (TO*)a.terms,
                 a.spec);
         } else {
-            k_terms_rowpass<TF, TO><<<dim3((a.nz + a.rz - 1) / a.rz, (unsigned)np), 256,
+            k_terms_rowpass<TF, TO><<<dim3((a.sep.nrz + a.rz - 1) / a.rz, (unsigned)np), 256,
                                       (1 + 8 * a.rz) * a.nx * sizeof(C), a.st>>>(
-                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nz, a.nx, a.rz, a.prof, (const C*)a.tw_x,
+                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nx, a.rz, a.prof, (const C*)a.tw_x, a.sep,
                 (TO*)a.terms, a.spec);
         }
         launches += 2;
@@ -308,21 +319,17 @@ cudaError_t terms_set_attrs(int lim)
 // (mz, mx), taken from the stored triangle a <= b, or by r-inversion
 // (Sec. 3.3) with parity sg
 template <typename T>
-__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, bool wedge, int nz, int nx,
-                                       int mz, int mx, T rho, T sigma)
+__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, bool wedge, const SepMap& sm,
+                                       int zr, int xr, int rho, int sigma)
 {
-    const long long N = (long long)nz * nx;
-    T sg;
+    const long long N = (long long)sm.nrz * sm.nrx;
+    int sg;                             // integer parities: no FP64 work per gather
     bool flip;
     const long long q = stored_pair(a, b, ny, wedge, rho, sigma, sg, flip);
     T v;
-    if (!flip) {
-        v = f[q * N + (long long)mz * nx + mx];
-    } else {
-        const int mzn = (nz - mz) % nz, mxn = (nx - mx) % nx;
-        v = f[q * N + (long long)mzn * nx + mxn];
-    }
-    return sg < (T)0 ? -v : v;          // a sign, not an FP64 multiply
+    if (!flip) v = f[q * N + (long long)zr * sm.nrx + xr];
+    else v = f[q * N + (long long)sm.zneg(zr) * sm.nrx + sm.xneg(xr)];
+    return sg < 0 ? -v : v;             // a sign, not an FP64 multiply
 }
 
 // plain path, pass 1: Phi_y -= 2 nu dA/dr_y, phi -= (nu/2) dA/dY, with
@@ -331,22 +338,22 @@ __device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, in
 // separation chunks): consecutive CTAs take the same separation chunk of
 // consecutive pairs, so neighbour rows stay in L2.
 __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
-                            int ny, int wedge, int nz, int nx, double nu, const double* __restrict__ fdw,
+                            int ny, int wedge, SepMap sm, double nu, const double* __restrict__ fdw,
                             const int* __restrict__ fdl0)
 {
-    const long long N = (long long)nz * nx;
+    const long long N = (long long)sm.nrz * sm.nrx;
     const long long p = blockIdx.x;
     const long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= N) return;
-    const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
+    const int mz = (int)(e / sm.nrx), mx = (int)(e - (long long)mz * sm.nrx);
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
     const double* A = terms + (long long)T_A * npair * N;
     double d1 = 0.0, d2 = 0.0;
     const int a1 = fdl0[i1], a2 = fdl0[i2];
     #pragma unroll
     for (int l = 0; l < 5; ++l) {
-        d1 += fdw[5 * i1 + l] * tri_value(A, a1 + l, i2, ny, wedge, nz, nx, mz, mx, 1.0, 1.0);
-        d2 += fdw[5 * i2 + l] * tri_value(A, i1, a2 + l, ny, wedge, nz, nx, mz, mx, 1.0, 1.0);
+        d1 += fdw[5 * i1 + l] * tri_value(A, a1 + l, i2, ny, wedge, sm, mz, mx, 1, 1);
+        d2 += fdw[5 * i2 + l] * tri_value(A, i1, a2 + l, ny, wedge, sm, mz, mx, 1, 1);
     }
     terms[((long long)T_PHIY * npair + p) * N + e] += -2.0 * nu * 0.5 * (d2 - d1);
     terms[((long long)T_PHI * npair + p) * N + e] += -0.5 * nu * (d1 + d2);
@@ -356,14 +363,14 @@ __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const i
 // Phi_y odd and phi even under r-inversion, Phi_y even and phi odd under the
 // combined inversion.
 __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
-                              int ny, int wedge, int nz, int nx, const double* __restrict__ fdw,
+                              int ny, int wedge, SepMap sm, const double* __restrict__ fdw,
                               const int* __restrict__ fdl0)
 {
-    const long long N = (long long)nz * nx;
+    const long long N = (long long)sm.nrz * sm.nrx;
     const long long p = blockIdx.x;
     const long long e = (long long)blockIdx.y * blockDim.x + threadIdx.x;
     if (e >= N) return;
-    const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
+    const int mz = (int)(e / sm.nrx), mx = (int)(e - (long long)mz * sm.nrx);
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
     const double* Py = terms + (long long)T_PHIY * npair * N;
     const double* Ph = terms + (long long)T_PHI * npair * N;
@@ -372,10 +379,10 @@ __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const
     #pragma unroll
     for (int l = 0; l < 5; ++l) {
         double w1 = fdw[5 * i1 + l], w2 = fdw[5 * i2 + l];
-        y1 += w1 * tri_value(Py, a1 + l, i2, ny, wedge, nz, nx, mz, mx, -1.0, 1.0);
-        y2 += w2 * tri_value(Py, i1, a2 + l, ny, wedge, nz, nx, mz, mx, -1.0, 1.0);
-        h1 += w1 * tri_value(Ph, a1 + l, i2, ny, wedge, nz, nx, mz, mx, 1.0, -1.0);
-        h2 += w2 * tri_value(Ph, i1, a2 + l, ny, wedge, nz, nx, mz, mx, 1.0, -1.0);
+        y1 += w1 * tri_value(Py, a1 + l, i2, ny, wedge, sm, mz, mx, -1, 1);
+        y2 += w2 * tri_value(Py, i1, a2 + l, ny, wedge, sm, mz, mx, -1, 1);
+        h1 += w1 * tri_value(Ph, a1 + l, i2, ny, wedge, sm, mz, mx, 1, -1);
+        h2 += w2 * tri_value(Ph, i1, a2 + l, ny, wedge, sm, mz, mx, 1, -1);
     }
     terms[((long long)T_RES * npair + p) * N + e] += 0.5 * (y2 - y1) + (h1 + h2);
 }
@@ -466,10 +473,10 @@ __device__ __forceinline__ void make_nb(Nb& nb, const float* f, float rho, float
 // spec[1], spec[2] (spectral parts of Phi_y, phi) receive the FD parts of S.
 // grid (npair, separation chunks of 256 SPT).
 __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spec, long long npair,
-                              const int* __restrict__ pair_i, int ny, int wedge, int nz, int nx, double nu,
+                              const int* __restrict__ pair_i, int ny, int wedge, SepMap sm, double nu,
                               const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
-    const long long N = (long long)nz * nx;
+    const long long N = (long long)sm.nrz * sm.nrx;
     const long long p = blockIdx.x;
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
     float w[10];
@@ -483,8 +490,8 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
         if (e >= N) return;
-        const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
-        const long long en = (long long)((nz - mz) % nz) * nx + (nx - mx) % nx;
+        const int mz = (int)(e / sm.nrx), mx = (int)(e - (long long)mz * sm.nrx);
+        const long long en = (long long)sm.zneg(mz) * sm.nrx + sm.xneg(mx);
         float d1 = 0.f, d2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
@@ -503,10 +510,10 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
 // spectral parts (spec[1] odd, spec[2] even) in FP32 plus the per-pair
 // one-point scalar.
 __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restrict__ spec, long long npair,
-                                const int* __restrict__ pair_i, int ny, int wedge, int nz, int nx,
+                                const int* __restrict__ pair_i, int ny, int wedge, SepMap sm,
                                 const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
-    const long long N = (long long)nz * nx;
+    const long long N = (long long)sm.nrz * sm.nrx;
     const long long p = blockIdx.x;
     const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
     float w[10];
@@ -520,8 +527,8 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
         if (e >= N) return;
-        const int mz = (int)(e / nx), mx = (int)(e - (long long)mz * nx);
-        const long long en = (long long)((nz - mz) % nz) * nx + (nx - mx) % nx;
+        const int mz = (int)(e / sm.nrx), mx = (int)(e - (long long)mz * sm.nrx);
+        const long long en = (long long)sm.zneg(mz) * sm.nrx + sm.xneg(mx);
         float y1 = 0.f, y2 = 0.f, h1 = 0.f, h2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
@@ -535,20 +542,20 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
 }
 
 int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
-                   int nz, int nx, double nu, const double* fdw, const int* fdl0, const double* prof,
+                   const SepMap& sm, double nu, const double* fdw, const int* fdl0, const double* prof,
                    cudaStream_t st)
 {
-    const long long N = (long long)nx * nz;
+    const long long N = (long long)sm.nrz * sm.nrx;
     dim3 gs((unsigned)npair, (unsigned)((N + 255) / 256));
     if (!fp32) {
-        k_stencil_A<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, nz, nx, nu, fdw, fdl0);
-        k_stencil_res<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, nz, nx, fdw, fdl0);
+        k_stencil_A<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, sm, nu, fdw, fdl0);
+        k_stencil_res<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, sm, fdw, fdl0);
     } else {
         float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
         k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
         dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
-        k_stencil_A32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, nz, nx, nu, fdl0, sc);
-        k_stencil_res32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, nz, nx, fdl0, sc);
+        k_stencil_A32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, sm, nu, fdl0, sc);
+        k_stencil_res32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, sm, fdl0, sc);
         return 3;
     }
     return 2;
