@@ -40,6 +40,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 FMA rate: the nominal 1.25 TFLOP/s of GB300 over 152 SMs at the 2070 MHz
 # maximum clock is 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM.
 FP64_FLOP_PER_CLK_SM = 4.0
+FP32_FLOP_PER_CLK_SM = 256.0
 N_SM = 152
 
 
@@ -104,7 +105,14 @@ def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
     cm = correlator_cmac(wl, ns)
     ms = stage_ms.get("correlate", 0.0)
     if ms > 0:
-        if f32:
+        if precision == "f32":
+            flops = 8.0 * cm
+            peak = N_SM * FP32_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            out["correlate"] = {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
+                                "unit": "TFLOP/s", "flops": flops, "launch_ms": ms,
+                                "traffic": NCU_TRAFFIC_GB.get("correlate"),
+                                "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x max SM clock"}
+        elif f32:
             flops = 48.0 * cm                      # 6 BF16 slice products x 8 real flops per complex MAC
             peak = pk["bf16_tflops"]
             out["correlate"] = {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
@@ -250,7 +258,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl")
     wl = S.WORKLOADS[args.workload]
     ns = wl.nsnap
-    prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3}[args.precision]
+    prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3, "f32": N.GKE_PREC_F32}[args.precision]
     coef = S.coefficients(wl)
     in_bytes = coef.nbytes
     stream = torch.cuda.current_stream()
@@ -321,9 +329,10 @@ def run_ours(args, world, rank, local):
     N.gke_destroy(plan)
 
     # split-BF16 path on the same inputs: throughput, speed-up and per-term error vs the FP64 GPU path
-    split = None
+    split = f32v = None
     if args.precision == "f64" and not args.no_split:
-        split = run_split_beside(args, wl, ns, f_dev, terms, ms, barrier, world)
+        split = run_split_beside(args, wl, ns, f_dev, terms, ms, barrier, world, "bf16x3")
+        f32v = run_split_beside(args, wl, ns, f_dev, terms, ms, barrier, world, "f32")
 
     # rooflines: every stage against its bound, the dominant stage reported as "roofline"
     pk, pk_kind = peaks()
@@ -341,11 +350,11 @@ def run_ours(args, world, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64" if args.precision == "f64" else "bf16x3/f32",
+                "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16x3/f32", "f32": "f32"}[args.precision],
                 "data": "synthetic", "config": config_of(wl, args.precision), "parallelism": f"replicas{world}",
                 "stage_ms": stage_ms,
                 "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
-                "stage_roofline": rl, "split_bf16x3": split,
+                "stage_roofline": rl, "split_bf16x3": split, "fp32_cuda_cores": f32v,
                 "cpu_baseline": cpu}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -353,8 +362,8 @@ def run_ours(args, world, rank, local):
         dist.destroy_process_group()
 
 
-def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world):
-    """Time the split-BF16 path on the FP64 run's inputs and compare its terms.
+def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world, precision):
+    """Time the split-BF16 (or FP32) path on the FP64 run's inputs and compare its terms.
 
     Error per term: max |split - f64| / max |f64| over all pairs and
     separations, against the FP64 GPU path (itself within 1e-12 of the
@@ -362,7 +371,8 @@ def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world):
     import torch
     import paper_1910_06409_gb300._native as N
     stream = torch.cuda.current_stream()
-    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), ns, N.GKE_PREC_BF16X3,
+    prec = {"bf16x3": N.GKE_PREC_BF16X3, "f32": N.GKE_PREC_F32}[precision]
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), ns, prec,
                       stream=stream.cuda_stream)
     npair = N.gke_npair(plan)
     t32 = torch.empty_like(terms64, dtype=torch.float32)
@@ -398,7 +408,7 @@ def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world):
         err[name] = diff / scale if scale > 0 else diff
     del t32
     pk, pk_kind = peaks()
-    rl = stage_rooflines(wl, ns, "bf16x3", stage_ms, pk, pk_kind)
+    rl = stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind)
     return {"value": world * npair * ns / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
             "speedup_vs_f64": ms64 / ms, "max_rel_err": err, "tolerance": 1e-6,
             "within_tolerance": all(e <= 1e-6 for e in err.values()),
@@ -415,7 +425,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--precision", choices=("f64", "bf16x3"), default="f64")
+    ap.add_argument("--precision", choices=("f64", "bf16x3", "f32"), default="f64")
     ap.add_argument("--workload", default=S.RETAU200.name, choices=sorted(S.WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -49,7 +49,7 @@
  *     {0, 0, 1, 4} keeps every fourth separation.  Undersampling selects
  *     from the full-resolution result (the transforms and every derivative
  *     run at full resolution), so the kept values are exact.
- *   - Output terms (double on the FP64 path, float on the split path):
+ *   - Output terms (double on the FP64 path, float on the FP32 and split paths):
  *       terms[GKE_NTERM][npair][nrz][nrx]     (nrz = nz, nrx = nx at full resolution)
  *     in the order GKE_TERM_* below: <du^2>, Phi_x, Phi_y, Phi_z, phi, xi
  *     and the residual of Eq. 3 (div_r Phi + d phi/dY - xi).
@@ -91,8 +91,9 @@ typedef enum {
     GKE_ERR_UNSUPPORTED = -7   /* grid size or option not supported by this build    */
 } gke_status;
 
-enum { GKE_PREC_F64 = 0,       /* plain FP64 correlator (DFMA)                        */
-       GKE_PREC_BF16X3 = 1 };  /* split-BF16 correlator on the tensor cores           */
+enum { GKE_PREC_F64 = 0,       /* plain FP64 path (DFMA)                              */
+       GKE_PREC_BF16X3 = 1,    /* split-BF16 correlator on the tensor cores, FP32 rest */
+       GKE_PREC_F32 = 2 };     /* FP32 correlator on the CUDA cores (FFMA), FP32 rest  */
 
 enum { GKE_DOMAIN_TRIANGLE = 0,  /* all pairs i1 <= i2                                  */
        GKE_DOMAIN_WEDGE = 1 };   /* y-inversion mirror sampling, half-channel wedge     */
@@ -138,7 +139,7 @@ gke_status gke_accumulate_snapshot(gke_plan_t plan, const void* fields, int nsna
 
 /* Step 3 (Sec. 3.2): write all terms for every pair and separation and,
  * if profiles != NULL, the profiles.  terms holds double on the FP64 path
- * (GKE_PREC_F64) and float on the split path (GKE_PREC_BF16X3).  GKE_ERR_STATE without samples;
+ * (GKE_PREC_F64) and float otherwise (GKE_PREC_BF16X3, GKE_PREC_F32).  GKE_ERR_STATE without samples;
  * GKE_ERR_NONFINITE if any accumulated input held a NaN or Inf (outputs are
  * then undefined).  May be called again; accumulators are left unchanged.  */
 gke_status gke_finalize_terms(gke_plan_t plan, void* terms, double* profiles);
@@ -152,7 +153,7 @@ gke_status gke_compute(gke_plan_t plan, const void* fields, int nsnap, void* ter
 gke_status gke_pair_labels(gke_plan_t plan, double* Y, double* ry, int* i1, int* i2);
 
 /* Sizes: number of pairs, and bytes of the terms array (element size 8 on
- * the FP64 path, 4 on the split path).                                       */
+ * the FP64 path, 4 otherwise).                                               */
 long long gke_npair(gke_plan_t plan);
 /* Kept separations: *nrz, *nrx (either may be NULL), and when mz / mx are
  * not NULL the kept indices m_z[nrz], m_x[nrx] (host arrays).              */

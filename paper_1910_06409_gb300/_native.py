@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgke.so")
 GKE_OK = 0
 STATUS = {0: "GKE_OK", -1: "GKE_ERR_ARG", -2: "GKE_ERR_STATE", -3: "GKE_ERR_OOM", -4: "GKE_ERR_CUDA",
           -5: "GKE_ERR_NONFINITE", -6: "GKE_ERR_IO", -7: "GKE_ERR_UNSUPPORTED"}
-GKE_PREC_F64, GKE_PREC_BF16X3 = 0, 1
+GKE_PREC_F64, GKE_PREC_BF16X3, GKE_PREC_F32 = 0, 1, 2
 GKE_DOMAIN_TRIANGLE, GKE_DOMAIN_WEDGE = 0, 1
 TERMS = ("A", "Phi_x", "Phi_y", "Phi_z", "phi", "xi", "residual")
 PROFILES = ("U", "V", "W", "P", "dUdy", "eps")

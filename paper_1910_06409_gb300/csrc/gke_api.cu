@@ -225,7 +225,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         g_plan_err = "nx and nz must be powers of two in this build";
         return GKE_ERR_UNSUPPORTED;
     }
-    if (d.precision != GKE_PREC_F64 && d.precision != GKE_PREC_BF16X3) {
+    if (d.precision != GKE_PREC_F64 && d.precision != GKE_PREC_BF16X3 && d.precision != GKE_PREC_F32) {
         g_plan_err = "unknown precision";
         return GKE_ERR_ARG;
     }
@@ -282,7 +282,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         if (e != cudaSuccess) return bail(GKE_ERR_OOM, std::string("cudaMalloc " #ptr ": ") +  \
                                                            cudaGetErrorString(e));             \
     } while (0)
-    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    const bool f32 = (d.precision != GKE_PREC_F64);
     p->csz = f32 ? sizeof(zf) : sizeof(zd);
 #define ALLOCB(ptr, bytes)                                                                          \
     do {                                                                                            \
@@ -541,7 +541,7 @@ extern "C" gke_status gke_set_mean(gke_plan_t p, const double* mean)
 static void products_stage(gke_plan_t p, const zd* f, int ns)
 {
     const gke_desc& d = p->d;
-    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    const bool f32 = (d.precision != GKE_PREC_F64);
     const Tiles t = pick_tiles(d.nx, d.nz, p->csz);
     ProdArgs a;
     a.fields = f; a.ns = ns; a.ny = d.ny; a.nz = d.nz; a.nx = d.nx; a.nxh = p->nxh; a.Nk = p->Nk;
@@ -586,15 +586,15 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
         CUDA_TRY(p, cudaStreamSynchronize(st));
         p->mean_frozen = true;
     }
-    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    const bool f32 = (d.precision != GKE_PREC_F64);
     {
         StageScope sc(p, GKE_STAGE_PRODUCTS);
         products_stage(p, f, ns);
     }
     {
         StageScope sc(p, GKE_STAGE_CORRELATE);
-        if (!f32) {
-            k_correlate_f64<<<dim3(Nk, NJOB), 256, 0, st>>>((const zd*)p->Xop, ns, ny, Nk, (zd*)p->raw);
+        if (d.precision != GKE_PREC_BF16X3) {
+            correlate_launch(f32, p->Xop, ns, ny, Nk, p->raw, st);
             p->launches += 1;
         } else {
             int nl = 0;
@@ -637,7 +637,7 @@ extern "C" gke_status gke_accumulate_snapshot(gke_plan_t p, const void* fields, 
 static void terms_stage(gke_plan_t p, void* terms_dev)
 {
     const gke_desc& d = p->d;
-    const bool f32 = (d.precision == GKE_PREC_BF16X3);
+    const bool f32 = (d.precision != GKE_PREC_F64);
     const Tiles t = pick_tiles(d.nx, d.nz, p->csz);
     TermArgs a;
     a.fp32 = f32; a.comb64 = p->comb_is64;
@@ -672,7 +672,7 @@ static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
     }
     {
         StageScope sc(p, GKE_STAGE_STENCIL);
-        p->launches += stencil_launch(d.precision == GKE_PREC_BF16X3, p->wedge ? 1 : 0, terms_dev, p->spec, p->npair,
+        p->launches += stencil_launch(d.precision != GKE_PREC_F64, p->wedge ? 1 : 0, terms_dev, p->spec, p->npair,
                                       p->pair_i, ny, p->sep, d.nu, p->fdw, p->fdl0, p->prof, st);
     }
     CUDA_TRY(p, cudaGetLastError());

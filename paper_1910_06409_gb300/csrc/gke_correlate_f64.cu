@@ -1,4 +1,4 @@
-// gke_correlate_f64.cu -- plain FP64 correlator.
+// gke_correlate_f64.cu -- CUDA-core correlator, FP64 (plain path) and FP32.
 //
 // For every wavenumber k the paper's Parseval step (Sec. 3.1, Eq. 8-9) needs
 // sums over snapshots of conj(a_hat(y, k)) b_hat(y', k) for the field pairs
@@ -12,10 +12,10 @@
 //   Gz  = conj(q) w + 2 [conj(uw) u + conj(vw) v + conj(ww) w]
 // (the y-flux triple terms are QV + X2 and QV - X2, formed later).
 //
-// CTA = one wavenumber and one job; it walks 32 x 32 tiles of (y, y'), each
-// thread holding a 2 x 2 block of complex accumulators, and writes the batch's
+// CTA = one wavenumber and one job; it walks tiles of (y, y'), each thread
+// holding an RB x RB block of complex accumulators, and writes the batch's
 // contraction to raw (8 x 8 pair-block layout, raw_index; D: y <= y' only).
-// DFMA bound.  When ny leaves a thin remainder past the last full tile (the
+// FP64: DFMA bound.  FP32: the same sums in FFMA with FP32 accumulation.  When ny leaves a thin remainder past the last full tile (the
 // Chebyshev grids ny = 32 m + 1 leave one wall row), that remainder is done
 // as row and column strips, one (y, y') per thread, instead of as mostly empty
 // padded tiles (which cost half as much again as the useful work at ny = 129).
@@ -44,7 +44,8 @@ void upload_jobs(cudaStream_t st)
 
 // acc += conj(a) b as four fused multiply-adds (written out: the plain
 // expression would contract to a multiply, an FMA and an add per component)
-__device__ __forceinline__ void cmac_conj(zd& acc, const zd a, const zd b)
+template <typename T>
+__device__ __forceinline__ void cmac_conj(cplx<T>& acc, const cplx<T> a, const cplx<T> b)
 {
     acc.x = fma(a.x, b.x, acc.x);
     acc.x = fma(a.y, b.y, acc.x);
@@ -52,15 +53,19 @@ __device__ __forceinline__ void cmac_conj(zd& acc, const zd a, const zd b)
     acc.y = fma(-a.y, b.x, acc.y);
 }
 
-#define CT 32       // tile edge
 #define SCH 8       // snapshots per shared-memory chunk
 #define STRIP_MAX 4 // widest remainder done as strips
 
+// T = double: RB = 2 (32 x 32 tiles, DFMA bound); T = float: RB = 4 (64 x 64
+// tiles, so each thread does 4 FFMA per shared-memory load)
+template <typename T, int RB>
 __global__ void __launch_bounds__(256)
-k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restrict__ raw)
+k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, cplx<T>* __restrict__ raw)
 {
-    __shared__ zd As[SCH][CT];
-    __shared__ zd Bs[SCH][CT];
+    typedef cplx<T> C;
+    constexpr int CT = 16 * RB;     // tile edge
+    __shared__ C As[SCH][CT];
+    __shared__ C Bs[SCH][CT];
     const int k = blockIdx.x, job = blockIdx.y;
     const bool herm = (job == NJSQ);
     const JobDesc& jd = c_jobs[job];
@@ -71,21 +76,21 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
     for (int tb0 = 0; tb0 < nt; ++tb0) {
         for (int tb1 = herm ? tb0 : 0; tb1 < nt; ++tb1) {
             const int y0 = tb0 * CT, y1 = tb1 * CT;
-            zd acc[2][2];
+            C acc[RB][RB];
             #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < RB; ++a)
                 #pragma unroll
-                for (int b = 0; b < 2; ++b) acc[a][b] = mk(0.0, 0.0);
+                for (int b = 0; b < RB; ++b) acc[a][b] = mk((T)0, (T)0);
             for (int t = 0; t < jd.nterm; ++t) {
-                const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
-                const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
-                const double c = jd.c[t];
+                const C* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+                const C* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+                const T c = (T)jd.c[t];
                 for (int s0 = 0; s0 < ns; s0 += SCH) {
                     __syncthreads();
                     for (int e = threadIdx.x; e < SCH * CT; e += blockDim.x) {
                         int ss = e / CT, yy = e - ss * CT;
                         int s = s0 + ss;
-                        zd va = mk(0.0, 0.0), vb = mk(0.0, 0.0);
+                        C va = mk((T)0, (T)0), vb = mk((T)0, (T)0);
                         if (s < ns && y0 + yy < ny) va = A[(long long)s * ny + y0 + yy];
                         if (s < ns && y1 + yy < ny) vb = B[(long long)s * ny + y1 + yy];
                         As[ss][yy] = c * va;
@@ -94,19 +99,20 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
                     __syncthreads();
                     #pragma unroll
                     for (int ss = 0; ss < SCH; ++ss) {
-                        const zd a[2] = {As[ss][ty], As[ss][ty + 16]};
-                        const zd bb[2] = {Bs[ss][tx], Bs[ss][tx + 16]};
+                        C a[RB], bb[RB];
                         #pragma unroll
-                        for (int i = 0; i < 2; ++i)
+                        for (int i = 0; i < RB; ++i) { a[i] = As[ss][ty + 16 * i]; bb[i] = Bs[ss][tx + 16 * i]; }
+                        #pragma unroll
+                        for (int i = 0; i < RB; ++i)
                             #pragma unroll
-                            for (int j = 0; j < 2; ++j) cmac_conj(acc[i][j], a[i], bb[j]);
+                            for (int j = 0; j < RB; ++j) cmac_conj(acc[i][j], a[i], bb[j]);
                     }
                 }
             }
             #pragma unroll
-            for (int a = 0; a < 2; ++a)
+            for (int a = 0; a < RB; ++a)
                 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
+                for (int b = 0; b < RB; ++b) {
                     int y = y0 + ty + 16 * a, yp = y1 + tx + 16 * b;
                     if (y >= ny || yp >= ny) continue;
                     if (herm && yp < y) continue;
@@ -130,15 +136,23 @@ k_correlate_f64(const zd* __restrict__ Xop, int ns, int ny, int Nk, zd* __restri
             y = f / rem;
             yp = cov + (f - y * rem);
         }
-        zd acc = mk(0.0, 0.0);
+        C acc = mk((T)0, (T)0);
         for (int t = 0; t < jd.nterm; ++t) {
-            const zd* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
-            const zd* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
-            const double c = jd.c[t];
+            const C* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+            const C* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+            const T c = (T)jd.c[t];
             for (int s = 0; s < ns; ++s) cmac_conj(acc, c * A[(long long)s * ny + y], B[(long long)s * ny + yp]);
         }
         raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc;
     }
+}
+
+void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, void* raw, cudaStream_t st)
+{
+    if (fp32)
+        k_correlate<float, 4><<<dim3(Nk, NJOB), 256, 0, st>>>((const zf*)Xop, ns, ny, Nk, (zf*)raw);
+    else
+        k_correlate<double, 2><<<dim3(Nk, NJOB), 256, 0, st>>>((const zd*)Xop, ns, ny, Nk, (zd*)raw);
 }
 
 }  // namespace gke

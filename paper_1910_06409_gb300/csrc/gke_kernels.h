@@ -16,7 +16,7 @@ int combine_kc(bool fp32);
 
 __global__ void k_mean_accum(const zd* fields, int ns, int ny, long long plane, double* mean_sum);
 __global__ void k_reduce_partials(const double* part, int nvals, int nb, double* out);
-__global__ void k_correlate_f64(const zd* Xop, int ns, int ny, int Nk, zd* raw);
+void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, void* raw, cudaStream_t st);
 
 // products stage (gke_products.cu); complex<TF> buffers passed as void*
 struct ProdArgs {

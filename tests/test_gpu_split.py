@@ -83,3 +83,31 @@ def test_split_tiny_vs_oracle(N):
     for t in range(N.GKE_NTERM):
         e = rel_err(got[t], ref["terms"][t][iu])
         assert e <= TOL_SPLIT, (N.TERMS[t], e)
+
+
+# ------------------------------------------------------------ FP32 variant
+# GKE_PREC_F32: the contractions in FP32 on the CUDA cores (FFMA, FP32
+# accumulation over K <= 4 x 32 products), everything after them as on the
+# split path.  Same bar as the split path.
+@pytest.mark.parametrize("shape", [(32, 32, 33, 4), (16, 16, 129, 3), (16, 8, 65, 20), (16, 8, 7, 3)])
+def test_f32_matches_f64(N, shape):
+    nx, nz, ny, ns = shape
+    wl = S.small(nx, nz, ny, ns, wid=90 + ny)
+    coef = S.coefficients(wl)
+    ref, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_F64)
+    got, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_F32)
+    errs = [rel_err(got[t], ref[t]) for t in range(N.GKE_NTERM)]
+    assert max(errs) <= TOL_SPLIT, dict(zip(N.TERMS, errs))
+    assert max(errs) > 0.0
+
+
+def test_f32_tiny_vs_oracle(N):
+    import oracle
+    wl = S.TINY
+    phys = S.physical(wl)
+    ref = oracle.full(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu)
+    got, _ = run_gpu(N, wl, S.to_coefficients(phys), precision=N.GKE_PREC_F32, calls=[3, 1])
+    iu = np.triu_indices(wl.ny)
+    for t in range(N.GKE_NTERM):
+        e = rel_err(got[t], ref["terms"][t][iu])
+        assert e <= TOL_SPLIT, (N.TERMS[t], e)
