@@ -63,7 +63,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
 
 // register-FFT column pass for nz = N1 N2: CTA = CW columns of one term of
 // one pair x N2 lanes (see fft2l)
-template <typename TF, typename TB, int N1, int N2>
+template <typename TF, typename TB, int N1, int N2, bool US>
 __global__ void __launch_bounds__(256)
 k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, int CW, double inv_count,
                   const cplx<TF>* __restrict__ tw_z, SepMap sm, cplx<TF>* __restrict__ W)
@@ -93,10 +93,10 @@ k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, i
     __syncthreads();
     fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
     if (kx < nxh) {
-        C* dst = W + (pl * NTERM + q) * (long long)sm.nrz * nxh;
+        C* dst = W + (pl * NTERM + q) * (long long)(US ? sm.nrz : N) * nxh;
         #pragma unroll
         for (int m = 0; m < N1; ++m) {
-            const int zr = sm.zrow(lane + N2 * m);
+            const int zr = US ? sm.zrow(lane + N2 * m) : lane + N2 * m;
             if (zr >= 0) dst[(long long)zr * nxh + kx] = v[m];
         }
     }
@@ -187,7 +187,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
 
 // register-FFT row pass for nx = N1 N2: CTA = RZ rows of one pair x N2 lanes;
 // the seven terms are transformed as four packed sequences (t0 + i t1, ...)
-template <typename TF, typename TO, int N1, int N2>
+template <typename TF, typename TO, int N1, int N2, bool US>
 __global__ void __launch_bounds__(256)
 k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
                   int ny, int RZ, const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x, SepMap sm,
@@ -201,6 +201,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
     __shared__ TF s_one[NTERM];
     const int lane = threadIdx.x % N2, r = threadIdx.x / N2;
     const int nz = sm.nrz;                 // rows kept (all nz at full resolution)
+    const int nrx = US ? sm.nrx : N;
     const int z = blockIdx.x * RZ + r;
     const bool live = z < nz;
     const long long pl = blockIdx.y, p = pair0 + pl;
@@ -211,7 +212,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
         onepoint(prof, ny, i1, i2, one);
         for (int t = 0; t < NTERM; ++t) s_one[t] = (TF)one[t];
     }
-    const long long NN = (long long)nz * sm.nrx;
+    const long long NN = (long long)nz * nrx;
     C* xr = xs + r * N1 * (N2 + 1);
     for (int jq = 0; jq < 4; ++jq) {
         const int ta = 2 * jq, tb = 2 * jq + 1;
@@ -232,9 +233,9 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
         if (live) {
             #pragma unroll
             for (int m = 0; m < N1; ++m) {
-                const int xr = sm.xcol(lane + N2 * m);
+                const int xr = US ? sm.xcol(lane + N2 * m) : lane + N2 * m;
                 if (xr < 0) continue;
-                const long long e = (long long)z * sm.nrx + xr;
+                const long long e = (long long)z * nrx + xr;
                 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int q = 2 * jq + h;
@@ -256,14 +257,20 @@ int terms_launch_t(const TermArgs& a)
 {
     typedef cplx<TF> C;
     const int nxh = a.nx / 2 + 1;
+    const bool us = a.sep.zpos != nullptr || a.sep.xpos != nullptr;      // undersampled output
     int launches = 0;
     for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk) {
         const long long np = a.pair_chunk < a.npair - p0 ? a.pair_chunk : a.npair - p0;
         if (a.nz == 256) {
             constexpr int CWR = 16;
-            k_terms_colpass_r<TF, TB, 16, 16><<<dim3((nxh + CWR - 1) / CWR, NTERM, (unsigned)np), CWR * 16,
-                                                (256 + 16 * (16 * CWR + 1)) * sizeof(C), a.st>>>(
-                (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
+            const dim3 g((nxh + CWR - 1) / CWR, NTERM, (unsigned)np);
+            const size_t sh = (256 + 16 * (16 * CWR + 1)) * sizeof(C);
+            if (us)
+                k_terms_colpass_r<TF, TB, 16, 16, true><<<g, CWR * 16, sh, a.st>>>(
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
+            else
+                k_terms_colpass_r<TF, TB, 16, 16, false><<<g, CWR * 16, sh, a.st>>>(
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
         } else {
             k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
                                       (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
@@ -271,10 +278,16 @@ int terms_launch_t(const TermArgs& a)
         }
         if (a.nx == 256) {
             constexpr int RZR = 4;
-            k_terms_rowpass_r<TF, TO, 16, 16><<<dim3((a.sep.nrz + RZR - 1) / RZR, (unsigned)np), RZR * 16,
-                                                (256 + RZR * 16 * 17) * sizeof(C), a.st>>>(
-                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.prof, (const C*)a.tw_x, a.sep, (TO*)a.terms,
-                a.spec);
+            const dim3 g((a.sep.nrz + RZR - 1) / RZR, (unsigned)np);
+            const size_t sh = (256 + RZR * 16 * 17) * sizeof(C);
+            if (us)
+                k_terms_rowpass_r<TF, TO, 16, 16, true><<<g, RZR * 16, sh, a.st>>>(
+                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.prof, (const C*)a.tw_x, a.sep, (TO*)a.terms,
+                    a.spec);
+            else
+                k_terms_rowpass_r<TF, TO, 16, 16, false><<<g, RZR * 16, sh, a.st>>>(
+                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.prof, (const C*)a.tw_x, a.sep, (TO*)a.terms,
+                    a.spec);
         } else {
             k_terms_rowpass<TF, TO><<<dim3((a.sep.nrz + a.rz - 1) / a.rz, (unsigned)np), 256,
                                       (1 + 8 * a.rz) * a.nx * sizeof(C), a.st>>>(
@@ -298,11 +311,16 @@ cudaError_t terms_set_attrs(int lim)
     const void* ks[] = {(const void*)k_terms_colpass<double, double>, (const void*)k_terms_rowpass<double, double>,
                         (const void*)k_terms_colpass<float, float>, (const void*)k_terms_colpass<float, double>,
                         (const void*)k_terms_rowpass<float, float>,
-                        (const void*)k_terms_colpass_r<double, double, 16, 16>,
-                        (const void*)k_terms_colpass_r<float, float, 16, 16>,
-                        (const void*)k_terms_colpass_r<float, double, 16, 16>,
-                        (const void*)k_terms_rowpass_r<double, double, 16, 16>,
-                        (const void*)k_terms_rowpass_r<float, float, 16, 16>};
+                        (const void*)k_terms_colpass_r<double, double, 16, 16, false>,
+                        (const void*)k_terms_colpass_r<float, float, 16, 16, false>,
+                        (const void*)k_terms_colpass_r<float, double, 16, 16, false>,
+                        (const void*)k_terms_rowpass_r<double, double, 16, 16, false>,
+                        (const void*)k_terms_rowpass_r<float, float, 16, 16, false>,
+                        (const void*)k_terms_colpass_r<double, double, 16, 16, true>,
+                        (const void*)k_terms_colpass_r<float, float, 16, 16, true>,
+                        (const void*)k_terms_colpass_r<float, double, 16, 16, true>,
+                        (const void*)k_terms_rowpass_r<double, double, 16, 16, true>,
+                        (const void*)k_terms_rowpass_r<float, float, 16, 16, true>};
     cudaError_t e = cudaSuccess;
     for (const void* k : ks) {
         cudaFuncAttributes fa;
@@ -318,18 +336,25 @@ cudaError_t terms_set_attrs(int lim)
 // value of a field at the ordered pair (a, b) and separation index
 // (mz, mx), taken from the stored triangle a <= b, or by r-inversion
 // (Sec. 3.3) with parity sg
-template <typename T>
-__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, bool wedge, const SepMap& sm,
+// v or -v by flipping the sign bit with an integer operation (no FP64 work)
+__device__ __forceinline__ double flip_sign(double v, bool neg)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)neg << 63));
+}
+
+template <bool WEDGE, bool US, typename T>
+__device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, int ny, const SepMap& sm,
                                        int zr, int xr, int rho, int sigma)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
     int sg;                             // integer parities: no FP64 work per gather
     bool flip;
-    const long long q = stored_pair(a, b, ny, wedge, rho, sigma, sg, flip);
+    const long long q = stored_pair(a, b, ny, WEDGE, rho, sigma, sg, flip);
     T v;
     if (!flip) v = f[q * N + (long long)zr * sm.nrx + xr];
-    else v = f[q * N + (long long)sm.zneg(zr) * sm.nrx + sm.xneg(xr)];
-    return sg < 0 ? -v : v;             // a sign, not an FP64 multiply
+    else if (US) v = f[q * N + (long long)sm.negz[zr] * sm.nrx + sm.negx[xr]];
+    else v = f[q * N + (long long)((sm.nz - zr) % sm.nz) * sm.nx + (sm.nx - xr) % sm.nx];
+    return flip_sign(v, sg < 0);
 }
 
 // plain path, pass 1: Phi_y -= 2 nu dA/dr_y, phi -= (nu/2) dA/dY, with
@@ -337,8 +362,9 @@ __device__ __forceinline__ T tri_value(const T* __restrict__ f, int a, int b, in
 // under r-inversion and under the combined inversion.  grid (npair,
 // separation chunks): consecutive CTAs take the same separation chunk of
 // consecutive pairs, so neighbour rows stay in L2.
+template <bool WEDGE, bool US>
 __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
-                            int ny, int wedge, SepMap sm, double nu, const double* __restrict__ fdw,
+                            int ny, SepMap sm, double nu, const double* __restrict__ fdw,
                             const int* __restrict__ fdl0)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
@@ -352,8 +378,8 @@ __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const i
     const int a1 = fdl0[i1], a2 = fdl0[i2];
     #pragma unroll
     for (int l = 0; l < 5; ++l) {
-        d1 += fdw[5 * i1 + l] * tri_value(A, a1 + l, i2, ny, wedge, sm, mz, mx, 1, 1);
-        d2 += fdw[5 * i2 + l] * tri_value(A, i1, a2 + l, ny, wedge, sm, mz, mx, 1, 1);
+        d1 += fdw[5 * i1 + l] * tri_value<WEDGE, US>(A, a1 + l, i2, ny, sm, mz, mx, 1, 1);
+        d2 += fdw[5 * i2 + l] * tri_value<WEDGE, US>(A, i1, a2 + l, ny, sm, mz, mx, 1, 1);
     }
     terms[((long long)T_PHIY * npair + p) * N + e] += -2.0 * nu * 0.5 * (d2 - d1);
     terms[((long long)T_PHI * npair + p) * N + e] += -0.5 * nu * (d1 + d2);
@@ -362,8 +388,9 @@ __global__ void k_stencil_A(double* __restrict__ terms, long long npair, const i
 // plain path, pass 2: res += dPhi_y/dr_y + dphi/dY by the same stencil;
 // Phi_y odd and phi even under r-inversion, Phi_y even and phi odd under the
 // combined inversion.
+template <bool WEDGE, bool US>
 __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const int* __restrict__ pair_i,
-                              int ny, int wedge, SepMap sm, const double* __restrict__ fdw,
+                              int ny, SepMap sm, const double* __restrict__ fdw,
                               const int* __restrict__ fdl0)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
@@ -379,10 +406,10 @@ __global__ void k_stencil_res(double* __restrict__ terms, long long npair, const
     #pragma unroll
     for (int l = 0; l < 5; ++l) {
         double w1 = fdw[5 * i1 + l], w2 = fdw[5 * i2 + l];
-        y1 += w1 * tri_value(Py, a1 + l, i2, ny, wedge, sm, mz, mx, -1, 1);
-        y2 += w2 * tri_value(Py, i1, a2 + l, ny, wedge, sm, mz, mx, -1, 1);
-        h1 += w1 * tri_value(Ph, a1 + l, i2, ny, wedge, sm, mz, mx, 1, -1);
-        h2 += w2 * tri_value(Ph, i1, a2 + l, ny, wedge, sm, mz, mx, 1, -1);
+        y1 += w1 * tri_value<WEDGE, US>(Py, a1 + l, i2, ny, sm, mz, mx, -1, 1);
+        y2 += w2 * tri_value<WEDGE, US>(Py, i1, a2 + l, ny, sm, mz, mx, -1, 1);
+        h1 += w1 * tri_value<WEDGE, US>(Ph, a1 + l, i2, ny, sm, mz, mx, 1, -1);
+        h2 += w2 * tri_value<WEDGE, US>(Ph, i1, a2 + l, ny, sm, mz, mx, 1, -1);
     }
     terms[((long long)T_RES * npair + p) * N + e] += 0.5 * (y2 - y1) + (h1 + h2);
 }
@@ -454,15 +481,16 @@ constexpr int SPT = 4;   // separations per thread in the split stencils
 // branch-free.
 struct Nb { const float* base[10]; float sg[10]; int mir[10]; };
 
+template <bool WEDGE>
 __device__ __forceinline__ void make_nb(Nb& nb, const float* f, float rho, float sigma, int i1, int i2, int a1,
-                                        int a2, int ny, bool wedge, long long N)
+                                        int a2, int ny, long long N)
 {
     #pragma unroll
     for (int l = 0; l < 10; ++l) {
         const int a = l < 5 ? a1 + l : i1, b = l < 5 ? i2 : a2 + (l - 5);
         float sg;
         bool flip;
-        nb.base[l] = f + stored_pair(a, b, ny, wedge, rho, sigma, sg, flip) * N;
+        nb.base[l] = f + stored_pair(a, b, ny, WEDGE, rho, sigma, sg, flip) * N;
         nb.sg[l] = sg;
         nb.mir[l] = flip;
     }
@@ -472,8 +500,9 @@ __device__ __forceinline__ void make_nb(Nb& nb, const float* f, float rho, float
 //   Phi_y += -nu (d_Y2 - d_Y1)(S + A1),  phi += -(nu/2) (d_Y1 + d_Y2)(S + A1);
 // spec[1], spec[2] (spectral parts of Phi_y, phi) receive the FD parts of S.
 // grid (npair, separation chunks of 256 SPT).
+template <bool WEDGE, bool US>
 __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spec, long long npair,
-                              const int* __restrict__ pair_i, int ny, int wedge, SepMap sm, double nu,
+                              const int* __restrict__ pair_i, int ny, SepMap sm, double nu,
                               const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
@@ -485,13 +514,14 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
     const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
     const float nuf = (float)nu;
     Nb nb;
-    make_nb(nb, spec, 1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, wedge, N);
+    make_nb<WEDGE>(nb, spec, 1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
     #pragma unroll
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
         if (e >= N) return;
         const int mz = (int)(e / sm.nrx), mx = (int)(e - (long long)mz * sm.nrx);
-        const long long en = (long long)sm.zneg(mz) * sm.nrx + sm.xneg(mx);
+        const long long en = US ? (long long)sm.negz[mz] * sm.nrx + sm.negx[mx]
+                                : (long long)((sm.nz - mz) % sm.nz) * sm.nx + (sm.nx - mx) % sm.nx;
         float d1 = 0.f, d2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
@@ -509,8 +539,9 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
 // pass 2, FP32: res += (d_Y2 - d_Y1) Phi_y / 2 + (d_Y1 + d_Y2) phi, the
 // spectral parts (spec[1] odd, spec[2] even) in FP32 plus the per-pair
 // one-point scalar.
+template <bool WEDGE, bool US>
 __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restrict__ spec, long long npair,
-                                const int* __restrict__ pair_i, int ny, int wedge, SepMap sm,
+                                const int* __restrict__ pair_i, int ny, SepMap sm,
                                 const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
@@ -521,14 +552,15 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
     for (int l = 0; l < 10; ++l) w[l] = sc[p * NSC + l];
     const float o = sc[p * NSC + 12];
     Nb ny_, nh_;
-    make_nb(ny_, spec + (long long)1 * npair * N, -1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, wedge, N);
-    make_nb(nh_, spec + (long long)2 * npair * N, 1.f, -1.f, i1, i2, fdl0[i1], fdl0[i2], ny, wedge, N);
+    make_nb<WEDGE>(ny_, spec + (long long)1 * npair * N, -1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
+    make_nb<WEDGE>(nh_, spec + (long long)2 * npair * N, 1.f, -1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
     #pragma unroll
     for (int u = 0; u < SPT; ++u) {
         const long long e = ((long long)blockIdx.y * SPT + u) * blockDim.x + threadIdx.x;
         if (e >= N) return;
         const int mz = (int)(e / sm.nrx), mx = (int)(e - (long long)mz * sm.nrx);
-        const long long en = (long long)sm.zneg(mz) * sm.nrx + sm.xneg(mx);
+        const long long en = US ? (long long)sm.negz[mz] * sm.nrx + sm.negx[mx]
+                                : (long long)((sm.nz - mz) % sm.nz) * sm.nx + (sm.nx - mx) % sm.nx;
         float y1 = 0.f, y2 = 0.f, h1 = 0.f, h2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
@@ -541,24 +573,36 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
     }
 }
 
-int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
-                   const SepMap& sm, double nu, const double* fdw, const int* fdl0, const double* prof,
-                   cudaStream_t st)
+template <bool WEDGE, bool US>
+static int stencil_launch_t(bool fp32, void* terms, float* spec, long long npair, const int* pair_i, int ny,
+                            const SepMap& sm, double nu, const double* fdw, const int* fdl0, const double* prof,
+                            cudaStream_t st)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
     dim3 gs((unsigned)npair, (unsigned)((N + 255) / 256));
     if (!fp32) {
-        k_stencil_A<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, sm, nu, fdw, fdl0);
-        k_stencil_res<<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, wedge, sm, fdw, fdl0);
-    } else {
-        float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
-        k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
-        dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
-        k_stencil_A32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, sm, nu, fdl0, sc);
-        k_stencil_res32<<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, wedge, sm, fdl0, sc);
-        return 3;
+        k_stencil_A<WEDGE, US><<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, sm, nu, fdw, fdl0);
+        k_stencil_res<WEDGE, US><<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, sm, fdw, fdl0);
+        return 2;
     }
-    return 2;
+    float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
+    k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
+    dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
+    k_stencil_A32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, nu, fdl0, sc);
+    k_stencil_res32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, fdl0, sc);
+    return 3;
+}
+
+int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
+                   const SepMap& sm, double nu, const double* fdw, const int* fdl0, const double* prof,
+                   cudaStream_t st)
+{
+    const bool us = sm.negz != nullptr;
+    if (wedge)
+        return us ? stencil_launch_t<true, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st)
+                  : stencil_launch_t<true, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st);
+    return us ? stencil_launch_t<false, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st)
+              : stencil_launch_t<false, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st);
 }
 
 // ------------------------------------------- profiles from the raw sums
