@@ -45,10 +45,14 @@
  *     each direction, with d = min(m, n - m) the distance from r = 0 in grid
  *     steps and {t1, t2, s1, s2} the option: m is kept when d < t1, or when
  *     t1 <= d < t2 and d is a multiple of s1, or when d >= t2 and d is a
- *     multiple of s2.  All four zero means every m (full resolution); e.g.
- *     {0, 0, 1, 4} keeps every fourth separation.  Undersampling selects
- *     from the full-resolution result (the transforms and every derivative
- *     run at full resolution), so the kept values are exact.
+ *     multiple of s2 (0 <= t1 <= t2, s2 >= 1, s1 >= 1 when t1 < t2; else
+ *     GKE_ERR_ARG).  All four zero means every m (full resolution); e.g.
+ *     {0, 0, 0, 4} keeps every fourth separation.  Thresholded undersampling
+ *     selects from the full-resolution result, so the kept values are
+ *     exact.  A uniform stride s dividing n in both directions ({0, 0, *, s})
+ *     is computed on the coarse grid instead: the spectra are aliased onto
+ *     it (exact), the wavenumbers run in chunks, and the per-pair sums shrink
+ *     by s_z s_x -- the memory-bounded mode for large grids.
  *   - Output terms (double on the FP64 path, float on the FP32 and split paths):
  *       terms[GKE_NTERM][npair][nrz][nrx]     (nrz = nz, nrx = nx at full resolution)
  *     in the order GKE_TERM_* below: <du^2>, Phi_x, Phi_y, Phi_z, phi, xi

@@ -36,6 +36,16 @@ struct gke_plan_s {
     std::vector<int> keep_z, keep_x;
     SepMap sep;
     int* sep_tab = nullptr;
+    // uniform undersampling by (sz, sx) done by spectral aliasing: the
+    // contractions run in chunks of R kz rows (Kc wavenumbers), each folded
+    // into the FP64 coarse spectra comb[npair][NTERM][nzd][nxd/2+1]
+    bool dec = false;
+    int nzt = 0, nxt = 0;                     // transform sizes of the terms stage (nzd, nxd when dec)
+    int R = 0, Kc = 0;                        // chunk rows and wavenumbers per chunk
+    void* cchunk = nullptr;                   // one chunk's per-pair spectra (triangle)
+    size_t n_acc = 0;                         // elements of the FP64 accumulator comb
+    zd *ttw_xd = nullptr, *ttw_zd = nullptr;  // twiddles of the transform sizes
+    zf *ttw_xf = nullptr, *ttw_zf = nullptr;
     // device workspaces; Xop, G, H, raw and W hold complex<TF>, TF = double on
     // the plain path and float on the split path
     void *Xop = nullptr, *G = nullptr, *H = nullptr, *raw = nullptr, *W = nullptr;
@@ -138,16 +148,27 @@ static void fornberg_d1(const double* x, int n, double z0, double* w)
 static const int EPS_KCHUNK = 16;
 // bytes of inverse-transform scratch per pair chunk
 static const long long W_CHUNK_BYTES = 120LL << 20;
+// bytes of contractions + per-pair spectra of one wavenumber chunk (uniform undersampling)
+static const size_t DEC_CHUNK_BYTES = (size_t)12 << 30;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 
 // separation indices kept along one direction (a-posteriori undersampling,
 // Sec. 3.4): with d = min(m, n - m), keep d < t1, multiples of s1 for
 // t1 <= d < t2 and multiples of s2 from t2 on; {0, 0, 0, 0} keeps all
+// stride s when the option keeps exactly the multiples of s (t2 = 0: every d
+// multiple of s2), else 0; all zero is stride 1
+static int uniform_stride(int n, const int u[4])
+{
+    if (!u[0] && !u[1] && !u[2] && !u[3]) return 1;
+    if (u[0] == 0 && u[1] == 0 && u[3] >= 1 && n % u[3] == 0) return u[3];
+    return 0;
+}
+
 static bool under_valid(const int u[4])
 {
     if (!u[0] && !u[1] && !u[2] && !u[3]) return true;
-    return u[0] >= 0 && u[1] >= u[0] && u[2] >= 1 && u[3] >= 1;
+    return u[0] >= 0 && u[1] >= u[0] && (u[1] == u[0] || u[2] >= 1) && u[3] >= 1;
 }
 static std::vector<int> kept_indices(int n, const int u[4])
 {
@@ -234,7 +255,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         return GKE_ERR_ARG;
     }
     if (!under_valid(d.under_x) || !under_valid(d.under_z)) {
-        g_plan_err = "undersampling {t1, t2, s1, s2} needs 0 <= t1 <= t2, s1 >= 1, s2 >= 1 (or all zero)";
+        g_plan_err = "undersampling {t1, t2, s1, s2} needs 0 <= t1 <= t2, s2 >= 1, s1 >= 1 if t1 < t2 (or all zero)";
         return GKE_ERR_ARG;
     }
     for (int j = 1; j < d.ny; ++j)
@@ -269,10 +290,22 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     p->keep_z = kept_indices(d.nz, d.under_z);
     p->keep_x = kept_indices(d.nx, d.under_x);
     const int nrz = (int)p->keep_z.size(), nrx = (int)p->keep_x.size();
-    const bool under = nrz < d.nz || nrx < d.nx;
+    bool under = nrz < d.nz || nrx < d.nx;
     p->sep = full_sep(d.nz, d.nx);
     p->sep.nrz = nrz;
     p->sep.nrx = nrx;
+    p->nzt = d.nz;
+    p->nxt = d.nx;
+    {
+        const int sz = uniform_stride(d.nz, d.under_z), sx = uniform_stride(d.nx, d.under_x);
+        if (sz && sx && (sz > 1 || sx > 1) && d.nz / sz >= 4 && d.nx / sx >= 4) {
+            p->dec = true;
+            p->nzt = d.nz / sz;
+            p->nxt = d.nx / sx;
+            p->sep = full_sep(p->nzt, p->nxt);     // the coarse grid is stored whole
+            under = false;
+        }
+    }
 
     auto bail = [&](gke_status s, const std::string& m) { g_plan_err = m; gke_destroy(p); return s; };
     cudaError_t e;
@@ -293,7 +326,24 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOCB(p->Xop, (size_t)NFIELD * Nk * ns * ny * p->csz);
     ALLOCB(p->G, (size_t)4 * ny * plane * p->csz);
     ALLOCB(p->H, (size_t)7 * ny * plane * p->csz);
-    const size_t raw_bytes = (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * Nk * p->csz;
+    const size_t raw_per_k = (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * p->csz;
+    if (p->dec) {
+        // chunk rows R: a power of two dividing nzd, at most nzd / 2, with the
+        // chunk's contractions and spectra within DEC_CHUNK_BYTES
+        const size_t per_row = (size_t)p->nxh * (raw_per_k + (size_t)p->npair_tri * NTERM * p->csz);
+        p->R = std::max(1, p->nzt / 2);
+        while (p->R > 1 && (size_t)p->R * per_row > DEC_CHUNK_BYTES) p->R /= 2;
+        p->Kc = p->R * p->nxh;
+        ALLOCB(p->raw, raw_per_k * p->Kc);
+        ALLOCB(p->cchunk, (size_t)p->npair_tri * NTERM * p->Kc * p->csz);
+        p->n_acc = (size_t)p->npair * NTERM * p->nzt * (p->nxt / 2 + 1);
+        ALLOC(p->comb, p->n_acc);
+        p->tsz = f32 ? sizeof(float) : sizeof(double);
+        if (f32) ALLOC(p->spec, (size_t)3 * p->npair * p->nxt * p->nzt + 13 * (size_t)p->npair);
+    } else {
+    p->Kc = Nk;
+    p->n_acc = (size_t)p->npair_tri * NTERM * Nk;
+    const size_t raw_bytes = raw_per_k * Nk;
     ALLOCB(p->raw, raw_bytes);
     if (p->wedge) {
         // the folded spectra of the output pairs (at most complex128) are
@@ -312,16 +362,26 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         p->comb_is64 = true;
         p->tsz = sizeof(double);
     }
+    }
     // pairs per inverse-transform chunk: the chunk's W scratch (W_CHUNK_BYTES)
     // mostly stays in L2 between the two passes, and each launch still fills
     // the GPU
+    const int nxth = p->nxt / 2 + 1, nrzt = p->sep.nrz;
     p->pair_chunk = std::max<long long>(
-        1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * nrz * p->nxh * p->csz)));
-    ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * nrz * p->nxh * p->csz);
+        1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * nrzt * nxth * p->csz)));
+    ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * nrzt * nxth * p->csz);
     ALLOC(p->tw_xd, d.nx);
     ALLOC(p->tw_zd, d.nz);
     ALLOC(p->tw_xf, d.nx);
     ALLOC(p->tw_zf, d.nz);
+    if (p->dec) {
+        ALLOC(p->ttw_xd, p->nxt);
+        ALLOC(p->ttw_zd, p->nzt);
+        ALLOC(p->ttw_xf, p->nxt);
+        ALLOC(p->ttw_zf, p->nzt);
+    } else {
+        p->ttw_xd = p->tw_xd; p->ttw_zd = p->tw_zd; p->ttw_xf = p->tw_xf; p->ttw_zf = p->tw_zf;
+    }
 #undef ALLOCB
     ALLOC(p->mean_sum, 4 * ny);
     ALLOC(p->mean, 4 * ny);
@@ -340,7 +400,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         ALLOC(p->part, p->part_count);
     }
     if (d.precision == GKE_PREC_BF16X3) {
-        gke_status s = split_alloc(p->split, ny, ns, Nk);
+        gke_status s = split_alloc(p->split, ny, ns, p->Kc);
         if (s != GKE_OK) return bail(s, "split workspace allocation failed");
     }
 #undef ALLOC
@@ -382,6 +442,20 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         if ((e = cudaMemcpyAsync(p->sep_tab, stab.data(), stab.size() * sizeof(int), cudaMemcpyHostToDevice, st)))
             return bail(GKE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
     }
+    if (p->dec) {
+        // twiddles of the coarse transforms: every s-th entry of the fine ones
+        const int sx = d.nx / p->nxt, sz = d.nz / p->nzt;
+        std::vector<zd> cx(p->nxt), cz(p->nzt);
+        std::vector<zf> cxf(p->nxt), czf(p->nzt);
+        for (int m = 0; m < p->nxt; ++m) { cx[m] = twx[m * sx]; cxf[m] = twxf[m * sx]; }
+        for (int m = 0; m < p->nzt; ++m) { cz[m] = twz[m * sz]; czf[m] = twzf[m * sz]; }
+        if ((e = cudaMemcpyAsync(p->ttw_xd, cx.data(), cx.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(p->ttw_zd, cz.data(), cz.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(p->ttw_xf, cxf.data(), cxf.size() * sizeof(zf), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(p->ttw_zf, czf.data(), czf.size() * sizeof(zf), cudaMemcpyHostToDevice, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            return bail(GKE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
     if ((e = cudaMemcpyAsync(p->tw_xd, twx.data(), twx.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->tw_zd, twz.data(), twz.size() * sizeof(zd), cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemcpyAsync(p->tw_xf, twxf.data(), twxf.size() * sizeof(zf), cudaMemcpyHostToDevice, st)) ||
@@ -411,7 +485,8 @@ extern "C" gke_status gke_reset(gke_plan_t p)
     p->mean_count = 0.0;
     p->snap_count = 0.0;
     p->mean_frozen = p->have_acc = p->finalized = false;
-    p->comb_is64 = (p->d.precision == GKE_PREC_F64);
+    p->comb_is64 = (p->d.precision == GKE_PREC_F64) || p->dec;
+    if (p->dec) CUDA_TRY(p, cudaMemsetAsync(p->comb, 0, p->n_acc * sizeof(zd), p->st));
     return GKE_OK;
 }
 
@@ -420,6 +495,10 @@ extern "C" void gke_destroy(gke_plan_t p)
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
     if (p->fold_owned) cudaFree(p->fold);
+    if (p->dec) {
+        void* extra[] = {p->cchunk, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
+        for (void* q : extra) if (q) cudaFree(q);
+    }
     void* ptrs[] = {p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
                     p->fdl0, p->pair_i, p->nonfinite, p->part, p->sep_tab};
@@ -591,17 +670,39 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
         StageScope sc(p, GKE_STAGE_PRODUCTS);
         products_stage(p, f, ns);
     }
-    {
+    auto correlate = [&](int k0, int Kc) -> gke_status {
         StageScope sc(p, GKE_STAGE_CORRELATE);
         if (d.precision != GKE_PREC_BF16X3) {
-            correlate_launch(f32, p->Xop, ns, ny, Nk, p->raw, st);
+            correlate_launch(f32, p->Xop, ns, ny, Nk, k0, Kc, p->raw, st);
             p->launches += 1;
-        } else {
-            int nl = 0;
-            gke_status s = split_correlate(p->split, (const zf*)p->Xop, ns, ny, Nk, (zf*)p->raw, st, p->err, &nl);
-            p->launches += nl;
-            if (s != GKE_OK) return s;
+            return GKE_OK;
         }
+        int nl = 0;
+        gke_status s = split_correlate(p->split, (const zf*)p->Xop, ns, ny, Nk, k0, Kc, (zf*)p->raw, st, p->err, &nl);
+        p->launches += nl;
+        return s;
+    };
+    if (p->dec) {
+        // chunks of R kz rows: contractions, per-pair spectra of the chunk, and
+        // their aliasing fold into the FP64 coarse spectra
+        for (int kz0 = 0; kz0 < d.nz; kz0 += p->R) {
+            const int k0 = kz0 * p->nxh;
+            gke_status s = correlate(k0, p->Kc);
+            if (s != GKE_OK) return s;
+            StageScope sc(p, GKE_STAGE_COMBINE);
+            p->launches += combine_launch(f32, !f32, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, k0,
+                                          p->Kc, p->Kc, p->cchunk, st);
+            p->launches += fold_dec_launch(!f32, p->cchunk, p->pair_i, p->npair, p->wedge ? 1 : 0, ny, d.nz, d.nx,
+                                           p->nzt, p->nxt, kz0, p->R, p->comb, st);
+        }
+        CUDA_TRY(p, cudaGetLastError());
+        p->snap_count += ns;
+        p->have_acc = true;
+        return GKE_OK;
+    }
+    {
+        gke_status s = correlate(0, Nk);
+        if (s != GKE_OK) return s;
     }
     {
         StageScope sc(p, GKE_STAGE_COMBINE);
@@ -614,7 +715,7 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
         }
         void* dst = p->comb_is64 ? (void*)p->comb : (void*)p->comb32;
         p->launches += combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof,
-                                      p->have_acc ? 1 : 0, dst, st);
+                                      p->have_acc ? 1 : 0, 0, Nk, Nk, dst, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     p->snap_count += ns;
@@ -638,18 +739,19 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
 {
     const gke_desc& d = p->d;
     const bool f32 = (d.precision != GKE_PREC_F64);
-    const Tiles t = pick_tiles(d.nx, d.nz, p->csz);
+    // transform sizes: the grid, or the coarse grid of uniform undersampling
+    const Tiles t = pick_tiles(p->nxt, p->nzt, p->csz);
     TermArgs a;
     a.fp32 = f32; a.comb64 = p->comb_is64;
     a.comb = p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32;
-    if (p->wedge) a.comb = p->fold;
+    if (p->wedge && !p->dec) a.comb = p->fold;
     a.W = p->W; a.spec = p->spec; a.pair_i = p->pair_i; a.npair = p->npair; a.pair_chunk = p->pair_chunk;
-    a.ny = d.ny; a.nz = d.nz; a.nx = d.nx;
+    a.ny = d.ny; a.nz = p->nzt; a.nx = p->nxt;
     a.cw = t.cw_tc;
     a.rz = t.rz_tr;
     a.inv_count = 1.0 / p->snap_count; a.prof = p->prof;
-    a.tw_x = f32 ? (const void*)p->tw_xf : (const void*)p->tw_xd;
-    a.tw_z = f32 ? (const void*)p->tw_zf : (const void*)p->tw_zd;
+    a.tw_x = f32 ? (const void*)p->ttw_xf : (const void*)p->ttw_xd;
+    a.tw_z = f32 ? (const void*)p->ttw_zf : (const void*)p->ttw_zd;
     a.terms = terms_dev; a.sep = p->sep; a.st = p->st;
     p->launches += terms_launch(a);
 }
@@ -664,7 +766,7 @@ static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
         k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, p->snap_count,
                                                       (long long)d.nx * d.nz, d.nu, p->wedge ? 1 : 0, p->fdw, p->fdl0, ny, p->prof);
         p->launches += 1;
-        if (p->wedge) {
+        if (p->wedge && !p->dec) {
             p->launches += mirror_fold_launch(p->comb_is64, p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32,
                                               p->pair_i, p->npair, ny, p->Nk, p->fold, st);
         }
@@ -728,7 +830,7 @@ extern "C" gke_status gke_compute(gke_plan_t p, const void* fields, int nsnap, v
 // ------------------------------------------------------- checkpoint files
 struct CkptHeader {
     char magic[8];
-    int version, nx, nz, ny, precision, have_acc, pair_domain;
+    int version, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt;
     double mean_count, snap_count, Lx, Lz, nu;
 };
 
@@ -737,7 +839,7 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     if (!p || !path) return p ? fail(p, GKE_ERR_ARG, "path is NULL") : GKE_ERR_ARG;
     const int ny = p->d.ny;
     const size_t n_mean = 4 * ny, n_stat = (size_t)NSTAT * ny;
-    const size_t n_comb = (size_t)p->npair_tri * NTERM * p->Nk;
+    const size_t n_comb = p->n_acc;
     // the stored per-pair sums are FP64; a split plan holding one batch in FP32 promotes first
     if (p->have_acc && !p->comb_is64) {
         if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
@@ -756,6 +858,8 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         h.have_acc = p->have_acc; h.mean_count = p->mean_count; h.snap_count = p->snap_count;
         h.Lx = p->d.Lx; h.Lz = p->d.Lz; h.nu = p->d.nu;
         h.pair_domain = p->d.pair_domain;
+        h.nzt = p->dec ? p->nzt : 0;
+        h.nxt = p->dec ? p->nxt : 0;
         bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
         std::vector<char> buf;
         auto put = [&](const void* dptr, size_t bytes) {
@@ -776,7 +880,7 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         return fail(p, GKE_ERR_IO, "not a GKE checkpoint");
     }
     if (h.nx != p->d.nx || h.nz != p->d.nz || h.ny != ny || h.Lx != p->d.Lx || h.Lz != p->d.Lz || h.nu != p->d.nu ||
-        h.pair_domain != p->d.pair_domain) {
+        h.pair_domain != p->d.pair_domain || h.nzt != (p->dec ? p->nzt : 0) || h.nxt != (p->dec ? p->nxt : 0)) {
         fclose(fp);
         return fail(p, GKE_ERR_ARG, "checkpoint grid does not match the plan");
     }

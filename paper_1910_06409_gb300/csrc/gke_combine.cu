@@ -53,7 +53,8 @@ int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::
 template <typename TI, typename TC, typename TO>
 __global__ void __launch_bounds__(256)
 k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
-          const double* __restrict__ prof, int beta, cplx<TO>* __restrict__ comb)
+          const double* __restrict__ prof, int beta, int kbase, int Kc, long long cstride,
+          cplx<TO>* __restrict__ comb)
 {
     constexpr int KC = CombCfg<TI>::KC;
     typedef cplx<TI> C;
@@ -62,7 +63,9 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
     // stage[slot][q][rr][cc]: slot 2 j = block of job j, 2 j + 1 = partner block
     // (rows y in [8b, 8b+8), columns y' in [8a, 8a+8)); D has no partner slot
     C* stage = (C*)sh_raw_cb;
-    const int nxh = nx / 2 + 1, Nk = nz * nxh;
+    // this launch covers the wavenumbers [kbase, kbase + Kc): raw holds them
+    // (chunk-local index kl), comb rows are cstride long from kl = 0
+    const int nxh = nx / 2 + 1, Nk = Kc;
     const int nblk = (ny + PB - 1) / PB;
     int bt = blockIdx.y, a = 0;
     while (bt >= nblk - a) { bt -= nblk - a; ++a; }
@@ -89,7 +92,7 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
     if (k0 >= Nk) break;
     __syncthreads();
     if (threadIdx.x >= 256 - KC) {
-        const int kk = threadIdx.x - (256 - KC), k = min(k0 + kk, Nk - 1);
+        const int kk = threadIdx.x - (256 - KC), k = kbase + min(k0 + kk, Nk - 1);
         const int kz_i = k / nxh, kx_i = k - kz_i * nxh;
         s_kx[kk] = (TC)(6.283185307179586476925286766559 * signed_bin(kx_i, nx) / Lx);
         s_kz[kk] = (TC)(6.283185307179586476925286766559 * signed_bin(kz_i, nz) / Lz);
@@ -146,15 +149,15 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         T[T_XI] = ((TC)2 * Upm) * S1 - dUp * S2;
         T[T_RES] = kx * mul_i(S4) + kz * mul_i(S6) + ((TC)(-2) * dU * kx) * mul_i(S0)
                  + ((TC)(-4) * nuc * (kx * kx + kz * kz)) * S0 - T[T_XI];
-        cplx<TO>* dst = comb + pair_index(i1, i2, ny) * NTERM * (long long)Nk + k;
+        cplx<TO>* dst = comb + pair_index(i1, i2, ny) * NTERM * cstride + k;
         #pragma unroll
         for (int t = 0; t < NTERM; ++t) {
             cplx<TO> v = mk((TO)T[t].x, (TO)T[t].y);
             if (beta) {
-                v = v + dst[(long long)t * Nk];
-                dst[(long long)t * Nk] = v;
+                v = v + dst[(long long)t * cstride];
+                dst[(long long)t * cstride] = v;
             } else {
-                st_stream(dst + (long long)t * Nk, v);
+                st_stream(dst + (long long)t * cstride, v);
             }
         }
     }
@@ -206,24 +209,109 @@ int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long 
     return 1;
 }
 
+// Uniform undersampling of the separations by s_z x s_x (Sec. 3.4), exact by
+// aliasing: the term at r = (s_z m_z, s_x m_x) is the inverse transform, on
+// the coarse nzd x nxd grid (nzd = nz / s_z, nxd = nx / s_x), of the spectrum
+//   G(kzd, kxd) = sum of F_H(kz, kx) over kz = kzd (mod nzd), kx = kxd (mod nxd),
+// F_H the Hermitian extension of the stored half spectrum (its kx = 0 and
+// kx = nx/2 columns taken as their Hermitian parts, as the full-size inverse
+// transform does).  G is accumulated in FP64 chunk by chunk: the chunk holds
+// the kz rows [kz0, kz0 + R) (R divides nzd, kz0 a multiple of R), so a coarse
+// row kzd receives at most one direct row of the chunk (kz = kzd mod nzd) and
+// one conjugate image row (nz - kz = kzd mod nzd).  A thread owns one coarse
+// bin and gathers both, so the sums are deterministic.  With the wedge the
+// spectra are first averaged with the image pair's (as in k_mirror_fold).
+template <typename TC>
+__global__ void k_fold_dec(const cplx<TC>* __restrict__ cchunk, const int* __restrict__ pair_o, int wedge, int ny,
+                           int nz, int nx, int nzd, int nxd, int kz0, int R, zd* __restrict__ dec)
+{
+    const int nxh = nx / 2 + 1, nxdh = nxd / 2 + 1, Kc = R * nxh;
+    const long long row = blockIdx.x;                 // po * NTERM + t
+    const long long po = row / NTERM;
+    const int t = (int)(row - po * NTERM);
+    const int i1 = pair_o[2 * po], i2 = pair_o[2 * po + 1];
+    const cplx<TC>* a = cchunk + (pair_index(i1, i2, ny) * NTERM + t) * (long long)Kc;
+    const cplx<TC>* b = wedge ? cchunk + (pair_index(ny - 1 - i2, ny - 1 - i1, ny) * NTERM + t) * (long long)Kc
+                              : nullptr;
+    const double sg = c_sigma[t];
+    // term spectrum at chunk row r, column kx (mirror-averaged on the wedge)
+    auto F = [&](int r, int kx) -> zd {
+        const long long kl = (long long)r * nxh + kx;
+        const cplx<TC> va = a[kl];
+        if (!wedge) return mk((double)va.x, (double)va.y);
+        const cplx<TC> vb = b[kl];
+        return mk(0.5 * ((double)va.x + sg * (double)vb.x), 0.5 * ((double)va.y - sg * (double)vb.y));
+    };
+    const int dlo = kz0 % nzd;                        // direct coarse rows: [dlo, dlo + R)
+    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < 2 * R * nxdh; it += gridDim.y * blockDim.x) {
+        const int br = it / nxdh, kxd = it - br * nxdh;
+        int kzd;
+        if (br < R) {
+            kzd = dlo + br;
+        } else {
+            kzd = ((nz - (kz0 + br - R)) % nz) % nzd;
+            if ((kzd - dlo + nzd) % nzd < R) continue;      // handled by the direct-row thread
+        }
+        const int od = (kzd - kz0 % nzd + nzd) % nzd;              // kz0 + od = kzd (mod nzd)
+        const int oi = ((nzd - kzd) % nzd - kz0 % nzd + nzd) % nzd; // kz0 + oi = -kzd (mod nzd)
+        const int rd = od < R ? od : -1, ri = oi < R ? oi : -1;     // chunk rows
+        double ax = 0.0, ay = 0.0;
+        for (int ix = 0; ix < nx / nxd; ++ix) {
+            const int kxf = kxd + ix * nxd;
+            const bool self = (kxf == 0 || 2 * kxf == nx);
+            if (rd >= 0 && 2 * kxf <= nx) {
+                const zd v = F(rd, kxf);
+                const double h = self ? 0.5 : 1.0;
+                ax += h * v.x;
+                ay += h * v.y;
+            }
+            if (ri >= 0 && (self || 2 * kxf > nx)) {
+                const zd v = F(ri, self ? kxf : nx - kxf);
+                const double h = self ? 0.5 : 1.0;
+                ax += h * v.x;
+                ay -= h * v.y;
+            }
+        }
+        zd* o = dec + row * (long long)nzd * nxdh + (long long)kzd * nxdh + kxd;
+        o->x += ax;
+        o->y += ay;
+    }
+}
+
+int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
+                    int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st)
+{
+    const int nxdh = nxd / 2 + 1;
+    dim3 g((unsigned)(nout * NTERM), (unsigned)std::min(16, (2 * R * nxdh + 255) / 256));
+    if (c64)
+        k_fold_dec<double><<<g, 256, 0, st>>>((const zd*)cchunk, pair_o, wedge, ny, nz, nx, nzd, nxd, kz0, R,
+                                              (zd*)dec);
+    else
+        k_fold_dec<float><<<g, 256, 0, st>>>((const zf*)cchunk, pair_o, wedge, ny, nz, nx, nzd, nxd, kz0, R,
+                                             (zd*)dec);
+    return 1;
+}
+
 // comb (+)= term spectra of one batch.  fp32_in: raw and arithmetic in FP32;
 // out64: comb is FP64 (else FP32)
+// wavenumbers [kbase, kbase + Kc) (raw holds that chunk); comb rows of
+// cstride values per (pair, term), chunk-local index kl at offset kl
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
-                   double nu, const double* prof, int beta, void* comb, cudaStream_t st)
+                   double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
+                   cudaStream_t st)
 {
-    const int nxh = nx / 2 + 1, Nk = nz * nxh;
     const int kc = combine_kc(fp32_in) * CHUNKS;
     const int nblk = (ny + PB - 1) / PB;
-    dim3 grid((Nk + kc - 1) / kc, nblk * (nblk + 1) / 2);
+    dim3 grid((Kc + kc - 1) / kc, nblk * (nblk + 1) / 2);
     if (!fp32_in)
         k_combine<double, double, double><<<grid, 256, combine_smem(false), st>>>(
-            (const zd*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, (zd*)comb);
+            (const zd*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, (zd*)comb);
     else if (out64)
         k_combine<float, float, double><<<grid, 256, combine_smem(true), st>>>(
-            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, (zd*)comb);
+            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, (zd*)comb);
     else
         k_combine<float, float, float><<<grid, 256, combine_smem(true), st>>>(
-            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, (zf*)comb);
+            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, (zf*)comb);
     return 1;
 }
 

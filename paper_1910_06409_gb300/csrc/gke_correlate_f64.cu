@@ -12,7 +12,7 @@
 //   Gz  = conj(q) w + 2 [conj(uw) u + conj(vw) v + conj(ww) w]
 // (the y-flux triple terms are QV + X2 and QV - X2, formed later).
 //
-// CTA = one wavenumber and one job; it walks tiles of (y, y'), each thread
+// CTA = one wavenumber of a chunk and one job; it walks tiles of (y, y'), each thread
 // holding an RB x RB block of complex accumulators, and writes the batch's
 // contraction to raw (8 x 8 pair-block layout, raw_index; D: y <= y' only).
 // FP64: DFMA bound.  FP32: the same sums in FFMA with FP32 accumulation.  When ny leaves a thin remainder past the last full tile (the
@@ -60,13 +60,13 @@ __device__ __forceinline__ void cmac_conj(cplx<T>& acc, const cplx<T> a, const c
 // tiles, so each thread does 4 FFMA per shared-memory load)
 template <typename T, int RB>
 __global__ void __launch_bounds__(256)
-k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, cplx<T>* __restrict__ raw)
+k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, cplx<T>* __restrict__ raw)
 {
     typedef cplx<T> C;
     constexpr int CT = 16 * RB;     // tile edge
     __shared__ C As[SCH][CT];
     __shared__ C Bs[SCH][CT];
-    const int k = blockIdx.x, job = blockIdx.y;
+    const int kl = blockIdx.x, k = k0 + kl, job = blockIdx.y;    // chunk-local and global wavenumber
     const bool herm = (job == NJSQ);
     const JobDesc& jd = c_jobs[job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -116,7 +116,7 @@ k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, cplx<T>* __
                     int y = y0 + ty + 16 * a, yp = y1 + tx + 16 * b;
                     if (y >= ny || yp >= ny) continue;
                     if (herm && yp < y) continue;
-                    raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc[a][b];
+                    raw[raw_index(job, kl, y, yp, Kc, (ny + 7) / 8)] = acc[a][b];
                 }
         }
     }
@@ -143,16 +143,17 @@ k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, cplx<T>* __
             const T c = (T)jd.c[t];
             for (int s = 0; s < ns; ++s) cmac_conj(acc, c * A[(long long)s * ny + y], B[(long long)s * ny + yp]);
         }
-        raw[raw_index(job, k, y, yp, Nk, (ny + 7) / 8)] = acc;
+        raw[raw_index(job, kl, y, yp, Kc, (ny + 7) / 8)] = acc;
     }
 }
 
-void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, void* raw, cudaStream_t st)
+// wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
+void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, int k0, int Kc, void* raw, cudaStream_t st)
 {
     if (fp32)
-        k_correlate<float, 4><<<dim3(Nk, NJOB), 256, 0, st>>>((const zf*)Xop, ns, ny, Nk, (zf*)raw);
+        k_correlate<float, 4><<<dim3(Kc, NJOB), 256, 0, st>>>((const zf*)Xop, ns, ny, Nk, k0, Kc, (zf*)raw);
     else
-        k_correlate<double, 2><<<dim3(Nk, NJOB), 256, 0, st>>>((const zd*)Xop, ns, ny, Nk, (zd*)raw);
+        k_correlate<double, 2><<<dim3(Kc, NJOB), 256, 0, st>>>((const zd*)Xop, ns, ny, Nk, k0, Kc, (zd*)raw);
 }
 
 }  // namespace gke

@@ -16,7 +16,7 @@ int combine_kc(bool fp32);
 
 __global__ void k_mean_accum(const zd* fields, int ns, int ny, long long plane, double* mean_sum);
 __global__ void k_reduce_partials(const double* part, int nvals, int nb, double* out);
-void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, void* raw, cudaStream_t st);
+void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, int k0, int Kc, void* raw, cudaStream_t st);
 
 // products stage (gke_products.cu); complex<TF> buffers passed as void*
 struct ProdArgs {
@@ -32,7 +32,10 @@ cudaError_t products_set_attrs(int lim);
 
 // term spectra (gke_combine.cu)
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
-                   double nu, const double* prof, int beta, void* comb, cudaStream_t st);
+                   double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
+                   cudaStream_t st);
+int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
+                    int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st);
 int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st);
 int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long nout, int ny, int Nk, void* out,
                        cudaStream_t st);

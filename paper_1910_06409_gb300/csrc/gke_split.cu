@@ -148,7 +148,7 @@ __device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
 // so each slice goes out as one 16-byte store.
 struct alignas(16) bf16x8 { bf16 v[8]; };
 
-__global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
+__global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
                                bf16* __restrict__ Aop)
 {
     long long b = blockIdx.x;
@@ -165,7 +165,7 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
     for (int e = 0; e < 8; ++e) {
         const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
-        if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k) * ns + s) * ny + y];
+        if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k0 + k) * ns + s) * ny + y];
         split3(sc * v.x, o[0].v[e], o[2].v[e], o[4].v[e]);      // slices of the real part
         split3(sc * v.y, o[1].v[e], o[3].v[e], o[5].v[e]);      // slices of the imaginary part
     }
@@ -175,7 +175,7 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
 }
 
 // Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi | -br
-__global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int Nk, int G, int MT, int cov,
+__global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
                                bf16* __restrict__ Bop)
 {
     long long b = blockIdx.x;
@@ -191,7 +191,7 @@ __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int N
     for (int e = 0; e < 8; ++e) {
         const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
-        if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k) * ns + s) * ny + y];
+        if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k0 + k) * ns + s) * ny + y];
         split3(v.x, br[0].v[e], br[1].v[e], br[2].v[e]);
         split3(v.y, bi[0].v[e], bi[1].v[e], bi[2].v[e]);
         #pragma unroll
@@ -359,10 +359,11 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
 // term of a column-edge entry the factor B[s][y']; where that factor is zero
 // for every snapshot the term is skipped (exact: it adds zeros).  With
 // no-slip walls (u = v = w = 0) only the p-v row survives.
-__global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, int cov, zf* __restrict__ raw)
+__global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, int cov,
+                            zf* __restrict__ raw)
 {
     __shared__ int nz_edge[NFIELD][4];       // field f has a nonzero value on edge row cov + i (i < 4)
-    const int k = blockIdx.x;
+    const int kl = blockIdx.x, k = k0 + kl;
     const int ne = ny - cov;
     for (int i = threadIdx.x; i < NFIELD * 4; i += blockDim.x) nz_edge[i / 4][i % 4] = 0;
     __syncthreads();
@@ -396,7 +397,7 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
                 si = fmaf(ar, b.y, fmaf(-ai, b.x, si));
             }
         }
-        raw[raw_index(job, k, y, yp, Nk, YB)] = mk(sr, si);
+        raw[raw_index(job, kl, y, yp, Kc, YB)] = mk(sr, si);
     }
 }
 
@@ -407,8 +408,10 @@ static void tile_geometry(int ny, int& MT, int& cov)
     else { MT = (ny + TM - 1) / TM; cov = ny; }
 }
 
-gke_status split_alloc(SplitWork& w, int ny, int ns, int Nk)
+// operand slices for Kc wavenumbers (one chunk)
+gke_status split_alloc(SplitWork& w, int ny, int ns, int Kc)
 {
+    const int Nk = Kc;
 
     int MT, cov;
     tile_geometry(ny, MT, cov);
@@ -438,22 +441,24 @@ cudaError_t split_setup(cudaStream_t st)
     return cudaFuncSetAttribute((const void*)k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
 }
 
-gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, zf* raw, cudaStream_t st,
-                           std::string& err, int* launches)
+// wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
+gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, zf* raw,
+                           cudaStream_t st, std::string& err, int* launches)
 {
     int MT, cov;
     tile_geometry(ny, MT, cov);
     const int G = (ns + KS - 1) / KS;
     bf16* Aop = (bf16*)w.ops;
-    bf16* Bop = (bf16*)((char*)w.ops + (size_t)Nk * NFIELD * G * MT * A_STAGE * sizeof(bf16));
+    bf16* Bop = (bf16*)((char*)w.ops + (size_t)Kc * NFIELD * G * MT * A_STAGE * sizeof(bf16));
     *launches = 0;
-    k_split_prep_A<<<(unsigned)((long long)Nk * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Aop);
-    k_split_prep_B<<<(unsigned)((long long)Nk * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, G, MT, cov, Bop);
+    k_split_prep_A<<<(unsigned)((long long)Kc * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov,
+                                                                                    Aop);
+    k_split_prep_B<<<(unsigned)((long long)Kc * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, Bop);
     const long long njt = (long long)NJSQ * MT * MT + MT * (MT + 1) / 2;
-    k_corr_tc<<<(unsigned)(Nk * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Nk, G, MT, ny, cov, raw, w.err);
+    k_corr_tc<<<(unsigned)(Kc * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Kc, G, MT, ny, cov, raw, w.err);
     *launches = 3;
     if (cov < ny) {
-        k_corr_edge<<<Nk, 256, 0, st>>>(Xop, ns, ny, Nk, cov, raw);
+        k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, cov, raw);
         *launches += 1;
     }
     cudaError_t e = cudaGetLastError();

@@ -2,11 +2,14 @@
 
 The paper keeps full resolution below a first threshold of |r|, one level of
 undersampling between two thresholds and a coarser one beyond, and notes that
-undersampling a posteriori loses no accuracy: every transform and derivative
-runs at full resolution and only the stored set shrinks.  So the kept values
-must be bit-identical to the full-resolution output at those separations, and
-within the FP64 bar of the oracle there.  The kept set is computed here from
-the rule documented in include/gke.h, independently of the library's tables.
+undersampling a posteriori loses no accuracy.  Thresholded undersampling
+selects from the full-resolution result, so the kept values must be
+bit-identical to the full-resolution output at those separations.  A uniform
+stride (s | n in both directions) instead aliases the spectra onto the coarse
+grid chunk by chunk and transforms there: the same values up to rounding.
+Both must be within the FP64 bar of the oracle.  The kept set is computed
+here from the rule documented in include/gke.h, independently of the
+library's tables.
 """
 import numpy as np
 import pytest
@@ -54,7 +57,13 @@ def run(N, wl, coef, precision=0, domain=0, ux=(0, 0, 0, 0), uz=(0, 0, 0, 0)):
         N.gke_destroy(plan)
 
 
-CASES = [((3, 6, 2, 4), (2, 5, 3, 5)), ((0, 0, 1, 4), (0, 0, 1, 4)), ((0, 0, 0, 0), (1, 1, 1, 8))]
+def uniform(n, u):
+    """True when the option keeps exactly the multiples of a stride dividing n."""
+    return not any(u) or (u[0] == 0 and u[1] == 0 and u[3] >= 1 and n % u[3] == 0)
+
+
+CASES = [((3, 6, 2, 4), (2, 5, 3, 5)), ((0, 0, 1, 4), (0, 0, 1, 4)), ((0, 0, 0, 0), (1, 1, 1, 8)),
+         ((0, 0, 0, 2), (0, 0, 0, 4)), ((0, 0, 0, 0), (0, 0, 1, 8))]
 
 
 @pytest.mark.parametrize("ux,uz", CASES)
@@ -66,12 +75,87 @@ def test_undersampled_equals_full_resolution_f64(N, ux, uz):
     full, _, _ = run(N, wl, coef)
     got, mz, mx = run(N, wl, coef, ux=ux, uz=uz)
     assert np.array_equal(mz, kept(wl.nz, uz)) and np.array_equal(mx, kept(wl.nx, ux))
-    assert np.array_equal(got, full[:, :, mz][:, :, :, mx])
+    sub = full[:, :, mz][:, :, :, mx]
+    if uniform(wl.nz, uz) and uniform(wl.nx, ux):
+        for t in range(N.GKE_NTERM):
+            assert rel_err(got[t], sub[t]) <= TOL_F64, N.TERMS[t]
+    else:
+        assert np.array_equal(got, sub)
     ref = oracle.full(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu)
     iu = np.triu_indices(wl.ny)
     for t in range(N.GKE_NTERM):
         want = ref["terms"][t][iu][:, mz][:, :, mx]
         assert rel_err(got[t], want) <= TOL_F64, N.TERMS[t]
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_stride_wedge_batches(N, precision):
+    """Uniform strides on the wedge with several batches (the streaming mode):
+    the oracle over snapshots and mirror images, read at the kept separations."""
+    import oracle
+    wl = S.small(32, 16, 17, 4, wid=83)
+    phys = S.physical(wl)
+    coef = S.to_coefficients(phys)
+    ux, uz = (0, 0, 0, 4), (0, 0, 0, 2)
+    import torch
+    y = S.cgl_grid(wl.ny)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 2, precision,
+                      pair_domain=N.GKE_DOMAIN_WEDGE, under_x=ux, under_z=uz)
+    try:
+        mz, mx = N.gke_separation_labels(plan)
+        tdt = torch.float64 if precision == 0 else torch.float32
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), len(mz), len(mx)), dtype=tdt, device="cuda")
+        f = torch.from_numpy(coef).cuda()
+        N.gke_accumulate_mean(plan, f, 2)
+        N.gke_accumulate_mean(plan, f[2:], 2)
+        N.gke_accumulate_snapshot(plan, f[:2], 2)
+        N.gke_accumulate_snapshot(plan, f[2:], 2)
+        N.gke_finalize_terms(plan, terms)
+        torch.cuda.synchronize()
+        got = terms.cpu().numpy().astype(np.float64)
+    finally:
+        N.gke_destroy(plan)
+    assert np.array_equal(mz, kept(wl.nz, uz)) and np.array_equal(mx, kept(wl.nx, ux))
+    ref = oracle.full(phys, y, wl.Lx, wl.Lz, wl.nu, mirror=True)
+    w = np.array(oracle.wedge_pairs(wl.ny))
+    tol = TOL_F64 if precision == 0 else 1e-6
+    for t in range(N.GKE_NTERM):
+        want = ref["terms"][t][w[:, 0], w[:, 1]][:, mz][:, :, mx]
+        assert rel_err(got[t], want) <= tol, (N.TERMS[t], rel_err(got[t], want))
+
+
+def test_stride_checkpoint_merge(N, tmp_path):
+    """Independent jobs (Sec. 3.4) on the coarse spectra merge to one pass."""
+    wl = S.small(16, 16, 17, 4, wid=84)
+    coef = S.coefficients(wl)
+    ux = uz = (0, 0, 0, 2)
+    one, _, _ = run(N, wl, coef, ux=ux, uz=uz)
+    import torch
+    y = S.cgl_grid(wl.ny)
+    f = torch.from_numpy(coef).cuda()
+    paths = []
+    for part in ((0, 2), (2, 4)):
+        plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 4, under_x=ux, under_z=uz)
+        try:
+            N.gke_accumulate_mean(plan, f, 4)
+            N.gke_accumulate_snapshot(plan, f[part[0]:part[1]], 2)
+            path = str(tmp_path / f"part{part[0]}.ckpt")
+            N.gke_checkpoint(plan, path)
+            paths.append(path)
+        finally:
+            N.gke_destroy(plan)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 4, under_x=ux, under_z=uz)
+    try:
+        N.gke_restore(plan, paths[0])
+        N.gke_merge(plan, paths[1])
+        mz, mx = N.gke_separation_labels(plan)
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), len(mz), len(mx)), dtype=torch.float64, device="cuda")
+        N.gke_finalize_terms(plan, terms)
+        torch.cuda.synchronize()
+        merged = terms.cpu().numpy()
+    finally:
+        N.gke_destroy(plan)
+    assert rel_err(merged, one) <= TOL_F64
 
 
 def test_undersampled_split_and_wedge(N):
