@@ -247,7 +247,107 @@ def config_of(wl, precision):
             "nu": wl.nu, "l2": "inputs and accumulators larger than L2 (no flush)"}
 
 
+# ------------------------------------------------------- input generation
+def _gen_snapshot(job):
+    """Worker: coefficients of snapshot s written into the shared array."""
+    from multiprocessing import shared_memory
+    name, s, shm_name, shape = job
+    wl = S.WORKLOADS[name]
+    shm = shared_memory.SharedMemory(name=shm_name)
+    try:
+        arr = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+        arr[s] = S.snapshot_coefficients(wl, s)
+    finally:
+        shm.close()
+    return s
+
+
+def coefficients_parallel(wl, dev):
+    """The workload's coefficients, generated snapshot by snapshot in spawned
+    worker processes (large grids), copied to the device `dev`."""
+    import torch
+    from multiprocessing import get_context, shared_memory
+    shape = (wl.nsnap, 4, wl.ny, wl.nz, wl.nxh)
+    nbytes = int(np.prod(shape)) * 16
+    shm = shared_memory.SharedMemory(create=True, size=nbytes)
+    try:
+        with get_context("spawn").Pool(min(16, os.cpu_count() or 1, wl.nsnap)) as pool:
+            pool.map(_gen_snapshot, [(wl.name, s, shm.name, shape) for s in range(wl.nsnap)])
+        arr = np.ndarray(shape, dtype=np.complex128, buffer=shm.buf)
+        out = torch.empty(shape, dtype=torch.complex128, device=dev)
+        for s in range(wl.nsnap):
+            out[s].copy_(torch.from_numpy(arr[s]))
+        del arr
+        return out
+    finally:
+        shm.close()
+        shm.unlink()
+
+
 # ------------------------------------------------------------------ ours
+def run_stream(args, world, rank, local):
+    """Streaming mode: the snapshots accumulated args.batch at a time, optional
+    mirror sampling on the wedge and uniform undersampling by args.stride (the
+    memory-bounded mode of large grids)."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    torch.cuda.set_device(local)
+    wl = S.WORKLOADS[args.workload]
+    ns = wl.nsnap
+    B = args.batch or ns
+    prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3, "f32": N.GKE_PREC_F32}[args.precision]
+    dom = N.GKE_DOMAIN_WEDGE if args.pair_domain == "wedge" else N.GKE_DOMAIN_TRIANGLE
+    st_opt = (0, 0, 0, args.stride) if args.stride > 1 else (0, 0, 0, 0)
+    f_dev = coefficients_parallel(wl, "cuda")
+    stream = torch.cuda.current_stream()
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), B, prec,
+                      stream=stream.cuda_stream, pair_domain=dom, under_x=st_opt, under_z=st_opt)
+    npair = N.gke_npair(plan)
+    mz, mx = N.gke_separation_labels(plan)
+    tdt = torch.float64 if args.precision == "f64" else torch.float32
+    terms = torch.empty((N.GKE_NTERM, npair, len(mz), len(mx)), dtype=tdt, device="cuda")
+
+    def step():
+        N.gke_reset(plan)
+        for b in range(0, ns, B):
+            N.gke_accumulate_mean(plan, f_dev[b:b + B], min(B, ns - b))
+        for b in range(0, ns, B):
+            N.gke_accumulate_snapshot(plan, f_dev[b:b + B], min(B, ns - b))
+        N.gke_finalize_terms(plan, terms)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    N.gke_set_timing(plan, True)
+    N.gke_stage_times(plan)
+    l0 = N.gke_launch_count(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = N.gke_launch_count(plan) - l0
+    stage_ms = {k: v / args.steps for k, v in N.gke_stage_times(plan).items()}
+    N.gke_destroy(plan)
+    ms = e0.elapsed_time(e1) / args.steps
+    pk, pk_kind = peaks()
+    rl = stage_rooflines(wl, ns, args.precision, {"correlate": stage_ms.get("correlate", 0.0)}, pk, pk_kind)
+    cfg = config_of(wl, args.precision)
+    cfg.update({"pair_domain": args.pair_domain, "stride": args.stride, "batch": B, "output_pairs": npair,
+                "separations": [int(len(mz)), int(len(mx))]})
+    line = {"metric": METRIC, "value": npair * ns / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16x3/f32", "f32": "f32"}[args.precision],
+            "data": "synthetic", "config": cfg, "stage_ms": stage_ms, "gpu_launches": launches,
+            "clocks": clk.summary(), "e2e": None, "roofline": rl.get("correlate"), "cpu_baseline": None,
+            "note": "streaming mode: outputs are output_pairs x separations; value counts output pairs"}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1910_06409_gb300._native as N
@@ -433,10 +533,16 @@ def main():
                     help="with --precision f64: skip the split-BF16 run beside it")
     ap.add_argument("--cpu-points", type=int, default=512)
     ap.add_argument("--ref-points", type=int, default=256)
+    ap.add_argument("--pair-domain", choices=("triangle", "wedge"), default="triangle",
+                    help="wedge: y-inversion mirror sampling on the half-channel wedge (streaming mode)")
+    ap.add_argument("--stride", type=int, default=1, help="uniform undersampling of r_x, r_z (streaming mode)")
+    ap.add_argument("--batch", type=int, default=0, help="snapshots per accumulate call (streaming mode)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.pair_domain != "triangle" or args.stride > 1 or args.batch:
+        run_stream(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

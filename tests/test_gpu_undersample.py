@@ -175,3 +175,52 @@ def test_undersampling_errors(N):
         with pytest.raises(N.GkeError) as e:
             N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 1, under_x=bad)
         assert e.value.status == -1
+
+
+# ------------------------------------ Re_tau~1000-shaped grid, streaming mode
+def test_retau1000_grid_streaming_spot_checks(N):
+    """512 x 512 x 257 (the Re_tau~1000-shaped grid) in the memory-bounded
+    mode: mirror sampling on the wedge, separations every 4th grid step,
+    snapshots streamed 2 at a time, split-BF16 contractions.  Sampled outputs
+    against the oracle over the snapshots and their mirror images."""
+    import oracle
+    import torch
+    base = S.RETAU1000
+    wl = S.Workload(base.name, base.wid, base.nx, base.nz, base.ny, 4, base.Lx, base.Lz, base.nu)
+    phys = S.physical(wl)
+    coef = S.to_coefficients(phys)
+    y = S.cgl_grid(wl.ny)
+    st = (0, 0, 0, 4)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 2, N.GKE_PREC_BF16X3,
+                      pair_domain=N.GKE_DOMAIN_WEDGE, under_x=st, under_z=st)
+    try:
+        mz, mx = N.gke_separation_labels(plan)
+        assert len(mz) == 128 and len(mx) == 128
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), 128, 128), dtype=torch.float32, device="cuda")
+        f = torch.from_numpy(coef).cuda()
+        for b in (0, 2):
+            N.gke_accumulate_mean(plan, f[b:b + 2], 2)
+        for b in (0, 2):
+            N.gke_accumulate_snapshot(plan, f[b:b + 2], 2)
+        N.gke_finalize_terms(plan, terms)
+        torch.cuda.synchronize()
+        got = terms.cpu().numpy().astype(np.float64)
+    finally:
+        N.gke_destroy(plan)
+    w = oracle.wedge_pairs(wl.ny)
+    windex = {p: i for i, p in enumerate(w)}
+    rng = np.random.default_rng(1000)
+    planes = [0, 1, 2, 60, 128, 200, 254, 256]
+    pts, idx = [], []
+    while len(pts) < 24:
+        a, b = sorted(rng.choice(planes, 2))
+        if a + b > wl.ny - 1:
+            continue
+        jz, jx = int(rng.integers(128)), int(rng.integers(128))
+        pts.append((a, b, int(mz[jz]), int(mx[jx])))
+        idx.append((windex[(a, b)], jz, jx))
+    ref = oracle.points(phys, y, wl.Lx, wl.Lz, wl.nu, pts, mirror=True)
+    scale = np.abs(got[:6]).reshape(6, -1).max(axis=1)
+    for n, (pw, jz, jx) in enumerate(idx):
+        err = np.abs(got[:6, pw, jz, jx] - ref["terms"][n]) / scale
+        assert err.max() <= 1e-6, (pts[n], err)
