@@ -52,7 +52,9 @@
  *     exact.  A uniform stride s dividing n in both directions ({0, 0, *, s})
  *     is computed on the coarse grid instead: the spectra are aliased onto
  *     it (exact), the wavenumbers run in chunks, and the per-pair sums shrink
- *     by s_z s_x -- the memory-bounded mode for large grids.
+ *     by s_z s_x -- the memory-bounded mode for large grids.  Plans whose
+ *     contractions would not fit in memory at once run in the same chunked
+ *     mode at stride 1.
  *   - Output terms (double on the FP64 path, float on the FP32 and split paths):
  *       terms[GKE_NTERM][npair][nrz][nrx]     (nrz = nz, nrx = nx at full resolution)
  *     in the order GKE_TERM_* below: <du^2>, Phi_x, Phi_y, Phi_z, phi, xi
@@ -108,7 +110,7 @@ enum { GKE_TERM_A = 0, GKE_TERM_PHI_X, GKE_TERM_PHI_Y, GKE_TERM_PHI_Z, GKE_TERM_
 enum { GKE_PROF_U = 0, GKE_PROF_V, GKE_PROF_W, GKE_PROF_P, GKE_PROF_DUDY, GKE_PROF_EPS, GKE_NPROF };
 
 typedef struct {
-    int nx, nz, ny;        /* grid; nx, nz powers of two in [8, 1024]; 5 <= ny <= 1024 */
+    int nx, nz, ny;        /* grid; nx, nz in [8, 1024], 2^a or 3 * 2^a; 5 <= ny <= 1024 */
     double Lx, Lz;         /* box lengths of the homogeneous directions (> 0)            */
     double nu;             /* kinematic viscosity (> 0)                                  */
     const double* y;       /* host pointer, y[ny], strictly increasing; copied            */

@@ -148,10 +148,14 @@ static void fornberg_d1(const double* x, int n, double z0, double* w)
 static const int EPS_KCHUNK = 16;
 // bytes of inverse-transform scratch per pair chunk
 static const long long W_CHUNK_BYTES = 120LL << 20;
-// bytes of contractions + per-pair spectra of one wavenumber chunk (uniform undersampling)
+// bytes of contractions + per-pair spectra of one wavenumber chunk (chunked mode)
 static const size_t DEC_CHUNK_BYTES = (size_t)12 << 30;
+// above this size of one batch's contractions the plan runs in the chunked mode
+static const size_t CHUNKED_RAW_BYTES = (size_t)96 << 30;
 
 static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+// transform lengths of the Stockham kernels: 2^a or 3 * 2^a
+static bool fft_len_ok(int n) { return is_pow2(n) || (n % 3 == 0 && is_pow2(n / 3)); }
 
 // separation indices kept along one direction (a-posteriori undersampling,
 // Sec. 3.4): with d = min(m, n - m), keep d < t1, multiples of s1 for
@@ -242,8 +246,8 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         return GKE_ERR_ARG;
     }
     if (!(d.Lx > 0) || !(d.Lz > 0) || !(d.nu > 0)) { g_plan_err = "Lx, Lz, nu must be > 0"; return GKE_ERR_ARG; }
-    if (!is_pow2(d.nx) || !is_pow2(d.nz)) {
-        g_plan_err = "nx and nz must be powers of two in this build";
+    if (!fft_len_ok(d.nx) || !fft_len_ok(d.nz)) {
+        g_plan_err = "nx and nz must be 2^a or 3 * 2^a in this build";
         return GKE_ERR_UNSUPPORTED;
     }
     if (d.precision != GKE_PREC_F64 && d.precision != GKE_PREC_BF16X3 && d.precision != GKE_PREC_F32) {
@@ -297,8 +301,12 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     p->nzt = d.nz;
     p->nxt = d.nx;
     {
+        // the chunked mode: under a uniform stride, or when one batch's
+        // contractions for all wavenumbers would exceed CHUNKED_RAW_BYTES
         const int sz = uniform_stride(d.nz, d.under_z), sx = uniform_stride(d.nx, d.under_x);
-        if (sz && sx && (sz > 1 || sx > 1) && d.nz / sz >= 4 && d.nx / sx >= 4) {
+        const size_t raw_all = (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * (size_t)Nk *
+                               (d.precision == GKE_PREC_F64 ? sizeof(zd) : sizeof(zf));
+        if (sz && sx && (sz > 1 || sx > 1 || raw_all > CHUNKED_RAW_BYTES) && d.nz / sz >= 4 && d.nx / sx >= 4) {
             p->dec = true;
             p->nzt = d.nz / sz;
             p->nxt = d.nx / sx;

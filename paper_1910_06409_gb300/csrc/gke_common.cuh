@@ -50,66 +50,90 @@ template <typename T> __device__ __forceinline__ cplx<T> mul_i(cplx<T> a) { retu
 __host__ __device__ __forceinline__ int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 
-// Forward transform X[k] = sum_n x[n] e^{-2 pi i n k / N}, N = 2^lg, of nb
-// sequences x[b * ld + n], by the whole thread block: Stockham autosort
-// (natural order in and out), one radix-2 stage first when lg is odd, then
-// radix-4 stages.  Stage with current span Ns and radix R: butterfly j takes
-// x[j + r N/R] (r < R), multiplies by w^(r (j mod Ns) N/(Ns R)), applies the
-// R-point DFT and stores to y[(j / Ns) Ns R + (j mod Ns) + r Ns]; the buffers
-// then swap.  tw[m] = e^{-2 pi i m / N}, m < N (host-computed, staged in
-// shared memory by the caller).  INV = true computes the unnormalised inverse
-// (conjugate in, forward transform, conjugate out).  Returns the buffer that
-// holds the result (x or y); begins and ends with __syncthreads().
-template <typename T, bool INV>
-__device__ cplx<T>* fft_block(cplx<T>* x, cplx<T>* y, int ld, int nb, int lg, const cplx<T>* tw)
+// One Stockham stage of radix R (2, 3 or 4) with current span Ns over nb
+// sequences of length N: butterfly j (< N/R) takes x[j + r N/R] (r < R),
+// multiplies by w^(r (j mod Ns) N/(Ns R)), applies the R-point DFT and stores
+// to y[(j / Ns) Ns R + (j mod Ns) + r Ns].  cin: conjugate the inputs (first
+// stage of an inverse transform).
+template <typename T, int R>
+__device__ __forceinline__ void fft_stage(const cplx<T>* x, cplx<T>* y, int ld, int nb, int N, int Ns, bool cin,
+                                          const cplx<T>* tw)
 {
-    const int N = 1 << lg;
-    __syncthreads();
-    int Ns = 1;
-    bool first = true;
-    if (lg & 1) {
-        const int nbf = N >> 1;
-        for (int t = threadIdx.x; t < nb * nbf; t += blockDim.x) {
-            const int b = t / nbf, j = t - b * nbf;
-            const cplx<T>* src = x + (size_t)b * ld;
-            cplx<T> v0 = src[j], v1 = src[j + nbf];
-            if (INV) { v0.y = -v0.y; v1.y = -v1.y; }
-            cplx<T>* dst = y + (size_t)b * ld;
-            dst[2 * j] = v0 + v1;          // Ns = 1: no twiddle, idxD = 2 j
-            dst[2 * j + 1] = v0 - v1;
+    const int nbf = N / R, tws = N / (Ns * R);
+    for (int t = threadIdx.x; t < nb * nbf; t += blockDim.x) {
+        const int b = t / nbf, j = t - b * nbf;
+        const int jm = j % Ns;
+        const cplx<T>* src = x + (size_t)b * ld;
+        cplx<T> v[R];
+        #pragma unroll
+        for (int r = 0; r < R; ++r) {
+            v[r] = src[j + r * nbf];
+            if (cin) v[r].y = -v[r].y;
         }
-        __syncthreads();
-        cplx<T>* tmp = x; x = y; y = tmp;
-        Ns = 2;
-        first = false;
-    }
-    while (Ns < N) {
-        const int nbf = N >> 2;
-        const int tws = N / (Ns * 4);
-        for (int t = threadIdx.x; t < nb * nbf; t += blockDim.x) {
-            const int b = t / nbf, j = t - b * nbf;
-            const int jm = j & (Ns - 1);
-            const cplx<T>* src = x + (size_t)b * ld;
-            cplx<T> v0 = src[j], v1 = src[j + nbf], v2 = src[j + 2 * nbf], v3 = src[j + 3 * nbf];
-            if (INV && first) { v0.y = -v0.y; v1.y = -v1.y; v2.y = -v2.y; v3.y = -v3.y; }
-            if (Ns > 1) {
-                const int m = jm * tws;
-                v1 = v1 * tw[m];
-                v2 = v2 * tw[2 * m];
-                v3 = v3 * tw[3 * m];
-            }
-            const cplx<T> a0 = v0 + v2, a1 = v0 - v2, a2 = v1 + v3;
-            const cplx<T> d = v1 - v3;
+        if (Ns > 1) {
+            #pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = v[r] * tw[r * jm * tws];
+        }
+        cplx<T>* dst = y + (size_t)b * ld + (j - jm) * R + jm;
+        if (R == 2) {
+            dst[0] = v[0] + v[1];
+            dst[Ns] = v[0] - v[1];
+        } else if (R == 3) {
+            // w = e^{-2 pi i/3} = -1/2 - i sqrt(3)/2
+            const T h = (T)0.5, s3 = (T)0.86602540378443864676;
+            const cplx<T> t1 = v[1] + v[2], t2 = v[1] - v[2];
+            const cplx<T> m1 = mk(v[0].x - h * t1.x, v[0].y - h * t1.y);
+            const cplx<T> m2 = mk(s3 * t2.y, -s3 * t2.x);          // -i sqrt(3)/2 (v1 - v2)
+            dst[0] = v[0] + t1;
+            dst[Ns] = m1 + m2;
+            dst[2 * Ns] = m1 - m2;
+        } else {
+            const cplx<T> a0 = v[0] + v[2], a1 = v[0] - v[2], a2 = v[1] + v[3];
+            const cplx<T> d = v[1] - v[3];
             const cplx<T> a3 = mk(d.y, -d.x);          // -i (v1 - v3)
-            cplx<T>* dst = y + (size_t)b * ld + (j - jm) * 4 + jm;
             dst[0] = a0 + a2;
             dst[Ns] = a1 + a3;
             dst[2 * Ns] = a0 - a2;
             dst[3 * Ns] = a1 - a3;
         }
+    }
+}
+
+// Forward transform X[k] = sum_n x[n] e^{-2 pi i n k / N} of nb sequences
+// x[b * ld + n], N = 2^a or 3 * 2^a, by the whole thread block: Stockham
+// autosort (natural order in and out) with a radix-3 stage when 3 divides N,
+// a radix-2 stage when a is odd, then radix-4 stages (fft_stage).
+// tw[m] = e^{-2 pi i m / N}, m < N (host-computed, staged in shared memory
+// by the caller).  INV = true computes the unnormalised inverse (conjugate
+// in, forward transform, conjugate out).  Returns the buffer that holds the
+// result (x or y); begins and ends with __syncthreads().
+template <typename T, bool INV>
+__device__ cplx<T>* fft_block(cplx<T>* x, cplx<T>* y, int ld, int nb, int N, const cplx<T>* tw)
+{
+    __syncthreads();
+    int Ns = 1;
+    bool first = true;
+    const int p2 = (N % 3 == 0) ? N / 3 : N;      // power-of-two part
+    auto swap = [&]() { cplx<T>* tmp = x; x = y; y = tmp; };
+    if (p2 != N) {
+        fft_stage<T, 3>(x, y, ld, nb, N, Ns, INV && first, tw);
         __syncthreads();
-        cplx<T>* tmp = x; x = y; y = tmp;
-        Ns <<= 2;
+        swap();
+        Ns *= 3;
+        first = false;
+    }
+    if (ilog2(p2) & 1) {
+        fft_stage<T, 2>(x, y, ld, nb, N, Ns, INV && first, tw);
+        __syncthreads();
+        swap();
+        Ns *= 2;
+        first = false;
+    }
+    while (Ns < N) {
+        fft_stage<T, 4>(x, y, ld, nb, N, Ns, INV && first, tw);
+        __syncthreads();
+        swap();
+        Ns *= 4;
         first = false;
     }
     if (INV) {

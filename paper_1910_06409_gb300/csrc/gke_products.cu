@@ -73,7 +73,6 @@ __global__ void k_col_inverse(const zd* __restrict__ fields_s, int ny, int nz, i
     C* b0 = stw + nz;                        // [CW][nz] x2 (ping-pong)
     C* b1 = b0 + CW * nz;
     const int kx0 = blockIdx.x * CW, y = blockIdx.y, f = blockIdx.z;
-    const int lg = ilog2(nz);
     load_twiddles(stw, tw_z, nz);
     const zd* src = fields_s + ((long long)f * ny + y) * nz * nxh;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
@@ -85,7 +84,7 @@ __global__ void k_col_inverse(const zd* __restrict__ fields_s, int ny, int nz, i
         }
         b0[c * nz + kz] = cvt<TF>(v);
     }
-    const C* res = fft_block<TF, true>(b0, b1, nz, CW, lg, stw);
+    const C* res = fft_block<TF, true>(b0, b1, nz, CW, nz, stw);
     C* dst = G + ((long long)f * ny + y) * nz * nxh;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
         int c = t % CW, z = t / CW, kx = kx0 + c;
@@ -190,7 +189,7 @@ __global__ void k_row_products(const cplx<TF>* __restrict__ G, int ny, int nz, i
 {
     typedef cplx<TF> C;
     extern __shared__ __align__(16) unsigned char sh_raw_rp[];
-    const int nxh = nx / 2 + 1, lg = ilog2(nx);
+    const int nxh = nx / 2 + 1;
     const int z0 = blockIdx.x * RZ, y = blockIdx.y;
     const int nrow = min(RZ, nz - z0);
     C* stw = (C*)sh_raw_rp;           // [nx] twiddles
@@ -208,7 +207,7 @@ __global__ void k_row_products(const cplx<TF>* __restrict__ G, int ny, int nz, i
         if (k == 0 || 2 * k == nx) { A.y = 0; B.y = 0; }
         inv0[(r * 2 + q) * nx + k] = mk(A.x - B.y, A.y + B.x);   // A + i B
     }
-    const C* ph = fft_block<TF, true>(inv0, inv1, nx, 2 * nrow, lg, stw);
+    const C* ph = fft_block<TF, true>(inv0, inv1, nx, 2 * nrow, nx, stw);
     double s_q = 0, s_uv = 0, s_pv = 0, s_qu = 0, s_qv = 0, s_qw = 0;
     for (int t = threadIdx.x; t < nrow * nx; t += blockDim.x) {
         int r = t / nx, x = t - r * nx;
@@ -222,13 +221,13 @@ __global__ void k_row_products(const cplx<TF>* __restrict__ G, int ny, int nz, i
         fwd[(r * 4 + 2) * nx + x] = mk(u * w, v * w);
         fwd[(r * 4 + 3) * nx + x] = mk(q, (TF)0);
     }
-    const C* sp = fft_block<TF, false>(fwd, inv0, nx, 4 * nrow, lg, stw);
+    const C* sp = fft_block<TF, false>(fwd, inv0, nx, 4 * nrow, nx, stw);
     const TF inx = (TF)1 / (TF)nx;
     const TF h = (TF)0.5 * inx;
     for (int t = threadIdx.x; t < nrow * 4 * nxh; t += blockDim.x) {
         int r = t / (4 * nxh), rem = t - r * 4 * nxh, j = rem / nxh, k = rem - j * nxh;
         const C* seq = sp + (r * 4 + j) * nx;
-        C Z = seq[k], Zc = conj(seq[(nx - k) & (nx - 1)]);
+        C Z = seq[k], Zc = conj(seq[(nx - k) % nx]);
         C A = h * (Z + Zc);
         C D = Z - Zc;
         C B = mk(h * D.y, -h * D.x);     // -i/2 (Z - Zc)
@@ -359,7 +358,6 @@ __global__ void k_col_forward(const cplx<TF>* __restrict__ H, int ny, int nz, in
     C* b0 = stw + nz;                       // [nb][nz] x2 (ping-pong)
     C* b1 = b0 + nb * nz;
     const int kx0 = blockIdx.x * CW, y0 = blockIdx.y * YB, j = blockIdx.z;
-    const int lg = ilog2(nz);
     const int Nk = nz * nxh;
     load_twiddles(stw, tw_z, nz);
     for (int t = threadIdx.x; t < nb * nz; t += blockDim.x) {
@@ -369,7 +367,7 @@ __global__ void k_col_forward(const cplx<TF>* __restrict__ H, int ny, int nz, in
         if (kx < nxh && y < ny) v = H[(((long long)j * ny + y) * nz + z) * nxh + kx];
         b0[(yy * CW + c) * nz + z] = v;
     }
-    const C* res = fft_block<TF, false>(b0, b1, nz, nb, lg, stw);
+    const C* res = fft_block<TF, false>(b0, b1, nz, nb, nz, stw);
     const TF inz = (TF)1 / (TF)nz;
     for (int t = threadIdx.x; t < nb * nz; t += blockDim.x) {
         int yy = t % YB, rem = t / YB, c = rem % CW, kz = rem / CW;

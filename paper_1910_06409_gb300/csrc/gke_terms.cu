@@ -37,7 +37,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
     C* stw = (C*)sh_raw_tc;
     C* b0 = stw + nz;
     C* b1 = b0 + CW * nz;
-    const int nxh = nx / 2 + 1, Nk = nz * nxh, lg = ilog2(nz);
+    const int nxh = nx / 2 + 1, Nk = nz * nxh;
     const int kx0 = blockIdx.x * CW, q = blockIdx.y;
     const long long pl = blockIdx.z, p = pair0 + pl;
     const TF ic = (TF)inv_count;
@@ -52,7 +52,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
         }
         b0[c * nz + kz_i] = v;
     }
-    const C* res = fft_block<TF, true>(b0, b1, nz, CW, lg, stw);
+    const C* res = fft_block<TF, true>(b0, b1, nz, CW, nz, stw);
     C* dst = W + (pl * NTERM + q) * (long long)sm.nrz * nxh;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
         const int c = t % CW, z = t / CW, kx_i = kx0 + c;
@@ -142,7 +142,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
     C* b0 = stw + nx;
     C* b1 = b0 + RZ * 4 * nx;
     __shared__ TF s_one[NTERM];
-    const int nxh = nx / 2 + 1, lg = ilog2(nx);
+    const int nxh = nx / 2 + 1;
     const int nz = sm.nrz;                 // rows kept (all nz at full resolution)
     const int z0 = blockIdx.x * RZ;
     const int nrow = min(RZ, nz - z0);
@@ -168,7 +168,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
         if (k == 0 || 2 * k == nx) { A.y = 0; B.y = 0; }
         b0[(r * 4 + j) * nx + k] = mk(A.x - B.y, A.y + B.x);
     }
-    const C* sh = fft_block<TF, true>(b0, b1, nx, 4 * nrow, lg, stw);
+    const C* sh = fft_block<TF, true>(b0, b1, nx, 4 * nrow, nx, stw);
     const long long N = (long long)nz * sm.nrx;
     for (int t = threadIdx.x; t < nrow * NTERM * nx; t += blockDim.x) {
         int r = t / (NTERM * nx), rem = t - r * NTERM * nx, q = rem / nx, x = rem - q * nx;

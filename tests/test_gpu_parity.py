@@ -94,7 +94,7 @@ def test_tiny_f64_full_parity(N, tiny):
     check_full(N, wl, got, prof, ref, TOL_F64)
 
 
-@pytest.mark.parametrize("shape", [(16, 8, 7, 3), (8, 32, 11, 1), (64, 16, 6, 2)])
+@pytest.mark.parametrize("shape", [(16, 8, 7, 3), (8, 32, 11, 1), (64, 16, 6, 2), (24, 12, 9, 2), (48, 96, 7, 2)])
 def test_ragged_f64_full_parity(N, shape):
     import oracle
     nx, nz, ny, ns = shape
@@ -169,7 +169,7 @@ def test_error_codes(N):
     finally:
         N.gke_destroy(plan)
     with pytest.raises(N.GkeError) as e:
-        N.gke_plan(12, 8, 6, 1.0, 1.0, 0.1, S.cgl_grid(6), 1)   # nx not a power of two
+        N.gke_plan(20, 8, 6, 1.0, 1.0, 0.1, S.cgl_grid(6), 1)   # nx neither 2^a nor 3 * 2^a
     assert e.value.status == -7
     with pytest.raises(N.GkeError) as e:
         N.gke_plan(8, 8, 6, 1.0, 1.0, 0.1, S.cgl_grid(6)[::-1], 1)

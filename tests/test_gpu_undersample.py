@@ -63,7 +63,7 @@ def uniform(n, u):
 
 
 CASES = [((3, 6, 2, 4), (2, 5, 3, 5)), ((0, 0, 1, 4), (0, 0, 1, 4)), ((0, 0, 0, 0), (1, 1, 1, 8)),
-         ((0, 0, 0, 2), (0, 0, 0, 4)), ((0, 0, 0, 0), (0, 0, 1, 8))]
+         ((0, 0, 0, 2), (0, 0, 0, 4)), ((0, 0, 0, 0), (0, 0, 1, 8)), ((0, 0, 0, 4), (0, 0, 0, 0))]
 
 
 @pytest.mark.parametrize("ux,uz", CASES)
@@ -224,3 +224,16 @@ def test_retau1000_grid_streaming_spot_checks(N):
     for n, (pw, jz, jx) in enumerate(idx):
         err = np.abs(got[:6, pw, jz, jx] - ref["terms"][n]) / scale
         assert err.max() <= 1e-6, (pts[n], err)
+
+
+def test_stride_on_three_times_power_of_two_grid(N):
+    """A 48 x 24 grid (radix-3 transforms) with stride 2 x 3 on the coarse 24 x 8 grid."""
+    import oracle
+    wl = S.small(24, 48, 9, 2, wid=85)
+    phys = S.physical(wl)
+    got, mz, mx = run(N, wl, S.to_coefficients(phys), ux=(0, 0, 0, 3), uz=(0, 0, 0, 2))
+    assert np.array_equal(mz, np.arange(0, 48, 2)) and np.array_equal(mx, np.arange(0, 24, 3))
+    ref = oracle.full(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu)
+    iu = np.triu_indices(wl.ny)
+    for t in range(N.GKE_NTERM):
+        assert rel_err(got[t], ref["terms"][t][iu][:, mz][:, :, mx]) <= TOL_F64, N.TERMS[t]
