@@ -348,6 +348,68 @@ def run_stream(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+GROUP = (("group_128x128x65_s32", 1), ("group_256x256x129_s16", 1), ("group_384x384x193_s8", 2))
+
+
+def run_group(args, world, rank, local):
+    """The three channel-shaped datasets of the grouped configuration, each
+    with its own plan, back to back on one stream; the 384 x 384 x 193 one at
+    separation stride 2 (its full-resolution triangle needs ~282 GB)."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    torch.cuda.set_device(local)
+    prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3, "f32": N.GKE_PREC_F32}[args.precision]
+    tdt = torch.float64 if args.precision == "f64" else torch.float32
+    stream = torch.cuda.current_stream()
+    sets = []
+    for name, stride in GROUP:
+        wl = S.WORKLOADS[name]
+        f = coefficients_parallel(wl, "cuda")
+        st = (0, 0, 0, stride) if stride > 1 else (0, 0, 0, 0)
+        plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), wl.nsnap, prec,
+                          stream=stream.cuda_stream, under_x=st, under_z=st)
+        mz, mx = N.gke_separation_labels(plan)
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), len(mz), len(mx)), dtype=tdt, device="cuda")
+        sets.append((wl, stride, plan, f, terms))
+    for _ in range(args.warmup):
+        for wl, _, plan, f, terms in sets:
+            N.gke_compute(plan, f, wl.nsnap, terms)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in sets]
+    l0 = sum(N.gke_launch_count(s[2]) for s in sets)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    per = [0.0] * len(sets)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            for i, (wl, _, plan, f, terms) in enumerate(sets):
+                ev[i][0].record(stream)
+                N.gke_compute(plan, f, wl.nsnap, terms)
+                ev[i][1].record(stream)
+            torch.cuda.synchronize()
+            for i in range(len(sets)):
+                per[i] += ev[i][0].elapsed_time(ev[i][1])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = sum(N.gke_launch_count(s[2]) for s in sets) - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    units = sum(N.gke_npair(s[2]) * s[0].nsnap for s in sets)
+    detail = [{"workload": wl.name, "stride": stride, "pairs": N.gke_npair(plan), "snapshots": wl.nsnap,
+               "ms_per_step": per[i] / args.steps} for i, (wl, stride, plan, _, _) in enumerate(sets)]
+    for s_ in sets:
+        N.gke_destroy(s_[2])
+    line = {"metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16x3/f32", "f32": "f32"}[args.precision],
+            "data": "synthetic", "config": {"workload": "group of three channel datasets", "datasets": detail,
+                                            "precision": args.precision},
+            "gpu_launches": launches, "clocks": clk.summary(), "e2e": None, "roofline": None,
+            "cpu_baseline": None, "note": "datasets run as separate plans back to back (no grouped launch)"}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1910_06409_gb300._native as N
@@ -526,7 +588,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("f64", "bf16x3", "f32"), default="f64")
-    ap.add_argument("--workload", default=S.RETAU200.name, choices=sorted(S.WORKLOADS))
+    ap.add_argument("--workload", default=S.RETAU200.name, choices=sorted(S.WORKLOADS) + ["group"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true",
@@ -541,6 +603,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "group":
+        run_group(args, world, rank, local)
     elif args.pair_domain != "triangle" or args.stride > 1 or args.batch:
         run_stream(args, world, rank, local)
     else:

@@ -237,3 +237,40 @@ def test_stride_on_three_times_power_of_two_grid(N):
     iu = np.triu_indices(wl.ny)
     for t in range(N.GKE_NTERM):
         assert rel_err(got[t], ref["terms"][t][iu][:, mz][:, :, mx]) <= TOL_F64, N.TERMS[t]
+
+
+def test_grid_384_chunked_spot_checks(N):
+    """The 384 x 384 x 193 grid of the grouped configuration (radix-3
+    transforms; one batch's FP64 contractions would take 332 GB, so the plan
+    runs in the chunked mode) at separation stride 2, two snapshots, FP64:
+    sampled outputs against the oracle."""
+    import oracle
+    import torch
+    base = S.GROUP_C
+    wl = S.Workload(base.name, base.wid, base.nx, base.nz, base.ny, 2, base.Lx, base.Lz, base.nu)
+    phys = S.physical(wl)
+    coef = S.to_coefficients(phys)
+    y = S.cgl_grid(wl.ny)
+    st = (0, 0, 0, 2)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 2, under_x=st, under_z=st)
+    try:
+        mz, mx = N.gke_separation_labels(plan)
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), len(mz), len(mx)), dtype=torch.float64, device="cuda")
+        N.gke_compute(plan, torch.from_numpy(coef).cuda(), 2, terms)
+        torch.cuda.synchronize()
+        got = terms.cpu().numpy()
+    finally:
+        N.gke_destroy(plan)
+    rng = np.random.default_rng(384)
+    planes = [0, 1, 2, 50, 96, 150, 191, 192]
+    pts, idx = [], []
+    for _ in range(24):
+        a, b = sorted(rng.choice(planes, 2))
+        jz, jx = int(rng.integers(len(mz))), int(rng.integers(len(mx)))
+        pts.append((a, b, int(mz[jz]), int(mx[jx])))
+        idx.append((a * wl.ny - a * (a - 1) // 2 + (b - a), jz, jx))
+    ref = oracle.points(phys, y, wl.Lx, wl.Lz, wl.nu, pts)
+    scale = np.abs(got[:6]).reshape(6, -1).max(axis=1)
+    for n, (p, jz, jx) in enumerate(idx):
+        err = np.abs(got[:6, p, jz, jx] - ref["terms"][n]) / scale
+        assert err.max() <= TOL_F64, (pts[n], err)
