@@ -194,12 +194,45 @@ template <typename T> __device__ __forceinline__ cplx<T> tw32(int j);
 template <> __device__ __forceinline__ zf tw32<float>(int j) { return c_tw32f[j]; }
 template <> __device__ __forceinline__ zd tw32<double>(int j) { return c_tw32d[j]; }
 
+// w * W_32^m (conjugate twiddle if INV) for m known at compile time after
+// unrolling: m = 0 and m = 8 (-i) cost no arithmetic, m = 4 and m = 12
+// ((+-1 - i)/sqrt 2) two additions and two multiplications
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> twiddle_mul(cplx<T> w, int m)
+{
+    const T c = (T)0.70710678118654752440;
+    if (m == 0) return w;
+    if (m == 8) return INV ? mk(-w.y, w.x) : mk(w.y, -w.x);
+    if (m == 4) return INV ? mk(c * (w.x - w.y), c * (w.x + w.y)) : mk(c * (w.x + w.y), c * (w.y - w.x));
+    if (m == 12) return INV ? mk(-c * (w.x + w.y), c * (w.x - w.y)) : mk(c * (w.y - w.x), -c * (w.x + w.y));
+    cplx<T> t = tw32<T>(m);
+    if (INV) t.y = -t.y;
+    return w * t;
+}
+
 template <int M> struct Lg2 { static constexpr int v = Lg2<M / 2>::v + 1; };
 template <> struct Lg2<1> { static constexpr int v = 0; };
 __host__ __device__ constexpr int brev_ct(int x, int bits) {
     int r = 0;
     for (int i = 0; i < bits; ++i) r = (r << 1) | ((x >> i) & 1);
     return r;
+}
+
+// butterflies of span LEN of the radix-2 DFT in registers (LEN a template
+// parameter, so every twiddle index is a compile-time constant), then LEN * 2
+template <typename T, int M, int LEN, bool INV>
+__device__ __forceinline__ void dft_stage(cplx<T>* a)
+{
+    #pragma unroll
+    for (int i = 0; i < M; i += LEN) {
+        #pragma unroll
+        for (int j = 0; j < LEN / 2; ++j) {
+            const cplx<T> u = a[i + j], w = twiddle_mul<T, INV>(a[i + j + LEN / 2], j * (32 / LEN));
+            a[i + j] = u + w;
+            a[i + j + LEN / 2] = u - w;
+        }
+    }
+    if constexpr (LEN < M) dft_stage<T, M, 2 * LEN, INV>(a);
 }
 
 // M-point DFT (M <= 32, power of two) of v[0..M) in registers, natural order in
@@ -211,23 +244,7 @@ __device__ __forceinline__ void dft_reg(cplx<T>* v)
     cplx<T> a[M];
     #pragma unroll
     for (int i = 0; i < M; ++i) a[brev_ct(i, Lg2<M>::v)] = v[i];
-    #pragma unroll
-    for (int len = 2; len <= M; len <<= 1) {
-        #pragma unroll
-        for (int i = 0; i < M; i += len) {
-            #pragma unroll
-            for (int j = 0; j < len / 2; ++j) {
-                cplx<T> u = a[i + j], w = a[i + j + len / 2];
-                if (j != 0) {
-                    cplx<T> t = tw32<T>(j * (32 / len));
-                    if (INV) t.y = -t.y;
-                    w = w * t;
-                }
-                a[i + j] = u + w;
-                a[i + j + len / 2] = u - w;
-            }
-        }
-    }
+    dft_stage<T, M, 2, INV>(a);
     #pragma unroll
     for (int i = 0; i < M; ++i) v[i] = a[i];
 }

@@ -24,13 +24,13 @@
 namespace gke {
 
 // -------------------------- column pass: inverse transform along z
-// W[pl][t][z][kx] = inv_count * sum_kz comb[p][t][kz, kx] e^{+i kz z}.
+// W[pl][t][z][kx] = sum_kz comb[p][t][kz, kx] e^{+i kz z} (the 1/count of the
+// average is applied by the row pass, with the one-point parts).
 // CTA = CW kx columns of one term of one pair; shared memory (1 + 2 CW) nz
 // complex.
 template <typename TF, typename TB>
 __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pair0, int nz, int nx, int CW,
-                                double inv_count, const cplx<TF>* __restrict__ tw_z, SepMap sm,
-                                cplx<TF>* __restrict__ W)
+                                const cplx<TF>* __restrict__ tw_z, SepMap sm, cplx<TF>* __restrict__ W)
 {
     typedef cplx<TF> C;
     extern __shared__ __align__(16) unsigned char sh_raw_tc[];
@@ -40,7 +40,6 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
     const int nxh = nx / 2 + 1, Nk = nz * nxh;
     const int kx0 = blockIdx.x * CW, q = blockIdx.y;
     const long long pl = blockIdx.z, p = pair0 + pl;
-    const TF ic = (TF)inv_count;
     load_twiddles(stw, tw_z, nz);
     const cplx<TB>* src = comb + (p * NTERM + q) * (long long)Nk;
     for (int t = threadIdx.x; t < CW * nz; t += blockDim.x) {
@@ -48,7 +47,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
         C v = mk((TF)0, (TF)0);
         if (kx_i < nxh) {
             const cplx<TB> x = src[(long long)kz_i * nxh + kx_i];
-            v = mk(ic * (TF)x.x, ic * (TF)x.y);
+            v = mk((TF)x.x, (TF)x.y);
         }
         b0[c * nz + kz_i] = v;
     }
@@ -65,7 +64,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
 // one pair x N2 lanes (see fft2l)
 template <typename TF, typename TB, int N1, int N2, bool US>
 __global__ void __launch_bounds__(256)
-k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, int CW, double inv_count,
+k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, int CW,
                   const cplx<TF>* __restrict__ tw_z, SepMap sm, cplx<TF>* __restrict__ W)
 {
     typedef cplx<TF> C;
@@ -77,7 +76,6 @@ k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, i
     const int kx = blockIdx.x * CW + c, q = blockIdx.y;
     const long long pl = blockIdx.z, p = pair0 + pl;
     const int Nk = N * nxh;
-    const TF ic = (TF)inv_count;
     load_twiddles(stw, tw_z, N);
     const cplx<TB>* src = comb + (p * NTERM + q) * (long long)Nk;
     C v[N1];
@@ -86,7 +84,7 @@ k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, i
         C x = mk((TF)0, (TF)0);
         if (kx < nxh) {
             const cplx<TB> b = ld_stream(src + (long long)(lane + N2 * m) * nxh + kx);
-            x = mk(ic * (TF)b.x, ic * (TF)b.y);
+            x = mk((TF)b.x, (TF)b.y);
         }
         v[m] = x;
     }
@@ -125,14 +123,14 @@ __device__ __forceinline__ void onepoint(const double* __restrict__ pr, int ny, 
 }
 
 // ------------------------------ row pass: C2R along x + one-point parts
-// terms[t][p][z][x] = sum_kx W[pl][t][z][kx] e^{+i kx x} + onepoint_t(Y1, Y2),
+// terms[t][p][z][x] = inv_count sum_kx W[pl][t][z][kx] e^{+i kx x} + onepoint_t(Y1, Y2),
 // stored as TO.  With spec != NULL the spectral parts of A, Phi_y and phi
 // (the terms the Step-3 stencils difference) also go to spec[3][p][z][x].
 // Terms are transformed two at a time (t0 + i t1).  CTA = RZ rows of one pair;
 // shared memory (1 + 8 RZ) nx complex.
 template <typename TF, typename TO>
 __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
-                                long long npair, int ny, int nx, int RZ,
+                                long long npair, int ny, int nx, int RZ, double inv_count,
                                 const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x, SepMap sm,
                                 TO* __restrict__ terms, float* __restrict__ spec)
 {
@@ -175,7 +173,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
         const int xr = sm.xcol(x);
         if (xr < 0) continue;
         C v = sh[(r * 4 + (q >> 1)) * nx + x];
-        const TF sp = (q & 1) ? v.y : v.x;
+        const TF sp = ((q & 1) ? v.y : v.x) * (TF)inv_count;
         const long long e = (long long)(z0 + r) * sm.nrx + xr;
         terms[((long long)q * npair + p) * N + e] = (TO)(sp + s_one[q]);
         if (spec != nullptr) {
@@ -190,8 +188,8 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
 template <typename TF, typename TO, int N1, int N2, bool US>
 __global__ void __launch_bounds__(256)
 k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
-                  int ny, int RZ, const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x, SepMap sm,
-                  TO* __restrict__ terms, float* __restrict__ spec)
+                  int ny, int RZ, double inv_count, const double* __restrict__ prof,
+                  const cplx<TF>* __restrict__ tw_x, SepMap sm, TO* __restrict__ terms, float* __restrict__ spec)
 {
     typedef cplx<TF> C;
     constexpr int N = N1 * N2, nxh = N / 2 + 1;
@@ -213,6 +211,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
         for (int t = 0; t < NTERM; ++t) s_one[t] = (TF)one[t];
     }
     const long long NN = (long long)nz * nrx;
+    const TF ic = (TF)inv_count;
     C* xr = xs + r * N1 * (N2 + 1);
     for (int jq = 0; jq < 4; ++jq) {
         const int ta = 2 * jq, tb = 2 * jq + 1;
@@ -240,7 +239,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
                 for (int h = 0; h < 2; ++h) {
                     const int q = 2 * jq + h;
                     if (q >= NTERM) break;
-                    const TF sp = h ? v[m].y : v[m].x;
+                    const TF sp = (h ? v[m].y : v[m].x) * ic;
                     st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[q]));
                     if (spec != nullptr) {
                         const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
@@ -267,14 +266,14 @@ int terms_launch_t(const TermArgs& a)
             const size_t sh = (256 + 16 * (16 * CWR + 1)) * sizeof(C);
             if (us)
                 k_terms_colpass_r<TF, TB, 16, 16, true><<<g, CWR * 16, sh, a.st>>>(
-                    (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, (C*)a.W);
             else
                 k_terms_colpass_r<TF, TB, 16, 16, false><<<g, CWR * 16, sh, a.st>>>(
-                    (const cplx<TB>*)a.comb, p0, nxh, CWR, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, (C*)a.W);
         } else {
             k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
                                       (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
-                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, a.inv_count, (const C*)a.tw_z, a.sep, (C*)a.W);
+                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, (const C*)a.tw_z, a.sep, (C*)a.W);
         }
         if (a.nx == 256) {
             constexpr int RZR = 4;
@@ -282,17 +281,17 @@ int terms_launch_t(const TermArgs& a)
             const size_t sh = (256 + RZR * 16 * 17) * sizeof(C);
             if (us)
                 k_terms_rowpass_r<TF, TO, 16, 16, true><<<g, RZR * 16, sh, a.st>>>(
-                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.prof, (const C*)a.tw_x, a.sep, (TO*)a.terms,
-                    a.spec);
+                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
+                    (TO*)a.terms, a.spec);
             else
                 k_terms_rowpass_r<TF, TO, 16, 16, false><<<g, RZR * 16, sh, a.st>>>(
-                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.prof, (const C*)a.tw_x, a.sep, (TO*)a.terms,
-                    a.spec);
+                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
+                    (TO*)a.terms, a.spec);
         } else {
             k_terms_rowpass<TF, TO><<<dim3((a.sep.nrz + a.rz - 1) / a.rz, (unsigned)np), 256,
                                       (1 + 8 * a.rz) * a.nx * sizeof(C), a.st>>>(
-                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nx, a.rz, a.prof, (const C*)a.tw_x, a.sep,
-                (TO*)a.terms, a.spec);
+                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nx, a.rz, a.inv_count, a.prof, (const C*)a.tw_x,
+                a.sep, (TO*)a.terms, a.spec);
         }
         launches += 2;
     }
