@@ -294,6 +294,8 @@ def run_stream(args, world, rank, local):
 
     torch.cuda.set_device(local)
     wl = S.WORKLOADS[args.workload]
+    if args.nsnap:
+        wl = S.Workload(wl.name, wl.wid, wl.nx, wl.nz, wl.ny, args.nsnap, wl.Lx, wl.Lz, wl.nu)
     ns = wl.nsnap
     B = args.batch or ns
     prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3, "f32": N.GKE_PREC_F32}[args.precision]
@@ -599,6 +601,7 @@ def main():
                     help="wedge: y-inversion mirror sampling on the half-channel wedge (streaming mode)")
     ap.add_argument("--stride", type=int, default=1, help="uniform undersampling of r_x, r_z (streaming mode)")
     ap.add_argument("--batch", type=int, default=0, help="snapshots per accumulate call (streaming mode)")
+    ap.add_argument("--nsnap", type=int, default=0, help="first n snapshots of the workload only (streaming mode)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
