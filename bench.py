@@ -62,10 +62,22 @@ def correlator_cmac(wl, ns):
     return Nk * ns * (3 * wl.npair + 14 * wl.ny * wl.ny)
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernels, from the ncu launch list of this benchmark's command
-# (profiles/launches_retau200.md); None where the kernel changed since.
-NCU_TRAFFIC_GB = {}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pass of each
+# stage's kernels at 256 x 256 x 129 x 16, from the ncu launch lists in
+# profiles/launches_{f64,split_bf16x3}_retau200_256x256x129_s16.md (GB); a
+# stage missing here reports null (not captured since its kernels changed).
+NCU_TRAFFIC_GB = {
+    "f64": {"correlate": 103.9, "combine": 94.8, "terms": 93.9, "stencil": 39.9, "products": 46.5},
+    "bf16x3": {"correlate": 65.8, "combine": 47.4, "terms": 54.0, "stencil": 28.8, "products": 27.5},
+}
+
+
+def ncu_traffic(wl, precision, stage):
+    """Captured DRAM bytes of a stage (only for the workload the capture ran)."""
+    if wl.name != S.RETAU200.name:
+        return None
+    gb = NCU_TRAFFIC_GB.get(precision, {}).get(stage)
+    return None if gb is None else int(gb * 1e9)
 
 
 def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
@@ -100,7 +112,7 @@ def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
             continue
         ach = b / (stage_ms[st] / 1e3) / 1e9
         out[st] = {"bound": "hbm", "achieved": ach, "peak": peak_bw, "unit": "GB/s", "frac": ach / peak_bw,
-                   "bytes": b, "launch_ms": stage_ms[st], "traffic": NCU_TRAFFIC_GB.get(st),
+                   "bytes": b, "launch_ms": stage_ms[st], "traffic": ncu_traffic(wl, precision, st),
                    "peak_source": f"hbm_gbs ({pk_kind})"}
     cm = correlator_cmac(wl, ns)
     ms = stage_ms.get("correlate", 0.0)
@@ -110,14 +122,14 @@ def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
             peak = N_SM * FP32_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             out["correlate"] = {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
                                 "unit": "TFLOP/s", "flops": flops, "launch_ms": ms,
-                                "traffic": NCU_TRAFFIC_GB.get("correlate"),
+                                "traffic": ncu_traffic(wl, precision, "correlate"),
                                 "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x max SM clock"}
         elif f32:
             flops = 48.0 * cm                      # 6 BF16 slice products x 8 real flops per complex MAC
             peak = pk["bf16_tflops"]
             out["correlate"] = {"bound": "tensor", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
                                 "unit": "TFLOP/s", "flops": flops, "launch_ms": ms,
-                                "traffic": NCU_TRAFFIC_GB.get("correlate"),
+                                "traffic": ncu_traffic(wl, precision, "correlate"),
                                 "peak_source": f"bf16_tflops ({pk_kind})",
                                 "note": "stage = operand split + tcgen05 contractions + edge row"}
         else:
@@ -125,7 +137,7 @@ def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
             peak = N_SM * FP64_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             out["correlate"] = {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12, "peak": peak,
                                 "unit": "TFLOP/s", "flops": flops, "launch_ms": ms,
-                                "traffic": NCU_TRAFFIC_GB.get("correlate"),
+                                "traffic": ncu_traffic(wl, precision, "correlate"),
                                 "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock "
                                                "(nominal 1.25 TFLOP/s FP64)"}
         out["correlate"]["frac"] = out["correlate"]["achieved"] / out["correlate"]["peak"]
