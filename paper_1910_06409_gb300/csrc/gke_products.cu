@@ -7,6 +7,8 @@
 // on two real rows at a time (packed as real and imaginary part of one
 // complex sequence).  The transform arithmetic runs in TF = double (plain
 // path) or float (split path); one-point sums are always FP64.
+#include <algorithm>
+
 #include "gke_common.cuh"
 #include "gke_kernels.h"
 
@@ -481,7 +483,10 @@ int products_launch(const ProdArgs& a)
         launches += 4;
     }
     const int neb = (Nk + a.eps_kchunk - 1) / a.eps_kchunk;
-    k_eps<TF><<<neb, 128, 0, st>>>(Xop, ns, ny, nz, nxh, nx, a.Lx, a.Lz, a.fdw, a.fdl0, a.eps_kchunk, a.part);
+    // one thread per wall-normal row: no second pass for a ragged last row
+    const int eps_threads = std::min(1024, (ny + 31) / 32 * 32);
+    k_eps<TF><<<neb, eps_threads, 0, st>>>(Xop, ns, ny, nz, nxh, nx, a.Lx, a.Lz, a.fdw, a.fdl0, a.eps_kchunk,
+                                          a.part);
     k_reduce_partials<<<(ny + 127) / 128, 128, 0, st>>>(a.part, ny, neb, a.stats + S_EPS * ny);
     return launches + 2;
 }
