@@ -31,6 +31,8 @@
 // CUDA cores.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+
 #include "gke_split.h"
 #include "gke_kernels.h"
 
@@ -84,6 +86,19 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
     for (int it = 0; it < (1 << 22); ++it) {
         if (mbar_try(b, parity)) return true;
+        if (it > 32) __nanosleep(200);
+    }
+    return false;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+// bounded wait that also gives up as soon as another role of the CTA has
+// raised the abort flag
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* b, uint32_t parity, volatile int* abort) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try(b, parity)) return true;
+        if (*abort) return false;
         if (it > 32) __nanosleep(200);
     }
     return false;
@@ -352,6 +367,195 @@ k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, in
     }
 }
 
+// ------------------------------------- persistent, warp-specialised variant
+// One CTA per SM walks the (wavenumber, contraction, tile) items
+// blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
+//   warp 0 (one lane): bulk copies of the operand blocks into a ring of NST
+//     shared-memory stages (full[s] completes when a stage's bytes land);
+//   warp 1 (one lane): the MMAs of an item into one of two 256-column TMEM
+//     accumulators, each stage released by a commit to empty[s], the
+//     finished accumulator announced by a commit to acc_full[b];
+//   warps 2-5: the epilogue of an item (TMEM -> registers -> shared memory ->
+//     8 x 8 pair blocks of raw), then acc_empty[b] for the MMA warp.
+// So the copies, the tensor cores and the raw writes of successive items
+// overlap.  Every wait is bounded; a timed-out wait raises the CTA's abort
+// flag (all roles leave their loops) and the device error flag, and the copies
+// and MMAs in flight are drained before the shared memory and TMEM go away.
+constexpr int NST = 3;                                  // operand stages
+constexpr int EPI_WARPS = 4;
+constexpr int TCP_THREADS = 64 + 32 * EPI_WARPS;
+constexpr int SMP_STAGE = SM_A + SM_B;                  // 61440 bytes
+constexpr int SMP_EPI = NST * SMP_STAGE;
+constexpr int SMP_BAR = SMP_EPI + EPI_WARPS * 32 * 33 * 8;
+constexpr int SMP_TOTAL = SMP_BAR + 256;
+constexpr uint32_t TMEM_COLS_P = 512;
+
+struct TcPipeBars {
+    uint64_t full[NST], empty[NST], acc_full[2], acc_empty[2], drain;
+    uint32_t tmem;
+    int abort;
+};
+
+__global__ void __launch_bounds__(TCP_THREADS, 1)
+k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, int G, int MT, int ny, int cov,
+               long long nitems, zf* __restrict__ raw, int* __restrict__ err)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    TcPipeBars* bars = (TcPipeBars*)(smem + SMP_BAR);
+    volatile int* abort = &bars->abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int njt = NJSQ * MT * MT + MT * (MT + 1) / 2;
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < NST; ++st) {
+            mbar_init(&bars->full[st], 1);
+            mbar_init(&bars->empty[st], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bars->acc_full[b], 1);
+            mbar_init(&bars->acc_empty[b], EPI_WARPS);
+        }
+        mbar_init(&bars->drain, 1);
+        bars->abort = (*(volatile int*)err != 0) ? 1 : 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&bars->tmem)),
+                     "r"(TMEM_COLS_P) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars->tmem;
+    auto fail = [&]() { *abort = 1; atomicExch(err, 1); };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int st = 0;
+            uint32_t ph = 0;
+            int issued = 0;
+            for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const int k = (int)(it / njt);
+                int job, mt, nt;
+                decode_tile((int)(it % njt), MT, job, mt, nt);
+                const TcJob& jd = c_tcjobs[job];
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int t = 0; t < jd.nterm; ++t)
+                        for (int g = 0; g < G; ++g) {
+                            if (!mbar_wait_ab(&bars->empty[st], ph ^ 1, abort)) { fail(); goto producer_done; }
+                            const uint32_t ba = pass ? 2 * A_BLK * 2 : SM_A, bb = pass ? B_BLK * 2 : SM_B;
+                            uint8_t* sa = smem + st * SMP_STAGE;
+                            mbar_expect_tx(&bars->full[st], ba + bb);
+                            bulk_g2s(sa, Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + mt) *
+                                                   (long long)A_STAGE, ba, &bars->full[st]);
+                            bulk_g2s(sa + SM_A, Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + nt) *
+                                                          (long long)B_STAGE, bb, &bars->full[st]);
+                            ++issued;
+                            if (++st == NST) { st = 0; ph ^= 1; }
+                        }
+            }
+        producer_done:
+            // no copy may be in flight when the CTA exits: wait for the last
+            // phase issued on every stage (bounded; earlier phases completed
+            // before the stage was reused)
+            for (int q = 0; q < NST && q < issued; ++q) {
+                const int last = issued - 1 - q;                 // issue index of a recent copy
+                mbar_wait(&bars->full[last % NST], (uint32_t)((last / NST) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int st = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+                const int job = [&] { int j, m, n; decode_tile((int)(it % njt), MT, j, m, n); return j; }();
+                const TcJob& jd = c_tcjobs[job];
+                if (!mbar_wait_ab(&bars->acc_empty[acc], aph ^ 1, abort)) { fail(); break; }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(acc * 256);
+                uint32_t accum = 0;
+                bool ok = true;
+                for (int pass = 0; pass < 2 && ok; ++pass)
+                    for (int t = 0; t < jd.nterm && ok; ++t)
+                        for (int g = 0; g < G; ++g) {
+                            if (!mbar_wait_ab(&bars->full[st], ph, abort)) { fail(); ok = false; break; }
+                            tc_fence_after();
+                            const uint8_t* sa = smem + st * SMP_STAGE;
+                            const uint8_t* sb = sa + SM_A;
+                            const int npr = pass ? 1 : 5;
+                            for (int pr = 0; pr < npr; ++pr) {
+                                const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
+                                const uint64_t a_re = sdesc(sa + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
+                                const uint64_t a_im = sdesc(sa + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
+                                const uint64_t b_1 = sdesc(sb + j * B_BLK * 2, B_LBO, CM_SBO);
+                                const uint64_t b_2 = sdesc(sb + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
+                                mma_bf16(d, a_re, b_1, IDESC, accum);
+                                accum = 1;
+                                mma_bf16(d, a_im, b_2, IDESC, 1);
+                            }
+                            mma_commit(&bars->empty[st]);
+                            if (++st == NST) { st = 0; ph ^= 1; }
+                        }
+                if (!ok) break;
+                mma_commit(&bars->acc_full[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1; }
+            }
+            // every MMA of this thread has completed before TMEM is released
+            mma_commit(&bars->drain);
+            mbar_wait(&bars->drain, 0);
+        }
+    } else {
+        const int q = warp & 3;                       // TMEM lane quarter of this warp
+        zf* xp = (zf*)(smem + SMP_EPI) + (warp - 2) * 32 * 33;
+        const int YB = (ny + 7) / 8;
+        int acc = 0;
+        uint32_t aph = 0;
+        for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
+            const int k = (int)(it / njt);
+            int job, mt, nt;
+            decode_tile((int)(it % njt), MT, job, mt, nt);
+            if (!mbar_wait_ab(&bars->acc_full[acc], aph, abort)) { fail(); break; }
+            tc_fence_after();
+            const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
+            for (int c = 0; c < 4; ++c) {
+                uint32_t re[32], im[32];
+                tmem_ld32(tbase + c * 32, re);
+                tmem_ld32(tbase + 128 + c * 32, im);
+                tmem_ld_wait();
+                #pragma unroll
+                for (int j = 0; j < 32; ++j) xp[lane * 33 + j] = mk(__uint_as_float(re[j]), __uint_as_float(im[j]));
+                __syncwarp();
+                const int e = 2 * lane, r8 = e >> 3, c8 = e & 7;
+                #pragma unroll
+                for (int rg = 0; rg < 4; ++rg) {
+                    const int yb = (mt * TM + q * 32) / 8 + rg;
+                    #pragma unroll
+                    for (int cg = 0; cg < 4; ++cg) {
+                        const int ypb = (nt * TM + c * 32) / 8 + cg;
+                        if (yb < YB && ypb < YB) {
+                            const zf a0 = xp[(8 * rg + r8) * 33 + 8 * cg + c8];
+                            const zf a1 = xp[(8 * rg + r8) * 33 + 8 * cg + c8 + 1];
+                            float4* dst = (float4*)(raw + ((((long long)job * YB + yb) * YB + ypb) * Nk + k) * 64 + e);
+                            __stcs(dst, make_float4(a0.x, a0.y, a1.x, a1.y));
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->acc_empty[acc]);
+            if (++acc == 2) { acc = 0; aph ^= 1; }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS_P) : "memory");
+    }
+}
+
 // ------------------------------------------- edge rows / columns (FP32)
 // Entries with y >= cov or y' >= cov (the last row / column of a 128 m + 1
 // grid), FP32 products and sums on the CUDA cores, same coefficients.  A term
@@ -438,7 +642,9 @@ cudaError_t split_setup(cudaStream_t st)
     };
     cudaError_t e = cudaMemcpyToSymbolAsync(c_tcjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void*)k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
+    e = cudaFuncSetAttribute((const void*)k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)k_corr_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, SMP_TOTAL);
 }
 
 // wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
@@ -455,7 +661,14 @@ gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, 
                                                                                     Aop);
     k_split_prep_B<<<(unsigned)((long long)Kc * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, Bop);
     const long long njt = (long long)NJSQ * MT * MT + MT * (MT + 1) / 2;
-    k_corr_tc<<<(unsigned)(Kc * njt), 128, SM_TOTAL, st>>>(Aop, Bop, Kc, G, MT, ny, cov, raw, w.err);
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const long long nitems = (long long)Kc * njt;
+        const unsigned grid = (unsigned)std::min<long long>(nitems, std::max(nsm, 1));
+        k_corr_tc_pipe<<<grid, TCP_THREADS, SMP_TOTAL, st>>>(Aop, Bop, Kc, G, MT, ny, cov, nitems, raw, w.err);
+    }
     *launches = 3;
     if (cov < ny) {
         k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, cov, raw);
