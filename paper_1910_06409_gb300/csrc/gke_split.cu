@@ -15,8 +15,8 @@
 // products of all terms go first and the large x0 y0 products last: an output
 // then sees 2 T G large additions (T terms, G snapshot groups) instead of 12 T G.
 //
-// Tensor-core mapping (one CTA = one wavenumber k, one contraction, one
-// 128 x 128 tile of (y, y')): D[128 x 256] in TMEM, columns 0..127 = Re,
+// Tensor-core mapping (one work item = one wavenumber k, one contraction,
+// one 128 x 128 tile of (y, y')): D[128 x 256] in TMEM, columns 0..127 = Re,
 // 128..255 = Im.  Per term, snapshot group of 16 and slice pair (i, j):
 //   mma(A = ar_i, B = [br_j | bi_j])      -> Re += ar br, Im += ar bi
 //   mma(A = ai_i, B = [bi_j | -br_j])     -> Re += ai bi, Im -= ai br
@@ -48,12 +48,9 @@ constexpr int A_STAGE = 6 * A_BLK;      // slices x parts (re, im), slice-major
 constexpr int B_STAGE = 3 * B_BLK;      // slices
 constexpr int SM_A = A_STAGE * 2;       // 24576 bytes
 constexpr int SM_B = B_STAGE * 2;       // 36864 bytes
-constexpr int SM_BAR = SM_A + SM_B;     // mbarriers + TMEM address slot
-constexpr int SM_TOTAL = 100 * 1024;    // at most two CTAs per SM: 2 x 256 TMEM columns
 constexpr int A_LBO = (TM / 8) * 128;       // 2048: K-adjacent core matrices in an A block
 constexpr int B_LBO = (3 * TM / 8) * 128;   // 6144: K-adjacent core matrices in a B block
 constexpr int CM_SBO = 128;                 // M/N-adjacent core matrices
-constexpr int TMEM_COLS = 256;
 
 // instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16 (7-9, 10-12),
 // K-major A and B (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
@@ -239,135 +236,7 @@ __device__ __forceinline__ void decode_tile(int jt, int MT, int& job, int& mt, i
     }
 }
 
-__global__ void __launch_bounds__(128, 1)
-k_corr_tc(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, int G, int MT, int ny, int cov,
-          zf* __restrict__ raw, int* __restrict__ err)
-{
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + SM_A;
-    uint64_t* bar_ld = (uint64_t*)(smem + SM_BAR);
-    uint64_t* bar_mma = bar_ld + 1;
-    uint32_t* tslot = (uint32_t*)(bar_ld + 2);
-    int* s_ok = (int*)(tslot + 1);
-    const int njt = NJSQ * MT * MT + MT * (MT + 1) / 2;
-    const int k = (int)(blockIdx.x / njt);
-    int job, mt, nt;
-    decode_tile((int)(blockIdx.x % njt), MT, job, mt, nt);
-    const int warp = threadIdx.x >> 5;
-
-    if (threadIdx.x == 0) {
-        mbar_init(bar_ld, 1);
-        mbar_init(bar_mma, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        // once any CTA has reported a timed-out wait, the rest skip their work
-        *s_ok = (*(volatile int*)err == 0) ? 1 : 0;
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
-                     "r"(TMEM_COLS) : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = *tslot;
-
-    if (threadIdx.x == 0 && *s_ok) {
-        const TcJob jd = c_tcjobs[job];
-        uint32_t ph_ld = 0, ph_mma = 0, acc = 0;
-        bool ok = true;
-        // pass 0: the cross-slice products of every term; pass 1: x0 y0 only
-        for (int pass = 0; pass < 2 && ok; ++pass) {
-            const uint32_t bytes_a = pass ? 2 * A_BLK * 2 : SM_A;
-            const uint32_t bytes_b = pass ? B_BLK * 2 : SM_B;
-            for (int t = 0; t < jd.nterm && ok; ++t) {
-                for (int g = 0; g < G && ok; ++g) {
-                    const bf16* srcA =
-                        Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + mt) * (long long)A_STAGE;
-                    const bf16* srcB =
-                        Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + nt) * (long long)B_STAGE;
-                    mbar_expect_tx(bar_ld, bytes_a + bytes_b);
-                    bulk_g2s(sA, srcA, bytes_a, bar_ld);
-                    bulk_g2s(sB, srcB, bytes_b, bar_ld);
-                    if (!mbar_wait(bar_ld, ph_ld)) {
-                        ok = false;
-                        mbar_wait(bar_ld, ph_ld);          // let copies in flight land before leaving
-                        break;
-                    }
-                    ph_ld ^= 1;
-                    tc_fence_after();
-                    const int npr = pass ? 1 : 5;
-                    for (int pr = 0; pr < npr; ++pr) {
-                        const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
-                        const uint64_t a_re = sdesc(sA + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
-                        const uint64_t a_im = sdesc(sA + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
-                        const uint64_t b_1 = sdesc(sB + j * B_BLK * 2, B_LBO, CM_SBO);
-                        const uint64_t b_2 = sdesc(sB + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
-                        mma_bf16(tmem, a_re, b_1, IDESC, acc);
-                        acc = 1;
-                        mma_bf16(tmem, a_im, b_2, IDESC, 1);
-                    }
-                    mma_commit(bar_mma);
-                    if (!mbar_wait(bar_mma, ph_mma)) {
-                        ok = false;
-                        mbar_wait(bar_mma, ph_mma);
-                        break;
-                    }
-                    ph_mma ^= 1;
-                }
-            }
-        }
-        if (!ok) { *s_ok = 0; atomicExch(err, 1); }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-
-    if (*s_ok) {
-        // TMEM lane = tile row.  Each warp moves its 32 rows x 32 columns
-        // through shared memory (the operand area is free now) and writes them
-        // as 16 8x8 pair blocks of the raw layout, 512 contiguous bytes per
-        // store instruction.
-        const int lane = threadIdx.x & 31;
-        const int YB = (ny + 7) / 8;
-        zf* xp = (zf*)smem + warp * 32 * 33;
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < 4; ++c) {
-            uint32_t re[32], im[32];
-            tmem_ld32(tbase + c * 32, re);
-            tmem_ld32(tbase + 128 + c * 32, im);
-            tmem_ld_wait();
-            #pragma unroll
-            for (int j = 0; j < 32; ++j) xp[lane * 33 + j] = mk(__uint_as_float(re[j]), __uint_as_float(im[j]));
-            __syncwarp();
-            const int e = 2 * lane, r8 = e >> 3, c8 = e & 7;          // two elements of an 8x8 block
-            #pragma unroll
-            for (int rg = 0; rg < 4; ++rg) {
-                const int yb = (mt * TM + warp * 32) / 8 + rg;
-                #pragma unroll
-                for (int cg = 0; cg < 4; ++cg) {
-                    const int ypb = (nt * TM + c * 32) / 8 + cg;
-                    if (yb < YB && ypb < YB) {
-                        const zf a0 = xp[(8 * rg + r8) * 33 + 8 * cg + c8], a1 = xp[(8 * rg + r8) * 33 + 8 * cg + c8 + 1];
-                        float4 v4 = make_float4(a0.x, a0.y, a1.x, a1.y);
-                        float4* dst = (float4*)(raw + ((((long long)job * YB + yb) * YB + ypb) * Nk + k) * 64 + e);
-                        __stcs(dst, v4);
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
-    }
-}
-
-// ------------------------------------- persistent, warp-specialised variant
+// ------------------------------------------------ tensor-core kernel
 // One CTA per SM walks the (wavenumber, contraction, tile) items
 // blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
 //   warp 0 (one lane): bulk copies of the operand blocks into a ring of NST
@@ -641,8 +510,6 @@ cudaError_t split_setup(cudaStream_t st)
         /* D  */ {3, {F_U, F_V, F_W, 0}, {0, 1, 2, 0}},
     };
     cudaError_t e = cudaMemcpyToSymbolAsync(c_tcjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void*)k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SM_TOTAL);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute((const void*)k_corr_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, SMP_TOTAL);
 }
