@@ -76,6 +76,10 @@ struct gke_plan_s {
     double mean_count = 0.0, snap_count = 0.0;
     bool mean_frozen = false, have_acc = false, finalized = false;
     std::vector<double> mean_sum_host;       // staging of the symmetrised mean sums
+    // host-output finalize: copies of finished term rows overlap the rest
+    cudaStream_t copy_st = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
+    void* host_terms = nullptr;
     std::string err;
 };
 
@@ -183,6 +187,13 @@ static std::vector<int> kept_indices(int n, const int u[4])
         if (all || d < u[0] || (d < u[1] ? d % u[2] == 0 : d % u[3] == 0)) k.push_back(m);
     }
     return k;
+}
+
+static bool is_pinned_host_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeHost;
 }
 
 static bool is_device_ptr(const void* p)
@@ -513,6 +524,8 @@ extern "C" void gke_destroy(gke_plan_t p)
     for (void* q : ptrs) if (q) cudaFree(q);
     split_free(p->split);
     for (auto& m : p->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto e : p->chunk_ev) cudaEventDestroy(e);
+    if (p->copy_st) cudaStreamDestroy(p->copy_st);
     for (auto e : p->spare) cudaEventDestroy(e);
     delete p;
 }
@@ -743,6 +756,28 @@ extern "C" gke_status gke_accumulate_snapshot(gke_plan_t p, const void* fields, 
     return snapshot_impl(p, f, nsnap);
 }
 
+// Host output: A, Phi_x, Phi_z and xi are final once the row pass of a pair
+// chunk has run (the Step-3 stencils change Phi_y, phi and the residual only),
+// so their rows of that chunk go to the host on a second stream while the
+// later chunks and the stencils run.
+static const int EARLY_TERMS[4] = {GKE_TERM_A, GKE_TERM_PHI_X, GKE_TERM_PHI_Z, GKE_TERM_XI};
+
+static void copy_chunk(void* ctx, long long p0, long long np)
+{
+    gke_plan_t p = (gke_plan_t)ctx;
+    if (!p->host_terms) return;
+    cudaEvent_t ev = take_event(p);
+    cudaEventRecord(ev, p->st);
+    cudaStreamWaitEvent(p->copy_st, ev, 0);
+    p->chunk_ev.push_back(ev);
+    const size_t row = (size_t)p->sep.nrz * p->sep.nrx * p->tsz;
+    for (int t : EARLY_TERMS) {
+        const size_t off = ((size_t)t * p->npair + (size_t)p0) * row;
+        cudaMemcpyAsync((char*)p->host_terms + off, (const char*)p->stage_terms + off, (size_t)np * row,
+                        cudaMemcpyDeviceToHost, p->copy_st);
+    }
+}
+
 static void terms_stage(gke_plan_t p, void* terms_dev)
 {
     const gke_desc& d = p->d;
@@ -761,6 +796,8 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     a.tw_x = f32 ? (const void*)p->ttw_xf : (const void*)p->ttw_xd;
     a.tw_z = f32 ? (const void*)p->ttw_zf : (const void*)p->ttw_zd;
     a.terms = terms_dev; a.sep = p->sep; a.st = p->st;
+    a.after_chunk = copy_chunk;
+    a.ctx = p;
     p->launches += terms_launch(a);
 }
 
@@ -801,18 +838,38 @@ extern "C" gke_status gke_finalize_terms(gke_plan_t p, void* terms, double* prof
     const bool dev_out = is_device_ptr(terms);
     const size_t tbytes = (size_t)gke_terms_bytes(p);
     void* tdev = terms;
+    // pinned host output: copies overlap the remaining work (pageable memory
+    // would make each early copy block the launching thread)
+    const bool early = !dev_out && is_pinned_host_ptr(terms);
     if (!dev_out) {
         if (!p->stage_terms) CUDA_TRY(p, dalloc(&p->stage_terms, tbytes / sizeof(double)));
+        if (early && !p->copy_st) CUDA_TRY(p, cudaStreamCreateWithFlags(&p->copy_st, cudaStreamNonBlocking));
         tdev = p->stage_terms;
+        p->host_terms = early ? terms : nullptr;
     }
     gke_status s = finalize_impl(p, tdev);
+    p->host_terms = nullptr;
     if (s != GKE_OK) return s;
-    if (!dev_out) CUDA_TRY(p, cudaMemcpyAsync(terms, tdev, tbytes, cudaMemcpyDeviceToHost, p->st));
+    if (!dev_out && !early) CUDA_TRY(p, cudaMemcpyAsync(terms, tdev, tbytes, cudaMemcpyDeviceToHost, p->st));
+    if (early) {
+        // the remaining terms (Phi_y, phi, residual) after the stencils; then
+        // the main stream waits for the early copies
+        const size_t row = (size_t)p->sep.nrz * p->sep.nrx * p->tsz * (size_t)p->npair;
+        for (int t : {GKE_TERM_PHI_Y, GKE_TERM_PHI, GKE_TERM_RESIDUAL})
+            CUDA_TRY(p, cudaMemcpyAsync((char*)terms + (size_t)t * row, (const char*)tdev + (size_t)t * row, row,
+                                        cudaMemcpyDeviceToHost, p->st));
+        cudaEvent_t done = take_event(p);
+        CUDA_TRY(p, cudaEventRecord(done, p->copy_st));
+        CUDA_TRY(p, cudaStreamWaitEvent(p->st, done, 0));
+        p->chunk_ev.push_back(done);
+    }
     if (profiles)
         CUDA_TRY(p, cudaMemcpyAsync(profiles, p->prof, GKE_NPROF * p->d.ny * sizeof(double), cudaMemcpyDefault, p->st));
     int bad = 0;
     CUDA_TRY(p, cudaMemcpyAsync(&bad, p->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, p->st));
     CUDA_TRY(p, cudaStreamSynchronize(p->st));
+    for (cudaEvent_t e : p->chunk_ev) p->spare.push_back(e);
+    p->chunk_ev.clear();
     p->finalized = true;
     if (p->d.precision == GKE_PREC_BF16X3) {
         gke_status ss = split_check(p->split, p->st, p->err);

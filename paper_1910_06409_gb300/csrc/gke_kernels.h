@@ -72,6 +72,9 @@ struct TermArgs {
     const void* comb; void* W; const int* pair_i; long long npair, pair_chunk;
     int ny, nz, nx, cw, rz; double inv_count; const double* prof; const void* tw_x; const void* tw_z;
     void* terms; float* spec; SepMap sep; cudaStream_t st;
+    // optional: called after the launches of each pair chunk [p0, p0 + np)
+    void (*after_chunk)(void* ctx, long long p0, long long np) = nullptr;
+    void* ctx = nullptr;
 };
 int terms_launch(const TermArgs& a);
 cudaError_t terms_set_attrs(int lim);

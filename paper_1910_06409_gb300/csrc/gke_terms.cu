@@ -294,6 +294,7 @@ int terms_launch_t(const TermArgs& a)
                 a.sep, (TO*)a.terms, a.spec);
         }
         launches += 2;
+        if (a.after_chunk) a.after_chunk(a.ctx, p0, np);
     }
     return launches;
 }
