@@ -78,6 +78,8 @@ struct gke_plan_s {
     std::vector<double> mean_sum_host;       // staging of the symmetrised mean sums
     // host-output finalize: copies of finished term rows overlap the rest
     cudaStream_t copy_st = nullptr;
+    cudaStream_t aux_st = nullptr;            // row passes of the inverse transforms
+    void* W2 = nullptr;                       // second transform scratch buffer
     std::vector<cudaEvent_t> chunk_ev;
     void* host_terms = nullptr;
     std::string err;
@@ -150,8 +152,8 @@ static void fornberg_d1(const double* x, int n, double z0, double* w)
 }
 
 static const int EPS_KCHUNK = 16;
-// bytes of inverse-transform scratch per pair chunk
-static const long long W_CHUNK_BYTES = 120LL << 20;
+// bytes of inverse-transform scratch per pair chunk (each of two buffers)
+static const long long W_CHUNK_BYTES = 192LL << 20;
 // bytes of contractions + per-pair spectra of one wavenumber chunk (chunked mode)
 static const size_t DEC_CHUNK_BYTES = (size_t)12 << 30;
 // above this size of one batch's contractions the plan runs in the chunked mode
@@ -382,13 +384,16 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         p->tsz = sizeof(double);
     }
     }
-    // pairs per inverse-transform chunk: the chunk's W scratch (W_CHUNK_BYTES)
-    // mostly stays in L2 between the two passes, and each launch still fills
-    // the GPU
+    // pairs per inverse-transform chunk (W_CHUNK_BYTES of scratch W, two
+    // buffers): the column pass of one chunk overlaps the row pass of the
+    // previous one on the auxiliary stream
     const int nxth = p->nxt / 2 + 1, nrzt = p->sep.nrz;
     p->pair_chunk = std::max<long long>(
         1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * nrzt * nxth * p->csz)));
     ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * nrzt * nxth * p->csz);
+    ALLOCB(p->W2, (size_t)p->pair_chunk * NTERM * nrzt * nxth * p->csz);
+    if ((e = cudaStreamCreateWithFlags(&p->aux_st, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(GKE_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
     ALLOC(p->tw_xd, d.nx);
     ALLOC(p->tw_zd, d.nz);
     ALLOC(p->tw_xf, d.nx);
@@ -514,6 +519,8 @@ extern "C" void gke_destroy(gke_plan_t p)
     if (!p) return;
     if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
     if (p->fold_owned) cudaFree(p->fold);
+    if (p->W2) cudaFree(p->W2);
+    if (p->aux_st) cudaStreamDestroy(p->aux_st);
     if (p->dec) {
         void* extra[] = {p->cchunk, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
@@ -762,12 +769,12 @@ extern "C" gke_status gke_accumulate_snapshot(gke_plan_t p, const void* fields, 
 // later chunks and the stencils run.
 static const int EARLY_TERMS[4] = {GKE_TERM_A, GKE_TERM_PHI_X, GKE_TERM_PHI_Z, GKE_TERM_XI};
 
-static void copy_chunk(void* ctx, long long p0, long long np)
+static void copy_chunk(void* ctx, long long p0, long long np, cudaStream_t st)
 {
     gke_plan_t p = (gke_plan_t)ctx;
     if (!p->host_terms) return;
     cudaEvent_t ev = take_event(p);
-    cudaEventRecord(ev, p->st);
+    cudaEventRecord(ev, st);
     cudaStreamWaitEvent(p->copy_st, ev, 0);
     p->chunk_ev.push_back(ev);
     const size_t row = (size_t)p->sep.nrz * p->sep.nrx * p->tsz;
@@ -798,6 +805,8 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     a.terms = terms_dev; a.sep = p->sep; a.st = p->st;
     a.after_chunk = copy_chunk;
     a.ctx = p;
+    a.st2 = p->aux_st;
+    a.W2 = p->W2;
     p->launches += terms_launch(a);
 }
 

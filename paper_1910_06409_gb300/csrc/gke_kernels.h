@@ -72,8 +72,12 @@ struct TermArgs {
     const void* comb; void* W; const int* pair_i; long long npair, pair_chunk;
     int ny, nz, nx, cw, rz; double inv_count; const double* prof; const void* tw_x; const void* tw_z;
     void* terms; float* spec; SepMap sep; cudaStream_t st;
-    // optional: called after the launches of each pair chunk [p0, p0 + np)
-    void (*after_chunk)(void* ctx, long long p0, long long np) = nullptr;
+    // optional: a second stream and scratch buffer (column and row passes of
+    // successive chunks overlap); a callback after the launches of each pair
+    // chunk [p0, p0 + np), given the stream its row pass ran on
+    cudaStream_t st2 = nullptr;
+    void* W2 = nullptr;
+    void (*after_chunk)(void* ctx, long long p0, long long np, cudaStream_t st) = nullptr;
     void* ctx = nullptr;
 };
 int terms_launch(const TermArgs& a);

@@ -257,44 +257,73 @@ int terms_launch_t(const TermArgs& a)
     typedef cplx<TF> C;
     const int nxh = a.nx / 2 + 1;
     const bool us = a.sep.zpos != nullptr || a.sep.xpos != nullptr;      // undersampled output
+    // With a second stream and a second scratch buffer, the column pass of
+    // chunk c + 1 runs on a.st while the row pass of chunk c runs on a.st2:
+    // the GPU stays full with chunks small enough for W to stay in L2.
+    const bool two = a.st2 != nullptr && a.W2 != nullptr;
+    cudaEvent_t ev_col[2] = {nullptr, nullptr}, ev_row[2] = {nullptr, nullptr};
+    if (two)
+        for (int i = 0; i < 2; ++i) {
+            cudaEventCreateWithFlags(&ev_col[i], cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&ev_row[i], cudaEventDisableTiming);
+        }
     int launches = 0;
-    for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk) {
+    long long c = 0;
+    for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk, ++c) {
         const long long np = a.pair_chunk < a.npair - p0 ? a.pair_chunk : a.npair - p0;
+        const int buf = two ? (int)(c & 1) : 0;
+        C* W = (C*)(buf ? a.W2 : a.W);
+        cudaStream_t sc = a.st, sr = two ? a.st2 : a.st;
+        if (two && c >= 2) cudaStreamWaitEvent(sc, ev_row[buf], 0);     // W buffer free again
         if (a.nz == 256) {
             constexpr int CWR = 16;
             const dim3 g((nxh + CWR - 1) / CWR, NTERM, (unsigned)np);
             const size_t sh = (256 + 16 * (16 * CWR + 1)) * sizeof(C);
             if (us)
-                k_terms_colpass_r<TF, TB, 16, 16, true><<<g, CWR * 16, sh, a.st>>>(
-                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, (C*)a.W);
+                k_terms_colpass_r<TF, TB, 16, 16, true><<<g, CWR * 16, sh, sc>>>(
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, W);
             else
-                k_terms_colpass_r<TF, TB, 16, 16, false><<<g, CWR * 16, sh, a.st>>>(
-                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, (C*)a.W);
+                k_terms_colpass_r<TF, TB, 16, 16, false><<<g, CWR * 16, sh, sc>>>(
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, W);
         } else {
             k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
-                                      (1 + 2 * a.cw) * a.nz * sizeof(C), a.st>>>(
-                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, (const C*)a.tw_z, a.sep, (C*)a.W);
+                                      (1 + 2 * a.cw) * a.nz * sizeof(C), sc>>>(
+                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, (const C*)a.tw_z, a.sep, W);
+        }
+        if (two) {
+            cudaEventRecord(ev_col[buf], sc);
+            cudaStreamWaitEvent(sr, ev_col[buf], 0);
         }
         if (a.nx == 256) {
             constexpr int RZR = 4;
             const dim3 g((a.sep.nrz + RZR - 1) / RZR, (unsigned)np);
             const size_t sh = (256 + RZR * 16 * 17) * sizeof(C);
             if (us)
-                k_terms_rowpass_r<TF, TO, 16, 16, true><<<g, RZR * 16, sh, a.st>>>(
-                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
+                k_terms_rowpass_r<TF, TO, 16, 16, true><<<g, RZR * 16, sh, sr>>>(
+                    W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
                     (TO*)a.terms, a.spec);
             else
-                k_terms_rowpass_r<TF, TO, 16, 16, false><<<g, RZR * 16, sh, a.st>>>(
-                    (const C*)a.W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
+                k_terms_rowpass_r<TF, TO, 16, 16, false><<<g, RZR * 16, sh, sr>>>(
+                    W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
                     (TO*)a.terms, a.spec);
         } else {
             k_terms_rowpass<TF, TO><<<dim3((a.sep.nrz + a.rz - 1) / a.rz, (unsigned)np), 256,
-                                      (1 + 8 * a.rz) * a.nx * sizeof(C), a.st>>>(
-                (const C*)a.W, a.pair_i, p0, a.npair, a.ny, a.nx, a.rz, a.inv_count, a.prof, (const C*)a.tw_x,
+                                      (1 + 8 * a.rz) * a.nx * sizeof(C), sr>>>(
+                W, a.pair_i, p0, a.npair, a.ny, a.nx, a.rz, a.inv_count, a.prof, (const C*)a.tw_x,
                 a.sep, (TO*)a.terms, a.spec);
         }
+        if (two) cudaEventRecord(ev_row[buf], sr);
         launches += 2;
-        if (a.after_chunk) a.after_chunk(a.ctx, p0, np);
+        if (a.after_chunk) a.after_chunk(a.ctx, p0, np, sr);
+    }
+    if (two) {
+        // join: the main stream waits for the last row passes
+        cudaStreamWaitEvent(a.st, ev_row[0], 0);
+        cudaStreamWaitEvent(a.st, ev_row[1], 0);
+        for (int i = 0; i < 2; ++i) {
+            cudaEventDestroy(ev_col[i]);
+            cudaEventDestroy(ev_row[i]);
+        }
     }
     return launches;
 }
