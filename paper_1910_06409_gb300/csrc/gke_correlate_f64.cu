@@ -3,13 +3,14 @@
 // For every wavenumber k the paper's Parseval step (Sec. 3.1, Eq. 8-9) needs
 // sums over snapshots of conj(a_hat(y, k)) b_hat(y', k) for the field pairs
 // of the expansion (Eq. 7).  Per k these are small dense complex products
-//   S(y, y') = sum_t c_t sum_s conj(A_t[s][y]) B_t[s][y']
+//   S(y, y') = sum_t sum_s conj(A_t[s][y]) B_t[s][y']
 // over the operand blocks Xop[f][k][s][y].  The contractions ("jobs"):
 //   D   = sum_i conj(u_i) u_i                    (Hermitian: pairs y <= y')
 //   E   = conj(u) v,   F = conj(p) v
 //   Gx  = conj(q) u + 2 [conj(uu) u + conj(uv) v + conj(uw) w]
 //   QV  = conj(q) v,   X2 = 2 [conj(uv) u + conj(vv) v + conj(vw) w]
 //   Gz  = conj(q) w + 2 [conj(uw) u + conj(vw) v + conj(ww) w]
+// (the operand blocks of uu .. vw already hold the factor 2: k_col_forward)
 // (the y-flux triple terms are QV + X2 and QV - X2, formed later).
 //
 // CTA = one wavenumber of a chunk and one job; it walks tiles of (y, y'), each thread
@@ -24,20 +25,20 @@
 
 namespace gke {
 
-struct JobDesc { int nterm; int fa[4]; int fb[4]; double c[4]; };
+struct JobDesc { int nterm; int fa[4]; int fb[4]; };
 
 __constant__ JobDesc c_jobs[NJSQ + 1];   // index NJSQ = D
 
 void upload_jobs(cudaStream_t st)
 {
     JobDesc h[NJSQ + 1] = {
-        /* E  */ {1, {F_U, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
-        /* F  */ {1, {F_P, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
-        /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {F_U, F_U, F_V, F_W}, {1, 2, 2, 2}},
-        /* QV */ {1, {F_Q, 0, 0, 0}, {F_V, 0, 0, 0}, {1, 0, 0, 0}},
-        /* X2 */ {3, {F_UV, F_VV, F_VW, 0}, {F_U, F_V, F_W, 0}, {2, 2, 2, 0}},
-        /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {F_W, F_U, F_V, F_W}, {1, 2, 2, 2}},
-        /* D  */ {3, {F_U, F_V, F_W, 0}, {F_U, F_V, F_W, 0}, {1, 1, 1, 0}},
+        /* E  */ {1, {F_U, 0, 0, 0}, {F_V, 0, 0, 0}},
+        /* F  */ {1, {F_P, 0, 0, 0}, {F_V, 0, 0, 0}},
+        /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {F_U, F_U, F_V, F_W}},
+        /* QV */ {1, {F_Q, 0, 0, 0}, {F_V, 0, 0, 0}},
+        /* X2 */ {3, {F_UV, F_VV, F_VW, 0}, {F_U, F_V, F_W, 0}},
+        /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {F_W, F_U, F_V, F_W}},
+        /* D  */ {3, {F_U, F_V, F_W, 0}, {F_U, F_V, F_W, 0}},
     };
     cudaMemcpyToSymbolAsync(c_jobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
 }
@@ -84,7 +85,6 @@ k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int
             for (int t = 0; t < jd.nterm; ++t) {
                 const C* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
                 const C* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
-                const T c = (T)jd.c[t];
                 for (int s0 = 0; s0 < ns; s0 += SCH) {
                     __syncthreads();
                     for (int e = threadIdx.x; e < SCH * CT; e += blockDim.x) {
@@ -93,7 +93,7 @@ k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int
                         C va = mk((T)0, (T)0), vb = mk((T)0, (T)0);
                         if (s < ns && y0 + yy < ny) va = A[(long long)s * ny + y0 + yy];
                         if (s < ns && y1 + yy < ny) vb = B[(long long)s * ny + y1 + yy];
-                        As[ss][yy] = c * va;
+                        As[ss][yy] = va;
                         Bs[ss][yy] = vb;
                     }
                     __syncthreads();
@@ -140,8 +140,7 @@ k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int
         for (int t = 0; t < jd.nterm; ++t) {
             const C* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
             const C* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
-            const T c = (T)jd.c[t];
-            for (int s = 0; s < ns; ++s) cmac_conj(acc, c * A[(long long)s * ny + y], B[(long long)s * ny + yp]);
+            for (int s = 0; s < ns; ++s) cmac_conj(acc, A[(long long)s * ny + y], B[(long long)s * ny + yp]);
         }
         raw[raw_index(job, kl, y, yp, Kc, (ny + 7) / 8)] = acc;
     }

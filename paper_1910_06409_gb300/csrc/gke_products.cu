@@ -159,7 +159,8 @@ k_col_forward_r(const cplx<TF>* __restrict__ H, int ny, int nxh, int CW, int YB,
     __syncthreads();
     fft2l<TF, N1, N2, false>(v, lane, xs + (yl * CW + c), N2 * nseq + 1, nseq, stw);
     if (live) {
-        const TF inz = (TF)1 / (TF)N;
+        // the pair products (uu .. vw) carry the factor 2 of the expansion
+        const TF inz = (j < 6 ? (TF)2 : (TF)1) / (TF)N;
         #pragma unroll
         for (int m = 0; m < N1; ++m) {
             const long long k = (long long)(lane + N2 * m) * nxh + kx;
@@ -346,8 +347,9 @@ k_row_products_r(const cplx<TF>* __restrict__ G, int ny, int nz, const cplx<TF>*
 }
 
 // ---------------------------------- forward transform along z (columns)
-// One snapshot: Xop[4 + j][k][s][y] = (1/nz) sum_z H[j][y][z][kx] e^{-i kz z}
-// for the seven products.  CTA = CW kx columns x YB planes of one product;
+// One snapshot: Xop[4 + j][k][s][y] = (c_j/nz) sum_z H[j][y][z][kx] e^{-i kz z}
+// for the seven products, c_j = 2 for the pair products uu .. vw (the factor
+// 2 of the correlation expansion, Eq. 7) and 1 for q.  CTA = CW kx columns x YB planes of one product;
 // dynamic shared memory (1 + 2 CW YB) nz complex.
 template <typename TF>
 __global__ void k_col_forward(const cplx<TF>* __restrict__ H, int ny, int nz, int nxh, int CW, int YB,
@@ -370,7 +372,7 @@ __global__ void k_col_forward(const cplx<TF>* __restrict__ H, int ny, int nz, in
         b0[(yy * CW + c) * nz + z] = v;
     }
     const C* res = fft_block<TF, false>(b0, b1, nz, nb, nz, stw);
-    const TF inz = (TF)1 / (TF)nz;
+    const TF inz = (j < 6 ? (TF)2 : (TF)1) / (TF)nz;     // pair products carry the factor 2 of the expansion
     for (int t = threadIdx.x; t < nb * nz; t += blockDim.x) {
         int yy = t % YB, rem = t / YB, c = rem % CW, kz = rem / CW;
         int kx = kx0 + c, y = y0 + yy;

@@ -154,8 +154,8 @@ __device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
     s2 = __float2bfloat16_rn(r2);
 }
 
-// Aop[k][f][g][mt][slice * 2 + part][A_BLK]; products (uu .. vw) carry the
-// factor 2 of the expansion; rows >= cov and snapshots >= ns are zero.  Thread
+// Aop[k][f][g][mt][slice * 2 + part][A_BLK] (the operands of uu .. vw carry the
+// factor 2 of the expansion already); rows >= cov and snapshots >= ns are zero.  Thread
 // = one row x 8 snapshots: the 8 values of a core-matrix row are contiguous,
 // so each slice goes out as one 16-byte store.
 struct alignas(16) bf16x8 { bf16 v[8]; };
@@ -168,7 +168,6 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
     const int g = (int)(b % G); b /= G;
     const int f = (int)(b % NFIELD);
     const int k = (int)(b / NFIELD);
-    const float sc = (f >= F_UU && f <= F_VW) ? 2.f : 1.f;
     bf16* dst = Aop + ((((long long)k * NFIELD + f) * G + g) * MT + mt) * (long long)A_STAGE;
     const int r = threadIdx.x % TM, kc = threadIdx.x / TM;          // blockDim = 2 TM
     const int y = mt * TM + r;
@@ -178,8 +177,8 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
         const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
         if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k0 + k) * ns + s) * ny + y];
-        split3(sc * v.x, o[0].v[e], o[2].v[e], o[4].v[e]);      // slices of the real part
-        split3(sc * v.y, o[1].v[e], o[3].v[e], o[5].v[e]);      // slices of the imaginary part
+        split3(v.x, o[0].v[e], o[2].v[e], o[4].v[e]);      // slices of the real part
+        split3(v.y, o[1].v[e], o[3].v[e], o[5].v[e]);      // slices of the imaginary part
     }
     const int idx = cm_index(r, kc * 8, TM);
     #pragma unroll
@@ -460,12 +459,11 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
         for (int t = 0; t < jd.nterm; ++t) {
             const int d = row_edge ? y - cov : yp - cov;
             if (d < 4 && !nz_edge[row_edge ? jd.fa[t] : jd.fb[t]][d]) continue;   // zero factor
-            const float c = (jd.fa[t] >= F_UU && jd.fa[t] <= F_VW) ? 2.f : 1.f;
             const zf* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
             const zf* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
             for (int s = 0; s < ns; ++s) {
                 const zf a = A[(long long)s * ny + y], b = B[(long long)s * ny + yp];
-                const float ar = c * a.x, ai = c * a.y;
+                const float ar = a.x, ai = a.y;
                 sr = fmaf(ar, b.x, fmaf(ai, b.y, sr));
                 si = fmaf(ar, b.y, fmaf(-ai, b.x, si));
             }
