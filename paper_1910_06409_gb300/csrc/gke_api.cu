@@ -49,6 +49,8 @@ struct gke_plan_s {
     // device workspaces; Xop, G, H, raw and W hold complex<TF>, TF = double on
     // the plain path and float on the split path
     void *Xop = nullptr, *G = nullptr, *H = nullptr, *raw = nullptr, *W = nullptr;
+    void *G2 = nullptr, *H2 = nullptr;        // second products buffers (odd snapshots)
+    double* part2 = nullptr;
     // per-pair term spectra summed over batches: FP64 (comb) on the plain path;
     // on the split path the first batch goes to comb32 and a second batch
     // promotes the sum to FP64 (comb, allocated then)
@@ -347,6 +349,8 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOCB(p->Xop, (size_t)NFIELD * Nk * ns * ny * p->csz);
     ALLOCB(p->G, (size_t)4 * ny * plane * p->csz);
     ALLOCB(p->H, (size_t)7 * ny * plane * p->csz);
+    ALLOCB(p->G2, (size_t)4 * ny * plane * p->csz);
+    ALLOCB(p->H2, (size_t)7 * ny * plane * p->csz);
     const size_t raw_per_k = (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * p->csz;
     if (p->dec) {
         // chunk rows R: a power of two dividing nzd, at most nzd / 2, with the
@@ -422,6 +426,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         size_t a2 = (size_t)ny * ((Nk + EPS_KCHUNK - 1) / EPS_KCHUNK);
         p->part_count = std::max(a1, a2);
         ALLOC(p->part, p->part_count);
+        ALLOC(p->part2, p->part_count);
     }
     if (d.precision == GKE_PREC_BF16X3) {
         gke_status s = split_alloc(p->split, ny, ns, p->Kc);
@@ -520,6 +525,10 @@ extern "C" void gke_destroy(gke_plan_t p)
     if (p->st) cudaStreamSynchronize(p->st); else cudaDeviceSynchronize();
     if (p->fold_owned) cudaFree(p->fold);
     if (p->W2) cudaFree(p->W2);
+    {
+        void* more[] = {p->G2, p->H2, p->part2};
+        for (void* q : more) if (q) cudaFree(q);
+    }
     if (p->aux_st) cudaStreamDestroy(p->aux_st);
     if (p->dec) {
         void* extra[] = {p->cchunk, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
@@ -658,6 +667,7 @@ static void products_stage(gke_plan_t p, const zd* f, int ns)
     a.part = p->part; a.stats = p->stats; a.nonfinite = p->nonfinite;
     a.cw_ci = t.cw_ci; a.rz_rp = t.rz_rp; a.cw_cf = t.cw_cf; a.yb_cf = t.yb_cf; a.eps_kchunk = EPS_KCHUNK;
     a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = p->fdw; a.fdl0 = p->fdl0; a.st = p->st;
+    a.st2 = p->aux_st; a.G2 = p->G2; a.H2 = p->H2; a.part2 = p->part2;
     p->launches += f32 ? products_launch<float>(a) : products_launch<double>(a);
 }
 

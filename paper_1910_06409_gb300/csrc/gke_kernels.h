@@ -26,6 +26,9 @@ struct ProdArgs {
     int cw_ci, rz_rp, cw_cf, yb_cf, eps_kchunk;
     double Lx, Lz; const double* fdw; const int* fdl0;
     cudaStream_t st;
+    // optional second stream and buffers: odd snapshots run there
+    cudaStream_t st2 = nullptr;
+    void* G2 = nullptr; void* H2 = nullptr; double* part2 = nullptr;
 };
 template <typename TF> int products_launch(const ProdArgs& a);
 cudaError_t products_set_attrs(int lim);

@@ -452,37 +452,75 @@ int products_launch(const ProdArgs& a)
     k_load_linear<TF><<<dim3((Nk + 31) / 32, (ny + 31) / 32, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk,
                                                                                            a.mean, Xop, a.nonfinite);
     ++launches;
+    // With a second stream and second G, H, part buffers, snapshot s runs on
+    // stream s % 2, so the transforms of two snapshots overlap; the row sums
+    // are still reduced into stats on the main stream in snapshot order.
+    const bool two = a.st2 != nullptr && a.G2 != nullptr && a.H2 != nullptr && a.part2 != nullptr;
+    cudaEvent_t ev_start = nullptr, ev_rp[2] = {nullptr, nullptr}, ev_red[2] = {nullptr, nullptr},
+                ev_end = nullptr;
+    if (two) {
+        cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&ev_end, cudaEventDisableTiming);
+        for (int i = 0; i < 2; ++i) {
+            cudaEventCreateWithFlags(&ev_rp[i], cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&ev_red[i], cudaEventDisableTiming);
+        }
+        cudaEventRecord(ev_start, st);                   // the second stream starts after earlier work
+        cudaStreamWaitEvent(a.st2, ev_start, 0);
+    }
     for (int s = 0; s < ns; ++s) {
         const zd* fs = a.fields + (size_t)s * 4 * ny * Nk;
+        const int b = two ? (s & 1) : 0;
+        cudaStream_t ss = b ? a.st2 : st;
+        C* G = (C*)(b ? a.G2 : a.G);
+        C* H = (C*)(b ? a.H2 : a.H);
+        double* part = b ? a.part2 : a.part;
+        if (two && s >= 2) cudaStreamWaitEvent(ss, ev_red[b], 0);     // part[b] read by the last reduction
         if (nz == 256) {
             constexpr int CWR = 16;
             k_col_inverse_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, ny, 4), CWR * 16,
-                                          (256 + 16 * (16 * CWR + 1)) * sizeof(C), st>>>(
-                fs, ny, nxh, CWR, a.mean, (const C*)a.tw_z, (C*)a.G);
+                                          (256 + 16 * (16 * CWR + 1)) * sizeof(C), ss>>>(
+                fs, ny, nxh, CWR, a.mean, (const C*)a.tw_z, G);
         } else {
-            k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), st>>>(
-                fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, (C*)a.G);
+            k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), ss>>>(
+                fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, G);
         }
         const int nrb = (nx == 256) ? (nz + 3) / 4 : (nz + a.rz_rp - 1) / a.rz_rp;
         if (nx == 256) {
             k_row_products_r<TF, 16, 16, 4><<<dim3(nrb, ny), 4 * 16, (256 + 4 * 16 * 17 + 4 * 4 * 256) * sizeof(C),
-                                              st>>>((const C*)a.G, ny, nz, (const C*)a.tw_x, (C*)a.H, a.part);
+                                              ss>>>((const C*)G, ny, nz, (const C*)a.tw_x, H, part);
         } else {
-            k_row_products<TF><<<dim3(nrb, ny), 256, (1 + 8 * a.rz_rp) * nx * sizeof(C), st>>>(
-                (const C*)a.G, ny, nz, nx, a.rz_rp, (const C*)a.tw_x, (C*)a.H, a.part);
+            k_row_products<TF><<<dim3(nrb, ny), 256, (1 + 8 * a.rz_rp) * nx * sizeof(C), ss>>>(
+                (const C*)G, ny, nz, nx, a.rz_rp, (const C*)a.tw_x, H, part);
         }
-        k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(a.part, 6 * ny, nrb, a.stats);
+        if (two) {
+            cudaEventRecord(ev_rp[b], ss);
+            cudaStreamWaitEvent(st, ev_rp[b], 0);
+        }
+        k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(part, 6 * ny, nrb, a.stats);
+        if (two) cudaEventRecord(ev_red[b], st);
         if (nz == 256) {
             constexpr int CWR = 4, YBR = 4;
             k_col_forward_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, (ny + YBR - 1) / YBR, 7), CWR * YBR * 16,
-                                          (256 + 16 * (16 * CWR * YBR + 1)) * sizeof(C), st>>>(
-                (const C*)a.H, ny, nxh, CWR, YBR, s, ns, (const C*)a.tw_z, Xop);
+                                          (256 + 16 * (16 * CWR * YBR + 1)) * sizeof(C), ss>>>(
+                (const C*)H, ny, nxh, CWR, YBR, s, ns, (const C*)a.tw_z, Xop);
         } else {
             k_col_forward<TF><<<dim3((nxh + a.cw_cf - 1) / a.cw_cf, (ny + a.yb_cf - 1) / a.yb_cf, 7), 256,
-                                (1 + 2 * a.cw_cf * a.yb_cf) * nz * sizeof(C), st>>>(
-                (const C*)a.H, ny, nz, nxh, a.cw_cf, a.yb_cf, s, ns, (const C*)a.tw_z, Xop);
+                                (1 + 2 * a.cw_cf * a.yb_cf) * nz * sizeof(C), ss>>>(
+                (const C*)H, ny, nz, nxh, a.cw_cf, a.yb_cf, s, ns, (const C*)a.tw_z, Xop);
         }
         launches += 4;
+    }
+    if (two) {
+        // join: the main stream waits for the second stream's last transforms
+        cudaEventRecord(ev_end, a.st2);
+        cudaStreamWaitEvent(st, ev_end, 0);
+        cudaEventDestroy(ev_start);
+        cudaEventDestroy(ev_end);
+        for (int i = 0; i < 2; ++i) {
+            cudaEventDestroy(ev_rp[i]);
+            cudaEventDestroy(ev_red[i]);
+        }
     }
     const int neb = (Nk + a.eps_kchunk - 1) / a.eps_kchunk;
     // one thread per wall-normal row: no second pass for a ragged last row
