@@ -157,7 +157,7 @@ static const int EPS_KCHUNK = 16;
 // bytes of inverse-transform scratch per pair chunk (each of two buffers)
 static const long long W_CHUNK_BYTES = 192LL << 20;
 // bytes of contractions + per-pair spectra of one wavenumber chunk (chunked mode)
-static const size_t DEC_CHUNK_BYTES = (size_t)12 << 30;
+static const size_t DEC_CHUNK_BYTES = (size_t)32 << 30;
 // above this size of one batch's contractions the plan runs in the chunked mode
 static const size_t CHUNKED_RAW_BYTES = (size_t)96 << 30;
 
@@ -357,7 +357,9 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         // chunk's contractions and spectra within DEC_CHUNK_BYTES
         const size_t per_row = (size_t)p->nxh * (raw_per_k + (size_t)p->npair_tri * NTERM * p->csz);
         p->R = std::max(1, p->nzt / 2);
-        while (p->R > 1 && (size_t)p->R * per_row > DEC_CHUNK_BYTES) p->R /= 2;
+        while (p->R > 1 && ((size_t)p->R * per_row > DEC_CHUNK_BYTES ||
+                            fold_dec_smem(!f32, p->R, d.nx, p->wedge) > (size_t)smem_limit()))
+            p->R /= 2;
         p->Kc = p->R * p->nxh;
         ALLOCB(p->raw, raw_per_k * p->Kc);
         ALLOCB(p->cchunk, (size_t)p->npair_tri * NTERM * p->Kc * p->csz);

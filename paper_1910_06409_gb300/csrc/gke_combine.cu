@@ -222,28 +222,41 @@ int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long 
 // bin and gathers both, so the sums are deterministic.  With the wedge the
 // spectra are first averaged with the image pair's (as in k_mirror_fold).
 template <typename TC>
-__global__ void k_fold_dec(const cplx<TC>* __restrict__ cchunk, const int* __restrict__ pair_o, int wedge, int ny,
-                           int nz, int nx, int nzd, int nxd, int kz0, int R, zd* __restrict__ dec)
+__global__ void __launch_bounds__(256)
+k_fold_dec(const cplx<TC>* __restrict__ cchunk, const int* __restrict__ pair_o, int wedge, int ny, int nz, int nx,
+           int nzd, int nxd, int kz0, int R, zd* __restrict__ dec)
 {
+    typedef cplx<TC> C;
+    extern __shared__ __align__(16) unsigned char sh_fold[];
     const int nxh = nx / 2 + 1, nxdh = nxd / 2 + 1, Kc = R * nxh;
     const long long row = blockIdx.x;                 // po * NTERM + t
     const long long po = row / NTERM;
     const int t = (int)(row - po * NTERM);
     const int i1 = pair_o[2 * po], i2 = pair_o[2 * po + 1];
-    const cplx<TC>* a = cchunk + (pair_index(i1, i2, ny) * NTERM + t) * (long long)Kc;
-    const cplx<TC>* b = wedge ? cchunk + (pair_index(ny - 1 - i2, ny - 1 - i1, ny) * NTERM + t) * (long long)Kc
-                              : nullptr;
-    const double sg = c_sigma[t];
+    // the chunk's spectra of the pair (and of its image pair on the wedge),
+    // read once, coalesced, into shared memory
+    C* sa = (C*)sh_fold;
+    C* sb = sa + Kc;
+    const C* a = cchunk + (pair_index(i1, i2, ny) * NTERM + t) * (long long)Kc;
+    for (int i = threadIdx.x; i < Kc; i += blockDim.x) sa[i] = ld_stream(a + i);
+    if (wedge) {
+        const C* b = cchunk + (pair_index(ny - 1 - i2, ny - 1 - i1, ny) * NTERM + t) * (long long)Kc;
+        for (int i = threadIdx.x; i < Kc; i += blockDim.x) sb[i] = ld_stream(b + i);
+    }
+    __syncthreads();
+    // arithmetic in TC (FP32 on the FP32 paths: FP64 work costs ~60 FP32
+    // operations here); the chunk's partial sums join the FP64 accumulator
+    const TC sg = (TC)c_sigma[t], hf = (TC)0.5;
     // term spectrum at chunk row r, column kx (mirror-averaged on the wedge)
-    auto F = [&](int r, int kx) -> zd {
-        const long long kl = (long long)r * nxh + kx;
-        const cplx<TC> va = a[kl];
-        if (!wedge) return mk((double)va.x, (double)va.y);
-        const cplx<TC> vb = b[kl];
-        return mk(0.5 * ((double)va.x + sg * (double)vb.x), 0.5 * ((double)va.y - sg * (double)vb.y));
+    auto F = [&](int r, int kx) -> C {
+        const int kl = r * nxh + kx;
+        const C va = sa[kl];
+        if (!wedge) return va;
+        const C vb = sb[kl];
+        return mk(hf * (va.x + sg * vb.x), hf * (va.y - sg * vb.y));
     };
     const int dlo = kz0 % nzd;                        // direct coarse rows: [dlo, dlo + R)
-    for (int it = blockIdx.y * blockDim.x + threadIdx.x; it < 2 * R * nxdh; it += gridDim.y * blockDim.x) {
+    for (int it = threadIdx.x; it < 2 * R * nxdh; it += blockDim.x) {
         const int br = it / nxdh, kxd = it - br * nxdh;
         int kzd;
         if (br < R) {
@@ -255,40 +268,44 @@ __global__ void k_fold_dec(const cplx<TC>* __restrict__ cchunk, const int* __res
         const int od = (kzd - kz0 % nzd + nzd) % nzd;              // kz0 + od = kzd (mod nzd)
         const int oi = ((nzd - kzd) % nzd - kz0 % nzd + nzd) % nzd; // kz0 + oi = -kzd (mod nzd)
         const int rd = od < R ? od : -1, ri = oi < R ? oi : -1;     // chunk rows
-        double ax = 0.0, ay = 0.0;
+        TC ax = 0, ay = 0;
         for (int ix = 0; ix < nx / nxd; ++ix) {
             const int kxf = kxd + ix * nxd;
             const bool self = (kxf == 0 || 2 * kxf == nx);
             if (rd >= 0 && 2 * kxf <= nx) {
-                const zd v = F(rd, kxf);
-                const double h = self ? 0.5 : 1.0;
+                const C v = F(rd, kxf);
+                const TC h = self ? hf : (TC)1;
                 ax += h * v.x;
                 ay += h * v.y;
             }
             if (ri >= 0 && (self || 2 * kxf > nx)) {
-                const zd v = F(ri, self ? kxf : nx - kxf);
-                const double h = self ? 0.5 : 1.0;
+                const C v = F(ri, self ? kxf : nx - kxf);
+                const TC h = self ? hf : (TC)1;
                 ax += h * v.x;
                 ay -= h * v.y;
             }
         }
         zd* o = dec + row * (long long)nzd * nxdh + (long long)kzd * nxdh + kxd;
-        o->x += ax;
-        o->y += ay;
+        o->x += (double)ax;
+        o->y += (double)ay;
     }
+}
+
+size_t fold_dec_smem(bool c64, int R, int nx, bool wedge)
+{
+    return (size_t)R * (nx / 2 + 1) * (c64 ? sizeof(zd) : sizeof(zf)) * (wedge ? 2 : 1);
 }
 
 int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
                     int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st)
 {
-    const int nxdh = nxd / 2 + 1;
-    dim3 g((unsigned)(nout * NTERM), (unsigned)std::min(16, (2 * R * nxdh + 255) / 256));
+    const size_t sh = fold_dec_smem(c64, R, nx, wedge != 0);
     if (c64)
-        k_fold_dec<double><<<g, 256, 0, st>>>((const zd*)cchunk, pair_o, wedge, ny, nz, nx, nzd, nxd, kz0, R,
-                                              (zd*)dec);
+        k_fold_dec<double><<<(unsigned)(nout * NTERM), 256, sh, st>>>((const zd*)cchunk, pair_o, wedge, ny, nz, nx,
+                                                                      nzd, nxd, kz0, R, (zd*)dec);
     else
-        k_fold_dec<float><<<g, 256, 0, st>>>((const zf*)cchunk, pair_o, wedge, ny, nz, nx, nzd, nxd, kz0, R,
-                                             (zd*)dec);
+        k_fold_dec<float><<<(unsigned)(nout * NTERM), 256, sh, st>>>((const zf*)cchunk, pair_o, wedge, ny, nz, nx,
+                                                                     nzd, nxd, kz0, R, (zd*)dec);
     return 1;
 }
 
@@ -328,8 +345,15 @@ cudaError_t combine_set_attrs()
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(true));
         if (e != cudaSuccess) return e;
     }
-    return cudaFuncSetAttribute((const void*)k_combine<double, double, double>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(false));
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_combine<double, double, double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(false));
+    if (e != cudaSuccess) return e;
+    int dev = 0, lim = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    e = cudaFuncSetAttribute((const void*)k_fold_dec<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute((const void*)k_fold_dec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 }  // namespace gke

@@ -39,6 +39,7 @@ int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, in
                    cudaStream_t st);
 int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
                     int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st);
+size_t fold_dec_smem(bool c64, int R, int nx, bool wedge);
 int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st);
 int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long nout, int ny, int Nk, void* out,
                        cudaStream_t st);
