@@ -607,8 +607,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true",
                     help="with --precision f64: skip the split-BF16 run beside it")
-    ap.add_argument("--cpu-points", type=int, default=512)
-    ap.add_argument("--ref-points", type=int, default=256)
+    ap.add_argument("--cpu-points", type=int, default=2048)
+    ap.add_argument("--ref-points", type=int, default=1024)
     ap.add_argument("--pair-domain", choices=("triangle", "wedge"), default="triangle",
                     help="wedge: y-inversion mirror sampling on the half-channel wedge (streaming mode)")
     ap.add_argument("--stride", type=int, default=1, help="uniform undersampling of r_x, r_z (streaming mode)")
