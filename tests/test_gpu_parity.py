@@ -270,3 +270,26 @@ def test_retau200_invariants(N, retau200):
     iu = np.triu_indices(ny)
     mean_r = A.mean(axis=(1, 2))
     assert np.abs(mean_r - (q[iu[0]] + q[iu[1]])).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pinned_host_output_matches_device(N, precision):
+    """Pinned host outputs take the overlapped copy path (finished term rows go
+    out per pair chunk on a second stream): bit-equal to device outputs."""
+    import torch
+    wl = S.small(16, 16, 33, 3, wid=44)
+    coef = S.coefficients(wl)
+    y = S.cgl_grid(wl.ny)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 3, precision)
+    try:
+        tdt = torch.float64 if precision == 0 else torch.float32
+        shape = (N.GKE_NTERM, N.gke_npair(plan), wl.nz, wl.nx)
+        dev = torch.empty(shape, dtype=tdt, device="cuda")
+        pinned = torch.empty(shape, dtype=tdt).pin_memory()
+        f = torch.from_numpy(coef).cuda()
+        N.gke_compute(plan, f, 3, dev)
+        N.gke_compute(plan, f, 3, pinned)
+        torch.cuda.synchronize()
+        assert torch.equal(dev.cpu(), pinned)
+    finally:
+        N.gke_destroy(plan)

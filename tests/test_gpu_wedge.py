@@ -108,3 +108,28 @@ def test_wedge_labels_and_errors(N):
     with pytest.raises(N.GkeError) as e:
         N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 1, pair_domain=2)
     assert e.value.status == -1
+
+
+def test_wedge_f32_thresholds_vs_oracle(N):
+    """FP32 contractions, mirror sampling and thresholded undersampling together."""
+    import oracle
+    import torch
+    wl = S.small(32, 16, 17, 3, wid=74)
+    phys = S.physical(wl)
+    y = S.cgl_grid(wl.ny)
+    ux, uz = (3, 8, 2, 4), (2, 4, 2, 4)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, 3, N.GKE_PREC_F32,
+                      pair_domain=N.GKE_DOMAIN_WEDGE, under_x=ux, under_z=uz)
+    try:
+        mz, mx = N.gke_separation_labels(plan)
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), len(mz), len(mx)), dtype=torch.float32, device="cuda")
+        N.gke_compute(plan, torch.from_numpy(S.to_coefficients(phys)).cuda(), 3, terms)
+        torch.cuda.synchronize()
+        got = terms.cpu().numpy().astype(np.float64)
+    finally:
+        N.gke_destroy(plan)
+    ref = oracle.full(phys, y, wl.Lx, wl.Lz, wl.nu, mirror=True)
+    w = np.array(oracle.wedge_pairs(wl.ny))
+    for t in range(N.GKE_NTERM):
+        want = ref["terms"][t][w[:, 0], w[:, 1]][:, mz][:, :, mx]
+        assert rel_err(got[t], want) <= TOL_SPLIT, N.TERMS[t]
