@@ -173,6 +173,12 @@ gke_status gke_reset(gke_plan_t plan);
  * term spectra, counts) to / from a file; linear, so restored partial sums combine
  * exactly with further calls (the paper's merge of independent jobs,
  * Sec. 3.4).  gke_merge adds a checkpoint's sums to the plan's.             */
+/* File layout (little endian): a header struct { char magic[8] "GKECKPT";
+ * int32 version = 3, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt;
+ * (4 bytes padding); float64 mean_count, snap_count, Lx, Lz, nu } (88 bytes),
+ * then float64 mean_sum[4][ny], float64 stats[7][ny] and, if have_acc, the
+ * complex128 per-pair sums.  Files of independent jobs can also be added on
+ * the host (paper_1910_06409_gb300/merge.py).                               */
 gke_status gke_checkpoint(gke_plan_t plan, const char* path);
 gke_status gke_restore(gke_plan_t plan, const char* path);
 gke_status gke_merge(gke_plan_t plan, const char* path);

@@ -205,6 +205,18 @@ def test_checkpoint_merge_equals_single_pass(N, tiny, tmp_path):
     finally:
         N.gke_destroy(plan)
     assert rel_err(got, full) < 1e-13
+    # the same merge done on the host by the checkpoint tool, then restored
+    from paper_1910_06409_gb300 import merge as M
+    merged = str(tmp_path / "merged.ckpt")
+    M.merge(paths, merged)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, wl.nsnap)
+    try:
+        N.gke_restore(plan, merged)
+        terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), wl.nz, wl.nx), dtype=torch.float64, device="cuda")
+        N.gke_finalize_terms(plan, terms)
+        assert np.array_equal(terms.cpu().numpy(), got)
+    finally:
+        N.gke_destroy(plan)
     with open(paths[0], "r+b") as fp:          # truncated file -> IO error
         fp.truncate(200)
     plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, wl.nsnap)
