@@ -359,7 +359,8 @@ def run_stream(args, world, rank, local):
             "data": "synthetic", "config": cfg, "stage_ms": stage_ms, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": None, "roofline": rl.get("correlate"), "cpu_baseline": None,
             "note": "streaming mode: outputs are output_pairs x separations; value counts output pairs"}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 GROUP = (("group_128x128x65_s32", 1), ("group_256x256x129_s16", 1), ("group_384x384x193_s8", 2))
@@ -421,7 +422,8 @@ def run_group(args, world, rank, local):
                                             "precision": args.precision},
             "gpu_launches": launches, "clocks": clk.summary(), "e2e": None, "roofline": None,
             "cpu_baseline": None, "note": "datasets run as separate plans back to back (no grouped launch)"}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_ours(args, world, rank, local):
