@@ -152,6 +152,9 @@ def test_error_codes(N):
         with pytest.raises(N.GkeError) as e:
             N.gke_accumulate_mean(plan, coef, 3)              # > max_snap
         assert e.value.status == -1
+        with pytest.raises(N.GkeError) as e:
+            N.gke_accumulate_mean(plan, coef, 0)              # empty batch
+        assert e.value.status == -1
         N.gke_accumulate_mean(plan, coef, 2)
         bad = coef.clone()
         bad[1, 2, 3, 1, 1] = float("nan")
@@ -258,6 +261,43 @@ def test_retau200_spot_checks_vs_oracle(N, retau200):
     for n, (a, b, mz, mx) in enumerate(pts):
         g = got[:6, _pidx(a, b, wl.ny), mz, mx]
         err = np.abs(g - ref["terms"][n]) / scale
+        assert err.max() <= TOL_F64, (pts[n], err)
+
+
+def test_retau200_split_spot_checks_vs_oracle(N, retau200):
+    """The split-BF16 path at the full 256 x 256 x 129 x 16 size, as the bench
+    runs it: sampled outputs against the oracle, 1e-6 of each term's largest
+    magnitude."""
+    import oracle
+    wl, phys, got64, prof = retau200
+    got, _ = run_gpu(N, wl, S.to_coefficients(phys), precision=N.GKE_PREC_BF16X3)
+    rng = np.random.default_rng(2025)
+    planes = [0, 1, 2, 40, 64, 90, 127, 128]
+    pts = []
+    for _ in range(30):
+        a, b = sorted(rng.choice(planes, 2))
+        pts.append((a, b, int(rng.integers(wl.nz)), int(rng.integers(wl.nx))))
+    ref = oracle.points(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu, pts)
+    scale = np.abs(got64[:6]).reshape(6, -1).max(axis=1)
+    for n, (a, b, mz, mx) in enumerate(pts):
+        err = np.abs(got[:6, _pidx(a, b, wl.ny), mz, mx] - ref["terms"][n]) / scale
+        assert err.max() <= 1e-6, (pts[n], err)
+
+
+def test_largest_grid_spot_checks(N):
+    """nx = nz = 1024 (the largest grid), the fewest wall-normal points (5) and
+    one snapshot: sampled outputs against the oracle."""
+    import oracle
+    wl = S.small(1024, 1024, 5, 1, wid=45)
+    phys = S.physical(wl)
+    got, _ = run_gpu(N, wl, S.to_coefficients(phys))
+    rng = np.random.default_rng(1024)
+    pts = [(int(a), int(b), int(rng.integers(1024)), int(rng.integers(1024)))
+           for a, b in [(0, 0), (0, 4), (1, 3), (2, 2), (3, 4), (0, 2)] for _ in range(3)]
+    ref = oracle.points(phys, S.cgl_grid(wl.ny), wl.Lx, wl.Lz, wl.nu, pts)
+    scale = np.abs(got[:6]).reshape(6, -1).max(axis=1)
+    for n, (a, b, mz, mx) in enumerate(pts):
+        err = np.abs(got[:6, _pidx(a, b, wl.ny), mz, mx] - ref["terms"][n]) / scale
         assert err.max() <= TOL_F64, (pts[n], err)
 
 
