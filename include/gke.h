@@ -154,6 +154,15 @@ gke_status gke_finalize_terms(gke_plan_t plan, void* terms, double* profiles);
  * gke_finalize_terms on a fresh plan state, staging host data once.        */
 gke_status gke_compute(gke_plan_t plan, const void* fields, int nsnap, void* terms, double* profiles);
 
+/* gke_compute as one CUDA graph: the first call (and any call with other
+ * pointers or nsnap) captures the whole pass -- reset, Step-1 mean frozen on
+ * the device, the batch, Step 3 -- from the plan's stream into a graph;
+ * later calls replay it.  Device pointers only (else GKE_ERR_ARG); the plan
+ * must have been created on a non-default stream (else GKE_ERR_UNSUPPORTED).
+ * Results equal gke_compute's; synchronises the stream like
+ * gke_finalize_terms.  Not part of the paper: a launch-overhead option.     */
+gke_status gke_compute_graph(gke_plan_t plan, const void* fields, int nsnap, void* terms, double* profiles);
+
 /* Host arrays of the pair labels: Y[npair], ry[npair], i1[npair], i2[npair]
  * (any may be NULL).                                                         */
 gke_status gke_pair_labels(gke_plan_t plan, double* Y, double* ry, int* i1, int* i2);

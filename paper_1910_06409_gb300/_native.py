@@ -25,7 +25,7 @@ GKE_NTERM, GKE_NPROF = len(TERMS), len(PROFILES)
 
 # every symbol include/gke.h declares
 EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_snapshot", "gke_finalize_terms",
-           "gke_compute", "gke_pair_labels", "gke_npair", "gke_separation_labels", "gke_terms_bytes", "gke_reset",
+           "gke_compute", "gke_compute_graph", "gke_pair_labels", "gke_npair", "gke_separation_labels", "gke_terms_bytes", "gke_reset",
            "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy")
@@ -65,6 +65,7 @@ def lib():
             "gke_accumulate_snapshot": (i, [vp, vp, i]),
             "gke_finalize_terms": (i, [vp, vp, vp]),
             "gke_compute": (i, [vp, vp, i, vp, vp]),
+            "gke_compute_graph": (i, [vp, vp, i, vp, vp]),
             "gke_pair_labels": (i, [vp, vp, vp, vp, vp]),
             "gke_npair": (ctypes.c_longlong, [vp]),
             "gke_separation_labels": (i, [vp, vp, vp, vp, vp]),
@@ -138,6 +139,10 @@ def gke_finalize_terms(plan, terms, profiles=None):
 
 def gke_compute(plan, fields, nsnap, terms, profiles=None):
     _check(lib().gke_compute(plan, ptr(fields), nsnap, ptr(terms), ptr(profiles)), plan)
+
+
+def gke_compute_graph(plan, fields, nsnap, terms, profiles=None):
+    _check(lib().gke_compute_graph(plan, ptr(fields), nsnap, ptr(terms), ptr(profiles)), plan)
 
 
 def gke_pair_labels(plan):

@@ -81,6 +81,12 @@ struct gke_plan_s {
     // host-output finalize: copies of finished term rows overlap the rest
     cudaStream_t copy_st = nullptr;
     cudaStream_t aux_st = nullptr;            // row passes of the inverse transforms
+    cudaEvent_t aux_ev[10] = {};              // events of the two-stream stages (products 6, transforms 4)
+    // graph replay (gke_compute_graph): the captured pass and what it was captured for
+    cudaGraphExec_t graph = nullptr;
+    const void* g_fields = nullptr; void* g_terms = nullptr; double* g_prof = nullptr;
+    int g_nsnap = 0;
+    long long g_launches = 0;
     void* W2 = nullptr;                       // second transform scratch buffer
     std::vector<cudaEvent_t> chunk_ev;
     void* host_terms = nullptr;
@@ -400,6 +406,9 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOCB(p->W2, (size_t)p->pair_chunk * NTERM * nrzt * nxth * p->csz);
     if ((e = cudaStreamCreateWithFlags(&p->aux_st, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(GKE_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    for (cudaEvent_t& ev : p->aux_ev)
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(GKE_ERR_CUDA, std::string("event: ") + cudaGetErrorString(e));
     ALLOC(p->tw_xd, d.nx);
     ALLOC(p->tw_zd, d.nz);
     ALLOC(p->tw_xf, d.nx);
@@ -532,6 +541,8 @@ extern "C" void gke_destroy(gke_plan_t p)
         for (void* q : more) if (q) cudaFree(q);
     }
     if (p->aux_st) cudaStreamDestroy(p->aux_st);
+    for (cudaEvent_t ev : p->aux_ev) if (ev) cudaEventDestroy(ev);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->dec) {
         void* extra[] = {p->cchunk, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
@@ -669,14 +680,16 @@ static void products_stage(gke_plan_t p, const zd* f, int ns)
     a.part = p->part; a.stats = p->stats; a.nonfinite = p->nonfinite;
     a.cw_ci = t.cw_ci; a.rz_rp = t.rz_rp; a.cw_cf = t.cw_cf; a.yb_cf = t.yb_cf; a.eps_kchunk = EPS_KCHUNK;
     a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = p->fdw; a.fdl0 = p->fdl0; a.st = p->st;
-    a.st2 = p->aux_st; a.G2 = p->G2; a.H2 = p->H2; a.part2 = p->part2;
+    a.st2 = p->aux_st; a.G2 = p->G2; a.H2 = p->H2; a.part2 = p->part2; a.ev = p->aux_ev;
     p->launches += f32 ? products_launch<float>(a) : products_launch<double>(a);
 }
+
+static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns);
 
 static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
 {
     const gke_desc& d = p->d;
-    const int ny = d.ny, Nk = p->Nk;
+    const int ny = d.ny;
     cudaStream_t st = p->st;
     if (!p->mean_frozen) {
         // mean = mean_sum / mean_count, computed once (host round trip of 4 ny doubles)
@@ -705,6 +718,15 @@ static gke_status snapshot_impl(gke_plan_t p, const zd* f, int ns)
         CUDA_TRY(p, cudaStreamSynchronize(st));
         p->mean_frozen = true;
     }
+    return enqueue_snapshot(p, f, ns);
+}
+
+// the kernels of one batch after the mean is frozen (no host synchronisation)
+static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
+{
+    const gke_desc& d = p->d;
+    const int ny = d.ny, Nk = p->Nk;
+    cudaStream_t st = p->st;
     const bool f32 = (d.precision != GKE_PREC_F64);
     {
         StageScope sc(p, GKE_STAGE_PRODUCTS);
@@ -819,6 +841,7 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     a.ctx = p;
     a.st2 = p->aux_st;
     a.W2 = p->W2;
+    a.ev = p->aux_ev + 6;
     p->launches += terms_launch(a);
 }
 
@@ -911,6 +934,91 @@ extern "C" gke_status gke_compute(gke_plan_t p, const void* fields, int nsnap, v
     if ((s = mean_impl(p, f, nsnap)) != GKE_OK) return s;
     if ((s = snapshot_impl(p, f, nsnap)) != GKE_OK) return s;
     return gke_finalize_terms(p, terms, profiles);
+}
+
+// ------------------------------------------------------------- graph replay
+// One pass as a pure device sequence (reset, Step-1 mean frozen on the device,
+// the batch, Step 3), for capture into a CUDA graph.
+static gke_status capture_pass(gke_plan_t p, const zd* f, int nsnap, void* terms, double* profiles)
+{
+    const gke_desc& d = p->d;
+    const int ny = d.ny;
+    cudaStream_t st = p->st;
+    CUDA_TRY(p, cudaMemsetAsync(p->mean_sum, 0, 4 * ny * sizeof(double), st));
+    CUDA_TRY(p, cudaMemsetAsync(p->stats, 0, NSTAT * ny * sizeof(double), st));
+    CUDA_TRY(p, cudaMemsetAsync(p->nonfinite, 0, sizeof(int), st));
+    if (p->dec) CUDA_TRY(p, cudaMemsetAsync(p->comb, 0, p->n_acc * sizeof(zd), st));
+    gke_status s = mean_impl(p, f, nsnap);
+    if (s != GKE_OK) return s;
+    k_freeze_mean<<<1, 1024, 0, st>>>(p->mean_sum, p->mean_count, p->wedge ? 1 : 0, ny, p->mean);
+    k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, 1.0, (long long)d.nx * d.nz,
+                                                  d.nu, p->wedge ? 1 : 0, p->fdw, p->fdl0, ny, p->prof);
+    p->launches += 2;
+    p->mean_frozen = true;
+    if ((s = enqueue_snapshot(p, f, nsnap)) != GKE_OK) return s;
+    if ((s = finalize_impl(p, terms)) != GKE_OK) return s;
+    if (profiles)
+        CUDA_TRY(p, cudaMemcpyAsync(profiles, p->prof, GKE_NPROF * ny * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return GKE_OK;
+}
+
+extern "C" gke_status gke_compute_graph(gke_plan_t p, const void* fields, int nsnap, void* terms, double* profiles)
+{
+    if (!p || !fields || !terms) return p ? fail(p, GKE_ERR_ARG, "NULL argument") : GKE_ERR_ARG;
+    if (nsnap < 1 || nsnap > p->d.max_snap) return fail(p, GKE_ERR_ARG, "nsnap out of range [1, max_snap]");
+    if (!is_device_ptr(fields) || !is_device_ptr(terms) || (profiles && !is_device_ptr(profiles)))
+        return fail(p, GKE_ERR_ARG, "gke_compute_graph takes device pointers only");
+    if (p->st == nullptr || p->st == cudaStreamLegacy || p->st == cudaStreamPerThread)
+        return fail(p, GKE_ERR_UNSUPPORTED, "gke_compute_graph needs a plan created on a non-default stream");
+    const bool same = p->graph && p->g_fields == fields && p->g_terms == terms && p->g_prof == profiles &&
+                      p->g_nsnap == nsnap;
+    auto fresh = [&]() {
+        p->mean_count = 0.0;
+        p->snap_count = 0.0;
+        p->mean_frozen = p->have_acc = p->finalized = false;
+        p->comb_is64 = (p->d.precision == GKE_PREC_F64) || p->dec;
+    };
+    if (!same) {
+        if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
+        const bool timing = p->timing;
+        const long long l0 = p->launches;
+        p->timing = false;
+        fresh();
+        CUDA_TRY(p, cudaStreamSynchronize(p->st));
+        cudaError_t e = cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) { p->timing = timing; return fail(p, GKE_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e)); }
+        const gke_status cs = capture_pass(p, (const zd*)fields, nsnap, terms, profiles);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->st, &g);
+        p->timing = timing;
+        if (cs != GKE_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return cs != GKE_OK ? cs : fail(p, GKE_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+        }
+        e = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { p->graph = nullptr; return fail(p, GKE_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e)); }
+        p->g_launches = p->launches - l0;
+        p->launches = l0;
+        p->g_fields = fields; p->g_terms = terms; p->g_prof = profiles; p->g_nsnap = nsnap;
+    }
+    // host state of the pass the graph runs
+    fresh();
+    p->mean_count = p->snap_count = nsnap;
+    p->mean_frozen = p->have_acc = true;
+    CUDA_TRY(p, cudaGraphLaunch(p->graph, p->st));
+    p->launches += p->g_launches;
+    int bad = 0;
+    CUDA_TRY(p, cudaMemcpyAsync(&bad, p->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, p->st));
+    CUDA_TRY(p, cudaStreamSynchronize(p->st));
+    p->finalized = true;
+    if (p->d.precision == GKE_PREC_BF16X3) {
+        gke_status ss = split_check(p->split, p->st, p->err);
+        if (ss != GKE_OK) return ss;
+    }
+    if (bad) return fail(p, GKE_ERR_NONFINITE, "non-finite value in the accumulated input");
+    return GKE_OK;
 }
 
 // ------------------------------------------------------- checkpoint files

@@ -29,6 +29,7 @@ struct ProdArgs {
     // optional second stream and buffers: odd snapshots run there
     cudaStream_t st2 = nullptr;
     void* G2 = nullptr; void* H2 = nullptr; double* part2 = nullptr;
+    const cudaEvent_t* ev = nullptr;      // 6 caller-owned events for st2 (else created per call)
 };
 template <typename TF> int products_launch(const ProdArgs& a);
 cudaError_t products_set_attrs(int lim);
@@ -81,6 +82,7 @@ struct TermArgs {
     // chunk [p0, p0 + np), given the stream its row pass ran on
     cudaStream_t st2 = nullptr;
     void* W2 = nullptr;
+    const cudaEvent_t* ev = nullptr;      // 4 caller-owned events for st2 (else created per call)
     void (*after_chunk)(void* ctx, long long p0, long long np, cudaStream_t st) = nullptr;
     void* ctx = nullptr;
 };
@@ -90,6 +92,7 @@ int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npa
                    const SepMap& sep, double nu, const double* fdw, const int* fdl0, const double* prof,
                    cudaStream_t st);
 
+__global__ void k_freeze_mean(double* mean_sum, double mean_count, int mirror, int ny, double* mean);
 __global__ void k_profiles(const double* mean_sum, double mean_count, const double* stats,
                            double snap_count, long long plane_points, double nu, int mirror, const double* fdw,
                            const int* fdl0, int ny, double* prof);

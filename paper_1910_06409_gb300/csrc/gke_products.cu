@@ -459,11 +459,16 @@ int products_launch(const ProdArgs& a)
     cudaEvent_t ev_start = nullptr, ev_rp[2] = {nullptr, nullptr}, ev_red[2] = {nullptr, nullptr},
                 ev_end = nullptr;
     if (two) {
-        cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
-        cudaEventCreateWithFlags(&ev_end, cudaEventDisableTiming);
-        for (int i = 0; i < 2; ++i) {
-            cudaEventCreateWithFlags(&ev_rp[i], cudaEventDisableTiming);
-            cudaEventCreateWithFlags(&ev_red[i], cudaEventDisableTiming);
+        if (a.ev) {
+            ev_start = a.ev[0]; ev_end = a.ev[1];
+            ev_rp[0] = a.ev[2]; ev_rp[1] = a.ev[3]; ev_red[0] = a.ev[4]; ev_red[1] = a.ev[5];
+        } else {
+            cudaEventCreateWithFlags(&ev_start, cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&ev_end, cudaEventDisableTiming);
+            for (int i = 0; i < 2; ++i) {
+                cudaEventCreateWithFlags(&ev_rp[i], cudaEventDisableTiming);
+                cudaEventCreateWithFlags(&ev_red[i], cudaEventDisableTiming);
+            }
         }
         cudaEventRecord(ev_start, st);                   // the second stream starts after earlier work
         cudaStreamWaitEvent(a.st2, ev_start, 0);
@@ -515,11 +520,13 @@ int products_launch(const ProdArgs& a)
         // join: the main stream waits for the second stream's last transforms
         cudaEventRecord(ev_end, a.st2);
         cudaStreamWaitEvent(st, ev_end, 0);
-        cudaEventDestroy(ev_start);
-        cudaEventDestroy(ev_end);
-        for (int i = 0; i < 2; ++i) {
-            cudaEventDestroy(ev_rp[i]);
-            cudaEventDestroy(ev_red[i]);
+        if (!a.ev) {
+            cudaEventDestroy(ev_start);
+            cudaEventDestroy(ev_end);
+            for (int i = 0; i < 2; ++i) {
+                cudaEventDestroy(ev_rp[i]);
+                cudaEventDestroy(ev_red[i]);
+            }
         }
     }
     const int neb = (Nk + a.eps_kchunk - 1) / a.eps_kchunk;

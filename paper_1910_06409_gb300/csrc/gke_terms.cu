@@ -262,11 +262,16 @@ int terms_launch_t(const TermArgs& a)
     // the GPU stays full with chunks small enough for W to stay in L2.
     const bool two = a.st2 != nullptr && a.W2 != nullptr;
     cudaEvent_t ev_col[2] = {nullptr, nullptr}, ev_row[2] = {nullptr, nullptr};
-    if (two)
-        for (int i = 0; i < 2; ++i) {
-            cudaEventCreateWithFlags(&ev_col[i], cudaEventDisableTiming);
-            cudaEventCreateWithFlags(&ev_row[i], cudaEventDisableTiming);
+    if (two) {
+        if (a.ev) {
+            ev_col[0] = a.ev[0]; ev_col[1] = a.ev[1]; ev_row[0] = a.ev[2]; ev_row[1] = a.ev[3];
+        } else {
+            for (int i = 0; i < 2; ++i) {
+                cudaEventCreateWithFlags(&ev_col[i], cudaEventDisableTiming);
+                cudaEventCreateWithFlags(&ev_row[i], cudaEventDisableTiming);
+            }
         }
+    }
     int launches = 0;
     long long c = 0;
     for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk, ++c) {
@@ -319,11 +324,12 @@ int terms_launch_t(const TermArgs& a)
     if (two) {
         // join: the main stream waits for the last row passes
         cudaStreamWaitEvent(a.st, ev_row[0], 0);
-        cudaStreamWaitEvent(a.st, ev_row[1], 0);
-        for (int i = 0; i < 2; ++i) {
-            cudaEventDestroy(ev_col[i]);
-            cudaEventDestroy(ev_row[i]);
-        }
+        if (c > 1) cudaStreamWaitEvent(a.st, ev_row[1], 0);
+        if (!a.ev)
+            for (int i = 0; i < 2; ++i) {
+                cudaEventDestroy(ev_col[i]);
+                cudaEventDestroy(ev_row[i]);
+            }
     }
     return launches;
 }
@@ -632,6 +638,23 @@ int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npa
                   : stencil_launch_t<true, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st);
     return us ? stencil_launch_t<false, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st)
               : stencil_launch_t<false, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st);
+}
+
+// ----------------------------------------------- Step-1 mean, on device
+// mean = mean_sum / mean_count; with mirror sampling the mean of the
+// snapshots and their images (U, W, P even about the centreline, V odd), and
+// mean_sum rewritten to match.  One block (both phases need every value).
+__global__ void k_freeze_mean(double* __restrict__ mean_sum, double mean_count, int mirror, int ny,
+                              double* __restrict__ mean)
+{
+    for (int i = threadIdx.x; i < 4 * ny; i += blockDim.x) {
+        const int f = i / ny, j = i - f * ny;
+        const double m = mean_sum[i] / mean_count;
+        mean[i] = mirror ? 0.5 * (m + (f == 1 ? -1.0 : 1.0) * (mean_sum[f * ny + ny - 1 - j] / mean_count)) : m;
+    }
+    __syncthreads();
+    if (mirror)
+        for (int i = threadIdx.x; i < 4 * ny; i += blockDim.x) mean_sum[i] = mean[i] * mean_count;
 }
 
 // ------------------------------------------- profiles from the raw sums
