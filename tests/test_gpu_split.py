@@ -111,3 +111,28 @@ def test_f32_tiny_vs_oracle(N):
     for t in range(N.GKE_NTERM):
         e = rel_err(got[t], ref["terms"][t][iu])
         assert e <= TOL_SPLIT, (N.TERMS[t], e)
+
+
+# ------------------------------------------- 256 x 256: register transforms
+# At nx = nz = 256 the split path runs the register-FFT column and row passes
+# (two streams, pair chunks); these cases reach them with FP32 and FP64
+# per-pair sums (one batch / two), the wedge and the a-posteriori separation
+# selection.
+@pytest.mark.parametrize("domain,calls", [(0, None), (0, [2, 1]), (1, None), (1, [1, 2])])
+def test_split_256_matches_f64(N, domain, calls):
+    wl = S.small(256, 256, 9, 3, wid=120 + domain)
+    coef = S.coefficients(wl)
+    ref, pref = run_gpu(N, wl, coef, precision=N.GKE_PREC_F64, domain=domain)
+    got, pgot = run_gpu(N, wl, coef, precision=N.GKE_PREC_BF16X3, calls=calls, domain=domain)
+    errs = [rel_err(got[t], ref[t]) for t in range(N.GKE_NTERM)]
+    assert max(errs) <= TOL_SPLIT, dict(zip(N.TERMS, errs))
+    assert max(errs) > 0.0
+
+
+def test_split_256_selection_equals_full(N):
+    from test_gpu_undersample import run
+    wl = S.small(256, 256, 9, 2, wid=125)
+    coef = S.coefficients(wl)
+    full, _, _ = run(N, wl, coef, N.GKE_PREC_BF16X3)
+    got, mz, mx = run(N, wl, coef, N.GKE_PREC_BF16X3, ux=(8, 64, 2, 8), uz=(4, 32, 4, 16))
+    assert np.array_equal(got, full[:, :, mz][:, :, :, mx])
