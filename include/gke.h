@@ -119,7 +119,21 @@ typedef struct {
     int pair_domain;       /* GKE_DOMAIN_*                                               */
     int under_x[4];        /* undersampling of r_x {t1, t2, s1, s2}; all 0 = full        */
     int under_z[4];        /* undersampling of r_z, same rule                            */
+    unsigned term_mask;    /* terms to compute: bit t = GKE_TERM t; 0 = all (see below)  */
 } gke_desc;
+
+/* term_mask: the plan computes the requested terms and the terms they are
+ * derived from -- A for Phi_y and phi (Step-3 FD parts, Eq. 10-11), and A,
+ * Phi_y, phi for the residual -- and runs only the contractions those need
+ * (A: D; Phi_x: Gx, D; Phi_y: QV, X2; Phi_z: Gz, D; phi: QV, X2, F; xi: E;
+ * residual: Gx, Gz, D, E).  Planes of the output outside that set are not
+ * written (their contents are unspecified); the planes inside it equal a
+ * full run's up to rounding.  Bits above GKE_NTERM: GKE_ERR_ARG.
+ * gke_term_set gives the set a mask expands to.  The products pass is the
+ * same for every mask (the one-point parts need it).                        */
+#define GKE_TERM_BIT(t) (1u << (t))
+#define GKE_ALL_TERMS ((1u << GKE_NTERM) - 1u)
+unsigned gke_term_set(unsigned term_mask);
 
 /* Create a plan: validates the descriptor, computes the FD weights and
  * twiddles on the host, allocates every workspace on the current device.
@@ -183,11 +197,13 @@ gke_status gke_reset(gke_plan_t plan);
  * exactly with further calls (the paper's merge of independent jobs,
  * Sec. 3.4).  gke_merge adds a checkpoint's sums to the plan's.             */
 /* File layout (little endian): a header struct { char magic[8] "GKECKPT";
- * int32 version = 3, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt;
- * (4 bytes padding); float64 mean_count, snap_count, Lx, Lz, nu } (88 bytes),
- * then float64 mean_sum[4][ny], float64 stats[7][ny] and, if have_acc, the
- * complex128 per-pair sums.  Files of independent jobs can also be added on
- * the host (paper_1910_06409_gb300/merge.py).                               */
+ * int32 version = 4, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt,
+ * term_set (gke_term_set of the plan's mask); float64 mean_count, snap_count,
+ * Lx, Lz, nu } (88 bytes), then float64 mean_sum[4][ny], float64 stats[7][ny]
+ * and, if have_acc, the complex128 per-pair sums.  Restore and merge need
+ * the same grid, domain and term set (else GKE_ERR_ARG).  Files of
+ * independent jobs can also be added on the host
+ * (paper_1910_06409_gb300/merge.py).                                        */
 gke_status gke_checkpoint(gke_plan_t plan, const char* path);
 gke_status gke_restore(gke_plan_t plan, const char* path);
 gke_status gke_merge(gke_plan_t plan, const char* path);

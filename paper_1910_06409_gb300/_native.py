@@ -25,8 +25,8 @@ GKE_NTERM, GKE_NPROF = len(TERMS), len(PROFILES)
 
 # every symbol include/gke.h declares
 EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_snapshot", "gke_finalize_terms",
-           "gke_compute", "gke_compute_graph", "gke_pair_labels", "gke_npair", "gke_separation_labels", "gke_terms_bytes", "gke_reset",
-           "gke_checkpoint",
+           "gke_compute", "gke_compute_graph", "gke_pair_labels", "gke_npair", "gke_separation_labels",
+           "gke_terms_bytes", "gke_term_set", "gke_reset", "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy")
 STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
@@ -37,7 +37,7 @@ class gke_desc(ctypes.Structure):
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("nu", ctypes.c_double),
                 ("y", ctypes.POINTER(ctypes.c_double)),
                 ("max_snap", ctypes.c_int), ("precision", ctypes.c_int), ("pair_domain", ctypes.c_int),
-                ("under_x", ctypes.c_int * 4), ("under_z", ctypes.c_int * 4)]
+                ("under_x", ctypes.c_int * 4), ("under_z", ctypes.c_int * 4), ("term_mask", ctypes.c_uint)]
 
 
 class GkeError(RuntimeError):
@@ -75,6 +75,7 @@ def lib():
             "gke_restore": (i, [vp, cp]),
             "gke_merge": (i, [vp, cp]),
             "gke_fd_weights": (i, [dp, i, i, dp]),
+            "gke_term_set": (ctypes.c_uint, [ctypes.c_uint]),
             "gke_set_timing": (i, [vp, i]),
             "gke_stage_times": (i, [vp, vp]),
             "gke_launch_count": (ctypes.c_longlong, [vp]),
@@ -110,11 +111,11 @@ def _check(status: int, plan) -> None:
 
 
 def gke_plan(nx, nz, ny, Lx, Lz, nu, y, max_snap, precision=GKE_PREC_F64, stream=None,
-             pair_domain=GKE_DOMAIN_TRIANGLE, under_x=(0, 0, 0, 0), under_z=(0, 0, 0, 0)):
+             pair_domain=GKE_DOMAIN_TRIANGLE, under_x=(0, 0, 0, 0), under_z=(0, 0, 0, 0), term_mask=0):
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), max_snap,
-                    precision, pair_domain, (ctypes.c_int * 4)(*under_x), (ctypes.c_int * 4)(*under_z))
+                    precision, pair_domain, (ctypes.c_int * 4)(*under_x), (ctypes.c_int * 4)(*under_z), term_mask)
     out = ctypes.c_void_p()
     st = lib().gke_plan(ctypes.byref(desc), stream, ctypes.byref(out))
     _check(st, None)
@@ -143,6 +144,10 @@ def gke_compute(plan, fields, nsnap, terms, profiles=None):
 
 def gke_compute_graph(plan, fields, nsnap, terms, profiles=None):
     _check(lib().gke_compute_graph(plan, ptr(fields), nsnap, ptr(terms), ptr(profiles)), plan)
+
+
+def gke_term_set(term_mask: int) -> int:
+    return lib().gke_term_set(term_mask)
 
 
 def gke_pair_labels(plan):
@@ -199,12 +204,12 @@ def gke_fd_weights(y, j):
     return l0, w
 
 
-def gke_compute_noalloc(nx, nz, ny, Lx, Lz, nu, y, fields, nsnap, terms, profiles=None, stream=None):
+def gke_compute_noalloc(nx, nz, ny, Lx, Lz, nu, y, fields, nsnap, terms, profiles=None, stream=None, term_mask=0):
     """FP64 pass without device allocation (device pointers only); raises GkeError."""
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsnap,
-                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE, (ctypes.c_int * 4)(), (ctypes.c_int * 4)())
+                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE, (ctypes.c_int * 4)(), (ctypes.c_int * 4)(), term_mask)
     st = lib().gke_compute_noalloc(ctypes.byref(desc), ptr(fields), nsnap, ptr(terms), ptr(profiles), stream)
     if st != GKE_OK:
         raise GkeError(st, "gke_compute_noalloc")

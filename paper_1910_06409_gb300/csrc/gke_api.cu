@@ -30,6 +30,7 @@ struct gke_plan_s {
     // npair_tri: pairs of the triangle, over which the spectra are summed
     long long npair = 0, npair_tri = 0;
     bool wedge = false;
+    unsigned tset = 0;                        // terms computed (term_set of the mask)
     void* fold = nullptr;                     // wedge: folded spectra (aliases raw when it fits)
     bool fold_owned = false;
     // kept separations (undersampling): host lists and the device map
@@ -283,6 +284,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         g_plan_err = "undersampling {t1, t2, s1, s2} needs 0 <= t1 <= t2, s2 >= 1, s1 >= 1 if t1 < t2 (or all zero)";
         return GKE_ERR_ARG;
     }
+    if (d.term_mask & ~GKE_ALL_TERMS) { g_plan_err = "term_mask has bits above GKE_NTERM"; return GKE_ERR_ARG; }
     for (int j = 1; j < d.ny; ++j)
         if (!(d.y[j] > d.y[j - 1])) { g_plan_err = "y must be strictly increasing"; return GKE_ERR_ARG; }
     if (d.pair_domain == GKE_DOMAIN_WEDGE) {
@@ -298,6 +300,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     gke_plan_t p = new (std::nothrow) gke_plan_s;
     if (!p) { g_plan_err = "host allocation failed"; return GKE_ERR_OOM; }
     p->d = d;
+    p->tset = term_set(d.term_mask);
     p->y.assign(d.y, d.y + d.ny);
     p->d.y = p->y.data();
     p->st = (cudaStream_t)stream;
@@ -515,6 +518,8 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     *out = p;
     return GKE_OK;
 }
+
+extern "C" unsigned gke_term_set(unsigned term_mask) { return term_set(term_mask & GKE_ALL_TERMS); }
 
 extern "C" gke_status gke_reset(gke_plan_t p)
 {
@@ -735,12 +740,13 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
     auto correlate = [&](int k0, int Kc) -> gke_status {
         StageScope sc(p, GKE_STAGE_CORRELATE);
         if (d.precision != GKE_PREC_BF16X3) {
-            correlate_launch(f32, p->Xop, ns, ny, Nk, k0, Kc, p->raw, st);
+            correlate_launch(f32, p->Xop, ns, ny, Nk, k0, Kc, p->raw, job_set(p->tset), st);
             p->launches += 1;
             return GKE_OK;
         }
         int nl = 0;
-        gke_status s = split_correlate(p->split, (const zf*)p->Xop, ns, ny, Nk, k0, Kc, (zf*)p->raw, st, p->err, &nl);
+        gke_status s = split_correlate(p->split, (const zf*)p->Xop, ns, ny, Nk, k0, Kc, (zf*)p->raw, job_set(p->tset),
+                                       st, p->err, &nl);
         p->launches += nl;
         return s;
     };
@@ -753,7 +759,7 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
             if (s != GKE_OK) return s;
             StageScope sc(p, GKE_STAGE_COMBINE);
             p->launches += combine_launch(f32, !f32, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, k0,
-                                          p->Kc, p->Kc, p->cchunk, st);
+                                          p->Kc, p->Kc, p->cchunk, p->tset, st);
             p->launches += fold_dec_launch(!f32, p->cchunk, p->pair_i, p->npair, p->wedge ? 1 : 0, ny, d.nz, d.nx,
                                            p->nzt, p->nxt, kz0, p->R, p->comb, st);
         }
@@ -777,7 +783,7 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
         }
         void* dst = p->comb_is64 ? (void*)p->comb : (void*)p->comb32;
         p->launches += combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof,
-                                      p->have_acc ? 1 : 0, 0, Nk, Nk, dst, st);
+                                      p->have_acc ? 1 : 0, 0, Nk, Nk, dst, p->tset, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     p->snap_count += ns;
@@ -813,6 +819,7 @@ static void copy_chunk(void* ctx, long long p0, long long np, cudaStream_t st)
     p->chunk_ev.push_back(ev);
     const size_t row = (size_t)p->sep.nrz * p->sep.nrx * p->tsz;
     for (int t : EARLY_TERMS) {
+        if (!((p->tset >> t) & 1u)) continue;
         const size_t off = ((size_t)t * p->npair + (size_t)p0) * row;
         cudaMemcpyAsync((char*)p->host_terms + off, (const char*)p->stage_terms + off, (size_t)np * row,
                         cudaMemcpyDeviceToHost, p->copy_st);
@@ -842,6 +849,7 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     a.st2 = p->aux_st;
     a.W2 = p->W2;
     a.ev = p->aux_ev + 6;
+    a.tmask = p->tset;
     p->launches += terms_launch(a);
 }
 
@@ -864,7 +872,7 @@ static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
     {
         StageScope sc(p, GKE_STAGE_STENCIL);
         p->launches += stencil_launch(d.precision != GKE_PREC_F64, p->wedge ? 1 : 0, terms_dev, p->spec, p->npair,
-                                      p->pair_i, ny, p->sep, d.nu, p->fdw, p->fdl0, p->prof, st);
+                                      p->pair_i, ny, p->sep, d.nu, p->fdw, p->fdl0, p->prof, p->tset, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     return GKE_OK;
@@ -894,13 +902,24 @@ extern "C" gke_status gke_finalize_terms(gke_plan_t p, void* terms, double* prof
     gke_status s = finalize_impl(p, tdev);
     p->host_terms = nullptr;
     if (s != GKE_OK) return s;
-    if (!dev_out && !early) CUDA_TRY(p, cudaMemcpyAsync(terms, tdev, tbytes, cudaMemcpyDeviceToHost, p->st));
+    if (!dev_out && !early) {
+        // the planes of the plan's term set
+        const size_t plane = tbytes / NTERM;
+        for (int t = 0; t < NTERM; ++t) {
+            if (!((p->tset >> t) & 1u)) continue;
+            int t1 = t;
+            while (t1 + 1 < NTERM && ((p->tset >> (t1 + 1)) & 1u)) ++t1;       // runs of planes in one copy
+            CUDA_TRY(p, cudaMemcpyAsync((char*)terms + t * plane, (const char*)tdev + t * plane,
+                                        (size_t)(t1 - t + 1) * plane, cudaMemcpyDeviceToHost, p->st));
+            t = t1;
+        }
+    }
     if (early) {
         // the remaining terms (Phi_y, phi, residual) after the stencils; then
         // the main stream waits for the early copies
         const size_t row = (size_t)p->sep.nrz * p->sep.nrx * p->tsz * (size_t)p->npair;
         for (int t : {GKE_TERM_PHI_Y, GKE_TERM_PHI, GKE_TERM_RESIDUAL})
-            CUDA_TRY(p, cudaMemcpyAsync((char*)terms + (size_t)t * row, (const char*)tdev + (size_t)t * row, row,
+            if ((p->tset >> t) & 1u) CUDA_TRY(p, cudaMemcpyAsync((char*)terms + (size_t)t * row, (const char*)tdev + (size_t)t * row, row,
                                         cudaMemcpyDeviceToHost, p->st));
         cudaEvent_t done = take_event(p);
         CUDA_TRY(p, cudaEventRecord(done, p->copy_st));
@@ -1022,11 +1041,16 @@ extern "C" gke_status gke_compute_graph(gke_plan_t p, const void* fields, int ns
 }
 
 // ------------------------------------------------------- checkpoint files
+static const int CKPT_VERSION = 4;
+static_assert(sizeof(int) == 4 && sizeof(double) == 8, "checkpoint layout");
+
 struct CkptHeader {
     char magic[8];
-    int version, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt;
+    int version, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt, term_set;
     double mean_count, snap_count, Lx, Lz, nu;
 };
+
+static_assert(sizeof(CkptHeader) == 88, "checkpoint header layout");
 
 static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save, 1 restore, 2 merge
 {
@@ -1048,12 +1072,13 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for writing: ") + path);
         CkptHeader h{};
         memcpy(h.magic, "GKECKPT", 8);
-        h.version = 3; h.nx = p->d.nx; h.nz = p->d.nz; h.ny = ny; h.precision = p->d.precision;
+        h.version = CKPT_VERSION; h.nx = p->d.nx; h.nz = p->d.nz; h.ny = ny; h.precision = p->d.precision;
         h.have_acc = p->have_acc; h.mean_count = p->mean_count; h.snap_count = p->snap_count;
         h.Lx = p->d.Lx; h.Lz = p->d.Lz; h.nu = p->d.nu;
         h.pair_domain = p->d.pair_domain;
         h.nzt = p->dec ? p->nzt : 0;
         h.nxt = p->dec ? p->nxt : 0;
+        h.term_set = (int)p->tset;
         bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
         std::vector<char> buf;
         auto put = [&](const void* dptr, size_t bytes) {
@@ -1069,14 +1094,15 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for reading: ") + path);
     CkptHeader h{};
-    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != 3) {
+    if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != CKPT_VERSION) {
         fclose(fp);
         return fail(p, GKE_ERR_IO, "not a GKE checkpoint");
     }
     if (h.nx != p->d.nx || h.nz != p->d.nz || h.ny != ny || h.Lx != p->d.Lx || h.Lz != p->d.Lz || h.nu != p->d.nu ||
-        h.pair_domain != p->d.pair_domain || h.nzt != (p->dec ? p->nzt : 0) || h.nxt != (p->dec ? p->nxt : 0)) {
+        h.pair_domain != p->d.pair_domain || h.nzt != (p->dec ? p->nzt : 0) || h.nxt != (p->dec ? p->nxt : 0) ||
+        h.term_set != (int)p->tset) {
         fclose(fp);
-        return fail(p, GKE_ERR_ARG, "checkpoint grid does not match the plan");
+        return fail(p, GKE_ERR_ARG, "checkpoint grid, domain or term set does not match the plan");
     }
     if (mode == 2 && p->mean_frozen && h.mean_count > 0 && !p->have_acc) {
         fclose(fp);

@@ -53,8 +53,8 @@ int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::
 template <typename TI, typename TC, typename TO>
 __global__ void __launch_bounds__(256)
 k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
-          const double* __restrict__ prof, int beta, int kbase, int Kc, long long cstride,
-          cplx<TO>* __restrict__ comb)
+          const double* __restrict__ prof, int beta, int kbase, int Kc, long long cstride, unsigned tmask,
+          unsigned jmask, cplx<TO>* __restrict__ comb)
 {
     constexpr int KC = CombCfg<TI>::KC;
     typedef cplx<TI> C;
@@ -107,7 +107,7 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         const int kq = k0 + q;
         const int yb = partner ? b : a, ypb = partner ? a : b;
         C v0 = mk((TI)0, (TI)0), v1 = v0;
-        if (kq < Nk) {
+        if (kq < Nk && ((jmask >> j) & 1u)) {         // contractions outside the term set stay zero
             const C* src = raw + ((((long long)j * nblk + yb) * nblk + ypb) * Nk + kq) * 64 + rr * PB + cc;
             if (sizeof(C) == 8) {
                 const float4 f4 = __ldcs((const float4*)src);
@@ -152,6 +152,7 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         cplx<TO>* dst = comb + pair_index(i1, i2, ny) * NTERM * cstride + k;
         #pragma unroll
         for (int t = 0; t < NTERM; ++t) {
+            if (!((tmask >> t) & 1u)) continue;
             cplx<TO> v = mk((TO)T[t].x, (TO)T[t].y);
             if (beta) {
                 v = v + dst[(long long)t * cstride];
@@ -315,20 +316,21 @@ int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long n
 // cstride values per (pair, term), chunk-local index kl at offset kl
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
                    double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
-                   cudaStream_t st)
+                   unsigned terms, cudaStream_t st)
 {
+    const unsigned jobs = job_set(terms);
     const int kc = combine_kc(fp32_in) * CHUNKS;
     const int nblk = (ny + PB - 1) / PB;
     dim3 grid((Kc + kc - 1) / kc, nblk * (nblk + 1) / 2);
     if (!fp32_in)
         k_combine<double, double, double><<<grid, 256, combine_smem(false), st>>>(
-            (const zd*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, (zd*)comb);
+            (const zd*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (zd*)comb);
     else if (out64)
         k_combine<float, float, double><<<grid, 256, combine_smem(true), st>>>(
-            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, (zd*)comb);
+            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (zd*)comb);
     else
         k_combine<float, float, float><<<grid, 256, combine_smem(true), st>>>(
-            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, (zf*)comb);
+            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (zf*)comb);
     return 1;
 }
 

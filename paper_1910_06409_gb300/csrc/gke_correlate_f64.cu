@@ -59,15 +59,19 @@ __device__ __forceinline__ void cmac_conj(cplx<T>& acc, const cplx<T> a, const c
 
 // T = double: RB = 2 (32 x 32 tiles, DFMA bound); T = float: RB = 4 (64 x 64
 // tiles, so each thread does 4 FFMA per shared-memory load)
+// the contractions one launch runs (a term mask may leave some out)
+struct JobList { int n; int j[NJOB]; };
+
 template <typename T, int RB>
 __global__ void __launch_bounds__(256)
-k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, cplx<T>* __restrict__ raw)
+k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, JobList jl,
+            cplx<T>* __restrict__ raw)
 {
     typedef cplx<T> C;
     constexpr int CT = 16 * RB;     // tile edge
     __shared__ C As[SCH][CT];
     __shared__ C Bs[SCH][CT];
-    const int kl = blockIdx.x, k = k0 + kl, job = blockIdx.y;    // chunk-local and global wavenumber
+    const int kl = blockIdx.x, k = k0 + kl, job = jl.j[blockIdx.y];    // chunk-local and global wavenumber
     const bool herm = (job == NJSQ);
     const JobDesc& jd = c_jobs[job];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -147,12 +151,17 @@ k_correlate(const cplx<T>* __restrict__ Xop, int ns, int ny, int Nk, int k0, int
 }
 
 // wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
-void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, int k0, int Kc, void* raw, cudaStream_t st)
+void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, int k0, int Kc, void* raw, unsigned jobs,
+                      cudaStream_t st)
 {
+    JobList jl{};
+    for (int j = 0; j < NJOB; ++j)
+        if ((jobs >> j) & 1u) jl.j[jl.n++] = j;
+    if (jl.n == 0) return;
     if (fp32)
-        k_correlate<float, 4><<<dim3(Kc, NJOB), 256, 0, st>>>((const zf*)Xop, ns, ny, Nk, k0, Kc, (zf*)raw);
+        k_correlate<float, 4><<<dim3(Kc, jl.n), 256, 0, st>>>((const zf*)Xop, ns, ny, Nk, k0, Kc, jl, (zf*)raw);
     else
-        k_correlate<double, 2><<<dim3(Kc, NJOB), 256, 0, st>>>((const zd*)Xop, ns, ny, Nk, k0, Kc, (zd*)raw);
+        k_correlate<double, 2><<<dim3(Kc, jl.n), 256, 0, st>>>((const zd*)Xop, ns, ny, Nk, k0, Kc, jl, (zd*)raw);
 }
 
 }  // namespace gke

@@ -11,12 +11,49 @@ namespace gke {
 enum Prof { PR_U = 0, PR_V, PR_W, PR_P, PR_DU, PR_EPS, PR_Q, PR_UV, PR_PV, PR_QU, PR_QV, PR_QW, NPR };
 
 void upload_jobs(cudaStream_t st);
+
+// Terms a request expands to: Phi_y and phi carry the Step-3 FD parts of A
+// (Eq. 10-11); the residual takes Y1 / Y2 derivatives of Phi_y and phi.
+inline unsigned term_set(unsigned m)
+{
+    const unsigned all = (1u << NTERM) - 1u;
+    m = m ? (m & all) : all;
+    if (m & (1u << T_RES)) m |= (1u << T_PHIY) | (1u << T_PHI);
+    if (m & ((1u << T_PHIY) | (1u << T_PHI))) m |= 1u << T_A;
+    return m;
+}
+
+// Contractions (bit j = job j) the spectra of a term set combine
+// (k_combine: A = -2 S0, Phi_x from Gx and D, Phi_y from QV and X2, Phi_z from
+// Gz and D, phi from QV, X2 and F, xi from E, the residual from Gx, Gz, D, E)
+inline unsigned job_set(unsigned t)
+{
+    auto b = [](int j) { return 1u << j; };
+    unsigned j = 0;
+    if (t & (1u << T_A)) j |= b(J_D);
+    if (t & (1u << T_PHIX)) j |= b(J_GX) | b(J_D);
+    if (t & (1u << T_PHIY)) j |= b(J_QV) | b(J_X);
+    if (t & (1u << T_PHIZ)) j |= b(J_GZ) | b(J_D);
+    if (t & (1u << T_PHI)) j |= b(J_QV) | b(J_X) | b(J_F);
+    if (t & (1u << T_XI)) j |= b(J_E);
+    if (t & (1u << T_RES)) j |= b(J_GX) | b(J_GZ) | b(J_D) | b(J_E);
+    return j;
+}
+
+// the n-th set bit of m (n < popcount(m))
+__host__ __device__ __forceinline__ int nth_bit(unsigned m, int n)
+{
+    for (int i = 0; i < 32; ++i)
+        if ((m >> i) & 1u) { if (n == 0) return i; --n; }
+    return -1;
+}
 size_t combine_smem(bool fp32);
 int combine_kc(bool fp32);
 
 __global__ void k_mean_accum(const zd* fields, int ns, int ny, long long plane, double* mean_sum);
 __global__ void k_reduce_partials(const double* part, int nvals, int nb, double* out);
-void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, int k0, int Kc, void* raw, cudaStream_t st);
+void correlate_launch(bool fp32, const void* Xop, int ns, int ny, int Nk, int k0, int Kc, void* raw, unsigned jobs,
+                      cudaStream_t st);
 
 // products stage (gke_products.cu); complex<TF> buffers passed as void*
 struct ProdArgs {
@@ -37,7 +74,7 @@ cudaError_t products_set_attrs(int lim);
 // term spectra (gke_combine.cu)
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
                    double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
-                   cudaStream_t st);
+                   unsigned terms, cudaStream_t st);
 int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
                     int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st);
 size_t fold_dec_smem(bool c64, int R, int nx, bool wedge);
@@ -77,6 +114,7 @@ struct TermArgs {
     const void* comb; void* W; const int* pair_i; long long npair, pair_chunk;
     int ny, nz, nx, cw, rz; double inv_count; const double* prof; const void* tw_x; const void* tw_z;
     void* terms; float* spec; SepMap sep; cudaStream_t st;
+    unsigned tmask = (1u << NTERM) - 1u;  // terms to transform (term_set)
     // optional: a second stream and scratch buffer (column and row passes of
     // successive chunks overlap); a callback after the launches of each pair
     // chunk [p0, p0 + np), given the stream its row pass ran on
@@ -90,7 +128,7 @@ int terms_launch(const TermArgs& a);
 cudaError_t terms_set_attrs(int lim);
 int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
                    const SepMap& sep, double nu, const double* fdw, const int* fdl0, const double* prof,
-                   cudaStream_t st);
+                   unsigned tmask, cudaStream_t st);
 
 __global__ void k_freeze_mean(double* mean_sum, double mean_count, int mirror, int ny, double* mean);
 __global__ void k_profiles(const double* mean_sum, double mean_count, const double* stats,

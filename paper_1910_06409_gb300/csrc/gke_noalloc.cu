@@ -99,6 +99,8 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
         d.ny < 5 || d.ny > 1024 || nsnap < 1)
         return fail(GKE_ERR_ARG, "sizes out of range (nx, nz powers of two in [8, 1024], 5 <= ny <= 1024, nsnap >= 1)");
     if (!(d.Lx > 0) || !(d.Lz > 0) || !(d.nu > 0)) return fail(GKE_ERR_ARG, "Lx, Lz, nu must be > 0");
+    if (d.term_mask & ~GKE_ALL_TERMS) return fail(GKE_ERR_ARG, "term_mask has bits above GKE_NTERM");
+    const unsigned tset = term_set(d.term_mask);
     for (int j = 1; j < d.ny; ++j)
         if (!(d.y[j] > d.y[j - 1])) return fail(GKE_ERR_ARG, "y must be strictly increasing");
     if (!is_device(fields) || !is_device(terms) || (profiles && !is_device(profiles)))
@@ -189,8 +191,8 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     a.cw_ci = cw_ci; a.rz_rp = rz_rp; a.cw_cf = cw_cf; a.yb_cf = yb_cf; a.eps_kchunk = eps_kchunk;
     a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = fdw; a.fdl0 = fdl0; a.st = st;
     products_launch<double>(a);
-    correlate_launch(false, Xop, ns, ny, Nk, 0, Nk, raw, st);
-    combine_launch(false, true, raw, ny, nz, nx, d.Lx, d.Lz, d.nu, prof, 0, 0, Nk, Nk, comb, st);
+    correlate_launch(false, Xop, ns, ny, Nk, 0, Nk, raw, job_set(tset), st);
+    combine_launch(false, true, raw, ny, nz, nx, d.Lx, d.Lz, d.nu, prof, 0, 0, Nk, Nk, comb, tset, st);
     // Step 3: profiles, inverse transforms, stencils
     k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, stats, (double)ns, (long long)nx * nz, d.nu, 0, fdw,
                                                   fdl0, ny, prof);
@@ -198,8 +200,9 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     t.fp32 = false; t.comb64 = true; t.comb = comb; t.W = W; t.pair_i = pair_i; t.npair = npair; t.pair_chunk = npair;
     t.ny = ny; t.nz = nz; t.nx = nx; t.cw = cw_tc; t.rz = rz_tr; t.inv_count = 1.0 / ns; t.prof = prof;
     t.tw_x = twx; t.tw_z = twz; t.terms = terms; t.spec = nullptr; t.sep = full_sep(nz, nx); t.st = st;
+    t.tmask = tset;
     terms_launch(t);
-    stencil_launch(false, 0, terms, nullptr, npair, pair_i, ny, full_sep(nz, nx), d.nu, fdw, fdl0, prof, st);
+    stencil_launch(false, 0, terms, nullptr, npair, pair_i, ny, full_sep(nz, nx), d.nu, fdw, fdl0, prof, tset, st);
     if (profiles) TRY(cudaMemcpyAsync(profiles, prof, GKE_NPROF * ny * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int bad = 0;
     TRY(cudaMemcpyAsync(&bad, nonfinite, sizeof(int), cudaMemcpyDeviceToHost, st));

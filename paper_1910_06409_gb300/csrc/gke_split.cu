@@ -218,17 +218,27 @@ __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int N
 }
 
 // ------------------------------------------------------ tensor-core kernel
-__device__ __forceinline__ void decode_tile(int jt, int MT, int& job, int& mt, int& nt)
+// the contractions one launch runs (a term mask may leave some out): the
+// square ones, 3 bits each in sq (nsq of them), and, if d, the Hermitian D
+struct TcSel { int nsq; unsigned sq; int d; };
+
+__host__ __device__ __forceinline__ int sel_tiles(const TcSel& s, int MT)
+{
+    return s.nsq * MT * MT + (s.d ? MT * (MT + 1) / 2 : 0);
+}
+
+__device__ __forceinline__ void decode_tile(int jt, int MT, const TcSel& sel, int& job, int& mt, int& nt)
 {
     const int sq = MT * MT;
-    if (jt < NJSQ * sq) {
-        job = jt / sq;
-        int r = jt - job * sq;
+    if (jt < sel.nsq * sq) {
+        const int js = jt / sq;
+        job = (int)((sel.sq >> (3 * js)) & 7u);
+        int r = jt - js * sq;
         mt = r / MT;
         nt = r - mt * MT;
     } else {
         job = NJSQ;
-        int r = jt - NJSQ * sq;
+        int r = jt - sel.nsq * sq;
         mt = 0;
         while (r >= MT - mt) { r -= MT - mt; ++mt; }
         nt = mt + r;
@@ -266,13 +276,13 @@ struct TcPipeBars {
 
 __global__ void __launch_bounds__(TCP_THREADS, 1)
 k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, int G, int MT, int ny, int cov,
-               long long nitems, zf* __restrict__ raw, int* __restrict__ err)
+               long long nitems, TcSel sel, zf* __restrict__ raw, int* __restrict__ err)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     TcPipeBars* bars = (TcPipeBars*)(smem + SMP_BAR);
     volatile int* abort = &bars->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int njt = NJSQ * MT * MT + MT * (MT + 1) / 2;
+    const int njt = sel_tiles(sel, MT);
     if (threadIdx.x == 0) {
         for (int st = 0; st < NST; ++st) {
             mbar_init(&bars->full[st], 1);
@@ -305,7 +315,7 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
             for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
                 const int k = (int)(it / njt);
                 int job, mt, nt;
-                decode_tile((int)(it % njt), MT, job, mt, nt);
+                decode_tile((int)(it % njt), MT, sel, job, mt, nt);
                 const TcJob& jd = c_tcjobs[job];
                 for (int pass = 0; pass < 2; ++pass)
                     for (int t = 0; t < jd.nterm; ++t)
@@ -336,7 +346,7 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
             int st = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
             for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
-                const int job = [&] { int j, m, n; decode_tile((int)(it % njt), MT, j, m, n); return j; }();
+                const int job = [&] { int j, m, n; decode_tile((int)(it % njt), MT, sel, j, m, n); return j; }();
                 const TcJob& jd = c_tcjobs[job];
                 if (!mbar_wait_ab(&bars->acc_empty[acc], aph ^ 1, abort)) { fail(); break; }
                 tc_fence_after();
@@ -381,7 +391,7 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
         for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
             const int k = (int)(it / njt);
             int job, mt, nt;
-            decode_tile((int)(it % njt), MT, job, mt, nt);
+            decode_tile((int)(it % njt), MT, sel, job, mt, nt);
             if (!mbar_wait_ab(&bars->acc_full[acc], aph, abort)) { fail(); break; }
             tc_fence_after();
             const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
@@ -432,7 +442,7 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
 // for every snapshot the term is skipped (exact: it adds zeros).  With
 // no-slip walls (u = v = w = 0) only the p-v row survives.
 __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, int cov,
-                            zf* __restrict__ raw)
+                            unsigned jobs, zf* __restrict__ raw)
 {
     __shared__ int nz_edge[NFIELD][4];       // field f has a nonzero value on edge row cov + i (i < 4)
     const int kl = blockIdx.x, k = k0 + kl;
@@ -453,7 +463,7 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
         const bool row_edge = e < n_row;
         if (row_edge) { y = cov + e / ny; yp = e % ny; }
         else { int r = e - n_row; y = r / ne; yp = cov + r % ne; }
-        if (job == NJSQ && yp < y) continue;
+        if ((job == NJSQ && yp < y) || !((jobs >> job) & 1u)) continue;
         const TcJob jd = c_tcjobs[job];
         float sr = 0.f, si = 0.f;
         for (int t = 0; t < jd.nterm; ++t) {
@@ -514,29 +524,35 @@ cudaError_t split_setup(cudaStream_t st)
 
 // wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
 gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, zf* raw,
-                           cudaStream_t st, std::string& err, int* launches)
+                           unsigned jobs, cudaStream_t st, std::string& err, int* launches)
 {
+    *launches = 0;
+    TcSel sel{};
+    for (int j = 0; j < NJSQ; ++j)
+        if ((jobs >> j) & 1u) sel.sq |= (unsigned)j << (3 * sel.nsq++);
+    sel.d = (jobs >> J_D) & 1u;
+    if (sel.nsq == 0 && !sel.d) return GKE_OK;
     int MT, cov;
     tile_geometry(ny, MT, cov);
     const int G = (ns + KS - 1) / KS;
     bf16* Aop = (bf16*)w.ops;
     bf16* Bop = (bf16*)((char*)w.ops + (size_t)Kc * NFIELD * G * MT * A_STAGE * sizeof(bf16));
-    *launches = 0;
     k_split_prep_A<<<(unsigned)((long long)Kc * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov,
                                                                                     Aop);
     k_split_prep_B<<<(unsigned)((long long)Kc * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, Bop);
-    const long long njt = (long long)NJSQ * MT * MT + MT * (MT + 1) / 2;
+    const long long njt = sel_tiles(sel, MT);
     {
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const long long nitems = (long long)Kc * njt;
         const unsigned grid = (unsigned)std::min<long long>(nitems, std::max(nsm, 1));
-        k_corr_tc_pipe<<<grid, TCP_THREADS, SMP_TOTAL, st>>>(Aop, Bop, Kc, G, MT, ny, cov, nitems, raw, w.err);
+        k_corr_tc_pipe<<<grid, TCP_THREADS, SMP_TOTAL, st>>>(Aop, Bop, Kc, G, MT, ny, cov, nitems, sel, raw,
+                                                              w.err);
     }
     *launches = 3;
     if (cov < ny) {
-        k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, cov, raw);
+        k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, cov, jobs, raw);
         *launches += 1;
     }
     cudaError_t e = cudaGetLastError();

@@ -17,7 +17,7 @@ struct SplitWork {
 gke_status split_alloc(SplitWork& w, int ny, int ns, int Kc);
 cudaError_t split_setup(cudaStream_t st);
 gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, zf* raw,
-                           cudaStream_t st, std::string& err, int* launches);
+                           unsigned jobs, cudaStream_t st, std::string& err, int* launches);
 gke_status split_check(SplitWork& w, cudaStream_t st, std::string& err);
 void split_free(SplitWork& w);
 

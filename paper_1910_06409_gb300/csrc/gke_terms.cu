@@ -30,7 +30,8 @@ namespace gke {
 // complex.
 template <typename TF, typename TB>
 __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pair0, int nz, int nx, int CW,
-                                const cplx<TF>* __restrict__ tw_z, SepMap sm, cplx<TF>* __restrict__ W)
+                                const cplx<TF>* __restrict__ tw_z, SepMap sm, unsigned tmask,
+                                cplx<TF>* __restrict__ W)
 {
     typedef cplx<TF> C;
     extern __shared__ __align__(16) unsigned char sh_raw_tc[];
@@ -38,7 +39,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
     C* b0 = stw + nz;
     C* b1 = b0 + CW * nz;
     const int nxh = nx / 2 + 1, Nk = nz * nxh;
-    const int kx0 = blockIdx.x * CW, q = blockIdx.y;
+    const int kx0 = blockIdx.x * CW, q = nth_bit(tmask, blockIdx.y);     // grid.y: the terms of tmask
     const long long pl = blockIdx.z, p = pair0 + pl;
     load_twiddles(stw, tw_z, nz);
     const cplx<TB>* src = comb + (p * NTERM + q) * (long long)Nk;
@@ -65,7 +66,7 @@ __global__ void k_terms_colpass(const cplx<TB>* __restrict__ comb, long long pai
 template <typename TF, typename TB, int N1, int N2, bool US>
 __global__ void __launch_bounds__(256)
 k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, int CW,
-                  const cplx<TF>* __restrict__ tw_z, SepMap sm, cplx<TF>* __restrict__ W)
+                  const cplx<TF>* __restrict__ tw_z, SepMap sm, unsigned tmask, cplx<TF>* __restrict__ W)
 {
     typedef cplx<TF> C;
     constexpr int N = N1 * N2;
@@ -73,7 +74,7 @@ k_terms_colpass_r(const cplx<TB>* __restrict__ comb, long long pair0, int nxh, i
     C* stw = (C*)sh_raw_tcr;
     C* xs = stw + N;
     const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
-    const int kx = blockIdx.x * CW + c, q = blockIdx.y;
+    const int kx = blockIdx.x * CW + c, q = nth_bit(tmask, blockIdx.y);
     const long long pl = blockIdx.z, p = pair0 + pl;
     const int Nk = N * nxh;
     load_twiddles(stw, tw_z, N);
@@ -132,7 +133,7 @@ template <typename TF, typename TO>
 __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
                                 long long npair, int ny, int nx, int RZ, double inv_count,
                                 const double* __restrict__ prof, const cplx<TF>* __restrict__ tw_x, SepMap sm,
-                                TO* __restrict__ terms, float* __restrict__ spec)
+                                unsigned tmask, TO* __restrict__ terms, float* __restrict__ spec)
 {
     typedef cplx<TF> C;
     extern __shared__ __align__(16) unsigned char sh_raw_tr[];
@@ -157,9 +158,9 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
         int z = z0 + r;
         int ta = 2 * j, tb = 2 * j + 1;
         const C* wa = W + ((pl * NTERM + ta) * nz + z) * nxh;
-        C A, B = mk((TF)0, (TF)0);
-        if (k < nxh) A = wa[k]; else A = conj(wa[nx - k]);
-        if (tb < NTERM) {
+        C A = mk((TF)0, (TF)0), B = A;               // terms outside tmask: zero, not stale W
+        if ((tmask >> ta) & 1u) { if (k < nxh) A = wa[k]; else A = conj(wa[nx - k]); }
+        if (tb < NTERM && ((tmask >> tb) & 1u)) {
             const C* wb = W + ((pl * NTERM + tb) * nz + z) * nxh;
             if (k < nxh) B = wb[k]; else B = conj(wb[nx - k]);
         }
@@ -171,7 +172,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
     for (int t = threadIdx.x; t < nrow * NTERM * nx; t += blockDim.x) {
         int r = t / (NTERM * nx), rem = t - r * NTERM * nx, q = rem / nx, x = rem - q * nx;
         const int xr = sm.xcol(x);
-        if (xr < 0) continue;
+        if (xr < 0 || !((tmask >> q) & 1u)) continue;
         C v = sh[(r * 4 + (q >> 1)) * nx + x];
         const TF sp = ((q & 1) ? v.y : v.x) * (TF)inv_count;
         const long long e = (long long)(z0 + r) * sm.nrx + xr;
@@ -189,7 +190,8 @@ template <typename TF, typename TO, int N1, int N2, bool US>
 __global__ void __launch_bounds__(256)
 k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
                   int ny, int RZ, double inv_count, const double* __restrict__ prof,
-                  const cplx<TF>* __restrict__ tw_x, SepMap sm, TO* __restrict__ terms, float* __restrict__ spec)
+                  const cplx<TF>* __restrict__ tw_x, SepMap sm, unsigned tmask, TO* __restrict__ terms,
+                  float* __restrict__ spec)
 {
     typedef cplx<TF> C;
     constexpr int N = N1 * N2, nxh = N / 2 + 1;
@@ -215,15 +217,17 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
     C* xr = xs + r * N1 * (N2 + 1);
     for (int jq = 0; jq < 4; ++jq) {
         const int ta = 2 * jq, tb = 2 * jq + 1;
+        const bool ha = (tmask >> ta) & 1u, hb = tb < NTERM && ((tmask >> tb) & 1u);
+        if (!ha && !hb) continue;                   // uniform over the CTA
         const C* wa = W + ((pl * NTERM + ta) * nz + (live ? z : 0)) * nxh;
         const C* wb = W + ((pl * NTERM + (tb < NTERM ? tb : ta)) * nz + (live ? z : 0)) * nxh;
         C v[N1];
         #pragma unroll
         for (int m = 0; m < N1; ++m) {
             const int k = lane + N2 * m;
-            C A, B = mk((TF)0, (TF)0);
-            if (k < nxh) A = wa[k]; else A = conj(wa[N - k]);
-            if (tb < NTERM) { if (k < nxh) B = wb[k]; else B = conj(wb[N - k]); }
+            C A = mk((TF)0, (TF)0), B = A;           // terms outside tmask: zero, not stale W
+            if (ha) { if (k < nxh) A = wa[k]; else A = conj(wa[N - k]); }
+            if (hb) { if (k < nxh) B = wb[k]; else B = conj(wb[N - k]); }
             if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
             v[m] = mk(A.x - B.y, A.y + B.x);
         }
@@ -239,6 +243,7 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
                 for (int h = 0; h < 2; ++h) {
                     const int q = 2 * jq + h;
                     if (q >= NTERM) break;
+                    if (!(h ? hb : ha)) continue;
                     const TF sp = (h ? v[m].y : v[m].x) * ic;
                     st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[q]));
                     if (spec != nullptr) {
@@ -273,6 +278,7 @@ int terms_launch_t(const TermArgs& a)
         }
     }
     int launches = 0;
+    const unsigned ntm = (unsigned)__builtin_popcount(a.tmask);     // column passes: the terms of tmask
     long long c = 0;
     for (long long p0 = 0; p0 < a.npair; p0 += a.pair_chunk, ++c) {
         const long long np = a.pair_chunk < a.npair - p0 ? a.pair_chunk : a.npair - p0;
@@ -282,18 +288,18 @@ int terms_launch_t(const TermArgs& a)
         if (two && c >= 2) cudaStreamWaitEvent(sc, ev_row[buf], 0);     // W buffer free again
         if (a.nz == 256) {
             constexpr int CWR = 16;
-            const dim3 g((nxh + CWR - 1) / CWR, NTERM, (unsigned)np);
+            const dim3 g((nxh + CWR - 1) / CWR, ntm, (unsigned)np);
             const size_t sh = (256 + 16 * (16 * CWR + 1)) * sizeof(C);
             if (us)
                 k_terms_colpass_r<TF, TB, 16, 16, true><<<g, CWR * 16, sh, sc>>>(
-                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, W);
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, a.tmask, W);
             else
                 k_terms_colpass_r<TF, TB, 16, 16, false><<<g, CWR * 16, sh, sc>>>(
-                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, W);
+                    (const cplx<TB>*)a.comb, p0, nxh, CWR, (const C*)a.tw_z, a.sep, a.tmask, W);
         } else {
-            k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, NTERM, (unsigned)np), 256,
+            k_terms_colpass<TF, TB><<<dim3((nxh + a.cw - 1) / a.cw, ntm, (unsigned)np), 256,
                                       (1 + 2 * a.cw) * a.nz * sizeof(C), sc>>>(
-                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, (const C*)a.tw_z, a.sep, W);
+                (const cplx<TB>*)a.comb, p0, a.nz, a.nx, a.cw, (const C*)a.tw_z, a.sep, a.tmask, W);
         }
         if (two) {
             cudaEventRecord(ev_col[buf], sc);
@@ -306,16 +312,16 @@ int terms_launch_t(const TermArgs& a)
             if (us)
                 k_terms_rowpass_r<TF, TO, 16, 16, true><<<g, RZR * 16, sh, sr>>>(
                     W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
-                    (TO*)a.terms, a.spec);
+                    a.tmask, (TO*)a.terms, a.spec);
             else
                 k_terms_rowpass_r<TF, TO, 16, 16, false><<<g, RZR * 16, sh, sr>>>(
                     W, a.pair_i, p0, a.npair, a.ny, RZR, a.inv_count, a.prof, (const C*)a.tw_x, a.sep,
-                    (TO*)a.terms, a.spec);
+                    a.tmask, (TO*)a.terms, a.spec);
         } else {
             k_terms_rowpass<TF, TO><<<dim3((a.sep.nrz + a.rz - 1) / a.rz, (unsigned)np), 256,
                                       (1 + 8 * a.rz) * a.nx * sizeof(C), sr>>>(
                 W, a.pair_i, p0, a.npair, a.ny, a.nx, a.rz, a.inv_count, a.prof, (const C*)a.tw_x,
-                a.sep, (TO*)a.terms, a.spec);
+                a.sep, a.tmask, (TO*)a.terms, a.spec);
         }
         if (two) cudaEventRecord(ev_row[buf], sr);
         launches += 2;
@@ -611,12 +617,16 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
 template <bool WEDGE, bool US>
 static int stencil_launch_t(bool fp32, void* terms, float* spec, long long npair, const int* pair_i, int ny,
                             const SepMap& sm, double nu, const double* fdw, const int* fdl0, const double* prof,
-                            cudaStream_t st)
+                            unsigned tmask, cudaStream_t st)
 {
+    // Phi_y and phi take the FD parts of A; the residual those of Phi_y and phi
+    const bool pass1 = (tmask & ((1u << T_PHIY) | (1u << T_PHI))) != 0, pass2 = ((tmask >> T_RES) & 1u) != 0;
+    if (!pass1) return 0;
     const long long N = (long long)sm.nrz * sm.nrx;
     dim3 gs((unsigned)npair, (unsigned)((N + 255) / 256));
     if (!fp32) {
         k_stencil_A<WEDGE, US><<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, sm, nu, fdw, fdl0);
+        if (!pass2) return 1;
         k_stencil_res<WEDGE, US><<<gs, 256, 0, st>>>((double*)terms, npair, pair_i, ny, sm, fdw, fdl0);
         return 2;
     }
@@ -624,20 +634,21 @@ static int stencil_launch_t(bool fp32, void* terms, float* spec, long long npair
     k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
     dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
     k_stencil_A32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, nu, fdl0, sc);
+    if (!pass2) return 2;
     k_stencil_res32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, fdl0, sc);
     return 3;
 }
 
 int stencil_launch(bool fp32, int wedge, void* terms, float* spec, long long npair, const int* pair_i, int ny,
                    const SepMap& sm, double nu, const double* fdw, const int* fdl0, const double* prof,
-                   cudaStream_t st)
+                   unsigned tmask, cudaStream_t st)
 {
     const bool us = sm.negz != nullptr;
     if (wedge)
-        return us ? stencil_launch_t<true, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st)
-                  : stencil_launch_t<true, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st);
-    return us ? stencil_launch_t<false, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st)
-              : stencil_launch_t<false, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, st);
+        return us ? stencil_launch_t<true, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, tmask, st)
+                  : stencil_launch_t<true, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, tmask, st);
+    return us ? stencil_launch_t<false, true>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, tmask, st)
+              : stencil_launch_t<false, false>(fp32, terms, spec, npair, pair_i, ny, sm, nu, fdw, fdl0, prof, tmask, st);
 }
 
 // ----------------------------------------------- Step-1 mean, on device

@@ -6,8 +6,8 @@ gke_checkpoint; this module adds the files on the host into one that
 gke_restore loads, with the same result as gke_merge.  File layout (little
 endian; the C struct of the library, include/gke.h):
 
-  header   char magic[8] = "GKECKPT\\0"; int32 version (3), nx, nz, ny,
-           precision, have_acc, pair_domain, nzt, nxt; 4 bytes padding;
+  header   char magic[8] = "GKECKPT\\0"; int32 version (4), nx, nz, ny,
+           precision, have_acc, pair_domain, nzt, nxt, term_set;
            float64 mean_count, snap_count, Lx, Lz, nu
   float64  mean_sum[4][ny]          Step-1 sums of U, V, W, P
   float64  stats[7][ny]             one-point sums
@@ -23,12 +23,12 @@ import numpy as np
 
 HEADER = np.dtype([("magic", "S8"), ("version", "<i4"), ("nx", "<i4"), ("nz", "<i4"), ("ny", "<i4"),
                    ("precision", "<i4"), ("have_acc", "<i4"), ("pair_domain", "<i4"), ("nzt", "<i4"),
-                   ("nxt", "<i4"), ("pad", "<i4"), ("mean_count", "<f8"), ("snap_count", "<f8"),
+                   ("nxt", "<i4"), ("term_set", "<i4"), ("mean_count", "<f8"), ("snap_count", "<f8"),
                    ("Lx", "<f8"), ("Lz", "<f8"), ("nu", "<f8")])
 MAGIC = b"GKECKPT"
-VERSION = 3
+VERSION = 4
 NSTAT = 7
-GRID = ("nx", "nz", "ny", "pair_domain", "nzt", "nxt", "Lx", "Lz", "nu")
+GRID = ("nx", "nz", "ny", "pair_domain", "nzt", "nxt", "term_set", "Lx", "Lz", "nu")
 
 
 class CheckpointError(ValueError):
@@ -69,7 +69,6 @@ def write(path: str, ck: dict) -> None:
         h[n] = v
     h["magic"] = MAGIC
     h["version"] = VERSION
-    h["pad"] = 0
     h["have_acc"] = 1 if ck["acc"] is not None else 0
     with open(path, "wb") as f:
         f.write(h.tobytes())

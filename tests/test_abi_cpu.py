@@ -69,3 +69,16 @@ def test_host_fd_weights_bad_args(native):
         native.gke_fd_weights(np.arange(4.0), 0)
     with pytest.raises(native.GkeError):
         native.gke_fd_weights(np.arange(8.0), 8)
+
+
+def test_term_set_closure(native):
+    """gke_term_set (host logic): Phi_y and phi bring A (their Step-3 FD
+    parts, Eq. 10-11); the residual brings Phi_y, phi and A; 0 means all."""
+    A, PX, PY, PZ, PH, XI, RES = (1 << t for t in range(7))
+    f = native.gke_term_set
+    assert f(0) == 127
+    assert f(A) == A and f(PX) == PX and f(PZ) == PZ and f(XI) == XI
+    assert f(PY) == PY | A and f(PH) == PH | A
+    assert f(RES) == RES | PY | PH | A
+    assert f(PX | XI) == PX | XI
+    assert f(127) == 127 and f(1 << 9) == 127      # bits above the terms are ignored here

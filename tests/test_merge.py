@@ -18,7 +18,7 @@ from paper_1910_06409_gb300 import merge as M
 
 def _fake(rank, ny=7, nacc=50):
     rng = np.random.default_rng(100 + rank)
-    hdr = {"nx": 16, "nz": 8, "ny": ny, "precision": 0, "pair_domain": 0, "nzt": 0, "nxt": 0,
+    hdr = {"nx": 16, "nz": 8, "ny": ny, "precision": 0, "pair_domain": 0, "nzt": 0, "nxt": 0, "term_set": 127,
            "mean_count": 2.0 + rank, "snap_count": 2.0 + rank, "Lx": 12.5, "Lz": 6.25, "nu": 0.005}
     return {"header": hdr, "mean_sum": rng.standard_normal(4 * ny), "stats": rng.standard_normal(M.NSTAT * ny),
             "acc": rng.standard_normal(nacc) + 1j * rng.standard_normal(nacc)}
@@ -49,6 +49,12 @@ def test_merge_rejects_mismatch_and_truncation(tmp_path):
     M.write(pb, b)
     with pytest.raises(M.CheckpointError):
         M.merge([pa, pb], str(tmp_path / "m.ckpt"))
+    c = _fake(2)
+    c["header"]["term_set"] = 1                 # accumulators of another term set
+    pc = str(tmp_path / "c.ckpt")
+    M.write(pc, c)
+    with pytest.raises(M.CheckpointError):
+        M.merge([pa, pc], str(tmp_path / "m.ckpt"))
     with open(pb, "wb") as f:
         f.write(b"GKECKPT")
     with pytest.raises(M.CheckpointError):
