@@ -120,7 +120,18 @@ typedef struct {
     int under_x[4];        /* undersampling of r_x {t1, t2, s1, s2}; all 0 = full        */
     int under_z[4];        /* undersampling of r_z, same rule                            */
     unsigned term_mask;    /* terms to compute: bit t = GKE_TERM t; 0 = all (see below)  */
+    const char* tune_cache;/* NULL: built-in schedule; else a tuning file (see below)    */
 } gke_desc;
+
+/* tune_cache: path of a text file of tuned schedules, one line per device
+ * and problem shape.  gke_plan looks the plan's line up; if there is none it
+ * times the candidates of each knob on the device (on the plan's workspaces,
+ * before any data arrives; results do not depend on the knobs) and appends
+ * the fastest: the pair-chunk size of the inverse transforms (scratch W of
+ * 48, 96 or 192 MiB per chunk) and the wavenumbers per CTA of the combine
+ * kernel (1, 2, 4 on the FP64 path; 2, 4, 8 otherwise).  An unreadable or
+ * unwritable file only skips the lookup or the store.  gke_plan_knobs reports
+ * what a plan uses.                                                         */
 
 /* term_mask: the plan computes the requested terms and the terms they are
  * derived from -- A for Phi_y and phi (Step-3 FD parts, Eq. 10-11), and A,
@@ -188,6 +199,11 @@ long long gke_npair(gke_plan_t plan);
  * not NULL the kept indices m_z[nrz], m_x[nrx] (host arrays).              */
 gke_status gke_separation_labels(gke_plan_t plan, int* nrz, int* nrx, int* mz, int* mx);
 long long gke_terms_bytes(gke_plan_t plan);
+
+/* Schedule of a plan: transform scratch per pair chunk (MiB), wavenumbers
+ * per combine CTA, and where they came from (0 built-in, 1 tuning file,
+ * 2 measured by this gke_plan).  NULL outputs are skipped.                  */
+gke_status gke_plan_knobs(gke_plan_t plan, int* w_chunk_mib, int* comb_kc, int* source);
 
 /* Forget all accumulated statistics and the mean.                            */
 gke_status gke_reset(gke_plan_t plan);

@@ -26,7 +26,7 @@ GKE_NTERM, GKE_NPROF = len(TERMS), len(PROFILES)
 # every symbol include/gke.h declares
 EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_snapshot", "gke_finalize_terms",
            "gke_compute", "gke_compute_graph", "gke_pair_labels", "gke_npair", "gke_separation_labels",
-           "gke_terms_bytes", "gke_term_set", "gke_reset", "gke_checkpoint",
+           "gke_terms_bytes", "gke_term_set", "gke_plan_knobs", "gke_reset", "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy")
 STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
@@ -37,7 +37,8 @@ class gke_desc(ctypes.Structure):
                 ("Lx", ctypes.c_double), ("Lz", ctypes.c_double), ("nu", ctypes.c_double),
                 ("y", ctypes.POINTER(ctypes.c_double)),
                 ("max_snap", ctypes.c_int), ("precision", ctypes.c_int), ("pair_domain", ctypes.c_int),
-                ("under_x", ctypes.c_int * 4), ("under_z", ctypes.c_int * 4), ("term_mask", ctypes.c_uint)]
+                ("under_x", ctypes.c_int * 4), ("under_z", ctypes.c_int * 4), ("term_mask", ctypes.c_uint),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class GkeError(RuntimeError):
@@ -76,6 +77,8 @@ def lib():
             "gke_merge": (i, [vp, cp]),
             "gke_fd_weights": (i, [dp, i, i, dp]),
             "gke_term_set": (ctypes.c_uint, [ctypes.c_uint]),
+            "gke_plan_knobs": (i, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]),
             "gke_set_timing": (i, [vp, i]),
             "gke_stage_times": (i, [vp, vp]),
             "gke_launch_count": (ctypes.c_longlong, [vp]),
@@ -111,11 +114,13 @@ def _check(status: int, plan) -> None:
 
 
 def gke_plan(nx, nz, ny, Lx, Lz, nu, y, max_snap, precision=GKE_PREC_F64, stream=None,
-             pair_domain=GKE_DOMAIN_TRIANGLE, under_x=(0, 0, 0, 0), under_z=(0, 0, 0, 0), term_mask=0):
+             pair_domain=GKE_DOMAIN_TRIANGLE, under_x=(0, 0, 0, 0), under_z=(0, 0, 0, 0), term_mask=0,
+             tune_cache=None):
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), max_snap,
-                    precision, pair_domain, (ctypes.c_int * 4)(*under_x), (ctypes.c_int * 4)(*under_z), term_mask)
+                    precision, pair_domain, (ctypes.c_int * 4)(*under_x), (ctypes.c_int * 4)(*under_z), term_mask,
+                    None if tune_cache is None else str(tune_cache).encode())
     out = ctypes.c_void_p()
     st = lib().gke_plan(ctypes.byref(desc), stream, ctypes.byref(out))
     _check(st, None)
@@ -144,6 +149,13 @@ def gke_compute(plan, fields, nsnap, terms, profiles=None):
 
 def gke_compute_graph(plan, fields, nsnap, terms, profiles=None):
     _check(lib().gke_compute_graph(plan, ptr(fields), nsnap, ptr(terms), ptr(profiles)), plan)
+
+
+def gke_plan_knobs(plan):
+    """(transform scratch per pair chunk in MiB, wavenumbers per combine CTA, source)."""
+    w, kc, src = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().gke_plan_knobs(plan, ctypes.byref(w), ctypes.byref(kc), ctypes.byref(src)), plan)
+    return w.value, kc.value, src.value
 
 
 def gke_term_set(term_mask: int) -> int:
@@ -209,7 +221,7 @@ def gke_compute_noalloc(nx, nz, ny, Lx, Lz, nu, y, fields, nsnap, terms, profile
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     desc = gke_desc(nx, nz, ny, Lx, Lz, nu, yy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), nsnap,
-                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE, (ctypes.c_int * 4)(), (ctypes.c_int * 4)(), term_mask)
+                    GKE_PREC_F64, GKE_DOMAIN_TRIANGLE, (ctypes.c_int * 4)(), (ctypes.c_int * 4)(), term_mask, None)
     st = lib().gke_compute_noalloc(ctypes.byref(desc), ptr(fields), nsnap, ptr(terms), ptr(profiles), stream)
     if st != GKE_OK:
         raise GkeError(st, "gke_compute_noalloc")

@@ -31,6 +31,9 @@ struct gke_plan_s {
     long long npair = 0, npair_tri = 0;
     bool wedge = false;
     unsigned tset = 0;                        // terms computed (term_set of the mask)
+    int comb_kc = 0;                          // wavenumbers per combine CTA (0 = default; tuner)
+    int w_mib = 0;                            // inverse-transform scratch per pair chunk, MiB (tuner)
+    int knob_source = 0;                      // 0 built-in, 1 tuning file, 2 measured
     void* fold = nullptr;                     // wedge: folded spectra (aliases raw when it fits)
     bool fold_owned = false;
     // kept separations (undersampling): host lists and the device map
@@ -257,6 +260,159 @@ template <typename T> static cudaError_t dalloc(T** p, size_t count)
 }
 
 // ------------------------------------------------------------------- plan
+// ------------------------------------------------------------- autotuner
+// Knobs of the schedule that do not change any result: the pair-chunk size
+// of the inverse transforms (scratch W per chunk) and the wavenumbers per
+// CTA of the combine kernel.  Tuned per device and problem shape, by timing
+// each candidate on the plan's own workspaces, and kept in a text file.
+static const int W_MIB_CAND[3] = {48, 96, 192};
+
+static long long pairs_for(const gke_plan_t p, int mib)
+{
+    const long long per = (long long)NTERM * p->sep.nrz * (p->nxt / 2 + 1) * (long long)p->csz;
+    return std::max<long long>(1, std::min<long long>(p->npair, ((long long)mib << 20) / per));
+}
+
+static std::string tune_key(const gke_plan_t p)
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceProp prop;
+    std::string name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown";
+    for (char& c : name)
+        if (c == ' ' || c == ':') c = '_';
+    const gke_desc& d = p->d;
+    char buf[512];
+    snprintf(buf, sizeof buf, "gke-tune-1 %s sm%d nx%d nz%d ny%d prec%d dom%d dec%d nzt%d nxt%d nrz%d nrx%d terms%u",
+             name.c_str(), nsm, d.nx, d.nz, d.ny, d.precision, d.pair_domain, p->dec ? 1 : 0, p->nzt, p->nxt,
+             p->sep.nrz, p->sep.nrx, p->tset);
+    return buf;
+}
+
+static bool tune_lookup(const char* path, const std::string& key, int& w_mib, int& kc)
+{
+    FILE* fp = fopen(path, "r");
+    if (!fp) return false;
+    char line[1024];
+    bool found = false;
+    while (fgets(line, sizeof line, fp)) {
+        const std::string l(line);
+        const size_t c = l.find(" : ");
+        if (c == std::string::npos || l.compare(0, c, key) != 0 || c != key.size()) continue;
+        int a = 0, b = 0;
+        if (sscanf(l.c_str() + c + 3, "w_mib=%d comb_kc=%d", &a, &b) == 2) { w_mib = a; kc = b; found = true; }
+    }
+    fclose(fp);
+    return found;
+}
+
+static void tune_store(const char* path, const std::string& key, int w_mib, int kc)
+{
+    FILE* fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s : w_mib=%d comb_kc=%d\n", key.c_str(), w_mib, kc);
+    fclose(fp);
+}
+
+// device time of f() on the plan's stream, the second of two runs
+template <typename F>
+static float time_twice(gke_plan_t p, F f)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    f();
+    cudaEventRecord(a, p->st);
+    f();
+    cudaEventRecord(b, p->st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms;
+}
+
+static void terms_stage(gke_plan_t p, void* terms_dev);
+
+// times the candidates on the plan's workspaces (their contents are not yet
+// data); each knob is set to its fastest candidate
+static gke_status tune_knobs(gke_plan_t p)
+{
+    const gke_desc& d = p->d;
+    const bool f32 = d.precision != GKE_PREC_F64;
+    const bool timing0 = p->timing;
+    p->timing = false;
+    const long long launches = p->launches;
+    // combine: one batch's spectra into the first-batch accumulator
+    {
+        const int cand[3] = {f32 ? 2 : 1, f32 ? 4 : 2, f32 ? 8 : 4};
+        float best = 0.f;
+        for (int kc : cand) {
+            const float ms = time_twice(p, [&] {
+                if (p->dec)
+                    combine_launch(f32, !f32, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, 0, p->Kc,
+                                   p->Kc, p->cchunk, p->tset, kc, p->st);
+                else
+                    combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, 0,
+                                   p->Nk, p->Nk, p->comb_is64 ? (void*)p->comb : (void*)p->comb32, p->tset, kc,
+                                   p->st);
+            });
+            if (p->comb_kc == 0 || ms < best) { best = ms; p->comb_kc = kc; }
+        }
+    }
+    // inverse transforms of the first pairs (two chunks of the largest
+    // candidate) into a scratch output
+    const long long P = std::min<long long>(p->npair, 2 * pairs_for(p, W_MIB_CAND[2]));
+    if (P > pairs_for(p, W_MIB_CAND[0])) {
+        const long long N = (long long)p->sep.nrz * p->sep.nrx;
+        void* out = nullptr;
+        float* spec = nullptr;
+        if (cudaMalloc(&out, (size_t)NTERM * P * N * p->tsz) != cudaSuccess ||
+            (f32 && cudaMalloc((void**)&spec, (size_t)3 * P * N * sizeof(float)) != cudaSuccess)) {
+            if (out) cudaFree(out);
+            cudaGetLastError();
+            p->timing = timing0;
+            return GKE_OK;                      // no room to tune: built-in choice
+        }
+        const long long npair = p->npair;
+        float* spec0 = p->spec;
+        const double cnt = p->snap_count;
+        p->npair = P;                            // terms_stage indexes outputs by npair
+        p->spec = spec;
+        p->snap_count = 1.0;
+        float best = 0.f;
+        for (int mib : W_MIB_CAND) {
+            p->pair_chunk = pairs_for(p, mib);
+            const float ms = time_twice(p, [&] { terms_stage(p, out); });
+            if (p->w_mib == 0 || ms < best) { best = ms; p->w_mib = mib; }
+        }
+        p->npair = npair;
+        p->spec = spec0;
+        p->snap_count = cnt;
+        cudaStreamSynchronize(p->st);
+        cudaFree(out);
+        if (spec) cudaFree(spec);
+    } else {
+        p->w_mib = W_MIB_CAND[2];
+    }
+    p->pair_chunk = pairs_for(p, p->w_mib);
+    p->launches = launches;
+    p->timing = timing0;
+    CUDA_TRY(p, cudaGetLastError());
+    return GKE_OK;
+}
+
+extern "C" gke_status gke_plan_knobs(gke_plan_t p, int* w_chunk_mib, int* comb_kc, int* source)
+{
+    if (!p) return GKE_ERR_ARG;
+    if (w_chunk_mib) *w_chunk_mib = p->w_mib ? p->w_mib : (int)(W_CHUNK_BYTES >> 20);
+    if (comb_kc) *comb_kc = p->comb_kc ? p->comb_kc : combine_kc(p->d.precision != GKE_PREC_F64);
+    if (source) *source = p->knob_source;
+    return GKE_OK;
+}
+
 extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* out)
 {
     if (!out) { g_plan_err = "out is NULL"; return GKE_ERR_ARG; }
@@ -513,6 +669,26 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     if (d.precision == GKE_PREC_BF16X3) {
         if ((e = split_setup(st)) != cudaSuccess) return bail(GKE_ERR_CUDA, std::string("split setup: ") + cudaGetErrorString(e));
     }
+    if (d.tune_cache) {
+        // the schedule: from the tuning file, else measured now and stored
+        const std::string key = tune_key(p);
+        int w = 0, kc = 0;
+        const bool hit = tune_lookup(d.tune_cache, key, w, kc) &&
+                         (w == W_MIB_CAND[0] || w == W_MIB_CAND[1] || w == W_MIB_CAND[2]) &&
+                         combine_kc_ok(d.precision != GKE_PREC_F64, kc);
+        if (hit) {
+            p->w_mib = w;
+            p->comb_kc = kc;
+            p->pair_chunk = pairs_for(p, w);
+            p->knob_source = 1;
+        } else {
+            gke_status ts = tune_knobs(p);
+            if (ts != GKE_OK) return bail(ts, p->err);
+            tune_store(d.tune_cache, key, p->w_mib, p->comb_kc);
+            p->knob_source = 2;
+        }
+    }
+    p->d.tune_cache = nullptr;                  // the caller's string is read during gke_plan only
     gke_status rs = gke_reset(p);
     if (rs != GKE_OK) return bail(rs, p->err);
     *out = p;
@@ -759,7 +935,7 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
             if (s != GKE_OK) return s;
             StageScope sc(p, GKE_STAGE_COMBINE);
             p->launches += combine_launch(f32, !f32, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, k0,
-                                          p->Kc, p->Kc, p->cchunk, p->tset, st);
+                                          p->Kc, p->Kc, p->cchunk, p->tset, p->comb_kc, st);
             p->launches += fold_dec_launch(!f32, p->cchunk, p->pair_i, p->npair, p->wedge ? 1 : 0, ny, d.nz, d.nx,
                                            p->nzt, p->nxt, kz0, p->R, p->comb, st);
         }
@@ -783,7 +959,7 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
         }
         void* dst = p->comb_is64 ? (void*)p->comb : (void*)p->comb32;
         p->launches += combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof,
-                                      p->have_acc ? 1 : 0, 0, Nk, Nk, dst, p->tset, st);
+                                      p->have_acc ? 1 : 0, 0, Nk, Nk, dst, p->tset, p->comb_kc, st);
     }
     CUDA_TRY(p, cudaGetLastError());
     p->snap_count += ns;

@@ -38,25 +38,26 @@ namespace gke {
 constexpr int PB = 8;     // pair block edge
 constexpr int CHUNKS = 1; // k chunks per CTA
 
+// KC = wavenumbers per CTA.  Default: ~30 KB of staging per CTA, so several
+// CTAs per SM hide the gather latency; the plan's tuner may pick another of
+// the instantiated widths (combine_kc_ok).
 template <typename TI> struct CombCfg;
-// ~30 KB of staging per CTA: several CTAs per SM hide the gather latency
 template <> struct CombCfg<float> { static constexpr int KC = 4; };
 template <> struct CombCfg<double> { static constexpr int KC = 2; };
 
-template <typename TI> constexpr size_t combine_smem_bytes()
+template <typename TI, int KC> constexpr size_t combine_smem_bytes()
 {
-    return (size_t)(2 * NJOB - 1) * CombCfg<TI>::KC * PB * (PB + 2) * sizeof(cplx<TI>);
+    return (size_t)(2 * NJOB - 1) * KC * PB * (PB + 2) * sizeof(cplx<TI>);
 }
-size_t combine_smem(bool fp32) { return fp32 ? combine_smem_bytes<float>() : combine_smem_bytes<double>(); }
 int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::KC; }
+bool combine_kc_ok(bool fp32, int kc) { return fp32 ? (kc == 2 || kc == 4 || kc == 8) : (kc == 1 || kc == 2 || kc == 4); }
 
-template <typename TI, typename TC, typename TO>
+template <typename TI, typename TC, typename TO, int KC>
 __global__ void __launch_bounds__(256)
 k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
           const double* __restrict__ prof, int beta, int kbase, int Kc, long long cstride, unsigned tmask,
           unsigned jmask, cplx<TO>* __restrict__ comb)
 {
-    constexpr int KC = CombCfg<TI>::KC;
     typedef cplx<TI> C;
     typedef cplx<TC> Z;
     extern __shared__ __align__(16) unsigned char sh_raw_cb[];
@@ -310,27 +311,55 @@ int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long n
     return 1;
 }
 
+template <typename TI, typename TO, int KC>
+static void combine_kc_launch(const void* raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
+                              const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
+                              unsigned terms, unsigned jobs, cudaStream_t st)
+{
+    const int kc = KC * CHUNKS;
+    const int nblk = (ny + PB - 1) / PB;
+    dim3 grid((Kc + kc - 1) / kc, nblk * (nblk + 1) / 2);
+    k_combine<TI, TI, TO, KC><<<grid, 256, combine_smem_bytes<TI, KC>(), st>>>(
+        (const cplx<TI>*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (cplx<TO>*)comb);
+}
+
+template <typename TI, typename TO>
+static void combine_t(int kc, const void* raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
+                      const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
+                      unsigned terms, unsigned jobs, cudaStream_t st)
+{
+#define GKE_COMB_ARGS raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, comb, terms, jobs, st
+    if constexpr (sizeof(TI) == 4) {
+        if (kc == 2) combine_kc_launch<TI, TO, 2>(GKE_COMB_ARGS);
+        else if (kc == 8) combine_kc_launch<TI, TO, 8>(GKE_COMB_ARGS);
+        else combine_kc_launch<TI, TO, 4>(GKE_COMB_ARGS);
+    } else {
+        if (kc == 1) combine_kc_launch<TI, TO, 1>(GKE_COMB_ARGS);
+        else if (kc == 4) combine_kc_launch<TI, TO, 4>(GKE_COMB_ARGS);
+        else combine_kc_launch<TI, TO, 2>(GKE_COMB_ARGS);
+    }
+#undef GKE_COMB_ARGS
+}
+
 // comb (+)= term spectra of one batch.  fp32_in: raw and arithmetic in FP32;
-// out64: comb is FP64 (else FP32)
+// out64: comb is FP64 (else FP32); kc: wavenumbers per CTA (0 = default)
 // wavenumbers [kbase, kbase + Kc) (raw holds that chunk); comb rows of
 // cstride values per (pair, term), chunk-local index kl at offset kl
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
                    double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
-                   unsigned terms, cudaStream_t st)
+                   unsigned terms, int kc, cudaStream_t st)
 {
     const unsigned jobs = job_set(terms);
-    const int kc = combine_kc(fp32_in) * CHUNKS;
-    const int nblk = (ny + PB - 1) / PB;
-    dim3 grid((Kc + kc - 1) / kc, nblk * (nblk + 1) / 2);
+    if (!combine_kc_ok(fp32_in, kc)) kc = combine_kc(fp32_in);
     if (!fp32_in)
-        k_combine<double, double, double><<<grid, 256, combine_smem(false), st>>>(
-            (const zd*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (zd*)comb);
+        combine_t<double, double>(kc, raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, comb, terms, jobs,
+                                  st);
     else if (out64)
-        k_combine<float, float, double><<<grid, 256, combine_smem(true), st>>>(
-            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (zd*)comb);
+        combine_t<float, double>(kc, raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, comb, terms, jobs,
+                                 st);
     else
-        k_combine<float, float, float><<<grid, 256, combine_smem(true), st>>>(
-            (const zf*)raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, terms, jobs, (zf*)comb);
+        combine_t<float, float>(kc, raw, ny, nz, nx, Lx, Lz, nu, prof, beta, kbase, Kc, cstride, comb, terms, jobs,
+                                st);
     return 1;
 }
 
@@ -342,13 +371,20 @@ int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t s
 
 cudaError_t combine_set_attrs()
 {
-    const void* ks[] = {(const void*)k_combine<float, float, float>, (const void*)k_combine<float, float, double>};
-    for (const void* k : ks) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(true));
-        if (e != cudaSuccess) return e;
-    }
-    cudaError_t e = cudaFuncSetAttribute((const void*)k_combine<double, double, double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)combine_smem(false));
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* k, size_t bytes) {
+        const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (r != cudaSuccess) e = r;
+    };
+    set((const void*)k_combine<double, double, double, 1>, combine_smem_bytes<double, 1>());
+    set((const void*)k_combine<double, double, double, 2>, combine_smem_bytes<double, 2>());
+    set((const void*)k_combine<double, double, double, 4>, combine_smem_bytes<double, 4>());
+    set((const void*)k_combine<float, float, float, 2>, combine_smem_bytes<float, 2>());
+    set((const void*)k_combine<float, float, float, 4>, combine_smem_bytes<float, 4>());
+    set((const void*)k_combine<float, float, float, 8>, combine_smem_bytes<float, 8>());
+    set((const void*)k_combine<float, float, double, 2>, combine_smem_bytes<float, 2>());
+    set((const void*)k_combine<float, float, double, 4>, combine_smem_bytes<float, 4>());
+    set((const void*)k_combine<float, float, double, 8>, combine_smem_bytes<float, 8>());
     if (e != cudaSuccess) return e;
     int dev = 0, lim = 0;
     cudaGetDevice(&dev);

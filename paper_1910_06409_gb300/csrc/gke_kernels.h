@@ -47,8 +47,8 @@ __host__ __device__ __forceinline__ int nth_bit(unsigned m, int n)
         if ((m >> i) & 1u) { if (n == 0) return i; --n; }
     return -1;
 }
-size_t combine_smem(bool fp32);
 int combine_kc(bool fp32);
+bool combine_kc_ok(bool fp32, int kc);
 
 __global__ void k_mean_accum(const zd* fields, int ns, int ny, long long plane, double* mean_sum);
 __global__ void k_reduce_partials(const double* part, int nvals, int nb, double* out);
@@ -74,7 +74,7 @@ cudaError_t products_set_attrs(int lim);
 // term spectra (gke_combine.cu)
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
                    double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
-                   unsigned terms, cudaStream_t st);
+                   unsigned terms, int kc, cudaStream_t st);
 int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
                     int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st);
 size_t fold_dec_smem(bool c64, int R, int nx, bool wedge);

@@ -192,7 +192,7 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = fdw; a.fdl0 = fdl0; a.st = st;
     products_launch<double>(a);
     correlate_launch(false, Xop, ns, ny, Nk, 0, Nk, raw, job_set(tset), st);
-    combine_launch(false, true, raw, ny, nz, nx, d.Lx, d.Lz, d.nu, prof, 0, 0, Nk, Nk, comb, tset, st);
+    combine_launch(false, true, raw, ny, nz, nx, d.Lx, d.Lz, d.nu, prof, 0, 0, Nk, Nk, comb, tset, 0, st);
     // Step 3: profiles, inverse transforms, stencils
     k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(mean_sum, (double)ns, stats, (double)ns, (long long)nx * nz, d.nu, 0, fdw,
                                                   fdl0, ny, prof);
