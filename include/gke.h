@@ -94,7 +94,7 @@ typedef enum {
     GKE_ERR_CUDA = -4,         /* a CUDA runtime call failed                         */
     GKE_ERR_NONFINITE = -5,    /* a NaN or Inf was found in the input               */
     GKE_ERR_IO = -6,           /* checkpoint file could not be read or written       */
-    GKE_ERR_UNSUPPORTED = -7   /* grid size or option not supported by this build    */
+    GKE_ERR_UNSUPPORTED = -7   /* grid size or option the library does not support   */
 } gke_status;
 
 enum { GKE_PREC_F64 = 0,       /* plain FP64 path (DFMA)                              */

@@ -425,7 +425,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     }
     if (!(d.Lx > 0) || !(d.Lz > 0) || !(d.nu > 0)) { g_plan_err = "Lx, Lz, nu must be > 0"; return GKE_ERR_ARG; }
     if (!fft_len_ok(d.nx) || !fft_len_ok(d.nz)) {
-        g_plan_err = "nx and nz must be 2^a or 3 * 2^a in this build";
+        g_plan_err = "nx and nz must be 2^a or 3 * 2^a (transform lengths of the library)";
         return GKE_ERR_UNSUPPORTED;
     }
     if (d.precision != GKE_PREC_F64 && d.precision != GKE_PREC_BF16X3 && d.precision != GKE_PREC_F32) {
