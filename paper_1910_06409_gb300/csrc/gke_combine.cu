@@ -45,9 +45,17 @@ template <typename TI> struct CombCfg;
 template <> struct CombCfg<float> { static constexpr int KC = 4; };
 template <> struct CombCfg<double> { static constexpr int KC = 2; };
 
+// Staging layout, in complex values: block (slot, q) every SQ, row rr every
+// SR, column cc contiguous.  With SR odd and SQ = 4 mod 16 the item reads of
+// a half-warp (4 wavenumbers q x 4 columns m of a row, or the transposed
+// partner: 4 q x 4 rows m) hit 16 distinct 8-byte bank pairs (FP32 values),
+// and the 8 reads of a quarter-warp distinct 16-byte ones (FP64, 2 q x 4 m).
+constexpr int SR = PB + 1, SQ = 84;
+static_assert(SQ >= PB * SR && SQ % 16 == 4 && SR % 2 == 1, "combine staging layout");
+
 template <typename TI, int KC> constexpr size_t combine_smem_bytes()
 {
-    return (size_t)(2 * NJOB - 1) * KC * PB * (PB + 2) * sizeof(cplx<TI>);
+    return (size_t)(2 * NJOB - 1) * KC * SQ * sizeof(cplx<TI>);
 }
 int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::KC; }
 bool combine_kc_ok(bool fp32, int kc) { return fp32 ? (kc == 2 || kc == 4 || kc == 8) : (kc == 1 || kc == 2 || kc == 4); }
@@ -72,9 +80,8 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
     while (bt >= nblk - a) { bt -= nblk - a; ++a; }
     const int b = a + bt;
     const int nslot = 2 * NJOB - 1;
-    // rows padded to PB + 2 values: 16-byte aligned rows, few bank conflicts
     auto at = [&](int slot, int q, int rr, int cc) -> C& {
-        return stage[((slot * KC + q) * PB + rr) * (PB + 2) + cc];
+        return stage[(slot * KC + q) * SQ + rr * SR + cc];
     };
     // per-wavenumber and per-pair coefficients, formed once per CTA (FP64
     // arithmetic costs as much as ~60 FP32 operations here, so none is done
