@@ -373,8 +373,11 @@ static gke_status tune_knobs(gke_plan_t p)
             (f32 && cudaMalloc((void**)&spec, (size_t)3 * P * N * sizeof(float)) != cudaSuccess)) {
             if (out) cudaFree(out);
             cudaGetLastError();
+            p->w_mib = W_MIB_CAND[2];           // no room to time it: the built-in chunk
+            p->pair_chunk = pairs_for(p, p->w_mib);
+            p->launches = launches;
             p->timing = timing0;
-            return GKE_OK;                      // no room to tune: built-in choice
+            return GKE_OK;
         }
         const long long npair = p->npair;
         float* spec0 = p->spec;
