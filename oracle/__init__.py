@@ -45,21 +45,46 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def load_library(path: str):
+    """Open a compiled copy of the oracle at `path` with its entry points typed.
+
+    The tests use it to load deliberately broken copies of gke_oracle.c (a
+    planted mistake must make a pin fail); everything else goes through the
+    default library built by build()."""
+    lib = ctypes.CDLL(path)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.oracle_full.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
+                                ctypes.c_int]
+    lib.oracle_points.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ip, dp, dp, ctypes.c_int]
+    lib.oracle_fd_weights.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
+    lib.oracle_fd_weights.restype = ctypes.c_int
+    return lib
+
+
+def compile_source(src_text: str, out_path: str) -> str:
+    """Compile C source text of the oracle (gcc, OpenMP) into `out_path`."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           "-D_DEFAULT_SOURCE", "-o", out_path, c_path, "-lm"])
+    return out_path
+
+
+def source_text() -> str:
+    """The oracle's C source."""
+    with open(_SRC) as f:
+        return f.read()
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
-        dp = ctypes.POINTER(ctypes.c_double)
-        ip = ctypes.POINTER(ctypes.c_int)
-        lib.oracle_full.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
-                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp, dp,
-                                    ctypes.c_int]
-        lib.oracle_points.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
-                                      ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
-                                      ip, dp, dp, ctypes.c_int]
-        lib.oracle_fd_weights.argtypes = [dp, ctypes.c_int, ctypes.c_int, dp]
-        lib.oracle_fd_weights.restype = ctypes.c_int
-        _lib = lib
+        _lib = load_library(build())
     return _lib
 
 
@@ -98,7 +123,7 @@ def wedge_pairs(ny: int):
 
 
 def full(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, nthreads: int = 0,
-         mirror: bool = False):
+         mirror: bool = False, lib=None):
     """All components and terms on the full square of ordered pairs.
 
     phys: float64 [ns][4][ny][nz][nx] (u, v, w, p including the mean).
@@ -106,6 +131,7 @@ def full(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, nthre
     (mirror_augment; y must be symmetric about its centre).
     Returns dict(comp=[12][ny][ny][nz][nx], terms=[7][ny][ny][nz][nx],
     prof=[6][ny]) with names COMPONENTS, TERMS, PROFILES.
+    lib: a library from load_library() instead of the default build.
     """
     if mirror:
         phys = mirror_augment(phys)
@@ -116,8 +142,8 @@ def full(phys: np.ndarray, y: np.ndarray, Lx: float, Lz: float, nu: float, nthre
     comp = np.zeros((len(COMPONENTS), ny, ny, nz, nx))
     terms = np.zeros((len(TERMS), ny, ny, nz, nx))
     prof = np.zeros((len(PROFILES), ny))
-    rc = _load().oracle_full(_dp(phys), ns, nx, nz, ny, _dp(y), Lx, Lz, nu, _dp(comp), _dp(terms),
-                             _dp(prof), nthreads)
+    rc = (lib or _load()).oracle_full(_dp(phys), ns, nx, nz, ny, _dp(y), Lx, Lz, nu, _dp(comp), _dp(terms),
+                                      _dp(prof), nthreads)
     if rc != 0:
         raise ValueError(f"oracle_full failed ({rc})")
     return {"comp": comp, "terms": terms, "prof": prof}
