@@ -208,16 +208,25 @@ gke_status gke_plan_knobs(gke_plan_t plan, int* w_chunk_mib, int* comb_kc, int* 
 /* Forget all accumulated statistics and the mean.                            */
 gke_status gke_reset(gke_plan_t plan);
 
-/* Save / restore the accumulated state (mean sums, one-point sums, per-pair
- * term spectra, counts) to / from a file; linear, so restored partial sums combine
- * exactly with further calls (the paper's merge of independent jobs,
- * Sec. 3.4).  gke_merge adds a checkpoint's sums to the plan's.             */
+/* Save / restore the accumulated state (mean sums, one-point sums, the
+ * spectra summed over snapshots, counts) to / from a file; linear, so
+ * restored partial sums combine exactly with further calls (the paper's
+ * merge of independent jobs, Sec. 3.4).  gke_merge adds a checkpoint's sums
+ * to the plan's.  The spectra of a job are taken about the Step-1 mean it
+ * froze, so jobs combine exactly only when they share that mean (set it with
+ * gke_set_mean, or run gke_accumulate_mean over the same snapshots in every
+ * job); gke_merge refuses (GKE_ERR_ARG) a file whose frozen mean differs
+ * from the plan's by more than rounding (1e-12 of the largest value).      */
 /* File layout (little endian): a header struct { char magic[8] "GKECKPT";
- * int32 version = 4, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt,
- * term_set (gke_term_set of the plan's mask); float64 mean_count, snap_count,
- * Lx, Lz, nu } (88 bytes), then float64 mean_sum[4][ny], float64 stats[7][ny]
- * and, if have_acc, the complex128 per-pair sums.  Restore and merge need
- * the same grid, domain and term set (else GKE_ERR_ARG).  Files of
+ * int32 version = 5, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt,
+ * term_set (gke_term_set of the plan's mask), acc_kind, reserved; float64
+ * mean_count, snap_count, Lx, Lz, nu } (96 bytes), then float64
+ * mean_sum[4][ny], float64 stats[7][ny] and, if have_acc, float64 mean[4][ny]
+ * (the frozen mean) and the complex128 spectra: acc_kind 0 = per-pair term
+ * spectra [npair][GKE_NTERM][...], acc_kind 1 = the six plane spectra that
+ * split-BF16 plans on the full triangle with ny <= 128 or ny = 129 sum
+ * [6][(npair + 3) / 4][nz (nx/2 + 1)][4].  Restore and merge need the same
+ * grid, domain, term set and acc_kind (else GKE_ERR_ARG).  Files of
  * independent jobs can also be added on the host
  * (paper_1910_06409_gb300/merge.py).                                        */
 gke_status gke_checkpoint(gke_plan_t plan, const char* path);

@@ -61,6 +61,15 @@ struct gke_plan_s {
     zd* comb = nullptr;
     zf* comb32 = nullptr;
     bool comb_is64 = false;
+    // split plane mode (BF16 x3, triangle, one 128-row tile): the correlator
+    // writes the plane spectra of each batch (pl32, FP32), summed in FP64
+    // (pl64) from the second batch on; no raw contractions, no combine
+    bool planes = false;
+    unsigned pset = 0;                        // planes the term set needs (plane_set)
+    long long npp = 0;                        // pairs per plane row: npair rounded up to a multiple of 4
+    zf* pl32 = nullptr;
+    zd* pl64 = nullptr;
+    bool pl_is64 = false;
     float* spec = nullptr;                    // split path: spectral parts of A, Phi_y, phi
     size_t tsz = 8;                           // bytes of one output term value
     zd *tw_xd = nullptr, *tw_zd = nullptr, *stage_in = nullptr;
@@ -270,7 +279,8 @@ static const int W_MIB_CAND[3] = {48, 96, 192};
 static long long pairs_for(const gke_plan_t p, int mib)
 {
     const long long per = (long long)NTERM * p->sep.nrz * (p->nxt / 2 + 1) * (long long)p->csz;
-    return std::max<long long>(1, std::min<long long>(p->npair, ((long long)mib << 20) / per));
+    const long long n = std::max<long long>(1, std::min<long long>(p->npair, ((long long)mib << 20) / per));
+    return p->planes ? std::max<long long>(4, n & ~3LL) : n;       // plane mode: whole pair groups
 }
 
 static std::string tune_key(const gke_plan_t p)
@@ -345,8 +355,10 @@ static gke_status tune_knobs(gke_plan_t p)
     const bool timing0 = p->timing;
     p->timing = false;
     const long long launches = p->launches;
-    // combine: one batch's spectra into the first-batch accumulator
-    {
+    // combine: one batch's spectra into the first-batch accumulator (plans
+    // that combine raw contractions; plane mode keeps the default)
+    if (p->planes) p->comb_kc = combine_kc(true);
+    else {
         const int cand[3] = {f32 ? 2 : 1, f32 ? 4 : 2, f32 ? 8 : 4};
         float best = 0.f;
         for (int kc : cand) {
@@ -498,6 +510,11 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         }
     }
 
+    // the split correlator writes the term planes directly when the wall-normal
+    // rows fit one 128-row tile (the full triangle; the wedge and the chunked
+    // mode combine raw contractions)
+    p->planes = d.precision == GKE_PREC_BF16X3 && !p->dec && !p->wedge && split_planes_ok(ny);
+    p->pset = plane_set(p->tset);
     auto bail = [&](gke_status s, const std::string& m) { g_plan_err = m; gke_destroy(p); return s; };
     cudaError_t e;
 #define ALLOC(ptr, n)                                                                          \
@@ -535,6 +552,14 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         ALLOC(p->comb, p->n_acc);
         p->tsz = f32 ? sizeof(float) : sizeof(double);
         if (f32) ALLOC(p->spec, (size_t)3 * p->npair * p->nxt * p->nzt + 13 * (size_t)p->npair);
+    } else if (p->planes) {
+        // the six plane spectra of one batch, [NPLANE][Nk][npp]
+        p->Kc = Nk;
+        p->npp = 4 * ((p->npair_tri + 3) / 4);
+        p->n_acc = (size_t)NPLANE * Nk * p->npp;
+        ALLOC(p->pl32, p->n_acc);
+        ALLOC(p->spec, (size_t)3 * p->npair * nrx * nrz + 13 * (size_t)p->npair);
+        p->tsz = sizeof(float);
     } else {
     p->Kc = Nk;
     p->n_acc = (size_t)p->npair_tri * NTERM * Nk;
@@ -562,8 +587,8 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     // buffers): the column pass of one chunk overlaps the row pass of the
     // previous one on the auxiliary stream
     const int nxth = p->nxt / 2 + 1, nrzt = p->sep.nrz;
-    p->pair_chunk = std::max<long long>(
-        1, std::min<long long>(p->npair, W_CHUNK_BYTES / ((long long)NTERM * nrzt * nxth * p->csz)));
+    p->pair_chunk = pairs_for(p, (int)(W_CHUNK_BYTES >> 20));
+    (void)nxth; (void)nrzt;
     ALLOCB(p->W, (size_t)p->pair_chunk * NTERM * nrzt * nxth * p->csz);
     ALLOCB(p->W2, (size_t)p->pair_chunk * NTERM * nrzt * nxth * p->csz);
     if ((e = cudaStreamCreateWithFlags(&p->aux_st, cudaStreamNonBlocking)) != cudaSuccess)
@@ -710,6 +735,7 @@ extern "C" gke_status gke_reset(gke_plan_t p)
     p->snap_count = 0.0;
     p->mean_frozen = p->have_acc = p->finalized = false;
     p->comb_is64 = (p->d.precision == GKE_PREC_F64) || p->dec;
+    p->pl_is64 = false;
     if (p->dec) CUDA_TRY(p, cudaMemsetAsync(p->comb, 0, p->n_acc * sizeof(zd), p->st));
     return GKE_OK;
 }
@@ -731,7 +757,7 @@ extern "C" void gke_destroy(gke_plan_t p)
         void* extra[] = {p->cchunk, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
     }
-    void* ptrs[] = {p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
+    void* ptrs[] = {p->pl32, p->pl64, p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
                     p->fdl0, p->pair_i, p->nonfinite, p->part, p->sep_tab};
     for (void* q : ptrs) if (q) cudaFree(q);
@@ -947,6 +973,32 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
         p->have_acc = true;
         return GKE_OK;
     }
+    if (p->planes) {
+        const long long per_plane = (long long)Nk * p->npp;
+        if (p->have_acc && !p->pl_is64) {
+            // second batch: the first batch's planes to the FP64 sums first
+            StageScope sc(p, GKE_STAGE_COMBINE);
+            if (!p->pl64) CUDA_TRY(p, dalloc(&p->pl64, p->n_acc));
+            p->launches += planes_accum_launch(p->pl32, per_plane, p->pset, 0, p->pl64, st);
+            p->pl_is64 = true;
+        }
+        {
+            StageScope sc(p, GKE_STAGE_CORRELATE);
+            int nl = 0;
+            gke_status s = split_correlate_planes(p->split, (const zf*)p->Xop, ns, ny, Nk, 0, Nk, p->pset, p->npp,
+                                                  p->prof, p->pl32, st, p->err, &nl);
+            p->launches += nl;
+            if (s != GKE_OK) return s;
+        }
+        if (p->pl_is64) {
+            StageScope sc(p, GKE_STAGE_COMBINE);
+            p->launches += planes_accum_launch(p->pl32, per_plane, p->pset, 1, p->pl64, st);
+        }
+        CUDA_TRY(p, cudaGetLastError());
+        p->snap_count += ns;
+        p->have_acc = true;
+        return GKE_OK;
+    }
     {
         gke_status s = correlate(0, Nk);
         if (s != GKE_OK) return s;
@@ -1025,6 +1077,13 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     a.terms = terms_dev; a.sep = p->sep; a.st = p->st;
     a.after_chunk = copy_chunk;
     a.ctx = p;
+    if (p->planes) {
+        a.planes = p->pl_is64 ? (const void*)p->pl64 : (const void*)p->pl32;
+        a.planes64 = p->pl_is64;
+        a.npp = p->npp;
+        a.Kc = p->Nk;
+        a.Lx = d.Lx; a.Lz = d.Lz; a.nu = d.nu;
+    }
     a.st2 = p->aux_st;
     a.W2 = p->W2;
     a.ev = p->aux_ev + 6;
@@ -1175,6 +1234,7 @@ extern "C" gke_status gke_compute_graph(gke_plan_t p, const void* fields, int ns
         p->snap_count = 0.0;
         p->mean_frozen = p->have_acc = p->finalized = false;
         p->comb_is64 = (p->d.precision == GKE_PREC_F64) || p->dec;
+        p->pl_is64 = false;
     };
     if (!same) {
         if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
@@ -1220,16 +1280,30 @@ extern "C" gke_status gke_compute_graph(gke_plan_t p, const void* fields, int ns
 }
 
 // ------------------------------------------------------- checkpoint files
-static const int CKPT_VERSION = 4;
+static const int CKPT_VERSION = 5;
 static_assert(sizeof(int) == 4 && sizeof(double) == 8, "checkpoint layout");
 
+// acc_kind: 0 = per-pair term spectra comb[npair][NTERM][...], 1 = the plane
+// spectra of the split plane mode [NPLANE][npair / 4][Nk][4]
 struct CkptHeader {
     char magic[8];
-    int version, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt, term_set;
+    int version, nx, nz, ny, precision, have_acc, pair_domain, nzt, nxt, term_set, acc_kind, reserved;
     double mean_count, snap_count, Lx, Lz, nu;
 };
 
-static_assert(sizeof(CkptHeader) == 88, "checkpoint header layout");
+static_assert(sizeof(CkptHeader) == 96, "checkpoint header layout");
+
+// largest difference between two mean profiles that still counts as the same
+// mean (rounding of sums taken in another order)
+static bool same_mean(const std::vector<double>& a, const std::vector<double>& b)
+{
+    double scale = 0.0, diff = 0.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        scale = std::max(scale, std::max(std::fabs(a[i]), std::fabs(b[i])));
+        diff = std::max(diff, std::fabs(a[i] - b[i]));
+    }
+    return diff <= 1e-12 * std::max(scale, 1e-300);
+}
 
 static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save, 1 restore, 2 merge
 {
@@ -1237,15 +1311,28 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     const int ny = p->d.ny;
     const size_t n_mean = 4 * ny, n_stat = (size_t)NSTAT * ny;
     const size_t n_comb = p->n_acc;
-    // the stored per-pair sums are FP64; a split plan holding one batch in FP32 promotes first
-    if (p->have_acc && !p->comb_is64) {
-        if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
-        promote_launch(p->comb32, (long long)n_comb, p->comb, p->st);
-        p->comb_is64 = true;
+    const int acc_kind = p->planes ? 1 : 0;
+    // the stored sums are FP64; a split plan holding one batch in FP32 promotes first
+    if (p->planes) {
+        if (p->have_acc && !p->pl_is64) {
+            if (!p->pl64) CUDA_TRY(p, dalloc(&p->pl64, n_comb));
+            planes_accum_launch(p->pl32, (long long)p->Nk * p->npp, (1u << NPLANE) - 1u, 0, p->pl64, p->st);
+            p->pl_is64 = true;
+        }
+        if (mode != 0 && !p->pl64) CUDA_TRY(p, dalloc(&p->pl64, n_comb));
+    } else {
+        if (p->have_acc && !p->comb_is64) {
+            if (!p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
+            promote_launch(p->comb32, (long long)n_comb, p->comb, p->st);
+            p->comb_is64 = true;
+        }
+        if (mode != 0 && !p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
     }
-    if (mode != 0 && !p->comb) CUDA_TRY(p, dalloc(&p->comb, n_comb));
+    zd* accp = p->planes ? p->pl64 : p->comb;
     CUDA_TRY(p, cudaStreamSynchronize(p->st));
-    CUDA_TRY(p, cudaStreamSynchronize(p->st));
+    // the mean the accumulated spectra were taken about (frozen by the first batch)
+    std::vector<double> frozen(n_mean, 0.0);
+    if (p->have_acc) CUDA_TRY(p, cudaMemcpy(frozen.data(), p->mean, n_mean * 8, cudaMemcpyDeviceToHost));
     if (mode == 0) {
         FILE* fp = fopen(path, "wb");
         if (!fp) return fail(p, GKE_ERR_IO, std::string("cannot open for writing: ") + path);
@@ -1258,6 +1345,7 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         h.nzt = p->dec ? p->nzt : 0;
         h.nxt = p->dec ? p->nxt : 0;
         h.term_set = (int)p->tset;
+        h.acc_kind = acc_kind;
         bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
         std::vector<char> buf;
         auto put = [&](const void* dptr, size_t bytes) {
@@ -1266,7 +1354,10 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
             return fwrite(buf.data(), 1, bytes, fp) == bytes;
         };
         ok = ok && put(p->mean_sum, n_mean * 8) && put(p->stats, n_stat * 8);
-        if (p->have_acc) ok = ok && put(p->comb, n_comb * 16);
+        if (p->have_acc) {
+            ok = ok && fwrite(frozen.data(), 8, n_mean, fp) == n_mean;
+            ok = ok && put(accp, n_comb * 16);
+        }
         ok = (fclose(fp) == 0) && ok;
         return ok ? GKE_OK : fail(p, GKE_ERR_IO, std::string("write failed: ") + path);
     }
@@ -1275,13 +1366,18 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     CkptHeader h{};
     if (fread(&h, sizeof(h), 1, fp) != 1 || memcmp(h.magic, "GKECKPT", 8) != 0 || h.version != CKPT_VERSION) {
         fclose(fp);
-        return fail(p, GKE_ERR_IO, "not a GKE checkpoint");
+        return fail(p, GKE_ERR_IO, "not a GKE checkpoint of this version");
     }
     if (h.nx != p->d.nx || h.nz != p->d.nz || h.ny != ny || h.Lx != p->d.Lx || h.Lz != p->d.Lz || h.nu != p->d.nu ||
         h.pair_domain != p->d.pair_domain || h.nzt != (p->dec ? p->nzt : 0) || h.nxt != (p->dec ? p->nxt : 0) ||
         h.term_set != (int)p->tset) {
         fclose(fp);
         return fail(p, GKE_ERR_ARG, "checkpoint grid, domain or term set does not match the plan");
+    }
+    if (h.have_acc && h.acc_kind != acc_kind) {
+        fclose(fp);
+        return fail(p, GKE_ERR_ARG, "checkpoint accumulator layout does not match the plan (plane spectra of the "
+                                    "split path on one 128-row tile vs per-pair term spectra)");
     }
     if (mode == 2 && p->mean_frozen && h.mean_count > 0 && !p->have_acc) {
         fclose(fp);
@@ -1304,16 +1400,41 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
         for (size_t i = 0; i < bytes / 8; ++i) a[i] += b[i];
         ok = cudaMemcpy(dptr, cur.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess;
     };
+    // the file's frozen mean follows its one-point sums; read the sums into
+    // host memory first so a refused merge leaves the plan unchanged
+    std::vector<double> f_mean_sum(n_mean), f_stats(n_stat), f_frozen(n_mean);
+    ok = fread(f_mean_sum.data(), 8, n_mean, fp) == n_mean && fread(f_stats.data(), 8, n_stat, fp) == n_stat;
+    if (ok && h.have_acc) ok = fread(f_frozen.data(), 8, n_mean, fp) == n_mean;
+    if (!ok) { fclose(fp); return fail(p, GKE_ERR_IO, std::string("read failed or truncated: ") + path); }
     const bool add = (mode == 2);
-    get(p->mean_sum, n_mean * 8, add, false);
-    get(p->stats, n_stat * 8, add, false);
+    if (add && p->have_acc && h.have_acc && !same_mean(frozen, f_frozen)) {
+        fclose(fp);
+        return fail(p, GKE_ERR_ARG, "checkpoint spectra were taken about another Step-1 mean: jobs to be merged "
+                                    "must share the mean (gke_set_mean, or gke_accumulate_mean over the same "
+                                    "snapshots)");
+    }
+    {
+        std::vector<double> cur(n_mean), curs(n_stat);
+        if (add) {
+            CUDA_TRY(p, cudaMemcpy(cur.data(), p->mean_sum, n_mean * 8, cudaMemcpyDeviceToHost));
+            CUDA_TRY(p, cudaMemcpy(curs.data(), p->stats, n_stat * 8, cudaMemcpyDeviceToHost));
+        }
+        for (size_t i = 0; i < n_mean; ++i) cur[i] = (add ? cur[i] : 0.0) + f_mean_sum[i];
+        for (size_t i = 0; i < n_stat; ++i) curs[i] = (add ? curs[i] : 0.0) + f_stats[i];
+        CUDA_TRY(p, cudaMemcpy(p->mean_sum, cur.data(), n_mean * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY(p, cudaMemcpy(p->stats, curs.data(), n_stat * 8, cudaMemcpyHostToDevice));
+    }
     if (h.have_acc) {
         const bool add_acc = add && p->have_acc;
-        get(p->comb, n_comb * 16, false, add_acc);
+        get(accp, n_comb * 16, false, add_acc);
     }
     fclose(fp);
     if (!ok) return fail(p, GKE_ERR_IO, std::string("read failed or truncated: ") + path);
-    if (h.have_acc) p->comb_is64 = true;
+    if (h.have_acc) {
+        if (p->planes) p->pl_is64 = true;
+        else p->comb_is64 = true;
+    }
+    const bool had_acc = p->have_acc;
     if (add) {
         p->mean_count += h.mean_count;
         p->snap_count += h.snap_count;
@@ -1325,10 +1446,9 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     }
     p->mean_frozen = false;
     if (p->have_acc) {
-        // the mean used by accumulated snapshots is the stored one: refreeze it
-        std::vector<double> m(4 * ny);
-        CUDA_TRY(p, cudaMemcpy(m.data(), p->mean_sum, m.size() * 8, cudaMemcpyDeviceToHost));
-        for (double& v : m) v /= p->mean_count;
+        // the mean the accumulated spectra were taken about: the plan's own, or
+        // the file's when the plan had no samples yet
+        const std::vector<double>& m = (add && had_acc) ? frozen : f_frozen;
         CUDA_TRY(p, cudaMemcpy(p->mean, m.data(), m.size() * 8, cudaMemcpyHostToDevice));
         k_profiles<<<(ny + 127) / 128, 128, 0, p->st>>>(p->mean_sum, p->mean_count, p->stats, 1.0,
                                                          (long long)p->d.nx * p->d.nz, p->d.nu, p->wedge ? 1 : 0,

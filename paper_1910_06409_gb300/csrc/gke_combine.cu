@@ -370,6 +370,32 @@ int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, in
     return 1;
 }
 
+// Plane mode (split correlator on one 128-row tile): the batches' FP32 plane
+// spectra summed in FP64, dst[j] = (beta ? dst[j] : 0) + src[j] for the
+// selected planes j (per_plane complex values each); beta = 0 promotes the
+// first batch before the second one is written over it
+__global__ void k_planes_accum(const zf* __restrict__ src, long long per_plane, unsigned planes, int beta,
+                               zd* __restrict__ dst)
+{
+    const int j = blockIdx.y;
+    if (!((planes >> j) & 1u)) return;
+    const zf* s = src + (long long)j * per_plane;
+    zd* d = dst + (long long)j * per_plane;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < per_plane;
+         i += (long long)gridDim.x * blockDim.x) {
+        const zf v = ld_stream(s + i);
+        zd o = mk((double)v.x, (double)v.y);
+        if (beta) o = o + d[i];
+        st_stream(d + i, o);
+    }
+}
+
+int planes_accum_launch(const void* src, long long per_plane, unsigned planes, int beta, void* dst, cudaStream_t st)
+{
+    k_planes_accum<<<dim3(152 * 4, NPLANE), 256, 0, st>>>((const zf*)src, per_plane, planes, beta, (zd*)dst);
+    return 1;
+}
+
 int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st)
 {
     k_promote<<<152 * 8, 256, 0, st>>>((const zf*)comb32, n, (zd*)comb64);

@@ -29,6 +29,13 @@ constexpr int J_D = NJSQ;          // Hermitian contraction D, stored after the 
 constexpr int NJOB = NJSQ + 1;
 // output terms
 enum Term { T_A = 0, T_PHIX, T_PHIY, T_PHIZ, T_PHI, T_XI, T_RES, NTERM };
+// Spectra written per (plane, wavenumber, pair) by the split correlator's
+// plane mode, from which the inverse transforms form the seven terms:
+// A; S4 = Gx - Gx^H and S6 = Gz - Gz^H (Phi_x, Phi_z without their D parts);
+// Phi_y; phi; xi.  Layout planes[NPLANE][Kc][npp], npp = npair rounded up
+// to a multiple of 4 (one wavenumber's values of consecutive pairs are
+// contiguous; four pairs fill a 32-byte sector).
+enum Plane { PL_A = 0, PL_S4, PL_PHIY, PL_S6, PL_PHI, PL_XI, NPLANE };
 // one-point statistics per y (FP64 sums over snapshots and the plane)
 enum Stat { S_Q = 0, S_UV, S_PV, S_QU, S_QV, S_QW, S_EPS, NSTAT };
 

@@ -40,6 +40,22 @@ inline unsigned job_set(unsigned t)
     return j;
 }
 
+// Planes (bit j = Plane j) the spectra of a term set are formed from:
+// A = A; Phi_x = S4 + (dU - 2 i nu kx) A; Phi_y; Phi_z = S6 - 2 i nu kz A;
+// phi; xi; residual = i kx Phi_x + i kz Phi_z - xi
+inline unsigned plane_set(unsigned t)
+{
+    auto b = [](int j) { return 1u << j; };
+    unsigned p = 0;
+    if (t & ((1u << T_A) | (1u << T_PHIX) | (1u << T_PHIZ) | (1u << T_RES))) p |= b(PL_A);
+    if (t & ((1u << T_PHIX) | (1u << T_RES))) p |= b(PL_S4);
+    if (t & (1u << T_PHIY)) p |= b(PL_PHIY);
+    if (t & ((1u << T_PHIZ) | (1u << T_RES))) p |= b(PL_S6);
+    if (t & (1u << T_PHI)) p |= b(PL_PHI);
+    if (t & ((1u << T_XI) | (1u << T_RES))) p |= b(PL_XI);
+    return p;
+}
+
 // the n-th set bit of m (n < popcount(m))
 __host__ __device__ __forceinline__ int nth_bit(unsigned m, int n)
 {
@@ -79,6 +95,7 @@ int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long n
                     int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st);
 size_t fold_dec_smem(bool c64, int R, int nx, bool wedge);
 int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st);
+int planes_accum_launch(const void* src, long long per_plane, unsigned planes, int beta, void* dst, cudaStream_t st);
 int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long nout, int ny, int Nk, void* out,
                        cudaStream_t st);
 cudaError_t combine_set_attrs();
@@ -123,6 +140,14 @@ struct TermArgs {
     const cudaEvent_t* ev = nullptr;      // 4 caller-owned events for st2 (else created per call)
     void (*after_chunk)(void* ctx, long long p0, long long np, cudaStream_t st) = nullptr;
     void* ctx = nullptr;
+    // split plane mode: the column pass forms the terms from the plane spectra
+    // planes[NPLANE][Kc][npp] (complex128 if planes64, else complex64)
+    // instead of reading comb; pair chunks are multiples of 4
+    const void* planes = nullptr;
+    bool planes64 = false;
+    long long npp = 0;
+    int Kc = 0;
+    double Lx = 0, Lz = 0, nu = 0;
 };
 int terms_launch(const TermArgs& a);
 cudaError_t terms_set_attrs(int lim);

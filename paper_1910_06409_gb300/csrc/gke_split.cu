@@ -18,11 +18,13 @@
 // Tensor-core mapping (one work item = one wavenumber k, one contraction,
 // one 128 x 128 tile of (y, y')): D[128 x 256] in TMEM, columns 0..127 = Re,
 // 128..255 = Im.  Per term, snapshot group of 16 and slice pair (i, j):
-//   mma(A = ar_i, B = [br_j | bi_j])      -> Re += ar br, Im += ar bi
-//   mma(A = ai_i, B = [bi_j | -br_j])     -> Re += ai bi, Im -= ai br
-// (M = 128, N = 256, K = 16, BF16 in, FP32 accumulate).  The B block holds
-// the rows br, bi, -br back to back, so both B views are 256-row windows of
-// it.  Operands are written by k_split_prep_* in the canonical K-major
+//   mma(A = ar_i, B = [br_j | bi_j], N = 256)       -> Re += ar br, Im += ar bi
+//   mma(A = ai_i, B = bi_j, N = 128) into Re         -> Re += ai bi
+//   mma(A = -ai_i, B = br_j, N = 128) into Im        -> Im -= ai br
+// (M = 128, K = 16, BF16 in, FP32 accumulate; the sign by the negate-A bit
+// of the instruction descriptor).  The B block holds the rows br, bi back to
+// back, so every B view is a window of it.  Operands are written by
+// k_split_prep_* in the canonical K-major
 // no-swizzle layout (8 x 16-byte core matrices; K-adjacent core matrices LBO
 // bytes apart, M/N-adjacent ones SBO = 128 bytes apart) and copied to shared
 // memory by the bulk-copy engine (cp.async.bulk, mbarrier transaction count).
@@ -43,22 +45,28 @@ typedef __nv_bfloat16 bf16;
 constexpr int TM = 128;                 // tile rows (y) = tile cols (y')
 constexpr int KS = 16;                  // snapshots per group = one MMA K step
 constexpr int A_BLK = TM * KS;          // bf16 per A block (128 rows x 16)
-constexpr int B_BLK = 3 * TM * KS;      // bf16 per B block (br | bi | -br rows x 16)
+constexpr int B_BLK = 2 * TM * KS;      // bf16 per B block (br | bi rows x 16)
 constexpr int A_STAGE = 6 * A_BLK;      // slices x parts (re, im), slice-major
 constexpr int B_STAGE = 3 * B_BLK;      // slices
 constexpr int SM_A = A_STAGE * 2;       // 24576 bytes
-constexpr int SM_B = B_STAGE * 2;       // 36864 bytes
+constexpr int SM_B = B_STAGE * 2;       // 24576 bytes
 constexpr int A_LBO = (TM / 8) * 128;       // 2048: K-adjacent core matrices in an A block
-constexpr int B_LBO = (3 * TM / 8) * 128;   // 6144: K-adjacent core matrices in a B block
+constexpr int B_LBO = (2 * TM / 8) * 128;   // 4096: K-adjacent core matrices in a B block
 constexpr int CM_SBO = 128;                 // M/N-adjacent core matrices
 
 // instruction descriptor, kind::f16: D = F32 (bits 4-5), A = B = BF16 (7-9, 10-12),
 // K-major A and B (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(256 >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t IDESC_N128 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(128 >> 3) << 17) |
+                                ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t NEG_A = 1u << 13;       // negate-A bit of the instruction descriptor
 
-struct TcJob { int nterm; int fa[4]; int fb[4]; };
+// one contraction: sum over its terms t of sign_t conj(A_fa[t]) B_fb[t]; bit t
+// of neg marks a term with sign -1 (the MMA's negate-A bit)
+struct TcJob { int nterm; int fa[5]; int fb[5]; unsigned neg; };
 __constant__ TcJob c_tcjobs[NJSQ + 1];
+__constant__ TcJob c_tcplanes[NPLANE];
 
 // cross-slice pairs (i, j), 0 < i + j <= 2; the pair (0, 0) goes last
 __constant__ int c_pi[5] = {1, 0, 2, 1, 0};
@@ -161,7 +169,7 @@ __device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
 struct alignas(16) bf16x8 { bf16 v[8]; };
 
 __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
-                               bf16* __restrict__ Aop)
+                               float pscale, bf16* __restrict__ Aop)
 {
     long long b = blockIdx.x;
     const int mt = (int)(b % MT); b /= MT;
@@ -177,6 +185,7 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
         const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
         if (y < cov && s < ns) v = Xop[(((long long)f * Nk + k0 + k) * ns + s) * ny + y];
+        if (f == F_P) v = pscale * v;                      // a power of two: exact
         split3(v.x, o[0].v[e], o[2].v[e], o[4].v[e]);      // slices of the real part
         split3(v.y, o[1].v[e], o[3].v[e], o[5].v[e]);      // slices of the imaginary part
     }
@@ -185,7 +194,7 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
     for (int q = 0; q < 6; ++q) *(bf16x8*)(dst + q * A_BLK + idx) = o[q];
 }
 
-// Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi | -br
+// Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi
 __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
                                bf16* __restrict__ Bop)
 {
@@ -197,7 +206,7 @@ __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int N
     bf16* dst = Bop + ((((long long)k * 3 + fb) * G + g) * MT + nt) * (long long)B_STAGE;
     const int r = threadIdx.x % TM, kc = threadIdx.x / TM;          // blockDim = 2 TM
     const int y = nt * TM + r;
-    bf16x8 br[3], bi[3], bn[3];
+    bf16x8 br[3], bi[3];
     #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int s = g * KS + kc * 8 + e;
@@ -205,15 +214,12 @@ __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int N
         if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k0 + k) * ns + s) * ny + y];
         split3(v.x, br[0].v[e], br[1].v[e], br[2].v[e]);
         split3(v.y, bi[0].v[e], bi[1].v[e], bi[2].v[e]);
-        #pragma unroll
-        for (int sl = 0; sl < 3; ++sl) bn[sl].v[e] = __hneg(br[sl].v[e]);
     }
     #pragma unroll
     for (int sl = 0; sl < 3; ++sl) {
         bf16* d = dst + sl * B_BLK;
-        *(bf16x8*)(d + cm_index(r, kc * 8, 3 * TM)) = br[sl];
-        *(bf16x8*)(d + cm_index(TM + r, kc * 8, 3 * TM)) = bi[sl];
-        *(bf16x8*)(d + cm_index(2 * TM + r, kc * 8, 3 * TM)) = bn[sl];
+        *(bf16x8*)(d + cm_index(r, kc * 8, 2 * TM)) = br[sl];
+        *(bf16x8*)(d + cm_index(TM + r, kc * 8, 2 * TM)) = bi[sl];
     }
 }
 
@@ -245,44 +251,116 @@ __device__ __forceinline__ void decode_tile(int jt, int MT, const TcSel& sel, in
     }
 }
 
+// What one launch of the tensor-core kernel runs and where it writes.
+//   raw mode (planes == 0): items (wavenumber, contraction, 128 x 128 tile),
+//     the tile written as FP32 contractions raw[job][yb][yb'][k][8][8];
+//   plane mode (planes != 0, one 128-row tile, cov <= 128): items
+//     (wavenumber, plane), the plane's term spectrum of every pair
+//     y <= y' < cov written to out[plane][k][pair] (FP32, npp >= npair pairs
+//     per row).
+struct TcArgs {
+    const bf16* Aop; const bf16* Bop;
+    int Kc, G, MT, ny, cov;
+    long long nitems;
+    TcSel sel; zf* raw;                       // raw mode
+    unsigned planes; int npl; long long npp;  // plane mode: selected planes, their count, padded pair count
+    zf* out; const double* prof;
+    int* err;
+};
+
 // ------------------------------------------------ tensor-core kernel
-// One CTA per SM walks the (wavenumber, contraction, tile) items
-// blockIdx.x, blockIdx.x + gridDim.x, ...  Roles:
+// One CTA per SM walks the work items blockIdx.x, blockIdx.x + gridDim.x, ...
+// Roles:
 //   warp 0 (one lane): bulk copies of the operand blocks into a ring of NST
 //     shared-memory stages (full[s] completes when a stage's bytes land);
 //   warp 1 (one lane): the MMAs of an item into one of two 256-column TMEM
 //     accumulators, each stage released by a commit to empty[s], the
 //     finished accumulator announced by a commit to acc_full[b];
 //   warps 2-5: the epilogue of an item (TMEM -> registers -> shared memory ->
-//     8 x 8 pair blocks of raw), then acc_empty[b] for the MMA warp.
-// So the copies, the tensor cores and the raw writes of successive items
+//     global memory), then acc_empty[b] for the MMA warp.
+// So the copies, the tensor cores and the output writes of successive items
 // overlap.  Every wait is bounded; a timed-out wait raises the CTA's abort
 // flag (all roles leave their loops) and the device error flag, and the copies
 // and MMAs in flight are drained before the shared memory and TMEM go away.
+//
+// Plane-mode epilogue.  With X the accumulator (X(y, y') in TMEM lane y) and
+// X^H(y, y') = conj X(y', y), the planes of one wavenumber are (Sec. 3.1,
+// Eq. 7 grouped by term; the factor 2 of the expansion rides on the product
+// operands):
+//   A     = -2 D                          D  = sum_i conj(u_i) u_i
+//   S4    = Gx - Gx^H                     Gx = conj(q) u + 2 sum_i conj(u u_i) u_i
+//   Phi_y = Gy - Gy^H                     Gy = conj(q) v + 2 sum_i conj(v u_i) u_i
+//   S6    = Gz - Gz^H                     Gz = conj(q) w + 2 sum_i conj(w u_i) u_i
+//   phi   = (H + H^H) / 2                 H  = conj(q) v - 2 sum_i conj(v u_i) u_i - 4 conj(p) v
+//   xi    = 2 U'(y') E + 2 U'(y) E^H      E  = conj(u) v
+// The partner values X(y', y) come through shared memory in 32 x 32 blocks.
+// Warp q holds the rows [32 q, 32 q + 32) and lays out its blocks (q, c),
+// c <= q (the lower triangle of the tile, in order c = 0, 1, ..); it then
+// forms its output blocks (q, b), b >= q, each from its own TMEM block and
+// the block (b, q) that warp b laid out, announced by a named barrier of the
+// two warps.  With these orders every warp does five block steps per item.
+// A consumed block holds the warp's outputs next, so each row of 32 pairs
+// leaves as one contiguous 256-byte store.  Blocks are swizzled (element
+// (r, c) of a block at r * 32 + ((c + r) mod 32)), so row and column
+// accesses of a half-warp hit 16 distinct bank pairs.
 constexpr int NST = 3;                                  // operand stages
 constexpr int EPI_WARPS = 4;
 constexpr int TCP_THREADS = 64 + 32 * EPI_WARPS;
-constexpr int SMP_STAGE = SM_A + SM_B;                  // 61440 bytes
+constexpr int SMP_STAGE = SM_A + SM_B;                  // 49152 bytes
 constexpr int SMP_EPI = NST * SMP_STAGE;
-constexpr int SMP_BAR = SMP_EPI + EPI_WARPS * 32 * 33 * 8;
+constexpr int EPI_BLOCKS = 10;                          // lower-triangle 32 x 32 blocks of a tile
+constexpr int EPI_BYTES = EPI_BLOCKS * 32 * 32 * 8;     // plane mode; raw mode uses 4 x 32 x 33 x 8
+constexpr int SMP_DUP = SMP_EPI + EPI_BYTES;            // 2 U'(y) for the xi plane
+constexpr int SMP_BAR = SMP_DUP + TM * 4;
 constexpr int SMP_TOTAL = SMP_BAR + 256;
 constexpr uint32_t TMEM_COLS_P = 512;
+static_assert(EPI_BYTES >= EPI_WARPS * 32 * 33 * 8, "raw-mode staging fits");
+static_assert(SMP_TOTAL <= 232448, "shared memory of one CTA");
 
 struct TcPipeBars {
     uint64_t full[NST], empty[NST], acc_full[2], acc_empty[2], drain;
     uint32_t tmem;
     int abort;
+    int eok;                                            // epilogue: the accumulator is ready
 };
 
+// named barrier of the four epilogue warps
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// named barriers 2..7 of the epilogue warp pairs (b, c), b > c: warp b
+// arrives once block (b, c) is laid out, warp c waits before reading it
+__device__ __forceinline__ int pair_bar(int b, int c) { return 2 + b * (b - 1) / 2 + c; }
+__device__ __forceinline__ void bar_arrive64(int id) { asm volatile("bar.arrive %0, 64;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ void bar_sync64(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+// slot of the lower-triangle block (b, c), c <= b; swizzled element offset
+__device__ __forceinline__ int tri_slot(int b, int c) { return b * (b + 1) / 2 + c; }
+__device__ __forceinline__ int swz(int r, int c) { return r * 32 + ((c + r) & 31); }
+
+template <bool PLANES>
+__device__ __forceinline__ void item_of(const TcArgs& a, int njt, long long it, int& k, int& job, int& mt, int& nt)
+{
+    if (PLANES) {
+        k = (int)(it / a.npl);
+        job = nth_bit(a.planes, (int)(it % a.npl));
+        mt = nt = 0;
+    } else {
+        k = (int)(it / njt);
+        decode_tile((int)(it % njt), a.MT, a.sel, job, mt, nt);
+    }
+}
+
+template <bool PLANES>
+__device__ __forceinline__ const TcJob& job_desc(int job) { return PLANES ? c_tcplanes[job] : c_tcjobs[job]; }
+
+template <bool PLANES>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
-k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int Nk, int G, int MT, int ny, int cov,
-               long long nitems, TcSel sel, zf* __restrict__ raw, int* __restrict__ err)
+k_corr_tc_pipe(const TcArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     TcPipeBars* bars = (TcPipeBars*)(smem + SMP_BAR);
     volatile int* abort = &bars->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int njt = sel_tiles(sel, MT);
+    const int njt = PLANES ? a.npl : sel_tiles(a.sel, a.MT);
+    const int G = a.G, MT = a.MT;
     if (threadIdx.x == 0) {
         for (int st = 0; st < NST; ++st) {
             mbar_init(&bars->full[st], 1);
@@ -293,8 +371,13 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
             mbar_init(&bars->acc_empty[b], EPI_WARPS);
         }
         mbar_init(&bars->drain, 1);
-        bars->abort = (*(volatile int*)err != 0) ? 1 : 0;
+        bars->abort = (*(volatile int*)a.err != 0) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (PLANES) {
+        float* s_dup = (float*)(smem + SMP_DUP);
+        for (int i = threadIdx.x; i < TM; i += blockDim.x)
+            s_dup[i] = i < a.ny ? 2.f * (float)a.prof[PR_DU * a.ny + i] : 0.f;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&bars->tmem)),
@@ -305,18 +388,17 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = bars->tmem;
-    auto fail = [&]() { *abort = 1; atomicExch(err, 1); };
+    auto fail = [&]() { *abort = 1; atomicExch(a.err, 1); };
 
     if (warp == 0) {
         if (lane == 0) {
             int st = 0;
             uint32_t ph = 0;
             int issued = 0;
-            for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
-                const int k = (int)(it / njt);
-                int job, mt, nt;
-                decode_tile((int)(it % njt), MT, sel, job, mt, nt);
-                const TcJob& jd = c_tcjobs[job];
+            for (long long it = blockIdx.x; it < a.nitems && !*abort; it += gridDim.x) {
+                int k, job, mt, nt;
+                item_of<PLANES>(a, njt, it, k, job, mt, nt);
+                const TcJob& jd = job_desc<PLANES>(job);
                 for (int pass = 0; pass < 2; ++pass)
                     for (int t = 0; t < jd.nterm; ++t)
                         for (int g = 0; g < G; ++g) {
@@ -324,10 +406,10 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
                             const uint32_t ba = pass ? 2 * A_BLK * 2 : SM_A, bb = pass ? B_BLK * 2 : SM_B;
                             uint8_t* sa = smem + st * SMP_STAGE;
                             mbar_expect_tx(&bars->full[st], ba + bb);
-                            bulk_g2s(sa, Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + mt) *
-                                                   (long long)A_STAGE, ba, &bars->full[st]);
-                            bulk_g2s(sa + SM_A, Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + nt) *
-                                                          (long long)B_STAGE, bb, &bars->full[st]);
+                            bulk_g2s(sa, a.Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + mt) *
+                                                     (long long)A_STAGE, ba, &bars->full[st]);
+                            bulk_g2s(sa + SM_A, a.Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + nt) *
+                                                            (long long)B_STAGE, bb, &bars->full[st]);
                             ++issued;
                             if (++st == NST) { st = 0; ph ^= 1; }
                         }
@@ -345,16 +427,20 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
         if (lane == 0) {
             int st = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
-            for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
-                const int job = [&] { int j, m, n; decode_tile((int)(it % njt), MT, sel, j, m, n); return j; }();
-                const TcJob& jd = c_tcjobs[job];
+            for (long long it = blockIdx.x; it < a.nitems && !*abort; it += gridDim.x) {
+                int k, job, mt, nt;
+                item_of<PLANES>(a, njt, it, k, job, mt, nt);
+                const TcJob& jd = job_desc<PLANES>(job);
                 if (!mbar_wait_ab(&bars->acc_empty[acc], aph ^ 1, abort)) { fail(); break; }
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(acc * 256);
                 uint32_t accum = 0;
                 bool ok = true;
                 for (int pass = 0; pass < 2 && ok; ++pass)
-                    for (int t = 0; t < jd.nterm && ok; ++t)
+                    for (int t = 0; t < jd.nterm && ok; ++t) {
+                        // a term of sign -1: the negate-A bit (13) of the instruction descriptor
+                        const uint32_t neg = ((jd.neg >> t) & 1u) ? NEG_A : 0u;
+                        const uint32_t id = IDESC | neg, id128 = IDESC_N128 | neg;
                         for (int g = 0; g < G; ++g) {
                             if (!mbar_wait_ab(&bars->full[st], ph, abort)) { fail(); ok = false; break; }
                             tc_fence_after();
@@ -365,15 +451,17 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
                                 const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
                                 const uint64_t a_re = sdesc(sa + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
                                 const uint64_t a_im = sdesc(sa + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
-                                const uint64_t b_1 = sdesc(sb + j * B_BLK * 2, B_LBO, CM_SBO);
-                                const uint64_t b_2 = sdesc(sb + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
-                                mma_bf16(d, a_re, b_1, IDESC, accum);
+                                const uint64_t b_ri = sdesc(sb + j * B_BLK * 2, B_LBO, CM_SBO);
+                                const uint64_t b_i = sdesc(sb + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
+                                mma_bf16(d, a_re, b_ri, id, accum);              // Re += ar br, Im += ar bi
                                 accum = 1;
-                                mma_bf16(d, a_im, b_2, IDESC, 1);
+                                mma_bf16(d, a_im, b_i, id128, 1);                // Re += ai bi
+                                mma_bf16(d + TM, a_im, b_ri, id128 ^ NEG_A, 1);  // Im -= ai br
                             }
                             mma_commit(&bars->empty[st]);
                             if (++st == NST) { st = 0; ph ^= 1; }
                         }
+                    }
                 if (!ok) break;
                 mma_commit(&bars->acc_full[acc]);
                 if (++acc == 2) { acc = 0; aph ^= 1; }
@@ -382,16 +470,15 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
             mma_commit(&bars->drain);
             mbar_wait(&bars->drain, 0);
         }
-    } else {
+    } else if (!PLANES) {
         const int q = warp & 3;                       // TMEM lane quarter of this warp
         zf* xp = (zf*)(smem + SMP_EPI) + (warp - 2) * 32 * 33;
-        const int YB = (ny + 7) / 8;
+        const int YB = (a.ny + 7) / 8;
         int acc = 0;
         uint32_t aph = 0;
-        for (long long it = blockIdx.x; it < nitems && !*abort; it += gridDim.x) {
-            const int k = (int)(it / njt);
-            int job, mt, nt;
-            decode_tile((int)(it % njt), MT, sel, job, mt, nt);
+        for (long long it = blockIdx.x; it < a.nitems && !*abort; it += gridDim.x) {
+            int k, job, mt, nt;
+            item_of<PLANES>(a, njt, it, k, job, mt, nt);
             if (!mbar_wait_ab(&bars->acc_full[acc], aph, abort)) { fail(); break; }
             tc_fence_after();
             const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
@@ -413,12 +500,109 @@ k_corr_tc_pipe(const bf16* __restrict__ Aop, const bf16* __restrict__ Bop, int N
                         if (yb < YB && ypb < YB) {
                             const zf a0 = xp[(8 * rg + r8) * 33 + 8 * cg + c8];
                             const zf a1 = xp[(8 * rg + r8) * 33 + 8 * cg + c8 + 1];
-                            float4* dst = (float4*)(raw + ((((long long)job * YB + yb) * YB + ypb) * Nk + k) * 64 + e);
+                            float4* dst = (float4*)(a.raw + ((((long long)job * YB + yb) * YB + ypb) * a.Kc + k) * 64 + e);
                             __stcs(dst, make_float4(a0.x, a0.y, a1.x, a1.y));
                         }
                     }
                 }
                 __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bars->acc_empty[acc]);
+            if (++acc == 2) { acc = 0; aph ^= 1; }
+        }
+    } else {
+        const int q = warp & 3;                       // TMEM lane quarter of this warp
+        const int et = threadIdx.x - 64;              // 0..127 over the epilogue warps
+        float2* blk = (float2*)(smem + SMP_EPI);      // EPI_BLOCKS swizzled 32 x 32 blocks
+        const float* s_dup = (const float*)(smem + SMP_DUP);
+        volatile int* eok = &bars->eok;
+        const int cov = a.cov, ny = a.ny;
+        const int y = 32 * q + lane;                  // this thread's row of the tile
+        const float dy = s_dup[y];
+        // pair_index(y, y') = rb + y' for this thread's row (32-bit: pairs < 2^31)
+        const int rb = (int)(pair_index(y, y, ny) - y);
+        int acc = 0;
+        uint32_t aph = 0;
+        for (long long it = blockIdx.x; it < a.nitems; it += gridDim.x) {
+            int k, job, mt, nt;
+            item_of<PLANES>(a, njt, it, k, job, mt, nt);
+            // one thread waits, so the four warps take the same decision; the
+            // barrier also orders this item's block writes after every warp's
+            // reads of the previous item
+            if (et == 0) *eok = mbar_wait_ab(&bars->acc_full[acc], aph, abort) ? 1 : 0;
+            epi_sync();
+            const bool ok = *eok != 0;
+            epi_sync();
+            if (!ok) { if (et == 0) fail(); break; }
+            tc_fence_after();
+            const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
+            zf* outp = a.out + ((long long)job * a.Kc + k) * a.npp;
+            // lay out the blocks (q, c), c <= q
+            for (int c = 0; c <= q; ++c) {
+                uint32_t re[32], im[32];
+                tmem_ld32(tbase + c * 32, re);
+                tmem_ld32(tbase + TM + c * 32, im);
+                tmem_ld_wait();
+                float2* bb = blk + tri_slot(q, c) * 1024;
+                #pragma unroll
+                for (int j = 0; j < 32; ++j) bb[swz(lane, j)] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+                if (c < q) bar_arrive64(pair_bar(q, c));
+                else __syncwarp();
+            }
+            // output blocks (q, b), b >= q
+            for (int b = q; b < 4; ++b) {
+                if (b > q) bar_sync64(pair_bar(b, q));
+                float2* bb = blk + tri_slot(b, q) * 1024;     // X(y', y): row y' - 32 b, column y - 32 q
+                uint32_t re[32], im[32];
+                tmem_ld32(tbase + b * 32, re);
+                tmem_ld32(tbase + TM + b * 32, im);
+                tmem_ld_wait();
+                // out = al X + be conj(X(y', y)): A (-2, 0), S4 / Phi_y / S6 (1, -1),
+                // phi (1/2, 1/2), xi (2 U'(y'), 2 U'(y))
+                float2 o[32];
+                if (job == PL_XI) {
+                    #pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float2 pv = bb[swz(j, lane)];
+                        const float al = s_dup[32 * b + j];
+                        o[j] = make_float2(al * __uint_as_float(re[j]) + dy * pv.x,
+                                           al * __uint_as_float(im[j]) - dy * pv.y);
+                    }
+                } else {
+                    const float al = job == PL_A ? -2.f : job == PL_PHI ? 0.5f : 1.f;
+                    const float be = job == PL_A ? 0.f : job == PL_PHI ? 0.5f : -1.f;
+                    #pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float2 pv = bb[swz(j, lane)];
+                        o[j] = make_float2(al * __uint_as_float(re[j]) + be * pv.x,
+                                           al * __uint_as_float(im[j]) - be * pv.y);
+                    }
+                }
+                __syncwarp();                                  // the block is consumed: it stages the outputs
+                #pragma unroll
+                for (int j = 0; j < 32; ++j) bb[swz(lane, j)] = o[j];
+                __syncwarp();
+                // row r of the block: pairs (32 q + r, 32 b + lane), consecutive
+                // pair indices rb(32 q + r) + 32 b + lane
+                const int yp = 32 * b + lane;
+                #pragma unroll
+                for (int r = 0; r < 32; ++r) o[r] = bb[swz(r, lane)];
+                if (b > q && 32 * b + 32 <= cov) {            // whole block above the diagonal
+                    #pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        const int base = __shfl_sync(0xffffffffu, rb, r);
+                        __stcs((float2*)(outp + base + yp), o[r]);
+                    }
+                } else {
+                    #pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        const int base = __shfl_sync(0xffffffffu, rb, r);
+                        const int yr = 32 * q + r;
+                        if (yr < cov && yp >= yr && yp < cov) __stcs((float2*)(outp + base + yp), o[r]);
+                    }
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -482,6 +666,89 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
     }
 }
 
+// Plane mode: the pairs (y, y') with y' >= cov (the wall row of a 128 m + 1
+// grid), in FP32 on the CUDA cores, with the plane definitions of the
+// tensor-core epilogue.  X = X(y, y') has the factor B[s][y'] on the edge row,
+// X^H needs X(y', y) with the factor conj(A[s][y']) there; terms whose edge
+// factor is zero for every snapshot are skipped (exact).  With no-slip walls
+// only the pressure term of the phi plane survives.
+__global__ void k_corr_edge_planes(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, int cov,
+                                   unsigned planes, long long npp, const double* __restrict__ prof,
+                                   zf* __restrict__ out)
+{
+    __shared__ int nz_edge[NFIELD][4];       // field f has a nonzero value on edge row cov + i (i < 4)
+    const int kl = blockIdx.x, k = k0 + kl;
+    const int ne = ny - cov;
+    for (int i = threadIdx.x; i < NFIELD * 4; i += blockDim.x) nz_edge[i / 4][i % 4] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < NFIELD * ns * ne; i += blockDim.x) {
+        const int f = i / (ns * ne), r = i - f * ns * ne, s = r / ne, d = r - s * ne;
+        const zf v = Xop[(((long long)f * Nk + k) * ns + s) * ny + cov + d];
+        if ((v.x != 0.f || v.y != 0.f) && d < 4) atomicOr(&nz_edge[f][d], 1);
+    }
+    __syncthreads();
+    // edge pairs (y, y'), y <= y', y' in [cov, ny): ne * cov + ne (ne + 1) / 2 of them
+    const int n_edge = ne * cov + ne * (ne + 1) / 2;
+    for (int e2 = threadIdx.x; e2 < NPLANE * n_edge; e2 += blockDim.x) {
+        const int pl = e2 / n_edge;
+        int e = e2 - pl * n_edge;
+        if (!((planes >> pl) & 1u)) continue;
+        int y, yp;
+        if (e < ne * cov) { y = e / ne; yp = cov + e % ne; }
+        else {
+            e -= ne * cov;
+            y = cov;
+            while (e >= ny - y) { e -= ny - y; ++y; }
+            yp = y + e;
+        }
+        const TcJob jd = c_tcplanes[pl];
+        // s1 = X(y, y'), s2 = X(y', y)
+        float s1r = 0.f, s1i = 0.f, s2r = 0.f, s2i = 0.f;
+        for (int t = 0; t < jd.nterm; ++t) {
+            const float c = (((jd.neg >> t) & 1u) ? -1.f : 1.f) * (jd.fa[t] == F_P ? 4.f : 1.f);
+            const zf* A = Xop + ((long long)jd.fa[t] * Nk + k) * ns * ny;
+            const zf* B = Xop + ((long long)jd.fb[t] * Nk + k) * ns * ny;
+            // a factor on an edge row that is zero for every snapshot zeroes the term
+            const int d = yp - cov, dy = y - cov;
+            const bool ye = dy >= 0 && dy < 4;
+            const bool z1 = (d < 4 && !nz_edge[jd.fb[t]][d]) || (ye && !nz_edge[jd.fa[t]][dy]);
+            const bool z2 = (d < 4 && !nz_edge[jd.fa[t]][d]) || (ye && !nz_edge[jd.fb[t]][dy]);
+            float ar, ai, br, bi;
+            if (!z1) {
+                float tr = 0.f, ti = 0.f;
+                for (int s = 0; s < ns; ++s) {
+                    const zf av = A[(long long)s * ny + y], bv = B[(long long)s * ny + yp];
+                    ar = av.x; ai = av.y; br = bv.x; bi = bv.y;
+                    tr = fmaf(ar, br, fmaf(ai, bi, tr));
+                    ti = fmaf(ar, bi, fmaf(-ai, br, ti));
+                }
+                s1r = fmaf(c, tr, s1r);
+                s1i = fmaf(c, ti, s1i);
+            }
+            if (!z2) {
+                float tr = 0.f, ti = 0.f;
+                for (int s = 0; s < ns; ++s) {
+                    const zf av = A[(long long)s * ny + yp], bv = B[(long long)s * ny + y];
+                    ar = av.x; ai = av.y; br = bv.x; bi = bv.y;
+                    tr = fmaf(ar, br, fmaf(ai, bi, tr));
+                    ti = fmaf(ar, bi, fmaf(-ai, br, ti));
+                }
+                s2r = fmaf(c, tr, s2r);
+                s2i = fmaf(c, ti, s2i);
+            }
+        }
+        zf v;
+        if (pl == PL_A) v = mk(-2.f * s1r, -2.f * s1i);
+        else if (pl == PL_PHI) v = mk(0.5f * (s1r + s2r), 0.5f * (s1i - s2i));
+        else if (pl == PL_XI) {
+            const float dy = 2.f * (float)prof[PR_DU * ny + y], dyp = 2.f * (float)prof[PR_DU * ny + yp];
+            v = mk(dyp * s1r + dy * s2r, dyp * s1i - dy * s2i);
+        } else v = mk(s1r - s2r, s1i + s2i);
+        const long long p = pair_index(y, yp, ny);
+        out[((long long)pl * Kc + kl) * npp + p] = v;
+    }
+}
+
 // ------------------------------------------------------------------- host
 static void tile_geometry(int ny, int& MT, int& cov)
 {
@@ -509,17 +776,63 @@ gke_status split_alloc(SplitWork& w, int ny, int ns, int Kc)
 cudaError_t split_setup(cudaStream_t st)
 {
     TcJob h[NJSQ + 1] = {
-        /* E  */ {1, {F_U, 0, 0, 0}, {1, 0, 0, 0}},
-        /* F  */ {1, {F_P, 0, 0, 0}, {1, 0, 0, 0}},
-        /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {0, 0, 1, 2}},
-        /* QV */ {1, {F_Q, 0, 0, 0}, {1, 0, 0, 0}},
-        /* X2 */ {3, {F_UV, F_VV, F_VW, 0}, {0, 1, 2, 0}},
-        /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {2, 0, 1, 2}},
-        /* D  */ {3, {F_U, F_V, F_W, 0}, {0, 1, 2, 0}},
+        /* E  */ {1, {F_U}, {F_V}, 0u},
+        /* F  */ {1, {F_P}, {F_V}, 0u},
+        /* GX */ {4, {F_Q, F_UU, F_UV, F_UW}, {F_U, F_U, F_V, F_W}, 0u},
+        /* QV */ {1, {F_Q}, {F_V}, 0u},
+        /* X2 */ {3, {F_UV, F_VV, F_VW}, {F_U, F_V, F_W}, 0u},
+        /* GZ */ {4, {F_Q, F_UW, F_VW, F_WW}, {F_W, F_U, F_V, F_W}, 0u},
+        /* D  */ {3, {F_U, F_V, F_W}, {F_U, F_V, F_W}, 0u},
     };
+    // planes (see the epilogue of k_corr_tc_pipe); B fields are u, v, w
+    // (indices 0, 1, 2 of the B operands); the pressure operand of the phi
+    // plane is split from 4 p (k_split_prep_A with pscale = 4)
+    TcJob hp[NPLANE] = {
+        /* A   : D  */ {3, {F_U, F_V, F_W}, {F_U, F_V, F_W}, 0u},
+        /* S4  : Gx */ {4, {F_Q, F_UU, F_UV, F_UW}, {F_U, F_U, F_V, F_W}, 0u},
+        /* PHIY: Gy */ {4, {F_Q, F_UV, F_VV, F_VW}, {F_V, F_U, F_V, F_W}, 0u},
+        /* S6  : Gz */ {4, {F_Q, F_UW, F_VW, F_WW}, {F_W, F_U, F_V, F_W}, 0u},
+        /* PHI : H  */ {5, {F_Q, F_UV, F_VV, F_VW, F_P}, {F_V, F_U, F_V, F_W, F_V}, 0x1Eu},
+        /* XI  : E  */ {1, {F_U}, {F_V}, 0u},
+    };
+    static_assert(F_U == 0 && F_V == 1 && F_W == 2, "B operands are u, v, w in field order");
     cudaError_t e = cudaMemcpyToSymbolAsync(c_tcjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void*)k_corr_tc_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, SMP_TOTAL);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tcplanes, hp, sizeof(hp), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)k_corr_tc_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMP_TOTAL);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)k_corr_tc_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMP_TOTAL);
+    return e;
+}
+
+bool split_planes_ok(int ny)
+{
+    int MT, cov;
+    tile_geometry(ny, MT, cov);
+    return MT == 1;
+}
+
+static int sm_count()
+{
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(nsm, 1);
+}
+
+// BF16 slices of the operands of wavenumbers [k0, k0 + Kc)
+static void split_prep(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, float pscale,
+                       cudaStream_t st, bf16*& Aop, bf16*& Bop, int& G, int& MT, int& cov)
+{
+    tile_geometry(ny, MT, cov);
+    G = (ns + KS - 1) / KS;
+    Aop = (bf16*)w.ops;
+    Bop = (bf16*)((char*)w.ops + (size_t)Kc * NFIELD * G * MT * A_STAGE * sizeof(bf16));
+    k_split_prep_A<<<(unsigned)((long long)Kc * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov,
+                                                                                    pscale, Aop);
+    k_split_prep_B<<<(unsigned)((long long)Kc * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, Bop);
 }
 
 // wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
@@ -532,27 +845,46 @@ gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, 
         if ((jobs >> j) & 1u) sel.sq |= (unsigned)j << (3 * sel.nsq++);
     sel.d = (jobs >> J_D) & 1u;
     if (sel.nsq == 0 && !sel.d) return GKE_OK;
-    int MT, cov;
-    tile_geometry(ny, MT, cov);
-    const int G = (ns + KS - 1) / KS;
-    bf16* Aop = (bf16*)w.ops;
-    bf16* Bop = (bf16*)((char*)w.ops + (size_t)Kc * NFIELD * G * MT * A_STAGE * sizeof(bf16));
-    k_split_prep_A<<<(unsigned)((long long)Kc * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov,
-                                                                                    Aop);
-    k_split_prep_B<<<(unsigned)((long long)Kc * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, Bop);
-    const long long njt = sel_tiles(sel, MT);
-    {
-        int dev = 0, nsm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const long long nitems = (long long)Kc * njt;
-        const unsigned grid = (unsigned)std::min<long long>(nitems, std::max(nsm, 1));
-        k_corr_tc_pipe<<<grid, TCP_THREADS, SMP_TOTAL, st>>>(Aop, Bop, Kc, G, MT, ny, cov, nitems, sel, raw,
-                                                              w.err);
-    }
+    TcArgs a{};
+    bf16 *Aop, *Bop;
+    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 1.f, st, Aop, Bop, a.G, a.MT, a.cov);
+    a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
+    a.sel = sel; a.raw = raw; a.err = w.err;
+    a.nitems = (long long)Kc * sel_tiles(sel, a.MT);
+    const unsigned grid = (unsigned)std::min<long long>(a.nitems, sm_count());
+    k_corr_tc_pipe<false><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
     *launches = 3;
-    if (cov < ny) {
-        k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, cov, jobs, raw);
+    if (a.cov < ny) {
+        k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, a.cov, jobs, raw);
+        *launches += 1;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) { err = std::string("split correlator launch: ") + cudaGetErrorString(e); return GKE_ERR_CUDA; }
+    return GKE_OK;
+}
+
+// plane mode (split_planes_ok(ny)): the term spectra of the selected planes
+// for wavenumbers [k0, k0 + Kc) into out[plane][Kc][npp]
+gke_status split_correlate_planes(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc,
+                                  unsigned planes, long long npp, const double* prof, zf* out, cudaStream_t st,
+                                  std::string& err, int* launches)
+{
+    *launches = 0;
+    planes &= (1u << NPLANE) - 1u;
+    if (!planes) return GKE_OK;
+    if (!split_planes_ok(ny)) { err = "split correlator: plane mode needs one 128-row tile"; return GKE_ERR_UNSUPPORTED; }
+    TcArgs a{};
+    bf16 *Aop, *Bop;
+    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 4.f, st, Aop, Bop, a.G, a.MT, a.cov);
+    a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
+    a.planes = planes; a.npl = __builtin_popcount(planes); a.npp = npp; a.out = out; a.prof = prof;
+    a.err = w.err;
+    a.nitems = (long long)Kc * a.npl;
+    const unsigned grid = (unsigned)std::min<long long>(a.nitems, sm_count());
+    k_corr_tc_pipe<true><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
+    *launches = 3;
+    if (a.cov < ny) {
+        k_corr_edge_planes<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, a.cov, planes, npp, prof, out);
         *launches += 1;
     }
     cudaError_t e = cudaGetLastError();

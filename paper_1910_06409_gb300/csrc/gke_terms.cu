@@ -256,6 +256,247 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
     }
 }
 
+// ------------------- column pass from the plane spectra (split plane mode)
+// The seven term spectra of a pair at wavenumber (kz, kx) from its planes
+// (Sec. 3.1, Eq. 7 grouped by term; the D parts of Phi_x, Phi_z and the
+// residual, whose coefficients depend on the pair and the wavenumber only,
+// are added here):
+//   A, Phi_x = S4 + (dU - 2 i nu kx) A, Phi_y, Phi_z = S6 - 2 i nu kz A, phi,
+//   xi, res = i kx Phi_x + i kz Phi_z - xi         (dU = U(Y2) - U(Y1)),
+// then the inverse transform along z into W, as k_terms_colpass.
+// Column (pair, kx): a CTA takes 4 kx of one group of 4 pairs, so the loads
+// of one kz row are four whole 32-byte sectors of the planes.
+// a cached load the compiler keeps in program order (not hoisted out of
+// the term loop, where it would hold a whole column in registers)
+__device__ __forceinline__ cplx<float> ld_ordered(const cplx<float>* p)
+{
+    cplx<float> r;
+    asm volatile("ld.global.v2.f32 {%0, %1}, [%2];" : "=f"(r.x), "=f"(r.y) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ cplx<double> ld_ordered(const cplx<double>* p)
+{
+    cplx<double> r;
+    asm volatile("ld.global.v2.f64 {%0, %1}, [%2];" : "=d"(r.x), "=d"(r.y) : "l"(p));
+    return r;
+}
+
+struct PlaneCols {
+    const void* planes; long long npp; int Kc;
+    const int* pair_i; const double* prof; int ny; double Lx, Lz, nu;
+};
+
+// register variant, nz = N1 N2: CTA = 16 columns x N2 lanes; all terms of
+// tmask (and those the residual is formed from) in one CTA
+template <typename TF, typename TB, int N1, int N2, bool US>
+__global__ void __launch_bounds__(256, 2)
+k_terms_colpass_planes_r(PlaneCols pc, long long pair0, long long npair, int nx, const cplx<TF>* __restrict__ tw_z,
+                         SepMap sm, unsigned tmask, cplx<TF>* __restrict__ W)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2, CW = 16;
+    extern __shared__ __align__(16) unsigned char sh_raw_tpr[];
+    C* stw = (C*)sh_raw_tpr;
+    C* xs = stw + N;
+    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
+    const int q4 = c & 3, nxh = nx / 2 + 1;
+    // grid.x: pair groups (consecutive CTAs read adjacent sectors), grid.y: kx groups
+    const int kx = blockIdx.y * 4 + (c >> 2);
+    const long long g = pair0 / 4 + blockIdx.x;
+    const long long p = 4 * g + q4, pl = p - pair0;
+    const bool live = kx < nxh && p < npair;
+    load_twiddles(stw, tw_z, N);
+    TF dU = 0, kxv = 0;
+    if (live) {
+        const int i1 = pc.pair_i[2 * p], i2 = pc.pair_i[2 * p + 1];
+        dU = (TF)(pc.prof[PR_U * pc.ny + i2] - pc.prof[PR_U * pc.ny + i1]);
+        kxv = (TF)(6.283185307179586476925286766559 * signed_bin(kx, nx) / pc.Lx);
+    }
+    const TF nu2 = (TF)(2.0 * pc.nu), kzs = (TF)(6.283185307179586476925286766559 / pc.Lz);
+    const cplx<TB>* base = (const cplx<TB>*)pc.planes + (long long)kx * pc.npp + p;
+    const long long pstride = (long long)pc.Kc * pc.npp, kzs_el = (long long)nxh * pc.npp;
+    // the planes are read once (streaming loads), except A, which up to three
+    // terms use and which is re-read through the caches; each column is
+    // walked with a pointer that steps N2 kz rows
+    const long long step = (long long)N2 * kzs_el;
+    const cplx<TB>* col0 = base + lane * kzs_el;
+    auto cv = [](cplx<TB> b) { return mk((TF)b.x, (TF)b.y); };
+    const bool want_res = (tmask >> T_RES) & 1u;
+    C r[N1], v[N1];
+    #pragma unroll
+    for (int m = 0; m < N1; ++m) r[m] = mk((TF)0, (TF)0);
+    C* dst0 = W + pl * NTERM * (long long)(US ? sm.nrz : N) * nxh;
+    #pragma unroll 1
+    for (int t = 0; t < NTERM; ++t) {
+        const bool out = (tmask >> t) & 1u;
+        if (!out && !(want_res && (t == T_PHIX || t == T_PHIZ || t == T_XI))) continue;   // uniform
+        if (!live) {
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) v[m] = mk((TF)0, (TF)0);
+        } else if (t == T_A) {
+            const cplx<TB>* pa = col0 + PL_A * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, pa += step) v[m] = cv(ld_ordered(pa));
+        } else if (t == T_PHIX) {
+            const cplx<TB>* ps = col0 + PL_S4 * pstride;
+            const cplx<TB>* pa = col0 + PL_A * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, ps += step, pa += step) {
+                const C s = cv(ld_stream(ps)), av = cv(ld_ordered(pa));
+                v[m] = mk(s.x + dU * av.x + nu2 * kxv * av.y, s.y + dU * av.y - nu2 * kxv * av.x);
+                r[m] = mk(r[m].x - kxv * v[m].y, r[m].y + kxv * v[m].x);
+            }
+        } else if (t == T_PHIZ) {
+            const cplx<TB>* ps = col0 + PL_S6 * pstride;
+            const cplx<TB>* pa = col0 + PL_A * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, ps += step, pa += step) {
+                const C s = cv(ld_stream(ps)), av = cv(ld_ordered(pa));
+                const TF kzv = kzs * (TF)signed_bin(lane + N2 * m, N);
+                v[m] = mk(s.x + nu2 * kzv * av.y, s.y - nu2 * kzv * av.x);
+                r[m] = mk(r[m].x - kzv * v[m].y, r[m].y + kzv * v[m].x);
+            }
+        } else if (t == T_XI) {
+            const cplx<TB>* px = col0 + PL_XI * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, px += step) {
+                v[m] = cv(ld_stream(px));
+                r[m] = r[m] - v[m];
+            }
+        } else if (t == T_RES) {
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) v[m] = r[m];
+        } else {
+            const cplx<TB>* pj = col0 + (t == T_PHIY ? PL_PHIY : PL_PHI) * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, pj += step) v[m] = cv(ld_stream(pj));
+        }
+        if (!out) continue;
+        __syncthreads();                     // exchange buffer free (twiddles ready)
+        fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
+        if (live) {
+            C* dst = dst0 + (long long)t * (US ? sm.nrz : N) * nxh;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const int zr = US ? sm.zrow(lane + N2 * m) : lane + N2 * m;
+                if (zr >= 0) dst[(long long)zr * nxh + kx] = v[m];
+            }
+        }
+    }
+}
+
+// shared-memory variant, any nz: CTA = 4 KXC columns (KXC kx of one pair group)
+template <typename TF, typename TB>
+__global__ void k_terms_colpass_planes(PlaneCols pc, long long pair0, long long npair, int nz, int nx, int KXC,
+                                       const cplx<TF>* __restrict__ tw_z, SepMap sm, unsigned tmask,
+                                       cplx<TF>* __restrict__ W)
+{
+    typedef cplx<TF> C;
+    extern __shared__ __align__(16) unsigned char sh_raw_tp[];
+    const int NC = 4 * KXC, nxh = nx / 2 + 1;
+    C* stw = (C*)sh_raw_tp;
+    C* b0 = stw + nz;
+    C* b1 = b0 + NC * nz;
+    C* rb = b1 + NC * nz;                     // residual spectrum of each column
+    __shared__ TF s_dU[64], s_kx[64];
+    const long long g = pair0 / 4 + blockIdx.x;             // grid.x: pair groups, grid.y: kx groups
+    load_twiddles(stw, tw_z, nz);
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+        const long long p = 4 * g + (c & 3);
+        const int kx = blockIdx.y * KXC + (c >> 2);
+        TF dU = 0;
+        if (p < npair) {
+            const int i1 = pc.pair_i[2 * p], i2 = pc.pair_i[2 * p + 1];
+            dU = (TF)(pc.prof[PR_U * pc.ny + i2] - pc.prof[PR_U * pc.ny + i1]);
+        }
+        s_dU[c] = dU;
+        s_kx[c] = kx < nxh ? (TF)(6.283185307179586476925286766559 * signed_bin(kx, nx) / pc.Lx) : (TF)0;
+    }
+    for (int e = threadIdx.x; e < NC * nz; e += blockDim.x) rb[e] = mk((TF)0, (TF)0);
+    __syncthreads();
+    const TF nu2 = (TF)(2.0 * pc.nu);
+    const long long pstride = (long long)pc.Kc * pc.npp;
+    const bool want_res = (tmask >> T_RES) & 1u;
+    for (int t = 0; t < NTERM; ++t) {
+        const bool out = (tmask >> t) & 1u;
+        if (!out && !(want_res && (t == T_PHIX || t == T_PHIZ || t == T_XI))) continue;   // uniform
+        __syncthreads();
+        for (int e = threadIdx.x; e < NC * nz; e += blockDim.x) {
+            const int c = e % NC, kz = e / NC;
+            const long long p = 4 * g + (c & 3);
+            const int kx = blockIdx.y * KXC + (c >> 2);
+            C v = mk((TF)0, (TF)0);
+            if (kx < nxh && p < npair) {
+                const cplx<TB>* src = (const cplx<TB>*)pc.planes + ((long long)kz * nxh + kx) * pc.npp + p;
+                auto ld = [&](int j) { const cplx<TB> b = src[j * pstride]; return mk((TF)b.x, (TF)b.y); };
+                C& r = rb[c * nz + kz];
+                if (t == T_A) v = ld(PL_A);
+                else if (t == T_PHIX) {
+                    const C s = ld(PL_S4), av = ld(PL_A);
+                    const TF kxv = s_kx[c];
+                    v = mk(s.x + s_dU[c] * av.x + nu2 * kxv * av.y, s.y + s_dU[c] * av.y - nu2 * kxv * av.x);
+                    r = mk(r.x - kxv * v.y, r.y + kxv * v.x);
+                } else if (t == T_PHIZ) {
+                    const C s = ld(PL_S6), av = ld(PL_A);
+                    const TF kzv = (TF)(6.283185307179586476925286766559 * signed_bin(kz, nz) / pc.Lz);
+                    v = mk(s.x + nu2 * kzv * av.y, s.y - nu2 * kzv * av.x);
+                    r = mk(r.x - kzv * v.y, r.y + kzv * v.x);
+                } else if (t == T_XI) {
+                    v = ld(PL_XI);
+                    r = r - v;
+                } else if (t == T_RES) v = r;
+                else v = ld(t == T_PHIY ? PL_PHIY : PL_PHI);
+            }
+            b0[c * nz + kz] = v;
+        }
+        if (!out) continue;
+        const C* res = fft_block<TF, true>(b0, b1, nz, NC, nz, stw);
+        for (int e = threadIdx.x; e < NC * nz; e += blockDim.x) {
+            const int c = e % NC, z = e / NC;
+            const long long p = 4 * g + (c & 3);
+            const int kx = blockIdx.y * KXC + (c >> 2);
+            const int zr = sm.zrow(z);
+            if (kx < nxh && p < npair && zr >= 0)
+                W[((p - pair0) * NTERM + t) * (long long)sm.nrz * nxh + (long long)zr * nxh + kx] = res[c * nz + z];
+        }
+    }
+}
+
+// columns of the shared-memory variant: 4 kx per CTA while its buffers fit
+static int planes_kxc(int nz, size_t csz)
+{
+    int kxc = 4;
+    while (kxc > 1 && (size_t)(1 + 3 * 4 * kxc) * nz * csz > 160 * 1024) kxc /= 2;
+    return kxc;
+}
+
+// the plane-mode column pass of one pair chunk (FP32 transforms only)
+template <typename TF, typename TB>
+static void colpass_planes_launch(const TermArgs& a, long long p0, long long np, cplx<TF>* W, cudaStream_t sc,
+                                  bool us)
+{
+    if constexpr (sizeof(TF) == 4) {
+        typedef cplx<TF> C;
+        const int nxh = a.nx / 2 + 1;
+        PlaneCols pc{a.planes, a.npp, a.Kc, a.pair_i, a.prof, a.ny, a.Lx, a.Lz, a.nu};
+        if (a.nz == 256) {
+            const dim3 g((unsigned)((np + 3) / 4), (nxh + 3) / 4);
+            const size_t sh = (256 + 16 * (16 * 16 + 1)) * sizeof(C);
+            if (us)
+                k_terms_colpass_planes_r<TF, TB, 16, 16, true><<<g, 256, sh, sc>>>(
+                    pc, p0, a.npair, a.nx, (const C*)a.tw_z, a.sep, a.tmask, W);
+            else
+                k_terms_colpass_planes_r<TF, TB, 16, 16, false><<<g, 256, sh, sc>>>(
+                    pc, p0, a.npair, a.nx, (const C*)a.tw_z, a.sep, a.tmask, W);
+        } else {
+            const int kxc = planes_kxc(a.nz, sizeof(C));
+            const dim3 g((unsigned)((np + 3) / 4), (nxh + kxc - 1) / kxc);
+            k_terms_colpass_planes<TF, TB><<<g, 256, (size_t)(1 + 3 * 4 * kxc) * a.nz * sizeof(C), sc>>>(
+                pc, p0, a.npair, a.nz, a.nx, kxc, (const C*)a.tw_z, a.sep, a.tmask, W);
+        }
+    }
+}
+
 template <typename TF, typename TB, typename TO>
 int terms_launch_t(const TermArgs& a)
 {
@@ -286,7 +527,8 @@ int terms_launch_t(const TermArgs& a)
         C* W = (C*)(buf ? a.W2 : a.W);
         cudaStream_t sc = a.st, sr = two ? a.st2 : a.st;
         if (two && c >= 2) cudaStreamWaitEvent(sc, ev_row[buf], 0);     // W buffer free again
-        if (a.nz == 256) {
+        if (a.planes) {
+            colpass_planes_launch<TF, TB>(a, p0, np, W, sc, us);        } else if (a.nz == 256) {
             constexpr int CWR = 16;
             const dim3 g((nxh + CWR - 1) / CWR, ntm, (unsigned)np);
             const size_t sh = (256 + 16 * (16 * CWR + 1)) * sizeof(C);
@@ -343,7 +585,7 @@ int terms_launch_t(const TermArgs& a)
 int terms_launch(const TermArgs& a)
 {
     if (!a.fp32) return terms_launch_t<double, double, double>(a);
-    if (a.comb64) return terms_launch_t<float, double, float>(a);
+    if (a.planes ? a.planes64 : a.comb64) return terms_launch_t<float, double, float>(a);
     return terms_launch_t<float, float, float>(a);
 }
 
@@ -361,7 +603,13 @@ cudaError_t terms_set_attrs(int lim)
                         (const void*)k_terms_colpass_r<float, float, 16, 16, true>,
                         (const void*)k_terms_colpass_r<float, double, 16, 16, true>,
                         (const void*)k_terms_rowpass_r<double, double, 16, 16, true>,
-                        (const void*)k_terms_rowpass_r<float, float, 16, 16, true>};
+                        (const void*)k_terms_rowpass_r<float, float, 16, 16, true>,
+                        (const void*)k_terms_colpass_planes_r<float, float, 16, 16, false>,
+                        (const void*)k_terms_colpass_planes_r<float, double, 16, 16, false>,
+                        (const void*)k_terms_colpass_planes_r<float, float, 16, 16, true>,
+                        (const void*)k_terms_colpass_planes_r<float, double, 16, 16, true>,
+                        (const void*)k_terms_colpass_planes<float, float>,
+                        (const void*)k_terms_colpass_planes<float, double>};
     cudaError_t e = cudaSuccess;
     for (const void* k : ks) {
         cudaFuncAttributes fa;

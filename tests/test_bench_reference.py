@@ -40,7 +40,7 @@ def test_merge_command_line(tmp_path):
         ck = {"header": {"nx": 8, "nz": 8, "ny": ny, "precision": 0, "pair_domain": 0, "nzt": 0, "nxt": 0,
                          "term_set": 127, "mean_count": 1.0, "snap_count": 1.0, "Lx": 1.0, "Lz": 1.0, "nu": 0.1},
               "mean_sum": rng.standard_normal(4 * ny), "stats": rng.standard_normal(M.NSTAT * ny),
-              "acc": rng.standard_normal(6) + 1j * rng.standard_normal(6)}
+              "mean": np.linspace(0.0, 1.0, 4 * ny), "acc": rng.standard_normal(6) + 1j * rng.standard_normal(6)}
         p = str(tmp_path / f"j{r}.ckpt")
         M.write(p, ck)
         paths.append(p)

@@ -20,8 +20,10 @@ def _fake(rank, ny=7, nacc=50):
     rng = np.random.default_rng(100 + rank)
     hdr = {"nx": 16, "nz": 8, "ny": ny, "precision": 0, "pair_domain": 0, "nzt": 0, "nxt": 0, "term_set": 127,
            "mean_count": 2.0 + rank, "snap_count": 2.0 + rank, "Lx": 12.5, "Lz": 6.25, "nu": 0.005}
+    # every job took its spectra about the same Step-1 mean
+    mean = np.random.default_rng(7).standard_normal(4 * ny)
     return {"header": hdr, "mean_sum": rng.standard_normal(4 * ny), "stats": rng.standard_normal(M.NSTAT * ny),
-            "acc": rng.standard_normal(nacc) + 1j * rng.standard_normal(nacc)}
+            "mean": mean, "acc": rng.standard_normal(nacc) + 1j * rng.standard_normal(nacc)}
 
 
 def test_merge_sums(tmp_path):
@@ -55,10 +57,32 @@ def test_merge_rejects_mismatch_and_truncation(tmp_path):
     M.write(pc, c)
     with pytest.raises(M.CheckpointError):
         M.merge([pa, pc], str(tmp_path / "m.ckpt"))
+    d = _fake(3)
+    d["header"]["acc_kind"] = 1                 # plane spectra of the split path
+    pd = str(tmp_path / "d.ckpt")
+    M.write(pd, d)
+    with pytest.raises(M.CheckpointError):
+        M.merge([pa, pd], str(tmp_path / "m.ckpt"))
     with open(pb, "wb") as f:
         f.write(b"GKECKPT")
     with pytest.raises(M.CheckpointError):
         M.read(pb)
+
+
+def test_merge_refuses_jobs_with_their_own_means(tmp_path):
+    # two jobs that each froze the mean of their own snapshot subset: their
+    # spectra are about different means and do not add (Step 1 precedes Step 2)
+    a, b = _fake(0), _fake(1)
+    b["mean"] = b["mean"] * (1.0 + 1e-6)
+    pa, pb = str(tmp_path / "a.ckpt"), str(tmp_path / "b.ckpt")
+    M.write(pa, a)
+    M.write(pb, b)
+    with pytest.raises(M.CheckpointError, match="mean"):
+        M.merge([pa, pb], str(tmp_path / "m.ckpt"))
+    # a difference at the rounding level of the sums is the same mean
+    b["mean"] = a["mean"] * (1.0 + 1e-15)
+    M.write(pb, b)
+    M.merge([pa, pb], str(tmp_path / "m.ckpt"))
 
 
 def _free_port():
