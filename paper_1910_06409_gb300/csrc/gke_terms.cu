@@ -470,6 +470,289 @@ static int planes_kxc(int nz, size_t csz)
     return kxc;
 }
 
+// ---------- plane mode at nz = nx = N1 N2: pair-contiguous W between the passes
+// The planes hold, per wavenumber, consecutive pairs contiguously, so both
+// passes take 16 consecutive pairs per CTA: the column pass reads one
+// 128-byte line per (plane, kz) and writes Wp[t][zr][kx][pl] (16 pairs = one
+// line per (term, z, kx)); the row pass reads those lines back and stages
+// its outputs in shared memory, so each pair's row of separations leaves as
+// one contiguous store.  pc = pairs per chunk (the stride of Wp's rows).
+template <typename TF, typename TB, int N1, int N2, bool US>
+__global__ void __launch_bounds__(256, 2)
+k_terms_colpass_pt(PlaneCols pc, long long pair0, long long npair, long long pchunk, int nx,
+                   const cplx<TF>* __restrict__ tw_z, SepMap sm, unsigned tmask, cplx<TF>* __restrict__ W)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2, CW = 16;
+    extern __shared__ __align__(16) unsigned char sh_raw_cpt[];
+    C* stw = (C*)sh_raw_cpt;
+    C* xs = stw + N;
+    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
+    const int nxh = nx / 2 + 1;
+    const int kx = blockIdx.y;
+    const long long pl = (long long)blockIdx.x * CW + c, p = pair0 + pl;
+    const bool live = p < npair && pl < pchunk;
+    load_twiddles(stw, tw_z, N);
+    TF dU = 0;
+    if (live) {
+        const int i1 = pc.pair_i[2 * p], i2 = pc.pair_i[2 * p + 1];
+        dU = (TF)(pc.prof[PR_U * pc.ny + i2] - pc.prof[PR_U * pc.ny + i1]);
+    }
+    const TF kxv = (TF)(6.283185307179586476925286766559 * signed_bin(kx, nx) / pc.Lx);
+    const TF nu2 = (TF)(2.0 * pc.nu), kzs = (TF)(6.283185307179586476925286766559 / pc.Lz);
+    const long long kzs_el = (long long)nxh * pc.npp, pstride = (long long)pc.Kc * pc.npp;
+    const long long step = (long long)N2 * kzs_el;
+    const cplx<TB>* col0 = (const cplx<TB>*)pc.planes + (long long)kx * pc.npp + p + lane * kzs_el;
+    auto cv = [](cplx<TB> b) { return mk((TF)b.x, (TF)b.y); };
+    const bool want_res = (tmask >> T_RES) & 1u;
+    C r[N1], v[N1];
+    #pragma unroll
+    for (int m = 0; m < N1; ++m) r[m] = mk((TF)0, (TF)0);
+    const int nrz = US ? sm.nrz : N;
+    #pragma unroll 1
+    for (int t = 0; t < NTERM; ++t) {
+        const bool out = (tmask >> t) & 1u;
+        if (!out && !(want_res && (t == T_PHIX || t == T_PHIZ || t == T_XI))) continue;   // uniform
+        if (!live) {
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) v[m] = mk((TF)0, (TF)0);
+        } else if (t == T_A) {
+            const cplx<TB>* pa = col0 + PL_A * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, pa += step) v[m] = cv(ld_ordered(pa));
+        } else if (t == T_PHIX) {
+            const cplx<TB>* ps = col0 + PL_S4 * pstride;
+            const cplx<TB>* pa = col0 + PL_A * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, ps += step, pa += step) {
+                const C s = cv(ld_stream(ps)), av = cv(ld_ordered(pa));
+                v[m] = mk(s.x + dU * av.x + nu2 * kxv * av.y, s.y + dU * av.y - nu2 * kxv * av.x);
+                r[m] = mk(r[m].x - kxv * v[m].y, r[m].y + kxv * v[m].x);
+            }
+        } else if (t == T_PHIZ) {
+            const cplx<TB>* ps = col0 + PL_S6 * pstride;
+            const cplx<TB>* pa = col0 + PL_A * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, ps += step, pa += step) {
+                const C s = cv(ld_stream(ps)), av = cv(ld_ordered(pa));
+                const TF kzv = kzs * (TF)signed_bin(lane + N2 * m, N);
+                v[m] = mk(s.x + nu2 * kzv * av.y, s.y - nu2 * kzv * av.x);
+                r[m] = mk(r[m].x - kzv * v[m].y, r[m].y + kzv * v[m].x);
+            }
+        } else if (t == T_XI) {
+            const cplx<TB>* px = col0 + PL_XI * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, px += step) {
+                v[m] = cv(ld_stream(px));
+                r[m] = r[m] - v[m];
+            }
+        } else if (t == T_RES) {
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) v[m] = r[m];
+        } else {
+            const cplx<TB>* pj = col0 + (t == T_PHIY ? PL_PHIY : PL_PHI) * pstride;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m, pj += step) v[m] = cv(ld_stream(pj));
+        }
+        if (!out) continue;
+        __syncthreads();                     // exchange buffer free (twiddles ready)
+        fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
+        if (live) {
+            C* dst = W + (long long)t * nrz * nxh * pchunk + (long long)kx * pchunk + pl;
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const int zr = US ? sm.zrow(lane + N2 * m) : lane + N2 * m;
+                if (zr >= 0) dst[(long long)zr * nxh * pchunk] = v[m];
+            }
+        }
+    }
+}
+
+// row pass from Wp: CTA = 16 consecutive pairs x one kept z row, N2 lanes per
+// pair; the seven terms as four packed sequences (t0 + i t1), outputs staged
+// per term pair in shared memory, then written pair row by pair row
+constexpr int RZ_PT = 4;           // z rows per CTA of k_terms_rowpass_pt
+template <typename TF, typename TO, int N1, int N2, bool US, int RZ = RZ_PT>
+__global__ void __launch_bounds__(N1 * N2)
+k_terms_rowpass_pt(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
+                   long long pchunk, int ny, double inv_count, const double* __restrict__ prof,
+                   const cplx<TF>* __restrict__ tw_x, SepMap sm, unsigned tmask, TO* __restrict__ terms,
+                   float* __restrict__ spec)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2, nxh = N / 2 + 1, CW = 16;
+    extern __shared__ __align__(16) unsigned char sh_raw_rpt[];
+    C* stw = (C*)sh_raw_rpt;
+    C* xs = stw + N;                                  // exchange: N1 (N2 CW + 1)
+    TF* ot = (TF*)xs;                                 // staged outputs [2][CW][N + 1], in the exchange buffer
+    static_assert(2 * CW * (N + 1) * sizeof(TF) <= N1 * (N2 * CW + 1) * sizeof(C), "staging fits the exchange buffer");
+    __shared__ TF s_one[CW][NTERM];
+    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
+    const long long pl0 = (long long)blockIdx.x * CW, pl = pl0 + c, p = pair0 + pl;
+    const bool live = p < npair && pl < pchunk;
+    const int nz = sm.nrz, nrx = US ? sm.nrx : N;
+    load_twiddles(stw, tw_x, N);
+    if (threadIdx.x < CW) {
+        const long long pp = pair0 + pl0 + threadIdx.x;
+        double one[NTERM] = {0, 0, 0, 0, 0, 0, 0};
+        if (pp < npair && pl0 + threadIdx.x < pchunk) onepoint(prof, ny, pair_i[2 * pp], pair_i[2 * pp + 1], one);
+        for (int t = 0; t < NTERM; ++t) s_one[threadIdx.x][t] = (TF)one[t];
+    }
+    const TF ic = (TF)inv_count;
+    const long long NN = (long long)nz * nrx;
+    const long long tstride = (long long)nz * nxh * pchunk;
+    // output column of this thread and the CTA's live pairs
+    const int xo = US ? sm.xcol(threadIdx.x) : (int)threadIdx.x;
+    const int nlive = (int)min((long long)CW, min(npair - (pair0 + pl0), pchunk - pl0));
+    // RZ consecutive kept z rows per CTA: each pair's outputs are RZ rows in a row
+    for (int zr = blockIdx.y * RZ; zr < min(nz, blockIdx.y * RZ + RZ); ++zr) {
+    const long long orow = (long long)zr * nrx + xo;
+    const C* wrow = W + (long long)zr * nxh * pchunk + pl;
+    for (int jq = 0; jq < 4; ++jq) {
+        const int ta = 2 * jq, tb = 2 * jq + 1;
+        const bool ha = (tmask >> ta) & 1u, hb = tb < NTERM && ((tmask >> tb) & 1u);
+        if (!ha && !hb) continue;                   // uniform over the CTA
+        const C* wa = wrow + ta * tstride;
+        const C* wb = wrow + (tb < NTERM ? tb : ta) * tstride;
+        C v[N1];
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const int k = lane + N2 * m;
+            C A = mk((TF)0, (TF)0), B = A;           // terms outside tmask: zero, not stale W
+            if (live) {
+                // kx above nx/2 reads its mirror row (Hermitian extension): plain
+                // loads, so the second read of a line hits L1
+                const long long off = (long long)(k < nxh ? k : N - k) * pchunk;
+                if (ha) A = wa[off];
+                if (hb) B = wb[off];
+                if (k >= nxh) { A.y = -A.y; B.y = -B.y; }
+            }
+            if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
+            v[m] = mk(A.x - B.y, A.y + B.x);
+        }
+        __syncthreads();                     // exchange and staging buffers free (s_one, twiddles ready)
+        fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
+        __syncthreads();                     // the exchange buffer now stages the outputs
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const int x = lane + N2 * m;
+            ot[c * (N + 1) + x] = v[m].x;
+            ot[(CW + c) * (N + 1) + x] = v[m].y;
+        }
+        __syncthreads();
+        // pair rows: thread = separation index x (blockDim = N), so each pair's
+        // row leaves as one contiguous store across the CTA
+        if (xo >= 0) {
+            #pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int q = 2 * jq + h;
+                if (q >= NTERM || !(h ? hb : ha)) continue;
+                const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
+                TO* tp = terms + ((long long)q * npair + pair0 + pl0) * NN + orow;
+                float* sq = (spec != nullptr && si >= 0) ? spec + ((long long)si * npair + pair0 + pl0) * NN + orow
+                                                          : nullptr;
+                const TF* src = ot + h * CW * (N + 1) + threadIdx.x;
+                #pragma unroll
+                for (int cc = 0; cc < CW; ++cc) {
+                    if (cc < nlive) {
+                        const TF sp = src[cc * (N + 1)] * ic;
+                        st_stream(tp + cc * NN, (TO)(sp + s_one[cc][q]));
+                        if (sq) st_stream(sq + cc * NN, (float)sp);
+                    }
+                }
+            }
+        }
+    }
+    }
+}
+
+
+// row pass from Wp, four pairs per sequence group: CTA = 4 consecutive pairs x
+// N2 lanes x 4 kept z rows (256 threads); a warp holds 4 pairs x 8 lanes of one
+// row, so its loads of Wp (4 pairs at 8 kx) and its stores of the terms (4
+// pairs x 8 consecutive separations) are whole 32-byte sectors.  The exchange
+// regions of the (row, pair) sequences are 4 mod 16 complex values apart, so
+// a half-warp (4 pairs x 4 lanes) hits 16 distinct bank pairs.
+template <typename TF, typename TO, int N1, int N2, bool US>
+__global__ void __launch_bounds__(256)
+k_terms_rowpass_p4(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
+                   long long npair, long long pchunk, int ny, double inv_count, const double* __restrict__ prof,
+                   const cplx<TF>* __restrict__ tw_x, SepMap sm, unsigned tmask, TO* __restrict__ terms,
+                   float* __restrict__ spec)
+{
+    typedef cplx<TF> C;
+    constexpr int N = N1 * N2, nxh = N / 2 + 1, NP = 4, NR = 256 / (NP * N2);
+    constexpr int REG = N1 * (N2 + 1) + 4;            // exchange region of one sequence (4 mod 16)
+    static_assert(REG % 16 == 4 && NR >= 1, "exchange layout");
+    extern __shared__ __align__(16) unsigned char sh_raw_rp4[];
+    C* stw = (C*)sh_raw_rp4;
+    C* xs = stw + N;
+    __shared__ TF s_one[NP][NTERM];
+    const int c = threadIdx.x % NP, lane = (threadIdx.x / NP) % N2, r = threadIdx.x / (NP * N2);
+    const long long pl = (long long)blockIdx.x * NP + c, p = pair0 + pl;
+    const bool live = p < npair && pl < pchunk;
+    const int nz = sm.nrz, nrx = US ? sm.nrx : N;
+    const int zr = blockIdx.y * NR + r;
+    const bool zlive = zr < nz;
+    load_twiddles(stw, tw_x, N);
+    if (threadIdx.x < NP) {
+        const long long pp = pair0 + (long long)blockIdx.x * NP + threadIdx.x;
+        double one[NTERM] = {0, 0, 0, 0, 0, 0, 0};
+        if (pp < npair && (long long)blockIdx.x * NP + threadIdx.x < pchunk)
+            onepoint(prof, ny, pair_i[2 * pp], pair_i[2 * pp + 1], one);
+        for (int t = 0; t < NTERM; ++t) s_one[threadIdx.x][t] = (TF)one[t];
+    }
+    const TF ic = (TF)inv_count;
+    const long long NN = (long long)nz * nrx;
+    const long long tstride = (long long)nz * nxh * pchunk;
+    const C* wrow = W + (long long)(zlive ? zr : 0) * nxh * pchunk + pl;
+    C* xr = xs + (r * NP + c) * REG;
+    for (int jq = 0; jq < 4; ++jq) {
+        const int ta = 2 * jq, tb = 2 * jq + 1;
+        const bool ha = (tmask >> ta) & 1u, hb = tb < NTERM && ((tmask >> tb) & 1u);
+        if (!ha && !hb) continue;                   // uniform over the CTA
+        const C* wa = wrow + ta * tstride;
+        const C* wb = wrow + (tb < NTERM ? tb : ta) * tstride;
+        C v[N1];
+        #pragma unroll
+        for (int m = 0; m < N1; ++m) {
+            const int k = lane + N2 * m;
+            C A = mk((TF)0, (TF)0), B = A;           // terms outside tmask: zero, not stale W
+            if (live && zlive) {
+                const long long off = (long long)(k < nxh ? k : N - k) * pchunk;
+                if (ha) A = wa[off];
+                if (hb) B = wb[off];
+                if (k >= nxh) { A.y = -A.y; B.y = -B.y; }
+            }
+            if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
+            v[m] = mk(A.x - B.y, A.y + B.x);
+        }
+        __syncthreads();                     // exchange buffer free (and s_one, twiddles ready)
+        fft2l<TF, N1, N2, true>(v, lane, xr, N2 + 1, 1, stw);
+        if (live && zlive) {
+            #pragma unroll
+            for (int m = 0; m < N1; ++m) {
+                const int x = lane + N2 * m;
+                const int xo = US ? sm.xcol(x) : x;
+                if (xo < 0) continue;
+                const long long e = (long long)zr * nrx + xo;
+                #pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = 2 * jq + h;
+                    if (q >= NTERM) break;
+                    if (!(h ? hb : ha)) continue;
+                    const TF sp = (h ? v[m].y : v[m].x) * ic;
+                    st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[c][q]));
+                    if (spec != nullptr) {
+                        const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
+                        if (si >= 0) st_stream(spec + ((long long)si * npair + p) * NN + e, (float)sp);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // the plane-mode column pass of one pair chunk (FP32 transforms only)
 template <typename TF, typename TB>
 static void colpass_planes_launch(const TermArgs& a, long long p0, long long np, cplx<TF>* W, cudaStream_t sc,
@@ -479,7 +762,17 @@ static void colpass_planes_launch(const TermArgs& a, long long p0, long long np,
         typedef cplx<TF> C;
         const int nxh = a.nx / 2 + 1;
         PlaneCols pc{a.planes, a.npp, a.Kc, a.pair_i, a.prof, a.ny, a.Lx, a.Lz, a.nu};
-        if (a.nz == 256) {
+        if (a.nz == 256 && a.nx == 256) {
+            // pair-contiguous W (k_terms_rowpass_pt reads it)
+            const dim3 g((unsigned)((np + 15) / 16), nxh);
+            const size_t sh = (256 + 16 * (16 * 16 + 1)) * sizeof(C);
+            if (us)
+                k_terms_colpass_pt<TF, TB, 16, 16, true><<<g, 256, sh, sc>>>(pc, p0, a.npair, a.pair_chunk, a.nx,
+                                                                            (const C*)a.tw_z, a.sep, a.tmask, W);
+            else
+                k_terms_colpass_pt<TF, TB, 16, 16, false><<<g, 256, sh, sc>>>(pc, p0, a.npair, a.pair_chunk, a.nx,
+                                                                             (const C*)a.tw_z, a.sep, a.tmask, W);
+        } else if (a.nz == 256) {
             const dim3 g((unsigned)((np + 3) / 4), (nxh + 3) / 4);
             const size_t sh = (256 + 16 * (16 * 16 + 1)) * sizeof(C);
             if (us)
@@ -494,6 +787,27 @@ static void colpass_planes_launch(const TermArgs& a, long long p0, long long np,
             k_terms_colpass_planes<TF, TB><<<g, 256, (size_t)(1 + 3 * 4 * kxc) * a.nz * sizeof(C), sc>>>(
                 pc, p0, a.npair, a.nz, a.nx, kxc, (const C*)a.tw_z, a.sep, a.tmask, W);
         }
+    }
+}
+
+// the row pass from the pair-contiguous W of k_terms_colpass_pt
+template <typename TF, typename TO>
+static void rowpass_pt_launch(const TermArgs& a, long long p0, long long np, const cplx<TF>* W, cudaStream_t sr,
+                              bool us)
+{
+    if constexpr (sizeof(TF) == 4) {
+        typedef cplx<TF> C;
+        // 4 pairs x 4 rows per CTA
+        const dim3 g((unsigned)((np + 3) / 4), (unsigned)((a.sep.nrz + 3) / 4));
+        const size_t sh = (256 + 16 * (16 * 17 + 4)) * sizeof(C);
+        if (us)
+            k_terms_rowpass_p4<TF, TO, 16, 16, true><<<g, 256, sh, sr>>>(
+                W, a.pair_i, p0, a.npair, a.pair_chunk, a.ny, a.inv_count, a.prof, (const C*)a.tw_x, a.sep, a.tmask,
+                (TO*)a.terms, a.spec);
+        else
+            k_terms_rowpass_p4<TF, TO, 16, 16, false><<<g, 256, sh, sr>>>(
+                W, a.pair_i, p0, a.npair, a.pair_chunk, a.ny, a.inv_count, a.prof, (const C*)a.tw_x, a.sep, a.tmask,
+                (TO*)a.terms, a.spec);
     }
 }
 
@@ -547,7 +861,9 @@ int terms_launch_t(const TermArgs& a)
             cudaEventRecord(ev_col[buf], sc);
             cudaStreamWaitEvent(sr, ev_col[buf], 0);
         }
-        if (a.nx == 256) {
+        if (sizeof(TF) == 4 && a.planes && a.nz == 256 && a.nx == 256) {
+            rowpass_pt_launch<TF, TO>(a, p0, np, W, sr, us);
+        } else if (a.nx == 256) {
             constexpr int RZR = 4;
             const dim3 g((a.sep.nrz + RZR - 1) / RZR, (unsigned)np);
             const size_t sh = (256 + RZR * 16 * 17) * sizeof(C);
@@ -609,7 +925,15 @@ cudaError_t terms_set_attrs(int lim)
                         (const void*)k_terms_colpass_planes_r<float, float, 16, 16, true>,
                         (const void*)k_terms_colpass_planes_r<float, double, 16, 16, true>,
                         (const void*)k_terms_colpass_planes<float, float>,
-                        (const void*)k_terms_colpass_planes<float, double>};
+                        (const void*)k_terms_colpass_planes<float, double>,
+                        (const void*)k_terms_colpass_pt<float, float, 16, 16, false>,
+                        (const void*)k_terms_colpass_pt<float, double, 16, 16, false>,
+                        (const void*)k_terms_colpass_pt<float, float, 16, 16, true>,
+                        (const void*)k_terms_colpass_pt<float, double, 16, 16, true>,
+                        (const void*)k_terms_rowpass_pt<float, float, 16, 16, false>,
+                        (const void*)k_terms_rowpass_pt<float, float, 16, 16, true>,
+                        (const void*)k_terms_rowpass_p4<float, float, 16, 16, false>,
+                        (const void*)k_terms_rowpass_p4<float, float, 16, 16, true>};
     cudaError_t e = cudaSuccess;
     for (const void* k : ks) {
         cudaFuncAttributes fa;
