@@ -68,7 +68,7 @@ def correlator_cmac(wl, ns):
 # stage missing here reports null (not captured since its kernels changed).
 NCU_TRAFFIC_GB = {
     "f64": {"correlate": 104.4, "combine": 94.8, "terms": 105.1, "stencil": 39.9, "products": 46.4},
-    "bf16x3": {"correlate": 65.8, "combine": 47.4, "terms": 60.2, "stencil": 28.8, "products": 27.4},
+    "bf16x3": {"stencil": 28.8, "products": 27.4},
 }
 
 
@@ -96,15 +96,18 @@ def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
     comb = wl.npair * 7 * Nk * cz
     terms = 7 * wl.npair * N * tz
     spec_arr = wl.npair * N * 4
+    # split-BF16 plans with one 128-row tile write six plane spectra per
+    # (wavenumber, pair) from the tensor-core epilogue: no raw contractions,
+    # no combine stage; the transforms read the planes
+    planes = precision == "bf16x3" and (ny <= 128 or ny == 129)
+    pl_bytes = 6 * Nk * (4 * ((wl.npair + 3) // 4)) * cz
     hbm = {
         "products": ns * 4 * ny * Nk * 16 + 11 * Nk * ns * ny * cz,
-        "combine": raw + comb,
-        "terms": comb + terms + (3 * spec_arr if f32 else 0),
+        "terms": (pl_bytes if planes else comb) + terms + (3 * spec_arr if f32 else 0),
         "stencil": (13 * spec_arr) if f32 else (9 * wl.npair * N * 8),
     }
-    if f32:
-        # contraction stage: operand split + tensor-core contractions + edge
-        hbm["correlate_bytes"] = 11 * Nk * ns * ny * cz + raw
+    if not planes:
+        hbm["combine"] = raw + comb
     peak_bw = pk["hbm_gbs"]
     out = {}
     for st, b in hbm.items():
@@ -526,14 +529,19 @@ def run_ours(args, world, rank, local):
         cpu = {"value": r, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
                "seconds": dt}
     if rank == 0:
+        # the split-BF16 result (the metric's subject) first and compact, the
+        # per-stage tables last, so a truncated tail of the line keeps it
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16x3/f32", "f32": "f32"}[args.precision],
-                "data": "synthetic", "config": config_of(wl, args.precision), "parallelism": f"replicas{world}",
-                "stage_ms": stage_ms,
-                "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "roofline": roof,
-                "stage_roofline": rl, "split_bf16x3": split, "fp32_cuda_cores": f32v,
-                "cpu_baseline": cpu}
+                "data": "synthetic",
+                "split_bf16x3": compact(split), "config": config_of(wl, args.precision),
+                "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
+                "parallelism": f"replicas{world}", "fp32_cuda_cores": compact(f32v),
+                "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+                "stage_roofline": {k: short_roof(v) for k, v in rl.items()},
+                "split_stage_roofline": None if split is None else {k: short_roof(v) for k, v in
+                                                                    split["stage_roofline"].items()}}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -571,13 +579,41 @@ def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world, precisi
     barrier()
     launches = N.gke_launch_count(plan) - l0
     stage_ms = {k: v / args.steps for k, v in N.gke_stage_times(plan).items()}
-    N.gke_destroy(plan)
+    N.gke_set_timing(plan, False)
     ms = e0.elapsed_time(e1) / args.steps
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    # end to end through the public call with pinned host buffers: the
+    # snapshots in and the terms out inside the timed region
+    e2e = None
+    if not args.no_e2e and precision == "bf16x3":
+        f_host = f_dev.cpu().pin_memory()
+        out_host = torch.empty(t32.shape, dtype=torch.float32).pin_memory()
+        N.gke_compute(plan, f_host, ns, out_host)
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 3))
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ke):
+            N.gke_compute(plan, f_host, ns, out_host)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = e0.elapsed_time(e1) / ke
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        e2e = {"value": world * npair * ns / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(f_host.numel() * f_host.element_size()),
+               "d2h_bytes_per_step": int(out_host.numel() * out_host.element_size())}
+        del f_host, out_host
+    N.gke_destroy(plan)
     err = {}
     for t, name in enumerate(TERM_NAMES):
         ref = terms64[t]
@@ -587,7 +623,7 @@ def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world, precisi
     del t32
     pk, pk_kind = peaks()
     rl = stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind)
-    return {"value": world * npair * ns / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+    return {"value": world * npair * ns / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "e2e": e2e,
             "speedup_vs_f64": ms64 / ms, "max_rel_err": err, "tolerance": 1e-6,
             "within_tolerance": all(e <= 1e-6 for e in err.values()),
             "stage_ms": stage_ms, "gpu_launches": launches, "roofline": rl.get("correlate"),
@@ -595,6 +631,26 @@ def run_split_beside(args, wl, ns, f_dev, terms64, ms64, barrier, world, precisi
 
 
 TERM_NAMES = ("A", "Phi_x", "Phi_y", "Phi_z", "phi", "xi", "residual")
+
+
+def short_roof(r):
+    """A stage roofline with rounded figures."""
+    if r is None:
+        return None
+    keep = ("bound", "achieved", "peak", "unit", "frac", "launch_ms", "traffic")
+    return {k: (round(r[k], 4) if isinstance(r.get(k), float) else r.get(k)) for k in keep if k in r}
+
+
+def compact(run):
+    """The split-path summary printed early in the JSON line."""
+    if run is None:
+        return None
+    return {"value": run["value"], "unit": run["unit"], "ms_per_step": round(run["ms_per_step"], 3),
+            "speedup_vs_f64": round(run["speedup_vs_f64"], 2),
+            "max_rel_err": {k: float("%.3g" % v) for k, v in run["max_rel_err"].items()},
+            "tolerance": run["tolerance"], "within_tolerance": run["within_tolerance"],
+            "roofline": short_roof(run["roofline"]), "e2e": run.get("e2e"),
+            "stage_ms": {k: round(v, 3) for k, v in run["stage_ms"].items()}, "gpu_launches": run["gpu_launches"]}
 
 
 def main():
