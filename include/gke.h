@@ -257,20 +257,22 @@ long long gke_launch_count(gke_plan_t plan);
 
 /* gke_compute without any device allocation, for callers that cannot call
  * cudaMalloc (code running inside a memory pool or allocator it must not
- * re-enter, runtimes that forbid device allocation after start-up, work
- * captured around fixed addresses).  The paper has no counterpart: this is a
- * deployment variant of the FP64 path.  Workspaces come from one file-scope
- * device array of GKE_NOALLOC_SCRATCH_BYTES that every GPU loading the
- * library holds until the process exits; problems needing more return
- * GKE_ERR_UNSUPPORTED (roughly: nx nz ny^2 <= 2e5 at 2 snapshots, e.g.
- * 16 x 16 x 17; use a plan above that).  FP64 precision only
- * (desc->precision = GKE_PREC_F64, else GKE_ERR_UNSUPPORTED); fields, terms
- * and profiles (may be NULL) must be device pointers (else GKE_ERR_ARG);
- * desc->max_snap is ignored.  The first call on a device finds the array's
- * device address and sets kernel attributes, so make it before any stream
- * capture.  All calls share the array: calls that overlap on the GPU race;
- * each call clears what must start at zero.  Synchronises `stream`.  Status
- * codes only (no message).                                                   */
+ * re-enter, runtimes that forbid device allocation after start-up).  The
+ * paper has no counterpart: this is a deployment variant of the FP64 path.
+ * Workspaces come from one file-scope device array of
+ * GKE_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; problems needing more return GKE_ERR_UNSUPPORTED
+ * (roughly: nx nz ny^2 <= 2e5 at 2 snapshots, e.g. 16 x 16 x 17; use a plan
+ * above that).  nx and nz as for gke_plan (2^a or 3 * 2^a in [8, 1024], else
+ * GKE_ERR_UNSUPPORTED); FP64 precision only (desc->precision = GKE_PREC_F64,
+ * else GKE_ERR_UNSUPPORTED), the triangle pair domain at full resolution;
+ * fields, terms and profiles (may be NULL) must be device pointers (else
+ * GKE_ERR_ARG); desc->max_snap is ignored.  The first call on a device finds
+ * the array's device address and sets kernel attributes, so make it before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race; each call clears what must start at zero.  Each call uploads its
+ * small tables (one copy each) and synchronises `stream` before returning.
+ * Status codes only (no message).                                            */
 #define GKE_NOALLOC_SCRATCH_BYTES (32u << 20)
 gke_status gke_compute_noalloc(const gke_desc* desc, const void* fields, int nsnap, double* terms,
                                double* profiles, void* stream);

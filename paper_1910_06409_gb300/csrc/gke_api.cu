@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <unistd.h>
 #include <type_traits>
 #include <vector>
 
@@ -172,7 +173,6 @@ static void fornberg_d1(const double* x, int n, double z0, double* w)
     for (int i = 0; i < n; ++i) w[i] = c1[i];
 }
 
-static const int EPS_KCHUNK = 16;
 // bytes of inverse-transform scratch per pair chunk (each of two buffers)
 static const long long W_CHUNK_BYTES = 192LL << 20;
 // bytes of contractions + per-pair spectra of one wavenumber chunk (chunked mode)
@@ -180,9 +180,6 @@ static const size_t DEC_CHUNK_BYTES = (size_t)32 << 30;
 // above this size of one batch's contractions the plan runs in the chunked mode
 static const size_t CHUNKED_RAW_BYTES = (size_t)96 << 30;
 
-static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
-// transform lengths of the Stockham kernels: 2^a or 3 * 2^a
-static bool fft_len_ok(int n) { return is_pow2(n) || (n % 3 == 0 && is_pow2(n / 3)); }
 
 // separation indices kept along one direction (a-posteriori undersampling,
 // Sec. 3.4): with d = min(m, n - m), keep d < t1, multiples of s1 for
@@ -232,26 +229,6 @@ static int smem_limit()
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return v;
-}
-
-// tile parameters of the transform kernels for a grid and a complex size:
-// each CTA keeps its ping-pong buffers and twiddles within 64 KB, so three
-// CTAs fit on an SM
-struct Tiles { int cw_ci, rz_rp, cw_cf, yb_cf, cw_tc, rz_tr; };
-static Tiles pick_tiles(int nx, int nz, size_t csz)
-{
-    Tiles t;
-    const size_t lim = 64 * 1024;
-    auto fits = [&](size_t elems) { return elems * csz <= lim; };
-    t.cw_ci = 16; while (t.cw_ci > 1 && !fits((size_t)(1 + 2 * t.cw_ci) * nz)) t.cw_ci /= 2;
-    t.rz_rp = 8;  while (t.rz_rp > 1 && !fits((size_t)(1 + 8 * t.rz_rp) * nx)) t.rz_rp /= 2;
-    t.cw_cf = 4; t.yb_cf = 8;
-    while (t.cw_cf * t.yb_cf > 1 && !fits((size_t)(1 + 2 * t.cw_cf * t.yb_cf) * nz)) {
-        if (t.cw_cf > 1) t.cw_cf /= 2; else t.yb_cf /= 2;
-    }
-    t.cw_tc = 16; while (t.cw_tc > 1 && !fits((size_t)(1 + 2 * t.cw_tc) * nz)) t.cw_tc /= 2;
-    t.rz_tr = 8;  while (t.rz_tr > 1 && !fits((size_t)(1 + 8 * t.rz_tr) * nx)) t.rz_tr /= 2;
-    return t;
 }
 
 static cudaError_t set_smem_attrs()
@@ -317,12 +294,29 @@ static bool tune_lookup(const char* path, const std::string& key, int& w_mib, in
     return found;
 }
 
+// The file's lines plus this one go to a private temporary file that is then
+// renamed over the tuning file, so processes storing at the same time (replica
+// ranks tuning one shape) never interleave partial lines; one of two racing
+// stores may be lost, which only means timing that shape again.  Lookups take
+// the last valid line of a key.
 static void tune_store(const char* path, const std::string& key, int w_mib, int kc)
 {
-    FILE* fp = fopen(path, "a");
-    if (!fp) return;
-    fprintf(fp, "%s : w_mib=%d comb_kc=%d\n", key.c_str(), w_mib, kc);
-    fclose(fp);
+    std::string text;
+    if (FILE* in = fopen(path, "r")) {
+        char buf[4096];
+        size_t n;
+        while ((n = fread(buf, 1, sizeof buf, in)) > 0) text.append(buf, n);
+        fclose(in);
+        if (!text.empty() && text.back() != '\n') text += '\n';
+    }
+    char line[1024];
+    snprintf(line, sizeof line, "%s : w_mib=%d comb_kc=%d\n", key.c_str(), w_mib, kc);
+    text += line;
+    const std::string tmp = std::string(path) + ".tmp." + std::to_string((long long)getpid());
+    FILE* out = fopen(tmp.c_str(), "w");
+    if (!out) return;
+    const bool ok = fwrite(text.data(), 1, text.size(), out) == text.size();
+    if (fclose(out) != 0 || !ok || rename(tmp.c_str(), path) != 0) remove(tmp.c_str());
 }
 
 // device time of f() on the plan's stream, the second of two runs
@@ -619,10 +613,7 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOC(p->nonfinite, 1);
     if (under) ALLOC(p->sep_tab, (size_t)d.nz + d.nx + nrz + nrx);
     {
-        const Tiles tl = pick_tiles(d.nx, d.nz, p->csz);
-        size_t a1 = (size_t)6 * ny * std::max((d.nz + tl.rz_rp - 1) / tl.rz_rp, (d.nz + 3) / 4);
-        size_t a2 = (size_t)ny * ((Nk + EPS_KCHUNK - 1) / EPS_KCHUNK);
-        p->part_count = std::max(a1, a2);
+        p->part_count = part_count(d.nz, ny, Nk, pick_tiles(d.nx, d.nz, p->csz));
         ALLOC(p->part, p->part_count);
         ALLOC(p->part2, p->part_count);
     }

@@ -3,6 +3,9 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
+
+#include <algorithm>
+
 #include "gke_common.cuh"
 
 namespace gke {
@@ -63,6 +66,42 @@ __host__ __device__ __forceinline__ int nth_bit(unsigned m, int n)
         if ((m >> i) & 1u) { if (n == 0) return i; --n; }
     return -1;
 }
+// Transform tile parameters for a grid and a complex size (bytes): each CTA
+// keeps its ping-pong buffers and twiddles within 64 KB, so three CTAs fit
+// on an SM.  The plan and the allocation-free entry point both use these.
+struct Tiles { int cw_ci, rz_rp, cw_cf, yb_cf, cw_tc, rz_tr; };
+inline Tiles pick_tiles(int nx, int nz, size_t csz)
+{
+    Tiles t;
+    const size_t lim = 64 * 1024;
+    auto fits = [&](size_t elems) { return elems * csz <= lim; };
+    t.cw_ci = 16; while (t.cw_ci > 1 && !fits((size_t)(1 + 2 * t.cw_ci) * nz)) t.cw_ci /= 2;
+    t.rz_rp = 8;  while (t.rz_rp > 1 && !fits((size_t)(1 + 8 * t.rz_rp) * nx)) t.rz_rp /= 2;
+    t.cw_cf = 4; t.yb_cf = 8;
+    while (t.cw_cf * t.yb_cf > 1 && !fits((size_t)(1 + 2 * t.cw_cf * t.yb_cf) * nz)) {
+        if (t.cw_cf > 1) t.cw_cf /= 2; else t.yb_cf /= 2;
+    }
+    t.cw_tc = 16; while (t.cw_tc > 1 && !fits((size_t)(1 + 2 * t.cw_tc) * nz)) t.cw_tc /= 2;
+    t.rz_tr = 8;  while (t.rz_tr > 1 && !fits((size_t)(1 + 8 * t.rz_tr) * nx)) t.rz_tr /= 2;
+    return t;
+}
+// wavenumbers per CTA of the dissipation sums, and the doubles of the
+// partial-sum buffer of the products stage (row sums of the row passes,
+// then the dissipation chunks)
+constexpr int EPS_KCHUNK = 16;
+inline size_t part_count(int nz, int ny, int Nk, const Tiles& t)
+{
+    const size_t rows = (size_t)6 * ny * std::max((nz + t.rz_rp - 1) / t.rz_rp, (nz + 3) / 4);
+    const size_t eps = (size_t)ny * ((Nk + EPS_KCHUNK - 1) / EPS_KCHUNK);
+    return std::max(rows, eps);
+}
+// transform lengths of the Stockham kernels: 2^a or 3 * 2^a
+inline bool fft_len_ok(int n)
+{
+    auto pow2 = [](int m) { return m > 0 && (m & (m - 1)) == 0; };
+    return pow2(n) || (n % 3 == 0 && pow2(n / 3));
+}
+
 int combine_kc(bool fp32);
 bool combine_kc_ok(bool fp32, int kc);
 

@@ -2,25 +2,27 @@
 // without any device allocation.
 //
 // Some callers cannot call cudaMalloc: code that runs inside a memory pool or
-// an allocator it must not re-enter, a host runtime that forbids device
-// allocation after start-up, or a pipeline already captured around fixed
-// addresses.  For them this entry point takes its workspaces from one
-// file-scope device array of GKE_NOALLOC_SCRATCH_BYTES (32 MiB) instead of
-// a plan.  Every GPU that loads the library holds that array until the
-// process exits.  The array's host-side name is only a stand-in: the device
-// address comes from cudaGetSymbolAddress, once per device, on the device's
-// first call (which also sets the kernels' shared-memory limits and
-// constants), so that first call should come before any stream capture.
+// an allocator it must not re-enter, or a host runtime that forbids device
+// allocation after start-up.  For them this entry point takes its workspaces
+// from one file-scope device array of GKE_NOALLOC_SCRATCH_BYTES (32 MiB)
+// instead of a plan.  Every GPU that loads the library holds that array
+// until the process exits.  The array's host-side name is only a stand-in:
+// the device address comes from cudaGetSymbolAddress, once per device, on
+// the device's first call (which also sets the kernels' shared-memory limits
+// and constants), so that first call should come before any stream capture.
 //
 // Every call uses the same array: calls that overlap on the GPU (on two
 // streams, or from two threads) race, and each call re-initialises the parts
 // that must start at zero.  Nothing here is allocated: no cudaMalloc,
-// cudaFree or allocating library routine is called.
+// cudaFree or allocating library routine is called, and the small host
+// tables (twiddles, finite-difference weights) live in fixed-size stack
+// buffers; the pair table is built on the device.  Each call uploads the
+// tables with one copy per table and synchronises the stream before it
+// returns.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
-#include <string>
 
 #include "../../include/gke.h"
 #include "gke_common.cuh"
@@ -34,8 +36,9 @@ namespace {
 
 constexpr int MAX_DEVICES = 64;
 unsigned char* g_scratch_dev[MAX_DEVICES] = {nullptr};   // device address of the array, per device
-// status only: this entry point keeps no message (its callers read the code)
-gke_status fail(gke_status s, const std::string&) { return s; }
+// status only: this entry point keeps no message (its callers read the code),
+// so the texts below are documentation and nothing is formatted
+gke_status fail(gke_status s, const char*) { return s; }
 
 // one-time set-up on the current device: array address, kernel attributes, constants
 gke_status setup_device(int dev, cudaStream_t st)
@@ -43,15 +46,15 @@ gke_status setup_device(int dev, cudaStream_t st)
     if (g_scratch_dev[dev]) return GKE_OK;
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return fail(GKE_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    if (e != cudaSuccess) return fail(GKE_ERR_CUDA, "cudaGetSymbolAddress failed");
     int lim = 0;
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if ((e = products_set_attrs(lim)) != cudaSuccess || (e = terms_set_attrs(lim)) != cudaSuccess ||
         (e = combine_set_attrs()) != cudaSuccess)
-        return fail(GKE_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+        return fail(GKE_ERR_CUDA, "kernel attributes");
     upload_jobs(st);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return fail(GKE_ERR_CUDA, std::string("set-up: ") + cudaGetErrorString(e));
+        return fail(GKE_ERR_CUDA, "set-up");
     g_scratch_dev[dev] = (unsigned char*)ptr;
     return GKE_OK;
 }
@@ -75,6 +78,19 @@ __global__ void k_div(const double* __restrict__ s, double c, int n, double* __r
     if (i < n) out[i] = s[i] / c;
 }
 
+// pair_i[2 q], pair_i[2 q + 1] = (i1, i2) of the row-major triangle pair q
+__global__ void k_pair_table(int ny, int* __restrict__ pair_i)
+{
+    const int i1 = blockIdx.x;
+    const long long q0 = pair_index(i1, i1, ny);
+    for (int i2 = i1 + threadIdx.x; i2 < ny; i2 += blockDim.x) {
+        pair_i[2 * (q0 + i2 - i1)] = i1;
+        pair_i[2 * (q0 + i2 - i1) + 1] = i2;
+    }
+}
+
+constexpr int MAX_N = 1024;        // largest nx, nz, ny (the plan's limits)
+
 bool is_device(const void* p)
 {
     cudaPointerAttributes a;
@@ -95,9 +111,10 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     for (int i = 0; i < 4; ++i)
         if (d.under_x[i] || d.under_z[i])
             return fail(GKE_ERR_UNSUPPORTED, "gke_compute_noalloc writes full-resolution separations only");
-    if (d.nx < 8 || d.nz < 8 || d.nx > 1024 || d.nz > 1024 || (d.nx & (d.nx - 1)) || (d.nz & (d.nz - 1)) ||
-        d.ny < 5 || d.ny > 1024 || nsnap < 1)
-        return fail(GKE_ERR_ARG, "sizes out of range (nx, nz powers of two in [8, 1024], 5 <= ny <= 1024, nsnap >= 1)");
+    if (d.nx < 8 || d.nz < 8 || d.nx > MAX_N || d.nz > MAX_N || d.ny < 5 || d.ny > MAX_N || nsnap < 1)
+        return fail(GKE_ERR_ARG, "sizes out of range (8 <= nx, nz <= 1024, 5 <= ny <= 1024, nsnap >= 1)");
+    if (!fft_len_ok(d.nx) || !fft_len_ok(d.nz))
+        return fail(GKE_ERR_UNSUPPORTED, "nx and nz must be 2^a or 3 * 2^a (transform lengths of the library)");
     if (!(d.Lx > 0) || !(d.Lz > 0) || !(d.nu > 0)) return fail(GKE_ERR_ARG, "Lx, Lz, nu must be > 0");
     if (d.term_mask & ~GKE_ALL_TERMS) return fail(GKE_ERR_ARG, "term_mask has bits above GKE_NTERM");
     const unsigned tset = term_set(d.term_mask);
@@ -113,14 +130,8 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
 
     const int nx = d.nx, nz = d.nz, ny = d.ny, nxh = nx / 2 + 1, Nk = nz * nxh, ns = nsnap;
     const long long npair = (long long)ny * (ny + 1) / 2;
-    // transform tiles: ping-pong buffers and twiddles within 64 KB (complex128)
-    auto fit = [](int start, int per, int fixed) { int c = start; while (c > 1 && (size_t)(fixed + per * c) * 16 > 65536) c /= 2; return c; };
-    const int cw_ci = fit(16, 2 * nz, nz), rz_rp = fit(8, 8 * nx, nx), cw_tc = fit(16, 2 * nz, nz), rz_tr = fit(8, 8 * nx, nx);
-    int cw_cf = 4, yb_cf = 8;
-    while (cw_cf * yb_cf > 1 && (size_t)(1 + 2 * cw_cf * yb_cf) * nz * 16 > 65536) { if (cw_cf > 1) cw_cf /= 2; else yb_cf /= 2; }
-    const int eps_kchunk = 64;
-    const int nrb = (nz + rz_rp - 1) / rz_rp > (nz + 3) / 4 ? (nz + rz_rp - 1) / rz_rp : (nz + 3) / 4;
-    const int neb = (Nk + eps_kchunk - 1) / eps_kchunk;
+    // transform tiles and partial sums as the plan path sizes them (complex128)
+    const Tiles tl = pick_tiles(nx, nz, sizeof(zd));
 
     Carve c{g_scratch_dev[dev], 0, (size_t)GKE_NOALLOC_SCRATCH_BYTES};
     zd* Xop = c.take<zd>((size_t)NFIELD * Nk * ns * ny);
@@ -139,39 +150,27 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     int* fdl0 = c.take<int>(ny);
     int* pair_i = c.take<int>(2 * npair);
     int* nonfinite = c.take<int>(1);
-    double* part = c.take<double>((size_t)(6 * ny * nrb > ny * neb ? 6 * ny * nrb : ny * neb));
+    double* part = c.take<double>(part_count(nz, ny, Nk, tl));
     if (!c.ok())
-        return fail(GKE_ERR_UNSUPPORTED, "problem needs " + std::to_string(c.off) + " bytes of workspace, more than the " +
-                                             std::to_string((size_t)GKE_NOALLOC_SCRATCH_BYTES) +
-                                             " of gke_compute_noalloc; use a plan (gke_plan) instead");
+        return fail(GKE_ERR_UNSUPPORTED, "workspace larger than GKE_NOALLOC_SCRATCH_BYTES: use a plan (gke_plan)");
 
-    // host tables (libm twiddles, FD weights, pair list), copied in small pieces
+    // host tables (libm twiddles, FD weights) in fixed-size stack buffers, one
+    // copy per table and one synchronisation before the buffers go out of
+    // scope; the pair list is built on the device
     cudaError_t e;
-#define TRY(call) do { if ((e = (call)) != cudaSuccess) return fail(GKE_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e)); } while (0)
-    for (int m = 0; m < nx; ++m) {
-        zd t; t.x = std::cos(2.0 * M_PI * m / nx); t.y = -std::sin(2.0 * M_PI * m / nx);
-        TRY(cudaMemcpyAsync(twx + m, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-        TRY(cudaStreamSynchronize(st));
-    }
-    for (int m = 0; m < nz; ++m) {
-        zd t; t.x = std::cos(2.0 * M_PI * m / nz); t.y = -std::sin(2.0 * M_PI * m / nz);
-        TRY(cudaMemcpyAsync(twz + m, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-        TRY(cudaStreamSynchronize(st));
-    }
-    for (int j = 0; j < ny; ++j) {
-        double w[5];
-        int l0 = gke_fd_weights(d.y, ny, j, w);
-        TRY(cudaMemcpyAsync(fdw + 5 * j, w, sizeof(w), cudaMemcpyHostToDevice, st));
-        TRY(cudaMemcpyAsync(fdl0 + j, &l0, sizeof(int), cudaMemcpyHostToDevice, st));
-        TRY(cudaStreamSynchronize(st));
-    }
-    for (int i1 = 0, q = 0; i1 < ny; ++i1) {
-        for (int i2 = i1; i2 < ny; ++i2, ++q) {
-            int ab[2] = {i1, i2};
-            TRY(cudaMemcpyAsync(pair_i + 2 * q, ab, sizeof(ab), cudaMemcpyHostToDevice, st));
-        }
-        TRY(cudaStreamSynchronize(st));
-    }
+#define TRY(call) do { if ((e = (call)) != cudaSuccess) return fail(GKE_ERR_CUDA, #call); } while (0)
+    zd h_twx[MAX_N], h_twz[MAX_N];
+    double h_fdw[5 * MAX_N];
+    int h_fdl0[MAX_N];
+    for (int m = 0; m < nx; ++m) { h_twx[m].x = std::cos(2.0 * M_PI * m / nx); h_twx[m].y = -std::sin(2.0 * M_PI * m / nx); }
+    for (int m = 0; m < nz; ++m) { h_twz[m].x = std::cos(2.0 * M_PI * m / nz); h_twz[m].y = -std::sin(2.0 * M_PI * m / nz); }
+    for (int j = 0; j < ny; ++j) h_fdl0[j] = gke_fd_weights(d.y, ny, j, h_fdw + 5 * j);
+    TRY(cudaMemcpyAsync(twx, h_twx, nx * sizeof(zd), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(twz, h_twz, nz * sizeof(zd), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(fdw, h_fdw, 5 * ny * sizeof(double), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(fdl0, h_fdl0, ny * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_pair_table<<<ny, 128, 0, st>>>(ny, pair_i);
+    TRY(cudaStreamSynchronize(st));
     // the array keeps the previous call's contents: clear the sums
     TRY(cudaMemsetAsync(mean_sum, 0, 4 * ny * sizeof(double), st));
     TRY(cudaMemsetAsync(stats, 0, NSTAT * ny * sizeof(double), st));
@@ -188,7 +187,7 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
     a.fields = f; a.ns = ns; a.ny = ny; a.nz = nz; a.nx = nx; a.nxh = nxh; a.Nk = Nk;
     a.mean = mean; a.Xop = Xop; a.G = G; a.H = H; a.tw_x = twx; a.tw_z = twz;
     a.part = part; a.stats = stats; a.nonfinite = nonfinite;
-    a.cw_ci = cw_ci; a.rz_rp = rz_rp; a.cw_cf = cw_cf; a.yb_cf = yb_cf; a.eps_kchunk = eps_kchunk;
+    a.cw_ci = tl.cw_ci; a.rz_rp = tl.rz_rp; a.cw_cf = tl.cw_cf; a.yb_cf = tl.yb_cf; a.eps_kchunk = EPS_KCHUNK;
     a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = fdw; a.fdl0 = fdl0; a.st = st;
     products_launch<double>(a);
     correlate_launch(false, Xop, ns, ny, Nk, 0, Nk, raw, job_set(tset), st);
@@ -198,7 +197,7 @@ extern "C" gke_status gke_compute_noalloc(const gke_desc* desc, const void* fiel
                                                   fdl0, ny, prof);
     TermArgs t;
     t.fp32 = false; t.comb64 = true; t.comb = comb; t.W = W; t.pair_i = pair_i; t.npair = npair; t.pair_chunk = npair;
-    t.ny = ny; t.nz = nz; t.nx = nx; t.cw = cw_tc; t.rz = rz_tr; t.inv_count = 1.0 / ns; t.prof = prof;
+    t.ny = ny; t.nz = nz; t.nx = nx; t.cw = tl.cw_tc; t.rz = tl.rz_tr; t.inv_count = 1.0 / ns; t.prof = prof;
     t.tw_x = twx; t.tw_z = twz; t.terms = terms; t.spec = nullptr; t.sep = full_sep(nz, nx); t.st = st;
     t.tmask = tset;
     terms_launch(t);

@@ -26,7 +26,7 @@ def test_noalloc_matches_plan_twice():
     import paper_1910_06409_gb300._native as N
 
     outs = []
-    for wid, shape in ((31, (16, 16, 17, 2)), (32, (16, 8, 13, 3))):
+    for wid, shape in ((31, (16, 16, 17, 2)), (32, (16, 8, 13, 3)), (34, (24, 12, 9, 2))):
         nx, nz, ny, ns = shape
         wl = S.small(nx, nz, ny, ns, wid=wid)
         y = S.cgl_grid(ny)
