@@ -319,6 +319,7 @@ static_assert(SMP_TOTAL <= 232448, "shared memory of one CTA");
 
 struct TcPipeBars {
     uint64_t full[NST], empty[NST], acc_full[2], acc_empty[2], drain;
+    uint64_t bfull, bempty;                             // resident B blocks (MODE 2)
     uint32_t tmem;
     int abort;
     int eok;                                            // epilogue: the accumulator is ready
@@ -335,26 +336,55 @@ __device__ __forceinline__ void bar_sync64(int id) { asm volatile("bar.sync %0, 
 __device__ __forceinline__ int tri_slot(int b, int c) { return b * (b + 1) / 2 + c; }
 __device__ __forceinline__ int swz(int r, int c) { return r * 32 + ((c + r) & 31); }
 
-template <bool PLANES>
-__device__ __forceinline__ void item_of(const TcArgs& a, int njt, long long it, int& k, int& job, int& mt, int& nt)
+// Work of one launch, item by item (item it = blockIdx.x, blockIdx.x +
+// gridDim.x, ...).  MODE 0: raw contractions, item = (wavenumber, contraction,
+// tile); MODE 1: planes, item = (wavenumber, plane); MODE 2: planes, item =
+// one wavenumber with all its planes in sequence ("units"), the B blocks of u,
+// v, w (one snapshot group) resident in shared memory for the whole item and
+// only the A blocks streamed through the stage ring.
+template <int MODE> struct Units {
+    int k, n, mt, nt, j0;
+    unsigned planes;
+    // contraction (MODE 0) or plane of unit un
+    __device__ __forceinline__ int job(int un) const { return MODE == 2 ? nth_bit(planes, un) : j0; }
+};
+template <int MODE>
+__device__ __forceinline__ Units<MODE> item_units(const TcArgs& a, int njt, long long it)
 {
-    if (PLANES) {
-        k = (int)(it / a.npl);
-        job = nth_bit(a.planes, (int)(it % a.npl));
-        mt = nt = 0;
+    Units<MODE> u;
+    u.planes = a.planes;
+    if (MODE == 2) {
+        u.k = (int)it;
+        u.n = a.npl;
+        u.j0 = 0;
+        u.mt = u.nt = 0;
+    } else if (MODE == 1) {
+        u.k = (int)(it / a.npl);
+        u.n = 1;
+        u.j0 = nth_bit(a.planes, (int)(it % a.npl));
+        u.mt = u.nt = 0;
     } else {
-        k = (int)(it / njt);
-        decode_tile((int)(it % njt), a.MT, a.sel, job, mt, nt);
+        u.k = (int)(it / njt);
+        u.n = 1;
+        decode_tile((int)(it % njt), a.MT, a.sel, u.j0, u.mt, u.nt);
     }
+    return u;
 }
 
-template <bool PLANES>
-__device__ __forceinline__ const TcJob& job_desc(int job) { return PLANES ? c_tcplanes[job] : c_tcjobs[job]; }
+template <int MODE>
+__device__ __forceinline__ const TcJob& job_desc(int job) { return MODE ? c_tcplanes[job] : c_tcjobs[job]; }
 
-template <bool PLANES>
+// shared-memory offsets of stage st: its A block and (MODE 0, 1) its B block;
+// MODE 2 keeps the three B blocks of the item at offset 0
+constexpr int SMP_BRES = 3 * SM_B;                      // resident B blocks (MODE 2)
+static_assert(SMP_BRES + NST * SM_A <= NST * SMP_STAGE, "resident B and the A ring fit the stage area");
+template <int MODE> __device__ __forceinline__ int stage_a(int st) { return MODE == 2 ? SMP_BRES + st * SM_A : st * SMP_STAGE; }
+
+template <int MODE>
 __global__ void __launch_bounds__(TCP_THREADS, 1)
 k_corr_tc_pipe(const TcArgs a)
 {
+    constexpr bool PLANES = MODE != 0;
     extern __shared__ __align__(1024) uint8_t smem[];
     TcPipeBars* bars = (TcPipeBars*)(smem + SMP_BAR);
     volatile int* abort = &bars->abort;
@@ -371,6 +401,8 @@ k_corr_tc_pipe(const TcArgs a)
             mbar_init(&bars->acc_empty[b], EPI_WARPS);
         }
         mbar_init(&bars->drain, 1);
+        mbar_init(&bars->bfull, 1);
+        mbar_init(&bars->bempty, 1);
         bars->abort = (*(volatile int*)a.err != 0) ? 1 : 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -393,92 +425,121 @@ k_corr_tc_pipe(const TcArgs a)
     if (warp == 0) {
         if (lane == 0) {
             int st = 0;
-            uint32_t ph = 0;
-            int issued = 0;
+            uint32_t ph = 0, bph = 0;
+            int issued = 0, b_issued = 0;
             for (long long it = blockIdx.x; it < a.nitems && !*abort; it += gridDim.x) {
-                int k, job, mt, nt;
-                item_of<PLANES>(a, njt, it, k, job, mt, nt);
-                const TcJob& jd = job_desc<PLANES>(job);
-                for (int pass = 0; pass < 2; ++pass)
-                    for (int t = 0; t < jd.nterm; ++t)
-                        for (int g = 0; g < G; ++g) {
-                            if (!mbar_wait_ab(&bars->empty[st], ph ^ 1, abort)) { fail(); goto producer_done; }
-                            const uint32_t ba = pass ? 2 * A_BLK * 2 : SM_A, bb = pass ? B_BLK * 2 : SM_B;
-                            uint8_t* sa = smem + st * SMP_STAGE;
-                            mbar_expect_tx(&bars->full[st], ba + bb);
-                            bulk_g2s(sa, a.Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + mt) *
-                                                     (long long)A_STAGE, ba, &bars->full[st]);
-                            bulk_g2s(sa + SM_A, a.Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + nt) *
-                                                            (long long)B_STAGE, bb, &bars->full[st]);
-                            ++issued;
-                            if (++st == NST) { st = 0; ph ^= 1; }
-                        }
+                const Units<MODE> u = item_units<MODE>(a, njt, it);
+                const int k = u.k;
+                // MODE 2: the item's B blocks replace the previous item's once
+                // its MMAs are done; the first NST A stages of the item go
+                // out before that wait, so the ring does not drain between items
+                bool b_done = MODE != 2;
+                int sidx = 0;
+                auto load_b = [&]() -> bool {
+                    if (!mbar_wait_ab(&bars->bempty, bph ^ 1, abort)) return false;
+                    mbar_expect_tx(&bars->bfull, SMP_BRES);
+                    for (int fb = 0; fb < 3; ++fb)
+                        bulk_g2s(smem + fb * SM_B, a.Bop + ((long long)k * 3 + fb) * G * MT * (long long)B_STAGE, SM_B,
+                                 &bars->bfull);
+                    ++b_issued;
+                    bph ^= 1;
+                    b_done = true;
+                    return true;
+                };
+                for (int un = 0; un < u.n; ++un) {
+                    const TcJob& jd = job_desc<MODE>(u.job(un));
+                    for (int pass = 0; pass < 2; ++pass)
+                        for (int t = 0; t < jd.nterm; ++t)
+                            for (int g = 0; g < G; ++g) {
+                                if (!mbar_wait_ab(&bars->empty[st], ph ^ 1, abort)) { fail(); goto producer_done; }
+                                const uint32_t ba = pass ? 2 * A_BLK * 2 : SM_A, bb = pass ? B_BLK * 2 : SM_B;
+                                uint8_t* sa = smem + stage_a<MODE>(st);
+                                mbar_expect_tx(&bars->full[st], MODE == 2 ? ba : ba + bb);
+                                bulk_g2s(sa, a.Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + u.mt) *
+                                                         (long long)A_STAGE, ba, &bars->full[st]);
+                                if (MODE != 2)
+                                    bulk_g2s(sa + SM_A, a.Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + u.nt) *
+                                                                    (long long)B_STAGE, bb, &bars->full[st]);
+                                ++issued;
+                                if (++st == NST) { st = 0; ph ^= 1; }
+                                if (!b_done && ++sidx == NST && !load_b()) { fail(); goto producer_done; }
+                            }
+                }
+                if (!b_done && !load_b()) { fail(); goto producer_done; }
             }
         producer_done:
             // no copy may be in flight when the CTA exits: wait for the last
-            // phase issued on every stage (bounded; earlier phases completed
-            // before the stage was reused)
+            // phase issued on every stage and on the resident B blocks
+            // (bounded; earlier phases completed before the buffer was reused)
             for (int q = 0; q < NST && q < issued; ++q) {
                 const int last = issued - 1 - q;                 // issue index of a recent copy
                 mbar_wait(&bars->full[last % NST], (uint32_t)((last / NST) & 1));
             }
+            if (b_issued) mbar_wait(&bars->bfull, (uint32_t)((b_issued - 1) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {
             int st = 0, acc = 0;
-            uint32_t ph = 0, aph = 0;
-            for (long long it = blockIdx.x; it < a.nitems && !*abort; it += gridDim.x) {
-                int k, job, mt, nt;
-                item_of<PLANES>(a, njt, it, k, job, mt, nt);
-                const TcJob& jd = job_desc<PLANES>(job);
-                if (!mbar_wait_ab(&bars->acc_empty[acc], aph ^ 1, abort)) { fail(); break; }
-                tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(acc * 256);
-                uint32_t accum = 0;
-                bool ok = true;
-                for (int pass = 0; pass < 2 && ok; ++pass)
-                    for (int t = 0; t < jd.nterm && ok; ++t) {
-                        // a term of sign -1: the negate-A bit (13) of the instruction descriptor
-                        const uint32_t neg = ((jd.neg >> t) & 1u) ? NEG_A : 0u;
-                        const uint32_t id = IDESC | neg, id128 = IDESC_N128 | neg;
-                        for (int g = 0; g < G; ++g) {
-                            if (!mbar_wait_ab(&bars->full[st], ph, abort)) { fail(); ok = false; break; }
-                            tc_fence_after();
-                            const uint8_t* sa = smem + st * SMP_STAGE;
-                            const uint8_t* sb = sa + SM_A;
-                            const int npr = pass ? 1 : 5;
-                            for (int pr = 0; pr < npr; ++pr) {
-                                const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
-                                const uint64_t a_re = sdesc(sa + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
-                                const uint64_t a_im = sdesc(sa + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
-                                const uint64_t b_ri = sdesc(sb + j * B_BLK * 2, B_LBO, CM_SBO);
-                                const uint64_t b_i = sdesc(sb + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
-                                mma_bf16(d, a_re, b_ri, id, accum);              // Re += ar br, Im += ar bi
-                                accum = 1;
-                                mma_bf16(d, a_im, b_i, id128, 1);                // Re += ai bi
-                                mma_bf16(d + TM, a_im, b_ri, id128 ^ NEG_A, 1);  // Im -= ai br
+            uint32_t ph = 0, aph = 0, bph = 0;
+            bool ok = true;
+            for (long long it = blockIdx.x; it < a.nitems && !*abort && ok; it += gridDim.x) {
+                const Units<MODE> u = item_units<MODE>(a, njt, it);
+                if (MODE == 2) {
+                    if (!mbar_wait_ab(&bars->bfull, bph, abort)) { fail(); break; }
+                    bph ^= 1;
+                }
+                for (int un = 0; un < u.n && ok; ++un) {
+                    const TcJob& jd = job_desc<MODE>(u.job(un));
+                    if (!mbar_wait_ab(&bars->acc_empty[acc], aph ^ 1, abort)) { fail(); ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t d = tmem + (uint32_t)(acc * 256);
+                    uint32_t accum = 0;
+                    for (int pass = 0; pass < 2 && ok; ++pass)
+                        for (int t = 0; t < jd.nterm && ok; ++t) {
+                            // a term of sign -1: the negate-A bit (13) of the instruction descriptor
+                            const uint32_t neg = ((jd.neg >> t) & 1u) ? NEG_A : 0u;
+                            const uint32_t id = IDESC | neg, id128 = IDESC_N128 | neg;
+                            for (int g = 0; g < G; ++g) {
+                                if (!mbar_wait_ab(&bars->full[st], ph, abort)) { fail(); ok = false; break; }
+                                tc_fence_after();
+                                const uint8_t* sa = smem + stage_a<MODE>(st);
+                                const uint8_t* sb = MODE == 2 ? smem + jd.fb[t] * SM_B : sa + SM_A;
+                                const int npr = pass ? 1 : 5;
+                                for (int pr = 0; pr < npr; ++pr) {
+                                    const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
+                                    const uint64_t a_re = sdesc(sa + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
+                                    const uint64_t a_im = sdesc(sa + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
+                                    const uint64_t b_ri = sdesc(sb + j * B_BLK * 2, B_LBO, CM_SBO);
+                                    const uint64_t b_i = sdesc(sb + j * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
+                                    mma_bf16(d, a_re, b_ri, id, accum);              // Re += ar br, Im += ar bi
+                                    accum = 1;
+                                    mma_bf16(d, a_im, b_i, id128, 1);                // Re += ai bi
+                                    mma_bf16(d + TM, a_im, b_ri, id128 ^ NEG_A, 1);  // Im -= ai br
+                                }
+                                mma_commit(&bars->empty[st]);
+                                if (++st == NST) { st = 0; ph ^= 1; }
                             }
-                            mma_commit(&bars->empty[st]);
-                            if (++st == NST) { st = 0; ph ^= 1; }
                         }
-                    }
-                if (!ok) break;
-                mma_commit(&bars->acc_full[acc]);
-                if (++acc == 2) { acc = 0; aph ^= 1; }
+                    if (!ok) break;
+                    mma_commit(&bars->acc_full[acc]);
+                    if (++acc == 2) { acc = 0; aph ^= 1; }
+                }
+                // the resident B blocks are free once this item's MMAs complete
+                if (MODE == 2 && ok) mma_commit(&bars->bempty);
             }
             // every MMA of this thread has completed before TMEM is released
             mma_commit(&bars->drain);
             mbar_wait(&bars->drain, 0);
         }
-    } else if (!PLANES) {
+    } else if (MODE == 0) {
         const int q = warp & 3;                       // TMEM lane quarter of this warp
         zf* xp = (zf*)(smem + SMP_EPI) + (warp - 2) * 32 * 33;
         const int YB = (a.ny + 7) / 8;
         int acc = 0;
         uint32_t aph = 0;
         for (long long it = blockIdx.x; it < a.nitems && !*abort; it += gridDim.x) {
-            int k, job, mt, nt;
-            item_of<PLANES>(a, njt, it, k, job, mt, nt);
+            const Units<MODE> u = item_units<MODE>(a, njt, it);
+            const int k = u.k, job = u.job(0), mt = u.mt, nt = u.nt;
             if (!mbar_wait_ab(&bars->acc_full[acc], aph, abort)) { fail(); break; }
             tc_fence_after();
             const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
@@ -525,9 +586,12 @@ k_corr_tc_pipe(const TcArgs a)
         const int rb = (int)(pair_index(y, y, ny) - y);
         int acc = 0;
         uint32_t aph = 0;
-        for (long long it = blockIdx.x; it < a.nitems; it += gridDim.x) {
-            int k, job, mt, nt;
-            item_of<PLANES>(a, njt, it, k, job, mt, nt);
+        bool go = true;
+        for (long long it = blockIdx.x; it < a.nitems && go; it += gridDim.x) {
+            const Units<MODE> u = item_units<MODE>(a, njt, it);
+            const int k = u.k;
+            for (int un = 0; un < u.n; ++un) {
+            const int job = u.job(un);
             // one thread waits, so the four warps take the same decision; the
             // barrier also orders this item's block writes after every warp's
             // reads of the previous item
@@ -535,7 +599,7 @@ k_corr_tc_pipe(const TcArgs a)
             epi_sync();
             const bool ok = *eok != 0;
             epi_sync();
-            if (!ok) { if (et == 0) fail(); break; }
+            if (!ok) { if (et == 0) fail(); go = false; break; }
             tc_fence_after();
             const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
             zf* outp = a.out + ((long long)job * a.Kc + k) * a.npp;
@@ -608,6 +672,7 @@ k_corr_tc_pipe(const TcArgs a)
             __syncwarp();
             if (lane == 0) mbar_arrive(&bars->acc_empty[acc]);
             if (++acc == 2) { acc = 0; aph ^= 1; }
+            }
         }
     }
     tc_fence_before();
@@ -798,12 +863,9 @@ cudaError_t split_setup(cudaStream_t st)
     static_assert(F_U == 0 && F_V == 1 && F_W == 2, "B operands are u, v, w in field order");
     cudaError_t e = cudaMemcpyToSymbolAsync(c_tcjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tcplanes, hp, sizeof(hp), 0, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void*)k_corr_tc_pipe<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMP_TOTAL);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute((const void*)k_corr_tc_pipe<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 SMP_TOTAL);
+    const void* ks[] = {(const void*)k_corr_tc_pipe<0>, (const void*)k_corr_tc_pipe<1>, (const void*)k_corr_tc_pipe<2>};
+    for (const void* k : ks)
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMP_TOTAL);
     return e;
 }
 
@@ -852,7 +914,7 @@ gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, 
     a.sel = sel; a.raw = raw; a.err = w.err;
     a.nitems = (long long)Kc * sel_tiles(sel, a.MT);
     const unsigned grid = (unsigned)std::min<long long>(a.nitems, sm_count());
-    k_corr_tc_pipe<false><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
+    k_corr_tc_pipe<0><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
     *launches = 3;
     if (a.cov < ny) {
         k_corr_edge<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, a.cov, jobs, raw);
@@ -879,9 +941,15 @@ gke_status split_correlate_planes(SplitWork& w, const zf* Xop, int ns, int ny, i
     a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
     a.planes = planes; a.npl = __builtin_popcount(planes); a.npp = npp; a.out = out; a.prof = prof;
     a.err = w.err;
-    a.nitems = (long long)Kc * a.npl;
+    // one snapshot group: one item per wavenumber with the B blocks resident
+    // (each B block is read once per wavenumber); else one item per plane
+    const bool resident = a.G == 1;
+    a.nitems = resident ? (long long)Kc : (long long)Kc * a.npl;
     const unsigned grid = (unsigned)std::min<long long>(a.nitems, sm_count());
-    k_corr_tc_pipe<true><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
+    if (resident)
+        k_corr_tc_pipe<2><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
+    else
+        k_corr_tc_pipe<1><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
     *launches = 3;
     if (a.cov < ny) {
         k_corr_edge_planes<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, a.cov, planes, npp, prof, out);
