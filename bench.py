@@ -15,6 +15,10 @@ ny = 129 Chebyshev points, 16 snapshots), plain FP64 path.
 
 --impl reference times the CPU oracle (direct averages, C/OpenMP) on the host
 cores on a bounded sample of the same workload.
+
+--passes P runs P untimed passes of the workload at --precision and prints the
+number of kernel launches per pass, nothing else: the program that ncu launch
+lists and single-kernel captures are taken on.
 """
 from __future__ import annotations
 
@@ -429,6 +433,26 @@ def run_group(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_passes(args):
+    """P untimed passes of one plan (no tuning runs, no FP64 run beside it)."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    wl = S.WORKLOADS[args.workload]
+    prec = {"f64": N.GKE_PREC_F64, "bf16x3": N.GKE_PREC_BF16X3, "f32": N.GKE_PREC_F32}[args.precision]
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), wl.nsnap, prec,
+                      stream=torch.cuda.current_stream().cuda_stream)
+    f_dev = torch.from_numpy(S.coefficients(wl)).cuda()
+    tdt = torch.float64 if args.precision == "f64" else torch.float32
+    terms = torch.empty((N.GKE_NTERM, N.gke_npair(plan), wl.nz, wl.nx), dtype=tdt, device="cuda")
+    for p in range(args.passes):
+        l0 = N.gke_launch_count(plan)
+        N.gke_compute(plan, f_dev, wl.nsnap, terms)
+        torch.cuda.synchronize()
+        print(f"pass {p}: {N.gke_launch_count(plan) - l0} launches", flush=True)
+    N.gke_destroy(plan)
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1910_06409_gb300._native as N
@@ -672,7 +696,12 @@ def main():
     ap.add_argument("--stride", type=int, default=1, help="uniform undersampling of r_x, r_z (streaming mode)")
     ap.add_argument("--batch", type=int, default=0, help="snapshots per accumulate call (streaming mode)")
     ap.add_argument("--nsnap", type=int, default=0, help="first n snapshots of the workload only (streaming mode)")
+    ap.add_argument("--passes", type=int, default=0,
+                    help="profiling target: run this many untimed passes, print launches per pass, exit")
     args = ap.parse_args()
+    if args.passes > 0:
+        run_passes(args)
+        return
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
