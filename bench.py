@@ -67,12 +67,14 @@ def correlator_cmac(wl, ns):
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per pass of each
-# stage's kernels at 256 x 256 x 129 x 16, from the ncu launch lists in
-# profiles/launches_{f64,split_bf16x3}_retau200_256x256x129_s16.md (GB); a
-# stage missing here reports null (not captured since its kernels changed).
+# stage's kernels at 256 x 256 x 129 x 16 (GB): ncu captures of the small
+# cases profile_256x256x17_s16 and profile_32x32x129_s16, scaled by pairs,
+# wall-normal planes or wavenumbers to the full size
+# (profiles/dram_small_cases_split_and_f64.md); a stage missing here reports
+# null (not captured since its kernels changed).
 NCU_TRAFFIC_GB = {
-    "f64": {"correlate": 104.4, "combine": 94.8, "terms": 105.1, "stencil": 39.9, "products": 46.4},
-    "bf16x3": {"stencil": 28.8, "products": 27.4},
+    "f64": {"correlate": 96.7, "combine": 93.0, "terms": 104.1, "stencil": 37.9, "products": 33.1},
+    "bf16x3": {"correlate": 36.7, "terms": 59.5, "stencil": 25.0, "products": 22.3},
 }
 
 
@@ -329,13 +331,13 @@ def run_stream(args, world, rank, local):
     tdt = torch.float64 if args.precision == "f64" else torch.float32
     terms = torch.empty((N.GKE_NTERM, npair, len(mz), len(mx)), dtype=tdt, device="cuda")
 
-    def step():
-        N.gke_reset(plan)
+    def step(pl=plan, out=terms):
+        N.gke_reset(pl)
         for b in range(0, ns, B):
-            N.gke_accumulate_mean(plan, f_dev[b:b + B], min(B, ns - b))
+            N.gke_accumulate_mean(pl, f_dev[b:b + B], min(B, ns - b))
         for b in range(0, ns, B):
-            N.gke_accumulate_snapshot(plan, f_dev[b:b + B], min(B, ns - b))
-        N.gke_finalize_terms(plan, terms)
+            N.gke_accumulate_snapshot(pl, f_dev[b:b + B], min(B, ns - b))
+        N.gke_finalize_terms(pl, out)
 
     for _ in range(args.warmup):
         step()
@@ -355,6 +357,22 @@ def run_stream(args, world, rank, local):
     stage_ms = {k: v / args.steps for k, v in N.gke_stage_times(plan).items()}
     N.gke_destroy(plan)
     ms = e0.elapsed_time(e1) / args.steps
+    # accuracy of a reduced-precision run: the same snapshots through an FP64
+    # plan with the same options (untimed), per-term max |x - f64| / max |f64|
+    err = None
+    if args.precision != "f64" and not args.no_f64_check:
+        plan64 = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), B, N.GKE_PREC_F64,
+                            stream=stream.cuda_stream, pair_domain=dom, under_x=st_opt, under_z=st_opt)
+        terms64 = torch.empty(terms.shape, dtype=torch.float64, device="cuda")
+        step(plan64, terms64)
+        torch.cuda.synchronize()
+        N.gke_destroy(plan64)
+        err = {}
+        for t, name in enumerate(TERM_NAMES):
+            scale = float(terms64[t].abs().max())
+            diff = float((terms[t].double() - terms64[t]).abs().max())
+            err[name] = float("%.3g" % (diff / scale if scale > 0 else diff))
+        del terms64
     pk, pk_kind = peaks()
     rl = stage_rooflines(wl, ns, args.precision, {"correlate": stage_ms.get("correlate", 0.0)}, pk, pk_kind)
     cfg = config_of(wl, args.precision)
@@ -363,7 +381,10 @@ def run_stream(args, world, rank, local):
     line = {"metric": METRIC, "value": npair * ns / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16x3/f32", "f32": "f32"}[args.precision],
-            "data": "synthetic", "config": cfg, "stage_ms": stage_ms, "gpu_launches": launches,
+            "data": "synthetic", "config": cfg,
+            "max_rel_err_vs_f64": err, "tolerance": 1e-6 if err is not None else None,
+            "within_tolerance": None if err is None else all(e <= 1e-6 for e in err.values()),
+            "stage_ms": stage_ms, "gpu_launches": launches,
             "clocks": clk.summary(), "e2e": None, "roofline": rl.get("correlate"), "cpu_baseline": None,
             "note": "streaming mode: outputs are output_pairs x separations; value counts output pairs"}
     if rank == 0:
@@ -696,6 +717,8 @@ def main():
     ap.add_argument("--stride", type=int, default=1, help="uniform undersampling of r_x, r_z (streaming mode)")
     ap.add_argument("--batch", type=int, default=0, help="snapshots per accumulate call (streaming mode)")
     ap.add_argument("--nsnap", type=int, default=0, help="first n snapshots of the workload only (streaming mode)")
+    ap.add_argument("--no-f64-check", action="store_true",
+                    help="streaming mode: skip the untimed FP64 run that measures the per-term error")
     ap.add_argument("--passes", type=int, default=0,
                     help="profiling target: run this many untimed passes, print launches per pass, exit")
     args = ap.parse_args()
