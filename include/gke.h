@@ -223,9 +223,13 @@ gke_status gke_reset(gke_plan_t plan);
  * mean_count, snap_count, Lx, Lz, nu } (96 bytes), then float64
  * mean_sum[4][ny], float64 stats[7][ny] and, if have_acc, float64 mean[4][ny]
  * (the frozen mean) and the complex128 spectra: acc_kind 0 = per-pair term
- * spectra [npair][GKE_NTERM][...], acc_kind 1 = the six plane spectra that
- * split-BF16 plans on the full triangle with ny <= 128 or ny = 129 sum
- * [6][(npair + 3) / 4][nz (nx/2 + 1)][4].  Restore and merge need the same
+ * spectra [npair][GKE_NTERM][nz (nx/2 + 1)], acc_kind 1 = the six plane
+ * spectra that split-BF16 plans on the full triangle with ny <= 128 or
+ * ny = 129 sum, [6][nz (nx/2 + 1)][npp], npp = npair rounded up to a multiple
+ * of 4, acc_kind 2 = the coarse term spectra of the chunked mode (uniform
+ * stride, or grids too large for one batch's contractions) for every pair of
+ * the triangle, also with the wedge domain, [npair_tri][GKE_NTERM][nzd]
+ * [nxd/2 + 1].  Restore and merge need the same
  * grid, domain, term set and acc_kind (else GKE_ERR_ARG).  Files of
  * independent jobs can also be added on the host
  * (paper_1910_06409_gb300/merge.py).                                        */

@@ -42,12 +42,17 @@ struct gke_plan_s {
     SepMap sep;
     int* sep_tab = nullptr;
     // uniform undersampling by (sz, sx) done by spectral aliasing: the
-    // contractions run in chunks of R kz rows (Kc wavenumbers), each folded
-    // into the FP64 coarse spectra comb[npair][NTERM][nzd][nxd/2+1]
+    // contractions run in chunks of whole conjugate classes of kz rows (at
+    // most R rows, Kc wavenumbers), each chunk's operands gathered into Xc and
+    // its contractions folded into the FP64 coarse spectra of every triangle
+    // pair, comb[npair_tri][NTERM][nzd][nxd/2+1] (the wedge's mirror average
+    // is formed from them at finalize)
     bool dec = false;
     int nzt = 0, nxt = 0;                     // transform sizes of the terms stage (nzd, nxd when dec)
-    int R = 0, Kc = 0;                        // chunk rows and wavenumbers per chunk
-    void* cchunk = nullptr;                   // one chunk's per-pair spectra (triangle)
+    int R = 0, Kc = 0;                        // chunk rows and wavenumbers (the largest chunk)
+    void* Xc = nullptr;                       // one chunk's gathered operands
+    int* dec_tab = nullptr;                   // per chunk: its kz rows, then its coarse rows
+    std::vector<int> ch_rows, ch_nrows, ch_crs, ch_ncr;   // offsets into dec_tab and counts
     size_t n_acc = 0;                         // elements of the FP64 accumulator comb
     zd *ttw_xd = nullptr, *ttw_zd = nullptr;  // twiddles of the transform sizes
     zf *ttw_xf = nullptr, *ttw_zf = nullptr;
@@ -350,20 +355,17 @@ static gke_status tune_knobs(gke_plan_t p)
     p->timing = false;
     const long long launches = p->launches;
     // combine: one batch's spectra into the first-batch accumulator (plans
-    // that combine raw contractions; plane mode keeps the default)
-    if (p->planes) p->comb_kc = combine_kc(true);
+    // that combine raw contractions per pair; plane mode and the chunked
+    // mode's fused fold keep the default)
+    if (p->planes || p->dec) p->comb_kc = combine_kc(f32);
     else {
         const int cand[3] = {f32 ? 2 : 1, f32 ? 4 : 2, f32 ? 8 : 4};
         float best = 0.f;
         for (int kc : cand) {
             const float ms = time_twice(p, [&] {
-                if (p->dec)
-                    combine_launch(f32, !f32, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, 0, p->Kc,
-                                   p->Kc, p->cchunk, p->tset, kc, p->st);
-                else
-                    combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, 0,
-                                   p->Nk, p->Nk, p->comb_is64 ? (void*)p->comb : (void*)p->comb32, p->tset, kc,
-                                   p->st);
+                combine_launch(f32, p->comb_is64, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, 0,
+                               p->Nk, p->Nk, p->comb_is64 ? (void*)p->comb : (void*)p->comb32, p->tset, kc,
+                               p->st);
             });
             if (p->comb_kc == 0 || ms < best) { best = ms; p->comb_kc = kc; }
         }
@@ -532,18 +534,53 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     ALLOCB(p->H2, (size_t)7 * ny * plane * p->csz);
     const size_t raw_per_k = (size_t)NJOB * ((ny + 7) / 8) * ((ny + 7) / 8) * 64 * p->csz;
     if (p->dec) {
-        // chunk rows R: a power of two dividing nzd, at most nzd / 2, with the
-        // chunk's contractions and spectra within DEC_CHUNK_BYTES
-        const size_t per_row = (size_t)p->nxh * (raw_per_k + (size_t)p->npair_tri * NTERM * p->csz);
-        p->R = std::max(1, p->nzt / 2);
-        while (p->R > 1 && ((size_t)p->R * per_row > DEC_CHUNK_BYTES ||
-                            fold_dec_smem(!f32, p->R, d.nx, p->wedge) > (size_t)smem_limit()))
-            p->R /= 2;
+        // conjugate classes of kz rows, {kz : kz mod nzd in {c, nzd - c}},
+        // c = 0 .. nzd/2, packed in order into chunks of at most R rows; R
+        // keeps a chunk's contractions and gathered operands within
+        // DEC_CHUNK_BYTES, but a chunk holds at least one class
+        const int nzd = p->nzt;
+        const size_t per_row = (size_t)p->nxh * (raw_per_k + (size_t)NFIELD * ns * ny * p->csz);
+        p->R = (int)std::max<size_t>((size_t)2 * (d.nz / nzd), DEC_CHUNK_BYTES / per_row);
+        std::vector<int> tab;
+        std::vector<int> rows, crs;
+        auto close_chunk = [&]() {
+            if (rows.empty()) return;
+            p->ch_rows.push_back((int)tab.size());
+            p->ch_nrows.push_back((int)rows.size());
+            tab.insert(tab.end(), rows.begin(), rows.end());
+            p->ch_crs.push_back((int)tab.size());
+            p->ch_ncr.push_back((int)crs.size());
+            tab.insert(tab.end(), crs.begin(), crs.end());
+            rows.clear();
+            crs.clear();
+        };
+        int rmax = 0;
+        for (int c = 0; c <= nzd / 2; ++c) {
+            const int c2 = (nzd - c) % nzd;
+            std::vector<int> cls;
+            for (int kz = 0; kz < d.nz; ++kz)
+                if (kz % nzd == c || kz % nzd == c2) cls.push_back(kz);
+            if (!rows.empty() && rows.size() + cls.size() > (size_t)p->R) close_chunk();
+            rows.insert(rows.end(), cls.begin(), cls.end());
+            crs.push_back(c);
+            if (c2 != c) crs.push_back(c2);
+            rmax = std::max(rmax, (int)rows.size());
+        }
+        close_chunk();
+        p->R = rmax;
         p->Kc = p->R * p->nxh;
         ALLOCB(p->raw, raw_per_k * p->Kc);
-        ALLOCB(p->cchunk, (size_t)p->npair_tri * NTERM * p->Kc * p->csz);
-        p->n_acc = (size_t)p->npair * NTERM * p->nzt * (p->nxt / 2 + 1);
+        ALLOCB(p->Xc, (size_t)NFIELD * p->Kc * ns * ny * p->csz);
+        ALLOCB(p->dec_tab, tab.size() * sizeof(int));
+        if ((e = cudaMemcpy(p->dec_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(GKE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+        const size_t ncoarse = (size_t)p->nzt * (p->nxt / 2 + 1);
+        p->n_acc = (size_t)p->npair_tri * NTERM * ncoarse;
         ALLOC(p->comb, p->n_acc);
+        if (p->wedge) {
+            ALLOCB(p->fold, (size_t)p->npair * NTERM * ncoarse * sizeof(zd));
+            p->fold_owned = true;
+        }
         p->tsz = f32 ? sizeof(float) : sizeof(double);
         if (f32) ALLOC(p->spec, (size_t)3 * p->npair * p->nxt * p->nzt + 13 * (size_t)p->npair);
     } else if (p->planes) {
@@ -745,7 +782,7 @@ extern "C" void gke_destroy(gke_plan_t p)
     for (cudaEvent_t ev : p->aux_ev) if (ev) cudaEventDestroy(ev);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->dec) {
-        void* extra[] = {p->cchunk, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
+        void* extra[] = {p->Xc, p->dec_tab, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
     }
     void* ptrs[] = {p->pl32, p->pl64, p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
@@ -933,31 +970,39 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
         StageScope sc(p, GKE_STAGE_PRODUCTS);
         products_stage(p, f, ns);
     }
-    auto correlate = [&](int k0, int Kc) -> gke_status {
+    // contractions of the wavenumbers [k0, k0 + Kc) of the operand set X
+    // (NkX wavenumbers) into raw
+    auto correlate = [&](const void* X, int NkX, int k0, int Kc) -> gke_status {
         StageScope sc(p, GKE_STAGE_CORRELATE);
         if (d.precision != GKE_PREC_BF16X3) {
-            correlate_launch(f32, p->Xop, ns, ny, Nk, k0, Kc, p->raw, job_set(p->tset), st);
+            correlate_launch(f32, X, ns, ny, NkX, k0, Kc, p->raw, job_set(p->tset), st);
             p->launches += 1;
             return GKE_OK;
         }
         int nl = 0;
-        gke_status s = split_correlate(p->split, (const zf*)p->Xop, ns, ny, Nk, k0, Kc, (zf*)p->raw, job_set(p->tset),
+        gke_status s = split_correlate(p->split, (const zf*)X, ns, ny, NkX, k0, Kc, (zf*)p->raw, job_set(p->tset),
                                        st, p->err, &nl);
         p->launches += nl;
         return s;
     };
     if (p->dec) {
-        // chunks of R kz rows: contractions, per-pair spectra of the chunk, and
-        // their aliasing fold into the FP64 coarse spectra
-        for (int kz0 = 0; kz0 < d.nz; kz0 += p->R) {
-            const int k0 = kz0 * p->nxh;
-            gke_status s = correlate(k0, p->Kc);
+        // chunks of conjugate row classes: the chunk's operands gathered, its
+        // contractions, and their fused combine + aliasing fold into the FP64
+        // coarse spectra of every triangle pair
+        for (size_t c = 0; c < p->ch_nrows.size(); ++c) {
+            const int nr = p->ch_nrows[c], Kc = nr * p->nxh;
+            const int* rows = p->dec_tab + p->ch_rows[c];
+            {
+                StageScope sc(p, GKE_STAGE_CORRELATE);
+                p->launches += gather_rows_launch(!f32, p->Xop, NFIELD, Nk, (long long)ns * ny, rows, nr, p->nxh,
+                                                  p->Xc, st);
+            }
+            gke_status s = correlate(p->Xc, Kc, 0, Kc);
             if (s != GKE_OK) return s;
             StageScope sc(p, GKE_STAGE_COMBINE);
-            p->launches += combine_launch(f32, !f32, p->raw, d.ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->prof, 0, k0,
-                                          p->Kc, p->Kc, p->cchunk, p->tset, p->comb_kc, st);
-            p->launches += fold_dec_launch(!f32, p->cchunk, p->pair_i, p->npair, p->wedge ? 1 : 0, ny, d.nz, d.nx,
-                                           p->nzt, p->nxt, kz0, p->R, p->comb, st);
+            p->launches += combine_fold_launch(!f32, p->raw, rows, nr, p->dec_tab + p->ch_crs[c], p->ch_ncr[c], ny,
+                                               d.nz, d.nx, p->nzt, p->nxt, d.Lx, d.Lz, d.nu, p->prof, p->tset,
+                                               p->comb, st);
         }
         CUDA_TRY(p, cudaGetLastError());
         p->snap_count += ns;
@@ -991,7 +1036,7 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
         return GKE_OK;
     }
     {
-        gke_status s = correlate(0, Nk);
+        gke_status s = correlate(p->Xop, Nk, 0, Nk);
         if (s != GKE_OK) return s;
     }
     {
@@ -1057,7 +1102,7 @@ static void terms_stage(gke_plan_t p, void* terms_dev)
     TermArgs a;
     a.fp32 = f32; a.comb64 = p->comb_is64;
     a.comb = p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32;
-    if (p->wedge && !p->dec) a.comb = p->fold;
+    if (p->wedge) a.comb = p->fold;
     a.W = p->W; a.spec = p->spec; a.pair_i = p->pair_i; a.npair = p->npair; a.pair_chunk = p->pair_chunk;
     a.ny = d.ny; a.nz = p->nzt; a.nx = p->nxt;
     a.cw = t.cw_tc;
@@ -1092,9 +1137,12 @@ static gke_status finalize_impl(gke_plan_t p, void* terms_dev)
         k_profiles<<<(ny + 127) / 128, 128, 0, st>>>(p->mean_sum, p->mean_count, p->stats, p->snap_count,
                                                       (long long)d.nx * d.nz, d.nu, p->wedge ? 1 : 0, p->fdw, p->fdl0, ny, p->prof);
         p->launches += 1;
-        if (p->wedge && !p->dec) {
+        if (p->wedge) {
+            // the wedge's output pairs: mirror average of the triangle's spectra
+            // (full or, in the chunked mode, coarse; aliasing commutes with it)
+            const int nk = p->dec ? p->nzt * (p->nxt / 2 + 1) : p->Nk;
             p->launches += mirror_fold_launch(p->comb_is64, p->comb_is64 ? (const void*)p->comb : (const void*)p->comb32,
-                                              p->pair_i, p->npair, ny, p->Nk, p->fold, st);
+                                              p->pair_i, p->npair, ny, nk, p->fold, st);
         }
         terms_stage(p, terms_dev);
     }
@@ -1302,7 +1350,7 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     const int ny = p->d.ny;
     const size_t n_mean = 4 * ny, n_stat = (size_t)NSTAT * ny;
     const size_t n_comb = p->n_acc;
-    const int acc_kind = p->planes ? 1 : 0;
+    const int acc_kind = p->planes ? 1 : p->dec ? 2 : 0;
     // the stored sums are FP64; a split plan holding one batch in FP32 promotes first
     if (p->planes) {
         if (p->have_acc && !p->pl_is64) {
@@ -1367,8 +1415,8 @@ static gke_status ckpt_io(gke_plan_t p, const char* path, int mode)   // 0 save,
     }
     if (h.have_acc && h.acc_kind != acc_kind) {
         fclose(fp);
-        return fail(p, GKE_ERR_ARG, "checkpoint accumulator layout does not match the plan (plane spectra of the "
-                                    "split path on one 128-row tile vs per-pair term spectra)");
+        return fail(p, GKE_ERR_ARG, "checkpoint accumulator layout does not match the plan (per-pair term spectra, "
+                                    "plane spectra of the split path, or coarse spectra of the chunked mode)");
     }
     if (mode == 2 && p->mean_frozen && h.mean_count > 0 && !p->have_acc) {
         fclose(fp);

@@ -60,6 +60,30 @@ template <typename TI, int KC> constexpr size_t combine_smem_bytes()
 int combine_kc(bool fp32) { return fp32 ? CombCfg<float>::KC : CombCfg<double>::KC; }
 bool combine_kc_ok(bool fp32, int kc) { return fp32 ? (kc == 2 || kc == 4 || kc == 8) : (kc == 1 || kc == 2 || kc == 4); }
 
+// The seven term spectra of one (pair, wavenumber) from the contractions
+// x12[j] = X_j(Y1, Y2) and x21[j] = conj X_j(Y2, Y1) (D has no partner).
+template <typename TC>
+__device__ __forceinline__ void pair_terms(const cplx<TC>* x12, const cplx<TC>* x21, TC kx, TC kz, TC dU, TC Upm,
+                                           TC dUp, TC nuc, cplx<TC>* T)
+{
+    typedef cplx<TC> Z;
+    const Z S0 = x12[J_D];
+    const Z S1 = x12[J_E] + x21[J_E], S2 = x21[J_E] - x12[J_E];
+    const Z S3 = x12[J_F] + x21[J_F];
+    const Z S4 = x12[J_GX] - x21[J_GX];
+    const Z S6 = x12[J_GZ] - x21[J_GZ];
+    const Z S5 = (x12[J_QV] + x12[J_X]) - (x21[J_QV] + x21[J_X]);
+    const Z S7 = (x12[J_QV] - x12[J_X]) + (x21[J_QV] - x21[J_X]);
+    T[T_A] = (TC)(-2) * S0;
+    T[T_PHIX] = S4 + ((TC)(-2) * dU) * S0 + ((TC)4 * nuc * kx) * mul_i(S0);
+    T[T_PHIY] = S5;
+    T[T_PHIZ] = S6 + ((TC)4 * nuc * kz) * mul_i(S0);
+    T[T_PHI] = (TC)0.5 * S7 - (TC)2 * S3;
+    T[T_XI] = ((TC)2 * Upm) * S1 - dUp * S2;
+    T[T_RES] = kx * mul_i(S4) + kz * mul_i(S6) + ((TC)(-2) * dU * kx) * mul_i(S0)
+             + ((TC)(-4) * nuc * (kx * kx + kz * kz)) * S0 - T[T_XI];
+}
+
 template <typename TI, typename TC, typename TO, int KC>
 __global__ void __launch_bounds__(256)
 k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, double Lz, double nu,
@@ -136,27 +160,20 @@ k_combine(const cplx<TI>* __restrict__ raw, int ny, int nz, int nx, double Lx, d
         if (k >= Nk || i1 >= ny || i2 >= ny || i2 < i1) continue;
         const TC kx = s_kx[kk], kz = s_kz[kk];
         const TC dU = s_dU[pm], Upm = s_Upm[pm], dUp = s_dUp[pm];
-        const TC nuc = (TC)nu;
-        auto v12 = [&](int j) { C v = at(2 * j, kk, r, m); return mk((TC)v.x, (TC)v.y); };
-        auto v21 = [&](int j) { C v = at(2 * j + 1, kk, m, r); return mk((TC)v.x, -(TC)v.y); };  // conj
-        const Z S0 = v12(J_D);
-        const Z E12 = v12(J_E), E21 = v21(J_E);
-        const Z S1 = E12 + E21, S2 = E21 - E12;
-        const Z S3 = v12(J_F) + v21(J_F);
-        const Z S4 = v12(J_GX) - v21(J_GX);
-        const Z S6 = v12(J_GZ) - v21(J_GZ);
-        const Z Q12 = v12(J_QV), Q21 = v21(J_QV), X12 = v12(J_X), X21 = v21(J_X);
-        const Z S5 = (Q12 + X12) - (Q21 + X21);
-        const Z S7 = (Q12 - X12) + (Q21 - X21);
+        Z x12[NJOB], x21[NJOB];
+        #pragma unroll
+        for (int j = 0; j < NJOB; ++j) {
+            const C v = at(2 * j, kk, r, m);
+            x12[j] = mk((TC)v.x, (TC)v.y);
+            if (j != J_D) {
+                const C w = at(2 * j + 1, kk, m, r);
+                x21[j] = mk((TC)w.x, -(TC)w.y);                           // conj
+            } else {
+                x21[j] = mk((TC)0, (TC)0);
+            }
+        }
         Z T[NTERM];
-        T[T_A] = (TC)(-2) * S0;
-        T[T_PHIX] = S4 + ((TC)(-2) * dU) * S0 + ((TC)4 * nuc * kx) * mul_i(S0);
-        T[T_PHIY] = S5;
-        T[T_PHIZ] = S6 + ((TC)4 * nuc * kz) * mul_i(S0);
-        T[T_PHI] = (TC)0.5 * S7 - (TC)2 * S3;
-        T[T_XI] = ((TC)2 * Upm) * S1 - dUp * S2;
-        T[T_RES] = kx * mul_i(S4) + kz * mul_i(S6) + ((TC)(-2) * dU * kx) * mul_i(S0)
-                 + ((TC)(-4) * nuc * (kx * kx + kz * kz)) * S0 - T[T_XI];
+        pair_terms<TC>(x12, x21, kx, kz, dU, Upm, dUp, (TC)nu, T);
         cplx<TO>* dst = comb + pair_index(i1, i2, ny) * NTERM * cstride + k;
         #pragma unroll
         for (int t = 0; t < NTERM; ++t) {
@@ -224,97 +241,156 @@ int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long 
 //   G(kzd, kxd) = sum of F_H(kz, kx) over kz = kzd (mod nzd), kx = kxd (mod nxd),
 // F_H the Hermitian extension of the stored half spectrum (its kx = 0 and
 // kx = nx/2 columns taken as their Hermitian parts, as the full-size inverse
-// transform does).  G is accumulated in FP64 chunk by chunk: the chunk holds
-// the kz rows [kz0, kz0 + R) (R divides nzd, kz0 a multiple of R), so a coarse
-// row kzd receives at most one direct row of the chunk (kz = kzd mod nzd) and
-// one conjugate image row (nz - kz = kzd mod nzd).  A thread owns one coarse
-// bin and gathers both, so the sums are deterministic.  With the wedge the
-// spectra are first averaged with the image pair's (as in k_mirror_fold).
-template <typename TC>
-__global__ void __launch_bounds__(256)
-k_fold_dec(const cplx<TC>* __restrict__ cchunk, const int* __restrict__ pair_o, int wedge, int ny, int nz, int nx,
-           int nzd, int nxd, int kz0, int R, zd* __restrict__ dec)
+// transform does).  So a stored value F(kz, kx), 0 <= kx <= nx/2, adds
+// h F to the bin (kz, kx) and h conj F to the bin (-kz, -kx) (mod nzd, nxd),
+// h = 1/2 on the columns kx = 0 and nx/2, else 1.
+//
+// The contractions run in chunks of whole conjugate classes of kz rows,
+// {kz : kz mod nzd in {c, -c}}: every source of the coarse rows c and -c then
+// lies in one chunk, and the FP64 coarse spectra of a row are read and
+// written once per batch.
+
+// dst[f][kl][e] = src[f][rows[i] nxh + kx][e], kl = i nxh + kx: the chunk's
+// wavenumbers gathered into a contiguous operand set (per_k values each)
+template <typename T>
+__global__ void k_gather_rows(const T* __restrict__ src, long long Nk, long long per_k, const int* __restrict__ rows,
+                              int nrows, int nxh, T* __restrict__ dst)
 {
-    typedef cplx<TC> C;
-    extern __shared__ __align__(16) unsigned char sh_fold[];
-    const int nxh = nx / 2 + 1, nxdh = nxd / 2 + 1, Kc = R * nxh;
-    const long long row = blockIdx.x;                 // po * NTERM + t
-    const long long po = row / NTERM;
-    const int t = (int)(row - po * NTERM);
-    const int i1 = pair_o[2 * po], i2 = pair_o[2 * po + 1];
-    // the chunk's spectra of the pair (and of its image pair on the wedge),
-    // read once, coalesced, into shared memory
-    C* sa = (C*)sh_fold;
-    C* sb = sa + Kc;
-    const C* a = cchunk + (pair_index(i1, i2, ny) * NTERM + t) * (long long)Kc;
-    for (int i = threadIdx.x; i < Kc; i += blockDim.x) sa[i] = ld_stream(a + i);
-    if (wedge) {
-        const C* b = cchunk + (pair_index(ny - 1 - i2, ny - 1 - i1, ny) * NTERM + t) * (long long)Kc;
-        for (int i = threadIdx.x; i < Kc; i += blockDim.x) sb[i] = ld_stream(b + i);
+    const int i = blockIdx.x, f = blockIdx.y;
+    const long long n = (long long)nxh * per_k;
+    const T* s = src + ((long long)f * Nk + (long long)rows[i] * nxh) * per_k;
+    T* d = dst + ((long long)f * nrows * nxh + (long long)i * nxh) * per_k;
+    for (long long e = threadIdx.x; e < n; e += blockDim.x) d[e] = s[e];
+}
+
+int gather_rows_launch(bool c64, const void* src, int nf, long long Nk, long long per_k, const int* rows, int nrows,
+                       int nxh, void* dst, cudaStream_t st)
+{
+    dim3 g((unsigned)nrows, (unsigned)nf);
+    if (c64) k_gather_rows<zd><<<g, 256, 0, st>>>((const zd*)src, Nk, per_k, rows, nrows, nxh, (zd*)dst);
+    else k_gather_rows<zf><<<g, 256, 0, st>>>((const zf*)src, Nk, per_k, rows, nrows, nxh, (zf*)dst);
+    return 1;
+}
+
+// FP32 sums are compensated (Kahan), FP64 ones plain
+template <typename TC> struct Acc {
+    cplx<TC> s;
+    __device__ __forceinline__ void zero() { s = mk((TC)0, (TC)0); }
+    __device__ __forceinline__ void add(cplx<TC> v) { s = s + v; }
+    __device__ __forceinline__ double re() const { return (double)s.x; }
+    __device__ __forceinline__ double im() const { return (double)s.y; }
+};
+template <> struct Acc<float> {
+    float sx, sy, cx, cy;
+    __device__ __forceinline__ void zero() { sx = sy = cx = cy = 0.f; }
+    __device__ __forceinline__ static void kahan(float& s, float& c, float v)
+    {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
     }
-    __syncthreads();
-    // arithmetic in TC (FP32 on the FP32 paths: FP64 work costs ~60 FP32
-    // operations here); the chunk's partial sums join the FP64 accumulator
-    const TC sg = (TC)c_sigma[t], hf = (TC)0.5;
-    // term spectrum at chunk row r, column kx (mirror-averaged on the wedge)
-    auto F = [&](int r, int kx) -> C {
-        const int kl = r * nxh + kx;
-        const C va = sa[kl];
-        if (!wedge) return va;
-        const C vb = sb[kl];
-        return mk(hf * (va.x + sg * vb.x), hf * (va.y - sg * vb.y));
-    };
-    const int dlo = kz0 % nzd;                        // direct coarse rows: [dlo, dlo + R)
-    for (int it = threadIdx.x; it < 2 * R * nxdh; it += blockDim.x) {
-        const int br = it / nxdh, kxd = it - br * nxdh;
-        int kzd;
-        if (br < R) {
-            kzd = dlo + br;
-        } else {
-            kzd = ((nz - (kz0 + br - R)) % nz) % nzd;
-            if ((kzd - dlo + nzd) % nzd < R) continue;      // handled by the direct-row thread
-        }
-        const int od = (kzd - kz0 % nzd + nzd) % nzd;              // kz0 + od = kzd (mod nzd)
-        const int oi = ((nzd - kzd) % nzd - kz0 % nzd + nzd) % nzd; // kz0 + oi = -kzd (mod nzd)
-        const int rd = od < R ? od : -1, ri = oi < R ? oi : -1;     // chunk rows
-        TC ax = 0, ay = 0;
-        for (int ix = 0; ix < nx / nxd; ++ix) {
-            const int kxf = kxd + ix * nxd;
-            const bool self = (kxf == 0 || 2 * kxf == nx);
-            if (rd >= 0 && 2 * kxf <= nx) {
-                const C v = F(rd, kxf);
-                const TC h = self ? hf : (TC)1;
-                ax += h * v.x;
-                ay += h * v.y;
+    __device__ __forceinline__ void add(zf v) { kahan(sx, cx, v.x); kahan(sy, cy, v.y); }
+    __device__ __forceinline__ double re() const { return (double)sx - (double)cx; }
+    __device__ __forceinline__ double im() const { return (double)sy - (double)cy; }
+};
+
+// One chunk's contractions -> the term spectra of every triangle pair ->
+// their coarse bins, added to dec[p][t][kzd][kxd] (FP64).  CTA = the 64
+// pairs of an 8 x 8 block (a, b), b >= a, times FK coarse columns kxd;
+// a thread owns one (pair, kxd) and walks the chunk's coarse rows, summing
+// for each the direct sources (kz = kzd, kx = kxd) and the conjugate images
+// (kz = -kzd, kx = -kxd) of the chunk's rows.  The 32 lanes of a warp are
+// 32 pairs of the block, so every contraction load is one contiguous
+// 256-byte row of the raw layout (the partner block's: 8 sectors).
+constexpr int FK = 4;
+template <typename TI, typename TC>
+__global__ void __launch_bounds__(64 * FK)
+k_combine_fold(const cplx<TI>* __restrict__ raw, const int* __restrict__ rows, int nrows,
+               const int* __restrict__ crs, int ncr, int ny, int nz, int nx, int nzd, int nxd, double Lx, double Lz,
+               double nu, const double* __restrict__ prof, unsigned tmask, unsigned jmask, zd* __restrict__ dec)
+{
+    typedef cplx<TI> C;
+    typedef cplx<TC> Z;
+    const int nxh = nx / 2 + 1, nxdh = nxd / 2 + 1, Kc = nrows * nxh;
+    const int nblk = (ny + PB - 1) / PB;
+    int bt = blockIdx.x, a = 0;
+    while (bt >= nblk - a) { bt -= nblk - a; ++a; }
+    const int b = a + bt;
+    const int pm = threadIdx.x & 63, r = pm >> 3, m = pm & 7;
+    const int kxd = blockIdx.y * FK + (threadIdx.x >> 6);
+    const int i1 = PB * a + r, i2 = PB * b + m;
+    if (kxd >= nxdh || i1 >= ny || i2 >= ny || i2 < i1) return;
+    const TC dU = (TC)(prof[PR_U * ny + i2] - prof[PR_U * ny + i1]);
+    const TC Upm = (TC)(0.5 * (prof[PR_DU * ny + i1] + prof[PR_DU * ny + i2]));
+    const TC dUp = (TC)(prof[PR_DU * ny + i2] - prof[PR_DU * ny + i1]);
+    const TC cx = (TC)(6.283185307179586476925286766559 / Lx), cz = (TC)(6.283185307179586476925286766559 / Lz);
+    const TC nuc = (TC)nu;
+    const long long jstride = (long long)nblk * nblk * Kc * 64;
+    const C* p12 = raw + ((long long)a * nblk + b) * Kc * 64 + pm;          // block (a, b), element (r, m)
+    const C* p21 = raw + ((long long)b * nblk + a) * Kc * 64 + m * PB + r;  // block (b, a), element (m, r)
+    const int kxm = (nxd - kxd) % nxd;                   // -kxd mod nxd
+    zd* out = dec + pair_index(i1, i2, ny) * NTERM * (long long)nzd * nxdh + kxd;
+    for (int ci = 0; ci < ncr; ++ci) {
+        const int kzd = crs[ci];
+        Acc<TC> acc[NTERM];
+        #pragma unroll
+        for (int t = 0; t < NTERM; ++t) acc[t].zero();
+        for (int i = 0; i < nrows; ++i) {
+            const int kz = rows[i];
+            const bool direct = kz % nzd == kzd, image = (nz - kz) % nzd == kzd;
+            if (!direct && !image) continue;
+            const TC kzv = cz * (TC)signed_bin(kz, nz);
+            // direct sources kx = kxd (mod nxd), then the images kx = -kxd
+            for (int pass = 0; pass < 2; ++pass) {
+                if (!(pass ? image : direct)) continue;
+                for (int kx = pass ? kxm : kxd; 2 * kx <= nx; kx += nxd) {
+                    const long long kl = (long long)i * nxh + kx;
+                    Z x12[NJOB], x21[NJOB];
+                    #pragma unroll
+                    for (int j = 0; j < NJOB; ++j) {
+                        C v = mk((TI)0, (TI)0), w = v;
+                        if ((jmask >> j) & 1u) {
+                            v = p12[j * jstride + kl * 64];
+                            if (j != J_D) w = p21[j * jstride + kl * 64];
+                        }
+                        x12[j] = mk((TC)v.x, (TC)v.y);
+                        x21[j] = mk((TC)w.x, -(TC)w.y);
+                    }
+                    Z T[NTERM];
+                    pair_terms<TC>(x12, x21, cx * (TC)signed_bin(kx, nx), kzv, dU, Upm, dUp, nuc, T);
+                    const TC h = (kx == 0 || 2 * kx == nx) ? (TC)0.5 : (TC)1;
+                    #pragma unroll
+                    for (int t = 0; t < NTERM; ++t)
+                        acc[t].add(mk(h * T[t].x, pass ? -h * T[t].y : h * T[t].y));
+                }
             }
-            if (ri >= 0 && (self || 2 * kxf > nx)) {
-                const C v = F(ri, self ? kxf : nx - kxf);
-                const TC h = self ? hf : (TC)1;
-                ax += h * v.x;
-                ay -= h * v.y;
-            }
         }
-        zd* o = dec + row * (long long)nzd * nxdh + (long long)kzd * nxdh + kxd;
-        o->x += (double)ax;
-        o->y += (double)ay;
+        #pragma unroll
+        for (int t = 0; t < NTERM; ++t) {
+            if (!((tmask >> t) & 1u)) continue;
+            zd* o = out + ((long long)t * nzd + kzd) * nxdh;
+            zd v = *o;
+            v.x += acc[t].re();
+            v.y += acc[t].im();
+            *o = v;
+        }
     }
 }
 
-size_t fold_dec_smem(bool c64, int R, int nx, bool wedge)
+int combine_fold_launch(bool c64, const void* raw, const int* rows, int nrows, const int* crs, int ncr, int ny,
+                        int nz, int nx, int nzd, int nxd, double Lx, double Lz, double nu, const double* prof,
+                        unsigned tmask, void* dec, cudaStream_t st)
 {
-    return (size_t)R * (nx / 2 + 1) * (c64 ? sizeof(zd) : sizeof(zf)) * (wedge ? 2 : 1);
-}
-
-int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
-                    int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st)
-{
-    const size_t sh = fold_dec_smem(c64, R, nx, wedge != 0);
+    const int nblk = (ny + PB - 1) / PB, nxdh = nxd / 2 + 1;
+    dim3 g((unsigned)(nblk * (nblk + 1) / 2), (unsigned)((nxdh + FK - 1) / FK));
+    const unsigned jm = job_set(tmask);
     if (c64)
-        k_fold_dec<double><<<(unsigned)(nout * NTERM), 256, sh, st>>>((const zd*)cchunk, pair_o, wedge, ny, nz, nx,
-                                                                      nzd, nxd, kz0, R, (zd*)dec);
+        k_combine_fold<double, double><<<g, 64 * FK, 0, st>>>((const zd*)raw, rows, nrows, crs, ncr, ny, nz, nx, nzd,
+                                                              nxd, Lx, Lz, nu, prof, tmask, jm, (zd*)dec);
     else
-        k_fold_dec<float><<<(unsigned)(nout * NTERM), 256, sh, st>>>((const zf*)cchunk, pair_o, wedge, ny, nz, nx,
-                                                                     nzd, nxd, kz0, R, (zd*)dec);
+        k_combine_fold<float, float><<<g, 64 * FK, 0, st>>>((const zf*)raw, rows, nrows, crs, ncr, ny, nz, nx, nzd,
+                                                            nxd, Lx, Lz, nu, prof, tmask, jm, (zd*)dec);
     return 1;
 }
 
@@ -418,13 +494,7 @@ cudaError_t combine_set_attrs()
     set((const void*)k_combine<float, float, double, 2>, combine_smem_bytes<float, 2>());
     set((const void*)k_combine<float, float, double, 4>, combine_smem_bytes<float, 4>());
     set((const void*)k_combine<float, float, double, 8>, combine_smem_bytes<float, 8>());
-    if (e != cudaSuccess) return e;
-    int dev = 0, lim = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    e = cudaFuncSetAttribute((const void*)k_fold_dec<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute((const void*)k_fold_dec<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    return e;
 }
 
 }  // namespace gke

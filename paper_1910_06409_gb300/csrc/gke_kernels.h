@@ -130,9 +130,15 @@ cudaError_t products_set_attrs(int lim);
 int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, int nx, double Lx, double Lz,
                    double nu, const double* prof, int beta, int kbase, int Kc, long long cstride, void* comb,
                    unsigned terms, int kc, cudaStream_t st);
-int fold_dec_launch(bool c64, const void* cchunk, const int* pair_o, long long nout, int wedge, int ny, int nz,
-                    int nx, int nzd, int nxd, int kz0, int R, void* dec, cudaStream_t st);
-size_t fold_dec_smem(bool c64, int R, int nx, bool wedge);
+// chunked mode: the chunk's wavenumber rows gathered into a contiguous
+// operand set, and the fused combine + aliasing fold of its contractions into
+// the FP64 coarse spectra of every triangle pair (rows: the chunk's kz rows,
+// crs: the coarse rows they complete)
+int gather_rows_launch(bool c64, const void* src, int nf, long long Nk, long long per_k, const int* rows, int nrows,
+                       int nxh, void* dst, cudaStream_t st);
+int combine_fold_launch(bool c64, const void* raw, const int* rows, int nrows, const int* crs, int ncr, int ny,
+                        int nz, int nx, int nzd, int nxd, double Lx, double Lz, double nu, const double* prof,
+                        unsigned tmask, void* dec, cudaStream_t st);
 int promote_launch(const void* comb32, long long n, void* comb64, cudaStream_t st);
 int planes_accum_launch(const void* src, long long per_plane, unsigned planes, int beta, void* dst, cudaStream_t st);
 int mirror_fold_launch(bool c64, const void* comb, const int* pair_w, long long nout, int ny, int Nk, void* out,

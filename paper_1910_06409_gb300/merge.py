@@ -14,8 +14,10 @@ endian; the C struct of the library, include/gke.h):
   float64  mean[4][ny]              the mean the spectra were taken about
                                     (only if have_acc)
   complex128 acc[...]               spectra (only if have_acc): per-pair term
-                                    spectra (acc_kind 0) or the plane spectra
+                                    spectra (acc_kind 0), the plane spectra
                                     of the split path on one 128-row tile (1)
+                                    or the coarse term spectra of the chunked
+                                    mode for every triangle pair (2)
 
 The spectra of each job are sums over its snapshots of products of
 fluctuations about a Step-1 mean, so jobs add exactly only when they used the
