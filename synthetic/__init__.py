@@ -146,6 +146,36 @@ def coefficients(wl: Workload, nsnap: int | None = None, out: np.ndarray | None 
     return out
 
 
+def snapshot_vorticity(wl: Workload, s: int):
+    """Inputs of Step 1 for velocity-vorticity databases, snapshot s:
+    (v_eta complex128 [2][ny][nz][nx/2+1], mean_uw float64 [2][ny]).
+
+    v and eta are drawn like the fields above (random half spectra with the
+    same amplitude, irfft2, then a wall envelope): v with (1 - y^2)^2 (v and
+    dv/dy vanish at no-slip walls), eta with (1 - y^2).  The plane averages of
+    u and w are (1 - y^2)(1 + 0.05 g_j) and 0.02 (1 - y^2) h_j with standard
+    normal g_j, h_j.  Seed: 1910_06409 + 1000*wid + 500 + s."""
+    rng = np.random.default_rng(SEED_BASE + 1000 * wl.wid + 500 + s)
+    amp = _amplitude(wl)
+    y = cgl_grid(wl.ny)
+    shape = (2, wl.ny, wl.nz, wl.nxh)
+    c = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * amp
+    phys = np.fft.irfft2(c, s=(wl.nz, wl.nx), axes=(-2, -1), norm="forward")
+    env = 1.0 - y * y
+    phys[0] *= (env * env)[:, None, None]
+    phys[1] *= env[:, None, None]
+    mean_uw = np.stack([env * (1.0 + 0.05 * rng.standard_normal(wl.ny)),
+                        0.02 * env * rng.standard_normal(wl.ny)])
+    return to_coefficients(phys), mean_uw
+
+
+def vorticity_inputs(wl: Workload, nsnap: int | None = None):
+    """(v_eta [nsnap][2][ny][nz][nx/2+1], mean_uw [nsnap][2][ny]) of snapshots 0..nsnap-1."""
+    n = wl.nsnap if nsnap is None else nsnap
+    pairs = [snapshot_vorticity(wl, s) for s in range(n)]
+    return np.stack([a for a, _ in pairs]), np.stack([b for _, b in pairs])
+
+
 def single_mode_fields(nx: int, nz: int, ny: int, nsnap: int, modes, Lx: float, Lz: float,
                        mean_u=None) -> np.ndarray:
     """Physical fields built from a few Fourier modes with y-dependent amplitudes.
