@@ -16,6 +16,10 @@ ny = 129 Chebyshev points, 16 snapshots), plain FP64 path.
 --impl reference times the CPU oracle (direct averages, C/OpenMP) on the host
 cores on a bounded sample of the same workload.
 
+--step1 times Step 1 for velocity-vorticity databases (u, w from v and the
+wall-normal vorticity, Poisson pressure) on the workload's snapshots and prints
+its own JSON line (snapshots/s).
+
 --passes P runs P untimed passes of the workload at --precision and prints the
 number of kernel launches per pass, nothing else: the program that ncu launch
 lists and single-kernel captures are taken on.
@@ -474,6 +478,72 @@ def run_passes(args):
     N.gke_destroy(plan)
 
 
+def run_step1(args, world, rank, local):
+    """Step 1 for velocity-vorticity databases: all snapshots of the workload
+    per step, inputs resident on the device; e2e through pinned host buffers."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    torch.cuda.set_device(local)
+    wl = S.WORKLOADS[args.workload]
+    ns = wl.nsnap
+    v_eta, mean_uw = S.vorticity_inputs(wl)
+    stream = torch.cuda.current_stream()
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, S.cgl_grid(wl.ny), ns, N.GKE_PREC_F64,
+                      stream=stream.cuda_stream)
+    v_dev, m_dev = torch.from_numpy(v_eta).cuda(), torch.from_numpy(mean_uw).cuda()
+    out = torch.empty((ns, 4) + v_eta.shape[2:], dtype=torch.complex128, device="cuda")
+    for _ in range(args.warmup):
+        N.gke_velocity_vorticity(plan, v_dev, m_dev, ns, out)
+    torch.cuda.synchronize()
+    l0 = N.gke_launch_count(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            N.gke_velocity_vorticity(plan, v_dev, m_dev, ns, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = N.gke_launch_count(plan) - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    e2e = None
+    if not args.no_e2e:
+        v_h = torch.from_numpy(v_eta).pin_memory()
+        m_h = torch.from_numpy(mean_uw).pin_memory()
+        o_h = torch.empty(out.shape, dtype=torch.complex128).pin_memory()
+        N.gke_velocity_vorticity(plan, v_h, m_h, ns, o_h)
+        t0 = time.perf_counter()
+        N.gke_velocity_vorticity(plan, v_h, m_h, ns, o_h)
+        ms_e2e = (time.perf_counter() - t0) * 1e3
+        e2e = {"value": ns / (ms_e2e / 1e3), "unit": "snapshots/s", "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(v_h.numel() * 16 + m_h.numel() * 8),
+               "d2h_bytes_per_step": int(o_h.numel() * 16)}
+    N.gke_destroy(plan)
+    # FP64 work of the transforms (5 N log2 N per complex length-N DFT): per
+    # snapshot 3 + 6 column DFTs of length nz per (y, kx), 5 row DFTs of
+    # length nx per (y, z)
+    lg = lambda n: float(np.log2(n))
+    flops = ns * wl.ny * ((3 + 6) * wl.nxh * 5 * wl.nz * lg(wl.nz) + wl.nz * 5 * 5 * wl.nx * lg(wl.nx))
+    pk, pk_kind = peaks()
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    ach = flops / (ms / 1e3) / 1e12
+    io_bytes = ns * 6 * wl.ny * wl.nz * wl.nxh * 16
+    line = {"metric": "Step-1 velocity-vorticity -> u, v, w, p snapshots/s", "value": ns / (ms / 1e3),
+            "unit": "snapshots/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "nx": wl.nx, "nz": wl.nz, "ny": wl.ny, "snapshots": ns,
+                       "l2": "inputs and outputs larger than L2 (no flush)"},
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                         "flops": flops, "note": "FP64 DFT work, 5 N log2 N per transform",
+                         "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock"},
+            "hbm": {"bytes": io_bytes, "achieved_gbs": io_bytes / (ms / 1e3) / 1e9, "peak_gbs": pk["hbm_gbs"],
+                    "note": "inputs read once and outputs written once"},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1910_06409_gb300._native as N
@@ -719,6 +789,8 @@ def main():
     ap.add_argument("--nsnap", type=int, default=0, help="first n snapshots of the workload only (streaming mode)")
     ap.add_argument("--no-f64-check", action="store_true",
                     help="streaming mode: skip the untimed FP64 run that measures the per-term error")
+    ap.add_argument("--step1", action="store_true",
+                    help="time Step 1 for velocity-vorticity databases on the workload's snapshots")
     ap.add_argument("--passes", type=int, default=0,
                     help="profiling target: run this many untimed passes, print launches per pass, exit")
     args = ap.parse_args()
@@ -728,6 +800,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.step1:
+        run_step1(args, world, rank, local)
     elif args.workload == "group":
         run_group(args, world, rank, local)
     elif args.pair_domain != "triangle" or args.stride > 1 or args.batch:

@@ -152,6 +152,30 @@ unsigned gke_term_set(unsigned term_mask);
  * allocated later except the staging buffer of a first host-output finalize. */
 gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* out);
 
+/* Step 1 (Sec. 3.2) for databases in velocity-vorticity form: the fields
+ * u, v, w, p of nsnap snapshots from the wall-normal velocity v and vorticity
+ * eta = du/dz - dw/dx and the plane averages of u and w, for the plan's grid.
+ *   v_eta    complex128 [nsnap][2][ny][nz][nx/2+1]: v, eta, forward-normalised
+ *            like `fields` (host or device);
+ *   mean_uw  float64 [nsnap][2][ny]: the (0, 0) modes of u and w (host or
+ *            device);
+ *   fields   complex128 [nsnap][4][ny][nz][nx/2+1] out (host or device), the
+ *            layout every gke_accumulate_* call reads.
+ * u, w (kx^2 + kz^2 > 0): the solution of continuity i kx u + dv/dy + i kz w = 0
+ * and eta = i kz u - i kx w; the (0, 0) modes are mean_uw, other modes with
+ * kx^2 + kz^2 = 0 are zero.  p: lap p = -d_i d_j (u_i u_j) (rho = 1), the six
+ * products of the total velocity formed on the collocation grid, with
+ * dp/dy = nu d2v/dy2 at both walls; p(y_0) = 0 fixes the (0, 0) mode.
+ * Odd x / z derivatives use the signed wavenumber (0 on the Nyquist lines),
+ * second derivatives its true square; d/dy and d2/dy2 are 5-point weights on
+ * the nodes of gke_fd_weights.  FP64 throughout, one snapshot at a time; the
+ * first call allocates about 13 ny nz (nx/2+1) x 16 bytes of workspace and
+ * factors the banded Poisson operators once per plan.  Returns after the
+ * last host copy when an argument is in host memory, else asynchronously on
+ * the plan's stream.  GKE_ERR_ARG on NULL pointers or nsnap < 1.              */
+gke_status gke_velocity_vorticity(gke_plan_t plan, const void* v_eta, const double* mean_uw, int nsnap,
+                                  void* fields);
+
 /* Step 1 (Sec. 3.2): add nsnap snapshots to the ensemble mean of u, v, w, p.
  * Only the k = 0 coefficients are read.  Must precede the first
  * gke_accumulate_snapshot; GKE_ERR_STATE afterwards.                         */

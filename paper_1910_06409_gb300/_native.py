@@ -28,7 +28,8 @@ EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_sn
            "gke_compute", "gke_compute_graph", "gke_pair_labels", "gke_npair", "gke_separation_labels",
            "gke_terms_bytes", "gke_term_set", "gke_plan_knobs", "gke_reset", "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
-           "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy")
+           "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy",
+           "gke_velocity_vorticity")
 STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
 
 
@@ -62,6 +63,7 @@ def lib():
         sig = {
             "gke_plan": (i, [ctypes.POINTER(gke_desc), vp, ctypes.POINTER(vp)]),
             "gke_accumulate_mean": (i, [vp, vp, i]),
+            "gke_velocity_vorticity": (i, [vp, vp, vp, i, vp]),
             "gke_set_mean": (i, [vp, vp]),
             "gke_accumulate_snapshot": (i, [vp, vp, i]),
             "gke_finalize_terms": (i, [vp, vp, vp]),
@@ -141,6 +143,10 @@ def gke_accumulate_snapshot(plan, fields, nsnap):
 
 def gke_finalize_terms(plan, terms, profiles=None):
     _check(lib().gke_finalize_terms(plan, ptr(terms), ptr(profiles)), plan)
+
+
+def gke_velocity_vorticity(plan, v_eta, mean_uw, nsnap, fields):
+    _check(lib().gke_velocity_vorticity(plan, ptr(v_eta), ptr(mean_uw), nsnap, ptr(fields)), plan)
 
 
 def gke_compute(plan, fields, nsnap, terms, profiles=None):

@@ -52,6 +52,13 @@ struct gke_plan_s {
     int R = 0, Kc = 0;                        // chunk rows and wavenumbers (the largest chunk)
     void* Xc = nullptr;                       // one chunk's gathered operands
     int* dec_tab = nullptr;                   // per chunk: its kz rows, then its coarse rows
+    // Step 1 for velocity-vorticity databases (allocated on first use):
+    // transform buffers of six fields, d2/dy2 weights, the factored Poisson
+    // operators, staging of host inputs and outputs
+    zd *s1_A = nullptr, *s1_B = nullptr, *s1_in = nullptr, *s1_out = nullptr;
+    double *s1_w2 = nullptr, *s1_ab = nullptr, *s1_mean = nullptr;
+    unsigned char* s1_piv = nullptr;
+    bool s1_ready = false;
     std::vector<int> ch_rows, ch_nrows, ch_crs, ch_ncr;   // offsets into dec_tab and counts
     size_t n_acc = 0;                         // elements of the FP64 accumulator comb
     zd *ttw_xd = nullptr, *ttw_zd = nullptr;  // twiddles of the transform sizes
@@ -149,6 +156,33 @@ struct StageScope {
 };
 
 // ------------------------------------------------------------- host helpers
+// Weights of the derivatives of orders 0..M at z0 on the nodes x[0..n), by
+// Fornberg's recursion (B. Fornberg, Math. Comp. 51 (1988) 699-706): c[m*n+i]
+// is the weight of node i in the m-th derivative.
+static void fornberg(const double* x, int n, double z0, int M, double* c)
+{
+    for (int i = 0; i < (M + 1) * n; ++i) c[i] = 0.0;
+    c[0] = 1.0;
+    double c1 = 1.0, c4 = x[0] - z0;
+    for (int i = 1; i < n; ++i) {
+        const int mn = std::min(i, M);
+        double c2 = 1.0;
+        const double c5 = c4;
+        c4 = x[i] - z0;
+        for (int j = 0; j < i; ++j) {
+            const double c3 = x[i] - x[j];
+            c2 *= c3;
+            if (j == i - 1) {
+                for (int m = mn; m >= 1; --m) c[m * n + i] = c1 * (m * c[(m - 1) * n + i - 1] - c5 * c[m * n + i - 1]) / c2;
+                c[i] = -c1 * c5 * c[i - 1] / c2;
+            }
+            for (int m = mn; m >= 1; --m) c[m * n + j] = (c4 * c[m * n + j] - m * c[(m - 1) * n + j]) / c3;
+            c[j] = c4 * c[j] / c3;
+        }
+        c1 = c2;
+    }
+}
+
 // First-derivative weights at z0 on the nodes x[0..n) by Fornberg's recursion
 // (B. Fornberg, Math. Comp. 51 (1988) 699-706), written for derivative
 // orders 0 and 1 only.
@@ -785,6 +819,8 @@ extern "C" void gke_destroy(gke_plan_t p)
         void* extra[] = {p->Xc, p->dec_tab, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
     }
+    void* s1[] = {p->s1_A, p->s1_B, p->s1_in, p->s1_out, p->s1_w2, p->s1_ab, p->s1_mean, p->s1_piv};
+    for (void* q : s1) if (q) cudaFree(q);
     void* ptrs[] = {p->pl32, p->pl64, p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
                     p->fdl0, p->pair_i, p->nonfinite, p->part, p->sep_tab};
@@ -1055,6 +1091,62 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
     CUDA_TRY(p, cudaGetLastError());
     p->snap_count += ns;
     p->have_acc = true;
+    return GKE_OK;
+}
+
+extern "C" gke_status gke_velocity_vorticity(gke_plan_t p, const void* v_eta, const double* mean_uw, int nsnap,
+                                              void* fields)
+{
+    if (!p || !v_eta || !mean_uw || !fields)
+        return p ? fail(p, GKE_ERR_ARG, "v_eta, mean_uw or fields is NULL") : GKE_ERR_ARG;
+    if (nsnap < 1) return fail(p, GKE_ERR_ARG, "nsnap < 1");
+    const gke_desc& d = p->d;
+    const int ny = d.ny;
+    const long long fs = (long long)ny * p->Nk;
+    cudaStream_t st = p->st;
+    if (!p->s1_ready) {
+        // workspaces, the d2/dy2 weights and the factored Poisson operators
+        if (!p->s1_A) CUDA_TRY(p, cudaMalloc((void**)&p->s1_A, (size_t)6 * fs * sizeof(zd)));
+        if (!p->s1_B) CUDA_TRY(p, cudaMalloc((void**)&p->s1_B, (size_t)6 * fs * sizeof(zd)));
+        if (!p->s1_w2) CUDA_TRY(p, cudaMalloc((void**)&p->s1_w2, (size_t)5 * ny * sizeof(double)));
+        if (!p->s1_mean) CUDA_TRY(p, cudaMalloc((void**)&p->s1_mean, (size_t)2 * ny * sizeof(double)));
+        if (!p->s1_piv) CUDA_TRY(p, cudaMalloc((void**)&p->s1_piv, (size_t)fs));
+        if (!p->s1_ab) CUDA_TRY(p, cudaMalloc((void**)&p->s1_ab, s1_band_doubles(ny, p->Nk) * sizeof(double)));
+        std::vector<double> w2(5 * ny), c(3 * 5);
+        for (int j = 0; j < ny; ++j) {
+            const int a = std::min(std::max(j - 2, 0), ny - 5);
+            fornberg(p->y.data() + a, 5, p->y[j], 2, c.data());
+            for (int l = 0; l < 5; ++l) w2[5 * j + l] = c[2 * 5 + l];
+        }
+        CUDA_TRY(p, cudaMemcpy(p->s1_w2, w2.data(), w2.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(p, s1_set_attrs(d.nx, d.nz));
+        p->launches += s1_factor_launch(ny, d.nz, d.nx, d.Lx, d.Lz, p->fdw, p->s1_w2, p->fdl0, p->s1_ab, p->s1_piv,
+                                        st);
+        CUDA_TRY(p, cudaGetLastError());
+        p->s1_ready = true;
+    }
+    const bool din = is_device_ptr(v_eta), dout = is_device_ptr(fields), dmean = is_device_ptr(mean_uw);
+    if (!din && !p->s1_in) CUDA_TRY(p, cudaMalloc((void**)&p->s1_in, (size_t)2 * fs * sizeof(zd)));
+    if (!dout && !p->s1_out) CUDA_TRY(p, cudaMalloc((void**)&p->s1_out, (size_t)4 * fs * sizeof(zd)));
+    for (int s = 0; s < nsnap; ++s) {
+        const zd* in = (const zd*)v_eta + (size_t)s * 2 * fs;
+        if (!din) {
+            CUDA_TRY(p, cudaMemcpyAsync(p->s1_in, in, (size_t)2 * fs * sizeof(zd), cudaMemcpyHostToDevice, st));
+            in = p->s1_in;
+        }
+        CUDA_TRY(p, cudaMemcpyAsync(p->s1_mean, mean_uw + (size_t)s * 2 * ny, (size_t)2 * ny * sizeof(double),
+                                    dmean ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        zd* out = dout ? (zd*)fields + (size_t)s * 4 * fs : p->s1_out;
+        p->launches += s1_snapshot_launch(in, p->s1_mean, ny, d.nz, d.nx, d.Lx, d.Lz, d.nu, p->fdw, p->s1_w2, p->fdl0,
+                                          p->tw_xd, p->tw_zd, p->s1_ab, p->s1_piv, p->s1_A, p->s1_B, out, st);
+        CUDA_TRY(p, cudaGetLastError());
+        if (!dout) {
+            CUDA_TRY(p, cudaMemcpyAsync((zd*)fields + (size_t)s * 4 * fs, p->s1_out, (size_t)4 * fs * sizeof(zd),
+                                        cudaMemcpyDeviceToHost, st));
+            CUDA_TRY(p, cudaStreamSynchronize(st));
+        }
+    }
+    if (!din || !dmean) CUDA_TRY(p, cudaStreamSynchronize(st));
     return GKE_OK;
 }
 

@@ -136,6 +136,16 @@ int combine_launch(bool fp32_in, bool out64, const void* raw, int ny, int nz, in
 // crs: the coarse rows they complete)
 int gather_rows_launch(bool c64, const void* src, int nf, long long Nk, long long per_k, const int* rows, int nrows,
                        int nxh, void* dst, cudaStream_t st);
+// Step 1 for velocity-vorticity databases (gke_step1.cu): the band storage
+// of the factored Poisson operators, shared-memory attributes, the
+// factorisation (once per plan) and the five kernels of one snapshot
+size_t s1_band_doubles(int ny, long long Nk);
+cudaError_t s1_set_attrs(int nx, int nz);
+int s1_factor_launch(int ny, int nz, int nx, double Lx, double Lz, const double* w1, const double* w2, const int* l0,
+                     double* ab, unsigned char* piv, cudaStream_t st);
+int s1_snapshot_launch(const zd* v_eta, const double* mean_uw, int ny, int nz, int nx, double Lx, double Lz,
+                       double nu, const double* w1, const double* w2, const int* l0, const zd* tw_x, const zd* tw_z,
+                       const double* ab, const unsigned char* piv, zd* bufA, zd* bufB, zd* out, cudaStream_t st);
 int combine_fold_launch(bool c64, const void* raw, const int* rows, int nrows, const int* crs, int ncr, int ny,
                         int nz, int nx, int nzd, int nxd, double Lx, double Lz, double nu, const double* prof,
                         unsigned tmask, void* dec, cudaStream_t st);
