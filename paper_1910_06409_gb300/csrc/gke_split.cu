@@ -737,24 +737,32 @@ __global__ void k_corr_edge(const zf* __restrict__ Xop, int ns, int ny, int Nk, 
 // X^H needs X(y', y) with the factor conj(A[s][y']) there; terms whose edge
 // factor is zero for every snapshot are skipped (exact).  With no-slip walls
 // only the pressure term of the phi plane survives.
-__global__ void k_corr_edge_planes(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, int cov,
-                                   unsigned planes, long long npp, const double* __restrict__ prof,
-                                   zf* __restrict__ out)
+__global__ void __launch_bounds__(256)
+k_corr_edge_planes(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int Kc, int cov,
+                   unsigned planes, long long npp, const double* __restrict__ prof, zf* __restrict__ out)
 {
-    __shared__ int nz_edge[NFIELD][4];       // field f has a nonzero value on edge row cov + i (i < 4)
-    const int kl = blockIdx.x, k = k0 + kl;
+    // one warp per wavenumber, eight per CTA
+    __shared__ unsigned s_nz[8][NFIELD];     // bit d: the field is nonzero on edge row cov + d (d < 4)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kl = blockIdx.x * 8 + warp;
+    if (kl >= Kc) return;
+    const int k = k0 + kl;
     const int ne = ny - cov;
-    for (int i = threadIdx.x; i < NFIELD * 4; i += blockDim.x) nz_edge[i / 4][i % 4] = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < NFIELD * ns * ne; i += blockDim.x) {
-        const int f = i / (ns * ne), r = i - f * ns * ne, s = r / ne, d = r - s * ne;
-        const zf v = Xop[(((long long)f * Nk + k) * ns + s) * ny + cov + d];
-        if ((v.x != 0.f || v.y != 0.f) && d < 4) atomicOr(&nz_edge[f][d], 1);
+    for (int f = 0; f < NFIELD; ++f) {
+        unsigned bits = 0;
+        for (int i = lane; i < ns * ne; i += 32) {
+            const int s2 = i / ne, d = i - s2 * ne;
+            const zf v = Xop[(((long long)f * Nk + k) * ns + s2) * ny + cov + d];
+            if ((v.x != 0.f || v.y != 0.f) && d < 4) bits |= 1u << d;
+        }
+        for (int o = 16; o; o >>= 1) bits |= __shfl_xor_sync(0xffffffffu, bits, o);
+        if (lane == 0) s_nz[warp][f] = bits;
     }
-    __syncthreads();
+    __syncwarp();
+    auto nz_edge = [&](int f, int d) -> bool { return (s_nz[warp][f] >> d) & 1u; };
     // edge pairs (y, y'), y <= y', y' in [cov, ny): ne * cov + ne (ne + 1) / 2 of them
     const int n_edge = ne * cov + ne * (ne + 1) / 2;
-    for (int e2 = threadIdx.x; e2 < NPLANE * n_edge; e2 += blockDim.x) {
+    for (int e2 = lane; e2 < NPLANE * n_edge; e2 += 32) {
         const int pl = e2 / n_edge;
         int e = e2 - pl * n_edge;
         if (!((planes >> pl) & 1u)) continue;
@@ -776,8 +784,8 @@ __global__ void k_corr_edge_planes(const zf* __restrict__ Xop, int ns, int ny, i
             // a factor on an edge row that is zero for every snapshot zeroes the term
             const int d = yp - cov, dy = y - cov;
             const bool ye = dy >= 0 && dy < 4;
-            const bool z1 = (d < 4 && !nz_edge[jd.fb[t]][d]) || (ye && !nz_edge[jd.fa[t]][dy]);
-            const bool z2 = (d < 4 && !nz_edge[jd.fa[t]][d]) || (ye && !nz_edge[jd.fb[t]][dy]);
+            const bool z1 = (d < 4 && !nz_edge(jd.fb[t], d)) || (ye && !nz_edge(jd.fa[t], dy));
+            const bool z2 = (d < 4 && !nz_edge(jd.fa[t], d)) || (ye && !nz_edge(jd.fb[t], dy));
             float ar, ai, br, bi;
             if (!z1) {
                 float tr = 0.f, ti = 0.f;
@@ -952,7 +960,7 @@ gke_status split_correlate_planes(SplitWork& w, const zf* Xop, int ns, int ny, i
         k_corr_tc_pipe<1><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);
     *launches = 3;
     if (a.cov < ny) {
-        k_corr_edge_planes<<<Kc, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, a.cov, planes, npp, prof, out);
+        k_corr_edge_planes<<<(Kc + 7) / 8, 256, 0, st>>>(Xop, ns, ny, Nk, k0, Kc, a.cov, planes, npp, prof, out);
         *launches += 1;
     }
     cudaError_t e = cudaGetLastError();

@@ -1138,8 +1138,8 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
         float d1 = 0.f, d2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
-            d1 += w[l] * nb.sg[l] * nb.base[l][nb.mir[l] ? en : e];
-            d2 += w[5 + l] * nb.sg[5 + l] * nb.base[5 + l][nb.mir[5 + l] ? en : e];
+            d1 = fmaf(w[l] * nb.sg[l], nb.base[l][nb.mir[l] ? en : e], d1);
+            d2 = fmaf(w[5 + l] * nb.sg[5 + l], nb.base[5 + l][nb.mir[5 + l] ? en : e], d2);
         }
         const float fy = -nuf * (d2 - d1), fp = -0.5f * nuf * (d1 + d2);
         terms[((long long)T_PHIY * npair + p) * N + e] += fy + oy;
@@ -1177,12 +1177,131 @@ __global__ void k_stencil_res32(float* __restrict__ terms, const float* __restri
         float y1 = 0.f, y2 = 0.f, h1 = 0.f, h2 = 0.f;
         #pragma unroll
         for (int l = 0; l < 5; ++l) {
-            y1 += w[l] * ny_.sg[l] * ny_.base[l][ny_.mir[l] ? en : e];
-            y2 += w[5 + l] * ny_.sg[5 + l] * ny_.base[5 + l][ny_.mir[5 + l] ? en : e];
-            h1 += w[l] * nh_.sg[l] * nh_.base[l][nh_.mir[l] ? en : e];
-            h2 += w[5 + l] * nh_.sg[5 + l] * nh_.base[5 + l][nh_.mir[5 + l] ? en : e];
+            y1 = fmaf(w[l] * ny_.sg[l], ny_.base[l][ny_.mir[l] ? en : e], y1);
+            y2 = fmaf(w[5 + l] * ny_.sg[5 + l], ny_.base[5 + l][ny_.mir[5 + l] ? en : e], y2);
+            h1 = fmaf(w[l] * nh_.sg[l], nh_.base[l][nh_.mir[l] ? en : e], h1);
+            h2 = fmaf(w[5 + l] * nh_.sg[5 + l], nh_.base[5 + l][nh_.mir[5 + l] ? en : e], h2);
         }
-        terms[((long long)T_RES * npair + p) * N + e] += 0.5f * (y2 - y1) + (h1 + h2) + o;
+        terms[((long long)T_RES * npair + p) * N + e] += __fadd_rn(fmaf(0.5f, y2 - y1, h1 + h2), o);
+    }
+}
+
+// Full separation grid (nx a multiple of 4): the same two passes with each
+// thread on four consecutive r_x of one r_z row, so a stored neighbour is
+// one 16-byte load and the row / column indices take no division per value;
+// an r-inverted neighbour reads its four values at -r one by one.
+__device__ __forceinline__ float4 nb_quad(const float* b, bool mir, long long e0, long long enb, int nx, int mx0)
+{
+    if (!mir) return *(const float4*)(b + e0);
+    return make_float4(b[enb + (mx0 == 0 ? 0 : nx - mx0)], b[enb + nx - mx0 - 1], b[enb + nx - mx0 - 2],
+                       b[enb + nx - mx0 - 3]);
+}
+__device__ __forceinline__ void fma4(float4& a, float c, float4 v)
+{
+    a.x = fmaf(c, v.x, a.x); a.y = fmaf(c, v.y, a.y); a.z = fmaf(c, v.z, a.z); a.w = fmaf(c, v.w, a.w);
+}
+__device__ __forceinline__ void add4(float* dst, float4 v)
+{
+    float4 o = *(float4*)dst;
+    o.x += v.x; o.y += v.y; o.z += v.z; o.w += v.w;
+    *(float4*)dst = o;
+}
+
+template <bool WEDGE, int QPT>
+__global__ void __launch_bounds__(256)
+k_stencil_A32q(float* __restrict__ terms, float* __restrict__ spec, long long npair, const int* __restrict__ pair_i,
+               int ny, int nz, int nx, double nu, const int* __restrict__ fdl0, const float* __restrict__ sc)
+{
+    // the pair's 10 neighbour rows of spec[0] (base, weight x sign, inverted?) once per CTA
+    __shared__ const float* s_base[10];
+    __shared__ float s_c[10];
+    __shared__ int s_mir[10];
+    const long long N = (long long)nz * nx;
+    const long long p = blockIdx.x;
+    if (threadIdx.x < 10) {
+        const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+        const int l = threadIdx.x;
+        const int a = l < 5 ? fdl0[i1] + l : i1, b = l < 5 ? i2 : fdl0[i2] + (l - 5);
+        float sg;
+        bool flip;
+        s_base[l] = spec + stored_pair(a, b, ny, WEDGE, 1.f, 1.f, sg, flip) * N;
+        s_c[l] = sc[p * NSC + l] * sg;
+        s_mir[l] = flip;
+    }
+    __syncthreads();
+    const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
+    const float a = -(float)nu, b = -0.5f * (float)nu;
+    #pragma unroll
+    for (int u = 0; u < QPT; ++u) {
+        const long long e0 = (((long long)blockIdx.y * QPT + u) * blockDim.x + threadIdx.x) * 4;
+        if (e0 < N) {
+            const int mz = (int)(e0 / nx), mx0 = (int)(e0 - (long long)mz * nx);
+            const long long enb = (long long)((nz - mz) % nz) * nx;
+            float4 d1 = make_float4(0.f, 0.f, 0.f, 0.f), d2 = d1;
+            #pragma unroll
+            for (int l = 0; l < 5; ++l) {
+                fma4(d1, s_c[l], nb_quad(s_base[l], s_mir[l], e0, enb, nx, mx0));
+                fma4(d2, s_c[5 + l], nb_quad(s_base[5 + l], s_mir[5 + l], e0, enb, nx, mx0));
+            }
+            const float4 fy = make_float4(a * (d2.x - d1.x), a * (d2.y - d1.y), a * (d2.z - d1.z), a * (d2.w - d1.w));
+            const float4 fp = make_float4(b * (d1.x + d2.x), b * (d1.y + d2.y), b * (d1.z + d2.z), b * (d1.w + d2.w));
+            add4(terms + ((long long)T_PHIY * npair + p) * N + e0,
+                 make_float4(fy.x + oy, fy.y + oy, fy.z + oy, fy.w + oy));
+            add4(terms + ((long long)T_PHI * npair + p) * N + e0,
+                 make_float4(fp.x + oh, fp.y + oh, fp.z + oh, fp.w + oh));
+            add4(spec + ((long long)1 * npair + p) * N + e0, fy);
+            add4(spec + ((long long)2 * npair + p) * N + e0, fp);
+        }
+    }
+}
+
+template <bool WEDGE>
+__global__ void __launch_bounds__(256)
+k_stencil_res32q(float* __restrict__ terms, const float* __restrict__ spec, long long npair,
+                 const int* __restrict__ pair_i, int ny, int nz, int nx, const int* __restrict__ fdl0,
+                 const float* __restrict__ sc)
+{
+    // the pair's 20 neighbour rows (base, weight x sign, inverted?) once per CTA
+    __shared__ const float* s_base[20];
+    __shared__ float s_c[20];
+    __shared__ int s_mir[20];
+    const long long N = (long long)nz * nx;
+    const long long p = blockIdx.x;
+    if (threadIdx.x < 20) {
+        const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+        const int h = threadIdx.x / 10, l = threadIdx.x % 10;       // h 0: Phi_y, 1: phi
+        const int a = l < 5 ? fdl0[i1] + l : i1, b = l < 5 ? i2 : fdl0[i2] + (l - 5);
+        float sg;
+        bool flip;
+        const long long q = stored_pair(a, b, ny, WEDGE, h ? 1.f : -1.f, h ? -1.f : 1.f, sg, flip);
+        s_base[threadIdx.x] = spec + ((long long)(1 + h) * npair + q) * N;
+        s_c[threadIdx.x] = sc[p * NSC + l] * sg;
+        s_mir[threadIdx.x] = flip;
+    }
+    __syncthreads();
+    const float o = sc[p * NSC + 12];
+    // 0.5 (d_Y2 - d_Y1) Phi_y + (d_Y1 + d_Y2) phi, in the order of k_stencil_res32
+    // (the a-posteriori separation selection, which runs that kernel, keeps
+    // bit-equal values); two quads per thread
+    #pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const long long e0 = (((long long)blockIdx.y * 2 + u) * blockDim.x + threadIdx.x) * 4;
+        if (e0 < N) {
+            const int mz = (int)(e0 / nx), mx0 = (int)(e0 - (long long)mz * nx);
+            const long long enb = (long long)((nz - mz) % nz) * nx;
+            float4 y1 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = y1, h1 = y1, h2 = y1;
+            #pragma unroll
+            for (int l = 0; l < 5; ++l) {
+                fma4(y1, s_c[l], nb_quad(s_base[l], s_mir[l], e0, enb, nx, mx0));
+                fma4(y2, s_c[5 + l], nb_quad(s_base[5 + l], s_mir[5 + l], e0, enb, nx, mx0));
+                fma4(h1, s_c[10 + l], nb_quad(s_base[10 + l], s_mir[10 + l], e0, enb, nx, mx0));
+                fma4(h2, s_c[15 + l], nb_quad(s_base[15 + l], s_mir[15 + l], e0, enb, nx, mx0));
+            }
+            auto r = [&](float a1, float a2, float b1, float b2) { return __fadd_rn(fmaf(0.5f, a2 - a1, b1 + b2), o); };
+            add4(terms + ((long long)T_RES * npair + p) * N + e0,
+                 make_float4(r(y1.x, y2.x, h1.x, h2.x), r(y1.y, y2.y, h1.y, h2.y), r(y1.z, y2.z, h1.z, h2.z),
+                             r(y1.w, y2.w, h1.w, h2.w)));
+        }
     }
 }
 
@@ -1204,6 +1323,15 @@ static int stencil_launch_t(bool fp32, void* terms, float* spec, long long npair
     }
     float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
     k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
+    if (!US && sm.nx % 4 == 0 && ((uintptr_t)terms & 15u) == 0) {
+        // one quad per thread in pass 1, two in pass 2 (its 20 neighbour rows)
+        dim3 g1((unsigned)npair, (unsigned)((N / 4 + 255) / 256)), g2((unsigned)npair, (unsigned)((N / 4 + 511) / 512));
+        k_stencil_A32q<WEDGE, 1><<<g1, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, nu, fdl0,
+                                                     sc);
+        if (!pass2) return 2;
+        k_stencil_res32q<WEDGE><<<g2, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, fdl0, sc);
+        return 3;
+    }
     dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
     k_stencil_A32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, nu, fdl0, sc);
     if (!pass2) return 2;
