@@ -32,31 +32,36 @@ template <typename TF> __device__ __forceinline__ cplx<TF> cvt(zd v) { return mk
 
 // ---------------------------------------------- linear fields -> operands
 // Xop[f][k][s][y] = fields[s][f][y][k] - mean_f(y) [k == 0], f = u, v, w, p.
-// 32x32 (k, y) tile transpose through shared memory; flags non-finite input.
+// Tile of 32 wavenumbers x one y chunk (the ny rows split into equal chunks
+// of at most ll_rows: 34 KB of shared memory) transposed through shared
+// memory in TF; flags non-finite input.
+template <typename TF> __host__ __device__ constexpr int ll_rows() { return sizeof(TF) == 4 ? 128 : 64; }
 template <typename TF>
-__global__ void k_load_linear(const zd* __restrict__ fields, int ns, int ny, int Nk,
-                              const double* __restrict__ mean, cplx<TF>* __restrict__ Xop,
-                              int* __restrict__ nonfinite)
+__global__ void __launch_bounds__(256)
+k_load_linear(const zd* __restrict__ fields, int ns, int ny, int Nk, int rows,
+              const double* __restrict__ mean, cplx<TF>* __restrict__ Xop, int* __restrict__ nonfinite)
 {
-    __shared__ zd tile[32][33];
-    const int k0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    __shared__ cplx<TF> tile[ll_rows<TF>()][33];
+    const int k0 = blockIdx.x * 32, y0 = blockIdx.y * rows;
     const int s = blockIdx.z / 4, f = blockIdx.z % 4;
+    const int nr = min(rows, ny - y0);
     int bad = 0;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int y = y0 + r, k = k0 + threadIdx.x;
-        if (y < ny && k < Nk) {
+    for (int r = threadIdx.y; r < nr; r += blockDim.y) {
+        const int y = y0 + r, k = k0 + threadIdx.x;
+        if (k < Nk) {
             zd v = fields[(((long long)s * 4 + f) * ny + y) * Nk + k];
             if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
             if (k == 0) v.x -= mean[f * ny + y];
-            tile[r][threadIdx.x] = v;
+            tile[r][threadIdx.x] = cvt<TF>(v);
         }
     }
     if (bad) atomicOr(nonfinite, 1);
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        int k = k0 + r, y = y0 + threadIdx.x;
-        if (y < ny && k < Nk)
-            Xop[(((long long)f * Nk + k) * ns + s) * ny + y] = cvt<TF>(tile[threadIdx.x][r]);
+    for (int kk = threadIdx.y; kk < 32; kk += blockDim.y) {
+        const int k = k0 + kk;
+        if (k >= Nk) break;
+        cplx<TF>* dst = Xop + (((long long)f * Nk + k) * ns + s) * ny + y0;
+        for (int r = threadIdx.x; r < nr; r += 32) dst[r] = tile[r][kk];
     }
 }
 
@@ -449,8 +454,11 @@ int products_launch(const ProdArgs& a)
     cudaStream_t st = a.st;
     C* Xop = (C*)a.Xop;
     int launches = 0;
-    k_load_linear<TF><<<dim3((Nk + 31) / 32, (ny + 31) / 32, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk,
-                                                                                           a.mean, Xop, a.nonfinite);
+    {
+        const int nch = (ny + ll_rows<TF>() - 1) / ll_rows<TF>(), rows = (ny + nch - 1) / nch;
+        k_load_linear<TF><<<dim3((Nk + 31) / 32, nch, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk, rows,
+                                                                                      a.mean, Xop, a.nonfinite);
+    }
     ++launches;
     // With a second stream and second G, H, part buffers, snapshot s runs on
     // stream s % 2, so the transforms of two snapshots overlap; the row sums
@@ -564,7 +572,7 @@ cudaError_t products_set_attrs(int lim)
 
 // explicit instantiations
 #define GKE_INST(TF)                                                                                       \
-    template __global__ void k_load_linear<TF>(const zd*, int, int, int, const double*, cplx<TF>*, int*);  \
+    template __global__ void k_load_linear<TF>(const zd*, int, int, int, int, const double*, cplx<TF>*, int*);  \
     template __global__ void k_col_inverse<TF>(const zd*, int, int, int, int, const double*,               \
                                                const cplx<TF>*, cplx<TF>*);                                \
     template __global__ void k_row_products<TF>(const cplx<TF>*, int, int, int, int, const cplx<TF>*,      \

@@ -1207,52 +1207,34 @@ __device__ __forceinline__ void add4(float* dst, float4 v)
     *(float4*)dst = o;
 }
 
-template <bool WEDGE, int QPT>
+template <bool WEDGE>
 __global__ void __launch_bounds__(256)
 k_stencil_A32q(float* __restrict__ terms, float* __restrict__ spec, long long npair, const int* __restrict__ pair_i,
                int ny, int nz, int nx, double nu, const int* __restrict__ fdl0, const float* __restrict__ sc)
 {
-    // the pair's 10 neighbour rows of spec[0] (base, weight x sign, inverted?) once per CTA
-    __shared__ const float* s_base[10];
-    __shared__ float s_c[10];
-    __shared__ int s_mir[10];
     const long long N = (long long)nz * nx;
     const long long p = blockIdx.x;
-    if (threadIdx.x < 10) {
-        const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
-        const int l = threadIdx.x;
-        const int a = l < 5 ? fdl0[i1] + l : i1, b = l < 5 ? i2 : fdl0[i2] + (l - 5);
-        float sg;
-        bool flip;
-        s_base[l] = spec + stored_pair(a, b, ny, WEDGE, 1.f, 1.f, sg, flip) * N;
-        s_c[l] = sc[p * NSC + l] * sg;
-        s_mir[l] = flip;
+    const long long e0 = ((long long)blockIdx.y * blockDim.x + threadIdx.x) * 4;
+    if (e0 >= N) return;
+    const int i1 = pair_i[2 * p], i2 = pair_i[2 * p + 1];
+    Nb nb;
+    make_nb<WEDGE>(nb, spec, 1.f, 1.f, i1, i2, fdl0[i1], fdl0[i2], ny, N);
+    const int mz = (int)(e0 / nx), mx0 = (int)(e0 - (long long)mz * nx);
+    const long long enb = (long long)((nz - mz) % nz) * nx;
+    float4 d1 = make_float4(0.f, 0.f, 0.f, 0.f), d2 = d1;
+    #pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        fma4(d1, sc[p * NSC + l] * nb.sg[l], nb_quad(nb.base[l], nb.mir[l], e0, enb, nx, mx0));
+        fma4(d2, sc[p * NSC + 5 + l] * nb.sg[5 + l], nb_quad(nb.base[5 + l], nb.mir[5 + l], e0, enb, nx, mx0));
     }
-    __syncthreads();
     const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
     const float a = -(float)nu, b = -0.5f * (float)nu;
-    #pragma unroll
-    for (int u = 0; u < QPT; ++u) {
-        const long long e0 = (((long long)blockIdx.y * QPT + u) * blockDim.x + threadIdx.x) * 4;
-        if (e0 < N) {
-            const int mz = (int)(e0 / nx), mx0 = (int)(e0 - (long long)mz * nx);
-            const long long enb = (long long)((nz - mz) % nz) * nx;
-            float4 d1 = make_float4(0.f, 0.f, 0.f, 0.f), d2 = d1;
-            #pragma unroll
-            for (int l = 0; l < 5; ++l) {
-                fma4(d1, s_c[l], nb_quad(s_base[l], s_mir[l], e0, enb, nx, mx0));
-                fma4(d2, s_c[5 + l], nb_quad(s_base[5 + l], s_mir[5 + l], e0, enb, nx, mx0));
-            }
-            const float4 fy = make_float4(a * (d2.x - d1.x), a * (d2.y - d1.y), a * (d2.z - d1.z), a * (d2.w - d1.w));
-            const float4 fp = make_float4(b * (d1.x + d2.x), b * (d1.y + d2.y), b * (d1.z + d2.z), b * (d1.w + d2.w));
-            add4(terms + ((long long)T_PHIY * npair + p) * N + e0,
-                 make_float4(fy.x + oy, fy.y + oy, fy.z + oy, fy.w + oy));
-            add4(terms + ((long long)T_PHI * npair + p) * N + e0,
-                 make_float4(fp.x + oh, fp.y + oh, fp.z + oh, fp.w + oh));
-            add4(spec + ((long long)1 * npair + p) * N + e0, fy);
-            add4(spec + ((long long)2 * npair + p) * N + e0, fp);
-        }
-    }
+    const float4 fy = make_float4(a * (d2.x - d1.x), a * (d2.y - d1.y), a * (d2.z - d1.z), a * (d2.w - d1.w));
+    const float4 fp = make_float4(b * (d1.x + d2.x), b * (d1.y + d2.y), b * (d1.z + d2.z), b * (d1.w + d2.w));
+    add4(terms + ((long long)T_PHIY * npair + p) * N + e0, make_float4(fy.x + oy, fy.y + oy, fy.z + oy, fy.w + oy));
+    add4(terms + ((long long)T_PHI * npair + p) * N + e0, make_float4(fp.x + oh, fp.y + oh, fp.z + oh, fp.w + oh));
+    add4(spec + ((long long)1 * npair + p) * N + e0, fy);
+    add4(spec + ((long long)2 * npair + p) * N + e0, fp);
 }
 
 template <bool WEDGE>
@@ -1324,10 +1306,10 @@ static int stencil_launch_t(bool fp32, void* terms, float* spec, long long npair
     float* sc = spec + (size_t)3 * npair * N;      // per-pair scalars after the three spectral parts
     k_stencil_pairs<<<(unsigned)((npair + 127) / 128), 128, 0, st>>>(pair_i, npair, ny, nu, fdw, fdl0, prof, sc);
     if (!US && sm.nx % 4 == 0 && ((uintptr_t)terms & 15u) == 0) {
-        // one quad per thread in pass 1, two in pass 2 (its 20 neighbour rows)
+        // one quad per thread in pass 1, two in pass 2 (its 20 neighbour rows
+        // resolved once per CTA)
         dim3 g1((unsigned)npair, (unsigned)((N / 4 + 255) / 256)), g2((unsigned)npair, (unsigned)((N / 4 + 511) / 512));
-        k_stencil_A32q<WEDGE, 1><<<g1, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, nu, fdl0,
-                                                     sc);
+        k_stencil_A32q<WEDGE><<<g1, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, nu, fdl0, sc);
         if (!pass2) return 2;
         k_stencil_res32q<WEDGE><<<g2, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, fdl0, sc);
         return 3;
