@@ -616,14 +616,14 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
             p->fold_owned = true;
         }
         p->tsz = f32 ? sizeof(float) : sizeof(double);
-        if (f32) ALLOC(p->spec, (size_t)3 * p->npair * p->nxt * p->nzt + 13 * (size_t)p->npair);
+        if (f32) ALLOC(p->spec, (size_t)3 * p->npair * p->nxt * p->nzt + 15 * (size_t)p->npair);
     } else if (p->planes) {
         // the six plane spectra of one batch, [NPLANE][Nk][npp]
         p->Kc = Nk;
         p->npp = 4 * ((p->npair_tri + 3) / 4);
         p->n_acc = (size_t)NPLANE * Nk * p->npp;
         ALLOC(p->pl32, p->n_acc);
-        ALLOC(p->spec, (size_t)3 * p->npair * nrx * nrz + 13 * (size_t)p->npair);
+        ALLOC(p->spec, (size_t)3 * p->npair * nrx * nrz + 15 * (size_t)p->npair);
         p->tsz = sizeof(float);
     } else {
     p->Kc = Nk;
@@ -639,8 +639,8 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     }
     if (f32) {
         ALLOC(p->comb32, (size_t)p->npair_tri * NTERM * Nk);
-        // spectral parts of A, Phi_y, phi, then 13 per-pair stencil scalars
-        ALLOC(p->spec, (size_t)3 * p->npair * nrx * nrz + 13 * (size_t)p->npair);
+        // spectral parts of A, Phi_y, phi, then 15 per-pair stencil scalars
+        ALLOC(p->spec, (size_t)3 * p->npair * nrx * nrz + 15 * (size_t)p->npair);
         p->tsz = sizeof(float);
     } else {
         ALLOC(p->comb, (size_t)p->npair_tri * NTERM * Nk);

@@ -125,8 +125,10 @@ __device__ __forceinline__ void onepoint(const double* __restrict__ pr, int ny, 
 
 // ------------------------------ row pass: C2R along x + one-point parts
 // terms[t][p][z][x] = inv_count sum_kx W[pl][t][z][kx] e^{+i kx x} + onepoint_t(Y1, Y2),
-// stored as TO.  With spec != NULL the spectral parts of A, Phi_y and phi
-// (the terms the Step-3 stencils difference) also go to spec[3][p][z][x].
+// stored as TO.  With spec != NULL (the FP32 path) the spectral parts of A,
+// Phi_y and phi (the terms the Step-3 stencils difference) go to
+// spec[3][p][z][x], and Phi_y and phi go there only: the first stencil pass
+// writes those two terms.
 // Terms are transformed two at a time (t0 + i t1).  CTA = RZ rows of one pair;
 // shared memory (1 + 8 RZ) nx complex.
 template <typename TF, typename TO>
@@ -176,7 +178,7 @@ __global__ void k_terms_rowpass(const cplx<TF>* __restrict__ W, const int* __res
         C v = sh[(r * 4 + (q >> 1)) * nx + x];
         const TF sp = ((q & 1) ? v.y : v.x) * (TF)inv_count;
         const long long e = (long long)(z0 + r) * sm.nrx + xr;
-        terms[((long long)q * npair + p) * N + e] = (TO)(sp + s_one[q]);
+        if (spec == nullptr || (q != T_PHIY && q != T_PHI)) terms[((long long)q * npair + p) * N + e] = (TO)(sp + s_one[q]);
         if (spec != nullptr) {
             const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
             if (si >= 0) spec[((long long)si * npair + p) * N + e] = (float)sp;
@@ -245,7 +247,8 @@ k_terms_rowpass_r(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i
                     if (q >= NTERM) break;
                     if (!(h ? hb : ha)) continue;
                     const TF sp = (h ? v[m].y : v[m].x) * ic;
-                    st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[q]));
+                    if (spec == nullptr || (q != T_PHIY && q != T_PHI))
+                        st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[q]));
                     if (spec != nullptr) {
                         const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
                         if (si >= 0) st_stream(spec + ((long long)si * npair + p) * NN + e, (float)sp);
@@ -568,105 +571,6 @@ k_terms_colpass_pt(PlaneCols pc, long long pair0, long long npair, long long pch
     }
 }
 
-// row pass from Wp: CTA = 16 consecutive pairs x one kept z row, N2 lanes per
-// pair; the seven terms as four packed sequences (t0 + i t1), outputs staged
-// per term pair in shared memory, then written pair row by pair row
-constexpr int RZ_PT = 4;           // z rows per CTA of k_terms_rowpass_pt
-template <typename TF, typename TO, int N1, int N2, bool US, int RZ = RZ_PT>
-__global__ void __launch_bounds__(N1 * N2)
-k_terms_rowpass_pt(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0, long long npair,
-                   long long pchunk, int ny, double inv_count, const double* __restrict__ prof,
-                   const cplx<TF>* __restrict__ tw_x, SepMap sm, unsigned tmask, TO* __restrict__ terms,
-                   float* __restrict__ spec)
-{
-    typedef cplx<TF> C;
-    constexpr int N = N1 * N2, nxh = N / 2 + 1, CW = 16;
-    extern __shared__ __align__(16) unsigned char sh_raw_rpt[];
-    C* stw = (C*)sh_raw_rpt;
-    C* xs = stw + N;                                  // exchange: N1 (N2 CW + 1)
-    TF* ot = (TF*)xs;                                 // staged outputs [2][CW][N + 1], in the exchange buffer
-    static_assert(2 * CW * (N + 1) * sizeof(TF) <= N1 * (N2 * CW + 1) * sizeof(C), "staging fits the exchange buffer");
-    __shared__ TF s_one[CW][NTERM];
-    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
-    const long long pl0 = (long long)blockIdx.x * CW, pl = pl0 + c, p = pair0 + pl;
-    const bool live = p < npair && pl < pchunk;
-    const int nz = sm.nrz, nrx = US ? sm.nrx : N;
-    load_twiddles(stw, tw_x, N);
-    if (threadIdx.x < CW) {
-        const long long pp = pair0 + pl0 + threadIdx.x;
-        double one[NTERM] = {0, 0, 0, 0, 0, 0, 0};
-        if (pp < npair && pl0 + threadIdx.x < pchunk) onepoint(prof, ny, pair_i[2 * pp], pair_i[2 * pp + 1], one);
-        for (int t = 0; t < NTERM; ++t) s_one[threadIdx.x][t] = (TF)one[t];
-    }
-    const TF ic = (TF)inv_count;
-    const long long NN = (long long)nz * nrx;
-    const long long tstride = (long long)nz * nxh * pchunk;
-    // output column of this thread and the CTA's live pairs
-    const int xo = US ? sm.xcol(threadIdx.x) : (int)threadIdx.x;
-    const int nlive = (int)min((long long)CW, min(npair - (pair0 + pl0), pchunk - pl0));
-    // RZ consecutive kept z rows per CTA: each pair's outputs are RZ rows in a row
-    for (int zr = blockIdx.y * RZ; zr < min(nz, blockIdx.y * RZ + RZ); ++zr) {
-    const long long orow = (long long)zr * nrx + xo;
-    const C* wrow = W + (long long)zr * nxh * pchunk + pl;
-    for (int jq = 0; jq < 4; ++jq) {
-        const int ta = 2 * jq, tb = 2 * jq + 1;
-        const bool ha = (tmask >> ta) & 1u, hb = tb < NTERM && ((tmask >> tb) & 1u);
-        if (!ha && !hb) continue;                   // uniform over the CTA
-        const C* wa = wrow + ta * tstride;
-        const C* wb = wrow + (tb < NTERM ? tb : ta) * tstride;
-        C v[N1];
-        #pragma unroll
-        for (int m = 0; m < N1; ++m) {
-            const int k = lane + N2 * m;
-            C A = mk((TF)0, (TF)0), B = A;           // terms outside tmask: zero, not stale W
-            if (live) {
-                // kx above nx/2 reads its mirror row (Hermitian extension): plain
-                // loads, so the second read of a line hits L1
-                const long long off = (long long)(k < nxh ? k : N - k) * pchunk;
-                if (ha) A = wa[off];
-                if (hb) B = wb[off];
-                if (k >= nxh) { A.y = -A.y; B.y = -B.y; }
-            }
-            if (k == 0 || 2 * k == N) { A.y = 0; B.y = 0; }
-            v[m] = mk(A.x - B.y, A.y + B.x);
-        }
-        __syncthreads();                     // exchange and staging buffers free (s_one, twiddles ready)
-        fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
-        __syncthreads();                     // the exchange buffer now stages the outputs
-        #pragma unroll
-        for (int m = 0; m < N1; ++m) {
-            const int x = lane + N2 * m;
-            ot[c * (N + 1) + x] = v[m].x;
-            ot[(CW + c) * (N + 1) + x] = v[m].y;
-        }
-        __syncthreads();
-        // pair rows: thread = separation index x (blockDim = N), so each pair's
-        // row leaves as one contiguous store across the CTA
-        if (xo >= 0) {
-            #pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                const int q = 2 * jq + h;
-                if (q >= NTERM || !(h ? hb : ha)) continue;
-                const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
-                TO* tp = terms + ((long long)q * npair + pair0 + pl0) * NN + orow;
-                float* sq = (spec != nullptr && si >= 0) ? spec + ((long long)si * npair + pair0 + pl0) * NN + orow
-                                                          : nullptr;
-                const TF* src = ot + h * CW * (N + 1) + threadIdx.x;
-                #pragma unroll
-                for (int cc = 0; cc < CW; ++cc) {
-                    if (cc < nlive) {
-                        const TF sp = src[cc * (N + 1)] * ic;
-                        st_stream(tp + cc * NN, (TO)(sp + s_one[cc][q]));
-                        if (sq) st_stream(sq + cc * NN, (float)sp);
-                    }
-                }
-            }
-        }
-    }
-    }
-}
-
-
 // row pass from Wp, four pairs per sequence group: CTA = 4 consecutive pairs x
 // N2 lanes x 4 kept z rows (256 threads); a warp holds 4 pairs x 8 lanes of one
 // row, so its loads of Wp (4 pairs at 8 kx) and its stores of the terms (4
@@ -674,7 +578,7 @@ k_terms_rowpass_pt(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_
 // regions of the (row, pair) sequences are 4 mod 16 complex values apart, so
 // a half-warp (4 pairs x 4 lanes) hits 16 distinct bank pairs.
 template <typename TF, typename TO, int N1, int N2, bool US>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_terms_rowpass_p4(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_i, long long pair0,
                    long long npair, long long pchunk, int ny, double inv_count, const double* __restrict__ prof,
                    const cplx<TF>* __restrict__ tw_x, SepMap sm, unsigned tmask, TO* __restrict__ terms,
@@ -742,7 +646,8 @@ k_terms_rowpass_p4(const cplx<TF>* __restrict__ W, const int* __restrict__ pair_
                     if (q >= NTERM) break;
                     if (!(h ? hb : ha)) continue;
                     const TF sp = (h ? v[m].y : v[m].x) * ic;
-                    st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[c][q]));
+                    if (spec == nullptr || (q != T_PHIY && q != T_PHI))
+                        st_stream(terms + ((long long)q * npair + p) * NN + e, (TO)(sp + s_one[c][q]));
                     if (spec != nullptr) {
                         const int si = (q == T_A) ? 0 : (q == T_PHIY) ? 1 : (q == T_PHI) ? 2 : -1;
                         if (si >= 0) st_stream(spec + ((long long)si * npair + p) * NN + e, (float)sp);
@@ -763,7 +668,7 @@ static void colpass_planes_launch(const TermArgs& a, long long p0, long long np,
         const int nxh = a.nx / 2 + 1;
         PlaneCols pc{a.planes, a.npp, a.Kc, a.pair_i, a.prof, a.ny, a.Lx, a.Lz, a.nu};
         if (a.nz == 256 && a.nx == 256) {
-            // pair-contiguous W (k_terms_rowpass_pt reads it)
+            // pair-contiguous W (k_terms_rowpass_p4 reads it)
             const dim3 g((unsigned)((np + 15) / 16), nxh);
             const size_t sh = (256 + 16 * (16 * 16 + 1)) * sizeof(C);
             if (us)
@@ -930,8 +835,6 @@ cudaError_t terms_set_attrs(int lim)
                         (const void*)k_terms_colpass_pt<float, double, 16, 16, false>,
                         (const void*)k_terms_colpass_pt<float, float, 16, 16, true>,
                         (const void*)k_terms_colpass_pt<float, double, 16, 16, true>,
-                        (const void*)k_terms_rowpass_pt<float, float, 16, 16, false>,
-                        (const void*)k_terms_rowpass_pt<float, float, 16, 16, true>,
                         (const void*)k_terms_rowpass_p4<float, float, 16, 16, false>,
                         (const void*)k_terms_rowpass_p4<float, float, 16, 16, true>};
     cudaError_t e = cudaSuccess;
@@ -1054,9 +957,11 @@ __device__ __forceinline__ void op_final(const double* pr, int ny, double nu, co
 // Per-pair scalars of the split stencils, computed once in FP64:
 //   sc[p] = { w1[0..5), w2[0..5) (FP32 copies of the FD weights of rows i1, i2),
 //             -nu (d_Y2 - d_Y1) A1, -(nu/2) (d_Y1 + d_Y2) A1,
-//             (d_Y2 - d_Y1) Phi_y1 / 2 + (d_Y1 + d_Y2) phi1 }
+//             (d_Y2 - d_Y1) Phi_y1 / 2 + (d_Y1 + d_Y2) phi1,
+//             the one-point parts of Phi_y and phi that the row pass adds
+//             to the other terms }
 // with A1, Phi_y1, phi1 the one-point parts (FD parts included).
-constexpr int NSC = 13;
+constexpr int NSC = 15;
 __global__ void k_stencil_pairs(const int* __restrict__ pair_i, long long npair, int ny, double nu,
                                 const double* __restrict__ fdw, const int* __restrict__ fdl0,
                                 const double* __restrict__ prof, float* __restrict__ sc)
@@ -1083,6 +988,10 @@ __global__ void k_stencil_pairs(const int* __restrict__ pair_i, long long npair,
     sc[p * NSC + 10] = (float)(-nu * (d2 - d1));
     sc[p * NSC + 11] = (float)(-0.5 * nu * (d1 + d2));
     sc[p * NSC + 12] = (float)(0.5 * (y2 - y1) + (h1 + h2));
+    double one[NTERM];
+    onepoint(prof, ny, i1, i2, one);
+    sc[p * NSC + 13] = (float)one[T_PHIY];
+    sc[p * NSC + 14] = (float)one[T_PHI];
 }
 
 constexpr int SPT = 4;   // separations per thread in the split stencils
@@ -1110,13 +1019,15 @@ __device__ __forceinline__ void make_nb(Nb& nb, const float* f, float rho, float
 }
 
 // pass 1, FP32: with S = spectral part of A (spec[0]),
-//   Phi_y += -nu (d_Y2 - d_Y1)(S + A1),  phi += -(nu/2) (d_Y1 + d_Y2)(S + A1);
-// spec[1], spec[2] (spectral parts of Phi_y, phi) receive the FD parts of S.
+//   Phi_y = spec[1] + one-point + -nu (d_Y2 - d_Y1)(S + A1),
+//   phi = spec[2] + one-point + -(nu/2) (d_Y1 + d_Y2)(S + A1)
+// (written for the terms in tmask); spec[1], spec[2] (spectral parts of
+// Phi_y, phi) receive the FD parts of S.
 // grid (npair, separation chunks of 256 SPT).
 template <bool WEDGE, bool US>
 __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spec, long long npair,
                               const int* __restrict__ pair_i, int ny, SepMap sm, double nu,
-                              const int* __restrict__ fdl0, const float* __restrict__ sc)
+                              const int* __restrict__ fdl0, const float* __restrict__ sc, unsigned tmask)
 {
     const long long N = (long long)sm.nrz * sm.nrx;
     const long long p = blockIdx.x;
@@ -1141,11 +1052,16 @@ __global__ void k_stencil_A32(float* __restrict__ terms, float* __restrict__ spe
             d1 = fmaf(w[l] * nb.sg[l], nb.base[l][nb.mir[l] ? en : e], d1);
             d2 = fmaf(w[5 + l] * nb.sg[5 + l], nb.base[5 + l][nb.mir[5 + l] ? en : e], d2);
         }
-        const float fy = -nuf * (d2 - d1), fp = -0.5f * nuf * (d1 + d2);
-        terms[((long long)T_PHIY * npair + p) * N + e] += fy + oy;
-        terms[((long long)T_PHI * npair + p) * N + e] += fp + oh;
-        spec[((long long)1 * npair + p) * N + e] += fy;
-        spec[((long long)2 * npair + p) * N + e] += fp;
+        // products rounded on their own (no contraction into the sums below),
+        // as in k_stencil_A32q, so the two kernels give bit-equal values
+        const float fy = __fmul_rn(-nuf, d2 - d1), fp = __fmul_rn(-0.5f * nuf, d1 + d2);
+        float* s1 = spec + ((long long)1 * npair + p) * N + e;
+        float* s2 = spec + ((long long)2 * npair + p) * N + e;
+        const float v1 = *s1, v2 = *s2;
+        if ((tmask >> T_PHIY) & 1u) terms[((long long)T_PHIY * npair + p) * N + e] = (v1 + sc[p * NSC + 13]) + (fy + oy);
+        if ((tmask >> T_PHI) & 1u) terms[((long long)T_PHI * npair + p) * N + e] = (v2 + sc[p * NSC + 14]) + (fp + oh);
+        *s1 = v1 + fy;
+        *s2 = v2 + fp;
     }
 }
 
@@ -1210,7 +1126,8 @@ __device__ __forceinline__ void add4(float* dst, float4 v)
 template <bool WEDGE>
 __global__ void __launch_bounds__(256)
 k_stencil_A32q(float* __restrict__ terms, float* __restrict__ spec, long long npair, const int* __restrict__ pair_i,
-               int ny, int nz, int nx, double nu, const int* __restrict__ fdl0, const float* __restrict__ sc)
+               int ny, int nz, int nx, double nu, const int* __restrict__ fdl0, const float* __restrict__ sc,
+               unsigned tmask)
 {
     const long long N = (long long)nz * nx;
     const long long p = blockIdx.x;
@@ -1229,12 +1146,24 @@ k_stencil_A32q(float* __restrict__ terms, float* __restrict__ spec, long long np
     }
     const float oy = sc[p * NSC + 10], oh = sc[p * NSC + 11];
     const float a = -(float)nu, b = -0.5f * (float)nu;
-    const float4 fy = make_float4(a * (d2.x - d1.x), a * (d2.y - d1.y), a * (d2.z - d1.z), a * (d2.w - d1.w));
-    const float4 fp = make_float4(b * (d1.x + d2.x), b * (d1.y + d2.y), b * (d1.z + d2.z), b * (d1.w + d2.w));
-    add4(terms + ((long long)T_PHIY * npair + p) * N + e0, make_float4(fy.x + oy, fy.y + oy, fy.z + oy, fy.w + oy));
-    add4(terms + ((long long)T_PHI * npair + p) * N + e0, make_float4(fp.x + oh, fp.y + oh, fp.z + oh, fp.w + oh));
-    add4(spec + ((long long)1 * npair + p) * N + e0, fy);
-    add4(spec + ((long long)2 * npair + p) * N + e0, fp);
+    const float4 fy = make_float4(__fmul_rn(a, d2.x - d1.x), __fmul_rn(a, d2.y - d1.y), __fmul_rn(a, d2.z - d1.z),
+                                  __fmul_rn(a, d2.w - d1.w));
+    const float4 fp = make_float4(__fmul_rn(b, d1.x + d2.x), __fmul_rn(b, d1.y + d2.y), __fmul_rn(b, d1.z + d2.z),
+                                  __fmul_rn(b, d1.w + d2.w));
+    float4* s1 = (float4*)(spec + ((long long)1 * npair + p) * N + e0);
+    float4* s2 = (float4*)(spec + ((long long)2 * npair + p) * N + e0);
+    const float4 v1 = *s1, v2 = *s2;
+    const float ty = sc[p * NSC + 13], th = sc[p * NSC + 14];
+    if ((tmask >> T_PHIY) & 1u)
+        *(float4*)(terms + ((long long)T_PHIY * npair + p) * N + e0) =
+            make_float4((v1.x + ty) + (fy.x + oy), (v1.y + ty) + (fy.y + oy), (v1.z + ty) + (fy.z + oy),
+                        (v1.w + ty) + (fy.w + oy));
+    if ((tmask >> T_PHI) & 1u)
+        *(float4*)(terms + ((long long)T_PHI * npair + p) * N + e0) =
+            make_float4((v2.x + th) + (fp.x + oh), (v2.y + th) + (fp.y + oh), (v2.z + th) + (fp.z + oh),
+                        (v2.w + th) + (fp.w + oh));
+    *s1 = make_float4(v1.x + fy.x, v1.y + fy.y, v1.z + fy.z, v1.w + fy.w);
+    *s2 = make_float4(v2.x + fp.x, v2.y + fp.y, v2.z + fp.z, v2.w + fp.w);
 }
 
 template <bool WEDGE>
@@ -1309,13 +1238,14 @@ static int stencil_launch_t(bool fp32, void* terms, float* spec, long long npair
         // one quad per thread in pass 1, two in pass 2 (its 20 neighbour rows
         // resolved once per CTA)
         dim3 g1((unsigned)npair, (unsigned)((N / 4 + 255) / 256)), g2((unsigned)npair, (unsigned)((N / 4 + 511) / 512));
-        k_stencil_A32q<WEDGE><<<g1, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, nu, fdl0, sc);
+        k_stencil_A32q<WEDGE><<<g1, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, nu, fdl0, sc,
+                                                  tmask);
         if (!pass2) return 2;
         k_stencil_res32q<WEDGE><<<g2, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm.nz, sm.nx, fdl0, sc);
         return 3;
     }
     dim3 g32((unsigned)npair, (unsigned)((N + 256 * SPT - 1) / (256 * SPT)));
-    k_stencil_A32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, nu, fdl0, sc);
+    k_stencil_A32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, nu, fdl0, sc, tmask);
     if (!pass2) return 2;
     k_stencil_res32<WEDGE, US><<<g32, 256, 0, st>>>((float*)terms, spec, npair, pair_i, ny, sm, fdl0, sc);
     return 3;
