@@ -142,7 +142,7 @@ k_col_inverse_r(const zd* __restrict__ fields_s, int ny, int nxh, int CW, const 
 // operand stores (y contiguous) and the loads (kx contiguous) both come in
 // runs of 32 bytes or more
 template <typename TF, int N1, int N2>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(512)
 k_col_forward_r(const cplx<TF>* __restrict__ H, int ny, int nxh, int CW, int YB, int s, int ns,
                 const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ Xop)
 {
@@ -513,7 +513,9 @@ int products_launch(const ProdArgs& a)
         k_reduce_partials<<<(6 * ny + 127) / 128, 128, 0, st>>>(part, 6 * ny, nrb, a.stats);
         if (two) cudaEventRecord(ev_red[b], st);
         if (nz == 256) {
-            constexpr int CWR = 4, YBR = 4;
+            // FP32: 8 planes per CTA (the operand stores come in 64-byte runs);
+            // FP64 keeps 4 (its exchange buffer would hold one CTA per SM)
+            constexpr int CWR = 4, YBR = sizeof(TF) == 4 ? 8 : 4;
             k_col_forward_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, (ny + YBR - 1) / YBR, 7), CWR * YBR * 16,
                                           (256 + 16 * (16 * CWR * YBR + 1)) * sizeof(C), ss>>>(
                 (const C*)H, ny, nxh, CWR, YBR, s, ns, (const C*)a.tw_z, Xop);
