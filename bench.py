@@ -78,7 +78,7 @@ def correlator_cmac(wl, ns):
 # null (not captured since its kernels changed).
 NCU_TRAFFIC_GB = {
     "f64": {"correlate": 96.7, "combine": 93.0, "terms": 104.1, "stencil": 37.9, "products": 33.1},
-    "bf16x3": {"correlate": 36.7, "terms": 59.5, "stencil": 25.0, "products": 22.3},
+    "bf16x3": {"correlate": 36.7, "products": 22.3},
 }
 
 
@@ -111,10 +111,14 @@ def stage_rooflines(wl, ns, precision, stage_ms, pk, pk_kind):
     # no combine stage; the transforms read the planes
     planes = precision == "bf16x3" and (ny <= 128 or ny == 129)
     pl_bytes = 6 * Nk * (4 * ((wl.npair + 3) // 4)) * cz
+    # FP32 paths: the row pass writes five terms and the spectral parts of A,
+    # Phi_y, phi; the first stencil pass reads those three parts, writes Phi_y
+    # and phi and updates two parts, the second reads the two and updates the
+    # residual (11 values per pair and separation)
     hbm = {
         "products": ns * 4 * ny * Nk * 16 + 11 * Nk * ns * ny * cz,
-        "terms": (pl_bytes if planes else comb) + terms + (3 * spec_arr if f32 else 0),
-        "stencil": (13 * spec_arr) if f32 else (9 * wl.npair * N * 8),
+        "terms": (pl_bytes if planes else comb) + (5 * terms // 7 + 3 * spec_arr if f32 else terms),
+        "stencil": (11 * spec_arr) if f32 else (9 * wl.npair * N * 8),
     }
     if not planes:
         hbm["combine"] = raw + comb
