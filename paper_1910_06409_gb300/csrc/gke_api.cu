@@ -59,6 +59,13 @@ struct gke_plan_s {
     double *s1_w2 = nullptr, *s1_ab = nullptr, *s1_mean = nullptr;
     unsigned char* s1_piv = nullptr;
     bool s1_ready = false;
+    // streamed input of gke_compute from pinned host memory: the k = 0
+    // coefficients for the Step-1 mean, then whole snapshots on up_st, each
+    // announced by up_ev[s] (products_stage passes up_active to the kernels)
+    zd* k0buf = nullptr;
+    cudaStream_t up_st = nullptr;
+    std::vector<cudaEvent_t> up_ev;
+    const cudaEvent_t* up_active = nullptr;
     std::vector<int> ch_rows, ch_nrows, ch_crs, ch_ncr;   // offsets into dec_tab and counts
     size_t n_acc = 0;                         // elements of the FP64 accumulator comb
     zd *ttw_xd = nullptr, *ttw_zd = nullptr;  // twiddles of the transform sizes
@@ -819,8 +826,10 @@ extern "C" void gke_destroy(gke_plan_t p)
         void* extra[] = {p->Xc, p->dec_tab, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
     }
-    void* s1[] = {p->s1_A, p->s1_B, p->s1_in, p->s1_out, p->s1_w2, p->s1_ab, p->s1_mean, p->s1_piv};
+    void* s1[] = {p->s1_A, p->s1_B, p->s1_in, p->s1_out, p->s1_w2, p->s1_ab, p->s1_mean, p->s1_piv, p->k0buf};
     for (void* q : s1) if (q) cudaFree(q);
+    for (cudaEvent_t e : p->up_ev) cudaEventDestroy(e);
+    if (p->up_st) cudaStreamDestroy(p->up_st);
     void* ptrs[] = {p->pl32, p->pl64, p->Xop, p->G, p->H, p->raw, p->comb, p->comb32, p->spec, p->W, p->tw_xd, p->tw_zd, p->tw_xf, p->tw_zf, p->stage_in,
                     p->mean_sum, p->mean, p->stats, p->prof, p->fdw, p->stage_terms, p->stage_prof,
                     p->fdl0, p->pair_i, p->nonfinite, p->part, p->sep_tab};
@@ -908,12 +917,15 @@ static gke_status device_fields(gke_plan_t p, const void* fields, int nsnap, con
     return GKE_OK;
 }
 
-static gke_status mean_impl(gke_plan_t p, const zd* f, int nsnap)
+// plane: elements between consecutive (snapshot, field, y) rows of f (Nk for
+// whole snapshots, 1 for a compact copy of the k = 0 coefficients)
+static gke_status mean_impl(gke_plan_t p, const zd* f, int nsnap, long long plane = -1)
 {
     const int ny = p->d.ny;
     {
         StageScope sc(p, GKE_STAGE_MEAN);
-        k_mean_accum<<<(4 * ny + 127) / 128, 128, 0, p->st>>>(f, nsnap, ny, (long long)p->Nk, p->mean_sum);
+        k_mean_accum<<<(4 * ny + 127) / 128, 128, 0, p->st>>>(f, nsnap, ny, plane < 0 ? (long long)p->Nk : plane,
+                                                              p->mean_sum);
         p->launches += 1;
     }
     CUDA_TRY(p, cudaGetLastError());
@@ -955,6 +967,7 @@ static void products_stage(gke_plan_t p, const zd* f, int ns)
     a.cw_ci = t.cw_ci; a.rz_rp = t.rz_rp; a.cw_cf = t.cw_cf; a.yb_cf = t.yb_cf; a.eps_kchunk = EPS_KCHUNK;
     a.Lx = d.Lx; a.Lz = d.Lz; a.fdw = p->fdw; a.fdl0 = p->fdl0; a.st = p->st;
     a.st2 = p->aux_st; a.G2 = p->G2; a.H2 = p->H2; a.part2 = p->part2; a.ev = p->aux_ev;
+    a.up_ev = p->up_active;
     p->launches += f32 ? products_launch<float>(a) : products_launch<double>(a);
 }
 
@@ -1311,12 +1324,54 @@ extern "C" gke_status gke_finalize_terms(gke_plan_t p, void* terms, double* prof
     return GKE_OK;
 }
 
+// Pinned host input of gke_compute, streamed: the k = 0 coefficients of every
+// (snapshot, field, y) into k0buf on the main stream (all the Step-1 mean
+// reads), then whole snapshots into stage_in on the upload stream, snapshot s
+// announced by up_ev[s], so the products of the first snapshots overlap the
+// copies of the later ones.
+static gke_status upload_streamed(gke_plan_t p, const zd* host, int nsnap)
+{
+    const int ny = p->d.ny;
+    const size_t per = (size_t)4 * ny * p->Nk;
+    if (!p->stage_in) CUDA_TRY(p, dalloc(&p->stage_in, (size_t)p->d.max_snap * per));
+    if (!p->k0buf) CUDA_TRY(p, dalloc(&p->k0buf, (size_t)p->d.max_snap * 4 * ny));
+    if (!p->up_st) CUDA_TRY(p, cudaStreamCreateWithFlags(&p->up_st, cudaStreamNonBlocking));
+    while ((int)p->up_ev.size() < nsnap) {
+        cudaEvent_t e;
+        CUDA_TRY(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        p->up_ev.push_back(e);
+    }
+    CUDA_TRY(p, cudaMemcpy2DAsync(p->k0buf, sizeof(zd), host, (size_t)p->Nk * sizeof(zd), sizeof(zd),
+                                  (size_t)nsnap * 4 * ny, cudaMemcpyHostToDevice, p->st));
+    // the upload stream starts after the main stream's earlier work (which may
+    // still read stage_in)
+    cudaEvent_t e0 = take_event(p);
+    CUDA_TRY(p, cudaEventRecord(e0, p->st));
+    CUDA_TRY(p, cudaStreamWaitEvent(p->up_st, e0, 0));
+    p->chunk_ev.push_back(e0);
+    for (int s = 0; s < nsnap; ++s) {
+        CUDA_TRY(p, cudaMemcpyAsync(p->stage_in + s * per, host + s * per, per * sizeof(zd), cudaMemcpyHostToDevice,
+                                    p->up_st));
+        CUDA_TRY(p, cudaEventRecord(p->up_ev[s], p->up_st));
+    }
+    return GKE_OK;
+}
+
 extern "C" gke_status gke_compute(gke_plan_t p, const void* fields, int nsnap, void* terms, double* profiles)
 {
     if (!p || !fields || !terms) return p ? fail(p, GKE_ERR_ARG, "NULL argument") : GKE_ERR_ARG;
     if (nsnap < 1 || nsnap > p->d.max_snap) return fail(p, GKE_ERR_ARG, "nsnap out of range [1, max_snap]");
     gke_status s = gke_reset(p);
     if (s != GKE_OK) return s;
+    if (!is_device_ptr(fields) && is_pinned_host_ptr(fields)) {
+        if ((s = upload_streamed(p, (const zd*)fields, nsnap)) != GKE_OK) return s;
+        if ((s = mean_impl(p, p->k0buf, nsnap, 1)) != GKE_OK) return s;
+        p->up_active = p->up_ev.data();
+        s = snapshot_impl(p, p->stage_in, nsnap);
+        p->up_active = nullptr;
+        if (s != GKE_OK) return s;
+        return gke_finalize_terms(p, terms, profiles);
+    }
     const zd* f;
     if ((s = device_fields(p, fields, nsnap, &f)) != GKE_OK) return s;
     if ((s = mean_impl(p, f, nsnap)) != GKE_OK) return s;

@@ -122,6 +122,9 @@ struct ProdArgs {
     cudaStream_t st2 = nullptr;
     void* G2 = nullptr; void* H2 = nullptr; double* part2 = nullptr;
     const cudaEvent_t* ev = nullptr;      // 6 caller-owned events for st2 (else created per call)
+    // optional: event s completes when snapshot s of `fields` has arrived on
+    // the device; each snapshot's linear operands and transforms wait for it
+    const cudaEvent_t* up_ev = nullptr;
 };
 template <typename TF> int products_launch(const ProdArgs& a);
 cudaError_t products_set_attrs(int lim);

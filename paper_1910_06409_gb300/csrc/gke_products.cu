@@ -38,12 +38,12 @@ template <typename TF> __device__ __forceinline__ cplx<TF> cvt(zd v) { return mk
 template <typename TF> __host__ __device__ constexpr int ll_rows() { return sizeof(TF) == 4 ? 128 : 64; }
 template <typename TF>
 __global__ void __launch_bounds__(256)
-k_load_linear(const zd* __restrict__ fields, int ns, int ny, int Nk, int rows,
+k_load_linear(const zd* __restrict__ fields, int ns, int ny, int Nk, int rows, int s0,
               const double* __restrict__ mean, cplx<TF>* __restrict__ Xop, int* __restrict__ nonfinite)
 {
     __shared__ cplx<TF> tile[ll_rows<TF>()][33];
     const int k0 = blockIdx.x * 32, y0 = blockIdx.y * rows;
-    const int s = blockIdx.z / 4, f = blockIdx.z % 4;
+    const int s = s0 + blockIdx.z / 4, f = blockIdx.z % 4;
     const int nr = min(rows, ny - y0);
     int bad = 0;
     for (int r = threadIdx.y; r < nr; r += blockDim.y) {
@@ -454,12 +454,12 @@ int products_launch(const ProdArgs& a)
     cudaStream_t st = a.st;
     C* Xop = (C*)a.Xop;
     int launches = 0;
-    {
-        const int nch = (ny + ll_rows<TF>() - 1) / ll_rows<TF>(), rows = (ny + nch - 1) / nch;
-        k_load_linear<TF><<<dim3((Nk + 31) / 32, nch, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk, rows,
+    const int nch = (ny + ll_rows<TF>() - 1) / ll_rows<TF>(), rows = (ny + nch - 1) / nch;
+    if (!a.up_ev) {
+        k_load_linear<TF><<<dim3((Nk + 31) / 32, nch, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk, rows, 0,
                                                                                       a.mean, Xop, a.nonfinite);
+        ++launches;
     }
-    ++launches;
     // With a second stream and second G, H, part buffers, snapshot s runs on
     // stream s % 2, so the transforms of two snapshots overlap; the row sums
     // are still reduced into stats on the main stream in snapshot order.
@@ -489,6 +489,13 @@ int products_launch(const ProdArgs& a)
         C* H = (C*)(b ? a.H2 : a.H);
         double* part = b ? a.part2 : a.part;
         if (two && s >= 2) cudaStreamWaitEvent(ss, ev_red[b], 0);     // part[b] read by the last reduction
+        if (a.up_ev) {
+            // this snapshot's data arrive on the upload stream
+            cudaStreamWaitEvent(ss, a.up_ev[s], 0);
+            k_load_linear<TF><<<dim3((Nk + 31) / 32, nch, 4), dim3(32, 8), 0, ss>>>(a.fields, ns, ny, Nk, rows, s,
+                                                                                     a.mean, Xop, a.nonfinite);
+            ++launches;
+        }
         if (nz == 256) {
             constexpr int CWR = 16;
             k_col_inverse_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, ny, 4), CWR * 16,
@@ -574,7 +581,8 @@ cudaError_t products_set_attrs(int lim)
 
 // explicit instantiations
 #define GKE_INST(TF)                                                                                       \
-    template __global__ void k_load_linear<TF>(const zd*, int, int, int, int, const double*, cplx<TF>*, int*);  \
+    template __global__ void k_load_linear<TF>(const zd*, int, int, int, int, int, const double*, cplx<TF>*,   \
+                                               int*);                                                        \
     template __global__ void k_col_inverse<TF>(const zd*, int, int, int, int, const double*,               \
                                                const cplx<TF>*, cplx<TF>*);                                \
     template __global__ void k_row_products<TF>(const cplx<TF>*, int, int, int, int, const cplx<TF>*,      \

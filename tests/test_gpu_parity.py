@@ -345,3 +345,34 @@ def test_pinned_host_output_matches_device(N, precision):
         assert torch.equal(dev.cpu(), pinned)
     finally:
         N.gke_destroy(plan)
+
+
+@pytest.mark.parametrize("precision,shape", [(0, (16, 16, 33, 3)), (1, (16, 16, 33, 3)), (1, (256, 256, 9, 3))])
+def test_pinned_host_input_matches_device(N, precision, shape):
+    """Pinned host inputs are streamed (k = 0 coefficients for the mean, then
+    snapshot by snapshot while the products of the earlier ones run):
+    bit-equal to device inputs, also into pinned host outputs."""
+    import torch
+    nx, nz, ny, ns = shape
+    wl = S.small(nx, nz, ny, ns, wid=45)
+    coef = S.coefficients(wl)
+    y = S.cgl_grid(wl.ny)
+    plan = N.gke_plan(wl.nx, wl.nz, wl.ny, wl.Lx, wl.Lz, wl.nu, y, ns, precision)
+    try:
+        tdt = torch.float64 if precision == 0 else torch.float32
+        shape_t = (N.GKE_NTERM, N.gke_npair(plan), wl.nz, wl.nx)
+        dev = torch.empty(shape_t, dtype=tdt, device="cuda")
+        out2 = torch.empty(shape_t, dtype=tdt, device="cuda")
+        pinned_out = torch.empty(shape_t, dtype=tdt).pin_memory()
+        f_dev = torch.from_numpy(coef).cuda()
+        f_pin = torch.from_numpy(coef).pin_memory()
+        prof_d, prof_h = np.zeros((N.GKE_NPROF, ny)), np.zeros((N.GKE_NPROF, ny))
+        N.gke_compute(plan, f_dev, ns, dev, prof_d)
+        N.gke_compute(plan, f_pin, ns, out2, prof_h)
+        N.gke_compute(plan, f_pin, ns, pinned_out)
+        torch.cuda.synchronize()
+        assert torch.equal(dev, out2)
+        assert torch.equal(dev.cpu(), pinned_out)
+        assert np.array_equal(prof_d, prof_h)
+    finally:
+        N.gke_destroy(plan)
