@@ -100,38 +100,50 @@ __global__ void k_col_inverse(const zd* __restrict__ fields_s, int ny, int nz, i
 }
 
 // Register-FFT versions of the column passes for nz = N1 N2 (two-level
-// transform, fft2l): CTA = CW adjacent columns x N2 lanes; lane n2 of column c
-// loads rows n2 + N2 m straight from global memory (consecutive columns =
-// consecutive addresses), one shared-memory exchange, stores straight back.
-// Shared memory: N twiddles + N1 (N2 CW + 1) complex.
+// transform, fft2l): CTA = CW adjacent columns x YB planes x N2 lanes; lane n2
+// of a sequence loads rows n2 + N2 m straight from global memory (consecutive
+// columns = consecutive addresses), one shared-memory exchange, stores
+// straight back.  The inverse pass also writes the snapshot's linear
+// operands Xop[f][k][s][y] (the mean-removed coefficients, runs of YB planes)
+// and flags non-finite input, so no separate loader runs.
+// Shared memory: N twiddles + N1 (N2 CW YB + 1) complex.
 template <typename TF, int N1, int N2>
-__global__ void __launch_bounds__(256)
-k_col_inverse_r(const zd* __restrict__ fields_s, int ny, int nxh, int CW, const double* __restrict__ mean,
-                const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ G)
+__global__ void __launch_bounds__(512)
+k_col_inverse_r(const zd* __restrict__ fields_s, int ny, int nxh, int CW, int YB, int s, int ns,
+                const double* __restrict__ mean, const cplx<TF>* __restrict__ tw_z, cplx<TF>* __restrict__ G,
+                cplx<TF>* __restrict__ Xop, int* __restrict__ nonfinite)
 {
     typedef cplx<TF> C;
     constexpr int N = N1 * N2;
     extern __shared__ __align__(16) unsigned char sh_raw_cir[];
     C* stw = (C*)sh_raw_cir;
     C* xs = stw + N;
-    const int c = threadIdx.x % CW, lane = threadIdx.x / CW;
-    const int kx = blockIdx.x * CW + c, y = blockIdx.y, f = blockIdx.z;
+    const int nseq = CW * YB;
+    const int c = threadIdx.x % CW, yl = (threadIdx.x / CW) % YB, lane = threadIdx.x / nseq;
+    const int kx = blockIdx.x * CW + c, y = blockIdx.y * YB + yl, f = blockIdx.z;
+    const bool live = kx < nxh && y < ny;
+    const long long Nk = (long long)N * nxh;
     load_twiddles(stw, tw_z, N);
     const zd* src = fields_s + ((long long)f * ny + y) * N * nxh;
+    C* xop = Xop + (((long long)f * Nk + kx) * ns + s) * ny + y;
+    int bad = 0;
     C v[N1];
     #pragma unroll
     for (int m = 0; m < N1; ++m) {
         const int kz = lane + N2 * m;
         zd x = mk(0.0, 0.0);
-        if (kx < nxh) {
+        if (live) {
             x = src[(long long)kz * nxh + kx];
+            if (!isfinite(x.x) || !isfinite(x.y)) bad = 1;
             if (kx == 0 && kz == 0) x.x -= mean[f * ny + y];
+            xop[(long long)kz * nxh * ns * ny] = cvt<TF>(x);
         }
         v[m] = cvt<TF>(x);
     }
+    if (bad) atomicOr(nonfinite, 1);
     __syncthreads();
-    fft2l<TF, N1, N2, true>(v, lane, xs + c, N2 * CW + 1, CW, stw);
-    if (kx < nxh) {
+    fft2l<TF, N1, N2, true>(v, lane, xs + (yl * CW + c), N2 * nseq + 1, nseq, stw);
+    if (live) {
         C* dst = G + ((long long)f * ny + y) * N * nxh;
         #pragma unroll
         for (int m = 0; m < N1; ++m) dst[(long long)(lane + N2 * m) * nxh + kx] = v[m];
@@ -455,7 +467,9 @@ int products_launch(const ProdArgs& a)
     C* Xop = (C*)a.Xop;
     int launches = 0;
     const int nch = (ny + ll_rows<TF>() - 1) / ll_rows<TF>(), rows = (ny + nch - 1) / nch;
-    if (!a.up_ev) {
+    // at nz = 256 the register column pass writes the linear operands itself
+    const bool fused_load = nz == 256;
+    if (!a.up_ev && !fused_load) {
         k_load_linear<TF><<<dim3((Nk + 31) / 32, nch, ns * 4), dim3(32, 8), 0, st>>>(a.fields, ns, ny, Nk, rows, 0,
                                                                                       a.mean, Xop, a.nonfinite);
         ++launches;
@@ -489,18 +503,18 @@ int products_launch(const ProdArgs& a)
         C* H = (C*)(b ? a.H2 : a.H);
         double* part = b ? a.part2 : a.part;
         if (two && s >= 2) cudaStreamWaitEvent(ss, ev_red[b], 0);     // part[b] read by the last reduction
-        if (a.up_ev) {
-            // this snapshot's data arrive on the upload stream
-            cudaStreamWaitEvent(ss, a.up_ev[s], 0);
+        if (a.up_ev) cudaStreamWaitEvent(ss, a.up_ev[s], 0);    // this snapshot's data arrive on the upload stream
+        if (a.up_ev && !fused_load) {
             k_load_linear<TF><<<dim3((Nk + 31) / 32, nch, 4), dim3(32, 8), 0, ss>>>(a.fields, ns, ny, Nk, rows, s,
                                                                                      a.mean, Xop, a.nonfinite);
             ++launches;
         }
         if (nz == 256) {
-            constexpr int CWR = 16;
-            k_col_inverse_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, ny, 4), CWR * 16,
-                                          (256 + 16 * (16 * CWR + 1)) * sizeof(C), ss>>>(
-                fs, ny, nxh, CWR, a.mean, (const C*)a.tw_z, G);
+            // FP32: 4 kx x 8 planes per CTA; FP64 4 x 4 (shared memory)
+            constexpr int CWR = 4, YBR = sizeof(TF) == 4 ? 8 : 4;
+            k_col_inverse_r<TF, 16, 16><<<dim3((nxh + CWR - 1) / CWR, (ny + YBR - 1) / YBR, 4), CWR * YBR * 16,
+                                          (256 + 16 * (16 * CWR * YBR + 1)) * sizeof(C), ss>>>(
+                fs, ny, nxh, CWR, YBR, s, ns, a.mean, (const C*)a.tw_z, G, Xop, a.nonfinite);
         } else {
             k_col_inverse<TF><<<dim3((nxh + a.cw_ci - 1) / a.cw_ci, ny, 4), 256, (1 + 2 * a.cw_ci) * nz * sizeof(C), ss>>>(
                 fs, ny, nz, nxh, a.cw_ci, a.mean, (const C*)a.tw_z, G);
