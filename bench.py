@@ -77,8 +77,8 @@ def correlator_cmac(wl, ns):
 # (profiles/dram_small_cases_split_and_f64.md); a stage missing here reports
 # null (not captured since its kernels changed).
 NCU_TRAFFIC_GB = {
-    "f64": {"correlate": 96.7, "combine": 93.0, "terms": 104.1, "stencil": 37.9, "products": 33.1},
-    "bf16x3": {"correlate": 36.7, "products": 22.3},
+    "f64": {"correlate": 96.7, "combine": 93.0, "terms": 104.0, "stencil": 38.0, "products": 27.8},
+    "bf16x3": {"correlate": 36.6, "terms": 55.9, "stencil": 20.5, "products": 16.4},
 }
 
 
