@@ -457,7 +457,10 @@ def run_group(args, world, rank, local):
             "data": "synthetic", "config": {"workload": "group of three channel datasets", "datasets": detail,
                                             "precision": args.precision},
             "gpu_launches": launches, "clocks": clk.summary(), "e2e": None, "roofline": None,
-            "cpu_baseline": None, "note": "datasets run as separate plans back to back (no grouped launch)"}
+            "cpu_baseline": None,
+            "note": "datasets run as separate plans back to back (no grouped launch); the 384x384x193 set runs "
+                    "at separation stride 2 in the chunked mode (exact aliasing onto a 192x192 separation grid) "
+                    "because its full-resolution outputs and accumulators exceed one GPU's memory"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
