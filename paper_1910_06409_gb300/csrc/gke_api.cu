@@ -51,6 +51,11 @@ struct gke_plan_s {
     int nzt = 0, nxt = 0;                     // transform sizes of the terms stage (nzd, nxd when dec)
     int R = 0, Kc = 0;                        // chunk rows and wavenumbers (the largest chunk)
     void* Xc = nullptr;                       // one chunk's gathered operands
+    // split path with at most 4 row tiles: the chunk's correlator writes the
+    // six plane spectra [NPLANE][Kc][npp] (in raw) and k_planes_fold aliases
+    // them; pair_tri lists the triangle's pairs for it
+    bool dec_planes = false;
+    int* pair_tri = nullptr;
     int* dec_tab = nullptr;                   // per chunk: its kz rows, then its coarse rows
     // Step 1 for velocity-vorticity databases (allocated on first use):
     // transform buffers of six fields, d2/dy2 weights, the factored Poisson
@@ -580,7 +585,10 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         // keeps a chunk's contractions and gathered operands within
         // DEC_CHUNK_BYTES, but a chunk holds at least one class
         const int nzd = p->nzt;
-        const size_t per_row = (size_t)p->nxh * (raw_per_k + (size_t)NFIELD * ns * ny * p->csz);
+        p->dec_planes = d.precision == GKE_PREC_BF16X3 && split_planes_ok(ny);
+        p->npp = 4 * ((p->npair_tri + 3) / 4);
+        const size_t chunk_per_k = p->dec_planes ? (size_t)NPLANE * p->npp * sizeof(zf) : raw_per_k;
+        const size_t per_row = (size_t)p->nxh * (chunk_per_k + (size_t)NFIELD * ns * ny * p->csz);
         p->R = (int)std::max<size_t>((size_t)2 * (d.nz / nzd), DEC_CHUNK_BYTES / per_row);
         std::vector<int> tab;
         std::vector<int> rows, crs;
@@ -610,7 +618,8 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
         close_chunk();
         p->R = rmax;
         p->Kc = p->R * p->nxh;
-        ALLOCB(p->raw, raw_per_k * p->Kc);
+        ALLOCB(p->raw, chunk_per_k * p->Kc);
+        if (p->dec_planes && p->wedge) ALLOCB(p->pair_tri, (size_t)2 * p->npair_tri * sizeof(int));
         ALLOCB(p->Xc, (size_t)NFIELD * p->Kc * ns * ny * p->csz);
         ALLOCB(p->dec_tab, tab.size() * sizeof(int));
         if ((e = cudaMemcpy(p->dec_tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
@@ -721,6 +730,15 @@ extern "C" gke_status gke_plan(const gke_desc* desc, void* stream, gke_plan_t* o
     for (int i1 = 0; i1 < ny; ++i1)
         for (int i2 = i1; i2 < (p->wedge ? ny - i1 : ny); ++i2) { pi[2 * q] = i1; pi[2 * q + 1] = i2; ++q; }
     cudaStream_t st = p->st;
+    if (p->pair_tri) {
+        // the triangle's pairs (the plane fold of the chunked wedge runs over all of them)
+        std::vector<int> pt(2 * p->npair_tri);
+        long long r = 0;
+        for (int i1 = 0; i1 < ny; ++i1)
+            for (int i2 = i1; i2 < ny; ++i2) { pt[2 * r] = i1; pt[2 * r + 1] = i2; ++r; }
+        if ((e = cudaMemcpy(p->pair_tri, pt.data(), pt.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(GKE_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+    }
     std::vector<int> stab;
     if (under) {
         // [zpos (nz) | xpos (nx) | negz (nrz) | negx (nrx)]
@@ -823,7 +841,7 @@ extern "C" void gke_destroy(gke_plan_t p)
     for (cudaEvent_t ev : p->aux_ev) if (ev) cudaEventDestroy(ev);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     if (p->dec) {
-        void* extra[] = {p->Xc, p->dec_tab, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
+        void* extra[] = {p->Xc, p->dec_tab, p->pair_tri, p->ttw_xd, p->ttw_zd, p->ttw_xf, p->ttw_zf};
         for (void* q : extra) if (q) cudaFree(q);
     }
     void* s1[] = {p->s1_A, p->s1_B, p->s1_in, p->s1_out, p->s1_w2, p->s1_ab, p->s1_mean, p->s1_piv, p->k0buf};
@@ -1045,6 +1063,22 @@ static gke_status enqueue_snapshot(gke_plan_t p, const zd* f, int ns)
                 StageScope sc(p, GKE_STAGE_CORRELATE);
                 p->launches += gather_rows_launch(!f32, p->Xop, NFIELD, Nk, (long long)ns * ny, rows, nr, p->nxh,
                                                   p->Xc, st);
+            }
+            if (p->dec_planes) {
+                {
+                    StageScope sc(p, GKE_STAGE_CORRELATE);
+                    int nl = 0;
+                    gke_status s = split_correlate_planes(p->split, (const zf*)p->Xc, ns, ny, Kc, 0, Kc, p->pset,
+                                                          p->npp, p->prof, (zf*)p->raw, st, p->err, &nl);
+                    p->launches += nl;
+                    if (s != GKE_OK) return s;
+                }
+                StageScope sc(p, GKE_STAGE_COMBINE);
+                p->launches += planes_fold_launch(p->raw, p->npp, Kc, rows, nr, p->dec_tab + p->ch_crs[c],
+                                                  p->ch_ncr[c], p->pair_tri ? p->pair_tri : p->pair_i, p->npair_tri,
+                                                  ny, d.nz, d.nx, p->nzt, p->nxt, d.Lx, d.Lz, d.nu, p->prof, p->tset,
+                                                  p->comb, st);
+                continue;
             }
             gke_status s = correlate(p->Xc, Kc, 0, Kc);
             if (s != GKE_OK) return s;

@@ -312,7 +312,13 @@ k_combine_fold(const cplx<TI>* __restrict__ raw, const int* __restrict__ rows, i
 {
     typedef cplx<TI> C;
     typedef cplx<TC> Z;
+    extern __shared__ int sh_cf[];                    // per chunk row: direct and image coarse rows
     const int nxh = nx / 2 + 1, nxdh = nxd / 2 + 1, Kc = nrows * nxh;
+    for (int i = threadIdx.x; i < nrows; i += blockDim.x) {
+        sh_cf[i] = rows[i] % nzd;
+        sh_cf[nrows + i] = (nz - rows[i]) % nzd;
+    }
+    __syncthreads();
     const int nblk = (ny + PB - 1) / PB;
     int bt = blockIdx.x, a = 0;
     while (bt >= nblk - a) { bt -= nblk - a; ++a; }
@@ -337,9 +343,9 @@ k_combine_fold(const cplx<TI>* __restrict__ raw, const int* __restrict__ rows, i
         #pragma unroll
         for (int t = 0; t < NTERM; ++t) acc[t].zero();
         for (int i = 0; i < nrows; ++i) {
-            const int kz = rows[i];
-            const bool direct = kz % nzd == kzd, image = (nz - kz) % nzd == kzd;
+            const bool direct = sh_cf[i] == kzd, image = sh_cf[nrows + i] == kzd;
             if (!direct && !image) continue;
+            const int kz = rows[i];
             const TC kzv = cz * (TC)signed_bin(kz, nz);
             // direct sources kx = kxd (mod nxd), then the images kx = -kxd
             for (int pass = 0; pass < 2; ++pass) {
@@ -386,11 +392,101 @@ int combine_fold_launch(bool c64, const void* raw, const int* rows, int nrows, c
     dim3 g((unsigned)(nblk * (nblk + 1) / 2), (unsigned)((nxdh + FK - 1) / FK));
     const unsigned jm = job_set(tmask);
     if (c64)
-        k_combine_fold<double, double><<<g, 64 * FK, 0, st>>>((const zd*)raw, rows, nrows, crs, ncr, ny, nz, nx, nzd,
+        k_combine_fold<double, double><<<g, 64 * FK, (size_t)2 * nrows * sizeof(int), st>>>((const zd*)raw, rows, nrows, crs, ncr, ny, nz, nx, nzd,
                                                               nxd, Lx, Lz, nu, prof, tmask, jm, (zd*)dec);
     else
-        k_combine_fold<float, float><<<g, 64 * FK, 0, st>>>((const zf*)raw, rows, nrows, crs, ncr, ny, nz, nx, nzd,
+        k_combine_fold<float, float><<<g, 64 * FK, (size_t)2 * nrows * sizeof(int), st>>>((const zf*)raw, rows, nrows, crs, ncr, ny, nz, nx, nzd,
                                                             nxd, Lx, Lz, nu, prof, tmask, jm, (zd*)dec);
+    return 1;
+}
+
+// Chunked mode on the split path in plane mode: the chunk's six plane
+// spectra planes[NPLANE][Kc][npp] (FP32, pair index fastest) give the seven
+// term spectra of a triangle pair as the transforms' column pass forms them
+// (Phi_x = S4 + (dU - 2 i nu kx) A, Phi_z = S6 - 2 i nu kz A, residual =
+// i kx Phi_x + i kz Phi_z - xi), which are aliased onto the coarse grid as in
+// k_combine_fold.  CTA = 128 consecutive pairs x 2 adjacent coarse columns:
+// four warps read 1 KB of one plane row at a time and the two columns' FP64
+// coarse bins fill whole 32-byte sectors.  The chunk rows that feed each
+// coarse row (direct and image) are listed once per CTA in shared memory.
+constexpr int PF_PAIRS = 128, PF_COLS = 2;
+__global__ void __launch_bounds__(PF_PAIRS * PF_COLS)
+k_planes_fold(const zf* __restrict__ planes, long long npp, int Kc, const int* __restrict__ rows, int nrows,
+              const int* __restrict__ crs, int ncr, const int* __restrict__ pair_tri, long long npair, int ny, int nz,
+              int nx, int nzd, int nxd, double Lx, double Lz, double nu, const double* __restrict__ prof,
+              unsigned tmask, zd* __restrict__ dec)
+{
+    // src[ci][j]: chunk row i * 2 + pass (0 direct, 1 image) of coarse row ci,
+    // cnt[ci] <= 2 nz / nzd of them (a coarse row has nz / nzd direct rows and
+    // as many images, all in its chunk)
+    extern __shared__ int sh_pf[];
+    const int ms = 2 * (nz / nzd);
+    int* cnt = sh_pf;
+    int* src = sh_pf + ncr;
+    const int nxh = nx / 2 + 1, nxdh = nxd / 2 + 1;
+    for (int ci = threadIdx.x; ci < ncr; ci += blockDim.x) {
+        const int kzd = crs[ci];
+        int n = 0;
+        for (int i = 0; i < nrows && n < ms; ++i) {
+            if (rows[i] % nzd == kzd) src[ci * ms + n++] = i * 2;
+            if ((nz - rows[i]) % nzd == kzd && n < ms) src[ci * ms + n++] = i * 2 + 1;
+        }
+        cnt[ci] = n;
+    }
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * PF_PAIRS + (threadIdx.x % PF_PAIRS);
+    const int kxd = blockIdx.y * PF_COLS + (int)(threadIdx.x / PF_PAIRS);
+    if (p >= npair || kxd >= nxdh) return;
+    const int i1 = pair_tri[2 * p], i2 = pair_tri[2 * p + 1];
+    const float dU = (float)(prof[PR_U * ny + i2] - prof[PR_U * ny + i1]);
+    const float cx = (float)(6.283185307179586476925286766559 / Lx), cz = (float)(6.283185307179586476925286766559 / Lz);
+    const float nu2 = (float)(2.0 * nu);
+    const int kxm = (nxd - kxd) % nxd;                   // -kxd mod nxd
+    const long long pstride = (long long)Kc * npp;
+    zd* out = dec + p * NTERM * (long long)nzd * nxdh + kxd;
+    for (int ci = 0; ci < ncr; ++ci) {
+        const int kzd = crs[ci];
+        Acc<float> acc[NTERM];
+        #pragma unroll
+        for (int t = 0; t < NTERM; ++t) acc[t].zero();
+        for (int j = 0; j < cnt[ci]; ++j) {
+            const int e = src[ci * ms + j], i = e >> 1, pass = e & 1;
+            const float kzv = cz * (float)signed_bin(rows[i], nz);
+            // direct sources kx = kxd (mod nxd), images kx = -kxd
+            for (int kx = pass ? kxm : kxd; 2 * kx <= nx; kx += nxd) {
+                const zf* q = planes + ((long long)i * nxh + kx) * npp + p;
+                const zf A = q[PL_A * pstride], S4 = q[PL_S4 * pstride], PY = q[PL_PHIY * pstride];
+                const zf S6 = q[PL_S6 * pstride], PH = q[PL_PHI * pstride], XI = q[PL_XI * pstride];
+                const float kxv = cx * (float)signed_bin(kx, nx);
+                const zf PX = mk(S4.x + dU * A.x + nu2 * kxv * A.y, S4.y + dU * A.y - nu2 * kxv * A.x);
+                const zf PZ = mk(S6.x + nu2 * kzv * A.y, S6.y - nu2 * kzv * A.x);
+                const zf RS = mk(-kxv * PX.y - kzv * PZ.y - XI.x, kxv * PX.x + kzv * PZ.x - XI.y);
+                const zf T[NTERM] = {A, PX, PY, PZ, PH, XI, RS};
+                const float h = (kx == 0 || 2 * kx == nx) ? 0.5f : 1.f;
+                #pragma unroll
+                for (int t = 0; t < NTERM; ++t) acc[t].add(mk(h * T[t].x, pass ? -h * T[t].y : h * T[t].y));
+            }
+        }
+        #pragma unroll
+        for (int t = 0; t < NTERM; ++t) {
+            if (!((tmask >> t) & 1u)) continue;
+            zd* o = out + ((long long)t * nzd + kzd) * nxdh;
+            zd v = *o;
+            v.x += acc[t].re();
+            v.y += acc[t].im();
+            *o = v;
+        }
+    }
+}
+
+int planes_fold_launch(const void* planes, long long npp, int Kc, const int* rows, int nrows, const int* crs, int ncr,
+                       const int* pair_tri, long long npair, int ny, int nz, int nx, int nzd, int nxd, double Lx,
+                       double Lz, double nu, const double* prof, unsigned tmask, void* dec, cudaStream_t st)
+{
+    const int nxdh = nxd / 2 + 1;
+    dim3 g((unsigned)((npair + PF_PAIRS - 1) / PF_PAIRS), (unsigned)((nxdh + PF_COLS - 1) / PF_COLS));
+    k_planes_fold<<<g, PF_PAIRS * PF_COLS, (size_t)(ncr + ncr * 2 * (nz / nzd)) * sizeof(int), st>>>((const zf*)planes, npp, Kc, rows, nrows, crs, ncr, pair_tri, npair, ny, nz, nx,
+                                      nzd, nxd, Lx, Lz, nu, prof, tmask, (zd*)dec);
     return 1;
 }
 

@@ -149,6 +149,9 @@ int s1_factor_launch(int ny, int nz, int nx, double Lx, double Lz, const double*
 int s1_snapshot_launch(const zd* v_eta, const double* mean_uw, int ny, int nz, int nx, double Lx, double Lz,
                        double nu, const double* w1, const double* w2, const int* l0, const zd* tw_x, const zd* tw_z,
                        const double* ab, const unsigned char* piv, zd* bufA, zd* bufB, zd* out, cudaStream_t st);
+int planes_fold_launch(const void* planes, long long npp, int Kc, const int* rows, int nrows, const int* crs, int ncr,
+                       const int* pair_tri, long long npair, int ny, int nz, int nx, int nzd, int nxd, double Lx,
+                       double Lz, double nu, const double* prof, unsigned tmask, void* dec, cudaStream_t st);
 int combine_fold_launch(bool c64, const void* raw, const int* rows, int nrows, const int* crs, int ncr, int ny,
                         int nz, int nx, int nzd, int nxd, double Lx, double Lz, double nu, const double* prof,
                         unsigned tmask, void* dec, cudaStream_t st);

@@ -50,6 +50,7 @@ constexpr int A_STAGE = 6 * A_BLK;      // slices x parts (re, im), slice-major
 constexpr int B_STAGE = 3 * B_BLK;      // slices
 constexpr int SM_A = A_STAGE * 2;       // 24576 bytes
 constexpr int SM_B = B_STAGE * 2;       // 24576 bytes
+constexpr int NFB = 4;                  // B operand slots per wavenumber: u, v, w, 2 U'(y) v
 constexpr int A_LBO = (TM / 8) * 128;       // 2048: K-adjacent core matrices in an A block
 constexpr int B_LBO = (2 * TM / 8) * 128;   // 4096: K-adjacent core matrices in a B block
 constexpr int CM_SBO = 128;                 // M/N-adjacent core matrices
@@ -67,6 +68,10 @@ constexpr uint32_t NEG_A = 1u << 13;       // negate-A bit of the instruction de
 struct TcJob { int nterm; int fa[5]; int fb[5]; unsigned neg; };
 __constant__ TcJob c_tcjobs[NJSQ + 1];
 __constant__ TcJob c_tcplanes[NPLANE];
+// planes of an off-diagonal tile pair (y in tile mt < nt, y' in tile nt): as
+// c_tcplanes, except that xi takes B = 2 U'(y') v (slot 3), so that the
+// partner-free form below needs no per-row factor
+__constant__ TcJob c_tcoff[NPLANE];
 
 // cross-slice pairs (i, j), 0 < i + j <= 2; the pair (0, 0) goes last
 __constant__ int c_pi[5] = {1, 0, 2, 1, 0};
@@ -194,24 +199,28 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
     for (int q = 0; q < 6; ++q) *(bf16x8*)(dst + q * A_BLK + idx) = o[q];
 }
 
-// Bop[k][fb][g][nt][slice][B_BLK], fb = u, v, w; rows br | bi
+// Bop[k][NFB][g][nt][slice][B_BLK], slots fb = u, v, w and (nfb = 4) the
+// product 2 U'(y) v in FP32; rows br | bi
 __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
-                               bf16* __restrict__ Bop)
+                               int nfb, const double* __restrict__ prof, bf16* __restrict__ Bop)
 {
     long long b = blockIdx.x;
     const int nt = (int)(b % MT); b /= MT;
     const int g = (int)(b % G); b /= G;
-    const int fb = (int)(b % 3);
-    const int k = (int)(b / 3);
-    bf16* dst = Bop + ((((long long)k * 3 + fb) * G + g) * MT + nt) * (long long)B_STAGE;
+    const int fb = (int)(b % nfb);
+    const int k = (int)(b / nfb);
+    bf16* dst = Bop + ((((long long)k * NFB + fb) * G + g) * MT + nt) * (long long)B_STAGE;
     const int r = threadIdx.x % TM, kc = threadIdx.x / TM;          // blockDim = 2 TM
     const int y = nt * TM + r;
+    const int src = fb == 3 ? F_V : fb;
+    const float sc = (fb == 3 && y < ny) ? 2.f * (float)prof[PR_DU * ny + y] : 1.f;
     bf16x8 br[3], bi[3];
     #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int s = g * KS + kc * 8 + e;
         zf v = mk(0.f, 0.f);
-        if (y < cov && s < ns) v = Xop[(((long long)fb * Nk + k0 + k) * ns + s) * ny + y];
+        if (y < cov && s < ns) v = Xop[(((long long)src * Nk + k0 + k) * ns + s) * ny + y];
+        if (fb == 3) v = mk(sc * v.x, sc * v.y);
         split3(v.x, br[0].v[e], br[1].v[e], br[2].v[e]);
         split3(v.y, bi[0].v[e], bi[1].v[e], bi[2].v[e]);
     }
@@ -264,6 +273,7 @@ struct TcArgs {
     long long nitems;
     TcSel sel; zf* raw;                       // raw mode
     unsigned planes; int npl; long long npp;  // plane mode: selected planes, their count, padded pair count
+    int ntp;                                  // plane mode: tile pairs (mt <= nt) per wavenumber
     zf* out; const double* prof;
     int* err;
 };
@@ -311,7 +321,8 @@ constexpr int SMP_EPI = NST * SMP_STAGE;
 constexpr int EPI_BLOCKS = 10;                          // lower-triangle 32 x 32 blocks of a tile
 constexpr int EPI_BYTES = EPI_BLOCKS * 32 * 32 * 8;     // plane mode; raw mode uses 4 x 32 x 33 x 8
 constexpr int SMP_DUP = SMP_EPI + EPI_BYTES;            // 2 U'(y) for the xi plane
-constexpr int SMP_BAR = SMP_DUP + TM * 4;
+constexpr int DUP_ROWS = 4 * TM;                        // rows of s_dup: plane mode covers up to 4 tiles
+constexpr int SMP_BAR = SMP_DUP + DUP_ROWS * 4;
 constexpr int SMP_TOTAL = SMP_BAR + 256;
 constexpr uint32_t TMEM_COLS_P = 512;
 static_assert(EPI_BYTES >= EPI_WARPS * 32 * 33 * 8, "raw-mode staging fits");
@@ -359,10 +370,16 @@ __device__ __forceinline__ Units<MODE> item_units(const TcArgs& a, int njt, long
         u.j0 = 0;
         u.mt = u.nt = 0;
     } else if (MODE == 1) {
-        u.k = (int)(it / a.npl);
+        // (wavenumber, tile pair mt <= nt of the upper triangle, plane)
+        const long long per_k = (long long)a.ntp * a.npl;
+        u.k = (int)(it / per_k);
+        const int r = (int)(it - (long long)u.k * per_k);
         u.n = 1;
-        u.j0 = nth_bit(a.planes, (int)(it % a.npl));
-        u.mt = u.nt = 0;
+        u.j0 = nth_bit(a.planes, r % a.npl);
+        int tp = r / a.npl, mt = 0;
+        while (tp >= a.MT - mt) { tp -= a.MT - mt; ++mt; }
+        u.mt = mt;
+        u.nt = mt + tp;
     } else {
         u.k = (int)(it / njt);
         u.n = 1;
@@ -373,6 +390,16 @@ __device__ __forceinline__ Units<MODE> item_units(const TcArgs& a, int njt, long
 
 template <int MODE>
 __device__ __forceinline__ const TcJob& job_desc(int job) { return MODE ? c_tcplanes[job] : c_tcjobs[job]; }
+
+// Off-diagonal tile pairs of plane mode (y in tile mt < nt, every y' > y):
+// a plane al X + be X^H is one accumulator without a transposition,
+//   al sum_t conj(A_t(y)) B_t(y') + be sum_t conj(B_t(y)) A_t(y')
+// (X^H(y, y') = conj X(y', y)), so after the jd.nterm terms X the same terms
+// run "swapped": the A role takes B_t in its B-operand layout at tile mt, the
+// B role A_t in its A-operand layout at tile nt (be = -1 for S4, Phi_y, S6:
+// the negate bit flips; +1 for phi and xi; A has no partner terms).
+__device__ __forceinline__ int off_terms(const TcJob& jd, int job) { return jd.nterm * (job == PL_A ? 1 : 2); }
+__device__ __forceinline__ bool off_flip(int job) { return job == PL_S4 || job == PL_PHIY || job == PL_S6; }
 
 // shared-memory offsets of stage st: its A block and (MODE 0, 1) its B block;
 // MODE 2 keeps the three B blocks of the item at offset 0
@@ -408,7 +435,7 @@ k_corr_tc_pipe(const TcArgs a)
     }
     if (PLANES) {
         float* s_dup = (float*)(smem + SMP_DUP);
-        for (int i = threadIdx.x; i < TM; i += blockDim.x)
+        for (int i = threadIdx.x; i < DUP_ROWS; i += blockDim.x)
             s_dup[i] = i < a.ny ? 2.f * (float)a.prof[PR_DU * a.ny + i] : 0.f;
     }
     if (warp == 1) {
@@ -439,7 +466,7 @@ k_corr_tc_pipe(const TcArgs a)
                     if (!mbar_wait_ab(&bars->bempty, bph ^ 1, abort)) return false;
                     mbar_expect_tx(&bars->bfull, SMP_BRES);
                     for (int fb = 0; fb < 3; ++fb)
-                        bulk_g2s(smem + fb * SM_B, a.Bop + ((long long)k * 3 + fb) * G * MT * (long long)B_STAGE, SM_B,
+                        bulk_g2s(smem + fb * SM_B, a.Bop + ((long long)k * NFB + fb) * G * MT * (long long)B_STAGE, SM_B,
                                  &bars->bfull);
                     ++b_issued;
                     bph ^= 1;
@@ -447,19 +474,26 @@ k_corr_tc_pipe(const TcArgs a)
                     return true;
                 };
                 for (int un = 0; un < u.n; ++un) {
-                    const TcJob& jd = job_desc<MODE>(u.job(un));
+                    const int job = u.job(un);
+                    const bool off = MODE == 1 && u.mt != u.nt;
+                    const TcJob& jd = off ? c_tcoff[job] : job_desc<MODE>(job);
+                    const int nterm = off ? off_terms(jd, job) : jd.nterm;
                     for (int pass = 0; pass < 2; ++pass)
-                        for (int t = 0; t < jd.nterm; ++t)
+                        for (int tt = 0; tt < nterm; ++tt)
                             for (int g = 0; g < G; ++g) {
                                 if (!mbar_wait_ab(&bars->empty[st], ph ^ 1, abort)) { fail(); goto producer_done; }
+                                const bool sw = tt >= jd.nterm;
+                                const int t = sw ? tt - jd.nterm : tt;
                                 const uint32_t ba = pass ? 2 * A_BLK * 2 : SM_A, bb = pass ? B_BLK * 2 : SM_B;
                                 uint8_t* sa = smem + stage_a<MODE>(st);
                                 mbar_expect_tx(&bars->full[st], MODE == 2 ? ba : ba + bb);
-                                bulk_g2s(sa, a.Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT + u.mt) *
-                                                         (long long)A_STAGE, ba, &bars->full[st]);
-                                if (MODE != 2)
-                                    bulk_g2s(sa + SM_A, a.Bop + ((((long long)k * 3 + jd.fb[t]) * G + g) * MT + u.nt) *
-                                                                    (long long)B_STAGE, bb, &bars->full[st]);
+                                const bf16* asrc = a.Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT +
+                                                            (sw ? u.nt : u.mt)) * (long long)A_STAGE;
+                                const bf16* bsrc = a.Bop + ((((long long)k * NFB + jd.fb[t]) * G + g) * MT +
+                                                            (sw ? u.mt : u.nt)) * (long long)B_STAGE;
+                                // swapped terms: the B operand's block in the A slot and vice versa
+                                bulk_g2s(sa, sw ? bsrc : asrc, ba, &bars->full[st]);
+                                if (MODE != 2) bulk_g2s(sa + SM_A, sw ? asrc : bsrc, bb, &bars->full[st]);
                                 ++issued;
                                 if (++st == NST) { st = 0; ph ^= 1; }
                                 if (!b_done && ++sidx == NST && !load_b()) { fail(); goto producer_done; }
@@ -489,15 +523,21 @@ k_corr_tc_pipe(const TcArgs a)
                     bph ^= 1;
                 }
                 for (int un = 0; un < u.n && ok; ++un) {
-                    const TcJob& jd = job_desc<MODE>(u.job(un));
+                    const int job = u.job(un);
+                    const bool off = MODE == 1 && u.mt != u.nt;
+                    const TcJob& jd = off ? c_tcoff[job] : job_desc<MODE>(job);
+                    const int nterm = off ? off_terms(jd, job) : jd.nterm;
                     if (!mbar_wait_ab(&bars->acc_empty[acc], aph ^ 1, abort)) { fail(); ok = false; break; }
                     tc_fence_after();
                     const uint32_t d = tmem + (uint32_t)(acc * 256);
                     uint32_t accum = 0;
                     for (int pass = 0; pass < 2 && ok; ++pass)
-                        for (int t = 0; t < jd.nterm && ok; ++t) {
+                        for (int tt = 0; tt < nterm && ok; ++tt) {
+                            const bool sw = tt >= jd.nterm;
+                            const int t = sw ? tt - jd.nterm : tt;
                             // a term of sign -1: the negate-A bit (13) of the instruction descriptor
-                            const uint32_t neg = ((jd.neg >> t) & 1u) ? NEG_A : 0u;
+                            const bool ng = (((jd.neg >> t) & 1u) != 0) != (sw && off_flip(job));
+                            const uint32_t neg = ng ? NEG_A : 0u;
                             const uint32_t id = IDESC | neg, id128 = IDESC_N128 | neg;
                             for (int g = 0; g < G; ++g) {
                                 if (!mbar_wait_ab(&bars->full[st], ph, abort)) { fail(); ok = false; break; }
@@ -505,6 +545,24 @@ k_corr_tc_pipe(const TcArgs a)
                                 const uint8_t* sa = smem + stage_a<MODE>(st);
                                 const uint8_t* sb = MODE == 2 ? smem + jd.fb[t] * SM_B : sa + SM_A;
                                 const int npr = pass ? 1 : 5;
+                                if (sw) {
+                                    // A role: conj(B_t(y)) from the B-layout block [br | bi] (slices of
+                                    // B_BLK); B role: A_t(y') from the A-layout blocks (re, im per slice)
+                                    for (int pr = 0; pr < npr; ++pr) {
+                                        const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
+                                        const uint64_t x_r = sdesc(sa + i * B_BLK * 2, B_LBO, CM_SBO);
+                                        const uint64_t x_i = sdesc(sa + i * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
+                                        const uint64_t y_r = sdesc(sb + (j * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
+                                        const uint64_t y_i = sdesc(sb + (j * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
+                                        mma_bf16(d, x_r, y_r, id128, 1);                 // Re += br ar
+                                        mma_bf16(d, x_i, y_i, id128, 1);                 // Re += bi ai
+                                        mma_bf16(d + TM, x_r, y_i, id128, 1);            // Im += br ai
+                                        mma_bf16(d + TM, x_i, y_r, id128 ^ NEG_A, 1);    // Im -= bi ar
+                                    }
+                                    mma_commit(&bars->empty[st]);
+                                    if (++st == NST) { st = 0; ph ^= 1; }
+                                    continue;
+                                }
                                 for (int pr = 0; pr < npr; ++pr) {
                                     const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
                                     const uint64_t a_re = sdesc(sa + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
@@ -581,9 +639,6 @@ k_corr_tc_pipe(const TcArgs a)
         volatile int* eok = &bars->eok;
         const int cov = a.cov, ny = a.ny;
         const int y = 32 * q + lane;                  // this thread's row of the tile
-        const float dy = s_dup[y];
-        // pair_index(y, y') = rb + y' for this thread's row (32-bit: pairs < 2^31)
-        const int rb = (int)(pair_index(y, y, ny) - y);
         int acc = 0;
         uint32_t aph = 0;
         bool go = true;
@@ -603,6 +658,41 @@ k_corr_tc_pipe(const TcArgs a)
             tc_fence_after();
             const uint32_t tbase = tmem + (uint32_t)(acc * 256) + ((uint32_t)(q * 32) << 16);
             zf* outp = a.out + ((long long)job * a.Kc + k) * a.npp;
+            // the item's tiles: rows y0 + [0, 128), columns y1 + [0, 128)
+            const int y0 = u.mt * TM, y1 = u.nt * TM, yg = y0 + y;
+            // pair_index(yg, y') = rb + y' for this thread's row (32-bit: pairs < 2^31)
+            const int rb = (int)(pair_index(yg, yg, ny) - yg);
+            if (u.mt != u.nt) {
+                // off-diagonal tile pair: the accumulator is the plane up to its
+                // scale (A -2, phi 1/2, else 1); each warp stages its rows in
+                // its own block for row-contiguous stores
+                const float al = job == PL_A ? -2.f : job == PL_PHI ? 0.5f : 1.f;
+                float2* bb = blk + q * 1024;
+                for (int b = 0; b < 4; ++b) {
+                    uint32_t re[32], im[32];
+                    tmem_ld32(tbase + b * 32, re);
+                    tmem_ld32(tbase + TM + b * 32, im);
+                    tmem_ld_wait();
+                    __syncwarp();
+                    #pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        bb[swz(lane, j)] = make_float2(al * __uint_as_float(re[j]), al * __uint_as_float(im[j]));
+                    __syncwarp();
+                    const int yp = y1 + 32 * b + lane;
+                    #pragma unroll
+                    for (int r = 0; r < 32; ++r) {
+                        const float2 o = bb[swz(r, lane)];
+                        const int base = __shfl_sync(0xffffffffu, rb, r);
+                        if (y0 + 32 * q + r < cov && yp < cov) __stcs((float2*)(outp + base + yp), o);
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bars->acc_empty[acc]);
+                if (++acc == 2) { acc = 0; aph ^= 1; }
+                continue;
+            }
+            const float dy = s_dup[yg];
             // lay out the blocks (q, c), c <= q
             for (int c = 0; c <= q; ++c) {
                 uint32_t re[32], im[32];
@@ -630,7 +720,7 @@ k_corr_tc_pipe(const TcArgs a)
                     #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const float2 pv = bb[swz(j, lane)];
-                        const float al = s_dup[32 * b + j];
+                        const float al = s_dup[y0 + 32 * b + j];
                         o[j] = make_float2(al * __uint_as_float(re[j]) + dy * pv.x,
                                            al * __uint_as_float(im[j]) - dy * pv.y);
                     }
@@ -648,12 +738,12 @@ k_corr_tc_pipe(const TcArgs a)
                 #pragma unroll
                 for (int j = 0; j < 32; ++j) bb[swz(lane, j)] = o[j];
                 __syncwarp();
-                // row r of the block: pairs (32 q + r, 32 b + lane), consecutive
-                // pair indices rb(32 q + r) + 32 b + lane
-                const int yp = 32 * b + lane;
+                // row r of the block: pairs (y0 + 32 q + r, y0 + 32 b + lane),
+                // consecutive pair indices rb(y0 + 32 q + r) + y0 + 32 b + lane
+                const int yp = y0 + 32 * b + lane;
                 #pragma unroll
                 for (int r = 0; r < 32; ++r) o[r] = bb[swz(r, lane)];
-                if (b > q && 32 * b + 32 <= cov) {            // whole block above the diagonal
+                if (b > q && y0 + 32 * b + 32 <= cov) {       // whole block above the diagonal
                     #pragma unroll
                     for (int r = 0; r < 32; ++r) {
                         const int base = __shfl_sync(0xffffffffu, rb, r);
@@ -663,7 +753,7 @@ k_corr_tc_pipe(const TcArgs a)
                     #pragma unroll
                     for (int r = 0; r < 32; ++r) {
                         const int base = __shfl_sync(0xffffffffu, rb, r);
-                        const int yr = 32 * q + r;
+                        const int yr = y0 + 32 * q + r;
                         if (yr < cov && yp >= yr && yp < cov) __stcs((float2*)(outp + base + yp), o[r]);
                     }
                 }
@@ -838,7 +928,7 @@ gke_status split_alloc(SplitWork& w, int ny, int ns, int Kc)
     tile_geometry(ny, MT, cov);
     const int G = (ns + KS - 1) / KS;
     w.a_bytes = (size_t)Nk * NFIELD * G * MT * A_STAGE * sizeof(bf16);
-    w.b_bytes = (size_t)Nk * 3 * G * MT * B_STAGE * sizeof(bf16);
+    w.b_bytes = (size_t)Nk * NFB * G * MT * B_STAGE * sizeof(bf16);
     if (cudaMalloc(&w.ops, w.a_bytes + w.b_bytes) != cudaSuccess) { w.ops = nullptr; return GKE_ERR_OOM; }
     if (cudaMalloc((void**)&w.err, sizeof(int)) != cudaSuccess) { w.err = nullptr; return GKE_ERR_OOM; }
     if (cudaMemset(w.err, 0, sizeof(int)) != cudaSuccess) return GKE_ERR_CUDA;
@@ -868,9 +958,15 @@ cudaError_t split_setup(cudaStream_t st)
         /* PHI : H  */ {5, {F_Q, F_UV, F_VV, F_VW, F_P}, {F_V, F_U, F_V, F_W, F_V}, 0x1Eu},
         /* XI  : E  */ {1, {F_U}, {F_V}, 0u},
     };
+    // off-diagonal tile pairs: xi = sum conj(u(y)) [2 U'(y') v(y')] + partner,
+    // B slot 3 = 2 U'(y) v
+    TcJob ho[NPLANE];
+    for (int i = 0; i < NPLANE; ++i) ho[i] = hp[i];
+    ho[PL_XI].fb[0] = 3;
     static_assert(F_U == 0 && F_V == 1 && F_W == 2, "B operands are u, v, w in field order");
     cudaError_t e = cudaMemcpyToSymbolAsync(c_tcjobs, h, sizeof(h), 0, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tcplanes, hp, sizeof(hp), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_tcoff, ho, sizeof(ho), 0, cudaMemcpyHostToDevice, st);
     const void* ks[] = {(const void*)k_corr_tc_pipe<0>, (const void*)k_corr_tc_pipe<1>, (const void*)k_corr_tc_pipe<2>};
     for (const void* k : ks)
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMP_TOTAL);
@@ -881,7 +977,7 @@ bool split_planes_ok(int ny)
 {
     int MT, cov;
     tile_geometry(ny, MT, cov);
-    return MT == 1;
+    return MT <= DUP_ROWS / TM;
 }
 
 static int sm_count()
@@ -893,8 +989,9 @@ static int sm_count()
 }
 
 // BF16 slices of the operands of wavenumbers [k0, k0 + Kc)
-static void split_prep(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, float pscale,
-                       cudaStream_t st, bf16*& Aop, bf16*& Bop, int& G, int& MT, int& cov)
+// nfb: B slots written (3: u, v, w; 4: also 2 U'(y) v, which prof gives)
+static void split_prep(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, float pscale, int nfb,
+                       const double* prof, cudaStream_t st, bf16*& Aop, bf16*& Bop, int& G, int& MT, int& cov)
 {
     tile_geometry(ny, MT, cov);
     G = (ns + KS - 1) / KS;
@@ -902,7 +999,8 @@ static void split_prep(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int 
     Bop = (bf16*)((char*)w.ops + (size_t)Kc * NFIELD * G * MT * A_STAGE * sizeof(bf16));
     k_split_prep_A<<<(unsigned)((long long)Kc * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov,
                                                                                     pscale, Aop);
-    k_split_prep_B<<<(unsigned)((long long)Kc * 3 * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, Bop);
+    k_split_prep_B<<<(unsigned)((long long)Kc * nfb * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, nfb,
+                                                                                 prof, Bop);
 }
 
 // wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
@@ -917,7 +1015,7 @@ gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, 
     if (sel.nsq == 0 && !sel.d) return GKE_OK;
     TcArgs a{};
     bf16 *Aop, *Bop;
-    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 1.f, st, Aop, Bop, a.G, a.MT, a.cov);
+    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 1.f, 3, nullptr, st, Aop, Bop, a.G, a.MT, a.cov);
     a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
     a.sel = sel; a.raw = raw; a.err = w.err;
     a.nitems = (long long)Kc * sel_tiles(sel, a.MT);
@@ -942,17 +1040,22 @@ gke_status split_correlate_planes(SplitWork& w, const zf* Xop, int ns, int ny, i
     *launches = 0;
     planes &= (1u << NPLANE) - 1u;
     if (!planes) return GKE_OK;
-    if (!split_planes_ok(ny)) { err = "split correlator: plane mode needs one 128-row tile"; return GKE_ERR_UNSUPPORTED; }
+    if (!split_planes_ok(ny)) { err = "split correlator: plane mode covers at most 4 tiles of 128 rows"; return GKE_ERR_UNSUPPORTED; }
     TcArgs a{};
     bf16 *Aop, *Bop;
-    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 4.f, st, Aop, Bop, a.G, a.MT, a.cov);
+    int MT0, cov0;
+    tile_geometry(ny, MT0, cov0);
+    // off-diagonal tile pairs take the xi plane from the 2 U'(y) v slot
+    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 4.f, MT0 > 1 ? 4 : 3, prof, st, Aop, Bop, a.G, a.MT, a.cov);
     a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
     a.planes = planes; a.npl = __builtin_popcount(planes); a.npp = npp; a.out = out; a.prof = prof;
+    a.ntp = a.MT * (a.MT + 1) / 2;
     a.err = w.err;
-    // one snapshot group: one item per wavenumber with the B blocks resident
-    // (each B block is read once per wavenumber); else one item per plane
-    const bool resident = a.G == 1;
-    a.nitems = resident ? (long long)Kc : (long long)Kc * a.npl;
+    // one tile and one snapshot group: one item per wavenumber with the B
+    // blocks resident (each B block is read once per wavenumber); else one
+    // item per (wavenumber, tile pair, plane)
+    const bool resident = a.G == 1 && a.MT == 1;
+    a.nitems = resident ? (long long)Kc : (long long)Kc * a.ntp * a.npl;
     const unsigned grid = (unsigned)std::min<long long>(a.nitems, sm_count());
     if (resident)
         k_corr_tc_pipe<2><<<grid, TCP_THREADS, SMP_TOTAL, st>>>(a);

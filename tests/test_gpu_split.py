@@ -136,3 +136,27 @@ def test_split_256_selection_equals_full(N):
     full, _, _ = run(N, wl, coef, N.GKE_PREC_BF16X3)
     got, mz, mx = run(N, wl, coef, N.GKE_PREC_BF16X3, ux=(8, 64, 2, 8), uz=(4, 32, 4, 16))
     assert np.array_equal(got, full[:, :, mz][:, :, :, mx])
+
+
+# --------------------------------------- plane mode over several row tiles
+# ny = 193 (two tiles, the second partly empty) and 257 (two full tiles and
+# the wall row): diagonal tile pairs by the shared-memory transposition,
+# off-diagonal ones by the partner-free MMA order; the full triangle, the
+# chunked mode at a uniform separation stride (plane chunks folded onto the
+# coarse grid) and the wedge; against the FP64 path on the same inputs.
+@pytest.mark.parametrize("ny,domain,stride,calls", [(257, 0, 1, None), (193, 0, 1, [2, 1]), (257, 0, 2, None),
+                                                    (193, 1, 2, [1, 2]), (257, 1, 4, None), (65, 0, 2, None)])
+def test_split_multi_tile_planes_match_f64(N, ny, domain, stride, calls):
+    from test_gpu_undersample import run
+    wl = S.small(16, 16, ny, 3, wid=140 + ny % 7 + domain)
+    coef = S.coefficients(wl)
+    u = (0, 0, 0, stride) if stride > 1 else (0, 0, 0, 0)
+    if stride > 1:
+        ref, _, _ = run(N, wl, coef, N.GKE_PREC_F64, domain=domain, ux=u, uz=u)
+        got, _, _ = run(N, wl, coef, N.GKE_PREC_BF16X3, domain=domain, ux=u, uz=u)
+    else:
+        ref, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_F64, domain=domain)
+        got, _ = run_gpu(N, wl, coef, precision=N.GKE_PREC_BF16X3, calls=calls, domain=domain)
+    errs = [rel_err(got[t], ref[t]) for t in range(N.GKE_NTERM)]
+    assert max(errs) <= TOL_SPLIT, dict(zip(N.TERMS, errs))
+    assert max(errs) > 0.0
