@@ -77,6 +77,22 @@ __constant__ TcJob c_tcoff[NPLANE];
 __constant__ int c_pi[5] = {1, 0, 2, 1, 0};
 __constant__ int c_pj[5] = {1, 2, 0, 0, 1};
 
+// Packed K (one snapshot group of ns <= 5): the six slice products of a term
+// in three MMA K steps instead of six zero-padded ones, one step per order of
+// magnitude so that an MMA never sums products of different sizes: step 0
+// the slice pairs (1, 1), (0, 2), (2, 0) (about 2^-16 of x0 y0), step 1
+// (1, 0), (0, 1) (2^-8), step 2 (0, 0).  Position c of step ks holds slice
+// pair c / ns of the step for snapshot c mod ns.  The K steps take the places
+// of the slices in the operand blocks (step ks at 2 ks A_BLK elements of an A
+// block and ks B_BLK = 2 ks A_BLK of a B block), so the copies and descriptors
+// keep their layout; as in the unpacked order, steps 0 and 1 of every term
+// go first (pass 0) and step 2 last (pass 1).
+constexpr int PK_MAX_NS = 5, PK_STEPS = 3;
+__device__ __forceinline__ int pk_pairs(int ks) { return 3 - ks; }      // slice pairs in step ks
+// slices (i of A, j of B) of pair sp of step ks
+__device__ __forceinline__ int pk_i(int ks, int sp) { return ks == 0 ? (sp == 0 ? 1 : sp == 1 ? 0 : 2) : ks == 1 ? (sp == 0 ? 1 : 0) : 0; }
+__device__ __forceinline__ int pk_j(int ks, int sp) { return ks == 0 ? (sp == 0 ? 1 : sp == 1 ? 2 : 0) : ks == 1 ? (sp == 0 ? 0 : 1) : 0; }
+
 // ------------------------------------------------------------------ PTX
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -174,7 +190,7 @@ __device__ __forceinline__ void split3(float x, bf16& s0, bf16& s1, bf16& s2) {
 struct alignas(16) bf16x8 { bf16 v[8]; };
 
 __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
-                               float pscale, bf16* __restrict__ Aop)
+                               float pscale, int nks, bf16* __restrict__ Aop)
 {
     long long b = blockIdx.x;
     const int mt = (int)(b % MT); b /= MT;
@@ -184,6 +200,33 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
     bf16* dst = Aop + ((((long long)k * NFIELD + f) * G + g) * MT + mt) * (long long)A_STAGE;
     const int r = threadIdx.x % TM, kc = threadIdx.x / TM;          // blockDim = 2 TM
     const int y = mt * TM + r;
+    if (nks) {
+        // packed K: the row's ns values split once, then placed by step
+        bf16 sr[PK_MAX_NS][3], si[PK_MAX_NS][3];
+        for (int s = 0; s < ns; ++s) {
+            zf v = mk(0.f, 0.f);
+            if (y < cov) v = Xop[(((long long)f * Nk + k0 + k) * ns + s) * ny + y];
+            if (f == F_P) v = pscale * v;                      // a power of two: exact
+            split3(v.x, sr[s][0], sr[s][1], sr[s][2]);
+            split3(v.y, si[s][0], si[s][1], si[s][2]);
+        }
+        const int idx = cm_index(r, kc * 8, TM);
+        const bf16 z = __float2bfloat16_rn(0.f);
+        for (int ks = 0; ks < PK_STEPS; ++ks) {
+            bf16x8 ore, oim;
+            #pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int c = kc * 8 + e, sp = c / ns, s = c - sp * ns;
+                const bool live = sp < pk_pairs(ks);
+                const int sl = live ? pk_i(ks, sp) : 0;
+                ore.v[e] = live ? sr[s][sl] : z;
+                oim.v[e] = live ? si[s][sl] : z;
+            }
+            *(bf16x8*)(dst + (2 * ks) * A_BLK + idx) = ore;
+            *(bf16x8*)(dst + (2 * ks + 1) * A_BLK + idx) = oim;
+        }
+        return;
+    }
     bf16x8 o[6];
     #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -202,7 +245,7 @@ __global__ void k_split_prep_A(const zf* __restrict__ Xop, int ns, int ny, int N
 // Bop[k][NFB][g][nt][slice][B_BLK], slots fb = u, v, w and (nfb = 4) the
 // product 2 U'(y) v in FP32; rows br | bi
 __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int Nk, int k0, int G, int MT, int cov,
-                               int nfb, const double* __restrict__ prof, bf16* __restrict__ Bop)
+                               int nfb, const double* __restrict__ prof, int nks, bf16* __restrict__ Bop)
 {
     long long b = blockIdx.x;
     const int nt = (int)(b % MT); b /= MT;
@@ -214,6 +257,33 @@ __global__ void k_split_prep_B(const zf* __restrict__ Xop, int ns, int ny, int N
     const int y = nt * TM + r;
     const int src = fb == 3 ? F_V : fb;
     const float sc = (fb == 3 && y < ny) ? 2.f * (float)prof[PR_DU * ny + y] : 1.f;
+    if (nks) {
+        // packed K (see k_split_prep_A): slice pk_j of B
+        bf16 sr[PK_MAX_NS][3], si[PK_MAX_NS][3];
+        for (int s = 0; s < ns; ++s) {
+            zf v = mk(0.f, 0.f);
+            if (y < cov) v = Xop[(((long long)src * Nk + k0 + k) * ns + s) * ny + y];
+            if (fb == 3) v = mk(sc * v.x, sc * v.y);
+            split3(v.x, sr[s][0], sr[s][1], sr[s][2]);
+            split3(v.y, si[s][0], si[s][1], si[s][2]);
+        }
+        const bf16 z = __float2bfloat16_rn(0.f);
+        for (int ks = 0; ks < PK_STEPS; ++ks) {
+            bf16x8 obr, obi;
+            #pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int c = kc * 8 + e, sp = c / ns, s = c - sp * ns;
+                const bool live = sp < pk_pairs(ks);
+                const int sl = live ? pk_j(ks, sp) : 0;
+                obr.v[e] = live ? sr[s][sl] : z;
+                obi.v[e] = live ? si[s][sl] : z;
+            }
+            bf16* d = dst + ks * B_BLK;
+            *(bf16x8*)(d + cm_index(r, kc * 8, 2 * TM)) = obr;
+            *(bf16x8*)(d + cm_index(TM + r, kc * 8, 2 * TM)) = obi;
+        }
+        return;
+    }
     bf16x8 br[3], bi[3];
     #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -274,6 +344,7 @@ struct TcArgs {
     TcSel sel; zf* raw;                       // raw mode
     unsigned planes; int npl; long long npp;  // plane mode: selected planes, their count, padded pair count
     int ntp;                                  // plane mode: tile pairs (mt <= nt) per wavenumber
+    int nks;                                  // packed K steps (one snapshot group of <= 5), else 0
     zf* out; const double* prof;
     int* err;
 };
@@ -464,9 +535,10 @@ k_corr_tc_pipe(const TcArgs a)
                 int sidx = 0;
                 auto load_b = [&]() -> bool {
                     if (!mbar_wait_ab(&bars->bempty, bph ^ 1, abort)) return false;
-                    mbar_expect_tx(&bars->bfull, SMP_BRES);
+                    const uint32_t bres = a.nks ? a.nks * B_BLK * 2 : SM_B;
+                    mbar_expect_tx(&bars->bfull, 3 * bres);
                     for (int fb = 0; fb < 3; ++fb)
-                        bulk_g2s(smem + fb * SM_B, a.Bop + ((long long)k * NFB + fb) * G * MT * (long long)B_STAGE, SM_B,
+                        bulk_g2s(smem + fb * SM_B, a.Bop + ((long long)k * NFB + fb) * G * MT * (long long)B_STAGE, bres,
                                  &bars->bfull);
                     ++b_issued;
                     bph ^= 1;
@@ -478,13 +550,17 @@ k_corr_tc_pipe(const TcArgs a)
                     const bool off = MODE == 1 && u.mt != u.nt;
                     const TcJob& jd = off ? c_tcoff[job] : job_desc<MODE>(job);
                     const int nterm = off ? off_terms(jd, job) : jd.nterm;
+                    // pass 0: the cross slices (packed: K steps 0 and 1), pass 1: (0, 0)
                     for (int pass = 0; pass < 2; ++pass)
                         for (int tt = 0; tt < nterm; ++tt)
                             for (int g = 0; g < G; ++g) {
                                 if (!mbar_wait_ab(&bars->empty[st], ph ^ 1, abort)) { fail(); goto producer_done; }
                                 const bool sw = tt >= jd.nterm;
                                 const int t = sw ? tt - jd.nterm : tt;
-                                const uint32_t ba = pass ? 2 * A_BLK * 2 : SM_A, bb = pass ? B_BLK * 2 : SM_B;
+                                const uint32_t ba = pass ? 2 * A_BLK * 2 : a.nks ? 4 * A_BLK * 2 : SM_A;
+                                const uint32_t bb = pass ? B_BLK * 2 : a.nks ? 2 * B_BLK * 2 : SM_B;
+                                // packed pass 1 copies K step 2 (offset 4 A_BLK = 2 B_BLK in either layout)
+                                const long long po = (a.nks && pass) ? 4LL * A_BLK : 0;
                                 uint8_t* sa = smem + stage_a<MODE>(st);
                                 mbar_expect_tx(&bars->full[st], MODE == 2 ? ba : ba + bb);
                                 const bf16* asrc = a.Aop + ((((long long)k * NFIELD + jd.fa[t]) * G + g) * MT +
@@ -492,8 +568,8 @@ k_corr_tc_pipe(const TcArgs a)
                                 const bf16* bsrc = a.Bop + ((((long long)k * NFB + jd.fb[t]) * G + g) * MT +
                                                             (sw ? u.mt : u.nt)) * (long long)B_STAGE;
                                 // swapped terms: the B operand's block in the A slot and vice versa
-                                bulk_g2s(sa, sw ? bsrc : asrc, ba, &bars->full[st]);
-                                if (MODE != 2) bulk_g2s(sa + SM_A, sw ? asrc : bsrc, bb, &bars->full[st]);
+                                bulk_g2s(sa, (sw ? bsrc : asrc) + po, ba, &bars->full[st]);
+                                if (MODE != 2) bulk_g2s(sa + SM_A, (sw ? asrc : bsrc) + po, bb, &bars->full[st]);
                                 ++issued;
                                 if (++st == NST) { st = 0; ph ^= 1; }
                                 if (!b_done && ++sidx == NST && !load_b()) { fail(); goto producer_done; }
@@ -544,12 +620,14 @@ k_corr_tc_pipe(const TcArgs a)
                                 tc_fence_after();
                                 const uint8_t* sa = smem + stage_a<MODE>(st);
                                 const uint8_t* sb = MODE == 2 ? smem + jd.fb[t] * SM_B : sa + SM_A;
-                                const int npr = pass ? 1 : 5;
+                                // slice pairs (i, j) of this stage, or the packed K steps 0, 1 (pass 0)
+                                // and 2 (pass 1: copied to the stage's front; resident B keeps it at 2)
+                                const int npr = pass ? 1 : a.nks ? 2 : 5;
                                 if (sw) {
                                     // A role: conj(B_t(y)) from the B-layout block [br | bi] (slices of
                                     // B_BLK); B role: A_t(y') from the A-layout blocks (re, im per slice)
                                     for (int pr = 0; pr < npr; ++pr) {
-                                        const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
+                                        const int i = pass ? 0 : a.nks ? pr : c_pi[pr], j = pass ? 0 : a.nks ? pr : c_pj[pr];
                                         const uint64_t x_r = sdesc(sa + i * B_BLK * 2, B_LBO, CM_SBO);
                                         const uint64_t x_i = sdesc(sa + i * B_BLK * 2 + (TM / 8) * 128, B_LBO, CM_SBO);
                                         const uint64_t y_r = sdesc(sb + (j * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
@@ -564,7 +642,8 @@ k_corr_tc_pipe(const TcArgs a)
                                     continue;
                                 }
                                 for (int pr = 0; pr < npr; ++pr) {
-                                    const int i = pass ? 0 : c_pi[pr], j = pass ? 0 : c_pj[pr];
+                                    const int i = pass ? 0 : a.nks ? pr : c_pi[pr];
+                                    const int j = pass ? (MODE == 2 && a.nks ? 2 : 0) : a.nks ? pr : c_pj[pr];
                                     const uint64_t a_re = sdesc(sa + (i * 2 + 0) * A_BLK * 2, A_LBO, CM_SBO);
                                     const uint64_t a_im = sdesc(sa + (i * 2 + 1) * A_BLK * 2, A_LBO, CM_SBO);
                                     const uint64_t b_ri = sdesc(sb + j * B_BLK * 2, B_LBO, CM_SBO);
@@ -991,16 +1070,18 @@ static int sm_count()
 // BF16 slices of the operands of wavenumbers [k0, k0 + Kc)
 // nfb: B slots written (3: u, v, w; 4: also 2 U'(y) v, which prof gives)
 static void split_prep(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, float pscale, int nfb,
-                       const double* prof, cudaStream_t st, bf16*& Aop, bf16*& Bop, int& G, int& MT, int& cov)
+                       const double* prof, cudaStream_t st, bf16*& Aop, bf16*& Bop, int& G, int& MT, int& cov,
+                       int& nks)
 {
     tile_geometry(ny, MT, cov);
     G = (ns + KS - 1) / KS;
+    nks = ns <= PK_MAX_NS ? PK_STEPS : 0;
     Aop = (bf16*)w.ops;
     Bop = (bf16*)((char*)w.ops + (size_t)Kc * NFIELD * G * MT * A_STAGE * sizeof(bf16));
     k_split_prep_A<<<(unsigned)((long long)Kc * NFIELD * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov,
-                                                                                    pscale, Aop);
+                                                                                    pscale, nks, Aop);
     k_split_prep_B<<<(unsigned)((long long)Kc * nfb * G * MT), 2 * TM, 0, st>>>(Xop, ns, ny, Nk, k0, G, MT, cov, nfb,
-                                                                                 prof, Bop);
+                                                                                 prof, nks, Bop);
 }
 
 // wavenumbers [k0, k0 + Kc) of Nk; raw holds the chunk (raw_index with Kc)
@@ -1015,7 +1096,7 @@ gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, 
     if (sel.nsq == 0 && !sel.d) return GKE_OK;
     TcArgs a{};
     bf16 *Aop, *Bop;
-    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 1.f, 3, nullptr, st, Aop, Bop, a.G, a.MT, a.cov);
+    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 1.f, 3, nullptr, st, Aop, Bop, a.G, a.MT, a.cov, a.nks);
     a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
     a.sel = sel; a.raw = raw; a.err = w.err;
     a.nitems = (long long)Kc * sel_tiles(sel, a.MT);
@@ -1046,7 +1127,7 @@ gke_status split_correlate_planes(SplitWork& w, const zf* Xop, int ns, int ny, i
     int MT0, cov0;
     tile_geometry(ny, MT0, cov0);
     // off-diagonal tile pairs take the xi plane from the 2 U'(y) v slot
-    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 4.f, MT0 > 1 ? 4 : 3, prof, st, Aop, Bop, a.G, a.MT, a.cov);
+    split_prep(w, Xop, ns, ny, Nk, k0, Kc, 4.f, MT0 > 1 ? 4 : 3, prof, st, Aop, Bop, a.G, a.MT, a.cov, a.nks);
     a.Aop = Aop; a.Bop = Bop; a.Kc = Kc; a.ny = ny;
     a.planes = planes; a.npl = __builtin_popcount(planes); a.npp = npp; a.out = out; a.prof = prof;
     a.ntp = a.MT * (a.MT + 1) / 2;
