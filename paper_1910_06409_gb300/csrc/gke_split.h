@@ -18,8 +18,8 @@ gke_status split_alloc(SplitWork& w, int ny, int ns, int Kc);
 cudaError_t split_setup(cudaStream_t st);
 gke_status split_correlate(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc, zf* raw,
                            unsigned jobs, cudaStream_t st, std::string& err, int* launches);
-// plane mode: grids whose wall-normal rows fit one 128-row tile (ny <= 128 or
-// ny = 129); the plane spectra of wavenumbers [k0, k0 + Kc) into
+// plane mode: grids whose wall-normal rows fit four 128-row tiles (ny <= 512
+// or ny = 513); the plane spectra of wavenumbers [k0, k0 + Kc) into
 // out[NPLANE][Kc][npp], npp >= npair a multiple of 4 (planes: bit j = Plane j)
 bool split_planes_ok(int ny);
 gke_status split_correlate_planes(SplitWork& w, const zf* Xop, int ns, int ny, int Nk, int k0, int Kc,
