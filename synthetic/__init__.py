@@ -197,3 +197,92 @@ def single_mode_fields(nx: int, nz: int, ny: int, nsnap: int, modes, Lx: float, 
     if mean_u is not None:
         out[:, 0] += mean_u(y)[None, :, None, None]
     return out
+
+
+# ------------------------------------------------ one homogeneous direction
+#
+# Stand-ins for a flow homogeneous in x only (a straight duct): the cross
+# section [-1, 1] x [-1, 1] is sampled on Chebyshev-Gauss-Lobatto grids in y
+# and z (walls at both ends of each).  For every (snapshot, field, y, z) a
+# complex Gaussian half spectrum in x with amplitude (1 + kx^2)^(-5/6),
+# kx = 2 pi m_x / L_x; the m_x = 0 mode and the Nyquist mode are zeroed; the
+# real field is irfft of it, times the wall envelope (1 - y^2)(1 - z^2).
+# Mean flow: U = (1 - y^2)(1 - z^2) on u, and a weak cross-flow
+# V = 0.02 z (1 - y^2)(1 - z^2), W = 0.02 y (1 - y^2)(1 - z^2) (so that every
+# mean-flow term is exercised; the fields are not Navier-Stokes solutions).
+# Coefficients for the GPU path: rfft over x with the forward normalisation,
+# [snapshot][field][y][z][m_x].  Seed of snapshot s: 1910_06409 + 1000*wid +
+# 700 + s (numpy PCG64).
+
+@dataclasses.dataclass(frozen=True)
+class DuctWorkload:
+    """Grid and sample sizes of one synthetic flow homogeneous in x only."""
+
+    name: str
+    wid: int
+    nx: int
+    ny: int
+    nz: int
+    nsnap: int
+    Lx: float = 4.0 * math.pi
+    nu: float = 1.0 / 200.0
+
+    @property
+    def nxh(self) -> int:
+        return self.nx // 2 + 1
+
+    @property
+    def npoint(self) -> int:
+        return self.ny * self.nz
+
+    @property
+    def npair(self) -> int:
+        return self.npoint * (self.npoint + 1) // 2
+
+
+# a case the oracle finishes in seconds (several 32-point tiles of the
+# cross-section pairs and a ragged tail), and the benchmark's duct
+DUCT_TINY = DuctWorkload("duct_16x9x7_s4", 11, 16, 9, 7, 4)
+DUCT = DuctWorkload("duct_256x33x33_s16", 12, 256, 33, 33, 16)
+DUCT_WORKLOADS = {w.name: w for w in (DUCT_TINY, DUCT)}
+
+
+def duct_small(nx: int, ny: int, nz: int, nsnap: int, wid: int = 91, Lx: float = 4.0 * math.pi,
+               nu: float = 1.0 / 200.0) -> DuctWorkload:
+    """A custom (test-sized) duct workload with the same generator."""
+    return DuctWorkload(f"duct_{nx}x{ny}x{nz}_s{nsnap}_w{wid}", wid, nx, ny, nz, nsnap, Lx, nu)
+
+
+def duct_snapshot_physical(wl: DuctWorkload, s: int) -> np.ndarray:
+    """Physical fields of snapshot s, float64 [4][ny][nz][nx] (mean flow included)."""
+    rng = np.random.default_rng(SEED_BASE + 1000 * wl.wid + 700 + s)
+    kx = 2.0 * np.pi * np.arange(wl.nxh) / wl.Lx
+    amp = (1.0 + kx * kx) ** (-5.0 / 6.0)
+    amp[0] = 0.0
+    amp[wl.nx // 2] = 0.0
+    shape = (4, wl.ny, wl.nz, wl.nxh)
+    c = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) * amp
+    phys = np.fft.irfft(c, n=wl.nx, axis=-1, norm="forward")
+    y = cgl_grid(wl.ny)[:, None]
+    z = cgl_grid(wl.nz)[None, :]
+    env = (1.0 - y * y) * (1.0 - z * z)
+    phys *= env[None, :, :, None]
+    phys[0] += env[:, :, None]
+    phys[1] += (0.02 * z * env)[:, :, None]
+    phys[2] += (0.02 * y * env)[:, :, None]
+    return phys
+
+
+def duct_physical(wl: DuctWorkload, nsnap: int | None = None) -> np.ndarray:
+    n = wl.nsnap if nsnap is None else nsnap
+    return np.stack([duct_snapshot_physical(wl, s) for s in range(n)])
+
+
+def duct_coefficients(wl: DuctWorkload, nsnap: int | None = None, out: np.ndarray | None = None) -> np.ndarray:
+    """complex128 [nsnap][4][ny][nz][nx/2+1]: rfft over x, forward normalisation."""
+    n = wl.nsnap if nsnap is None else nsnap
+    if out is None:
+        out = np.empty((n, 4, wl.ny, wl.nz, wl.nxh), dtype=np.complex128)
+    for s in range(n):
+        out[s] = np.fft.rfft(duct_snapshot_physical(wl, s), axis=-1, norm="forward")
+    return out
