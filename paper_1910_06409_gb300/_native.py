@@ -29,7 +29,13 @@ EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_sn
            "gke_terms_bytes", "gke_term_set", "gke_plan_knobs", "gke_reset", "gke_checkpoint",
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy",
-           "gke_velocity_vorticity")
+           "gke_velocity_vorticity",
+           "gke1h_plan", "gke1h_compute", "gke1h_npair", "gke1h_set_timing", "gke1h_stage_times",
+           "gke1h_launch_count", "gke1h_last_error", "gke1h_destroy")
+# the variant with one homogeneous direction (include/gke1h.h)
+TERMS_1H = ("A", "Phi_x", "Phi_y", "Phi_z", "psi_y", "psi_z", "xi", "residual")
+PROFILES_1H = ("U", "V", "W", "P", "dUdy", "dUdz", "dVdy", "dVdz", "dWdy", "dWdz", "eps")
+GKE1H_NTERM, GKE1H_NPROF = len(TERMS_1H), len(PROFILES_1H)
 STAGES = ("mean", "products", "correlate", "combine", "terms", "stencil")
 
 
@@ -40,6 +46,13 @@ class gke_desc(ctypes.Structure):
                 ("max_snap", ctypes.c_int), ("precision", ctypes.c_int), ("pair_domain", ctypes.c_int),
                 ("under_x", ctypes.c_int * 4), ("under_z", ctypes.c_int * 4), ("term_mask", ctypes.c_uint),
                 ("tune_cache", ctypes.c_char_p)]
+
+
+class gke1h_desc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("nu", ctypes.c_double),
+                ("y", ctypes.POINTER(ctypes.c_double)), ("z", ctypes.POINTER(ctypes.c_double)),
+                ("max_snap", ctypes.c_int)]
 
 
 class GkeError(RuntimeError):
@@ -87,6 +100,14 @@ def lib():
             "gke_compute_noalloc": (i, [ctypes.POINTER(gke_desc), vp, i, vp, vp, vp]),
             "gke_last_error": (cp, [vp]),
             "gke_destroy": (None, [vp]),
+            "gke1h_plan": (i, [ctypes.POINTER(gke1h_desc), vp, ctypes.POINTER(vp)]),
+            "gke1h_compute": (i, [vp, vp, i, vp, vp]),
+            "gke1h_npair": (ctypes.c_longlong, [vp]),
+            "gke1h_set_timing": (i, [vp, i]),
+            "gke1h_stage_times": (i, [vp, vp]),
+            "gke1h_launch_count": (ctypes.c_longlong, [vp]),
+            "gke1h_last_error": (cp, [vp]),
+            "gke1h_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -256,3 +277,54 @@ def gke_last_error(plan) -> str:
 
 def gke_destroy(plan):
     lib().gke_destroy(plan)
+
+
+# ------------------------------------------------- one homogeneous direction
+
+def _check1h(status: int, plan) -> None:
+    if status != GKE_OK:
+        msg = lib().gke1h_last_error(plan)
+        raise GkeError(status, msg.decode() if msg else "")
+
+
+def gke1h_plan(nx, ny, nz, Lx, nu, y, z, max_snap, stream=None):
+    import numpy as np
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    desc = gke1h_desc(nx, ny, nz, Lx, nu, yy.ctypes.data_as(dp), zz.ctypes.data_as(dp), max_snap)
+    out = ctypes.c_void_p()
+    _check1h(lib().gke1h_plan(ctypes.byref(desc), stream, ctypes.byref(out)), None)
+    return out.value
+
+
+def gke1h_compute(plan, fields, nsnap, terms, profiles=None):
+    _check1h(lib().gke1h_compute(plan, ptr(fields), nsnap, ptr(terms), ptr(profiles)), plan)
+
+
+def gke1h_npair(plan) -> int:
+    return lib().gke1h_npair(plan)
+
+
+def gke1h_set_timing(plan, on: bool):
+    _check1h(lib().gke1h_set_timing(plan, 1 if on else 0), plan)
+
+
+def gke1h_stage_times(plan):
+    import numpy as np
+    ms = np.zeros(len(STAGES))
+    _check1h(lib().gke1h_stage_times(plan, ptr(ms)), plan)
+    return dict(zip(STAGES, ms.tolist()))
+
+
+def gke1h_launch_count(plan) -> int:
+    return lib().gke1h_launch_count(plan)
+
+
+def gke1h_last_error(plan) -> str:
+    m = lib().gke1h_last_error(plan)
+    return m.decode() if m else ""
+
+
+def gke1h_destroy(plan):
+    lib().gke1h_destroy(plan)

@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI library that need no GPU.
 
-* libgke.so loads and exports every function include/gke.h declares;
+* libgke.so loads and exports every function include/gke.h and
+  include/gke1h.h declare;
 * the host FD weights (Fornberg's recursion) are exact on quartics on the
   wall-normal grids of the workloads, and agree with the oracle's independent
   moment-system solve;
@@ -27,9 +28,15 @@ def native():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "gke.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(gke_[a-z_0-9]+)\s*\(", src)))
+    """every function the headers under include/ declare"""
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(gke1?h?_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(native):
@@ -82,3 +89,19 @@ def test_term_set_closure(native):
     assert f(RES) == RES | PY | PH | A
     assert f(PX | XI) == PX | XI
     assert f(127) == 127 and f(1 << 9) == 127      # bits above the terms are ignored here
+
+
+def test_one_homog_plan_argument_errors(native):
+    """gke1h_plan validates its descriptor before touching the device."""
+    y, z = S.cgl_grid(9), S.cgl_grid(7)
+    bad = [dict(nx=16, ny=4, nz=7), dict(nx=16, ny=9, nz=3), dict(nx=10, ny=9, nz=7), dict(nx=1024, ny=9, nz=7)]
+    codes = []
+    for b in bad:
+        with pytest.raises(native.GkeError) as e:
+            native.gke1h_plan(b["nx"], b["ny"], b["nz"], 1.0, 0.01, S.cgl_grid(max(b["ny"], 1)),
+                              S.cgl_grid(max(b["nz"], 1)), 2)
+        codes.append(e.value.status)
+    assert codes == [-1, -1, -7, -7]
+    with pytest.raises(native.GkeError) as e:
+        native.gke1h_plan(16, 9, 7, 1.0, 0.01, y[::-1].copy(), z, 2)
+    assert e.value.status == -1 and "increasing" in str(e.value)
