@@ -551,6 +551,156 @@ def run_step1(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------- one homogeneous direction
+METRIC_1H = "GKE one-homogeneous-direction (p1,p2)-pair correlations/s, FP64"
+
+
+def correlator_cmac_1h(wl, ns):
+    """Complex multiply-adds of the one-direction correlator per pass: 37
+    contractions over the snapshots for every pair p1 <= p2 and wavenumber
+    (nine velocity pairs, eight for Phi_x, ten each for the y and z fluxes)."""
+    return 37 * ns * wl.npair * wl.nxh
+
+
+def oracle_sample_1h(wl, phys, npts, seed=0):
+    """Time the one-direction oracle on npts sampled (pair, separation) points.
+    Returns (pair-snapshots/s, seconds, description)."""
+    from oracle import one_homog as O1
+    rng = np.random.default_rng(seed)
+    P = wl.npoint
+    pts = []
+    for _ in range(npts):
+        a, b = sorted(rng.integers(0, P, 2).tolist())
+        pts.append((a, b, int(rng.integers(wl.nx))))
+    t0 = time.perf_counter()
+    O1.points(phys, S.cgl_grid(wl.ny), S.cgl_grid(wl.nz), wl.Lx, wl.nu, pts)
+    dt = time.perf_counter() - t0
+    rate = npts / float(wl.nx) * wl.nsnap / dt
+    desc = (f"{npts} (pair, separation) points of {wl.name}, all terms but the residual, including the "
+            f"oracle's per-call set-up; rate = points/nx x snapshots / time")
+    return rate, dt, desc
+
+
+def config_1h(wl):
+    return {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "nz": wl.nz, "snapshots": wl.nsnap,
+            "pairs": wl.npair, "precision": "f64", "Lx": round(wl.Lx, 6), "nu": wl.nu,
+            "l2": "operands, spectra and terms larger than L2 (no flush)"}
+
+
+def run_one_homog(args, world, rank, local):
+    """The GKE of a flow homogeneous in x only (a duct): all snapshots per
+    step, inputs resident on the device; e2e through pinned host buffers."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    torch.cuda.set_device(local)
+    wl = S.DUCT_WORKLOADS[args.workload]
+    ns = wl.nsnap
+    coef = S.duct_coefficients(wl)
+    stream = torch.cuda.current_stream()
+    y, z = S.cgl_grid(wl.ny), S.cgl_grid(wl.nz)
+    plan = N.gke1h_plan(wl.nx, wl.ny, wl.nz, wl.Lx, wl.nu, y, z, ns, stream=stream.cuda_stream)
+    f_dev = torch.from_numpy(coef).cuda()
+    terms = torch.empty((N.GKE1H_NTERM, wl.npair, wl.nx), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        N.gke1h_compute(plan, f_dev, ns, terms)
+    torch.cuda.synchronize()
+    l0 = N.gke1h_launch_count(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            N.gke1h_compute(plan, f_dev, ns, terms)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = N.gke1h_launch_count(plan) - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-stage device times of one more pass (events on the plan's stream)
+    N.gke1h_set_timing(plan, True)
+    N.gke1h_compute(plan, f_dev, ns, terms)
+    stage_ms = N.gke1h_stage_times(plan)
+    N.gke1h_set_timing(plan, False)
+    e2e = None
+    if not args.no_e2e:
+        f_h = torch.from_numpy(coef).pin_memory()
+        t_h = torch.empty(tuple(terms.shape), dtype=torch.float64).pin_memory()
+        N.gke1h_compute(plan, f_h, ns, t_h)
+        t0 = time.perf_counter()
+        for _ in range(2):
+            N.gke1h_compute(plan, f_h, ns, t_h)
+        ms_e2e = (time.perf_counter() - t0) * 1e3 / 2
+        e2e = {"value": wl.npair * ns / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+               "h2d_bytes_per_step": int(f_h.numel() * 16), "d2h_bytes_per_step": int(t_h.numel() * 8)}
+        del t_h
+    del terms
+    N.gke1h_destroy(plan)
+    pk, pk_kind = peaks()
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    cms = stage_ms.get("correlate", 0.0)
+    flops = 8.0 * correlator_cmac_1h(wl, ns)
+    ach = flops / (cms / 1e3) / 1e12 if cms > 0 else 0.0
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "flops": flops, "launch_ms": cms, "traffic": None, "stage": "correlate",
+            "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock (nominal 1.25 TFLOP/s FP64)"}
+    cpu = None
+    if not args.no_cpu:
+        phys = S.duct_physical(wl)
+        rate, dt, desc = oracle_sample_1h(wl, phys, args.cpu_points // 8)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc,
+               "seconds": dt}
+    line = {"metric": METRIC_1H, "value": wl.npair * ns / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_1h(wl),
+            "roofline": roof, "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "e2e": e2e,
+            "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference_1h(args, world, rank):
+    if rank != 0:
+        return
+    wl = S.DUCT_WORKLOADS[args.workload]
+    phys = S.duct_physical(wl)
+    from oracle import one_homog as O1
+    O1.build()
+    npts = max(8, args.ref_points // 8)
+    for _ in range(args.warmup):
+        oracle_sample_1h(wl, phys, 8, seed=99)
+    times, rates = [], []
+    for k in range(args.steps):
+        r, dt, desc = oracle_sample_1h(wl, phys, npts, seed=k)
+        times.append(dt)
+        rates.append(r)
+    value = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC_1H, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_1h(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_passes_1h(args):
+    """P untimed passes of the one-direction plan (profiling target)."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    wl = S.DUCT_WORKLOADS[args.workload]
+    plan = N.gke1h_plan(wl.nx, wl.ny, wl.nz, wl.Lx, wl.nu, S.cgl_grid(wl.ny), S.cgl_grid(wl.nz), wl.nsnap,
+                        stream=torch.cuda.current_stream().cuda_stream)
+    f_dev = torch.from_numpy(S.duct_coefficients(wl)).cuda()
+    terms = torch.empty((N.GKE1H_NTERM, wl.npair, wl.nx), dtype=torch.float64, device="cuda")
+    for p in range(args.passes):
+        l0 = N.gke1h_launch_count(plan)
+        N.gke1h_compute(plan, f_dev, wl.nsnap, terms)
+        torch.cuda.synchronize()
+        print(f"pass {p}: {N.gke1h_launch_count(plan) - l0} launches", flush=True)
+    N.gke1h_destroy(plan)
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_1910_06409_gb300._native as N
@@ -792,7 +942,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("f64", "bf16x3", "f32"), default="f64")
-    ap.add_argument("--workload", default=S.RETAU200.name, choices=sorted(S.WORKLOADS) + ["group"])
+    ap.add_argument("--workload", default=S.RETAU200.name,
+                    choices=sorted(S.WORKLOADS) + sorted(S.DUCT_WORKLOADS) + ["group"],
+                    help="a channel workload, 'group', or a duct (one homogeneous direction)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-split", action="store_true",
@@ -811,11 +963,14 @@ def main():
     ap.add_argument("--passes", type=int, default=0,
                     help="profiling target: run this many untimed passes, print launches per pass, exit")
     args = ap.parse_args()
+    duct = args.workload in S.DUCT_WORKLOADS
     if args.passes > 0:
-        run_passes(args)
+        (run_passes_1h if duct else run_passes)(args)
         return
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if duct:
+        (run_reference_1h(args, world, rank) if args.impl == "reference" else run_one_homog(args, world, rank, local))
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     elif args.step1:
         run_step1(args, world, rank, local)

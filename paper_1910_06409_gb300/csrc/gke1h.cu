@@ -13,11 +13,13 @@
 //              operand blocks X[f][m_x][s][p] and the one-point sums.
 //              k1_onepoint: eps (Parseval in x, stencils in y and z) and the
 //              one-point parts of the terms.
-//   correlate  k1_correlate, one CTA per (m_x, tile pair): the snapshot sums
+//   correlate  k1_correlate, one CTA per (tile pair, m_x): the snapshot sums
 //              of the correlation products of Eq. 7 (Parseval, Eq. 8-9), 20
 //              contractions, each added into the per-pair term spectra with
 //              its coefficients; then the one-point parts and the mean-flow
-//              couplings.  Only term spectra reach HBM.
+//              couplings.  Only term spectra reach HBM.  A remainder of at
+//              most 8 points past the last full tile runs as strips
+//              (k1_correlate_strip) instead of as padded tiles.
 //   terms      k1_transform: the inverse x transform of every (term, pair).
 //   stencil    k1_stencil_a: the Step-3 parts -2 nu dA/dr_y, -2 nu dA/dr_z,
 //              -(nu/2) dA/dY, -(nu/2) dA/dZ (Eq. 10-11 in y and in z);
@@ -233,34 +235,38 @@ k1_products(const zd* __restrict__ f, int ns, int P, int nx, const zd* __restric
 
 // eps by Parseval in x (signed wavenumber, 0 at the Nyquist index; weight 2
 // on the interior wavenumbers) with stencil derivatives in y and z of the
-// operand blocks; then the one-point parts of the terms.
-__global__ void k1_onepoint(const zd* __restrict__ X, int ns, int ny, int nz, int nx, double kx0, double nu,
-                            const double* __restrict__ wy, const int* __restrict__ ly, const double* __restrict__ wz,
-                            const int* __restrict__ lz, const double* __restrict__ m1, double* __restrict__ prof,
-                            double* __restrict__ op)
+// operand blocks; then the one-point parts of the terms.  One CTA per point:
+// the threads share the (component, wavenumber, snapshot) triples.
+__global__ void __launch_bounds__(128)
+k1_onepoint(const zd* __restrict__ X, int ns, int ny, int nz, int nx, double kx0, double nu,
+            const double* __restrict__ wy, const int* __restrict__ ly, const double* __restrict__ wz,
+            const int* __restrict__ lz, const double* __restrict__ m1, double* __restrict__ prof,
+            double* __restrict__ op)
 {
     const int P = ny * nz, nxh = nx / 2 + 1;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= P) return;
+    const int p = blockIdx.x;
     const int iy = p / nz, iz = p - iy * nz;
     double e = 0.0;
-    for (int i = 0; i < 3; ++i)
-        for (int m = 0; m < nxh; ++m) {
-            const double k = (2 * m == nx) ? 0.0 : kx0 * m;
-            const double ck = (m == 0 || 2 * m == nx) ? 1.0 : 2.0;
-            const zd* B = X + ((long long)i * nxh + m) * ns * P;
-            for (int s = 0; s < ns; ++s) {
-                const zd* row = B + (long long)s * P;
-                const zd a = row[p];
-                zd dy = mk(0.0, 0.0), dz = mk(0.0, 0.0);
-                for (int l = 0; l < 5; ++l) {
-                    const zd t = row[(ly[iy] + l) * nz + iz], u = row[iy * nz + lz[iz] + l];
-                    dy.x = fma(wy[5 * iy + l], t.x, dy.x); dy.y = fma(wy[5 * iy + l], t.y, dy.y);
-                    dz.x = fma(wz[5 * iz + l], u.x, dz.x); dz.y = fma(wz[5 * iz + l], u.y, dz.y);
-                }
-                e += ck * (k * k * (a.x * a.x + a.y * a.y) + dy.x * dy.x + dy.y * dy.y + dz.x * dz.x + dz.y * dz.y);
-            }
+    for (int t = threadIdx.x; t < 3 * nxh * ns; t += blockDim.x) {
+        const int i = t / (nxh * ns), r = t - i * nxh * ns, m = r / ns, s = r - m * ns;
+        const double k = (2 * m == nx) ? 0.0 : kx0 * m;
+        const double ck = (m == 0 || 2 * m == nx) ? 1.0 : 2.0;
+        const zd* row = X + (((long long)i * nxh + m) * ns + s) * P;
+        const zd a = row[p];
+        zd dy = mk(0.0, 0.0), dz = mk(0.0, 0.0);
+        for (int l = 0; l < 5; ++l) {
+            const zd t1 = row[(ly[iy] + l) * nz + iz], t2 = row[iy * nz + lz[iz] + l];
+            dy.x = fma(wy[5 * iy + l], t1.x, dy.x); dy.y = fma(wy[5 * iy + l], t1.y, dy.y);
+            dz.x = fma(wz[5 * iz + l], t2.x, dz.x); dz.y = fma(wz[5 * iz + l], t2.y, dz.y);
         }
+        e += ck * (k * k * (a.x * a.x + a.y * a.y) + dy.x * dy.x + dy.y * dy.y + dz.x * dz.x + dz.y * dz.y);
+    }
+    __shared__ double red[4];
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    e = red[0] + red[1] + red[2] + red[3];
     const double eps = nu * e / ns;
     prof[(long long)R_EPS * P + p] = eps;
     auto M = [&](int k) { return m1[(long long)k * P + p]; };
@@ -280,6 +286,7 @@ __global__ void k1_onepoint(const zd* __restrict__ X, int ns, int ny, int nz, in
 // -------------------------------------------------------------- correlate
 #define CT 32        // tile edge (points)
 #define SCH 8        // snapshots per shared-memory chunk
+#define STRIP_MAX 8  // widest remainder past the last full tile done as strips
 
 __device__ __forceinline__ void cmac(zd& acc, const zd a, const zd b)     // acc += conj(a) b
 {
@@ -289,8 +296,74 @@ __device__ __forceinline__ void cmac(zd& acc, const zd a, const zd b)     // acc
     acc.y = fma(-a.y, b.x, acc.y);
 }
 
-// CTA = (tile pair T1 <= T2, wavenumber m); 16 x 16 threads, each an RB x RB
-// block of pairs (p1 = T1 CT + ty + 16 a, p2 = T2 CT + tx + 16 b).
+// add contraction jb's value at (q1, q2) into the accumulators of that pair
+__device__ __forceinline__ void add_job(zd* T, const Job& jb, const zd acc, int q1, int q2, int P,
+                                        const double* __restrict__ prof)
+{
+    #pragma unroll
+    for (int t = 0; t < 6; ++t) {
+        const double c = jb.c[t];
+        if (c == 0.0) continue;
+        T[t].x = fma(c, acc.x, T[t].x);
+        T[t].y = fma(c, acc.y, T[t].y);
+    }
+    if (jb.ra >= 0) {
+        // xi: <u_a(p1) u_b(p2)'> enters -2 <du_i du_k> (d_k U_i)* - 2 <du_i u_k*> d(d_k U_i)
+        // with weight 2 d_b U_a(p2) (b = y, z) + 2 d_a U_b(p1) (a = y, z)
+        const int ra = jb.ra, rb = jb.rb;
+        double c = 0.0;
+        if (rb >= 1 && q2 < P) c += 2.0 * prof[(long long)(R_G + 2 * ra + rb - 1) * P + q2];
+        if (ra >= 1 && q1 < P) c += 2.0 * prof[(long long)(R_G + 2 * rb + ra - 1) * P + q1];
+        T[A_XI].x = fma(c, acc.x, T[A_XI].x);
+        T[A_XI].y = fma(c, acc.y, T[A_XI].y);
+    }
+}
+
+// snapshot average, one-point parts (m = 0), mean-flow couplings and the
+// residual's spectral part; writes the eight spectra of pair (q1 <= q2)
+__device__ __forceinline__ void finish_pair(const zd* T, int q1, int q2, int m, int nx, double kx0, double nu,
+                                            int ns, int P, const double* __restrict__ prof,
+                                            const double* __restrict__ op, zd* __restrict__ spec, long long npair)
+{
+    const int nxh = nx / 2 + 1;
+    const double inv = 1.0 / ns;
+    const double k = (2 * m == nx) ? 0.0 : kx0 * m;
+    zd v[NACC];
+    #pragma unroll
+    for (int t = 0; t < NACC; ++t) v[t] = mk(T[t].x * inv, T[t].y * inv);
+    auto O = [&](int r, int q) { return op[(long long)r * P + q]; };
+    auto U = [&](int r, int q) { return prof[(long long)r * P + q]; };
+    if (m == 0) {
+        v[A_A].x += O(O_K, q1) + O(O_K, q2);
+        v[A_PHIX].x += O(O_SX, q2) - O(O_SX, q1);
+        v[A_PHIY].x += O(O_SY, q2) - O(O_SY, q1);
+        v[A_PHIZ].x += O(O_SZ, q2) - O(O_SZ, q1);
+        v[A_PSIY].x += 0.5 * (O(O_SY, q1) + O(O_SY, q2)) + 2.0 * (O(O_PY, q1) + O(O_PY, q2));
+        v[A_PSIZ].x += 0.5 * (O(O_SZ, q1) + O(O_SZ, q2)) + 2.0 * (O(O_PZ, q1) + O(O_PZ, q2));
+        v[A_XI].x += O(O_E0, q1) + O(O_E0, q2);
+    }
+    const zd A = v[A_A];
+    const double dU = U(R_U, q2) - U(R_U, q1), dV = U(R_V, q2) - U(R_V, q1), dW = U(R_W, q2) - U(R_W, q1);
+    const double Vs = 0.5 * (U(R_V, q1) + U(R_V, q2)), Ws = 0.5 * (U(R_W, q1) + U(R_W, q2));
+    // Phi_x += dU A - 2 nu (i k) A
+    v[A_PHIX].x += dU * A.x + 2.0 * nu * k * A.y;
+    v[A_PHIX].y += dU * A.y - 2.0 * nu * k * A.x;
+    v[A_PHIY].x += dV * A.x; v[A_PHIY].y += dV * A.y;
+    v[A_PHIZ].x += dW * A.x; v[A_PHIZ].y += dW * A.y;
+    v[A_PSIY].x += Vs * A.x; v[A_PSIY].y += Vs * A.y;
+    v[A_PSIZ].x += Ws * A.x; v[A_PSIZ].y += Ws * A.y;
+    // residual spectrum: i k Phi_x - xi (the stencil parts come later)
+    const zd res = mk(-k * v[A_PHIX].y - v[A_XI].x, k * v[A_PHIX].x - v[A_XI].y);
+    const long long pr = tri(q1, q2, P);
+    #pragma unroll
+    for (int t = 0; t < NACC; ++t) spec[((long long)t * nxh + m) * npair + pr] = v[t];
+    spec[((long long)NACC * nxh + m) * npair + pr] = res;
+}
+
+// CTA = (tile pair T1 <= T2 of the nt full tiles, wavenumber m); 16 x 16
+// threads, each an RB x RB block of pairs (p1 = T1 CT + ty + 16 a,
+// p2 = T2 CT + tx + 16 b).  With strips, the points past the last full tile
+// are left to k1_correlate_strip; otherwise the last tile is padded.
 __global__ void __launch_bounds__(256, 1)
 k1_correlate(const zd* __restrict__ X, int ns, int P, int nx, int nt, double kx0, double nu,
              const double* __restrict__ prof, const double* __restrict__ op, zd* __restrict__ spec, long long npair)
@@ -359,7 +432,7 @@ k1_correlate(const zd* __restrict__ X, int ns, int P, int nx, int nt, double kx0
                     acc[a][b].y = fma(wt, part[a][b].y, acc[a][b].y);
                 }
         }
-        // add the contraction into the term spectra
+        // the contraction into the term spectra (as add_job, one coefficient test per job)
         #pragma unroll
         for (int t = 0; t < 6; ++t) {
             const double c = jb.c[t];
@@ -373,8 +446,6 @@ k1_correlate(const zd* __restrict__ X, int ns, int P, int nx, int nt, double kx0
                 }
         }
         if (jb.ra >= 0) {
-            // xi: <u_a(p1) u_b(p2)'> enters -2 <du_i du_k> (d_k U_i)* - 2 <du_i u_k*> d(d_k U_i)
-            // with weight 2 d_b U_a(p2) (b = y, z) + 2 d_a U_b(p1) (a = y, z)
             const int ra = jb.ra, rb = jb.rb;
             #pragma unroll
             for (int a = 0; a < RB; ++a)
@@ -388,52 +459,62 @@ k1_correlate(const zd* __restrict__ X, int ns, int P, int nx, int nt, double kx0
                 }
         }
     }
-    // snapshot average, one-point parts (m = 0), mean-flow couplings, residual
-    const double inv = 1.0 / ns;
-    const double k = (2 * m == nx) ? 0.0 : kx0 * m;
     #pragma unroll
     for (int a = 0; a < RB; ++a)
         #pragma unroll
         for (int b = 0; b < RB; ++b) {
-            const int q1 = p1[a], q2 = p2[b];
-            if (q1 >= P || q2 >= P || q2 < q1) continue;
+            if (p1[a] >= P || p2[b] >= P || p2[b] < p1[a]) continue;
             zd v[NACC];
             #pragma unroll
-            for (int t = 0; t < NACC; ++t) v[t] = mk(T[t][a][b].x * inv, T[t][a][b].y * inv);
-            auto O = [&](int r, int q) { return op[(long long)r * P + q]; };
-            auto U = [&](int r, int q) { return prof[(long long)r * P + q]; };
-            if (m == 0) {
-                v[A_A].x += O(O_K, q1) + O(O_K, q2);
-                v[A_PHIX].x += O(O_SX, q2) - O(O_SX, q1);
-                v[A_PHIY].x += O(O_SY, q2) - O(O_SY, q1);
-                v[A_PHIZ].x += O(O_SZ, q2) - O(O_SZ, q1);
-                v[A_PSIY].x += 0.5 * (O(O_SY, q1) + O(O_SY, q2)) + 2.0 * (O(O_PY, q1) + O(O_PY, q2));
-                v[A_PSIZ].x += 0.5 * (O(O_SZ, q1) + O(O_SZ, q2)) + 2.0 * (O(O_PZ, q1) + O(O_PZ, q2));
-                v[A_XI].x += O(O_E0, q1) + O(O_E0, q2);
-            }
-            const zd A = v[A_A];
-            const double dU = U(R_U, q2) - U(R_U, q1), dV = U(R_V, q2) - U(R_V, q1), dW = U(R_W, q2) - U(R_W, q1);
-            const double Vs = 0.5 * (U(R_V, q1) + U(R_V, q2)), Ws = 0.5 * (U(R_W, q1) + U(R_W, q2));
-            // Phi_x += dU A - 2 nu (i k) A
-            v[A_PHIX].x += dU * A.x + 2.0 * nu * k * A.y;
-            v[A_PHIX].y += dU * A.y - 2.0 * nu * k * A.x;
-            v[A_PHIY].x += dV * A.x; v[A_PHIY].y += dV * A.y;
-            v[A_PHIZ].x += dW * A.x; v[A_PHIZ].y += dW * A.y;
-            v[A_PSIY].x += Vs * A.x; v[A_PSIY].y += Vs * A.y;
-            v[A_PSIZ].x += Ws * A.x; v[A_PSIZ].y += Ws * A.y;
-            // residual spectrum: i k Phi_x - xi (the stencil parts come later)
-            const zd res = mk(-k * v[A_PHIX].y - v[A_XI].x, k * v[A_PHIX].x - v[A_XI].y);
-            const long long pr = tri(q1, q2, P);
-            #pragma unroll
-            for (int t = 0; t < NACC; ++t) spec[((long long)t * nxh + m) * npair + pr] = v[t];
-            spec[((long long)NACC * nxh + m) * npair + pr] = res;
+            for (int t = 0; t < NACC; ++t) v[t] = T[t][a][b];
+            finish_pair(v, p1[a], p2[b], m, nx, kx0, nu, ns, P, prof, op, spec, npair);
         }
 }
 
+// The pairs (p1 <= p2) with p2 >= cov (the points past the last full tile):
+// one thread per (pair, wavenumber), the same contractions one pair at a time;
+// consecutive threads take consecutive p1 (coalesced operand loads).
+__global__ void __launch_bounds__(128)
+k1_correlate_strip(const zd* __restrict__ X, int ns, int P, int nx, int cov, double kx0, double nu,
+                   const double* __restrict__ prof, const double* __restrict__ op, zd* __restrict__ spec,
+                   long long npair)
+{
+    const int nxh = nx / 2 + 1;
+    const int rem = P - cov;
+    // pairs of the strip: p2 = cov + r, p1 = 0 .. p2; n = rem cov + rem (rem + 1) / 2
+    const long long n = (long long)rem * cov + (long long)rem * (rem + 1) / 2;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * nxh) return;
+    const int m = (int)(e / n);                       // consecutive threads: consecutive p1 of one p2
+    long long k = e - (long long)m * n;
+    int r = 0;
+    while (k >= cov + r + 1) { k -= cov + r + 1; ++r; }
+    const int q2 = cov + r, q1 = (int)k;
+    zd T[NACC];
+    #pragma unroll
+    for (int t = 0; t < NACC; ++t) T[t] = mk(0.0, 0.0);
+    for (int j = 0; j < NJ; ++j) {
+        const Job& jb = c_job[j];
+        zd acc = mk(0.0, 0.0);
+        for (int t = 0; t < jb.nt; ++t) {
+            const zd* A = X + ((long long)jb.fa[t] * nxh + m) * ns * P;
+            const zd* B = X + ((long long)jb.fb[t] * nxh + m) * ns * P;
+            zd part = mk(0.0, 0.0);
+            for (int s = 0; s < ns; ++s) cmac(part, A[(long long)s * P + q1], B[(long long)s * P + q2]);
+            acc.x = fma(jb.w[t], part.x, acc.x);
+            acc.y = fma(jb.w[t], part.y, acc.y);
+        }
+        add_job(T, jb, acc, q1, q2, P, prof);
+    }
+    finish_pair(T, q1, q2, m, nx, kx0, nu, ns, P, prof, op, spec, npair);
+}
+
 // ------------------------------------------------------------- transforms
-// CTA = NB consecutive pairs of one term: the Hermitian spectrum of each pair
-// (nx/2 + 1 wavenumbers, imaginary parts dropped at m = 0 and m = nx/2), the
-// block inverse transform, the real parts written as terms[t][pair][m_x].
+// CTA = 2 NB consecutive pairs of one term.  The spectra (nx/2 + 1
+// wavenumbers each, imaginary parts dropped at m = 0 and m = nx/2) are
+// staged in shared memory; pairs 2b and 2b + 1 share one complex sequence,
+// H_2b + i H_2b+1 with H the Hermitian extension, whose inverse transform
+// has the two real correlations as its real and imaginary parts.
 __global__ void __launch_bounds__(256)
 k1_transform(const zd* __restrict__ spec, int nx, long long npair, int NB, const zd* __restrict__ tw,
              double* __restrict__ terms)
@@ -443,23 +524,32 @@ k1_transform(const zd* __restrict__ spec, int nx, long long npair, int NB, const
     zd* b0 = sm;
     zd* b1 = sm + (size_t)NB * nx;
     zd* stw = sm + (size_t)2 * NB * nx;
+    zd* stg = stw + nx;                               // [2 NB][nxh]
     gke::load_twiddles(stw, tw, nx);
     const int t = blockIdx.y;
-    const long long pr0 = (long long)blockIdx.x * NB;
-    const int nb = (int)std::min<long long>(NB, npair - pr0);
-    for (int e = threadIdx.x; e < nxh * NB; e += blockDim.x) {
-        const int m = e / NB, b = e - m * NB;
-        if (b >= nb) continue;
-        zd v = spec[((long long)t * nxh + m) * npair + pr0 + b];
+    const long long pr0 = (long long)blockIdx.x * 2 * NB;
+    const int np = (int)std::min<long long>(2 * NB, npair - pr0);
+    for (int e = threadIdx.x; e < nxh * 2 * NB; e += blockDim.x) {
+        const int m = e / (2 * NB), c = e - m * 2 * NB;
+        zd v = mk(0.0, 0.0);
+        if (c < np) v = spec[((long long)t * nxh + m) * npair + pr0 + c];
         if (m == 0 || 2 * m == nx) v.y = 0.0;
-        b0[b * nx + m] = v;
-        if (m > 0 && 2 * m < nx) b0[b * nx + nx - m] = mk(v.x, -v.y);
+        stg[c * nxh + m] = v;
     }
-    for (int e = threadIdx.x; e < (NB - nb) * nx; e += blockDim.x) b0[nb * nx + e] = mk(0.0, 0.0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < NB * nx; e += blockDim.x) {
+        const int b = e / nx, k = e - b * nx;
+        const bool lo = 2 * k <= nx;
+        const zd a = stg[(2 * b) * nxh + (lo ? k : nx - k)];
+        const zd c = stg[(2 * b + 1) * nxh + (lo ? k : nx - k)];
+        const double ay = lo ? a.y : -a.y, cy = lo ? c.y : -c.y;
+        b0[b * nx + k] = mk(a.x - cy, ay + c.x);
+    }
     zd* r = gke::fft_block<double, true>(b0, b1, nx, NB, nx, stw);
-    for (int e = threadIdx.x; e < nb * nx; e += blockDim.x) {
-        const int b = e / nx, x = e - b * nx;
-        terms[((long long)t * npair + pr0 + b) * nx + x] = r[b * nx + x].x;
+    for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
+        const int c = e / nx, x = e - c * nx;
+        const zd z = r[(c >> 1) * nx + x];
+        terms[((long long)t * npair + pr0 + c) * nx + x] = (c & 1) ? z.y : z.x;
     }
 }
 
@@ -675,7 +765,7 @@ extern "C" gke_status gke1h_plan(const gke1h_desc* d, void* stream, gke1h_plan_t
     if (s != GKE_OK) { free_plan(p); return fail1(nullptr, s, "uploading the plan's tables failed"); }
     p->smem_prod = (int)(sizeof(zd) * (14 * p->nx + p->nx));
     p->NB = std::max(1, 2048 / p->nx);
-    p->smem_tr = (int)(sizeof(zd) * (2 * p->NB * p->nx + p->nx));
+    p->smem_tr = (int)(sizeof(zd) * (3 * p->NB * p->nx + 2 * p->NB + p->nx));
     if (cudaFuncSetAttribute(k1_products, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_prod) != cudaSuccess ||
         cudaFuncSetAttribute(k1_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_tr) != cudaSuccess) {
         cudaGetLastError();
@@ -730,20 +820,30 @@ extern "C" gke_status gke1h_compute(gke1h_plan_t p, const void* fields, int nsna
     {
         Scope1 sc(p, GKE_STAGE_PRODUCTS);
         k1_products<<<P, 256, p->smem_prod, p->st>>>(f, ns, P, nx, p->tw, p->prof, p->X, p->m1, p->bad);
-        k1_onepoint<<<(P + 127) / 128, 128, 0, p->st>>>(p->X, ns, p->ny, p->nz, nx, kx0, p->nu, p->wy, p->ly,
+        k1_onepoint<<<P, 128, 0, p->st>>>(p->X, ns, p->ny, p->nz, nx, kx0, p->nu, p->wy, p->ly,
                                                         p->wz, p->lz, p->m1, p->prof, p->op);
         p->launches += 2;
     }
     {
         Scope1 sc(p, GKE_STAGE_CORRELATE);
-        const long long ntp = (long long)p->nt * (p->nt + 1) / 2;
-        k1_correlate<<<dim3((unsigned)ntp, nxh), 256, 0, p->st>>>(p->X, ns, P, nx, p->nt, kx0, p->nu, p->prof,
+        const int nfull = P / CT, rem = P - nfull * CT;
+        const bool strips = nfull > 0 && rem > 0 && rem <= STRIP_MAX;
+        const int nt = strips ? nfull : p->nt;
+        const long long ntp = (long long)nt * (nt + 1) / 2;
+        k1_correlate<<<dim3((unsigned)ntp, nxh), 256, 0, p->st>>>(p->X, ns, P, nx, nt, kx0, p->nu, p->prof,
                                                                   p->op, p->spec, p->npair);
         p->launches += 1;
+        if (strips) {
+            const int cov = nfull * CT;
+            const long long n = ((long long)rem * cov + (long long)rem * (rem + 1) / 2) * nxh;
+            k1_correlate_strip<<<(unsigned)((n + 127) / 128), 128, 0, p->st>>>(p->X, ns, P, nx, cov, kx0, p->nu,
+                                                                              p->prof, p->op, p->spec, p->npair);
+            p->launches += 1;
+        }
     }
     {
         Scope1 sc(p, GKE_STAGE_TERMS);
-        const long long nblk = (p->npair + p->NB - 1) / p->NB;
+        const long long nblk = (p->npair + 2 * p->NB - 1) / (2 * p->NB);
         k1_transform<<<dim3((unsigned)nblk, GKE1H_NTERM), 256, p->smem_tr, p->st>>>(p->spec, nx, p->npair, p->NB,
                                                                                  p->tw, T);
         p->launches += 1;

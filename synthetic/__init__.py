@@ -244,7 +244,10 @@ class DuctWorkload:
 # cross-section pairs and a ragged tail), and the benchmark's duct
 DUCT_TINY = DuctWorkload("duct_16x9x7_s4", 11, 16, 9, 7, 4)
 DUCT = DuctWorkload("duct_256x33x33_s16", 12, 256, 33, 33, 16)
-DUCT_WORKLOADS = {w.name: w for w in (DUCT_TINY, DUCT)}
+# the benchmark's x grid and snapshot count on a 17 x 17 cross section: the
+# spectra (0.7 GB) exceed L2, small enough for multi-pass profiler captures
+DUCT_PROFILE = DuctWorkload("duct_256x17x17_s16", 13, 256, 17, 17, 16)
+DUCT_WORKLOADS = {w.name: w for w in (DUCT_TINY, DUCT, DUCT_PROFILE)}
 
 
 def duct_small(nx: int, ny: int, nz: int, nsnap: int, wid: int = 91, Lx: float = 4.0 * math.pi,
