@@ -20,7 +20,8 @@
 //              couplings.  Only term spectra reach HBM.  A remainder of at
 //              most 8 points past the last full tile runs as strips
 //              (k1_correlate_strip) instead of as padded tiles.
-//   terms      k1_transform: the inverse x transform of every (term, pair).
+//   terms      k1_transform_r (nx = 128, 256, 512; register FFT) or
+//              k1_transform: the inverse x transform of every (term, pair).
 //   stencil    k1_stencil_a: the Step-3 parts -2 nu dA/dr_y, -2 nu dA/dr_z,
 //              -(nu/2) dA/dY, -(nu/2) dA/dZ (Eq. 10-11 in y and in z);
 //              k1_stencil_res: the residual's r_y, r_z, Y, Z divergences.
@@ -553,71 +554,143 @@ k1_transform(const zd* __restrict__ spec, int nx, long long npair, int NB, const
     }
 }
 
-// --------------------------------------------------------------- stencils
-// Value of term t at the ordered pair (q1, q2), separation index m: stored
-// when q1 <= q2, else by r-inversion from (q2, q1, -m) with sign sg.
-__device__ __forceinline__ double at_pair(const double* __restrict__ plane, int q1, int q2, int m, int nx, int P,
-                                          long long npair, double sg)
+// Register-FFT variant for nx = N1 N2 (gke::fft2l, twiddles resolved at
+// compile time): CTA = RZ sequences x N2 lanes, each sequence two pairs
+// packed as above; lane l holds the wavenumbers l + N2 j of its sequence.
+template <int N1, int N2>
+__global__ void __launch_bounds__(256)
+k1_transform_r(const zd* __restrict__ spec, long long npair, const zd* __restrict__ tw, double* __restrict__ terms)
 {
-    (void)npair;
-    if (q1 <= q2) return plane[tri(q1, q2, P) * nx + m];
-    const int mm = m == 0 ? 0 : nx - m;
-    return sg * plane[tri(q2, q1, P) * nx + mm];
+    constexpr int N = N1 * N2, nxh = N / 2 + 1, RZ = 256 / N2;
+    extern __shared__ zd sm[];
+    zd* stw = sm;
+    zd* xs = sm + N;
+    const int lane = threadIdx.x % N2, r = threadIdx.x / N2;
+    const int t = blockIdx.y;
+    const long long pa = ((long long)blockIdx.x * RZ + r) * 2, pb = pa + 1;
+    const bool la = pa < npair, lb = pb < npair;
+    gke::load_twiddles(stw, tw, N);
+    // spectra [t][m][pair]: the two pairs of a sequence share 32-byte sectors
+    const zd* sa = spec + (long long)t * nxh * npair + (la ? pa : 0);
+    const zd* sb = spec + (long long)t * nxh * npair + (lb ? pb : 0);
+    zd v[N1];
+    #pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const int k = lane + N2 * j;
+        const bool lo = 2 * k <= N;
+        zd a = mk(0.0, 0.0), b = a;
+        if (la) { a = sa[(long long)(lo ? k : N - k) * npair]; if (!lo) a.y = -a.y; }
+        if (lb) { b = sb[(long long)(lo ? k : N - k) * npair]; if (!lo) b.y = -b.y; }
+        if (k == 0 || 2 * k == N) { a.y = 0.0; b.y = 0.0; }
+        v[j] = mk(a.x - b.y, a.y + b.x);
+    }
+    __syncthreads();                                  // twiddles staged
+    gke::fft2l<double, N1, N2, true>(v, lane, xs + r * N1 * (N2 + 1), N2 + 1, 1, stw);
+    #pragma unroll
+    for (int j = 0; j < N1; ++j) {
+        const int x = lane + N2 * j;
+        if (la) terms[((long long)t * npair + pa) * N + x] = v[j].x;
+        if (lb) terms[((long long)t * npair + pb) * N + x] = v[j].y;
+    }
 }
 
+// --------------------------------------------------------------- stencils
+// CTA = G pairs (4, or 256 / nx below nx = 64).  The 20 neighbour pairs of each pair
+// (5 stencil nodes in each of Y1, Y2, Z1, Z2) are resolved once per CTA into
+// shared memory: the offset of the stored pair's row and whether it is the
+// r-inverted one (q1 > q2: read (q2, q1) at -m, times the term's parity).
 struct Sten { const double* wy; const int* ly; const double* wz; const int* lz; int ny, nz; };
 
-// the four stencil derivatives d_Y1, d_Y2, d_Z1, d_Z2 of one plane at (q1, q2, m)
-struct D4 { double y1, y2, z1, z2; };
-__device__ __forceinline__ D4 derivs4(const double* __restrict__ plane, const Sten& S, int q1, int q2, int m,
-                                      int nx, int P, long long npair, double sg)
+constexpr int SG = 32;        // most pairs per CTA (nx >= 8)
+
+__device__ __forceinline__ void neighbours(const Sten& S, const int* __restrict__ pq, long long pr0, int G,
+                                           int nx, long long npair, long long (*off)[20], signed char (*flip)[20],
+                                           double (*w)[20])
 {
-    const int iy1 = q1 / S.nz, iz1 = q1 - iy1 * S.nz, iy2 = q2 / S.nz, iz2 = q2 - iy2 * S.nz;
-    D4 d{0.0, 0.0, 0.0, 0.0};
-    #pragma unroll
-    for (int l = 0; l < 5; ++l) {
-        d.y1 = fma(S.wy[5 * iy1 + l], at_pair(plane, (S.ly[iy1] + l) * S.nz + iz1, q2, m, nx, P, npair, sg), d.y1);
-        d.y2 = fma(S.wy[5 * iy2 + l], at_pair(plane, q1, (S.ly[iy2] + l) * S.nz + iz2, m, nx, P, npair, sg), d.y2);
-        d.z1 = fma(S.wz[5 * iz1 + l], at_pair(plane, iy1 * S.nz + S.lz[iz1] + l, q2, m, nx, P, npair, sg), d.z1);
-        d.z2 = fma(S.wz[5 * iz2 + l], at_pair(plane, q1, iy2 * S.nz + S.lz[iz2] + l, m, nx, P, npair, sg), d.z2);
+    const int P = S.ny * S.nz;
+    for (int e = threadIdx.x; e < G * 20; e += blockDim.x) {
+        const int g = e / 20, j = e - g * 20, dir = j / 5, l = j - dir * 5;
+        const long long pr = pr0 + g;
+        if (pr >= npair) continue;
+        const int q1 = pq[2 * pr], q2 = pq[2 * pr + 1];
+        const int iy1 = q1 / S.nz, iz1 = q1 - iy1 * S.nz, iy2 = q2 / S.nz, iz2 = q2 - iy2 * S.nz;
+        int a = q1, b = q2;
+        double wt;
+        if (dir == 0)      { a = (S.ly[iy1] + l) * S.nz + iz1; wt = S.wy[5 * iy1 + l]; }
+        else if (dir == 1) { b = (S.ly[iy2] + l) * S.nz + iz2; wt = S.wy[5 * iy2 + l]; }
+        else if (dir == 2) { a = iy1 * S.nz + S.lz[iz1] + l;   wt = S.wz[5 * iz1 + l]; }
+        else               { b = iy2 * S.nz + S.lz[iz2] + l;   wt = S.wz[5 * iz2 + l]; }
+        const bool f = a > b;
+        off[g][j] = tri(f ? b : a, f ? a : b, P) * nx;
+        flip[g][j] = f ? 1 : 0;
+        w[g][j] = wt;
     }
-    return d;
+    __syncthreads();
+}
+
+// d_Y1, d_Y2, d_Z1, d_Z2 of one plane at separation m of CTA pair g
+__device__ __forceinline__ void derivs4(const double* __restrict__ plane, const long long* off,
+                                        const signed char* flip, const double* w, int m, int nx, double sg,
+                                        double d[4])
+{
+    const int mm = m == 0 ? 0 : nx - m;
+    #pragma unroll
+    for (int dir = 0; dir < 4; ++dir) {
+        double acc = 0.0;
+        #pragma unroll
+        for (int l = 0; l < 5; ++l) {
+            const int j = 5 * dir + l;
+            const double v = flip[j] ? sg * plane[off[j] + mm] : plane[off[j] + m];
+            acc = fma(w[j], v, acc);
+        }
+        d[dir] = acc;
+    }
 }
 
 __global__ void __launch_bounds__(256)
 k1_stencil_a(double* __restrict__ terms, const int* __restrict__ pq, Sten S, int nx, long long npair, double nu)
 {
-    const int P = S.ny * S.nz;
-    const long long n = npair * nx;
+    __shared__ long long off[SG][20];
+    __shared__ signed char flip[SG][20];
+    __shared__ double w[SG][20];
+    const int G = nx >= 64 ? 4 : 256 / nx;
+    const long long pr0 = (long long)blockIdx.x * G;
+    neighbours(S, pq, pr0, G, nx, npair, off, flip, w);
     const double* Ap = terms + (long long)GKE1H_TERM_A * npair * nx;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long pr = e / nx;
-        const int m = (int)(e - pr * nx);
-        const int q1 = pq[2 * pr], q2 = pq[2 * pr + 1];
-        const D4 d = derivs4(Ap, S, q1, q2, m, nx, P, npair, 1.0);
-        terms[((long long)GKE1H_TERM_PHI_Y * npair + pr) * nx + m] -= nu * (d.y2 - d.y1);
-        terms[((long long)GKE1H_TERM_PHI_Z * npair + pr) * nx + m] -= nu * (d.z2 - d.z1);
-        terms[((long long)GKE1H_TERM_PSI_Y * npair + pr) * nx + m] -= 0.5 * nu * (d.y1 + d.y2);
-        terms[((long long)GKE1H_TERM_PSI_Z * npair + pr) * nx + m] -= 0.5 * nu * (d.z1 + d.z2);
+    for (int e = threadIdx.x; e < G * nx; e += blockDim.x) {
+        const int g = e / nx, m = e - g * nx;
+        const long long pr = pr0 + g;
+        if (pr >= npair) continue;
+        double d[4];
+        derivs4(Ap, off[g], flip[g], w[g], m, nx, 1.0, d);
+        terms[((long long)GKE1H_TERM_PHI_Y * npair + pr) * nx + m] -= nu * (d[1] - d[0]);
+        terms[((long long)GKE1H_TERM_PHI_Z * npair + pr) * nx + m] -= nu * (d[3] - d[2]);
+        terms[((long long)GKE1H_TERM_PSI_Y * npair + pr) * nx + m] -= 0.5 * nu * (d[0] + d[1]);
+        terms[((long long)GKE1H_TERM_PSI_Z * npair + pr) * nx + m] -= 0.5 * nu * (d[2] + d[3]);
     }
 }
 
 __global__ void __launch_bounds__(256)
 k1_stencil_res(double* __restrict__ terms, const int* __restrict__ pq, Sten S, int nx, long long npair)
 {
-    const int P = S.ny * S.nz;
-    const long long n = npair * nx;
+    __shared__ long long off[SG][20];
+    __shared__ signed char flip[SG][20];
+    __shared__ double w[SG][20];
+    const int G = nx >= 64 ? 4 : 256 / nx;
+    const long long pr0 = (long long)blockIdx.x * G;
+    neighbours(S, pq, pr0, G, nx, npair, off, flip, w);
     auto plane = [&](int t) { return terms + (long long)t * npair * nx; };
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const long long pr = e / nx;
-        const int m = (int)(e - pr * nx);
-        const int q1 = pq[2 * pr], q2 = pq[2 * pr + 1];
-        const D4 fy = derivs4(plane(GKE1H_TERM_PHI_Y), S, q1, q2, m, nx, P, npair, -1.0);
-        const D4 fz = derivs4(plane(GKE1H_TERM_PHI_Z), S, q1, q2, m, nx, P, npair, -1.0);
-        const D4 sy = derivs4(plane(GKE1H_TERM_PSI_Y), S, q1, q2, m, nx, P, npair, 1.0);
-        const D4 sz = derivs4(plane(GKE1H_TERM_PSI_Z), S, q1, q2, m, nx, P, npair, 1.0);
+    for (int e = threadIdx.x; e < G * nx; e += blockDim.x) {
+        const int g = e / nx, m = e - g * nx;
+        const long long pr = pr0 + g;
+        if (pr >= npair) continue;
+        double fy[4], fz[4], sy[4], sz[4];
+        derivs4(plane(GKE1H_TERM_PHI_Y), off[g], flip[g], w[g], m, nx, -1.0, fy);
+        derivs4(plane(GKE1H_TERM_PHI_Z), off[g], flip[g], w[g], m, nx, -1.0, fz);
+        derivs4(plane(GKE1H_TERM_PSI_Y), off[g], flip[g], w[g], m, nx, 1.0, sy);
+        derivs4(plane(GKE1H_TERM_PSI_Z), off[g], flip[g], w[g], m, nx, 1.0, sz);
         terms[((long long)GKE1H_TERM_RESIDUAL * npair + pr) * nx + m] +=
-            0.5 * (fy.y2 - fy.y1) + 0.5 * (fz.z2 - fz.z1) + (sy.y1 + sy.y2) + (sz.z1 + sz.z2);
+            0.5 * (fy[1] - fy[0]) + 0.5 * (fz[3] - fz[2]) + (sy[0] + sy[1]) + (sz[2] + sz[3]);
     }
 }
 
@@ -635,6 +708,7 @@ struct gke1h_plan_s {
     int *ly = nullptr, *lz = nullptr, *pq = nullptr, *bad = nullptr;
     zd *tw = nullptr, *X = nullptr, *spec = nullptr, *fin = nullptr;
     int smem_prod = 0, smem_tr = 0, NB = 0;
+    bool reg_tr = false;                 // register-FFT transform (nx = 128, 256, 512)
     bool timing = false;
     struct Mark { int stage; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -766,8 +840,19 @@ extern "C" gke_status gke1h_plan(const gke1h_desc* d, void* stream, gke1h_plan_t
     p->smem_prod = (int)(sizeof(zd) * (14 * p->nx + p->nx));
     p->NB = std::max(1, 2048 / p->nx);
     p->smem_tr = (int)(sizeof(zd) * (3 * p->NB * p->nx + 2 * p->NB + p->nx));
+    cudaError_t ea = cudaSuccess;
+    if (p->nx == 128 || p->nx == 256 || p->nx == 512) {
+        const void* fn = p->nx == 128 ? (const void*)k1_transform_r<16, 8>
+                       : p->nx == 256 ? (const void*)k1_transform_r<16, 16> : (const void*)k1_transform_r<32, 16>;
+        const int n2 = p->nx == 128 ? 8 : 16, n1 = p->nx / n2;
+        p->smem_tr = (int)(sizeof(zd) * (p->nx + (256 / n2) * n1 * (n2 + 1)));
+        ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_tr);
+        p->reg_tr = true;
+    } else {
+        ea = cudaFuncSetAttribute(k1_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_tr);
+    }
     if (cudaFuncSetAttribute(k1_products, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_prod) != cudaSuccess ||
-        cudaFuncSetAttribute(k1_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, p->smem_tr) != cudaSuccess) {
+        ea != cudaSuccess) {
         cudaGetLastError();
         free_plan(p);
         return fail1(nullptr, GKE_ERR_CUDA, "shared-memory attributes refused");
@@ -843,16 +928,25 @@ extern "C" gke_status gke1h_compute(gke1h_plan_t p, const void* fields, int nsna
     }
     {
         Scope1 sc(p, GKE_STAGE_TERMS);
-        const long long nblk = (p->npair + 2 * p->NB - 1) / (2 * p->NB);
-        k1_transform<<<dim3((unsigned)nblk, GKE1H_NTERM), 256, p->smem_tr, p->st>>>(p->spec, nx, p->npair, p->NB,
-                                                                                 p->tw, T);
+        if (p->reg_tr) {
+            const int n2 = nx == 128 ? 8 : 16;
+            const long long per = 2LL * (256 / n2);     // pairs per CTA
+            const dim3 g((unsigned)((p->npair + per - 1) / per), GKE1H_NTERM);
+            if (nx == 128) k1_transform_r<16, 8><<<g, 256, p->smem_tr, p->st>>>(p->spec, p->npair, p->tw, T);
+            else if (nx == 256) k1_transform_r<16, 16><<<g, 256, p->smem_tr, p->st>>>(p->spec, p->npair, p->tw, T);
+            else k1_transform_r<32, 16><<<g, 256, p->smem_tr, p->st>>>(p->spec, p->npair, p->tw, T);
+        } else {
+            const long long nblk = (p->npair + 2 * p->NB - 1) / (2 * p->NB);
+            k1_transform<<<dim3((unsigned)nblk, GKE1H_NTERM), 256, p->smem_tr, p->st>>>(p->spec, nx, p->npair,
+                                                                                     p->NB, p->tw, T);
+        }
         p->launches += 1;
     }
     {
         Scope1 sc(p, GKE_STAGE_STENCIL);
         Sten S{p->wy, p->ly, p->wz, p->lz, p->ny, p->nz};
-        const long long n = p->npair * nx;
-        const int grid = (int)std::min<long long>((n + 255) / 256, 152LL * 16);
+        const int G = nx >= 64 ? 4 : 256 / nx;
+        const unsigned grid = (unsigned)((p->npair + G - 1) / G);
         k1_stencil_a<<<grid, 256, 0, p->st>>>(T, p->pq, S, nx, p->npair, p->nu);
         k1_stencil_res<<<grid, 256, 0, p->st>>>(T, p->pq, S, nx, p->npair);
         p->launches += 2;

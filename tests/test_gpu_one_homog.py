@@ -56,7 +56,7 @@ def _triangle(full):
 
 
 @pytest.mark.parametrize("dims,host", [((16, 9, 7, 4), False), ((24, 6, 11, 3), True), ((8, 5, 5, 1), False),
-                                       ((12, 7, 10, 2), True)])
+                                       ((12, 7, 10, 2), True), ((128, 5, 6, 2), False), ((512, 5, 5, 1), True)])
 def test_full_parity_with_oracle(dims, host):
     nx, ny, nz, ns = dims
     wl = S.duct_small(nx, ny, nz, ns, wid=31)
