@@ -555,6 +555,12 @@ def run_step1(args, world, rank, local):
 METRIC_1H = "GKE one-homogeneous-direction (p1,p2)-pair correlations/s, FP64"
 
 
+# DRAM bytes of one k1_correlate launch on the small case duct_256x17x17_s16
+# (41,905 pairs), scaled in proportion to the pairs of the workload run
+# (profiles/k1_correlate_profile_duct_256x17x17_s16.md)
+NCU_CORR_1H = (0.745e9, 41905)
+
+
 def correlator_cmac_1h(wl, ns):
     """Complex multiply-adds of the one-direction correlator per pass: 37
     contractions over the snapshots for every pair p1 <= p2 and wavenumber
@@ -641,7 +647,9 @@ def run_one_homog(args, world, rank, local):
     flops = 8.0 * correlator_cmac_1h(wl, ns)
     ach = flops / (cms / 1e3) / 1e12 if cms > 0 else 0.0
     roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "flops": flops, "launch_ms": cms, "traffic": None, "stage": "correlate",
+            "flops": flops, "launch_ms": cms, "stage": "correlate",
+            "traffic": int(NCU_CORR_1H[0] * wl.npair / NCU_CORR_1H[1]) if ns == 16 else None,
+            "traffic_note": "small-case ncu capture scaled by pairs",
             "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x max SM clock (nominal 1.25 TFLOP/s FP64)"}
     cpu = None
     if not args.no_cpu:
