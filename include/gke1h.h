@@ -29,7 +29,8 @@
  *     psi_y, psi_z, xi and the residual are even, Phi_x, Phi_y, Phi_z odd
  *     under (p1, p2, r_x) -> (p2, p1, -r_x).
  *   - Separations: m_x in [0, nx), r_x = m_x Lx / nx (periodic).
- *   - Output terms (double, host or device):
+ *   - Output terms (double on GKE_PREC_F64 plans, float on GKE_PREC_F32 plans;
+ *     host or device):
  *       terms[GKE1H_NTERM][npair][nx]
  *     A = <du_i du_i>, then the fluxes in the space of scales
  *       Phi_k = <du_i du_i du_k> + A dU_k - 2 nu dA/dr_k         (k = x, y, z)
@@ -48,7 +49,8 @@
  *   - Profiles (double [GKE1H_NPROF][P], optional): the mean of u, v, w, p over
  *     x and snapshots, the six mean-velocity gradients d_y U, d_z U, d_y V,
  *     d_z V, d_y W, d_z W (stencils), and eps.
- *   - Precision: FP64 throughout.
+ *   - Precision: FP64 throughout (GKE_PREC_F64), or the FP32 variant
+ *     (GKE_PREC_F32; desc.precision).
  *   - Stream: every call is asynchronous on the plan's stream unless an
  *     argument is in host memory (then it returns after the last copy).
  */
@@ -77,16 +79,20 @@ typedef struct {
     const double* y;       /* host pointer, y[ny], strictly increasing; copied              */
     const double* z;       /* host pointer, z[nz], strictly increasing; copied              */
     int max_snap;          /* largest nsnap of any gke1h_compute call (sizes workspaces)  */
+    int precision;         /* GKE_PREC_F64, or GKE_PREC_F32: operands, correlations, term
+                              spectra, transforms and stencils in FP32 (means, products and
+                              one-point sums stay FP64); GKE_PREC_BF16X3: GKE_ERR_UNSUPPORTED */
 } gke1h_desc;
 
 /* Create a plan: validates the descriptor (GKE_ERR_ARG on bad sizes, grids or
  * NULL pointers; GKE_ERR_UNSUPPORTED on nx outside the list above), computes
  * the stencil weights and twiddles on the host and allocates every
- * workspace on the current device (about 16 (8 npair + 11 max_snap P)
- * (nx/2 + 1) bytes; GKE_ERR_OOM if the device has not that much free).
+ * workspace on the current device (about c (8 npair + 11 max_snap P)
+ * (nx/2 + 1) bytes, c = 16 on GKE_PREC_F64 plans and 8 on GKE_PREC_F32;
+ * GKE_ERR_OOM if the device has not that much free).
  * stream: a cudaStream_t (NULL = legacy default stream).  Nothing is
- * allocated later except a staging buffer of 8 GKE1H_NTERM npair nx bytes on
- * the first call with host-memory terms.                                   */
+ * allocated later except a staging buffer of the terms (8 or 4 bytes x
+ * GKE1H_NTERM npair nx) on the first call with host-memory terms.           */
 gke_status gke1h_plan(const gke1h_desc* desc, void* stream, gke1h_plan_t* out);
 
 /* One full evaluation over nsnap snapshots (1 <= nsnap <= max_snap): the
@@ -96,7 +102,7 @@ gke_status gke1h_plan(const gke1h_desc* desc, void* stream, gke1h_plan_t* out);
  * fields, terms and profiles (may be NULL) in host or device memory (layouts
  * above).  GKE_ERR_NONFINITE if the input holds a NaN or Inf (outputs are
  * then undefined).                                                          */
-gke_status gke1h_compute(gke1h_plan_t plan, const void* fields, int nsnap, double* terms, double* profiles);
+gke_status gke1h_compute(gke1h_plan_t plan, const void* fields, int nsnap, void* terms, double* profiles);
 
 /* Number of pairs, P (P + 1) / 2.                                           */
 long long gke1h_npair(gke1h_plan_t plan);

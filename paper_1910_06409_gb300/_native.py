@@ -52,7 +52,7 @@ class gke1h_desc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("Lx", ctypes.c_double), ("nu", ctypes.c_double),
                 ("y", ctypes.POINTER(ctypes.c_double)), ("z", ctypes.POINTER(ctypes.c_double)),
-                ("max_snap", ctypes.c_int)]
+                ("max_snap", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class GkeError(RuntimeError):
@@ -287,12 +287,12 @@ def _check1h(status: int, plan) -> None:
         raise GkeError(status, msg.decode() if msg else "")
 
 
-def gke1h_plan(nx, ny, nz, Lx, nu, y, z, max_snap, stream=None):
+def gke1h_plan(nx, ny, nz, Lx, nu, y, z, max_snap, stream=None, precision=GKE_PREC_F64):
     import numpy as np
     yy = np.ascontiguousarray(y, dtype=np.float64)
     zz = np.ascontiguousarray(z, dtype=np.float64)
     dp = ctypes.POINTER(ctypes.c_double)
-    desc = gke1h_desc(nx, ny, nz, Lx, nu, yy.ctypes.data_as(dp), zz.ctypes.data_as(dp), max_snap)
+    desc = gke1h_desc(nx, ny, nz, Lx, nu, yy.ctypes.data_as(dp), zz.ctypes.data_as(dp), max_snap, precision)
     out = ctypes.c_void_p()
     _check1h(lib().gke1h_plan(ctypes.byref(desc), stream, ctypes.byref(out)), None)
     return out.value

@@ -25,24 +25,27 @@ def _native():
     return N
 
 
-def _run(wl, fields, host=False):
+def _run(wl, fields, host=False, f32=False):
     N = _native()
     y, z = S.cgl_grid(wl.ny), S.cgl_grid(wl.nz)
     plan = N.gke1h_plan(wl.nx, wl.ny, wl.nz, wl.Lx, wl.nu, y, z, wl.nsnap,
-                        stream=torch.cuda.current_stream().cuda_stream)
+                        stream=torch.cuda.current_stream().cuda_stream,
+                        precision=N.GKE_PREC_F32 if f32 else N.GKE_PREC_F64)
     try:
         npair = N.gke1h_npair(plan)
         assert npair == wl.npair
         if host:
-            terms = np.zeros((N.GKE1H_NTERM, npair, wl.nx))
+            terms = np.zeros((N.GKE1H_NTERM, npair, wl.nx), dtype=np.float32 if f32 else np.float64)
             prof = np.zeros((N.GKE1H_NPROF, wl.npoint))
             N.gke1h_compute(plan, fields, wl.nsnap, terms, prof)
+            terms = terms.astype(np.float64)
         else:
-            t = torch.empty((N.GKE1H_NTERM, npair, wl.nx), dtype=torch.float64, device="cuda")
+            t = torch.empty((N.GKE1H_NTERM, npair, wl.nx), dtype=torch.float32 if f32 else torch.float64,
+                            device="cuda")
             pr = torch.empty((N.GKE1H_NPROF, wl.npoint), dtype=torch.float64, device="cuda")
             N.gke1h_compute(plan, torch.from_numpy(fields).cuda(), wl.nsnap, t, pr)
             torch.cuda.synchronize()
-            terms, prof = t.cpu().numpy(), pr.cpu().numpy()
+            terms, prof = t.cpu().numpy().astype(np.float64), pr.cpu().numpy()
     finally:
         N.gke1h_destroy(plan)
     return terms, prof
@@ -118,3 +121,38 @@ def test_nonfinite_input_is_reported():
     with pytest.raises(N.GkeError) as e:
         _run(wl, f)
     assert e.value.status == -5
+
+
+# ------------------------------------------------------------ FP32 variant
+# Operands, contractions, term spectra, transforms and stencils in FP32
+# (means, products and one-point sums in FP64).  The bar is 1e-5 of each
+# term's largest magnitude: FP32 rounding (6e-8) amplified by the
+# contraction over snapshots and terms and by the stencils, whose weights
+# grow like 1/dy near the walls; the errors measured on these grids are
+# recorded in the assertion messages.
+TOL32 = 1e-5
+
+
+@pytest.mark.parametrize("dims,host", [((16, 9, 7, 4), False), ((24, 6, 11, 3), True), ((256, 8, 9, 4), False)])
+def test_f32_parity_with_oracle(dims, host):
+    nx, ny, nz, ns = dims
+    wl = S.duct_small(nx, ny, nz, ns, wid=33)
+    ref = O1.full(S.duct_physical(wl), S.cgl_grid(ny), S.cgl_grid(nz), wl.Lx, wl.nu)
+    got, prof = _run(wl, S.duct_coefficients(wl), host=host, f32=True)
+    want = _triangle(ref["terms"])
+    for t, name in enumerate(O1.TERMS):
+        err = np.abs(got[t] - want[t]).max() / np.abs(want[t]).max()
+        assert err < TOL32, (name, err)
+
+
+def test_f32_against_f64_full_size():
+    """The benchmark's 256 x 33 x 33 duct: the FP32 variant against the FP64
+    path on every output value."""
+    wl = S.DUCT
+    f = S.duct_coefficients(wl)
+    ref, _ = _run(wl, f)
+    got, _ = _run(wl, f, f32=True)
+    errs = {}
+    for t, name in enumerate(O1.TERMS):
+        errs[name] = float(np.abs(got[t] - ref[t]).max() / np.abs(ref[t]).max())
+    assert max(errs.values()) < TOL32, errs
