@@ -639,6 +639,9 @@ def run_one_homog(args, world, rank, local):
         e2e = {"value": wl.npair * ns / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
                "h2d_bytes_per_step": int(f_h.numel() * 16), "d2h_bytes_per_step": int(t_h.numel() * 8)}
         del t_h
+    f32 = None
+    if not args.no_split:
+        f32 = run_f32_beside_1h(wl, ns, f_dev, terms, ms, y, z, stream)
     del terms
     N.gke1h_destroy(plan)
     pk, pk_kind = peaks()
@@ -660,10 +663,52 @@ def run_one_homog(args, world, rank, local):
     line = {"metric": METRIC_1H, "value": wl.npair * ns / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_1h(wl),
-            "roofline": roof, "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "e2e": e2e,
+            "f32": f32, "roofline": roof, "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()}, "e2e": e2e,
             "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_f32_beside_1h(wl, ns, f_dev, terms64, ms64, y, z, stream, steps=5, warmup=2):
+    """The FP32 variant on the same inputs: device time per pass, speed-up
+    over FP64, per-term maximum deviation from the FP64 result (relative to
+    each FP64 term's largest magnitude) and its correlator roofline."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    plan = N.gke1h_plan(wl.nx, wl.ny, wl.nz, wl.Lx, wl.nu, y, z, ns, stream=stream.cuda_stream,
+                        precision=N.GKE_PREC_F32)
+    t32 = torch.empty(tuple(terms64.shape), dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        N.gke1h_compute(plan, f_dev, ns, t32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        N.gke1h_compute(plan, f_dev, ns, t32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    N.gke1h_set_timing(plan, True)
+    N.gke1h_compute(plan, f_dev, ns, t32)
+    stage_ms = N.gke1h_stage_times(plan)
+    N.gke1h_destroy(plan)
+    err = {}
+    for t, name in enumerate(N.TERMS_1H):
+        ref = terms64[t]
+        err[name] = float("%.3g" % float((t32[t].double() - ref).abs().max() / ref.abs().max()))
+    del t32
+    pk, _ = peaks()
+    peak = N_SM * FP32_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    cms = stage_ms.get("correlate", 0.0)
+    flops = 8.0 * correlator_cmac_1h(wl, ns)
+    ach = flops / (cms / 1e3) / 1e12 if cms > 0 else 0.0
+    return {"value": wl.npair * ns / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 3),
+            "speedup_vs_f64": round(ms64 / ms, 2), "max_rel_err_vs_f64": err,
+            "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+            "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                         "frac": round(ach / peak, 4), "launch_ms": round(cms, 3), "stage": "correlate",
+                         "peak_source": "derived: 152 SM x 128 FFMA/clk x 2 flop x max SM clock"}}
 
 
 def run_reference_1h(args, world, rank):
