@@ -30,6 +30,20 @@ def test_reference_arm_json_line():
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
 
 
+def test_reference_arm_duct_json_line():
+    """The reference arm of the one-homogeneous-direction workload."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload",
+                        "duct_16x9x7_s4", "--steps", "1", "--warmup", "0", "--ref-points", "64"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["config"]["workload"] == "duct_16x9x7_s4"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
 def test_merge_command_line(tmp_path):
     from paper_1910_06409_gb300 import merge as M
     ny = 5

@@ -269,3 +269,23 @@ def test_planted_mistakes_are_caught(tmp_path, i):
     caught = (max(_closed_form_errors(lib)) > 1e-6 or max(_exchange_error(lib).values()) > 1e-6
               or max(_channel_errors(lib).values()) > 1e-6)
     assert caught, new
+
+
+def test_points_equal_full():
+    """The sampled mode (used by the full-size GPU test) gives the full
+    mode's components and terms, including the stencil parts it evaluates
+    from A at the neighbour pairs directly."""
+    ns, nx, ny, nz = 2, 8, 6, 7
+    phys = _random_fields(ns, nx, ny, nz, 31)
+    y, z = _grid(ny, 11), _grid(nz, 12)
+    ref = O1.full(phys, y, z, 2.0, 0.02)
+    P = ny * nz
+    rng = np.random.default_rng(4)
+    pts = [(0, 0, 0), (P - 1, 0, 3), (5, 40, 7), (17, 17, 4)] + [
+        (int(a), int(b), int(m)) for a, b, m in zip(rng.integers(0, P, 12), rng.integers(0, P, 12),
+                                                       rng.integers(0, nx, 12))]
+    got = O1.points(phys, y, z, 2.0, 0.02, pts)
+    for q, (a, b, m) in enumerate(pts):
+        np.testing.assert_allclose(got["comp"][q], ref["comp"][:, a, b, m], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(got["terms"][q], ref["terms"][:7, a, b, m], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(got["prof"], ref["prof"])
