@@ -669,6 +669,48 @@ def run_one_homog(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def one_homog_compact(steps=3, warmup=2):
+    """The duct workload's FP64 pass and the FP32 variant beside it, as a
+    compact summary for the channel benchmark's line (device-resident inputs,
+    CUDA events on the plan's stream)."""
+    import torch
+    import paper_1910_06409_gb300._native as N
+
+    wl = S.DUCT
+    ns = wl.nsnap
+    stream = torch.cuda.current_stream()
+    y, z = S.cgl_grid(wl.ny), S.cgl_grid(wl.nz)
+    f_dev = torch.from_numpy(S.duct_coefficients(wl)).cuda()
+    plan = N.gke1h_plan(wl.nx, wl.ny, wl.nz, wl.Lx, wl.nu, y, z, ns, stream=stream.cuda_stream)
+    terms = torch.empty((N.GKE1H_NTERM, wl.npair, wl.nx), dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        N.gke1h_compute(plan, f_dev, ns, terms)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        N.gke1h_compute(plan, f_dev, ns, terms)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    N.gke1h_set_timing(plan, True)
+    N.gke1h_compute(plan, f_dev, ns, terms)
+    stage_ms = N.gke1h_stage_times(plan)
+    N.gke1h_destroy(plan)
+    f32 = run_f32_beside_1h(wl, ns, f_dev, terms, ms, y, z, stream, steps=steps, warmup=1)
+    del terms, f_dev
+    torch.cuda.empty_cache()
+    pk, _ = peaks()
+    peak = N_SM * FP64_FLOP_PER_CLK_SM * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    cms = stage_ms.get("correlate", 0.0)
+    frac = 8.0 * correlator_cmac_1h(wl, ns) / (cms / 1e3) / 1e12 / peak if cms > 0 else None
+    return {"metric": METRIC_1H, "workload": wl.name, "value": wl.npair * ns / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": round(ms, 3), "correlator_fp64_frac": None if frac is None else round(frac, 4),
+            "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
+            "f32": {"value": f32["value"], "ms_per_step": f32["ms_per_step"],
+                    "speedup_vs_f64": f32["speedup_vs_f64"], "max_rel_err_vs_f64": f32["max_rel_err_vs_f64"]}}
+
+
 def run_f32_beside_1h(wl, ns, f_dev, terms64, ms64, y, z, stream, steps=5, warmup=2):
     """The FP32 variant on the same inputs: device time per pass, speed-up
     over FP64, per-term maximum deviation from the FP64 result (relative to
@@ -845,6 +887,13 @@ def run_ours(args, world, rank, local):
         split = run_split_beside(args, wl, ns, f_dev, terms, ms, barrier, world, "bf16x3", pinned)
         f32v = run_split_beside(args, wl, ns, f_dev, terms, ms, barrier, world, "f32")
     pinned = None
+    # the one-homogeneous-direction variant on its duct workload, compact
+    one_h = None
+    if args.precision == "f64" and not args.no_split and world == 1:
+        try:
+            one_h = one_homog_compact()
+        except Exception as e:          # a failure here must not lose the channel line
+            one_h = {"error": str(e)[:200]}
 
     # rooflines: every stage against its bound, the dominant stage reported as "roofline"
     pk, pk_kind = peaks()
@@ -866,7 +915,7 @@ def run_ours(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": {"f64": "f64", "bf16x3": "bf16x3/f32", "f32": "f32"}[args.precision],
                 "data": "synthetic",
-                "split_bf16x3": compact(split), "config": config_of(wl, args.precision),
+                "split_bf16x3": compact(split), "one_homog": one_h, "config": config_of(wl, args.precision),
                 "roofline": roof, "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "cpu_baseline": cpu,
                 "parallelism": f"replicas{world}", "fp32_cuda_cores": compact(f32v),
                 "stage_ms": {k: round(v, 3) for k, v in stage_ms.items()},
