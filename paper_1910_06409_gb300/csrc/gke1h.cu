@@ -424,8 +424,9 @@ k1_correlate(const cplx<TF>* __restrict__ X, int ns, int P, int nx, int nt, doub
 {
     typedef cplx<TF> C;
     constexpr int RB = 2;
-    __shared__ C As[SCH][CT];
-    __shared__ C Bs[SCH][CT];
+    constexpr int SC = sizeof(TF) == 4 ? 2 * SCH : SCH;     // snapshots per staged chunk
+    __shared__ C As[SC][CT];
+    __shared__ C Bs[SC][CT];
     const int nxh = nx / 2 + 1;
     const int m = blockIdx.y;
     int T1 = 0, rem = blockIdx.x;
@@ -449,43 +450,33 @@ k1_correlate(const cplx<TF>* __restrict__ X, int ns, int P, int nx, int nt, doub
             #pragma unroll
             for (int b = 0; b < RB; ++b) acc[a][b] = mk((TF)0, (TF)0);
         for (int t = 0; t < jb.nt; ++t) {
+            // the term's weight (real) scales its A operand as it is staged:
+            // conj(w a) b = w conj(a) b, so the sum goes straight into acc
             const TF wt = (TF)jb.w[t];
             const C* A = X + ((long long)jb.fa[t] * nxh + m) * ns * P;
             const C* B = X + ((long long)jb.fb[t] * nxh + m) * ns * P;
-            C part[RB][RB];
-            #pragma unroll
-            for (int a = 0; a < RB; ++a)
-                #pragma unroll
-                for (int b = 0; b < RB; ++b) part[a][b] = mk((TF)0, (TF)0);
-            for (int s0 = 0; s0 < ns; s0 += SCH) {
+            for (int s0 = 0; s0 < ns; s0 += SC) {
                 __syncthreads();
-                for (int e = threadIdx.x; e < SCH * CT; e += blockDim.x) {
+                for (int e = threadIdx.x; e < SC * CT; e += blockDim.x) {
                     const int ss = e / CT, yy = e - ss * CT, s = s0 + ss;
                     C va = mk((TF)0, (TF)0), vb = va;
-                    if (s < ns && T1 * CT + yy < P) va = A[(long long)s * P + T1 * CT + yy];
+                    if (s < ns && T1 * CT + yy < P) { va = A[(long long)s * P + T1 * CT + yy]; va.x *= wt; va.y *= wt; }
                     if (s < ns && T2 * CT + yy < P) vb = B[(long long)s * P + T2 * CT + yy];
                     As[ss][yy] = va;
                     Bs[ss][yy] = vb;
                 }
                 __syncthreads();
                 #pragma unroll
-                for (int ss = 0; ss < SCH; ++ss) {
+                for (int ss = 0; ss < SC; ++ss) {
                     C av[RB], bv[RB];
                     #pragma unroll
                     for (int i = 0; i < RB; ++i) { av[i] = As[ss][ty + 16 * i]; bv[i] = Bs[ss][tx + 16 * i]; }
                     #pragma unroll
                     for (int a = 0; a < RB; ++a)
                         #pragma unroll
-                        for (int b = 0; b < RB; ++b) cmac(part[a][b], av[a], bv[b]);
+                        for (int b = 0; b < RB; ++b) cmac(acc[a][b], av[a], bv[b]);
                 }
             }
-            #pragma unroll
-            for (int a = 0; a < RB; ++a)
-                #pragma unroll
-                for (int b = 0; b < RB; ++b) {
-                    acc[a][b].x = fma(wt, part[a][b].x, acc[a][b].x);
-                    acc[a][b].y = fma(wt, part[a][b].y, acc[a][b].y);
-                }
         }
         // the contraction into the term spectra (as add_job, one coefficient test per job)
         #pragma unroll
