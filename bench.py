@@ -558,7 +558,7 @@ METRIC_1H = "GKE one-homogeneous-direction (p1,p2)-pair correlations/s, FP64"
 # DRAM bytes of one k1_correlate launch on the small case duct_256x17x17_s16
 # (41,905 pairs), scaled in proportion to the pairs of the workload run
 # (profiles/k1_correlate_profile_duct_256x17x17_s16.md)
-NCU_CORR_1H = (0.745e9, 41905)
+NCU_CORR_1H = (0.749e9, 41905)
 
 
 def correlator_cmac_1h(wl, ns):
