@@ -4,7 +4,7 @@
 // The paper's method (Sec. 3) with Parseval in x only and the second
 // inhomogeneous direction z handled like the wall-normal one (Sec. 5): every
 // pair of cross-section points (p1, p2) plays the part of a (Y1, Y2) pair.
-// Stages of one evaluation, all FP64:
+// Stages of one evaluation (FP64 plans; FP32 plans as noted at the end):
 //   mean       k1_mean: U_f(p), the m_x = 0 coefficient averaged over the
 //              snapshots (Step 1); k1_grad: d_y U_i, d_z U_i by the stencils.
 //   products   k1_products, one CTA per point p: per snapshot the inverse x
@@ -25,9 +25,11 @@
 //   stencil    k1_stencil_a: the Step-3 parts -2 nu dA/dr_y, -2 nu dA/dr_z,
 //              -(nu/2) dA/dY, -(nu/2) dA/dZ (Eq. 10-11 in y and in z);
 //              k1_stencil_res: the residual's r_y, r_z, Y, Z divergences.
-//              FP32 variant: the spectra, transforms and stencils carry the
-//              correlation parts only; k1_offsets then adds each pair's
-//              rx-independent one-point parts (and their stencil parts) in
+//   FP32 plans: operands, contractions, spectra, transforms and stencils
+//              in FP32 (means, products pass and one-point sums in FP64);
+//              the spectra, transforms and stencils carry the correlation
+//              parts only; k1_offsets then adds each pair's rx-independent
+//              one-point parts (and their stencil parts), formed in
 //              FP64, so that FP32 storage does not round them.
 #include <cuda_runtime.h>
 
