@@ -105,3 +105,15 @@ def test_one_homog_plan_argument_errors(native):
     with pytest.raises(native.GkeError) as e:
         native.gke1h_plan(16, 9, 7, 1.0, 0.01, y[::-1].copy(), z, 2)
     assert e.value.status == -1 and "increasing" in str(e.value)
+
+
+def test_one_homog_precision_errors(native):
+    """Only GKE_PREC_F64 and GKE_PREC_F32 plans exist for one homogeneous
+    direction; the descriptor is refused before the device is touched."""
+    y, z = S.cgl_grid(9), S.cgl_grid(7)
+    with pytest.raises(native.GkeError) as e:
+        native.gke1h_plan(16, 9, 7, 1.0, 0.01, y, z, 2, precision=native.GKE_PREC_BF16X3)
+    assert e.value.status == -7
+    with pytest.raises(native.GkeError) as e:
+        native.gke1h_plan(16, 9, 7, 1.0, 0.01, y, z, 2, precision=5)
+    assert e.value.status == -1

@@ -156,3 +156,26 @@ def test_f32_against_f64_full_size():
     for t, name in enumerate(O1.TERMS):
         errs[name] = float(np.abs(got[t] - ref[t]).max() / np.abs(ref[t]).max())
     assert max(errs.values()) < TOL32, errs
+
+
+def test_snapshot_count_errors():
+    """nsnap outside [1, max_snap] and a missing output are refused before
+    any launch (GKE_ERR_ARG), and the plan stays usable."""
+    N = _native()
+    wl = S.duct_small(8, 5, 6, 2, wid=34)
+    f = torch.from_numpy(S.duct_coefficients(wl)).cuda()
+    plan = N.gke1h_plan(wl.nx, wl.ny, wl.nz, wl.Lx, wl.nu, S.cgl_grid(wl.ny), S.cgl_grid(wl.nz), wl.nsnap)
+    try:
+        t = torch.empty((N.GKE1H_NTERM, wl.npair, wl.nx), dtype=torch.float64, device="cuda")
+        for ns in (0, wl.nsnap + 1):
+            with pytest.raises(N.GkeError) as e:
+                N.gke1h_compute(plan, f, ns, t)
+            assert e.value.status == -1
+        with pytest.raises(N.GkeError) as e:
+            N.gke1h_compute(plan, f, wl.nsnap, None)
+        assert e.value.status == -1
+        N.gke1h_compute(plan, f, wl.nsnap, t)
+        torch.cuda.synchronize()
+        assert torch.isfinite(t).all()
+    finally:
+        N.gke1h_destroy(plan)
