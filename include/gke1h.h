@@ -107,6 +107,14 @@ gke_status gke1h_compute(gke1h_plan_t plan, const void* fields, int nsnap, void*
 /* Number of pairs, P (P + 1) / 2.                                           */
 long long gke1h_npair(gke1h_plan_t plan);
 
+/* Host utility (no plan, no GPU): the labels of the npair = P (P + 1) / 2
+ * output pairs of grids y[ny], z[nz], in output order (p1 <= p2, p1
+ * outer): the point indices p1[], p2[] (p = iy nz + iz) and the coordinates
+ * Y1 = y[p1 / nz], Z1 = z[p1 % nz], Y2, Z2.  Any output may be NULL.
+ * Returns npair, or -1 on bad arguments (NULL grids, ny or nz < 1).          */
+long long gke1h_pair_labels(int ny, int nz, const double* y, const double* z, int* p1, int* p2, double* Y1,
+                            double* Z1, double* Y2, double* Z2);
+
 /* Stage timing as for gke_set_timing / gke_stage_times (ms[GKE_NSTAGE]:
  * mean, products and one-point sums, correlate (with the per-pair term
  * spectra), combine (always 0), inverse transforms, stencils).             */

@@ -30,7 +30,8 @@ EXPORTS = ("gke_plan", "gke_accumulate_mean", "gke_set_mean", "gke_accumulate_sn
            "gke_restore", "gke_merge", "gke_fd_weights", "gke_set_timing", "gke_stage_times",
            "gke_launch_count", "gke_compute_noalloc", "gke_last_error", "gke_destroy",
            "gke_velocity_vorticity",
-           "gke1h_plan", "gke1h_compute", "gke1h_npair", "gke1h_set_timing", "gke1h_stage_times",
+           "gke1h_plan", "gke1h_compute", "gke1h_npair", "gke1h_pair_labels", "gke1h_set_timing",
+           "gke1h_stage_times",
            "gke1h_launch_count", "gke1h_last_error", "gke1h_destroy")
 # the variant with one homogeneous direction (include/gke1h.h)
 TERMS_1H = ("A", "Phi_x", "Phi_y", "Phi_z", "psi_y", "psi_z", "xi", "residual")
@@ -103,6 +104,7 @@ def lib():
             "gke1h_plan": (i, [ctypes.POINTER(gke1h_desc), vp, ctypes.POINTER(vp)]),
             "gke1h_compute": (i, [vp, vp, i, vp, vp]),
             "gke1h_npair": (ctypes.c_longlong, [vp]),
+            "gke1h_pair_labels": (ctypes.c_longlong, [i, i, dp, dp, vp, vp, vp, vp, vp, vp]),
             "gke1h_set_timing": (i, [vp, i]),
             "gke1h_stage_times": (i, [vp, vp]),
             "gke1h_launch_count": (ctypes.c_longlong, [vp]),
@@ -304,6 +306,23 @@ def gke1h_compute(plan, fields, nsnap, terms, profiles=None):
 
 def gke1h_npair(plan) -> int:
     return lib().gke1h_npair(plan)
+
+
+def gke1h_pair_labels(y, z):
+    """(p1, p2, Y1, Z1, Y2, Z2) arrays of the output pairs of grids y, z."""
+    import numpy as np
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    zz = np.ascontiguousarray(z, dtype=np.float64)
+    P = len(yy) * len(zz)
+    n = P * (P + 1) // 2
+    p1, p2 = np.zeros(n, dtype=np.int32), np.zeros(n, dtype=np.int32)
+    Y1, Z1, Y2, Z2 = (np.zeros(n) for _ in range(4))
+    dp = ctypes.POINTER(ctypes.c_double)
+    got = lib().gke1h_pair_labels(len(yy), len(zz), yy.ctypes.data_as(dp), zz.ctypes.data_as(dp), ptr(p1), ptr(p2),
+                                  ptr(Y1), ptr(Z1), ptr(Y2), ptr(Z2))
+    if got != n:
+        raise GkeError(-1, "bad arguments")
+    return p1, p2, Y1, Z1, Y2, Z2
 
 
 def gke1h_set_timing(plan, on: bool):

@@ -1158,6 +1158,24 @@ extern "C" gke_status gke1h_compute(gke1h_plan_t p, const void* fields, int nsna
 
 extern "C" long long gke1h_npair(gke1h_plan_t p) { return p ? p->npair : -1; }
 
+extern "C" long long gke1h_pair_labels(int ny, int nz, const double* y, const double* z, int* p1, int* p2,
+                                       double* Y1, double* Z1, double* Y2, double* Z2)
+{
+    if (!y || !z || ny < 1 || nz < 1) return -1;
+    const long long P = (long long)ny * nz;
+    long long k = 0;
+    for (long long a = 0; a < P; ++a)
+        for (long long b = a; b < P; ++b, ++k) {
+            if (p1) p1[k] = (int)a;
+            if (p2) p2[k] = (int)b;
+            if (Y1) Y1[k] = y[a / nz];
+            if (Z1) Z1[k] = z[a % nz];
+            if (Y2) Y2[k] = y[b / nz];
+            if (Z2) Z2[k] = z[b % nz];
+        }
+    return k;
+}
+
 extern "C" gke_status gke1h_set_timing(gke1h_plan_t p, int on)
 {
     if (!p) return GKE_ERR_ARG;

@@ -117,3 +117,17 @@ def test_one_homog_precision_errors(native):
     with pytest.raises(native.GkeError) as e:
         native.gke1h_plan(16, 9, 7, 1.0, 0.01, y, z, 2, precision=5)
     assert e.value.status == -1
+
+
+def test_one_homog_pair_labels(native):
+    """Output pair order of the one-direction path: p1 <= p2, row-major."""
+    y, z = S.cgl_grid(6), S.cgl_grid(5)
+    p1, p2, Y1, Z1, Y2, Z2 = native.gke1h_pair_labels(y, z)
+    i1, i2 = np.triu_indices(30)
+    np.testing.assert_array_equal(p1, i1)
+    np.testing.assert_array_equal(p2, i2)
+    np.testing.assert_array_equal(Y1, y[i1 // 5])
+    np.testing.assert_array_equal(Z2, z[i2 % 5])
+    np.testing.assert_array_equal(Z1, z[i1 % 5])
+    np.testing.assert_array_equal(Y2, y[i2 // 5])
+    assert native.lib().gke1h_pair_labels(0, 5, None, None, None, None, None, None, None, None) == -1
